@@ -1,0 +1,13 @@
+"""CPU oracle for the foveated renderer: slow, plain, float64.
+
+TEST INFRASTRUCTURE.  Only ``tests/``, ``__graft_entry__.smoke()`` and the
+``cpu_baseline`` / reference leg of ``bench.py`` may import, call or link
+anything under this directory.  The product path (the CUDA library and its
+Python binding) never does, and shares no code with it.
+
+Modules:
+  mask     -- Eq. 1-3: threshold table, hashed noise, sample mask, C_max, ids
+  march    -- FP64 emission-absorption ray marcher (C, OpenMP), dense / masked
+  net      -- FP64 U-Net forward / backward, kernel prediction + blend, loss, Adam
+  metrics  -- PSNR, SSIM
+"""

@@ -1,0 +1,270 @@
+"""Seeded synthetic inputs for the foveated volume renderer.
+
+This module produces the INPUT bytes that both the CUDA path and the CPU
+oracle consume: scalar volumes, transfer-function tables, cameras, focal
+points and network weights.  It holds none of the method's arithmetic (no
+mask, no ray marching, no network layer), only random draws and the
+procedural shapes that stand in for the paper's CT / simulation datasets
+(Table "datasets" of the paper), which are not available.
+
+Recipes (all seeded, all deterministic on CPU):
+
+* ``blob_volume``: sum of isotropic Gaussian blobs, centres U[sigma, n-sigma]^3,
+  sigma ~ U[4, 12] voxels, amplitude ~ U[0.2, 1], clamped to [0, 1].
+* ``value_noise_volume``: fractal value noise, ``octaves`` octaves with lattice
+  spacing 32, 16, 8, 4 voxels and amplitudes 1, 1/2, 1/4, 1/8, lattice values
+  U[0, 1], smoothstep-weighted trilinear interpolation, normalised to [0, 1].
+* ``turbulence_volume``: the same octaves but summing |2 n - 1|.
+* ``transfer_function``: 256-entry piecewise-linear RGBA table from 4 seeded
+  control points (position U[0,1] sorted, rgb U[0,1], alpha U[0, alpha_max])
+  plus implicit end points (0, rgb_0, 0) and (1, rgb_3, alpha_3).
+* ``orbit_camera``: perspective pinhole on a seeded orbit around the volume.
+* ``focal_point``: uniform in the central 50 % of the screen.
+* ``net_weights``: Kaiming-uniform weights, zero biases, in the flat order
+  given by ``NET_LAYERS``.
+
+Voxel layout everywhere is x fastest: ``vol[z, y, x]``.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+import torch
+
+# ---------------------------------------------------------------------------
+# volumes
+# ---------------------------------------------------------------------------
+
+
+def _interp_matrix(n: int, spacing: int, dtype=torch.float64, device="cpu") -> torch.Tensor:
+    """[n, L] matrix mapping lattice values to voxel-centre values along one
+    axis with smoothstep weights (value-noise interpolation)."""
+    nlat = n // spacing + 2
+    x = (torch.arange(n, dtype=dtype, device=device) + 0.5) / spacing
+    j0 = torch.floor(x)
+    t = x - j0
+    w = t * t * (3.0 - 2.0 * t)
+    m = torch.zeros(n, nlat, dtype=dtype, device=device)
+    idx = j0.long()
+    m[torch.arange(n, device=device), idx] = 1.0 - w
+    m[torch.arange(n, device=device), idx + 1] = w
+    return m
+
+
+def _noise_octave(n: int, spacing: int, gen: torch.Generator, device) -> torch.Tensor:
+    nlat = n // spacing + 2
+    lat = torch.rand(nlat, nlat, nlat, generator=gen, dtype=torch.float64).to(device)
+    m = _interp_matrix(n, spacing, device=device)
+    # separable smoothstep-trilinear: apply the 1-D matrix along x, y, z
+    v = torch.einsum("xa,cba->cbx", m, lat)
+    v = torch.einsum("yb,cbx->cyx", m, v)
+    v = torch.einsum("zc,cyx->zyx", m, v)
+    return v
+
+
+def value_noise_volume(n: int = 256, seed: int = 2, octaves: int = 4, base_spacing: int = 32,
+                       device="cpu", turbulence: bool = False) -> torch.Tensor:
+    """Fractal value noise in [0, 1], float64 tensor [n, n, n] on ``device``."""
+    gen = torch.Generator(device="cpu").manual_seed(int(seed))
+    acc = torch.zeros(n, n, n, dtype=torch.float64, device=device)
+    amp_sum = 0.0
+    for o in range(octaves):
+        spacing = max(1, base_spacing >> o)
+        amp = 0.5 ** o
+        nv = _noise_octave(n, spacing, gen, device)
+        if turbulence:
+            nv = (2.0 * nv - 1.0).abs()
+        acc += amp * nv
+        amp_sum += amp
+    return (acc / amp_sum).clamp_(0.0, 1.0)
+
+
+def turbulence_volume(n: int, seed: int, octaves: int = 4, device="cpu") -> torch.Tensor:
+    return value_noise_volume(n, seed, octaves, base_spacing=max(4, n // 8), device=device,
+                              turbulence=True)
+
+
+def blob_volume(n: int = 64, seed: int = 1, nblobs: int = 8, sigma_range=(4.0, 12.0),
+                amp_range=(0.2, 1.0), device="cpu") -> torch.Tensor:
+    """Sum of seeded isotropic Gaussian blobs, float64 [n, n, n] in [0, 1]."""
+    rng = np.random.default_rng(seed)
+    x = torch.arange(n, dtype=torch.float64, device=device) + 0.5
+    acc = torch.zeros(n, n, n, dtype=torch.float64, device=device)
+    scale = n / 64.0
+    for _ in range(nblobs):
+        sigma = rng.uniform(*sigma_range) * scale
+        c = rng.uniform(sigma, n - sigma, size=3)
+        a = rng.uniform(*amp_range)
+        gx = torch.exp(-0.5 * ((x - c[0]) / sigma) ** 2)
+        gy = torch.exp(-0.5 * ((x - c[1]) / sigma) ** 2)
+        gz = torch.exp(-0.5 * ((x - c[2]) / sigma) ** 2)
+        acc += a * gz[:, None, None] * gy[None, :, None] * gx[None, None, :]
+    return acc.clamp_(0.0, 1.0)
+
+
+def training_volume(n: int, seed: int, device="cpu") -> torch.Tensor:
+    """Blobs plus 4-octave turbulence, quantised to uint16 (stored as int32
+    carrier in torch since torch has no uint16 arithmetic on every version);
+    returns a torch.int16 tensor holding the uint16 bit pattern."""
+    b = blob_volume(n, seed, nblobs=8, device=device)
+    t = turbulence_volume(n, seed + 7919, device=device)
+    v = (0.65 * b + 0.35 * t).clamp_(0.0, 1.0)
+    q = torch.round(v * 65535.0).to(torch.int32)
+    return (q - 65536 * (q >= 32768).to(torch.int32)).to(torch.int16)
+
+
+# ---------------------------------------------------------------------------
+# transfer function, camera, focal point
+# ---------------------------------------------------------------------------
+
+
+def transfer_function(seed: int, n: int = 256, alpha_max: float = 0.5, npoints: int = 4) -> np.ndarray:
+    """[n, 4] float32 RGBA table, piecewise linear through seeded control points."""
+    rng = np.random.default_rng(seed)
+    xs = np.sort(rng.uniform(0.0, 1.0, npoints))
+    rgb = rng.uniform(0.0, 1.0, (npoints, 3))
+    al = rng.uniform(0.0, alpha_max, npoints)
+    px = np.concatenate([[0.0], xs, [1.0]])
+    prgb = np.concatenate([rgb[:1], rgb, rgb[-1:]], axis=0)
+    pa = np.concatenate([[0.0], al, al[-1:]])
+    g = np.arange(n, dtype=np.float64) / (n - 1)
+    out = np.empty((n, 4), dtype=np.float64)
+    for c in range(3):
+        out[:, c] = np.interp(g, px, prgb[:, c])
+    out[:, 3] = np.interp(g, px, pa)
+    return out.astype(np.float32)
+
+
+@dataclass
+class Camera:
+    eye: tuple
+    target: tuple
+    up: tuple
+    fov_y_deg: float
+    width: int
+    height: int
+
+
+def orbit_camera(seed: int, frame: int = 0, nframes: int = 64, width: int = 1920, height: int = 1080,
+                 fov_y_deg: float = 45.0, radius_factor: float = 1.8, extent=(1.0, 1.0, 1.0)) -> Camera:
+    """Seeded orbit: start azimuth U[0, 2 pi), elevation amplitude U[0.2, 0.6] rad,
+    one revolution per ``nframes`` frames, radius = radius_factor x box diagonal."""
+    rng = np.random.default_rng(seed)
+    az0 = rng.uniform(0.0, 2.0 * math.pi)
+    el_amp = rng.uniform(0.2, 0.6)
+    diag = math.sqrt(sum(e * e for e in extent))
+    r = radius_factor * diag
+    az = az0 + 2.0 * math.pi * frame / nframes
+    el = el_amp * math.sin(2.0 * math.pi * frame / nframes + 0.7)
+    eye = (r * math.cos(el) * math.cos(az), r * math.sin(el), r * math.cos(el) * math.sin(az))
+    return Camera(eye=eye, target=(0.0, 0.0, 0.0), up=(0.0, 1.0, 0.0), fov_y_deg=fov_y_deg,
+                  width=width, height=height)
+
+
+def random_camera(rng: np.random.Generator, width: int, height: int, rmin=0.9, rmax=1.8,
+                  fov_y_deg: float = 45.0) -> Camera:
+    """Random view direction on the sphere, random radius factor, small target jitter."""
+    v = rng.normal(size=3)
+    v /= np.linalg.norm(v)
+    r = rng.uniform(rmin, rmax) * math.sqrt(3.0)
+    tgt = rng.uniform(-0.15, 0.15, 3)
+    eye = tgt + r * v
+    up = (0.0, 1.0, 0.0) if abs(v[1]) < 0.95 else (1.0, 0.0, 0.0)
+    return Camera(eye=tuple(float(e) for e in eye), target=tuple(float(t) for t in tgt), up=up,
+                  fov_y_deg=fov_y_deg, width=width, height=height)
+
+
+def focal_point(seed: int, frame: int, width: int, height: int) -> tuple:
+    """Focal point in pixel units, uniform in the central 50 % of the screen."""
+    rng = np.random.default_rng([int(seed), int(frame)])
+    return (float(width * rng.uniform(0.25, 0.75)), float(height * rng.uniform(0.25, 0.75)))
+
+
+@dataclass
+class Foveation:
+    """Focal point in pixels; radius / falloff in fractions of the half diagonal."""
+    focal_px: tuple
+    fovea_radius: float = 0.10
+    falloff_sigma: float = 0.10
+    p_base: float = 0.05
+    seed: int = 0
+    frame: int = 0
+
+
+@dataclass
+class MarchParams:
+    step_vox: float = 0.5
+    term_alpha: float = 0.99
+    bg: tuple = (0.0, 0.0, 0.0)
+    shading: int = 1
+
+
+# ---------------------------------------------------------------------------
+# network weights
+# ---------------------------------------------------------------------------
+
+# (name, cin, cout, ksize) in the flat weight order; each layer stores
+# W[cout][cin][k][k] followed by b[cout], float32.
+NET_LAYERS = (
+    ("enc0a", 5, 16, 3), ("enc0b", 16, 16, 3),
+    ("enc1a", 16, 32, 3), ("enc1b", 32, 32, 3),
+    ("bota", 32, 64, 3), ("botb", 64, 64, 3),
+    ("dec1a", 96, 32, 3), ("dec1b", 32, 32, 3),
+    ("dec0a", 48, 16, 3), ("dec0b", 16, 16, 3),
+    ("head", 16, 29, 1),
+)
+
+
+def net_param_count(layers=NET_LAYERS) -> int:
+    return sum(co * ci * k * k + co for _, ci, co, k in layers)
+
+
+def net_weights(seed: int = 3, layers=NET_LAYERS) -> np.ndarray:
+    """Seeded Kaiming-uniform weights (bound sqrt(6 / fan_in)), zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for _, ci, co, k in layers:
+        bound = math.sqrt(6.0 / (ci * k * k))
+        parts.append(rng.uniform(-bound, bound, co * ci * k * k))
+        parts.append(np.zeros(co))
+    return np.concatenate(parts).astype(np.float32)
+
+
+def split_weights(flat: np.ndarray, layers=NET_LAYERS) -> dict:
+    """Views of the flat weight vector as {name: (W[co,ci,k,k], b[co])}."""
+    out, off = {}, 0
+    for name, ci, co, k in layers:
+        nw = co * ci * k * k
+        w = flat[off:off + nw].reshape(co, ci, k, k)
+        off += nw
+        b = flat[off:off + co]
+        off += co
+        out[name] = (w, b)
+    assert off == flat.size
+    return out
+
+
+# ---------------------------------------------------------------------------
+# named workloads
+# ---------------------------------------------------------------------------
+
+
+def dense_small_workload(seed: int = 1, frame: int = 0):
+    """64^3 float32 blobs, 128x128 camera, 4-point TF: the small dense case."""
+    vol = blob_volume(64, seed).to(torch.float32).numpy()
+    tf = transfer_function(seed, alpha_max=0.5)
+    cam = orbit_camera(seed, frame, width=128, height=128)
+    return vol, tf, cam, MarchParams(shading=0)
+
+
+def foveated_1080p_workload(seed: int = 2, frame: int = 0, n: int = 256, width: int = 1920,
+                            height: int = 1080, vol: np.ndarray | None = None):
+    """256^3 float32 fractal value noise, 1920x1080, Phong, step 0.5 voxel."""
+    if vol is None:
+        vol = value_noise_volume(n, seed).to(torch.float32).numpy()
+    tf = transfer_function(seed + 1000, alpha_max=0.08)
+    cam = orbit_camera(seed, frame, width=width, height=height)
+    fov = Foveation(focal_px=focal_point(seed, frame, width, height), seed=seed, frame=frame)
+    return vol, tf, cam, fov, MarchParams(shading=1)

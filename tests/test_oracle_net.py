@@ -1,0 +1,285 @@
+"""Pins for the oracle network, kernel prediction, loss and optimiser --
+against library routines (torch float64 on CPU), brute force, closed forms
+and finite differences.  No GPU."""
+import math
+
+import numpy as np
+import pytest
+import torch
+import torch.nn.functional as F
+
+from oracle import metrics
+from oracle import net as on
+from paper_2209_09965_gb300 import workloads as wl
+
+torch.set_default_dtype(torch.float64)
+
+
+def T(a):
+    return torch.from_numpy(np.asarray(a, np.float64))
+
+
+def test_conv_matches_direct_sum():
+    rng = np.random.default_rng(0)
+    x = rng.normal(size=(1, 2, 4, 5))
+    w = rng.normal(size=(3, 2, 3, 3))
+    b = rng.normal(size=3)
+    out = on.conv2d(x, w, b)
+    ref = np.zeros((1, 3, 4, 5))
+    for o in range(3):
+        for yy in range(4):
+            for xx in range(5):
+                s = b[o]
+                for c in range(2):
+                    for i in range(3):
+                        for j in range(3):
+                            sy, sx = yy + i - 1, xx + j - 1
+                            if 0 <= sy < 4 and 0 <= sx < 5:
+                                s += w[o, c, i, j] * x[0, c, sy, sx]
+                ref[0, o, yy, xx] = s
+    assert np.max(np.abs(out - ref)) < 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 3])
+def test_conv_and_grads_match_torch(k):
+    rng = np.random.default_rng(k)
+    x = rng.normal(size=(2, 5, 7, 6))
+    w = rng.normal(size=(4, 5, k, k))
+    b = rng.normal(size=4)
+    g = rng.normal(size=(2, 4, 7, 6))
+    xt, wt, bt = T(x).requires_grad_(), T(w).requires_grad_(), T(b).requires_grad_()
+    yt = F.conv2d(xt, wt, bt, padding=k // 2)
+    yt.backward(T(g))
+    assert np.max(np.abs(on.conv2d(x, w, b) - yt.detach().numpy())) < 1e-12
+    gx, gw, gb = on.conv2d_backward(x, w, g)
+    assert np.max(np.abs(gx - xt.grad.numpy())) < 1e-11
+    assert np.max(np.abs(gw - wt.grad.numpy())) < 1e-11
+    assert np.max(np.abs(gb - bt.grad.numpy())) < 1e-11
+
+
+def test_pool_and_upsample_match_torch():
+    rng = np.random.default_rng(1)
+    x = rng.normal(size=(2, 3, 6, 10))
+    assert np.max(np.abs(on.avgpool2(x) - F.avg_pool2d(T(x), 2).numpy())) < 1e-14
+    ref = F.interpolate(T(x), scale_factor=2, mode="bilinear", align_corners=False).numpy()
+    assert np.max(np.abs(on.upsample2(x) - ref)) < 1e-14
+    # adjoints
+    gu = rng.normal(size=(2, 3, 12, 20))
+    assert abs((on.upsample2(x) * gu).sum() - (x * on.upsample2_backward(gu, 6, 10)).sum()) < 1e-10
+    gp = rng.normal(size=(2, 3, 3, 5))
+    assert abs((on.avgpool2(x) * gp).sum() - (x * on.avgpool2_backward(gp)).sum()) < 1e-10
+
+
+def _head_and_sparse(rng, n=1, h=9, w=11, density=0.3):
+    head = rng.normal(size=(n, 29, h, w))
+    sp = np.zeros((n, 5, h, w))
+    m = rng.uniform(size=(n, h, w)) < density
+    sp[:, 0:4] = rng.uniform(size=(n, 4, h, w)) * m[:, None]
+    sp[:, 4] = m
+    return head, sp
+
+
+def test_kp_one_hot_is_shifted_copy():
+    rng = np.random.default_rng(2)
+    head, sp = _head_and_sparse(rng, density=1.0)                 # every pixel valid
+    dy, dx = 1, -2
+    q = (dy + 2) * 5 + (dx + 2)
+    head[:, 3:28] = -1e3
+    head[:, 3 + q] = 1e3
+    head[:, 28] = 1e3                                             # a = 1 -> pure KP
+    out, _ = on.kp_blend(head, sp)
+    h, w = sp.shape[2:]
+    inner = out[0, :, 0:h - dy, -dx:]                             # where p + q is inside the frame
+    assert np.max(np.abs(inner - sp[0, 0:3, dy:, 0:w + dx])) < 1e-12
+    head[:, 28] = -1e3                                            # a = 0 -> direct prediction
+    out, _ = on.kp_blend(head, sp)
+    assert np.max(np.abs(out - head[:, 0:3])) < 1e-12
+
+
+def test_kp_uniform_logits_is_masked_box_filter_and_empty_window_falls_back():
+    rng = np.random.default_rng(3)
+    head, sp = _head_and_sparse(rng, density=0.2)
+    head[:, 3:28] = 0.7
+    head[:, 28] = 50.0
+    out, _ = on.kp_blend(head, sp)
+    a = 1 / (1 + math.exp(-50.0))
+    h, w = sp.shape[2:]
+    for y in range(h):
+        for x in range(w):
+            ys = slice(max(0, y - 2), min(h, y + 3))
+            xs = slice(max(0, x - 2), min(w, x + 3))
+            m = sp[0, 4, ys, xs]
+            if m.sum() == 0:
+                exp = head[0, 0:3, y, x]
+            else:
+                kp = (sp[0, 0:3, ys, xs] * m).sum(axis=(1, 2)) / m.sum()
+                exp = a * kp + (1 - a) * head[0, 0:3, y, x]
+            assert np.max(np.abs(out[0, :, y, x] - exp)) < 1e-12
+
+
+def test_kp_blend_backward_finite_differences():
+    rng = np.random.default_rng(4)
+    head, sp = _head_and_sparse(rng, h=6, w=7, density=0.35)
+    g = rng.normal(size=(1, 3, 6, 7))
+    out, cache = on.kp_blend(head, sp)
+    gh = on.kp_blend_backward(g, cache)
+    eps = 1e-6
+    idx = [tuple(rng.integers(0, s) for s in head.shape) for _ in range(40)]
+    for i in idx:
+        hp, hm = head.copy(), head.copy()
+        hp[i] += eps
+        hm[i] -= eps
+        fd = ((on.kp_blend(hp, sp)[0] - on.kp_blend(hm, sp)[0]) * g).sum() / (2 * eps)
+        assert abs(fd - gh[i]) < 1e-7 * max(1.0, abs(fd))
+
+
+def _torch_forward(params, sparse):
+    """The same network written with torch library layers, float64."""
+    x = T(sparse)
+    p = {k: (T(w), T(b)) for k, (w, b) in params.items()}
+
+    def cbr(name, t):
+        return F.relu(F.conv2d(t, p[name][0], p[name][1], padding=1))
+
+    up = lambda t: F.interpolate(t, scale_factor=2, mode="bilinear", align_corners=False)
+    e0 = cbr("enc0b", cbr("enc0a", x))
+    e1 = cbr("enc1b", cbr("enc1a", F.avg_pool2d(e0, 2)))
+    bt = cbr("botb", cbr("bota", F.avg_pool2d(e1, 2)))
+    d1 = cbr("dec1b", cbr("dec1a", torch.cat([up(bt), e1], 1)))
+    d0 = cbr("dec0b", cbr("dec0a", torch.cat([up(d1), e0], 1)))
+    head = F.conv2d(d0, p["head"][0], p["head"][1])
+    rgb_d, logit, zl = head[:, 0:3], head[:, 3:28], head[:, 28:29]
+    wq = torch.softmax(logit, 1)
+    c = F.unfold(x[:, 0:3], 5, padding=2).view(x.shape[0], 3, 25, *x.shape[2:])
+    m = F.unfold(x[:, 4:5], 5, padding=2).view(x.shape[0], 25, *x.shape[2:])
+    den = (wq * m).sum(1, keepdim=True)
+    num = (wq[:, None] * m[:, None] * c).sum(2)
+    kp = torch.where(den >= 1e-12, num / den.clamp_min(1e-300), rgb_d)
+    a = torch.sigmoid(zl)
+    return a * kp + (1 - a) * rgb_d
+
+
+def _random_params(chans, seed):
+    rng = np.random.default_rng(seed)
+    params = {}
+    for name, ci, co, k in on.layer_table(chans):
+        params[name] = (rng.normal(size=(co, ci, k, k)) * math.sqrt(2.0 / (ci * k * k)),
+                        rng.normal(size=co) * 0.1)
+    return params
+
+
+def test_forward_matches_torch_composition():
+    params = on.unpack(wl.net_weights(seed=5))
+    rng = np.random.default_rng(6)
+    _, sp = _head_and_sparse(rng, n=2, h=16, w=24, density=0.25)
+    out = on.forward(params, sp)
+    ref = _torch_forward(params, sp).numpy()
+    assert np.max(np.abs(out - ref)) < 1e-11
+
+
+def test_forward_pads_to_multiple_of_four():
+    params = _random_params((4, 8, 8), 7)
+    rng = np.random.default_rng(8)
+    _, sp = _head_and_sparse(rng, n=1, h=10, w=13, density=0.4)
+    out = on.forward(params, sp)
+    big = np.zeros((1, 5, 12, 16))
+    big[:, :, :10, :13] = sp
+    ref = _torch_forward(params, big).numpy()[:, :, :10, :13]
+    assert out.shape == (1, 3, 10, 13) and np.max(np.abs(out - ref)) < 1e-11
+
+
+def test_backward_matches_autograd_and_finite_differences():
+    chans = (4, 8, 8)
+    params = _random_params(chans, 9)
+    rng = np.random.default_rng(10)
+    _, sp = _head_and_sparse(rng, n=2, h=8, w=8, density=0.4)
+    g = rng.normal(size=(2, 3, 8, 8))
+    out, cache = on.forward(params, sp, return_cache=True)
+    grads = on.backward(params, cache, g)
+    # autograd of the torch composition
+    tp = {k: (T(w).requires_grad_(), T(b).requires_grad_()) for k, (w, b) in params.items()}
+    import types
+    yt = _torch_forward({k: (v[0], v[1]) for k, v in params.items()}, sp)   # value check
+    assert np.max(np.abs(yt.numpy() - out)) < 1e-11
+    x = T(sp)
+
+    def fwd(pt):
+        def cbr(name, t):
+            return F.relu(F.conv2d(t, pt[name][0], pt[name][1], padding=1))
+        up = lambda t: F.interpolate(t, scale_factor=2, mode="bilinear", align_corners=False)
+        e0 = cbr("enc0b", cbr("enc0a", x))
+        e1 = cbr("enc1b", cbr("enc1a", F.avg_pool2d(e0, 2)))
+        bt = cbr("botb", cbr("bota", F.avg_pool2d(e1, 2)))
+        d1 = cbr("dec1b", cbr("dec1a", torch.cat([up(bt), e1], 1)))
+        d0 = cbr("dec0b", cbr("dec0a", torch.cat([up(d1), e0], 1)))
+        head = F.conv2d(d0, pt["head"][0], pt["head"][1])
+        rgb_d, logit, zl = head[:, 0:3], head[:, 3:28], head[:, 28:29]
+        wq = torch.softmax(logit, 1)
+        c = F.unfold(x[:, 0:3], 5, padding=2).view(x.shape[0], 3, 25, *x.shape[2:])
+        m = F.unfold(x[:, 4:5], 5, padding=2).view(x.shape[0], 25, *x.shape[2:])
+        den = (wq * m).sum(1, keepdim=True)
+        num = (wq[:, None] * m[:, None] * c).sum(2)
+        kp = torch.where(den >= 1e-12, num / den.clamp_min(1e-300), rgb_d)
+        a = torch.sigmoid(zl)
+        return a * kp + (1 - a) * rgb_d
+
+    (fwd(tp) * T(g)).sum().backward()
+    for name in params:
+        assert np.max(np.abs(grads[name][0] - tp[name][0].grad.numpy())) < 1e-10, name
+        assert np.max(np.abs(grads[name][1] - tp[name][1].grad.numpy())) < 1e-10, name
+    # finite differences on a few weights of every layer
+    eps = 1e-6
+    for name in params:
+        w = params[name][0]
+        for _ in range(3):
+            i = tuple(rng.integers(0, s) for s in w.shape)
+            old = w[i]
+            w[i] = old + eps
+            fp = (on.forward(params, sp) * g).sum()
+            w[i] = old - eps
+            fm = (on.forward(params, sp) * g).sum()
+            w[i] = old
+            fd = (fp - fm) / (2 * eps)
+            assert abs(fd - grads[name][0][i]) < 1e-6 * max(1.0, abs(fd)), name
+
+
+def test_loss_closed_form_and_finite_differences():
+    rng = np.random.default_rng(11)
+    t = rng.uniform(size=(2, 3, 6, 7))
+    # constant offset: the gradient terms vanish, L1 = |c|
+    loss, _ = on.loss_l1_grad(t + 0.25, t)
+    assert abs(loss - 0.25) < 1e-12
+    p = rng.uniform(size=t.shape)
+    loss, g = on.loss_l1_grad(p, t)
+    eps = 1e-7
+    for _ in range(30):
+        i = tuple(rng.integers(0, s) for s in p.shape)
+        pp, pm = p.copy(), p.copy()
+        pp[i] += eps
+        pm[i] -= eps
+        fd = (on.loss_l1_grad(pp, t)[0] - on.loss_l1_grad(pm, t)[0]) / (2 * eps)
+        assert abs(fd - g[i]) < 1e-6
+
+
+def test_adam_first_steps_closed_form():
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -0.01, 2.0])
+    p1, m, v = on.adam_step(p, g, np.zeros(3), np.zeros(3), 1, lr=1e-3)
+    # after one step m_hat = g and v_hat = g^2: the update is lr * g / (|g| + eps)
+    assert np.allclose(p1, p - 1e-3 * g / (np.abs(g) + 1e-8), atol=1e-15)
+    # a constant gradient keeps m_hat = g, v_hat = g^2 at every step
+    q, m, v = p, np.zeros(3), np.zeros(3)
+    for s in range(1, 6):
+        q, m, v = on.adam_step(q, g, m, v, s, lr=1e-3)
+    assert np.allclose(q, p - 5e-3 * g / (np.abs(g) + 1e-8), atol=1e-13)
+
+
+def test_psnr_ssim_closed_forms():
+    rng = np.random.default_rng(12)
+    a = rng.uniform(0.2, 0.8, (3, 32, 32))
+    assert abs(metrics.psnr(a, a + 0.01) - 40.0) < 1e-9
+    assert abs(metrics.ssim(a, a) - 1.0) < 1e-12
+    x = np.full((3, 20, 20), 0.3)
+    y = np.full((3, 20, 20), 0.6)
+    c1 = 0.01 ** 2
+    assert abs(metrics.ssim(x, y) - (2 * 0.18 + c1) / (0.09 + 0.36 + c1)) < 1e-12
