@@ -1,0 +1,247 @@
+/*
+ * fvn.h -- C ABI of the GB300 foveated volume renderer (libfvn.so).
+ *
+ * The hot path of FoVolNet (Bauer, Wu, Ma, arXiv 2209.09965): a seeded
+ * foveated sample mask and its compaction, a sparse ray march of a scalar
+ * volume through the compacted pixel list, and neural reconstruction of the
+ * full frame from the sparse samples.
+ *
+ * Conventions for every call:
+ *  - Buffers named "device" are CUDA device pointers owned by the caller; the
+ *    library never frees them.  Buffers named "host" are ordinary host memory
+ *    read before the call returns.
+ *  - Calls that take a `stream` (a cudaStream_t passed as void*, NULL = the
+ *    legacy default stream) only enqueue work on it and return without
+ *    synchronising the host, unless stated otherwise.
+ *  - Every argument is validated before anything is enqueued.  On error the
+ *    call returns a negative fvn_status, leaves every output untouched and
+ *    records a message for fvn_last_error().  Nothing throws across the ABI.
+ *  - Images are planar float32: [C][H][W], x fastest, y = 0 at the top.
+ *    Volumes are [nz][ny][nx], x fastest.
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef FVN_H
+#define FVN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    FVN_OK = 0,
+    FVN_ERR_ARG = -1,          /* invalid argument (null pointer, size, range) */
+    FVN_ERR_CUDA = -2,         /* a CUDA runtime call failed */
+    FVN_ERR_OOM = -3,          /* device or pinned allocation failed */
+    FVN_ERR_UNSUPPORTED = -4,  /* valid request this build does not support */
+    FVN_ERR_STATE = -5         /* call out of order (e.g. no weights loaded) */
+} fvn_status;
+
+/* Voxel types; integer types are normalised by their maximum (u8 / 255,
+ * u16 / 65535), floating types are clamped to [0, 1]. */
+typedef enum { FVN_U8 = 0, FVN_U16 = 1, FVN_F16 = 2, FVN_F32 = 3 } fvn_dtype;
+
+/* Arithmetic of the reconstruction convolutions (FP32 accumulation). */
+typedef enum { FVN_PREC_FP16 = 0, FVN_PREC_FP8 = 1 } fvn_precision;
+
+typedef struct fvn_ctx fvn_ctx;
+
+/* Scalar volume; data is a device pointer, 1 <= nx, ny, nz <= 4096. */
+typedef struct {
+    const void* data;
+    int nx, ny, nz;
+    int dtype;                 /* fvn_dtype */
+} fvn_volume;
+
+/* 1-D RGBA transfer function: device pointer to n entries of float RGBA
+ * (n in [2, 4096]); looked up at continuous index v (n - 1), linear between
+ * entries, alpha is the per-sample opacity. */
+typedef struct {
+    const float* rgba;
+    int n;
+} fvn_tf;
+
+/* Pinhole camera in world space; the volume box is centred at the origin and
+ * scaled so that its longest axis has length 1.  fov_y_deg in (0, 180);
+ * 1 <= width, height <= 16384. */
+typedef struct {
+    float eye[3], target[3], up[3];
+    float fov_y_deg;
+    int width, height;
+} fvn_camera;
+
+/* Foveation (Eq. 1-2 of the paper).  focal_px: focal point in pixels
+ * (pixel centres at x + 0.5).  fovea_radius r0 and falloff_sigma s are
+ * fractions of the half diagonal R = sqrt(W^2 + H^2) / 2; p_base is the
+ * periphery density P_b.  tau(d) = 1 for d <= r0, else
+ * P_b + (1 - P_b) exp(-((d - r0) / s)^2 / 2).  seed and frame select the
+ * per-pixel hashed noise. */
+typedef struct {
+    float focal_px[2];
+    float fovea_radius, falloff_sigma, p_base;
+    uint32_t seed, frame;
+} fvn_foveation;
+
+/* Ray-march parameters: step in voxels (> 0), early-termination opacity
+ * (0, 1], background colour, shading 0 = none, 1 = Phong headlight. */
+typedef struct {
+    float step_vox;
+    float term_alpha;
+    float bg[3];
+    int shading;
+} fvn_march_params;
+
+/* Create a context on the current CUDA device.  Synchronises the host. */
+fvn_status fvn_create(fvn_ctx** out);
+
+/* Free a context and everything it owns.  Synchronises the device. */
+fvn_status fvn_destroy(fvn_ctx* ctx);
+
+/* Last error message of this context (or of the calling thread when ctx is
+ * NULL); never NULL, "" when there was none. */
+const char* fvn_last_error(const fvn_ctx* ctx);
+
+/*
+ * fvn_make_mask -- binary sample mask and its stream compaction.
+ * Paper: "Sample Maps" (M(u, v) = 1 iff N(u, v) < tau(u, v); Eq. 1-2) and
+ * "Stream Compaction" (pack the valid pixels into a small buffer).
+ *
+ * N(u, v) is the top 24 bits of a 32-bit integer hash of (seed, frame, x, y);
+ * tau is taken from a 16384-entry table of floor(tau 2^24) indexed by the
+ * squared half-pixel distance to the focal point (built on the host in
+ * float64 and cached in the context).  The decision is integer-only and
+ * bit-exact.
+ *
+ * mask  : device uint8 [h][w], written 0 / 1 for every pixel.
+ * ids   : device int32 [>= w*h], receives the ids y*w + x of the sampled
+ *         pixels in an unspecified order (tile by tile).
+ * count : device int32, receives the number of sampled pixels.
+ * The first call with a new (w, h, r0, s, P_b) builds and uploads the table
+ * and is the only one that does host work beyond argument checks.
+ */
+fvn_status fvn_make_mask(fvn_ctx* ctx, const fvn_foveation* fov, int w, int h, uint8_t* mask,
+                         int32_t* ids, int32_t* count, void* stream);
+
+/*
+ * fvn_march -- emission-absorption ray march of the volume.
+ * Paper: "Foveated Rendering" / "Rendering" (a CUDA ray-marching DVR renderer
+ * casting one ray per valid pixel of the compacted buffer, with the results
+ * projected back to their full-frame positions).
+ *
+ * Per ray: slab test against the volume box, samples at
+ * t_k = max(t_enter, 0) + k step for every t_k < t_exit, trilinear fetch
+ * (clamp to edge), transfer-function lookup, optional Phong shading from
+ * central differences, front-to-back compositing, termination once
+ * A >= term_alpha.
+ *
+ * ids == NULL: dense march, every pixel of the camera frame.
+ * ids != NULL: sparse march of the *count pixel ids in ids (count is a
+ *              device int32, read by the kernel, so the call needs no host
+ *              synchronisation after fvn_make_mask); every other pixel of
+ *              rgbam is written 0.
+ * rgbam    : device float [5][h][w]: R, G, B (composited over bg), A, and the
+ *            mask channel M (1 where a ray was cast).
+ * nsamples : optional device uint64 accumulator; the number of classified
+ *            samples is ADDED to it (NULL to skip).
+ */
+fvn_status fvn_march(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
+                     const fvn_march_params* mp, const int32_t* ids, const int32_t* count, float* rgbam,
+                     unsigned long long* nsamples, void* stream);
+
+/*
+ * fvn_load_weights -- install reconstruction-network weights.
+ * Paper: "Model Precision & Optimization" (train in FP32, run with weights
+ * truncated to 16-bit).  host_w: host float32, the flat layer order
+ * enc0a(5->16) enc0b(16->16) enc1a(16->32) enc1b(32->32) bota(32->64)
+ * botb(64->64) dec1a(96->32) dec1b(32->32) dec0a(48->16) dec0b(16->16)
+ * head(16->29, 1x1); each layer W[cout][cin][k][k] then b[cout].  n must
+ * equal fvn_weight_count().  Converts to the FP16 and FP8 layouts of the
+ * kernels.  Synchronises the host.
+ */
+fvn_status fvn_load_weights(fvn_ctx* ctx, const float* host_w, size_t n);
+size_t fvn_weight_count(void);
+
+/*
+ * fvn_reconstruct -- full frame from the sparse samples.
+ * Paper: "Reconstruction Network" (a U-Net direct prediction "D" whose
+ * decoder state drives per-pixel kernel prediction "K"; Fig. "network
+ * architecture"), slim variant: 3 levels of 16/32/64 channels, two 3x3
+ * conv + ReLU per level, 2x2 average pooling, bilinear x2 up-sampling with
+ * skip concatenation, a 1x1 head giving the direct RGB, 25 kernel logits and
+ * a blend logit; softmax 5x5 kernel applied to the sparse samples normalised
+ * by the sampled weights, blended with the direct RGB by sigmoid(blend).
+ *
+ * rgbam : device float [5][h][w] from fvn_march (M = 0 where not sampled).
+ * rgb   : device float [3][h][w] output.
+ * precision : FVN_PREC_FP16 or FVN_PREC_FP8 operands, FP32 accumulation.
+ * Needs fvn_load_weights first (FVN_ERR_STATE otherwise).  Uses context
+ * workspace sized on first use for (w, h).
+ */
+fvn_status fvn_reconstruct(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
+                           void* stream);
+
+/*
+ * fvn_render -- one foveated frame: fvn_make_mask, sparse fvn_march and
+ * fvn_reconstruct on context workspace, no host synchronisation.
+ * Paper: Fig. "pipeline" (sample mask -> compaction -> sparse rendering ->
+ * reconstruction).  rgb: device float [3][h][w] with (w, h) from the camera.
+ * rgbam_out: optional device float [5][h][w] copy target for the sparse frame
+ * (NULL to skip).
+ */
+fvn_status fvn_render(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
+                      const fvn_foveation* fov, const fvn_march_params* mp, int precision, float* rgb,
+                      float* rgbam_out, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Training kernels (FP32, NCHW with batch N).  Paper: "Training" and "Loss"
+ * sections (the network is trained in FP32).  These are the forward and
+ * backward pieces behind the Python autograd functions; all pointers are
+ * device float32, all calls asynchronous on `stream`.
+ * ------------------------------------------------------------------------ */
+
+/* y = conv_k(x) + b, optional ReLU; x is the channel concatenation of xa
+ * [N][ca][H][W] and xb [N][cb][H][W] (xb may be NULL with cb = 0);
+ * w [cout][ca+cb][k][k]; k in {1, 3}, zero padding k/2. */
+fvn_status fvn_conv_fwd(const float* xa, int ca, const float* xb, int cb, int n, int h, int w_,
+                        const float* w, const float* b, int cout, int k, int relu, float* y, void* stream);
+
+/* Gradients of the layer above.  gy is dL/dy; y_relu (the saved ReLU output,
+ * or NULL for a layer without ReLU) masks it to dL/dz.  gxa / gxb receive
+ * dL/dx (overwritten; either may be NULL to skip), gw / gb receive dL/dw,
+ * dL/db (overwritten). */
+fvn_status fvn_conv_bwd(const float* xa, int ca, const float* xb, int cb, int n, int h, int w_,
+                        const float* w, int cout, int k, const float* gy, const float* y_relu,
+                        float* gxa, float* gxb, float* gw, float* gb, void* stream);
+
+/* 2x2 average pooling and its adjoint ([N][C][H][W] -> [N][C][H/2][W/2]). */
+fvn_status fvn_avgpool2_fwd(const float* x, int nc, int h, int w_, float* y, void* stream);
+fvn_status fvn_avgpool2_bwd(const float* gy, int nc, int h, int w_, float* gx, void* stream);
+
+/* Bilinear x2 up-sampling (half-pixel centres, edge clamp) and its adjoint;
+ * h, w are the input (coarse) sizes. */
+fvn_status fvn_upsample2_fwd(const float* x, int nc, int h, int w_, float* y, void* stream);
+fvn_status fvn_upsample2_bwd(const float* gy, int nc, int h, int w_, float* gx, void* stream);
+
+/* Kernel prediction + blend: head [N][29][H][W], sparse [N][5][H][W] ->
+ * out [N][3][H][W]; and dL/dhead from dL/dout. */
+fvn_status fvn_kp_blend_fwd(const float* head, const float* sparse, int n, int h, int w_, float* out,
+                            void* stream);
+fvn_status fvn_kp_blend_bwd(const float* head, const float* sparse, const float* gout, int n, int h,
+                            int w_, float* ghead, void* stream);
+
+/* L1 + lam * (L1 of x / y forward differences), each a mean over its own
+ * elements, over pred / target [N][C][H][W].  loss: device float scalar
+ * (overwritten); gpred: dL/dpred (overwritten). */
+fvn_status fvn_loss_l1grad(const float* pred, const float* target, int nc, int h, int w_, float lam,
+                           float* loss, float* gpred, void* stream);
+
+/* One bias-corrected Adam step on n parameters (step >= 1). */
+fvn_status fvn_adam_step(float* p, const float* g, float* m, float* v, size_t n, int step, float lr,
+                         float beta1, float beta2, float eps, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FVN_H */

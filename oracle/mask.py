@@ -76,7 +76,14 @@ def tau_of_distance(d: float, r0: float, s: float, p_base: float) -> float:
 
 
 def tau_table(width: int, height: int, fovea_radius: float, falloff_sigma: float, p_base: float):
-    """(tau_b as float64 [NBINS], T_b as uint32 [NBINS], shift)."""
+    """(tau_b as float64 [NBINS], T_b as uint32 [NBINS], shift).
+
+    The profile parameters are single-precision values (as they are passed
+    to the renderer); they are rounded to float32 first and the table is
+    then evaluated in float64."""
+    fovea_radius = float(np.float32(fovea_radius))
+    falloff_sigma = float(np.float32(falloff_sigma))
+    p_base = float(np.float32(p_base))
     shift = bin_shift(width, height)
     big_r = 0.5 * math.sqrt(float(width) * width + float(height) * height)
     taus = np.empty(NBINS, dtype=np.float64)

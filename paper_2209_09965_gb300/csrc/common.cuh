@@ -1,0 +1,111 @@
+// Shared host-side definitions of libfvn: the context, error reporting and
+// launch helpers.  Device kernels live in the per-stage .cu files.
+#pragma once
+
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+
+#include <string>
+
+#include "../../include/fvn.h"
+
+namespace fvn {
+
+constexpr int kLutBins = 16384;       // threshold-table entries
+constexpr int kLutCache = 8;          // distinct foveation profiles kept per context
+constexpr int kMaxSide = 16384;       // largest frame side accepted
+constexpr int kMaxVolSide = 4096;     // largest volume side accepted
+
+struct LutEntry {
+    bool valid = false;
+    int w = 0, h = 0;
+    float r0 = 0.f, s = 0.f, pb = 0.f;
+    int shift = 0;
+    uint64_t last_use = 0;
+    uint32_t* d_lut = nullptr;        // device copy, kLutBins entries
+    uint32_t* h_lut = nullptr;        // pinned host copy, never modified after upload
+};
+
+// Per-layer inference weights: FP16 in the shared-memory layout of the conv
+// kernels ([tap][cin/8][cout][8]) plus FP32 bias; FP8 copies with per-output
+// channel scales.
+struct ConvW {
+    int cin = 0, cin_pad = 0, cout = 0, k = 0;
+    __half* w16 = nullptr;
+    uint8_t* w8 = nullptr;            // e4m3, same layout as w16
+    float* scale8 = nullptr;          // per output channel dequantisation scale
+    float* bias = nullptr;
+};
+
+constexpr int kNumLayers = 11;
+
+struct ReconWorkspace {
+    int w = 0, h = 0;                 // frame the buffers were sized for
+    size_t bytes = 0;
+    void* base = nullptr;
+};
+
+struct RenderWorkspace {
+    int w = 0, h = 0;
+    uint8_t* mask = nullptr;
+    int32_t* ids = nullptr;
+    int32_t* count = nullptr;
+    float* rgbam = nullptr;
+};
+
+}  // namespace fvn
+
+struct fvn_ctx {
+    int device = 0;
+    int num_sms = 0;
+    std::string err;
+    fvn::LutEntry lut[fvn::kLutCache];
+    uint64_t lut_clock = 0;
+    int* d_ticket = nullptr;          // 64 march work-queue counters (stream-ordered reset)
+    unsigned ticket_ring = 0;         // next counter to use, so queued launches do not share one
+    bool has_weights = false;
+    fvn::ConvW layers[fvn::kNumLayers];
+    float* head_w = nullptr;          // FP32 [29][16] + [29] bias for the head / KP stage
+    float* d_act_scale = nullptr;     // FP8 per-layer activation scales
+    fvn::ReconWorkspace recon_ws;
+    fvn::RenderWorkspace render_ws;
+};
+
+namespace fvn {
+
+fvn_status set_error(fvn_ctx* ctx, fvn_status st, const char* fmt, ...);
+
+#define FVN_CHECK_ARG(ctx, cond, ...)                                   \
+    do {                                                                \
+        if (!(cond)) return ::fvn::set_error((ctx), FVN_ERR_ARG, __VA_ARGS__); \
+    } while (0)
+
+#define FVN_CUDA(ctx, call)                                                           \
+    do {                                                                              \
+        cudaError_t e_ = (call);                                                      \
+        if (e_ != cudaSuccess)                                                        \
+            return ::fvn::set_error((ctx), e_ == cudaErrorMemoryAllocation ? FVN_ERR_OOM : FVN_ERR_CUDA, \
+                                    "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Launch-error check after a kernel launch.
+#define FVN_LAUNCH_CHECK(ctx) FVN_CUDA((ctx), cudaGetLastError())
+
+fvn_status validate_volume(fvn_ctx* ctx, const fvn_volume* vol);
+fvn_status validate_camera(fvn_ctx* ctx, const fvn_camera* cam);
+
+// Stage entry points used by fvn_render (no argument validation).
+fvn_status make_mask_impl(fvn_ctx* ctx, const fvn_foveation* fov, int w, int h, uint8_t* mask, int32_t* ids,
+                          int32_t* count, cudaStream_t st);
+fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
+                      const fvn_march_params* mp, const int32_t* ids, const int32_t* count, float* rgbam,
+                      unsigned long long* nsamples, cudaStream_t st);
+fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
+                            cudaStream_t st);
+
+}  // namespace fvn

@@ -1,0 +1,148 @@
+// Context lifetime, error reporting, argument validation and the one-frame
+// driver fvn_render (mask -> compaction -> sparse march -> reconstruction,
+// the pipeline of the paper's Fig. "pipeline").
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include "common.cuh"
+
+namespace {
+thread_local std::string g_thread_err;
+}
+
+namespace fvn {
+
+fvn_status set_error(fvn_ctx* ctx, fvn_status st, const char* fmt, ...) {
+    char buf[1024];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx) ctx->err = buf;
+    g_thread_err = buf;
+    return st;
+}
+
+fvn_status validate_volume(fvn_ctx* ctx, const fvn_volume* vol) {
+    FVN_CHECK_ARG(ctx, vol != nullptr, "volume descriptor is NULL");
+    FVN_CHECK_ARG(ctx, vol->data != nullptr, "volume data pointer is NULL");
+    FVN_CHECK_ARG(ctx, vol->nx >= 1 && vol->ny >= 1 && vol->nz >= 1 && vol->nx <= kMaxVolSide &&
+                           vol->ny <= kMaxVolSide && vol->nz <= kMaxVolSide,
+                  "volume dims %d x %d x %d outside [1, %d]", vol->nx, vol->ny, vol->nz, kMaxVolSide);
+    FVN_CHECK_ARG(ctx, vol->dtype >= FVN_U8 && vol->dtype <= FVN_F32, "unknown volume dtype %d", vol->dtype);
+    return FVN_OK;
+}
+
+fvn_status validate_camera(fvn_ctx* ctx, const fvn_camera* cam) {
+    FVN_CHECK_ARG(ctx, cam != nullptr, "camera is NULL");
+    FVN_CHECK_ARG(ctx, cam->width >= 1 && cam->height >= 1 && cam->width <= kMaxSide && cam->height <= kMaxSide,
+                  "camera size %d x %d outside [1, %d]", cam->width, cam->height, kMaxSide);
+    FVN_CHECK_ARG(ctx, cam->fov_y_deg > 0.f && cam->fov_y_deg < 180.f, "fov_y_deg %g outside (0, 180)",
+                  (double)cam->fov_y_deg);
+    double f[3], up[3];
+    for (int a = 0; a < 3; ++a) {
+        f[a] = (double)cam->target[a] - cam->eye[a];
+        up[a] = cam->up[a];
+        FVN_CHECK_ARG(ctx, isfinite(cam->eye[a]) && isfinite(cam->target[a]) && isfinite(cam->up[a]),
+                      "camera has a non-finite coordinate");
+    }
+    double c[3] = {f[1] * up[2] - f[2] * up[1], f[2] * up[0] - f[0] * up[2], f[0] * up[1] - f[1] * up[0]};
+    double fl = sqrt(f[0] * f[0] + f[1] * f[1] + f[2] * f[2]);
+    double cl = sqrt(c[0] * c[0] + c[1] * c[1] + c[2] * c[2]);
+    FVN_CHECK_ARG(ctx, fl > 0.0, "camera eye equals target");
+    FVN_CHECK_ARG(ctx, cl > 1e-12 * fl, "camera up is parallel to the view direction");
+    return FVN_OK;
+}
+
+}  // namespace fvn
+
+using namespace fvn;
+
+extern "C" fvn_status fvn_create(fvn_ctx** out) {
+    if (!out) return set_error(nullptr, FVN_ERR_ARG, "out pointer is NULL");
+    fvn_ctx* ctx = new (std::nothrow) fvn_ctx();
+    if (!ctx) return set_error(nullptr, FVN_ERR_OOM, "host allocation failed");
+    cudaError_t e = cudaGetDevice(&ctx->device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_ticket, 64 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_ticket, 0, 64 * sizeof(int));
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) {
+        fvn_status st = set_error(nullptr, e == cudaErrorMemoryAllocation ? FVN_ERR_OOM : FVN_ERR_CUDA,
+                                  "fvn_create: %s", cudaGetErrorString(e));
+        if (ctx->d_ticket) cudaFree(ctx->d_ticket);
+        delete ctx;
+        return st;
+    }
+    *out = ctx;
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_destroy(fvn_ctx* ctx) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    cudaDeviceSynchronize();
+    for (auto& l : ctx->lut) {
+        if (l.d_lut) cudaFree(l.d_lut);
+        if (l.h_lut) cudaFreeHost(l.h_lut);
+    }
+    for (auto& L : ctx->layers) {
+        cudaFree(L.w16);
+        cudaFree(L.w8);
+        cudaFree(L.scale8);
+        cudaFree(L.bias);
+    }
+    cudaFree(ctx->head_w);
+    cudaFree(ctx->d_act_scale);
+    cudaFree(ctx->d_ticket);
+    cudaFree(ctx->recon_ws.base);
+    cudaFree(ctx->render_ws.mask);
+    cudaFree(ctx->render_ws.ids);
+    cudaFree(ctx->render_ws.count);
+    cudaFree(ctx->render_ws.rgbam);
+    delete ctx;
+    return FVN_OK;
+}
+
+extern "C" const char* fvn_last_error(const fvn_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_thread_err.c_str();
+}
+
+extern "C" fvn_status fvn_render(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
+                                 const fvn_foveation* fov, const fvn_march_params* mp, int precision, float* rgb,
+                                 float* rgbam_out, void* stream) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    fvn_status st;
+    if ((st = validate_volume(ctx, vol)) != FVN_OK) return st;
+    if ((st = validate_camera(ctx, cam)) != FVN_OK) return st;
+    FVN_CHECK_ARG(ctx, tf && tf->rgba && tf->n >= 2 && tf->n <= 4096, "bad transfer function");
+    FVN_CHECK_ARG(ctx, fov != nullptr, "foveation is NULL");
+    FVN_CHECK_ARG(ctx, mp && mp->step_vox > 0.f && mp->term_alpha > 0.f && mp->term_alpha <= 1.f,
+                  "bad march parameters");
+    FVN_CHECK_ARG(ctx, rgb != nullptr, "rgb output is NULL");
+    FVN_CHECK_ARG(ctx, precision == FVN_PREC_FP16 || precision == FVN_PREC_FP8, "unknown precision %d", precision);
+    if (!ctx->has_weights) return set_error(ctx, FVN_ERR_STATE, "no weights loaded (call fvn_load_weights)");
+    const int w = cam->width, h = cam->height;
+    RenderWorkspace& ws = ctx->render_ws;
+    if (ws.w != w || ws.h != h) {
+        // Growing the workspace is the one synchronising step of this call.
+        FVN_CUDA(ctx, cudaDeviceSynchronize());
+        cudaFree(ws.mask);
+        cudaFree(ws.ids);
+        cudaFree(ws.count);
+        cudaFree(ws.rgbam);
+        ws = RenderWorkspace();
+        size_t npix = (size_t)w * h;
+        FVN_CUDA(ctx, cudaMalloc(&ws.mask, npix));
+        FVN_CUDA(ctx, cudaMalloc(&ws.ids, npix * sizeof(int32_t)));
+        FVN_CUDA(ctx, cudaMalloc(&ws.count, sizeof(int32_t)));
+        FVN_CUDA(ctx, cudaMalloc(&ws.rgbam, 5 * npix * sizeof(float)));
+        ws.w = w;
+        ws.h = h;
+    }
+    cudaStream_t s = as_stream(stream);
+    float* rgbam = rgbam_out ? rgbam_out : ws.rgbam;
+    if ((st = make_mask_impl(ctx, fov, w, h, ws.mask, ws.ids, ws.count, s)) != FVN_OK) return st;
+    if ((st = march_impl(ctx, vol, tf, cam, mp, ws.ids, ws.count, rgbam, nullptr, s)) != FVN_OK) return st;
+    return reconstruct_impl(ctx, rgbam, w, h, precision, rgb, s);
+}

@@ -1,0 +1,547 @@
+// Training kernels of the reconstruction network, FP32 (paper: "Training",
+// "Loss", "Model Precision & Optimization": the network is trained in full
+// 32-bit precision).  NCHW tensors with a batch dimension.  These are the
+// forward / backward pieces called by the Python autograd functions.
+//
+//  - conv (k = 1 or 3, zero padding k/2) with bias and optional ReLU, whose
+//    input may be the channel concatenation of two tensors (skip
+//    connections without a copy);
+//  - its data gradient (the same kernel with flipped, transposed weights and
+//    the ReLU mask applied to the incoming gradient on load) and its weight /
+//    bias gradient (per-CTA partial sums over a pixel range, FP32 atomics);
+//  - 2x2 average pooling, bilinear x2 up-sampling and their adjoints;
+//  - the kernel-prediction blend forward / backward;
+//  - the L1 + image-gradient loss and Adam.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace fvn {
+
+constexpr int CT = 16;          // output-pixel tile side of the conv kernels
+constexpr int CO_T = 16;        // output channels per CTA
+
+// y[n][co][p] (+)= sum_ci sum_tap W(co, ci, tap) x[n][ci][p + tap - r]
+// FWD:  W(co, ci, tap) = w[co][ci][tap], x = xa ++ xb, epilogue bias / ReLU.
+// DGRAD: x = gy masked by (y_relu > 0), W(co', ci', tap) = w[ci'][co'][flip(tap)],
+//        output split into gxa / gxb.
+template <int K, bool DGRAD>
+__global__ void __launch_bounds__(CT* CT) conv_f32_kernel(const float* __restrict__ xa, int ca,
+                                                          const float* __restrict__ xb, int cb,
+                                                          const float* __restrict__ mask_src, int n_in, int h,
+                                                          int w_, const float* __restrict__ wt,
+                                                          const float* __restrict__ bias, int n_out, int relu,
+                                                          float* __restrict__ ya, int ya_c, float* __restrict__ yb,
+                                                          int tiles_x) {
+    constexpr int R = K / 2, HT = CT + 2 * R;
+    __shared__ float s_in[HT][HT + 1];
+    __shared__ float s_w[CO_T][K * K];
+    const int tile = blockIdx.x;
+    const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
+    const int co0 = blockIdx.y * CO_T;
+    const int n = blockIdx.z;
+    const int lx = threadIdx.x % CT, ly = threadIdx.x / CT;
+    const int x = tx * CT + lx, y = ty * CT + ly;
+    const long long hw = (long long)h * w_;
+    float acc[CO_T];
+#pragma unroll
+    for (int j = 0; j < CO_T; ++j) acc[j] = 0.f;
+    for (int ci = 0; ci < n_in; ++ci) {
+        const float* src;
+        const float* msk = nullptr;
+        if (!DGRAD) {
+            src = ci < ca ? xa + ((long long)n * ca + ci) * hw : xb + ((long long)n * cb + (ci - ca)) * hw;
+        } else {
+            src = xa + ((long long)n * n_in + ci) * hw;
+            if (mask_src) msk = mask_src + ((long long)n * n_in + ci) * hw;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < HT * HT; i += CT * CT) {
+            const int hy = i / HT, hx = i - hy * HT;
+            const int gy = ty * CT + hy - R, gx = tx * CT + hx - R;
+            float v = 0.f;
+            if (gy >= 0 && gx >= 0 && gy < h && gx < w_) {
+                const long long o = (long long)gy * w_ + gx;
+                v = __ldg(src + o);
+                if (msk && !(__ldg(msk + o) > 0.f)) v = 0.f;
+            }
+            s_in[hy][hx] = v;
+        }
+        for (int i = threadIdx.x; i < CO_T * K * K; i += CT * CT) {
+            const int j = i / (K * K), tap = i - j * K * K;
+            const int co = co0 + j;
+            float v = 0.f;
+            if (co < n_out) {
+                if (!DGRAD) v = __ldg(wt + ((long long)co * n_in + ci) * K * K + tap);
+                else v = __ldg(wt + ((long long)ci * n_out + co) * K * K + (K * K - 1 - tap));
+            }
+            s_w[j][tap] = v;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int ky = 0; ky < K; ++ky)
+#pragma unroll
+            for (int kx = 0; kx < K; ++kx) {
+                const float v = s_in[ly + ky][lx + kx];
+#pragma unroll
+                for (int j = 0; j < CO_T; ++j) acc[j] = fmaf(s_w[j][ky * K + kx], v, acc[j]);
+            }
+    }
+    if (x >= w_ || y >= h) return;
+    const long long p = (long long)y * w_ + x;
+#pragma unroll
+    for (int j = 0; j < CO_T; ++j) {
+        const int co = co0 + j;
+        if (co >= n_out) break;
+        float v = acc[j];
+        if (!DGRAD) {
+            v += __ldg(bias + co);
+            if (relu) v = fmaxf(v, 0.f);
+            ya[((long long)n * n_out + co) * hw + p] = v;
+        } else {
+            if (co < ya_c) {
+                if (ya) ya[((long long)n * ya_c + co) * hw + p] = v;
+            } else if (yb) {
+                yb[((long long)n * (n_out - ya_c) + (co - ya_c)) * hw + p] = v;
+            }
+        }
+    }
+}
+
+// dL/dw[co][ci][tap] and dL/db[co]: each CTA reduces a 16 x 16 (co, ci) block
+// over a range of 16 x 16 pixel tiles and adds its partial sums atomically.
+template <int K>
+__global__ void __launch_bounds__(256) conv_wgrad_kernel(const float* __restrict__ xa, int ca,
+                                                         const float* __restrict__ xb, int cb,
+                                                         const float* __restrict__ gy,
+                                                         const float* __restrict__ y_relu, int n, int h, int w_,
+                                                         int cout, float* __restrict__ gw, float* __restrict__ gb,
+                                                         int tiles_x, int tiles_per_img, int tiles_per_cta) {
+    constexpr int R = K / 2, HT = CT + 2 * R;
+    __shared__ float s_g[16][CT * CT];
+    __shared__ float s_x[16][HT * HT];
+    const int cin = ca + cb;
+    const int co0 = blockIdx.x * 16, ci0 = blockIdx.y * 16;
+    const int tco = threadIdx.x / 16, tci = threadIdx.x % 16;
+    const long long hw = (long long)h * w_;
+    float acc[K * K];
+#pragma unroll
+    for (int i = 0; i < K * K; ++i) acc[i] = 0.f;
+    float accb = 0.f;
+    const int total_tiles = n * tiles_per_img;
+    const int t_begin = blockIdx.z * tiles_per_cta;
+    const int t_end = std::min(total_tiles, t_begin + tiles_per_cta);
+    for (int tt = t_begin; tt < t_end; ++tt) {
+        const int img = tt / tiles_per_img, tl = tt - img * tiles_per_img;
+        const int ty = tl / tiles_x, tx = tl - ty * tiles_x;
+        __syncthreads();
+        for (int i = threadIdx.x; i < 16 * CT * CT; i += 256) {
+            const int j = i / (CT * CT), pp = i - j * CT * CT;
+            const int yy = ty * CT + pp / CT, xx = tx * CT + pp % CT;
+            const int co = co0 + j;
+            float v = 0.f;
+            if (co < cout && yy < h && xx < w_) {
+                const long long o = ((long long)img * cout + co) * hw + (long long)yy * w_ + xx;
+                v = __ldg(gy + o);
+                if (y_relu && !(__ldg(y_relu + o) > 0.f)) v = 0.f;
+            }
+            s_g[j][pp] = v;
+        }
+        for (int i = threadIdx.x; i < 16 * HT * HT; i += 256) {
+            const int j = i / (HT * HT), pp = i - j * HT * HT;
+            const int yy = ty * CT + pp / HT - R, xx = tx * CT + pp % HT - R;
+            const int ci = ci0 + j;
+            float v = 0.f;
+            if (ci < cin && yy >= 0 && xx >= 0 && yy < h && xx < w_) {
+                const float* src = ci < ca ? xa + ((long long)img * ca + ci) * hw
+                                           : xb + ((long long)img * cb + (ci - ca)) * hw;
+                v = __ldg(src + (long long)yy * w_ + xx);
+            }
+            s_x[j][pp] = v;
+        }
+        __syncthreads();
+        for (int pp = 0; pp < CT * CT; ++pp) {
+            const float g = s_g[tco][pp];
+            const int py = pp / CT, px = pp % CT;
+            accb += g;
+#pragma unroll
+            for (int ky = 0; ky < K; ++ky)
+#pragma unroll
+                for (int kx = 0; kx < K; ++kx) acc[ky * K + kx] = fmaf(g, s_x[tci][(py + ky) * HT + px + kx], acc[ky * K + kx]);
+        }
+    }
+    const int co = co0 + tco, ci = ci0 + tci;
+    if (co < cout && ci < cin) {
+#pragma unroll
+        for (int i = 0; i < K * K; ++i) atomicAdd(gw + ((long long)co * cin + ci) * K * K + i, acc[i]);
+    }
+    if (blockIdx.y == 0 && tci == 0 && co < cout) atomicAdd(gb + co, accb);
+}
+
+__global__ void avgpool2_fwd_kernel(const float* __restrict__ x, long long nc, int h, int w_, float* __restrict__ y) {
+    const int ho = h / 2, wo = w_ / 2;
+    const long long total = nc * ho * wo;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long c = i / ((long long)ho * wo);
+        const int r = (int)(i - c * ho * wo);
+        const int yy = r / wo, xx = r - yy * wo;
+        const float* p = x + c * h * w_ + (long long)(2 * yy) * w_ + 2 * xx;
+        y[i] = 0.25f * (p[0] + p[1] + p[w_] + p[w_ + 1]);
+    }
+}
+
+__global__ void avgpool2_bwd_kernel(const float* __restrict__ gy, long long nc, int h, int w_, float* __restrict__ gx) {
+    const int ho = h / 2, wo = w_ / 2;
+    const long long total = nc * h * w_;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long c = i / ((long long)h * w_);
+        const int r = (int)(i - c * h * w_);
+        const int yy = r / w_, xx = r - yy * w_;
+        gx[i] = 0.25f * gy[c * ho * wo + (long long)(yy / 2) * wo + xx / 2];
+    }
+}
+
+// weight of coarse index i in fine sample o of the x2 bilinear up-sampling
+// (source (o + 0.5)/2 - 0.5 clamped at 0, upper neighbour clamped to n - 1)
+__device__ __forceinline__ void up_src(int o, int n, int& i0, int& i1, float& t) {
+    float s = fmaxf((o + 0.5f) * 0.5f - 0.5f, 0.f);
+    i0 = (int)s;
+    t = s - i0;
+    i1 = min(i0 + 1, n - 1);
+}
+
+__global__ void upsample2_fwd_kernel(const float* __restrict__ x, long long nc, int h, int w_, float* __restrict__ y) {
+    const int H2 = 2 * h, W2 = 2 * w_;
+    const long long total = nc * H2 * W2;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long c = i / ((long long)H2 * W2);
+        const int r = (int)(i - c * H2 * W2);
+        const int oy = r / W2, ox = r - oy * W2;
+        int y0, y1, x0, x1;
+        float ty, tx;
+        up_src(oy, h, y0, y1, ty);
+        up_src(ox, w_, x0, x1, tx);
+        const float* p = x + c * h * w_;
+        const float top = (1.f - tx) * p[y0 * w_ + x0] + tx * p[y0 * w_ + x1];
+        const float bot = (1.f - tx) * p[y1 * w_ + x0] + tx * p[y1 * w_ + x1];
+        y[i] = (1.f - ty) * top + ty * bot;
+    }
+}
+
+__device__ __forceinline__ float up_weight(int o, int i, int n) {
+    int i0, i1;
+    float t;
+    up_src(o, n, i0, i1, t);
+    return (i0 == i ? 1.f - t : 0.f) + (i1 == i ? t : 0.f);
+}
+
+__global__ void upsample2_bwd_kernel(const float* __restrict__ gy, long long nc, int h, int w_, float* __restrict__ gx) {
+    const int H2 = 2 * h, W2 = 2 * w_;
+    const long long total = nc * h * w_;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long c = i / ((long long)h * w_);
+        const int r = (int)(i - c * h * w_);
+        const int iy = r / w_, ix = r - iy * w_;
+        const float* g = gy + c * H2 * W2;
+        float s = 0.f;
+        for (int oy = max(2 * iy - 1, 0); oy <= min(2 * iy + 2, H2 - 1); ++oy) {
+            const float wy = up_weight(oy, iy, h);
+            if (wy == 0.f) continue;
+            for (int ox = max(2 * ix - 1, 0); ox <= min(2 * ix + 2, W2 - 1); ++ox) {
+                const float wx = up_weight(ox, ix, w_);
+                if (wx != 0.f) s += wy * wx * g[(long long)oy * W2 + ox];
+            }
+        }
+        gx[i] = s;
+    }
+}
+
+// kernel prediction + blend, per pixel (see the inference head kernel)
+template <bool BWD>
+__global__ void kp_blend_kernel(const float* __restrict__ head, const float* __restrict__ sparse, int n, int h,
+                                int w_, const float* __restrict__ gout, float* __restrict__ out) {
+    const long long hw = (long long)h * w_;
+    const long long total = (long long)n * hw;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const long long img = i / hw;
+        const int r = (int)(i - img * hw);
+        const int y = r / w_, x = r - y * w_;
+        const float* hd = head + img * 29 * hw + r;
+        const float* sp = sparse + img * 5 * hw;
+        float lg[25], mx = -INFINITY;
+#pragma unroll
+        for (int q = 0; q < 25; ++q) {
+            lg[q] = hd[(3 + q) * hw];
+            mx = fmaxf(mx, lg[q]);
+        }
+        float es = 0.f;
+#pragma unroll
+        for (int q = 0; q < 25; ++q) {
+            lg[q] = expf(lg[q] - mx);
+            es += lg[q];
+        }
+        const float inv = 1.f / es;
+        float m[25], c[25][3];
+        float den = 0.f, num[3] = {0.f, 0.f, 0.f};
+#pragma unroll
+        for (int q = 0; q < 25; ++q) {
+            lg[q] *= inv;   // softmax weight w_q
+            const int yy = y + q / 5 - 2, xx = x + q % 5 - 2;
+            m[q] = 0.f;
+            c[q][0] = c[q][1] = c[q][2] = 0.f;
+            if (yy >= 0 && xx >= 0 && yy < h && xx < w_) {
+                const long long o = (long long)yy * w_ + xx;
+                m[q] = sp[4 * hw + o];
+                c[q][0] = sp[o];
+                c[q][1] = sp[hw + o];
+                c[q][2] = sp[2 * hw + o];
+            }
+            const float wm = lg[q] * m[q];
+            den += wm;
+            num[0] = fmaf(wm, c[q][0], num[0]);
+            num[1] = fmaf(wm, c[q][1], num[1]);
+            num[2] = fmaf(wm, c[q][2], num[2]);
+        }
+        const bool valid = den >= 1e-12f;
+        float rd[3] = {hd[0], hd[hw], hd[2 * hw]};
+        float kp[3];
+        for (int ch = 0; ch < 3; ++ch) kp[ch] = valid ? num[ch] / den : rd[ch];
+        const float z = hd[28 * hw];
+        const float a = 1.f / (1.f + expf(-z));
+        if (!BWD) {
+            float* o = out + img * 3 * hw + r;
+            for (int ch = 0; ch < 3; ++ch) o[ch * hw] = a * kp[ch] + (1.f - a) * rd[ch];
+        } else {
+            const float* go = gout + img * 3 * hw + r;
+            float* gh = out + img * 29 * hw + r;
+            float g[3] = {go[0], go[hw], go[2 * hw]};
+            float ga = 0.f;
+            for (int ch = 0; ch < 3; ++ch) {
+                ga += g[ch] * (kp[ch] - rd[ch]);
+                gh[ch * hw] = g[ch] * (1.f - a) + (valid ? 0.f : g[ch] * a);
+            }
+            gh[28 * hw] = ga * a * (1.f - a);
+            float dw[25], sdw = 0.f;
+#pragma unroll
+            for (int q = 0; q < 25; ++q) {
+                float s = 0.f;
+                if (valid)
+                    for (int ch = 0; ch < 3; ++ch) s += g[ch] * a * m[q] * (c[q][ch] - kp[ch]);
+                dw[q] = valid ? s / den : 0.f;
+                sdw += lg[q] * dw[q];
+            }
+#pragma unroll
+            for (int q = 0; q < 25; ++q) gh[(3 + q) * hw] = lg[q] * (dw[q] - sdw);
+        }
+    }
+}
+
+// L1 + lam (L1 of forward differences), gradient and (atomically summed) loss
+__global__ void loss_kernel(const float* __restrict__ p, const float* __restrict__ t, long long nc, int h, int w_,
+                            float lam, float* __restrict__ loss, float* __restrict__ g) {
+    const long long hw = (long long)h * w_;
+    const long long total = nc * hw;
+    const double n1 = (double)total, nx = (double)nc * h * (w_ - 1), ny = (double)nc * (h - 1) * w_;
+    const float i1 = (float)(1.0 / n1), ix = nx > 0 ? (float)(lam / nx) : 0.f, iy = ny > 0 ? (float)(lam / ny) : 0.f;
+    float part = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
+        const int r = (int)(i % hw);
+        const int y = r / w_, x = r - y * w_;
+        const float d = p[i] - t[i];
+        auto sgn = [](float v) { return (float)((v > 0.f) - (v < 0.f)); };
+        float gi = sgn(d) * i1;
+        part += fabsf(d) * i1;
+        if (x + 1 < w_) {
+            const float dx = (p[i + 1] - t[i + 1]) - d;
+            gi -= sgn(dx) * ix;
+            part += fabsf(dx) * ix;
+        }
+        if (x > 0) gi += sgn(d - (p[i - 1] - t[i - 1])) * ix;
+        if (y + 1 < h) {
+            const float dy = (p[i + w_] - t[i + w_]) - d;
+            gi -= sgn(dy) * iy;
+            part += fabsf(dy) * iy;
+        }
+        if (y > 0) gi += sgn(d - (p[i - w_] - t[i - w_])) * iy;
+        g[i] = gi;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(loss, part);
+}
+
+__global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps, float c1,
+                            float c2) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
+static int grid_for(fvn_ctx* ctx, long long total) {
+    long long g = (total + 255) / 256;
+    const long long cap = 32LL * (ctx->num_sms > 0 ? ctx->num_sms : 148);
+    return (int)std::max(1LL, std::min(g, cap));
+}
+
+}  // namespace fvn
+
+using namespace fvn;
+
+namespace {
+fvn_ctx* train_ctx() {
+    // Training kernels are context-free; a process-wide descriptor carries the
+    // SM count used for grid sizing and the error text.
+    static fvn_ctx* c = [] {
+        fvn_ctx* x = new fvn_ctx();
+        cudaGetDevice(&x->device);
+        cudaDeviceGetAttribute(&x->num_sms, cudaDevAttrMultiProcessorCount, x->device);
+        return x;
+    }();
+    return c;
+}
+}  // namespace
+
+extern "C" fvn_status fvn_conv_fwd(const float* xa, int ca, const float* xb, int cb, int n, int h, int w_,
+                                   const float* w, const float* b, int cout, int k, int relu, float* y, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, xa && w && b && y && (cb == 0 || xb), "null tensor");
+    FVN_CHECK_ARG(ctx, ca >= 1 && cb >= 0 && n >= 1 && h >= 1 && w_ >= 1 && cout >= 1, "bad sizes");
+    FVN_CHECK_ARG(ctx, k == 1 || k == 3, "k must be 1 or 3");
+    const int tiles_x = (w_ + CT - 1) / CT;
+    dim3 grid(tiles_x * ((h + CT - 1) / CT), (cout + CO_T - 1) / CO_T, n);
+    if (k == 3)
+        conv_f32_kernel<3, false><<<grid, CT * CT, 0, as_stream(stream)>>>(xa, ca, xb, cb, nullptr, ca + cb, h, w_, w,
+                                                                           b, cout, relu, y, cout, nullptr, tiles_x);
+    else
+        conv_f32_kernel<1, false><<<grid, CT * CT, 0, as_stream(stream)>>>(xa, ca, xb, cb, nullptr, ca + cb, h, w_, w,
+                                                                           b, cout, relu, y, cout, nullptr, tiles_x);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_conv_bwd(const float* xa, int ca, const float* xb, int cb, int n, int h, int w_,
+                                   const float* w, int cout, int k, const float* gy, const float* y_relu, float* gxa,
+                                   float* gxb, float* gw, float* gb, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    cudaStream_t st = as_stream(stream);
+    FVN_CHECK_ARG(ctx, xa && w && gy && (cb == 0 || xb), "null tensor");
+    FVN_CHECK_ARG(ctx, (gw == nullptr) == (gb == nullptr), "gw and gb must both be set or both NULL");
+    FVN_CHECK_ARG(ctx, ca >= 1 && cb >= 0 && n >= 1 && h >= 1 && w_ >= 1 && cout >= 1, "bad sizes");
+    FVN_CHECK_ARG(ctx, k == 1 || k == 3, "k must be 1 or 3");
+    const int cin = ca + cb;
+    const int tiles_x = (w_ + CT - 1) / CT;
+    const int tiles = tiles_x * ((h + CT - 1) / CT);
+    if (gxa || gxb) {
+        dim3 grid(tiles, (cin + CO_T - 1) / CO_T, n);
+        if (k == 3)
+            conv_f32_kernel<3, true><<<grid, CT * CT, 0, st>>>(gy, cout, nullptr, 0, y_relu, cout, h, w_, w, nullptr,
+                                                               cin, 0, gxa, ca, gxb, tiles_x);
+        else
+            conv_f32_kernel<1, true><<<grid, CT * CT, 0, st>>>(gy, cout, nullptr, 0, y_relu, cout, h, w_, w, nullptr,
+                                                               cin, 0, gxa, ca, gxb, tiles_x);
+        FVN_LAUNCH_CHECK(ctx);
+    }
+    if (gw) {
+        FVN_CUDA(ctx, cudaMemsetAsync(gw, 0, sizeof(float) * (size_t)cout * cin * k * k, st));
+        FVN_CUDA(ctx, cudaMemsetAsync(gb, 0, sizeof(float) * (size_t)cout, st));
+        const int gco = (cout + 15) / 16, gci = (cin + 15) / 16;
+        const long long total_tiles = (long long)n * tiles;
+        const int sms = train_ctx()->num_sms > 0 ? train_ctx()->num_sms : 148;
+        long long parts = std::max(1LL, (4LL * sms) / (gco * gci));
+        parts = std::min(parts, total_tiles);
+        const int per = (int)((total_tiles + parts - 1) / parts);
+        parts = (total_tiles + per - 1) / per;
+        dim3 grid(gco, gci, (unsigned)parts);
+        if (k == 3)
+            conv_wgrad_kernel<3><<<grid, 256, 0, st>>>(xa, ca, xb, cb, gy, y_relu, n, h, w_, cout, gw, gb, tiles_x,
+                                                       tiles, per);
+        else
+            conv_wgrad_kernel<1><<<grid, 256, 0, st>>>(xa, ca, xb, cb, gy, y_relu, n, h, w_, cout, gw, gb, tiles_x,
+                                                       tiles, per);
+        FVN_LAUNCH_CHECK(ctx);
+    }
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_avgpool2_fwd(const float* x, int nc, int h, int w_, float* y, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, x && y && nc >= 1 && h >= 2 && w_ >= 2 && h % 2 == 0 && w_ % 2 == 0, "bad pool arguments");
+    avgpool2_fwd_kernel<<<grid_for(train_ctx(), (long long)nc * h * w_ / 4), 256, 0, as_stream(stream)>>>(x, nc, h, w_, y);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_avgpool2_bwd(const float* gy, int nc, int h, int w_, float* gx, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, gx && gy && nc >= 1 && h >= 2 && w_ >= 2 && h % 2 == 0 && w_ % 2 == 0, "bad pool arguments");
+    avgpool2_bwd_kernel<<<grid_for(train_ctx(), (long long)nc * h * w_), 256, 0, as_stream(stream)>>>(gy, nc, h, w_, gx);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_upsample2_fwd(const float* x, int nc, int h, int w_, float* y, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, x && y && nc >= 1 && h >= 1 && w_ >= 1, "bad upsample arguments");
+    upsample2_fwd_kernel<<<grid_for(train_ctx(), (long long)nc * h * w_ * 4), 256, 0, as_stream(stream)>>>(x, nc, h, w_, y);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_upsample2_bwd(const float* gy, int nc, int h, int w_, float* gx, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, gx && gy && nc >= 1 && h >= 1 && w_ >= 1, "bad upsample arguments");
+    upsample2_bwd_kernel<<<grid_for(train_ctx(), (long long)nc * h * w_), 256, 0, as_stream(stream)>>>(gy, nc, h, w_, gx);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_kp_blend_fwd(const float* head, const float* sparse, int n, int h, int w_, float* out,
+                                       void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, head && sparse && out && n >= 1 && h >= 1 && w_ >= 1, "bad kp arguments");
+    kp_blend_kernel<false><<<grid_for(train_ctx(), (long long)n * h * w_), 256, 0, as_stream(stream)>>>(
+        head, sparse, n, h, w_, nullptr, out);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_kp_blend_bwd(const float* head, const float* sparse, const float* gout, int n, int h,
+                                       int w_, float* ghead, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, head && sparse && gout && ghead && n >= 1 && h >= 1 && w_ >= 1, "bad kp arguments");
+    kp_blend_kernel<true><<<grid_for(train_ctx(), (long long)n * h * w_), 256, 0, as_stream(stream)>>>(
+        head, sparse, n, h, w_, gout, ghead);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_loss_l1grad(const float* pred, const float* target, int nc, int h, int w_, float lam,
+                                      float* loss, float* gpred, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, pred && target && loss && gpred && nc >= 1 && h >= 1 && w_ >= 1, "bad loss arguments");
+    FVN_CUDA(ctx, cudaMemsetAsync(loss, 0, sizeof(float), as_stream(stream)));
+    loss_kernel<<<grid_for(train_ctx(), (long long)nc * h * w_), 256, 0, as_stream(stream)>>>(pred, target, nc, h, w_,
+                                                                                               lam, loss, gpred);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_adam_step(float* p, const float* g, float* m, float* v, size_t n, int step, float lr,
+                                    float beta1, float beta2, float eps, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, p && g && m && v && n >= 1 && step >= 1, "bad adam arguments");
+    const float c1 = (float)(1.0 - pow((double)beta1, step));
+    const float c2 = (float)(1.0 - pow((double)beta2, step));
+    adam_kernel<<<grid_for(train_ctx(), (long long)n), 256, 0, as_stream(stream)>>>(p, g, m, v, n, lr, beta1, beta2,
+                                                                                    eps, c1, c2);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}

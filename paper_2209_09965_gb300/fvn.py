@@ -1,0 +1,283 @@
+"""Python binding of libfvn (ctypes): argument marshalling only.
+
+Every function forwards torch CUDA tensors (as device pointers) and the
+current CUDA stream to the C ABI declared in ``include/fvn.h``; every step of
+the computation runs in the library's CUDA kernels.  There is no CPU
+fallback: if the library is missing or was not built, importing this module
+raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfvn.so")
+
+FVN_OK = 0
+U8, U16, F16, F32 = 0, 1, 2, 3
+PREC_FP16, PREC_FP8 = 0, 1
+
+_STATUS = {0: "FVN_OK", -1: "FVN_ERR_ARG", -2: "FVN_ERR_CUDA", -3: "FVN_ERR_OOM", -4: "FVN_ERR_UNSUPPORTED",
+           -5: "FVN_ERR_STATE"}
+
+# every symbol include/fvn.h declares
+EXPORTS = (
+    "fvn_create", "fvn_destroy", "fvn_last_error", "fvn_make_mask", "fvn_march", "fvn_load_weights",
+    "fvn_weight_count", "fvn_reconstruct", "fvn_render", "fvn_conv_fwd", "fvn_conv_bwd", "fvn_avgpool2_fwd",
+    "fvn_avgpool2_bwd", "fvn_upsample2_fwd", "fvn_upsample2_bwd", "fvn_kp_blend_fwd", "fvn_kp_blend_bwd",
+    "fvn_loss_l1grad", "fvn_adam_step",
+)
+
+
+class FvnError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Volume(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("dtype", ctypes.c_int)]
+
+
+class TF(ctypes.Structure):
+    _fields_ = [("rgba", ctypes.c_void_p), ("n", ctypes.c_int)]
+
+
+class CameraC(ctypes.Structure):
+    _fields_ = [("eye", ctypes.c_float * 3), ("target", ctypes.c_float * 3), ("up", ctypes.c_float * 3),
+                ("fov_y_deg", ctypes.c_float), ("width", ctypes.c_int), ("height", ctypes.c_int)]
+
+
+class FoveationC(ctypes.Structure):
+    _fields_ = [("focal_px", ctypes.c_float * 2), ("fovea_radius", ctypes.c_float),
+                ("falloff_sigma", ctypes.c_float), ("p_base", ctypes.c_float), ("seed", ctypes.c_uint32),
+                ("frame", ctypes.c_uint32)]
+
+
+class MarchParamsC(ctypes.Structure):
+    _fields_ = [("step_vox", ctypes.c_float), ("term_alpha", ctypes.c_float), ("bg", ctypes.c_float * 3),
+                ("shading", ctypes.c_int)]
+
+
+def _load():
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"libfvn is not built ({LIB_PATH} missing); run __graft_entry__.build()")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, I, F = ctypes.c_void_p, ctypes.c_int, ctypes.c_float
+    sig = {
+        "fvn_create": [P],
+        "fvn_destroy": [P],
+        "fvn_make_mask": [P, P, I, I, P, P, P, P],
+        "fvn_march": [P, P, P, P, P, P, P, P, P, P],
+        "fvn_load_weights": [P, P, ctypes.c_size_t],
+        "fvn_reconstruct": [P, P, I, I, I, P, P],
+        "fvn_render": [P, P, P, P, P, P, I, P, P, P],
+        "fvn_conv_fwd": [P, I, P, I, I, I, I, P, P, I, I, I, P, P],
+        "fvn_conv_bwd": [P, I, P, I, I, I, I, P, I, I, P, P, P, P, P, P, P],
+        "fvn_avgpool2_fwd": [P, I, I, I, P, P],
+        "fvn_avgpool2_bwd": [P, I, I, I, P, P],
+        "fvn_upsample2_fwd": [P, I, I, I, P, P],
+        "fvn_upsample2_bwd": [P, I, I, I, P, P],
+        "fvn_kp_blend_fwd": [P, P, I, I, I, P, P],
+        "fvn_kp_blend_bwd": [P, P, P, I, I, I, P, P],
+        "fvn_loss_l1grad": [P, P, I, I, I, F, P, P, P],
+        "fvn_adam_step": [P, P, P, P, ctypes.c_size_t, I, F, F, F, F, P],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_int
+    lib.fvn_last_error.argtypes = [P]
+    lib.fvn_last_error.restype = ctypes.c_char_p
+    lib.fvn_weight_count.argtypes = []
+    lib.fvn_weight_count.restype = ctypes.c_size_t
+    return lib
+
+
+lib = _load()
+
+
+def _check(status, ctx=None):
+    if status != FVN_OK:
+        msg = lib.fvn_last_error(ctx).decode(errors="replace")
+        raise FvnError(status, msg)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if isinstance(t, torch.Tensor):
+        if not t.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not t.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return ctypes.c_void_p(t.data_ptr())
+    return t
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+_DTYPE = {torch.uint8: U8, torch.int16: U16, torch.float16: F16, torch.float32: F32}
+if hasattr(torch, "uint16"):
+    _DTYPE[torch.uint16] = U16
+
+
+def volume(t: torch.Tensor) -> Volume:
+    """Descriptor of a [nz, ny, nx] CUDA volume (uint16 may be carried as int16)."""
+    if t.dim() != 3 or t.dtype not in _DTYPE:
+        raise ValueError("volume must be a 3-D uint8 / uint16 / float16 / float32 CUDA tensor")
+    nz, ny, nx = t.shape
+    return Volume(_ptr(t), nx, ny, nz, _DTYPE[t.dtype])
+
+
+def transfer_function(t: torch.Tensor) -> TF:
+    if t.dim() != 2 or t.shape[1] != 4 or t.dtype != torch.float32:
+        raise ValueError("transfer function must be a [n, 4] float32 CUDA tensor")
+    return TF(_ptr(t), t.shape[0])
+
+
+def camera(cam) -> CameraC:
+    c = CameraC()
+    c.eye[:] = [float(v) for v in cam.eye]
+    c.target[:] = [float(v) for v in cam.target]
+    c.up[:] = [float(v) for v in cam.up]
+    c.fov_y_deg = float(cam.fov_y_deg)
+    c.width, c.height = int(cam.width), int(cam.height)
+    return c
+
+
+def foveation(f) -> FoveationC:
+    c = FoveationC()
+    c.focal_px[:] = [float(f.focal_px[0]), float(f.focal_px[1])]
+    c.fovea_radius, c.falloff_sigma, c.p_base = float(f.fovea_radius), float(f.falloff_sigma), float(f.p_base)
+    c.seed, c.frame = int(f.seed) & 0xFFFFFFFF, int(f.frame) & 0xFFFFFFFF
+    return c
+
+
+def march_params(mp) -> MarchParamsC:
+    c = MarchParamsC()
+    c.step_vox, c.term_alpha = float(mp.step_vox), float(mp.term_alpha)
+    c.bg[:] = [float(v) for v in mp.bg]
+    c.shading = int(mp.shading)
+    return c
+
+
+def weight_count() -> int:
+    return int(lib.fvn_weight_count())
+
+
+class Context:
+    """Owns an fvn_ctx (threshold tables, work-queue counters, weights and
+    reconstruction workspace) on the current CUDA device."""
+
+    def __init__(self):
+        h = ctypes.c_void_p()
+        _check(lib.fvn_create(ctypes.byref(h)))
+        self.h = h
+
+    def close(self):
+        if self.h:
+            lib.fvn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def last_error(self) -> str:
+        return lib.fvn_last_error(self.h).decode(errors="replace")
+
+    def _chk(self, st):
+        _check(st, self.h)
+
+    # --- hot path -----------------------------------------------------------
+    def make_mask(self, fov, w, h, mask, ids, count, stream=None):
+        self._chk(lib.fvn_make_mask(self.h, ctypes.byref(foveation(fov)), int(w), int(h), _ptr(mask), _ptr(ids),
+                                    _ptr(count), _stream(stream)))
+
+    def march(self, vol, tf, cam, mp, rgbam, ids=None, count=None, nsamples=None, stream=None):
+        v, t, c, m = volume(vol), transfer_function(tf), camera(cam), march_params(mp)
+        self._chk(lib.fvn_march(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c), ctypes.byref(m),
+                                _ptr(ids), _ptr(count), _ptr(rgbam), _ptr(nsamples), _stream(stream)))
+
+    def load_weights(self, flat):
+        a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
+        self._chk(lib.fvn_load_weights(self.h, a.ctypes.data_as(ctypes.c_void_p), a.size))
+
+    def reconstruct(self, rgbam, w, h, rgb, precision=PREC_FP16, stream=None):
+        self._chk(lib.fvn_reconstruct(self.h, _ptr(rgbam), int(w), int(h), int(precision), _ptr(rgb),
+                                      _stream(stream)))
+
+    def render(self, vol, tf, cam, fov, mp, rgb, precision=PREC_FP16, rgbam_out=None, stream=None):
+        v, t, c, m = volume(vol), transfer_function(tf), camera(cam), march_params(mp)
+        f = foveation(fov)
+        self._chk(lib.fvn_render(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c), ctypes.byref(f),
+                                 ctypes.byref(m), int(precision), _ptr(rgb), _ptr(rgbam_out), _stream(stream)))
+
+
+# --- training kernels (context-free) -----------------------------------------
+def conv_fwd(xa, xb, w, b, relu, y, stream=None):
+    n, ca, h, wd = xa.shape
+    cb = 0 if xb is None else xb.shape[1]
+    cout, _, k, _ = w.shape
+    _check(lib.fvn_conv_fwd(_ptr(xa), ca, _ptr(xb), cb, n, h, wd, _ptr(w), _ptr(b), cout, k, int(bool(relu)),
+                            _ptr(y), _stream(stream)))
+
+
+def conv_bwd(xa, xb, w, gy, y_relu, gxa, gxb, gw, gb, stream=None):
+    n, ca, h, wd = xa.shape
+    cb = 0 if xb is None else xb.shape[1]
+    cout, _, k, _ = w.shape
+    _check(lib.fvn_conv_bwd(_ptr(xa), ca, _ptr(xb), cb, n, h, wd, _ptr(w), cout, k, _ptr(gy), _ptr(y_relu),
+                            _ptr(gxa), _ptr(gxb), _ptr(gw), _ptr(gb), _stream(stream)))
+
+
+def avgpool2_fwd(x, y, stream=None):
+    n, c, h, w = x.shape
+    _check(lib.fvn_avgpool2_fwd(_ptr(x), n * c, h, w, _ptr(y), _stream(stream)))
+
+
+def avgpool2_bwd(gy, gx, stream=None):
+    n, c, h, w = gx.shape
+    _check(lib.fvn_avgpool2_bwd(_ptr(gy), n * c, h, w, _ptr(gx), _stream(stream)))
+
+
+def upsample2_fwd(x, y, stream=None):
+    n, c, h, w = x.shape
+    _check(lib.fvn_upsample2_fwd(_ptr(x), n * c, h, w, _ptr(y), _stream(stream)))
+
+
+def upsample2_bwd(gy, gx, stream=None):
+    n, c, h, w = gx.shape
+    _check(lib.fvn_upsample2_bwd(_ptr(gy), n * c, h, w, _ptr(gx), _stream(stream)))
+
+
+def kp_blend_fwd(head, sparse, out, stream=None):
+    n, _, h, w = head.shape
+    _check(lib.fvn_kp_blend_fwd(_ptr(head), _ptr(sparse), n, h, w, _ptr(out), _stream(stream)))
+
+
+def kp_blend_bwd(head, sparse, gout, ghead, stream=None):
+    n, _, h, w = head.shape
+    _check(lib.fvn_kp_blend_bwd(_ptr(head), _ptr(sparse), _ptr(gout), n, h, w, _ptr(ghead), _stream(stream)))
+
+
+def loss_l1grad(pred, target, lam, loss, gpred, stream=None):
+    n, c, h, w = pred.shape
+    _check(lib.fvn_loss_l1grad(_ptr(pred), _ptr(target), n * c, h, w, float(lam), _ptr(loss), _ptr(gpred),
+                               _stream(stream)))
+
+
+def adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(lib.fvn_adam_step(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), int(step), float(lr), float(beta1),
+                             float(beta2), float(eps), _stream(stream)))

@@ -1,0 +1,175 @@
+"""GPU parity: fused mask + compaction (bit-exact) and the ray march
+(1e-4 max-abs) against the oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mask as omask
+from oracle import march as om
+from paper_2209_09965_gb300 import workloads as wl
+from tests.parity import march_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fvn():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2209_09965_gb300 import fvn as f
+    return f
+
+
+@pytest.fixture(scope="module")
+def ctx(fvn):
+    c = fvn.Context()
+    yield c
+    c.close()
+
+
+def gpu_mask(ctx, fov, w, h):
+    dev = torch.device("cuda")
+    mask = torch.full((h, w), 7, dtype=torch.uint8, device=dev)
+    ids = torch.full((w * h,), -1, dtype=torch.int32, device=dev)
+    count = torch.full((1,), -5, dtype=torch.int32, device=dev)
+    ctx.make_mask(fov, w, h, mask, ids, count)
+    torch.cuda.synchronize()
+    n = int(count.item())
+    return mask.cpu().numpy(), ids[:n].cpu().numpy(), n, ids.cpu().numpy()
+
+
+@pytest.mark.parametrize("w,h,seed,frame,fp", [
+    (1920, 1080, 2, 0, (960.0, 540.0)),
+    (1920, 1080, 2, 17, (500.5, 300.25)),
+    (1920, 1080, 99, 63, (1600.0, 900.0)),
+    (1280, 720, 4, 5, (-20.0, 800.0)),          # focal point outside: clamped
+    (3840, 2160, 7, 1, (1000.0, 1000.0)),
+    (97, 61, 1, 2, (40.0, 20.0)),               # ragged: not a multiple of the 32 x 8 tile
+    (1, 1, 3, 3, (0.5, 0.5)),
+    (1, 300, 3, 4, (0.5, 150.0)),
+    (333, 1, 3, 4, (100.0, 0.5)),
+])
+def test_mask_bit_exact(ctx, fvn, w, h, seed, frame, fp):
+    fov = wl.Foveation(focal_px=fp, seed=seed, frame=frame)
+    m, ids, n, ids_full = gpu_mask(ctx, fov, w, h)
+    m_ref, ids_ref, cmax = omask.make_mask(w, h, fp, seed=seed, frame=frame)
+    assert np.array_equal(m, m_ref)
+    assert n == ids_ref.size
+    assert np.array_equal(np.sort(ids), ids_ref)          # order is unspecified: compare as sets
+    assert np.all(ids_full[n:] == -1)                     # nothing written past count
+
+
+@pytest.mark.parametrize("pb,r0,s", [(1.0, 0.1, 0.1), (0.0, 0.0, 0.0), (0.3, 0.25, 0.05)])
+def test_mask_profiles(ctx, pb, r0, s):
+    fov = wl.Foveation(focal_px=(321.0, 123.0), fovea_radius=r0, falloff_sigma=s, p_base=pb, seed=8, frame=9)
+    m, ids, n, _ = gpu_mask(ctx, fov, 640, 360)
+    m_ref, ids_ref, _ = omask.make_mask(640, 360, fov.focal_px, r0, s, pb, seed=8, frame=9)
+    assert np.array_equal(m, m_ref) and np.array_equal(np.sort(ids), ids_ref)
+    if pb == 1.0:
+        assert n == 640 * 360
+
+
+def run_march(ctx, vol, tf, cam, mp, ids=None):
+    dev = torch.device("cuda")
+    v = torch.from_numpy(np.ascontiguousarray(vol)).to(dev)
+    t = torch.from_numpy(tf).to(dev)
+    out = torch.full((5, cam.height, cam.width), 123.0, dtype=torch.float32, device=dev)
+    ns = torch.zeros(1, dtype=torch.int64, device=dev)
+    if ids is None:
+        ctx.march(v, t, cam, mp, out, nsamples=ns)
+    else:
+        ids = np.asarray(ids, np.int32)
+        i = torch.from_numpy(ids if ids.size else np.zeros(1, np.int32)).to(dev)
+        c = torch.tensor([ids.size], dtype=torch.int32, device=dev)
+        ctx.march(v, t, cam, mp, out, ids=i, count=c, nsamples=ns)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), int(ns.item())
+
+
+def test_march_dense_small_blobs(ctx):
+    vol, tf, cam, mp = wl.dense_small_workload(seed=1)
+    out, ns = run_march(ctx, vol, tf, cam, mp)
+    err, namb = march_parity(vol, tf, cam, mp, out)
+    _, amb, ns_ref = om.march(vol, tf, cam, mp)
+    assert abs(ns - ns_ref) <= 2 * max(1, namb)
+    assert np.all(out[4] == 1.0)
+
+
+@pytest.mark.parametrize("shading", [0, 1])
+@pytest.mark.parametrize("frame", [0, 21])
+def test_march_dense_small_blobs_frames(ctx, shading, frame):
+    vol, tf, cam, mp = wl.dense_small_workload(seed=1, frame=frame)
+    mp = wl.MarchParams(shading=shading)
+    out, _ = run_march(ctx, vol, tf, cam, mp)
+    march_parity(vol, tf, cam, mp, out)
+
+
+@pytest.mark.parametrize("dtype", ["u8", "u16", "f16", "f32"])
+def test_march_volume_dtypes(ctx, dtype):
+    base = wl.value_noise_volume(40, seed=3, base_spacing=8).numpy()
+    vol = {"u8": np.round(base * 255).astype(np.uint8), "u16": np.round(base * 65535).astype(np.uint16),
+           "f16": base.astype(np.float16), "f32": base.astype(np.float32)}[dtype]
+    vol_t = vol.view(np.int16) if dtype == "u16" else vol
+    tf = wl.transfer_function(4, alpha_max=0.15)
+    cam = wl.orbit_camera(3, 2, width=72, height=40)
+    mp = wl.MarchParams(shading=1)
+    out, _ = run_march(ctx, vol_t, tf, cam, mp)
+    march_parity(vol, tf, cam, mp, out)
+
+
+@pytest.mark.parametrize("n,seed", [(2, 0), (3, 1), (4, 2), (4, 3)])
+def test_march_tiny_grids_random_cameras(ctx, n, seed):
+    rng = np.random.default_rng(seed)
+    vol = rng.uniform(0, 1, (n, n + 1, n)).astype(np.float32)
+    tf = np.zeros((256, 4), np.float32)
+    tf[:, :3] = rng.uniform(0, 1, 3)
+    tf[:, 0] = np.linspace(0.1, 0.9, 256)
+    tf[:, 3] = np.linspace(0.0, 0.6, 256)
+    for k in range(4):
+        v = rng.normal(size=3)
+        r = [1.6, 0.3, 0.05, 2.5][k]           # outside, inside, near centre, far
+        eye = tuple(r * v / np.linalg.norm(v))
+        cam = wl.Camera(eye=eye, target=(0.02, -0.03, 0.01), up=(0, 1, 0), fov_y_deg=60.0, width=13, height=9)
+        mp = wl.MarchParams(0.5, 0.95, (0.1, 0.2, 0.3), k % 2)
+        out, _ = run_march(ctx, vol, tf, cam, mp)
+        march_parity(vol, tf, cam, mp, out, max_amb_frac=0.05)
+
+
+def test_march_sparse_1080p_full_frame(ctx):
+    vol, tf, cam, fov, mp = wl.foveated_1080p_workload(seed=2, frame=0)
+    _, ids, _ = omask.make_mask(1920, 1080, fov.focal_px, seed=fov.seed, frame=fov.frame)
+    perm = np.random.default_rng(0).permutation(ids)      # any order
+    out, ns = run_march(ctx, vol, tf, cam, mp, ids=perm)
+    err, namb = march_parity(vol, tf, cam, mp, out, ids=ids)
+    flat = out.reshape(5, -1)
+    rest = np.setdiff1d(np.arange(1920 * 1080), ids)
+    assert np.all(flat[:, rest] == 0.0)
+    assert np.all(flat[4, ids] == 1.0)
+
+
+def test_march_dense_1080p_sampled(ctx):
+    vol, tf, cam, fov, mp = wl.foveated_1080p_workload(seed=3, frame=5)
+    out, ns = run_march(ctx, vol, tf, cam, mp)
+    sample = np.sort(np.random.default_rng(1).choice(1920 * 1080, 60000, replace=False)).astype(np.int32)
+    march_parity(vol, tf, cam, mp, out, ids=sample)
+    assert ns > 0
+
+
+def test_march_empty_id_list(ctx):
+    vol, tf, cam, mp = wl.dense_small_workload(seed=1)
+    out, ns = run_march(ctx, vol, tf, cam, mp, ids=np.zeros(0, np.int32))
+    assert ns == 0 and np.all(out == 0.0)
+
+
+def test_march_argument_errors(ctx, fvn):
+    vol, tf, cam, mp = wl.dense_small_workload(seed=1)
+    dev = torch.device("cuda")
+    v = torch.from_numpy(vol).to(dev)
+    t = torch.from_numpy(tf).to(dev)
+    out = torch.zeros(5, cam.height, cam.width, device=dev)
+    bad = wl.MarchParams(step_vox=0.0)
+    with pytest.raises(fvn.FvnError, match="step_vox"):
+        ctx.march(v, t, cam, bad, out)
+    cam2 = wl.Camera(eye=(1, 1, 1), target=(1, 1, 1), up=(0, 1, 0), fov_y_deg=45, width=8, height=8)
+    with pytest.raises(fvn.FvnError, match="eye equals target"):
+        ctx.march(v, t, cam2, mp, out)
