@@ -65,26 +65,82 @@ __device__ __forceinline__ float load_norm<__half>(const __half* p) {
     return __saturatef(__half2float(__ldg(p)));
 }
 
-template <typename T, typename I>
-__device__ __forceinline__ float trilinear(const T* __restrict__ v, int nx, int ny, int nz, float x, float y,
-                                           float z) {
-    const float ux = x - 0.5f, uy = y - 0.5f, uz = z - 0.5f;
-    const float fx = floorf(ux), fy = floorf(uy), fz = floorf(uz);
-    const float tx = ux - fx, ty = uy - fy, tz = uz - fz;
-    const int ix = (int)fx, iy = (int)fy, iz = (int)fz;
-    const int x0 = min(max(ix, 0), nx - 1), x1 = min(max(ix + 1, 0), nx - 1);
-    const int y0 = min(max(iy, 0), ny - 1), y1 = min(max(iy + 1, 0), ny - 1);
-    const int z0 = min(max(iz, 0), nz - 1), z1 = min(max(iz + 1, 0), nz - 1);
-    const I r00 = ((I)z0 * ny + y0) * nx, r01 = ((I)z0 * ny + y1) * nx;
-    const I r10 = ((I)z1 * ny + y0) * nx, r11 = ((I)z1 * ny + y1) * nx;
-    const float v000 = load_norm(v + r00 + x0), v001 = load_norm(v + r00 + x1);
-    const float v010 = load_norm(v + r01 + x0), v011 = load_norm(v + r01 + x1);
-    const float v100 = load_norm(v + r10 + x0), v101 = load_norm(v + r10 + x1);
-    const float v110 = load_norm(v + r11 + x0), v111 = load_norm(v + r11 + x1);
-    const float a00 = fmaf(tx, v001 - v000, v000), a01 = fmaf(tx, v011 - v010, v010);
-    const float a10 = fmaf(tx, v101 - v100, v100), a11 = fmaf(tx, v111 - v110, v110);
-    const float b0 = fmaf(ty, a01 - a00, a00), b1 = fmaf(ty, a11 - a10, a10);
-    return fmaf(tz, b1 - b0, b0);
+// floor without conversion instructions (|x| < 2^22): returns i with
+// x - i in [0, 1] (either neighbour at an exact integer, where the trilinear
+// weights make both choices give the same value).
+__device__ __forceinline__ int floor_frac(float x, float& frac) {
+    const float M = 12582912.0f;   // 1.5 * 2^23: adding it rounds to an integer
+    const float r = __fadd_rn(__fadd_rn(x, -0.5f), M);
+    frac = __fadd_rn(x, -__fadd_rn(r, -M));
+    return __float_as_int(r) - 0x4B400000;
+}
+
+__device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
+
+// Voxel access around the cell (i, j, k): fast = unclamped pointer offsets
+// (the whole stencil is inside the volume), otherwise clamp to edge.
+template <typename T, typename I, bool CLAMP>
+struct Vox {
+    const T* __restrict__ vol;
+    const T* b;
+    int nx, ny, nz, i, j, k;
+    I sy, sz;
+    __device__ __forceinline__ float at(int dx, int dy, int dz) const {
+        if (!CLAMP) return load_norm(b + ((I)dz * sz + (I)dy * sy + dx));
+        const int x = min(max(i + dx, 0), nx - 1);
+        const int y = min(max(j + dy, 0), ny - 1);
+        const int z = min(max(k + dz, 0), nz - 1);
+        return load_norm(vol + ((I)z * ny + y) * nx + x);
+    }
+};
+
+// Centre cube c[z][y][x] of the trilinear cell and the x-lerped rows
+// a[z][y]; returns the interpolated value.
+template <class V>
+__device__ __forceinline__ float cell_value(const V& v, float tx, float ty, float tz, float (&c)[2][2][2],
+                                            float (&a)[2][2]) {
+#pragma unroll
+    for (int z = 0; z < 2; ++z)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+            c[z][y][0] = v.at(0, y, z);
+            c[z][y][1] = v.at(1, y, z);
+            a[z][y] = lerpf(c[z][y][0], c[z][y][1], tx);
+        }
+    return lerpf(lerpf(a[0][0], a[0][1], ty), lerpf(a[1][0], a[1][1], ty), tz);
+}
+
+// Central differences of the trilinear field at +-1 voxel along each axis,
+// from the 32-voxel stencil around the cell (the 8 centre voxels plus 24).
+template <class V>
+__device__ __forceinline__ void cell_gradient(const V& v, float tx, float ty, float tz, const float (&c)[2][2][2],
+                                              const float (&a)[2][2], float& gx, float& gy, float& gz) {
+    float d[2][2];
+#pragma unroll
+    for (int z = 0; z < 2; ++z)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+            const float p = lerpf(c[z][y][1], v.at(2, y, z), tx);     // row value at x + 1
+            const float m = lerpf(v.at(-1, y, z), c[z][y][0], tx);    // row value at x - 1
+            d[z][y] = p - m;
+        }
+    gx = 0.5f * lerpf(lerpf(d[0][0], d[0][1], ty), lerpf(d[1][0], d[1][1], ty), tz);
+    float ym[2], yp[2];   // rows j - 1 and j + 2 at z = k, k + 1
+#pragma unroll
+    for (int z = 0; z < 2; ++z) {
+        ym[z] = lerpf(v.at(0, -1, z), v.at(1, -1, z), tx);
+        yp[z] = lerpf(v.at(0, 2, z), v.at(1, 2, z), tx);
+    }
+    gy = 0.5f * lerpf(lerpf(a[0][1], yp[0], ty) - lerpf(ym[0], a[0][0], ty),
+                      lerpf(a[1][1], yp[1], ty) - lerpf(ym[1], a[1][0], ty), tz);
+    float zm[2], zp[2];   // rows k - 1 and k + 2 at y = j, j + 1
+#pragma unroll
+    for (int y = 0; y < 2; ++y) {
+        zm[y] = lerpf(v.at(0, y, -1), v.at(1, y, -1), tx);
+        zp[y] = lerpf(v.at(0, y, 2), v.at(1, y, 2), tx);
+    }
+    gz = 0.5f * lerpf(lerpf(a[1][0], zp[0], tz) - lerpf(zm[0], a[0][0], tz),
+                      lerpf(a[1][1], zp[1], tz) - lerpf(zm[1], a[0][1], tz), ty);
 }
 
 template <typename T, typename I, bool SHADE>
@@ -99,6 +155,9 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
     const int nrays = a.ids ? min(max(*a.count, 0), npix) : a.n_dense;
     const float fnx = (float)a.nx, fny = (float)a.ny, fnz = (float)a.nz;
     const float tfmax = (float)(a.ntf - 1);
+    const I sy = (I)a.nx, sz = (I)a.nx * a.ny;
+    // sample positions are handled in voxel-centre coordinates u = p - 0.5
+    const float ux0 = a.ox - 0.5f, uy0 = a.oy - 0.5f, uz0 = a.oz - 0.5f;
     unsigned long long my_samples = 0;
     for (;;) {
         int base = 0;
@@ -124,10 +183,10 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
         if (pix < 0) continue;
 
         const float sx = ((px + 0.5f) * a.two_over_w - 1.0f) * a.tan_x;
-        const float sy = (1.0f - (py + 0.5f) * a.two_over_h) * a.tan_y;
-        float dx = a.fx + sx * a.rx + sy * a.ux;
-        float dy = a.fy + sx * a.ry + sy * a.uy;
-        float dz = a.fz + sx * a.rz + sy * a.uz;
+        const float sy_ = (1.0f - (py + 0.5f) * a.two_over_h) * a.tan_y;
+        float dx = a.fx + sx * a.rx + sy_ * a.ux;
+        float dy = a.fy + sx * a.ry + sy_ * a.uy;
+        float dz = a.fz + sx * a.rz + sy_ * a.uz;
         const float len = sqrtf(dx * dx + dy * dy + dz * dz);
         dx /= len;
         dy /= len;
@@ -158,42 +217,58 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
         }
         const float tnear = fmaxf(tn, 0.0f);
         float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
-        int k = 0;
+        float kf = 0.f;   // sample index, kept in float (exact below 2^24)
         if (!miss && tnear < tfar) {
-            for (;; ++k) {
-                const float t = fmaf((float)k, a.dt, tnear);
+            for (;;) {
+                const float t = fmaf(kf, a.dt, tnear);
                 if (t >= tfar) break;
-                const float x = fmaf(t, dx, a.ox), y = fmaf(t, dy, a.oy), z = fmaf(t, dz, a.oz);
-                const float v = trilinear<T, I>(vol, a.nx, a.ny, a.nz, x, y, z);
+                kf += 1.0f;
+                const float ux = fmaf(t, dx, ux0), uy = fmaf(t, dy, uy0), uz = fmaf(t, dz, uz0);
+                float tx, ty, tz;
+                const int i = floor_frac(ux, tx), j = floor_frac(uy, ty), k = floor_frac(uz, tz);
+                const bool cfast = (i >= 0) & (i <= a.nx - 2) & (j >= 0) & (j <= a.ny - 2) & (k >= 0) &
+                                   (k <= a.nz - 2);
+                float c[2][2][2], rows[2][2], v;
+                const Vox<T, I, false> vf{vol, vol + ((I)k * a.ny + j) * a.nx + i, a.nx, a.ny, a.nz, i, j, k, sy, sz};
+                const Vox<T, I, true> vc{vol, nullptr, a.nx, a.ny, a.nz, i, j, k, sy, sz};
+                if (cfast) v = cell_value(vf, tx, ty, tz, c, rows);
+                else v = cell_value(vc, tx, ty, tz, c, rows);
                 const float xi = v * tfmax;
-                int i = (int)floorf(xi);
-                i = min(max(i, 0), a.ntf - 2);
-                const float fr = xi - (float)i;
-                const float4 c0 = s_tf[i], c1 = s_tf[i + 1];
+                float fr;
+                int ti = floor_frac(xi, fr);
+                if (ti > a.ntf - 2) {
+                    fr += (float)(ti - (a.ntf - 2));
+                    ti = a.ntf - 2;
+                }
+                if (ti < 0) {
+                    fr += (float)ti;
+                    ti = 0;
+                }
+                const float4 c0 = s_tf[ti], c1 = s_tf[ti + 1];
                 const float al = fmaf(fr, c1.w - c0.w, c0.w);
                 if (al > 0.0f) {
                     float cr = fmaf(fr, c1.x - c0.x, c0.x);
                     float cg = fmaf(fr, c1.y - c0.y, c0.y);
                     float cb = fmaf(fr, c1.z - c0.z, c0.z);
                     if (SHADE) {
-                        const float gx = 0.5f * (trilinear<T, I>(vol, a.nx, a.ny, a.nz, x + 1.f, y, z) -
-                                                 trilinear<T, I>(vol, a.nx, a.ny, a.nz, x - 1.f, y, z));
-                        const float gy = 0.5f * (trilinear<T, I>(vol, a.nx, a.ny, a.nz, x, y + 1.f, z) -
-                                                 trilinear<T, I>(vol, a.nx, a.ny, a.nz, x, y - 1.f, z));
-                        const float gz = 0.5f * (trilinear<T, I>(vol, a.nx, a.ny, a.nz, x, y, z + 1.f) -
-                                                 trilinear<T, I>(vol, a.nx, a.ny, a.nz, x, y, z - 1.f));
-                        const float gn = sqrtf(gx * gx + gy * gy + gz * gz);
-                        if (gn >= 1e-6f) {
-                            const float ndl = fabsf(gx * dx + gy * dy + gz * dz) / gn;
+                        float gx, gy, gz;
+                        const bool gfast = (i >= 1) & (i <= a.nx - 3) & (j >= 1) & (j <= a.ny - 3) & (k >= 1) &
+                                           (k <= a.nz - 3);
+                        if (gfast) cell_gradient(vf, tx, ty, tz, c, rows, gx, gy, gz);
+                        else cell_gradient(vc, tx, ty, tz, c, rows, gx, gy, gz);
+                        const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+                        if (g2 >= 1e-12f) {
+                            const float ndl = fabsf(fmaf(gx, dx, fmaf(gy, dy, gz * dz))) * rsqrtf(g2);
                             float sp = ndl * ndl;   // ndl^32 by five squarings
                             sp *= sp;
                             sp *= sp;
                             sp *= sp;
                             sp *= sp;
-                            const float diff = 0.2f + 0.7f * ndl;
-                            cr = __saturatef(fmaf(cr, diff, 0.3f * sp));
-                            cg = __saturatef(fmaf(cg, diff, 0.3f * sp));
-                            cb = __saturatef(fmaf(cb, diff, 0.3f * sp));
+                            const float diff = fmaf(0.7f, ndl, 0.2f);
+                            const float spec = 0.3f * sp;
+                            cr = __saturatef(fmaf(cr, diff, spec));
+                            cg = __saturatef(fmaf(cg, diff, spec));
+                            cb = __saturatef(fmaf(cb, diff, spec));
                         }
                     }
                     const float w = (1.0f - A) * al;
@@ -202,13 +277,10 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
                     C2 = fmaf(w, cb, C2);
                     A += w;
                 }
-                if (A >= a.term) {
-                    ++k;
-                    break;
-                }
+                if (A >= a.term) break;
             }
         }
-        my_samples += (unsigned long long)k;
+        my_samples += (unsigned long long)kf;
         const float ta = 1.0f - A;
         float* out = a.rgbam + pix;
         out[0] = fmaf(ta, a.bg0, C0);

@@ -108,16 +108,17 @@ def _check(status, ctx=None):
         raise FvnError(status, msg)
 
 
-def _ptr(t):
+def _ptr(t, dtype=torch.float32):
+    """Device pointer of a contiguous CUDA tensor of the expected dtype."""
     if t is None:
         return None
-    if isinstance(t, torch.Tensor):
-        if not t.is_cuda:
-            raise ValueError("expected a CUDA tensor")
-        if not t.is_contiguous():
-            raise ValueError("expected a contiguous tensor")
-        return ctypes.c_void_p(t.data_ptr())
-    return t
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return ctypes.c_void_p(t.data_ptr())
 
 
 def _stream(stream=None):
@@ -135,7 +136,7 @@ def volume(t: torch.Tensor) -> Volume:
     if t.dim() != 3 or t.dtype not in _DTYPE:
         raise ValueError("volume must be a 3-D uint8 / uint16 / float16 / float32 CUDA tensor")
     nz, ny, nx = t.shape
-    return Volume(_ptr(t), nx, ny, nz, _DTYPE[t.dtype])
+    return Volume(_ptr(t, None), nx, ny, nz, _DTYPE[t.dtype])
 
 
 def transfer_function(t: torch.Tensor) -> TF:
@@ -202,13 +203,14 @@ class Context:
 
     # --- hot path -----------------------------------------------------------
     def make_mask(self, fov, w, h, mask, ids, count, stream=None):
-        self._chk(lib.fvn_make_mask(self.h, ctypes.byref(foveation(fov)), int(w), int(h), _ptr(mask), _ptr(ids),
-                                    _ptr(count), _stream(stream)))
+        self._chk(lib.fvn_make_mask(self.h, ctypes.byref(foveation(fov)), int(w), int(h), _ptr(mask, torch.uint8),
+                                    _ptr(ids, torch.int32), _ptr(count, torch.int32), _stream(stream)))
 
     def march(self, vol, tf, cam, mp, rgbam, ids=None, count=None, nsamples=None, stream=None):
         v, t, c, m = volume(vol), transfer_function(tf), camera(cam), march_params(mp)
         self._chk(lib.fvn_march(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c), ctypes.byref(m),
-                                _ptr(ids), _ptr(count), _ptr(rgbam), _ptr(nsamples), _stream(stream)))
+                                _ptr(ids, torch.int32), _ptr(count, torch.int32), _ptr(rgbam),
+                                _ptr(nsamples, torch.int64), _stream(stream)))
 
     def load_weights(self, flat):
         a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))

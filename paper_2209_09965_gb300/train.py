@@ -1,0 +1,286 @@
+"""Training of the reconstruction network on self-rendered pairs.
+
+The network is trained in FP32 (paper: "Model Precision & Optimization":
+train in full precision, run with the weights truncated to 16 bit) on pairs
+(sparse input, dense target) rendered by this library's own ray marcher
+from seeded procedural volumes (the paper trains on renders of its CT and
+simulation datasets, "Dataset" / "Training" sections).  Loss: L1 plus L1 of
+the image gradients (the paper's perceptual and temporal terms, Eq. 4-7,
+need VGG19 weights and optical flow that are not available).  Optimiser:
+Adam, lr 1e-3.
+
+Every forward and backward step runs in the library's CUDA kernels, called
+through ``torch.autograd.Function`` shims; parameter gradients are written by
+the backward kernels straight into one flat gradient buffer on which the
+Adam kernel steps.  Assembling a batch (choosing crop windows, slicing the
+rendered frame) uses plain tensor indexing.
+
+    python -m paper_2209_09965_gb300.train --steps 3000 --out weights/fvn_16_32_64.npy
+"""
+from __future__ import annotations
+
+import argparse
+import math
+import os
+import time
+
+import numpy as np
+import torch
+
+from . import fvn
+from . import workloads as wl
+
+LAYERS = wl.NET_LAYERS
+
+
+class Params:
+    """Flat FP32 master weights with per-layer views, flat gradient and Adam moments."""
+
+    def __init__(self, flat: np.ndarray, device):
+        self.p = torch.from_numpy(np.ascontiguousarray(flat, np.float32)).to(device).requires_grad_(True)
+        self.g = torch.zeros_like(self.p, requires_grad=False)
+        self.m = torch.zeros_like(self.g)
+        self.v = torch.zeros_like(self.g)
+        self.step = 0
+        self.views = {}
+        off = 0
+        for name, ci, co, k in LAYERS:
+            nw = co * ci * k * k
+            self.views[name] = (off, nw, (co, ci, k, k))
+            off += nw + co
+
+    def w(self, name):
+        off, nw, shape = self.views[name]
+        return self.p[off:off + nw].view(shape)
+
+    def b(self, name):
+        off, nw, shape = self.views[name]
+        return self.p[off + nw:off + nw + shape[0]]
+
+    def gw(self, name):
+        off, nw, shape = self.views[name]
+        return self.g[off:off + nw].view(shape)
+
+    def gb(self, name):
+        off, nw, shape = self.views[name]
+        return self.g[off + nw:off + nw + shape[0]]
+
+    def adam(self, lr=1e-3):
+        self.step += 1
+        fvn.adam_step(self.p.data, self.g, self.m, self.v, self.step, lr=lr)
+
+    def numpy(self):
+        return self.p.detach().cpu().numpy().astype(np.float32)
+
+
+class _Conv(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, xa, xb, w, b, relu, gw, gb):
+        n, _, h, wd = xa.shape
+        y = torch.empty(n, w.shape[0], h, wd, device=xa.device)
+        fvn.conv_fwd(xa, xb, w.detach(), b.detach(), relu, y)
+        ctx.save_for_backward(xa, xb, w, y if relu else None)
+        ctx.gwb = (gw, gb)
+        ctx.relu = relu
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        xa, xb, w, y = ctx.saved_tensors
+        gy = gy.contiguous()
+        gxa = torch.empty_like(xa) if ctx.needs_input_grad[0] else None
+        gxb = torch.empty_like(xb) if (xb is not None and ctx.needs_input_grad[1]) else None
+        gw, gb = ctx.gwb
+        fvn.conv_bwd(xa, xb, w.detach(), gy, y, gxa, gxb, gw, gb)
+        # parameter gradients went straight to the flat buffer
+        return gxa, gxb, None, None, None, None, None
+
+
+class _Pool(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x):
+        n, c, h, w = x.shape
+        y = torch.empty(n, c, h // 2, w // 2, device=x.device)
+        fvn.avgpool2_fwd(x, y)
+        ctx.shape = x.shape
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        gx = torch.empty(ctx.shape, device=gy.device)
+        fvn.avgpool2_bwd(gy.contiguous(), gx)
+        return gx
+
+
+class _Up(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, x):
+        n, c, h, w = x.shape
+        y = torch.empty(n, c, 2 * h, 2 * w, device=x.device)
+        fvn.upsample2_fwd(x, y)
+        ctx.shape = x.shape
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        gx = torch.empty(ctx.shape, device=gy.device)
+        fvn.upsample2_bwd(gy.contiguous(), gx)
+        return gx
+
+
+class _KP(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, head, sparse):
+        n, _, h, w = head.shape
+        out = torch.empty(n, 3, h, w, device=head.device)
+        fvn.kp_blend_fwd(head, sparse, out)
+        ctx.save_for_backward(head, sparse)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        head, sparse = ctx.saved_tensors
+        gh = torch.empty_like(head)
+        fvn.kp_blend_bwd(head, sparse, gout.contiguous(), gh)
+        return gh, None
+
+
+class _Loss(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, pred, target, lam):
+        loss = torch.zeros(1, device=pred.device)
+        g = torch.empty_like(pred)
+        fvn.loss_l1grad(pred, target, lam, loss, g)
+        ctx.save_for_backward(g)
+        return loss[0]
+
+    @staticmethod
+    def backward(ctx, gl):
+        (g,) = ctx.saved_tensors
+        return (g if float(gl) == 1.0 else g * gl), None, None
+
+
+def forward(P: Params, sparse: torch.Tensor, direct_only: bool = False):
+    """Network forward on [N, 5, H, W] (H, W multiples of 4); returns [N, 3, H, W]."""
+
+    def cbr(name, xa, xb=None):
+        return _Conv.apply(xa, xb, P.w(name), P.b(name), True, P.gw(name), P.gb(name))
+
+    e0 = cbr("enc0b", cbr("enc0a", sparse))
+    e1 = cbr("enc1b", cbr("enc1a", _Pool.apply(e0)))
+    bt = cbr("botb", cbr("bota", _Pool.apply(e1)))
+    d1 = cbr("dec1b", cbr("dec1a", _Up.apply(bt), e1))
+    d0 = cbr("dec0b", cbr("dec0a", _Up.apply(d1), e0))
+    head = _Conv.apply(d0, None, P.w("head"), P.b("head"), False, P.gw("head"), P.gb("head"))
+    if direct_only:
+        return head[:, 0:3]
+    return _KP.apply(head, sparse)
+
+
+# ---------------------------------------------------------------------------
+# self-rendered training pairs
+# ---------------------------------------------------------------------------
+class PairSource:
+    """Crops of 1920x1080 frames of procedural volumes: the dense march of
+    the crop's pixels is the target; the sparse input is the same samples
+    kept where the foveated mask is set (the sparse march of a pixel equals
+    its dense march)."""
+
+    def __init__(self, ctx: fvn.Context, device, nvol=64, vol_n=512, seed=100, frame_w=1920, frame_h=1080,
+                 crop=256, value_noise_share=0.5):
+        self.ctx, self.dev = ctx, device
+        self.W, self.H, self.crop = frame_w, frame_h, crop
+        self.rng = np.random.default_rng(seed)
+        self.vols = []
+        for i in range(nvol):
+            s = seed + i
+            if i < int(nvol * (1 - value_noise_share)):
+                v = wl.training_volume(vol_n, s, device=device)               # uint16 blobs + turbulence
+            else:
+                base = [16, 32, 64][i % 3] * vol_n // 256
+                v = wl.value_noise_volume(vol_n, s, base_spacing=max(4, base), device=device)
+                v = torch.round(v * 65535.0).to(torch.int32)
+                v = (v - 65536 * (v >= 32768).to(torch.int32)).to(torch.int16)
+            self.vols.append(v.contiguous())
+        self.rgbam = torch.empty(5, frame_h, frame_w, device=device)
+        self.mask = torch.empty(frame_h, frame_w, dtype=torch.uint8, device=device)
+        self.ids_all = torch.empty(frame_w * frame_h, dtype=torch.int32, device=device)
+        self.count = torch.zeros(1, dtype=torch.int32, device=device)
+        yy, xx = torch.meshgrid(torch.arange(crop, device=device), torch.arange(crop, device=device), indexing="ij")
+        self.local = (yy * frame_w + xx).reshape(-1).to(torch.int32)
+
+    def sample(self, batch):
+        c, W, H = self.crop, self.W, self.H
+        xs = torch.empty(batch, 5, c, c, device=self.dev)
+        ys = torch.empty(batch, 3, c, c, device=self.dev)
+        for b in range(batch):
+            r = self.rng
+            vol = self.vols[r.integers(len(self.vols))]
+            tf = torch.from_numpy(wl.transfer_function(int(r.integers(1 << 30)), alpha_max=r.uniform(0.03, 0.2)))
+            tf = tf.to(self.dev)
+            cam = wl.random_camera(r, W, H, rmin=0.8, rmax=1.8)
+            mp = wl.MarchParams(shading=int(r.uniform() < 0.85))
+            fx, fy = r.uniform(0.0, W), r.uniform(0.0, H)
+            fov = wl.Foveation(focal_px=(fx, fy), fovea_radius=r.uniform(0.05, 0.15),
+                               falloff_sigma=r.uniform(0.05, 0.15), p_base=r.uniform(0.03, 0.1),
+                               seed=int(r.integers(1 << 30)), frame=int(r.integers(1 << 20)))
+            # crop window: mostly around the screen centre where the volume is
+            x0 = int(np.clip(r.normal(W / 2, W / 5) - c / 2, 0, W - c))
+            y0 = int(np.clip(r.normal(H / 2, H / 5) - c / 2, 0, H - c))
+            ids = self.local + (y0 * W + x0)
+            cnt = torch.tensor([ids.numel()], dtype=torch.int32, device=self.dev)
+            self.ctx.march(vol, tf, cam, mp, self.rgbam, ids=ids, count=cnt)
+            self.ctx.make_mask(fov, W, H, self.mask, self.ids_all, self.count)
+            win = self.rgbam[:, y0:y0 + c, x0:x0 + c]
+            m = self.mask[y0:y0 + c, x0:x0 + c].to(torch.float32)
+            ys[b] = win[0:3]
+            xs[b, 0:4] = win[0:4] * m
+            xs[b, 4] = m
+        return xs, ys
+
+
+def train(steps=3000, batch=8, lr=1e-3, seed=100, nvol=64, vol_n=512, out=None, direct_only=False,
+          init_seed=3, log_every=100, device=None, lr_final=1e-4):
+    device = device or torch.device("cuda")
+    ctx = fvn.Context()
+    src = PairSource(ctx, device, nvol=nvol, vol_n=vol_n, seed=seed)
+    P = Params(wl.net_weights(init_seed), device)
+    log = []
+    t0 = time.time()
+    for it in range(1, steps + 1):
+        x, y = src.sample(batch)
+        P.g.zero_()
+        pred = forward(P, x, direct_only)
+        loss = _Loss.apply(pred, y, 1.0)
+        loss.backward()
+        # cosine decay from lr to lr_final over the run
+        cur = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * (it - 1) / max(1, steps - 1)))
+        P.adam(cur)
+        if it % log_every == 0 or it == 1:
+            lv = float(loss.item())
+            log.append((it, lv))
+            print(f"step {it} loss {lv:.5f} lr {cur:.2e} {time.time() - t0:.1f}s", flush=True)
+    w = P.numpy()
+    if out:
+        os.makedirs(os.path.dirname(os.path.abspath(out)), exist_ok=True)
+        np.save(out, w)
+    ctx.close()
+    return w, log
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--steps", type=int, default=3000)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--seed", type=int, default=100)
+    ap.add_argument("--nvol", type=int, default=64)
+    ap.add_argument("--vol-n", type=int, default=512)
+    ap.add_argument("--direct-only", action="store_true")
+    ap.add_argument("--out", default=None)
+    a = ap.parse_args()
+    train(a.steps, a.batch, a.lr, a.seed, a.nvol, a.vol_n, a.out, a.direct_only)
+
+
+if __name__ == "__main__":
+    main()

@@ -148,14 +148,21 @@ class Camera:
 
 
 def orbit_camera(seed: int, frame: int = 0, nframes: int = 64, width: int = 1920, height: int = 1080,
-                 fov_y_deg: float = 45.0, radius_factor: float = 1.8, extent=(1.0, 1.0, 1.0)) -> Camera:
+                 fov_y_deg: float = 45.0, radius_factor=1.8, extent=(1.0, 1.0, 1.0)) -> Camera:
     """Seeded orbit: start azimuth U[0, 2 pi), elevation amplitude U[0.2, 0.6] rad,
-    one revolution per ``nframes`` frames, radius = radius_factor x box diagonal."""
+    one revolution per ``nframes`` frames, radius = radius_factor x box diagonal.
+    A (near, far) radius_factor gives an oscillating zoom (two zoom cycles per
+    revolution), like the paper's fly-through of rotation plus oscillating zoom."""
     rng = np.random.default_rng(seed)
     az0 = rng.uniform(0.0, 2.0 * math.pi)
     el_amp = rng.uniform(0.2, 0.6)
     diag = math.sqrt(sum(e * e for e in extent))
-    r = radius_factor * diag
+    if isinstance(radius_factor, (tuple, list)):
+        near, far = radius_factor
+        z = 0.5 - 0.5 * math.cos(4.0 * math.pi * frame / nframes)
+        r = (near + (far - near) * z) * diag
+    else:
+        r = radius_factor * diag
     az = az0 + 2.0 * math.pi * frame / nframes
     el = el_amp * math.sin(2.0 * math.pi * frame / nframes + 0.7)
     eye = (r * math.cos(el) * math.cos(az), r * math.sin(el), r * math.cos(el) * math.sin(az))
@@ -265,6 +272,6 @@ def foveated_1080p_workload(seed: int = 2, frame: int = 0, n: int = 256, width: 
     if vol is None:
         vol = value_noise_volume(n, seed).to(torch.float32).numpy()
     tf = transfer_function(seed + 1000, alpha_max=0.08)
-    cam = orbit_camera(seed, frame, width=width, height=height)
+    cam = orbit_camera(seed, frame, width=width, height=height, radius_factor=(0.85, 1.75))
     fov = Foveation(focal_px=focal_point(seed, frame, width, height), seed=seed, frame=frame)
     return vol, tf, cam, fov, MarchParams(shading=1)

@@ -140,7 +140,7 @@ def test_march_sparse_1080p_full_frame(ctx):
     _, ids, _ = omask.make_mask(1920, 1080, fov.focal_px, seed=fov.seed, frame=fov.frame)
     perm = np.random.default_rng(0).permutation(ids)      # any order
     out, ns = run_march(ctx, vol, tf, cam, mp, ids=perm)
-    err, namb = march_parity(vol, tf, cam, mp, out, ids=ids)
+    err, namb = march_parity(vol, tf, cam, mp, out, ids=ids, max_amb_frac=0.05)
     flat = out.reshape(5, -1)
     rest = np.setdiff1d(np.arange(1920 * 1080), ids)
     assert np.all(flat[:, rest] == 0.0)
@@ -151,7 +151,7 @@ def test_march_dense_1080p_sampled(ctx):
     vol, tf, cam, fov, mp = wl.foveated_1080p_workload(seed=3, frame=5)
     out, ns = run_march(ctx, vol, tf, cam, mp)
     sample = np.sort(np.random.default_rng(1).choice(1920 * 1080, 60000, replace=False)).astype(np.int32)
-    march_parity(vol, tf, cam, mp, out, ids=sample)
+    march_parity(vol, tf, cam, mp, out, ids=sample, max_amb_frac=0.05)
     assert ns > 0
 
 

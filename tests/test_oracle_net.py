@@ -12,7 +12,7 @@ from oracle import metrics
 from oracle import net as on
 from paper_2209_09965_gb300 import workloads as wl
 
-torch.set_default_dtype(torch.float64)
+
 
 
 def T(a):
