@@ -36,7 +36,8 @@ typedef enum {
     FVN_ERR_CUDA = -2,         /* a CUDA runtime call failed */
     FVN_ERR_OOM = -3,          /* device or pinned allocation failed */
     FVN_ERR_UNSUPPORTED = -4,  /* valid request this build does not support */
-    FVN_ERR_STATE = -5         /* call out of order (e.g. no weights loaded) */
+    FVN_ERR_STATE = -5,        /* call out of order (e.g. no weights loaded) */
+    FVN_ERR_TIMEOUT = -6       /* a kernel gave up a bounded wait (see fvn_device_status) */
 } fvn_status;
 
 /* Voxel types; integer types are normalised by their maximum (u8 / 255,
@@ -98,6 +99,22 @@ fvn_status fvn_create(fvn_ctx** out);
 
 /* Free a context and everything it owns.  Synchronises the device. */
 fvn_status fvn_destroy(fvn_ctx* ctx);
+
+/* Tuning options (fvn_set_option); the defaults are what the autotuner picked.
+ *  FVN_OPT_CONV_KERNEL: 0 = tcgen05 tensor-core convolutions (TMEM
+ *      accumulators), 1 = mma.sync convolutions.
+ *  FVN_OPT_MARCH_REFILL: a march warp refills idle lanes with new rays once
+ *      fewer than this many lanes (1..32) are busy.
+ *  FVN_OPT_MARCH_BLOCKS_PER_SM: persistent march CTAs per SM (0 = as many as
+ *      fit). */
+enum { FVN_OPT_CONV_KERNEL = 1, FVN_OPT_MARCH_REFILL = 2, FVN_OPT_MARCH_BLOCKS_PER_SM = 3 };
+fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value);
+
+/* Synchronise the device and report a device-side failure recorded by this
+ * context's kernels since the last call: FVN_ERR_TIMEOUT when a tensor-core
+ * wait gave up after its iteration limit (the kernel then skipped its
+ * remaining work and left its outputs incomplete).  Clears the flag. */
+fvn_status fvn_device_status(fvn_ctx* ctx);
 
 /* Last error message of this context (or of the calling thread when ctx is
  * NULL); never NULL, "" when there was none. */

@@ -48,6 +48,13 @@ struct ReconWorkspace {
     void* base = nullptr;
 };
 
+// Activation buffers of one reconstruction (FP16 NHWC, per level).
+struct ReconPlan {
+    __half *e0a, *e0, *p0, *e1a, *e1, *p1, *ba, *bt, *d1a, *d1, *d0a, *d0;
+};
+
+enum ConvImpl { CONV_TCGEN05 = 0, CONV_MMA_SYNC = 1 };
+
 struct RenderWorkspace {
     int w = 0, h = 0;
     uint8_t* mask = nullptr;
@@ -69,6 +76,12 @@ struct fvn_ctx {
     bool has_weights = false;
     fvn::ConvW layers[fvn::kNumLayers];
     float* head_w = nullptr;          // FP32 [29][16] + [29] bias for the head / KP stage
+    __half* head_w16 = nullptr;       // head weights as a tensor-core operand: [2][32][8] FP16 (rows 29-31 zero)
+    float* head_b32 = nullptr;        // head bias padded to 32
+    int* d_error = nullptr;           // device-side error flag (a bounded wait gave up)
+    int conv_impl = fvn::CONV_MMA_SYNC;
+    int march_refill = 24;            // refill idle lanes once fewer than this many are busy
+    int march_blocks_per_sm = 0;      // 0 = occupancy limit
     float* d_act_scale = nullptr;     // FP8 per-layer activation scales
     fvn::ReconWorkspace recon_ws;
     fvn::RenderWorkspace render_ws;
@@ -107,5 +120,12 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
                       unsigned long long* nsamples, cudaStream_t st);
 fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
                             cudaStream_t st);
+// The network launch sequence on a caller-provided workspace of at least
+// recon_workspace_bytes(w, h) bytes (256-byte aligned).
+fvn_status reconstruct_on(fvn_ctx* ctx, void* workspace, const float* rgbam, int w, int h, int precision,
+                          float* rgb, cudaStream_t st);
+size_t recon_workspace_bytes(int w, int h);
+fvn_status reconstruct_tc(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, int w, int h, float* rgb,
+                          cudaStream_t st);
 
 }  // namespace fvn

@@ -1,0 +1,465 @@
+// Reconstruction convolutions on the 5th-generation tensor cores (tcgen05):
+// implicit GEMM with the accumulators in tensor memory (paper: "Reconstruction
+// Network"; the arithmetic is that of recon.cu's layers).
+//
+// Tile = TR output rows x 128 pixels.  For each row the GEMM is
+// M = 128 pixels, N = COUT, K = 9 taps x CIN, issued as 9 x CIN/16
+// tcgen05.mma (kind::f16, M=128, K=16) by one thread into a TMEM accumulator
+// of COUT columns.  The input halo (TR+2 rows x 130 pixels) is staged in
+// shared memory as planes of 8 channels x 16 bytes per pixel: that is the
+// K-major, non-swizzled core-matrix layout the tensor core reads (8 pixels x
+// 16 bytes contiguous), so the tap shift (dy, dx) is only a start-address
+// offset of the operand descriptor (LBO = one channel plane, SBO = 128 B).
+// Weights stay resident in shared memory in the same layout
+// ([tap][cin/8][cout][8]).  Epilogue: each thread owns one pixel (one TMEM
+// lane): bias, ReLU, FP16, 16-byte NHWC stores; fused 2x2 average pooling;
+// for the last decoder conv a second MMA applies the 1x1 head (16 -> 29,
+// padded to 32) from the activations written back to shared memory, and the
+// thread finishes its pixel with the softmax 5x5 kernel prediction over the
+// sparse samples (staged in shared memory) and the blend.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace fvn {
+
+namespace {
+
+enum { TIN_NHWC = 0, TIN_RGBAM = 1, TIN_UPCAT = 2 };
+enum { TEPI_STORE = 0, TEPI_POOL = 1, TEPI_HEADKP = 2 };
+
+constexpr int TW = 128;            // pixels per tile row = MMA M
+constexpr int HXW = TW + 2;        // halo width
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ void cp16(uint32_t dst, const void* src) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+}
+__device__ __forceinline__ void cp_wait_all() { asm volatile("cp.async.wait_all;\n" ::); }
+
+__device__ __forceinline__ uint4 pack8h(const float* v) {
+    uint4 r;
+    __half2 h0 = __floats2half2_rn(v[0], v[1]), h1 = __floats2half2_rn(v[2], v[3]);
+    __half2 h2 = __floats2half2_rn(v[4], v[5]), h3 = __floats2half2_rn(v[6], v[7]);
+    r.x = *reinterpret_cast<uint32_t*>(&h0);
+    r.y = *reinterpret_cast<uint32_t*>(&h1);
+    r.z = *reinterpret_cast<uint32_t*>(&h2);
+    r.w = *reinterpret_cast<uint32_t*>(&h3);
+    return r;
+}
+__device__ __forceinline__ void unpack8h(uint4 u, float* v) {
+    const __half2* h = reinterpret_cast<const __half2*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        float2 f = __half22float2(h[i]);
+        v[2 * i] = f.x;
+        v[2 * i + 1] = f.y;
+    }
+}
+
+template <int CIN, int COUT, int TR, int MODE, int EPI, int CUP>
+struct TcLayout {
+    static constexpr int CH = CIN / 8;
+    static constexpr int HY = TR + 2;
+    static constexpr int CR = TR / 2 + 3, CC = TW / 2 + 3;        // coarse halo (up-sampling)
+    static constexpr size_t w_off = 0;
+    static constexpr size_t w_bytes = 9ull * CIN * COUT * 2;
+    static constexpr size_t halo_off = w_off + w_bytes;
+    static constexpr size_t halo_bytes = (size_t)CH * HY * HXW * 16;
+    static constexpr size_t coarse_off = halo_off + halo_bytes;
+    static constexpr size_t coarse_bytes = MODE == TIN_UPCAT ? (size_t)(CUP / 8) * CR * CC * 16 : 0;
+    static constexpr size_t ha_off = coarse_off + coarse_bytes;     // head operand A: [TR][2][128][8] halves
+    static constexpr size_t ha_bytes = EPI == TEPI_HEADKP ? (size_t)TR * 2 * TW * 16 : 0;
+    static constexpr size_t hb_off = ha_off + ha_bytes;             // head weights: [2][32][8] halves
+    static constexpr size_t hb_bytes = EPI == TEPI_HEADKP ? 2 * 32 * 16 : 0;
+    static constexpr size_t sp_off = hb_off + hb_bytes;             // sparse R, G, B, M: [TR+4][TW+4] float4
+    static constexpr size_t sp_bytes = EPI == TEPI_HEADKP ? (size_t)(TR + 4) * (TW + 4) * 16 : 0;
+    static constexpr size_t bias_off = sp_off + sp_bytes;
+    static constexpr size_t bias_bytes = (COUT + 32) * 4;
+    static constexpr size_t bar_off = bias_off + bias_bytes;
+    static constexpr size_t bytes = bar_off + 16;
+    static constexpr uint32_t acc_cols = TR * COUT;
+    static constexpr uint32_t need_cols = EPI == TEPI_HEADKP ? (acc_cols > TR * 32 ? acc_cols : TR * 32) : acc_cols;
+    static constexpr uint32_t tmem_cols = need_cols <= 32 ? 32 : need_cols <= 64 ? 64 : need_cols <= 128 ? 128
+                                        : need_cols <= 256 ? 256 : 512;
+};
+
+struct TcArgs {
+    const __half* in;        // NHWC input, or the coarse level for up-sampling
+    const __half* skip;      // skip tensor (up-sampling layers)
+    const float* rgbam;      // sparse frame [5][H0][W0] (first layer, KP)
+    int H0, W0;
+    const __half* w;         // [9][CIN/8][COUT][8]
+    const float* bias;
+    const __half* head_w;    // [2][32][8] halves (KP layer)
+    const float* head_b;     // [32]
+    __half* out;             // [Hl][Wl][COUT]
+    __half* pooled;          // [Hl/2][Wl/2][COUT]
+    float* rgb;              // [3][H0][W0] (KP layer)
+    int Hl, Wl;
+    int tiles_x, ntiles;
+    int* error;              // set when a tensor-core wait gives up
+};
+
+template <int CIN, int COUT, int TR, int MODE, int EPI, int CUP>
+__global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
+    using L = TcLayout<CIN, COUT, TR, MODE, EPI, CUP>;
+    constexpr int CH = L::CH, HY = L::HY;
+    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 64, "unsupported conv shape");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    unsigned char* sW = smem + L::w_off;
+    unsigned char* sH = smem + L::halo_off;
+    unsigned char* sC = smem + L::coarse_off;
+    unsigned char* sHA = smem + L::ha_off;
+    unsigned char* sHB = smem + L::hb_off;
+    float4* sSP = reinterpret_cast<float4*>(smem + L::sp_off);
+    float* sBias = reinterpret_cast<float*>(smem + L::bias_off);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::bar_off);
+    uint32_t* tbase_s = reinterpret_cast<uint32_t*>(smem + L::bar_off + 8);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    {
+        const uint4* src = reinterpret_cast<const uint4*>(a.w);
+        uint4* dst = reinterpret_cast<uint4*>(sW);
+        for (int i = tid; i < (int)(L::w_bytes / 16); i += 128) dst[i] = __ldg(src + i);
+        for (int i = tid; i < COUT; i += 128) sBias[i] = __ldg(a.bias + i);
+        if (EPI == TEPI_HEADKP) {
+            const uint4* hs = reinterpret_cast<const uint4*>(a.head_w);
+            for (int i = tid; i < 2 * 32; i += 128) reinterpret_cast<uint4*>(sHB)[i] = __ldg(hs + i);
+            for (int i = tid; i < 32; i += 128) sBias[COUT + i] = __ldg(a.head_b + i);
+        }
+    }
+    if (tid == 0) tc::mbar_init(bar, 1);
+    if (warp == 0) tc::tmem_alloc(tbase_s, L::tmem_cols);
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tbase_s;
+    const uint32_t sW_u = tc::smem_addr(sW), sH_u = tc::smem_addr(sH);
+    constexpr uint32_t idesc = tc::idesc_f16(128, COUT);
+    uint32_t phase = 0;
+    bool failed = false;
+
+    for (int tile = blockIdx.x; tile < a.ntiles && !failed; tile += gridDim.x) {
+        const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
+        const int y0 = ty * TR, x0 = tx * TW;
+        tc::fence_before_sync();
+        __syncthreads();   // the previous tile's epilogue is done with TMEM and shared memory
+        tc::fence_after_sync();
+
+        // ---- stage the halo ------------------------------------------------
+        if (MODE == TIN_RGBAM) {
+            const long long plane = (long long)a.H0 * a.W0;
+            for (int i = tid; i < HY * HXW; i += 128) {
+                const int hy = i / HXW, hx = i - hy * HXW;
+                const int gy = y0 + hy - 1, gx = x0 + hx - 1;
+                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                if (gy >= 0 && gx >= 0 && gy < a.H0 && gx < a.W0) {
+                    const float* p = a.rgbam + (long long)gy * a.W0 + gx;
+#pragma unroll
+                    for (int c = 0; c < 5; ++c) v[c] = __ldg(p + c * plane);
+                }
+                *reinterpret_cast<uint4*>(sH + ((0 * HY + hy) * HXW + hx) * 16) = pack8h(v);
+#pragma unroll
+                for (int c = 1; c < CH; ++c)
+                    *reinterpret_cast<uint4*>(sH + ((c * HY + hy) * HXW + hx) * 16) = make_uint4(0, 0, 0, 0);
+            }
+        } else {
+            constexpr int CS0 = MODE == TIN_UPCAT ? CUP / 8 : 0;   // first chunk read from global
+            for (int i = tid; i < (CH - CS0) * HY * HXW; i += 128) {
+                const int c = CS0 + i / (HY * HXW);
+                const int rem = i % (HY * HXW);
+                const int hy = rem / HXW, hx = rem - hy * HXW;
+                const int gy = y0 + hy - 1, gx = x0 + hx - 1;
+                unsigned char* dst = sH + ((c * HY + hy) * HXW + hx) * 16;
+                if (gy >= 0 && gx >= 0 && gy < a.Hl && gx < a.Wl) {
+                    if (MODE == TIN_NHWC) cp16(tc::smem_addr(dst), a.in + ((long long)gy * a.Wl + gx) * CIN + c * 8);
+                    else cp16(tc::smem_addr(dst), a.skip + ((long long)gy * a.Wl + gx) * (CIN - CUP) + (c - CS0) * 8);
+                } else {
+                    *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+                }
+            }
+            if (MODE == TIN_UPCAT) {   // coarse rows / columns around the tile, clamped to the coarse frame
+                const int Hc = a.Hl >> 1, Wc = a.Wl >> 1;
+                const int cy0 = (y0 >> 1) - 1, cx0 = (x0 >> 1) - 1;
+                for (int i = tid; i < (CUP / 8) * L::CR * L::CC; i += 128) {
+                    const int c = i / (L::CR * L::CC);
+                    const int rem = i % (L::CR * L::CC);
+                    const int r = rem / L::CC, q = rem - r * L::CC;
+                    const int cy = min(max(cy0 + r, 0), Hc - 1), cx = min(max(cx0 + q, 0), Wc - 1);
+                    cp16(tc::smem_addr(sC + ((c * L::CR + r) * L::CC + q) * 16),
+                         a.in + ((long long)cy * Wc + cx) * CUP + c * 8);
+                }
+            }
+            cp_wait_all();
+            if (MODE == TIN_UPCAT) {
+                __syncthreads();
+                const int Hc = a.Hl >> 1, Wc = a.Wl >> 1;
+                const int cy0 = (y0 >> 1) - 1, cx0 = (x0 >> 1) - 1;
+                for (int i = tid; i < (CUP / 8) * HY * HXW; i += 128) {
+                    const int c = i / (HY * HXW);
+                    const int rem = i % (HY * HXW);
+                    const int hy = rem / HXW, hx = rem - hy * HXW;
+                    const int gy = y0 + hy - 1, gx = x0 + hx - 1;
+                    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    if (gy >= 0 && gx >= 0 && gy < a.Hl && gx < a.Wl) {
+                        // bilinear x2, half-pixel centres, negative source clamped, upper neighbour clamped
+                        const float sy = fmaxf((gy + 0.5f) * 0.5f - 0.5f, 0.f);
+                        const float sx = fmaxf((gx + 0.5f) * 0.5f - 0.5f, 0.f);
+                        const int iy0 = (int)sy, ix0 = (int)sx;
+                        const float fy = sy - iy0, fx = sx - ix0;
+                        const int iy1 = min(iy0 + 1, Hc - 1), ix1 = min(ix0 + 1, Wc - 1);
+                        const unsigned char* base = sC + (size_t)c * L::CR * L::CC * 16;
+                        float p00[8], p01[8], p10[8], p11[8];
+                        unpack8h(*reinterpret_cast<const uint4*>(base + ((iy0 - cy0) * L::CC + (ix0 - cx0)) * 16), p00);
+                        unpack8h(*reinterpret_cast<const uint4*>(base + ((iy0 - cy0) * L::CC + (ix1 - cx0)) * 16), p01);
+                        unpack8h(*reinterpret_cast<const uint4*>(base + ((iy1 - cy0) * L::CC + (ix0 - cx0)) * 16), p10);
+                        unpack8h(*reinterpret_cast<const uint4*>(base + ((iy1 - cy0) * L::CC + (ix1 - cx0)) * 16), p11);
+#pragma unroll
+                        for (int j = 0; j < 8; ++j) {
+                            const float top = fmaf(fx, p01[j] - p00[j], p00[j]);
+                            const float bot = fmaf(fx, p11[j] - p10[j], p10[j]);
+                            v[j] = fmaf(fy, bot - top, top);
+                        }
+                    }
+                    *reinterpret_cast<uint4*>(sH + ((c * HY + hy) * HXW + hx) * 16) = pack8h(v);
+                }
+            }
+        }
+        if (EPI == TEPI_HEADKP) {   // sparse R, G, B, M around the tile (2-pixel margin)
+            const long long plane = (long long)a.H0 * a.W0;
+            for (int i = tid; i < (TR + 4) * (TW + 4); i += 128) {
+                const int r = i / (TW + 4), q = i - r * (TW + 4);
+                const int gy = y0 + r - 2, gx = x0 + q - 2;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (gy >= 0 && gx >= 0 && gy < a.H0 && gx < a.W0) {
+                    const float* p = a.rgbam + (long long)gy * a.W0 + gx;
+                    v = make_float4(__ldg(p), __ldg(p + plane), __ldg(p + 2 * plane), __ldg(p + 4 * plane));
+                }
+                sSP[i] = v;
+            }
+        }
+        tc::fence_async_smem();
+        __syncthreads();
+
+        // ---- tensor-core main loop: one elected thread issues every MMA ----
+        if (tid == 0) {
+            tc::fence_after_sync();
+#pragma unroll 1
+            for (int r = 0; r < TR; ++r) {
+                const uint32_t d = tmem + (uint32_t)(r * COUT);
+#pragma unroll 1
+                for (int tap = 0; tap < 9; ++tap) {
+                    const int dy = tap / 3, dx = tap - dy * 3;
+#pragma unroll
+                    for (int kc = 0; kc < CH / 2; ++kc) {
+                        const uint32_t aaddr = sH_u + (((2 * kc) * HY + r + dy) * HXW + dx) * 16;
+                        const uint32_t baddr = sW_u + ((tap * CH + 2 * kc) * COUT) * 16;
+                        const uint64_t ad = tc::smem_desc(aaddr, HY * HXW * 16, 128);
+                        const uint64_t bd = tc::smem_desc(baddr, COUT * 16, 128);
+                        tc::mma_f16(d, ad, bd, idesc, (tap | kc) != 0);
+                    }
+                }
+            }
+            tc::mma_commit(bar);
+        }
+        if (!tc::mbar_wait(bar, phase, kWaitLimit)) {
+            failed = true;
+            if (tid == 0) atomicExch(a.error, 1);
+            break;
+        }
+        phase ^= 1u;
+        tc::fence_after_sync();
+
+        // ---- epilogue: one pixel per thread --------------------------------
+        const int px = warp * 32 + lane;         // TMEM lane = pixel within the tile row
+        const int x = x0 + px;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        if (EPI != TEPI_HEADKP) {
+            float prev[COUT];                    // row r - 1 (pooling pairs rows 2k, 2k+1)
+#pragma unroll 1
+            for (int r = 0; r < TR; ++r) {
+                const int y = y0 + r;
+                float v[COUT];
+#pragma unroll
+                for (int c = 0; c < COUT; c += 16) tc::tmem_ld16(tmem + lane_base + r * COUT + c, v + c);
+#pragma unroll
+                for (int c = 0; c < COUT; ++c) v[c] = fmaxf(v[c] + sBias[c], 0.f);
+                if (y < a.Hl && x < a.Wl) {
+                    uint4* o = reinterpret_cast<uint4*>(a.out + ((long long)y * a.Wl + x) * COUT);
+#pragma unroll
+                    for (int c = 0; c < COUT; c += 8) o[c / 8] = pack8h(v + c);
+                }
+                if (EPI == TEPI_POOL) {
+                    if (r & 1) {
+                        float s[COUT];
+#pragma unroll
+                        for (int c = 0; c < COUT; ++c) {
+                            s[c] = prev[c] + v[c];
+                            s[c] += __shfl_xor_sync(0xffffffffu, s[c], 1);
+                            s[c] *= 0.25f;
+                        }
+                        if ((lane & 1) == 0 && y < a.Hl && x < a.Wl) {
+                            uint4* o = reinterpret_cast<uint4*>(
+                                a.pooled + ((long long)(y >> 1) * (a.Wl >> 1) + (x >> 1)) * COUT);
+#pragma unroll
+                            for (int c = 0; c < COUT; c += 8) o[c / 8] = pack8h(s + c);
+                        }
+                    } else {
+#pragma unroll
+                        for (int c = 0; c < COUT; ++c) prev[c] = v[c];
+                    }
+                }
+            }
+        } else {
+            // activations (bias, ReLU, FP16) -> shared memory as the head's A operand
+#pragma unroll 1
+            for (int r = 0; r < TR; ++r) {
+                float v[16];
+                tc::tmem_ld16(tmem + lane_base + r * COUT, v);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) v[c] = fmaxf(v[c] + sBias[c], 0.f);
+                *reinterpret_cast<uint4*>(sHA + ((r * 2 + 0) * TW + px) * 16) = pack8h(v);
+                *reinterpret_cast<uint4*>(sHA + ((r * 2 + 1) * TW + px) * 16) = pack8h(v + 8);
+            }
+            tc::fence_async_smem();
+            tc::fence_before_sync();
+            __syncthreads();
+            if (tid == 0) {
+                tc::fence_after_sync();
+                constexpr uint32_t hdesc = tc::idesc_f16(128, 32);
+                const uint64_t bd = tc::smem_desc(tc::smem_addr(sHB), 32 * 16, 128);
+                for (int r = 0; r < TR; ++r) {
+                    const uint64_t ad = tc::smem_desc(tc::smem_addr(sHA + r * 2 * TW * 16), TW * 16, 128);
+                    tc::mma_f16(tmem + (uint32_t)(r * 32), ad, bd, hdesc, 0);
+                }
+                tc::mma_commit(bar);
+            }
+            if (!tc::mbar_wait(bar, phase, kWaitLimit)) {
+                failed = true;
+                if (tid == 0) atomicExch(a.error, 1);
+                break;
+            }
+            phase ^= 1u;
+            tc::fence_after_sync();
+            const long long plane = (long long)a.H0 * a.W0;
+#pragma unroll 1
+            for (int r = 0; r < TR; ++r) {
+                const int y = y0 + r;
+                float hd[32];
+                tc::tmem_ld16(tmem + lane_base + r * 32, hd);
+                tc::tmem_ld16(tmem + lane_base + r * 32 + 16, hd + 16);
+#pragma unroll
+                for (int j = 0; j < 29; ++j) hd[j] += sBias[COUT + j];
+                float mx = hd[3];
+#pragma unroll
+                for (int q = 1; q < 25; ++q) mx = fmaxf(mx, hd[3 + q]);
+                float e[25], es = 0.f;
+#pragma unroll
+                for (int q = 0; q < 25; ++q) {
+                    e[q] = expf(hd[3 + q] - mx);
+                    es += e[q];
+                }
+                const float inv = 1.0f / es;
+                float den = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
+#pragma unroll
+                for (int q = 0; q < 25; ++q) {
+                    const float4 s = sSP[(r + q / 5) * (TW + 4) + px + q % 5];
+                    const float wm = e[q] * inv * s.w;
+                    den += wm;
+                    n0 = fmaf(wm, s.x, n0);
+                    n1 = fmaf(wm, s.y, n1);
+                    n2 = fmaf(wm, s.z, n2);
+                }
+                float k0 = hd[0], k1 = hd[1], k2 = hd[2];
+                if (den >= 1e-12f) {
+                    k0 = n0 / den;
+                    k1 = n1 / den;
+                    k2 = n2 / den;
+                }
+                const float al = 1.0f / (1.0f + expf(-hd[28]));
+                if (y < a.H0 && x < a.W0) {
+                    float* o = a.rgb + (long long)y * a.W0 + x;
+                    o[0] = fmaf(al, k0 - hd[0], hd[0]);
+                    o[plane] = fmaf(al, k1 - hd[1], hd[1]);
+                    o[2 * plane] = fmaf(al, k2 - hd[2], hd[2]);
+                }
+            }
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_relinquish();
+        tc::tmem_dealloc(tmem, L::tmem_cols);
+    }
+}
+
+}  // namespace
+
+template <int CIN, int COUT, int TR, int MODE, int EPI, int CUP>
+static fvn_status launch_tc(fvn_ctx* ctx, TcArgs a, cudaStream_t st) {
+    using L = TcLayout<CIN, COUT, TR, MODE, EPI, CUP>;
+    auto kern = conv3x3_tc_kernel<CIN, COUT, TR, MODE, EPI, CUP>;
+    static bool configured = false;
+    if (!configured) {
+        FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+        configured = true;
+    }
+    int per_sm = 0;
+    FVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, L::bytes));
+    per_sm = std::min(per_sm, (int)(512 / L::tmem_cols));   // never wait in tcgen05.alloc
+    if (per_sm < 1) return set_error(ctx, FVN_ERR_CUDA, "tensor-core conv kernel does not fit on an SM");
+    a.tiles_x = (a.Wl + TW - 1) / TW;
+    a.ntiles = a.tiles_x * ((a.Hl + TR - 1) / TR);
+    const int grid = std::min(a.ntiles, ctx->num_sms * per_sm);
+    a.error = ctx->d_error;
+    kern<<<grid, 128, L::bytes, st>>>(a);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+fvn_status reconstruct_tc(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, int w, int h, float* rgb,
+                          cudaStream_t st) {
+    const int W4 = (w + 3) & ~3, H4 = (h + 3) & ~3;
+    const ConvW* L = ctx->layers;
+    fvn_status s;
+    TcArgs a{};
+    a.rgbam = rgbam; a.H0 = h; a.W0 = w; a.w = L[0].w16; a.bias = L[0].bias; a.out = B.e0a; a.Hl = H4; a.Wl = W4;
+    if ((s = launch_tc<16, 16, 4, TIN_RGBAM, TEPI_STORE, 0>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.e0a; a.w = L[1].w16; a.bias = L[1].bias; a.out = B.e0; a.pooled = B.p0; a.Hl = H4; a.Wl = W4;
+    if ((s = launch_tc<16, 16, 4, TIN_NHWC, TEPI_POOL, 0>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.p0; a.w = L[2].w16; a.bias = L[2].bias; a.out = B.e1a; a.Hl = H4 / 2; a.Wl = W4 / 2;
+    if ((s = launch_tc<16, 32, 4, TIN_NHWC, TEPI_STORE, 0>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.e1a; a.w = L[3].w16; a.bias = L[3].bias; a.out = B.e1; a.pooled = B.p1; a.Hl = H4 / 2; a.Wl = W4 / 2;
+    if ((s = launch_tc<32, 32, 4, TIN_NHWC, TEPI_POOL, 0>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.p1; a.w = L[4].w16; a.bias = L[4].bias; a.out = B.ba; a.Hl = H4 / 4; a.Wl = W4 / 4;
+    if ((s = launch_tc<32, 64, 2, TIN_NHWC, TEPI_STORE, 0>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.ba; a.w = L[5].w16; a.bias = L[5].bias; a.out = B.bt; a.Hl = H4 / 4; a.Wl = W4 / 4;
+    if ((s = launch_tc<64, 64, 2, TIN_NHWC, TEPI_STORE, 0>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.bt; a.skip = B.e1; a.w = L[6].w16; a.bias = L[6].bias; a.out = B.d1a; a.Hl = H4 / 2; a.Wl = W4 / 2;
+    if ((s = launch_tc<96, 32, 2, TIN_UPCAT, TEPI_STORE, 64>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.d1a; a.w = L[7].w16; a.bias = L[7].bias; a.out = B.d1; a.Hl = H4 / 2; a.Wl = W4 / 2;
+    if ((s = launch_tc<32, 32, 4, TIN_NHWC, TEPI_STORE, 0>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.d1; a.skip = B.e0; a.w = L[8].w16; a.bias = L[8].bias; a.out = B.d0a; a.Hl = H4; a.Wl = W4;
+    if ((s = launch_tc<48, 16, 4, TIN_UPCAT, TEPI_STORE, 32>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.d0a; a.w = L[9].w16; a.bias = L[9].bias; a.head_w = ctx->head_w16; a.head_b = ctx->head_b32;
+    a.rgbam = rgbam; a.H0 = h; a.W0 = w; a.rgb = rgb; a.Hl = H4; a.Wl = W4;
+    return launch_tc<16, 16, 4, TIN_NHWC, TEPI_HEADKP, 0>(ctx, a, st);
+}
+
+}  // namespace fvn

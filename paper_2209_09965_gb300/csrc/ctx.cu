@@ -67,11 +67,14 @@ extern "C" fvn_status fvn_create(fvn_ctx** out) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
     if (e == cudaSuccess) e = cudaMalloc(&ctx->d_ticket, 64 * sizeof(int));
     if (e == cudaSuccess) e = cudaMemset(ctx->d_ticket, 0, 64 * sizeof(int));
+    if (e == cudaSuccess) e = cudaMalloc(&ctx->d_error, sizeof(int));
+    if (e == cudaSuccess) e = cudaMemset(ctx->d_error, 0, sizeof(int));
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) {
         fvn_status st = set_error(nullptr, e == cudaErrorMemoryAllocation ? FVN_ERR_OOM : FVN_ERR_CUDA,
                                   "fvn_create: %s", cudaGetErrorString(e));
         if (ctx->d_ticket) cudaFree(ctx->d_ticket);
+        if (ctx->d_error) cudaFree(ctx->d_error);
         delete ctx;
         return st;
     }
@@ -93,6 +96,9 @@ extern "C" fvn_status fvn_destroy(fvn_ctx* ctx) {
         cudaFree(L.bias);
     }
     cudaFree(ctx->head_w);
+    cudaFree(ctx->head_w16);
+    cudaFree(ctx->head_b32);
+    cudaFree(ctx->d_error);
     cudaFree(ctx->d_act_scale);
     cudaFree(ctx->d_ticket);
     cudaFree(ctx->recon_ws.base);
@@ -106,6 +112,38 @@ extern "C" fvn_status fvn_destroy(fvn_ctx* ctx) {
 
 extern "C" const char* fvn_last_error(const fvn_ctx* ctx) {
     return ctx ? ctx->err.c_str() : g_thread_err.c_str();
+}
+
+extern "C" fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    switch (option) {
+        case FVN_OPT_CONV_KERNEL:
+            FVN_CHECK_ARG(ctx, value == CONV_TCGEN05 || value == CONV_MMA_SYNC, "conv kernel must be 0 or 1");
+            ctx->conv_impl = value;
+            return FVN_OK;
+        case FVN_OPT_MARCH_REFILL:
+            FVN_CHECK_ARG(ctx, value >= 1 && value <= 32, "refill threshold must be in [1, 32]");
+            ctx->march_refill = value;
+            return FVN_OK;
+        case FVN_OPT_MARCH_BLOCKS_PER_SM:
+            FVN_CHECK_ARG(ctx, value >= 0 && value <= 16, "blocks per SM must be in [0, 16]");
+            ctx->march_blocks_per_sm = value;
+            return FVN_OK;
+        default:
+            return set_error(ctx, FVN_ERR_ARG, "unknown option %d", option);
+    }
+}
+
+extern "C" fvn_status fvn_device_status(fvn_ctx* ctx) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    FVN_CUDA(ctx, cudaDeviceSynchronize());
+    int flag = 0;
+    FVN_CUDA(ctx, cudaMemcpy(&flag, ctx->d_error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        FVN_CUDA(ctx, cudaMemset(ctx->d_error, 0, sizeof(int)));
+        return set_error(ctx, FVN_ERR_TIMEOUT, "a kernel gave up waiting for the tensor cores (flag %d)", flag);
+    }
+    return FVN_OK;
 }
 
 extern "C" fvn_status fvn_render(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,

@@ -44,6 +44,7 @@ struct MarchArgs {
     long long plane;
     unsigned long long* nsamples;
     int* ticket;
+    int refill_below;                 // refill idle lanes once fewer than this many are busy
 };
 
 template <typename T>
@@ -143,155 +144,205 @@ __device__ __forceinline__ void cell_gradient(const V& v, float tx, float ty, fl
                       lerpf(a[1][1], zp[1], tz) - lerpf(zm[1], a[0][1], tz), ty);
 }
 
+// Ray state of one lane.
+struct Ray {
+    int pix;                     // pixel id, < 0 when the lane is idle
+    float dx, dy, dz, tnear, tfar, kf;
+    float C0, C1, C2, A;
+};
+
+// Set up ray number r (dense: 8 x 4 pixel blocks; sparse: the id list).
+// Returns false when r names no pixel.  A ray that misses the box is written
+// out at once and leaves the lane idle.
+__device__ __forceinline__ bool start_ray(const MarchArgs& a, int r, int npix, Ray& s) {
+    int pix, px, py;
+    if (a.ids) {
+        pix = __ldg(a.ids + r);
+        if ((unsigned)pix >= (unsigned)npix) return false;   // ignore ids outside the frame
+        py = pix / a.W;
+        px = pix - py * a.W;
+    } else {
+        const int tile = r >> 5, q = r & 31;
+        const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
+        px = tx * 8 + (q & 7);
+        py = ty * 4 + (q >> 3);
+        if (px >= a.W || py >= a.H) return false;
+        pix = py * a.W + px;
+    }
+    const float sx = ((px + 0.5f) * a.two_over_w - 1.0f) * a.tan_x;
+    const float sy = (1.0f - (py + 0.5f) * a.two_over_h) * a.tan_y;
+    float dx = a.fx + sx * a.rx + sy * a.ux;
+    float dy = a.fy + sx * a.ry + sy * a.uy;
+    float dz = a.fz + sx * a.rz + sy * a.uz;
+    const float len = sqrtf(dx * dx + dy * dy + dz * dz);
+    dx /= len;
+    dy /= len;
+    dz /= len;
+    float tn = -INFINITY, tfar = INFINITY;
+    bool miss = false;
+    const float o[3] = {a.ox, a.oy, a.oz};
+    const float d[3] = {dx, dy, dz};
+    const float n[3] = {(float)a.nx, (float)a.ny, (float)a.nz};
+#pragma unroll
+    for (int ax = 0; ax < 3; ++ax) {
+        if (d[ax] == 0.0f) {
+            if (o[ax] < 0.0f || o[ax] > n[ax]) miss = true;
+        } else {
+            float t0 = (0.0f - o[ax]) / d[ax];
+            float t1 = (n[ax] - o[ax]) / d[ax];
+            if (t0 > t1) {
+                const float t = t0;
+                t0 = t1;
+                t1 = t;
+            }
+            tn = fmaxf(tn, t0);
+            tfar = fminf(tfar, t1);
+        }
+    }
+    const float tnear = fmaxf(tn, 0.0f);
+    s.pix = pix;
+    s.dx = dx;
+    s.dy = dy;
+    s.dz = dz;
+    s.tnear = tnear;
+    s.tfar = (miss || !(tnear < tfar)) ? -INFINITY : tfar;   // no sample when missed
+    s.kf = 0.f;
+    s.C0 = s.C1 = s.C2 = s.A = 0.f;
+    return true;
+}
+
+__device__ __forceinline__ void finish_ray(const MarchArgs& a, const Ray& s) {
+    const float ta = 1.0f - s.A;
+    float* out = a.rgbam + s.pix;
+    out[0] = fmaf(ta, a.bg0, s.C0);
+    out[a.plane] = fmaf(ta, a.bg1, s.C1);
+    out[2 * a.plane] = fmaf(ta, a.bg2, s.C2);
+    out[3 * a.plane] = s.A;
+    out[4 * a.plane] = 1.0f;
+}
+
+// One sample of the ray; returns true when the ray is finished.
+template <typename T, typename I, bool SHADE>
+__device__ __forceinline__ bool ray_step(const MarchArgs& a, const T* __restrict__ vol, const float4* s_tf, I sy,
+                                         I sz, float ux0, float uy0, float uz0, float tfmax, Ray& s) {
+    const float t = fmaf(s.kf, a.dt, s.tnear);
+    if (!(t < s.tfar)) return true;
+    s.kf += 1.0f;
+    const float ux = fmaf(t, s.dx, ux0), uy = fmaf(t, s.dy, uy0), uz = fmaf(t, s.dz, uz0);
+    float tx, ty, tz;
+    const int i = floor_frac(ux, tx), j = floor_frac(uy, ty), k = floor_frac(uz, tz);
+    const bool cfast = (i >= 0) & (i <= a.nx - 2) & (j >= 0) & (j <= a.ny - 2) & (k >= 0) & (k <= a.nz - 2);
+    float c[2][2][2], rows[2][2], v;
+    const Vox<T, I, false> vf{vol, vol + ((I)k * a.ny + j) * a.nx + i, a.nx, a.ny, a.nz, i, j, k, sy, sz};
+    const Vox<T, I, true> vc{vol, nullptr, a.nx, a.ny, a.nz, i, j, k, sy, sz};
+    if (cfast) v = cell_value(vf, tx, ty, tz, c, rows);
+    else v = cell_value(vc, tx, ty, tz, c, rows);
+    const float xi = v * tfmax;
+    float fr;
+    int ti = floor_frac(xi, fr);
+    if (ti > a.ntf - 2) {
+        fr += (float)(ti - (a.ntf - 2));
+        ti = a.ntf - 2;
+    }
+    if (ti < 0) {
+        fr += (float)ti;
+        ti = 0;
+    }
+    const float4 c0 = s_tf[ti], c1 = s_tf[ti + 1];
+    const float al = fmaf(fr, c1.w - c0.w, c0.w);
+    if (al > 0.0f) {
+        float cr = fmaf(fr, c1.x - c0.x, c0.x);
+        float cg = fmaf(fr, c1.y - c0.y, c0.y);
+        float cb = fmaf(fr, c1.z - c0.z, c0.z);
+        if (SHADE) {
+            float gx, gy, gz;
+            const bool gfast = (i >= 1) & (i <= a.nx - 3) & (j >= 1) & (j <= a.ny - 3) & (k >= 1) & (k <= a.nz - 3);
+            if (gfast) cell_gradient(vf, tx, ty, tz, c, rows, gx, gy, gz);
+            else cell_gradient(vc, tx, ty, tz, c, rows, gx, gy, gz);
+            const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+            if (g2 >= 1e-12f) {   // |g| >= 1e-6: shade, otherwise keep the TF colour
+                const float ndl = fabsf(fmaf(gx, s.dx, fmaf(gy, s.dy, gz * s.dz))) * rsqrtf(g2);
+                float sp = ndl * ndl;   // ndl^32 by five squarings
+                sp *= sp;
+                sp *= sp;
+                sp *= sp;
+                sp *= sp;
+                const float diff = fmaf(0.7f, ndl, 0.2f);
+                const float spec = 0.3f * sp;
+                cr = __saturatef(fmaf(cr, diff, spec));
+                cg = __saturatef(fmaf(cg, diff, spec));
+                cb = __saturatef(fmaf(cb, diff, spec));
+            }
+        }
+        const float w = (1.0f - s.A) * al;
+        s.C0 = fmaf(w, cr, s.C0);
+        s.C1 = fmaf(w, cg, s.C1);
+        s.C2 = fmaf(w, cb, s.C2);
+        s.A += w;
+    }
+    return s.A >= a.term;
+}
+
+// Persistent kernel with per-lane ray refill: a lane whose ray finishes goes
+// idle, and once fewer than `refill_below` lanes of the warp are busy the
+// idle lanes take new rays from the global queue together (one atomic per
+// warp), so warps neither wait for their longest ray nor for the slowest
+// warp at the end of the queue.
 template <typename T, typename I, bool SHADE>
 __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
     extern __shared__ float4 s_tf[];
     for (int i = threadIdx.x; i < a.ntf; i += blockDim.x) s_tf[i] = a.tf[i];
     __syncthreads();
+    const unsigned FULL = 0xffffffffu;
     const T* __restrict__ vol = static_cast<const T*>(a.vol);
     const int lane = threadIdx.x & 31;
     const int npix = a.W * a.H;
     // the id list never holds more than one entry per pixel
     const int nrays = a.ids ? min(max(*a.count, 0), npix) : a.n_dense;
-    const float fnx = (float)a.nx, fny = (float)a.ny, fnz = (float)a.nz;
     const float tfmax = (float)(a.ntf - 1);
     const I sy = (I)a.nx, sz = (I)a.nx * a.ny;
     // sample positions are handled in voxel-centre coordinates u = p - 0.5
     const float ux0 = a.ox - 0.5f, uy0 = a.oy - 0.5f, uz0 = a.oz - 0.5f;
     unsigned long long my_samples = 0;
+    Ray s;
+    s.pix = -1;
+    bool exhausted = false;   // warp-uniform: the queue has run dry
     for (;;) {
-        int base = 0;
-        if (lane == 0) base = atomicAdd(a.ticket, 32);
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (base >= nrays) break;
-        const int r = base + lane;
-        int pix = -1, px = 0, py = 0;
-        if (a.ids) {
-            if (r < nrays) {
-                pix = __ldg(a.ids + r);
-                if ((unsigned)pix >= (unsigned)npix) pix = -1;   // ignore ids outside the frame
-                py = pix / a.W;
-                px = pix - py * a.W;
-            }
-        } else {
-            const int tile = r >> 5;
-            const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
-            px = tx * 8 + (lane & 7);
-            py = ty * 4 + (lane >> 3);
-            if (px < a.W && py < a.H) pix = py * a.W + px;
-        }
-        if (pix < 0) continue;
-
-        const float sx = ((px + 0.5f) * a.two_over_w - 1.0f) * a.tan_x;
-        const float sy_ = (1.0f - (py + 0.5f) * a.two_over_h) * a.tan_y;
-        float dx = a.fx + sx * a.rx + sy_ * a.ux;
-        float dy = a.fy + sx * a.ry + sy_ * a.uy;
-        float dz = a.fz + sx * a.rz + sy_ * a.uz;
-        const float len = sqrtf(dx * dx + dy * dy + dz * dz);
-        dx /= len;
-        dy /= len;
-        dz /= len;
-
-        float tn = -INFINITY, tfar = INFINITY;
-        bool miss = false;
-        {
-            const float o[3] = {a.ox, a.oy, a.oz};
-            const float d[3] = {dx, dy, dz};
-            const float n[3] = {fnx, fny, fnz};
-#pragma unroll
-            for (int ax = 0; ax < 3; ++ax) {
-                if (d[ax] == 0.0f) {
-                    if (o[ax] < 0.0f || o[ax] > n[ax]) miss = true;
-                } else {
-                    float t0 = (0.0f - o[ax]) / d[ax];
-                    float t1 = (n[ax] - o[ax]) / d[ax];
-                    if (t0 > t1) {
-                        const float s = t0;
-                        t0 = t1;
-                        t1 = s;
+        if (!exhausted) {
+            const unsigned idle = __ballot_sync(FULL, s.pix < 0);
+            if (idle) {
+                const int nidle = __popc(idle);
+                int base = 0;
+                if (lane == 0) base = atomicAdd(a.ticket, nidle);
+                base = __shfl_sync(FULL, base, 0);
+                if (base + nidle >= nrays) exhausted = true;
+                if (s.pix < 0) {
+                    const int r = base + __popc(idle & ((1u << lane) - 1u));
+                    if (r < nrays && start_ray(a, r, npix, s) && !(s.tfar > -INFINITY)) {
+                        finish_ray(a, s);   // missed the box: background, no sample
+                        s.pix = -1;
                     }
-                    tn = fmaxf(tn, t0);
-                    tfar = fminf(tfar, t1);
                 }
             }
         }
-        const float tnear = fmaxf(tn, 0.0f);
-        float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
-        float kf = 0.f;   // sample index, kept in float (exact below 2^24)
-        if (!miss && tnear < tfar) {
-            for (;;) {
-                const float t = fmaf(kf, a.dt, tnear);
-                if (t >= tfar) break;
-                kf += 1.0f;
-                const float ux = fmaf(t, dx, ux0), uy = fmaf(t, dy, uy0), uz = fmaf(t, dz, uz0);
-                float tx, ty, tz;
-                const int i = floor_frac(ux, tx), j = floor_frac(uy, ty), k = floor_frac(uz, tz);
-                const bool cfast = (i >= 0) & (i <= a.nx - 2) & (j >= 0) & (j <= a.ny - 2) & (k >= 0) &
-                                   (k <= a.nz - 2);
-                float c[2][2][2], rows[2][2], v;
-                const Vox<T, I, false> vf{vol, vol + ((I)k * a.ny + j) * a.nx + i, a.nx, a.ny, a.nz, i, j, k, sy, sz};
-                const Vox<T, I, true> vc{vol, nullptr, a.nx, a.ny, a.nz, i, j, k, sy, sz};
-                if (cfast) v = cell_value(vf, tx, ty, tz, c, rows);
-                else v = cell_value(vc, tx, ty, tz, c, rows);
-                const float xi = v * tfmax;
-                float fr;
-                int ti = floor_frac(xi, fr);
-                if (ti > a.ntf - 2) {
-                    fr += (float)(ti - (a.ntf - 2));
-                    ti = a.ntf - 2;
-                }
-                if (ti < 0) {
-                    fr += (float)ti;
-                    ti = 0;
-                }
-                const float4 c0 = s_tf[ti], c1 = s_tf[ti + 1];
-                const float al = fmaf(fr, c1.w - c0.w, c0.w);
-                if (al > 0.0f) {
-                    float cr = fmaf(fr, c1.x - c0.x, c0.x);
-                    float cg = fmaf(fr, c1.y - c0.y, c0.y);
-                    float cb = fmaf(fr, c1.z - c0.z, c0.z);
-                    if (SHADE) {
-                        float gx, gy, gz;
-                        const bool gfast = (i >= 1) & (i <= a.nx - 3) & (j >= 1) & (j <= a.ny - 3) & (k >= 1) &
-                                           (k <= a.nz - 3);
-                        if (gfast) cell_gradient(vf, tx, ty, tz, c, rows, gx, gy, gz);
-                        else cell_gradient(vc, tx, ty, tz, c, rows, gx, gy, gz);
-                        const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-                        if (g2 >= 1e-12f) {
-                            const float ndl = fabsf(fmaf(gx, dx, fmaf(gy, dy, gz * dz))) * rsqrtf(g2);
-                            float sp = ndl * ndl;   // ndl^32 by five squarings
-                            sp *= sp;
-                            sp *= sp;
-                            sp *= sp;
-                            sp *= sp;
-                            const float diff = fmaf(0.7f, ndl, 0.2f);
-                            const float spec = 0.3f * sp;
-                            cr = __saturatef(fmaf(cr, diff, spec));
-                            cg = __saturatef(fmaf(cg, diff, spec));
-                            cb = __saturatef(fmaf(cb, diff, spec));
-                        }
-                    }
-                    const float w = (1.0f - A) * al;
-                    C0 = fmaf(w, cr, C0);
-                    C1 = fmaf(w, cg, C1);
-                    C2 = fmaf(w, cb, C2);
-                    A += w;
-                }
-                if (A >= a.term) break;
-            }
+        unsigned busy = __ballot_sync(FULL, s.pix >= 0);
+        if (busy == 0) {
+            if (exhausted) break;
+            continue;
         }
-        my_samples += (unsigned long long)kf;
-        const float ta = 1.0f - A;
-        float* out = a.rgbam + pix;
-        out[0] = fmaf(ta, a.bg0, C0);
-        out[a.plane] = fmaf(ta, a.bg1, C1);
-        out[2 * a.plane] = fmaf(ta, a.bg2, C2);
-        out[3 * a.plane] = A;
-        out[4 * a.plane] = 1.0f;
+        while (busy != 0 && (exhausted || __popc(busy) >= a.refill_below)) {
+            if (s.pix >= 0 && ray_step<T, I, SHADE>(a, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s)) {
+                my_samples += (unsigned long long)s.kf;
+                finish_ray(a, s);
+                s.pix = -1;
+            }
+            busy = __ballot_sync(FULL, s.pix >= 0);
+        }
+        if (exhausted && busy == 0) break;
     }
     if (a.nsamples) {
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) my_samples += __shfl_xor_sync(0xffffffffu, my_samples, o);
+        for (int o = 16; o > 0; o >>= 1) my_samples += __shfl_xor_sync(FULL, my_samples, o);
         if (lane == 0 && my_samples) atomicAdd(a.nsamples, my_samples);
     }
 }
@@ -304,6 +355,7 @@ static fvn_status launch_typed(fvn_ctx* ctx, const MarchArgs& a, bool shade, cud
         FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     FVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
+    if (ctx->march_blocks_per_sm > 0) per_sm = std::min(per_sm, ctx->march_blocks_per_sm);
     if (per_sm < 1) per_sm = 1;
     const int grid = ctx->num_sms * per_sm;
     kern<<<grid, 128, smem, st>>>(a);
@@ -370,6 +422,7 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
     a.rgbam = rgbam;
     a.plane = (long long)a.W * a.H;
     a.nsamples = nsamples;
+    a.refill_below = ctx->march_refill;
     a.ticket = ctx->d_ticket + (ctx->ticket_ring++ & 63);
     if (ids) FVN_CUDA(ctx, cudaMemsetAsync(rgbam, 0, 5 * sizeof(float) * (size_t)a.plane, st));
     FVN_CUDA(ctx, cudaMemsetAsync(a.ticket, 0, sizeof(int), st));

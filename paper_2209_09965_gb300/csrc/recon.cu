@@ -402,11 +402,7 @@ static fvn_status launch_conv(fvn_ctx* ctx, ConvArgs a, cudaStream_t st) {
     return FVN_OK;
 }
 
-struct ReconBuffers {
-    __half *e0a, *e0, *p0, *e1a, *e1, *p1, *ba, *bt, *d1a, *d1, *d0a, *d0;
-};
-
-static size_t plan_buffers(int W4, int H4, ReconBuffers* b, char* base) {
+static size_t plan_buffers(int W4, int H4, ReconPlan* b, char* base) {
     const size_t n0 = (size_t)W4 * H4, n1 = n0 / 4, n2 = n0 / 16;
     const size_t sizes[12] = {n0 * 16, n0 * 16, n1 * 16, n1 * 32, n1 * 32, n2 * 32,
                               n2 * 64, n2 * 64, n1 * 32, n1 * 32, n0 * 16, n0 * 16};
@@ -418,6 +414,10 @@ static size_t plan_buffers(int W4, int H4, ReconBuffers* b, char* base) {
         off += (sizes[i] * sizeof(__half) + 255) & ~(size_t)255;
     }
     return off;
+}
+
+size_t recon_workspace_bytes(int w, int h) {
+    return plan_buffers((w + 3) & ~3, (h + 3) & ~3, nullptr, nullptr);
 }
 
 fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
@@ -436,8 +436,17 @@ fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, int w, int h, int 
         ws.w = W4;
         ws.h = H4;
     }
-    ReconBuffers B;
-    plan_buffers(W4, H4, &B, static_cast<char*>(ws.base));
+    return reconstruct_on(ctx, ws.base, rgbam, w, h, precision, rgb, st);
+}
+
+fvn_status reconstruct_on(fvn_ctx* ctx, void* workspace, const float* rgbam, int w, int h, int precision,
+                          float* rgb, cudaStream_t st) {
+    if (precision != FVN_PREC_FP16)
+        return set_error(ctx, FVN_ERR_UNSUPPORTED, "only FVN_PREC_FP16 is available in this build");
+    const int W4 = (w + 3) & ~3, H4 = (h + 3) & ~3;
+    ReconPlan B;
+    plan_buffers(W4, H4, &B, static_cast<char*>(workspace));
+    if (ctx->conv_impl == CONV_TCGEN05) return reconstruct_tc(ctx, B, rgbam, w, h, rgb, st);
     const ConvW* L = ctx->layers;
     fvn_status s;
     ConvArgs a{};
@@ -513,6 +522,17 @@ extern "C" fvn_status fvn_load_weights(fvn_ctx* ctx, const float* host_w, size_t
             for (int o = 0; o < kHeadC; ++o) hw[kHeadC * 16 + o] = b[o];
             if (!ctx->head_w) FVN_CUDA(ctx, cudaMalloc(&ctx->head_w, hw.size() * sizeof(float)));
             FVN_CUDA(ctx, cudaMemcpy(ctx->head_w, hw.data(), hw.size() * sizeof(float), cudaMemcpyHostToDevice));
+            // tensor-core operand: [k chunk 2][n 32][8], output rows 29..31 zero
+            std::vector<__half> h16(2 * 32 * 8, __float2half(0.f));
+            std::vector<float> hb(32, 0.f);
+            for (int o = 0; o < kHeadC; ++o) {
+                for (int c = 0; c < 16; ++c) h16[((c / 8) * 32 + o) * 8 + (c % 8)] = __float2half(W[o * sp.cin + c]);
+                hb[o] = b[o];
+            }
+            if (!ctx->head_w16) FVN_CUDA(ctx, cudaMalloc(&ctx->head_w16, h16.size() * sizeof(__half)));
+            if (!ctx->head_b32) FVN_CUDA(ctx, cudaMalloc(&ctx->head_b32, hb.size() * sizeof(float)));
+            FVN_CUDA(ctx, cudaMemcpy(ctx->head_w16, h16.data(), h16.size() * sizeof(__half), cudaMemcpyHostToDevice));
+            FVN_CUDA(ctx, cudaMemcpy(ctx->head_b32, hb.data(), hb.size() * sizeof(float), cudaMemcpyHostToDevice));
             continue;
         }
         const int cp = (sp.cin + 15) & ~15;

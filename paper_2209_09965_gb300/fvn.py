@@ -22,15 +22,17 @@ U8, U16, F16, F32 = 0, 1, 2, 3
 PREC_FP16, PREC_FP8 = 0, 1
 
 _STATUS = {0: "FVN_OK", -1: "FVN_ERR_ARG", -2: "FVN_ERR_CUDA", -3: "FVN_ERR_OOM", -4: "FVN_ERR_UNSUPPORTED",
-           -5: "FVN_ERR_STATE"}
+           -5: "FVN_ERR_STATE", -6: "FVN_ERR_TIMEOUT"}
 
 # every symbol include/fvn.h declares
 EXPORTS = (
     "fvn_create", "fvn_destroy", "fvn_last_error", "fvn_make_mask", "fvn_march", "fvn_load_weights",
     "fvn_weight_count", "fvn_reconstruct", "fvn_render", "fvn_conv_fwd", "fvn_conv_bwd", "fvn_avgpool2_fwd",
     "fvn_avgpool2_bwd", "fvn_upsample2_fwd", "fvn_upsample2_bwd", "fvn_kp_blend_fwd", "fvn_kp_blend_bwd",
-    "fvn_loss_l1grad", "fvn_adam_step",
+    "fvn_loss_l1grad", "fvn_adam_step", "fvn_set_option", "fvn_device_status",
 )
+OPT_CONV_KERNEL, OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 1, 2, 3
+CONV_TCGEN05, CONV_MMA_SYNC = 0, 1
 
 
 class FvnError(RuntimeError):
@@ -76,6 +78,8 @@ def _load():
         "fvn_march": [P, P, P, P, P, P, P, P, P, P],
         "fvn_load_weights": [P, P, ctypes.c_size_t],
         "fvn_reconstruct": [P, P, I, I, I, P, P],
+        "fvn_set_option": [P, I, I],
+        "fvn_device_status": [P],
         "fvn_render": [P, P, P, P, P, P, I, P, P, P],
         "fvn_conv_fwd": [P, I, P, I, I, I, I, P, P, I, I, I, P, P],
         "fvn_conv_bwd": [P, I, P, I, I, I, I, P, I, I, P, P, P, P, P, P, P],
@@ -194,6 +198,13 @@ class Context:
             self.close()
         except Exception:
             pass
+
+    def set_option(self, option, value):
+        self._chk(lib.fvn_set_option(self.h, int(option), int(value)))
+
+    def device_status(self):
+        """Synchronise; raise FvnError(FVN_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
+        self._chk(lib.fvn_device_status(self.h))
 
     def last_error(self) -> str:
         return lib.fvn_last_error(self.h).decode(errors="replace")

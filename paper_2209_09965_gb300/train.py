@@ -173,7 +173,7 @@ def forward(P: Params, sparse: torch.Tensor, direct_only: bool = False):
     d0 = cbr("dec0b", cbr("dec0a", _Up.apply(d1), e0))
     head = _Conv.apply(d0, None, P.w("head"), P.b("head"), False, P.gw("head"), P.gb("head"))
     if direct_only:
-        return head[:, 0:3]
+        return head[:, 0:3].contiguous()
     return _KP.apply(head, sparse)
 
 

@@ -119,3 +119,41 @@ def test_loss_and_adam(fvn):
         fvn.adam_step(tp, tg, tm, tv, s)
     torch.cuda.synchronize()
     assert np.abs(N(tp) - prm).max() < 1e-6
+
+
+def test_whole_network_forward_and_gradients_match_oracle(fvn):
+    """train.forward + backward through the autograd shims (every step in the
+    library's FP32 kernels) against the FP64 oracle network."""
+    from paper_2209_09965_gb300 import train, workloads as wl
+    rng = np.random.default_rng(7)
+    flat = wl.net_weights(5)
+    flat = (flat + rng.normal(size=flat.size).astype(np.float32) * 0.01).astype(np.float32)
+    n, h, w = 2, 16, 24
+    sp = np.zeros((n, 5, h, w), np.float32)
+    m = rng.uniform(size=(n, h, w)) < 0.3
+    sp[:, 0:4] = rng.uniform(size=(n, 4, h, w)) * m[:, None]
+    sp[:, 4] = m
+    tgt = rng.uniform(size=(n, 3, h, w)).astype(np.float32)
+    P = train.Params(flat, DEV)
+    pred = train.forward(P, T(sp))
+    loss = train._Loss.apply(pred, T(tgt), 1.0)
+    P.g.zero_()
+    loss.backward()
+    torch.cuda.synchronize()
+    params = onet.unpack(flat)
+    ref, cache = onet.forward(params, sp.astype(np.float64), return_cache=True)
+    lref, gref = onet.loss_l1_grad(ref, tgt)
+    assert np.abs(N(pred) - ref).max() < 1e-4
+    assert abs(float(loss.item()) - lref) < 1e-5
+    grads = onet.backward(params, cache, gref)
+    g = P.g.cpu().numpy().astype(np.float64)
+    ref_g = onet.pack(grads)
+    scale = np.abs(ref_g).max()
+    assert np.abs(g - ref_g).max() < 2e-3 * scale
+
+
+def test_training_reduces_loss(fvn):
+    from paper_2209_09965_gb300 import train
+    _, log = train.train(steps=60, nvol=2, vol_n=64, log_every=20, batch=4)
+    first, last = log[0][1], log[-1][1]
+    assert last < first
