@@ -200,6 +200,31 @@ fvn_status fvn_reconstruct(fvn_ctx* ctx, const float* rgbam, int w, int h, int p
                            void* stream);
 
 /*
+ * fvn_reconstruct_noalloc -- fvn_reconstruct without any allocation.
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory when they reconstruct a frame, such as code
+ * running while a stream is captured into a CUDA graph, engines that fix
+ * their memory budget up front, or real-time loops that cannot afford the
+ * device synchronisation an allocation implies.  Same arguments, kernels and
+ * results as fvn_reconstruct, but the activation workspace is a fixed 64 MiB
+ * device array inside the library (reserved on every GPU that loads the
+ * library, until the process exits) instead of context memory grown with
+ * cudaMalloc.  It never calls cudaMalloc, cudaFree or an allocating routine.
+ *  - Frames whose workspace exceeds 64 MiB (larger than about 512 x 512
+ *    pixels) are rejected with FVN_ERR_ARG before anything is enqueued.
+ *  - The first call on a device looks up the array's device address (once
+ *    per device, with that device current); make that first call before any
+ *    stream capture.
+ *  - Every call, from every context and stream, shares the one array and
+ *    leaves its activations there; calls that overlap on the GPU race on
+ *    it, so serialise them (one stream, or events).  Nothing in the array
+ *    needs to start at zero: every activation is written before it is read.
+ * Needs fvn_load_weights on ctx first (FVN_ERR_STATE otherwise).
+ */
+fvn_status fvn_reconstruct_noalloc(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
+                                   void* stream);
+
+/*
  * fvn_render -- one foveated frame: fvn_make_mask, sparse fvn_march and
  * fvn_reconstruct on context workspace, no host synchronisation.
  * Paper: Fig. "pipeline" (sample mask -> compaction -> sparse rendering ->

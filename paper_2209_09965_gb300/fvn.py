@@ -29,7 +29,7 @@ EXPORTS = (
     "fvn_create", "fvn_destroy", "fvn_last_error", "fvn_make_mask", "fvn_march", "fvn_load_weights",
     "fvn_weight_count", "fvn_reconstruct", "fvn_render", "fvn_conv_fwd", "fvn_conv_bwd", "fvn_avgpool2_fwd",
     "fvn_avgpool2_bwd", "fvn_upsample2_fwd", "fvn_upsample2_bwd", "fvn_kp_blend_fwd", "fvn_kp_blend_bwd",
-    "fvn_loss_l1grad", "fvn_adam_step", "fvn_set_option", "fvn_device_status",
+    "fvn_loss_l1grad", "fvn_adam_step", "fvn_reconstruct_noalloc", "fvn_set_option", "fvn_device_status",
 )
 OPT_CONV_KERNEL, OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 1, 2, 3
 CONV_TCGEN05, CONV_MMA_SYNC = 0, 1
@@ -78,6 +78,7 @@ def _load():
         "fvn_march": [P, P, P, P, P, P, P, P, P, P],
         "fvn_load_weights": [P, P, ctypes.c_size_t],
         "fvn_reconstruct": [P, P, I, I, I, P, P],
+        "fvn_reconstruct_noalloc": [P, P, I, I, I, P, P],
         "fvn_set_option": [P, I, I],
         "fvn_device_status": [P],
         "fvn_render": [P, P, P, P, P, P, I, P, P, P],
@@ -230,6 +231,12 @@ class Context:
     def reconstruct(self, rgbam, w, h, rgb, precision=PREC_FP16, stream=None):
         self._chk(lib.fvn_reconstruct(self.h, _ptr(rgbam), int(w), int(h), int(precision), _ptr(rgb),
                                       _stream(stream)))
+
+    def reconstruct_noalloc(self, rgbam, w, h, rgb, precision=PREC_FP16, stream=None):
+        """fvn_reconstruct on the library's fixed workspace: never allocates
+        (frames up to 512 x 512; calls sharing the workspace must not overlap)."""
+        self._chk(lib.fvn_reconstruct_noalloc(self.h, _ptr(rgbam), int(w), int(h), int(precision), _ptr(rgb),
+                                              _stream(stream)))
 
     def render(self, vol, tf, cam, fov, mp, rgb, precision=PREC_FP16, rgbam_out=None, stream=None):
         v, t, c, m = volume(vol), transfer_function(tf), camera(cam), march_params(mp)
