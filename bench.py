@@ -34,7 +34,7 @@ WEIGHTS = os.path.join(ROOT, "paper_2209_09965_gb300", "weights", "fvn_16_32_64.
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=64)
+    p.add_argument("--steps", type=int, default=256)
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -79,7 +79,7 @@ class ClockSampler:
     def start(self):
         try:
             self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
-                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
                                          stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -264,6 +264,7 @@ def main():
         c0 = torch.zeros(1, dtype=torch.int32, device=dev)
         ctx.make_mask(fov, W, H, m0, i0, c0)
         tuned = {"march": autotune.tune_march(ctx, vol, tf, cam, mp, rgbam, ids=i0, count=c0),
+                 "dense_march": autotune.tune_march(ctx, vol, tf, cam, mp, dense),
                  "conv": autotune.tune_conv(ctx, rgbam, W, H, rgb)}
         ctx.device_status()
 

@@ -103,11 +103,20 @@ fvn_status fvn_destroy(fvn_ctx* ctx);
 /* Tuning options (fvn_set_option); the defaults are what the autotuner picked.
  *  FVN_OPT_CONV_KERNEL: 0 = tcgen05 tensor-core convolutions (TMEM
  *      accumulators), 1 = mma.sync convolutions.
- *  FVN_OPT_MARCH_REFILL: a march warp refills idle lanes with new rays once
- *      fewer than this many lanes (1..32) are busy.
- *  FVN_OPT_MARCH_BLOCKS_PER_SM: persistent march CTAs per SM (0 = as many as
- *      fit). */
-enum { FVN_OPT_CONV_KERNEL = 1, FVN_OPT_MARCH_REFILL = 2, FVN_OPT_MARCH_BLOCKS_PER_SM = 3 };
+ *  FVN_OPT_MARCH_REFILL: a sparse-march warp refills idle lanes with new
+ *      rays once fewer than this many lanes (1..32) are busy (1 = only whole
+ *      32-ray packets).
+ *  FVN_OPT_MARCH_BLOCKS_PER_SM: persistent sparse-march CTAs per SM (0 = as
+ *      many as fit).
+ *  FVN_OPT_MARCH_REFILL_DENSE, FVN_OPT_MARCH_BLOCKS_PER_SM_DENSE: the same
+ *      for the dense march (ids == NULL). */
+enum {
+    FVN_OPT_CONV_KERNEL = 1,
+    FVN_OPT_MARCH_REFILL = 2,
+    FVN_OPT_MARCH_BLOCKS_PER_SM = 3,
+    FVN_OPT_MARCH_REFILL_DENSE = 4,
+    FVN_OPT_MARCH_BLOCKS_PER_SM_DENSE = 5
+};
 fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value);
 
 /* Synchronise the device and report a device-side failure recorded by this

@@ -35,16 +35,19 @@ def _time(fn, reps=3):
 
 
 def tune_march(ctx: fvn.Context, vol, tf, cam, mp, rgbam, ids=None, count=None,
-               refills=(8, 16, 24, 28, 32), blocks=(0, 4, 6)):
-    """Pick (refill threshold, CTAs per SM) for the march of this frame."""
+               refills=(1, 8, 16, 24, 28), blocks=(0, 4, 6)):
+    """Pick (refill threshold, CTAs per SM) for the march of this frame: the
+    sparse march when ids are given, the dense march otherwise."""
+    o_refill = fvn.OPT_MARCH_REFILL if ids is not None else fvn.OPT_MARCH_REFILL_DENSE
+    o_blocks = fvn.OPT_MARCH_BLOCKS_PER_SM if ids is not None else fvn.OPT_MARCH_BLOCKS_PER_SM_DENSE
     results = {}
     for r, b in itertools.product(refills, blocks):
-        ctx.set_option(fvn.OPT_MARCH_REFILL, r)
-        ctx.set_option(fvn.OPT_MARCH_BLOCKS_PER_SM, b)
+        ctx.set_option(o_refill, r)
+        ctx.set_option(o_blocks, b)
         results[(r, b)] = _time(lambda: ctx.march(vol, tf, cam, mp, rgbam, ids=ids, count=count))
     best = min(results, key=results.get)
-    ctx.set_option(fvn.OPT_MARCH_REFILL, best[0])
-    ctx.set_option(fvn.OPT_MARCH_BLOCKS_PER_SM, best[1])
+    ctx.set_option(o_refill, best[0])
+    ctx.set_option(o_blocks, best[1])
     return {"refill": best[0], "blocks_per_sm": best[1], "ms": results[best],
             "candidates": {f"{k[0]}/{k[1]}": round(v, 4) for k, v in results.items()}}
 

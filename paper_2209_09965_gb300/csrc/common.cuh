@@ -79,9 +79,13 @@ struct fvn_ctx {
     __half* head_w16 = nullptr;       // head weights as a tensor-core operand: [2][32][8] FP16 (rows 29-31 zero)
     float* head_b32 = nullptr;        // head bias padded to 32
     int* d_error = nullptr;           // device-side error flag (a bounded wait gave up)
-    int conv_impl = fvn::CONV_MMA_SYNC;
-    int march_refill = 24;            // refill idle lanes once fewer than this many are busy
-    int march_blocks_per_sm = 0;      // 0 = occupancy limit
+    int conv_impl = fvn::CONV_TCGEN05;
+    int march_refill = 24;            // sparse march: refill idle lanes once fewer than this many are busy
+    int march_blocks_per_sm = 0;      // sparse march CTAs per SM, 0 = occupancy limit
+    int march_refill_dense = 1;       // dense march: 1 = whole 32-ray packets only
+    int march_blocks_per_sm_dense = 0;
+    void* pad_buf = nullptr;          // padded copy of the volume read by the march
+    size_t pad_bytes = 0;
     float* d_act_scale = nullptr;     // FP8 per-layer activation scales
     fvn::ReconWorkspace recon_ws;
     fvn::RenderWorkspace render_ws;

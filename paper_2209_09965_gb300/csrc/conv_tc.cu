@@ -411,9 +411,13 @@ static fvn_status launch_tc(fvn_ctx* ctx, TcArgs a, cudaStream_t st) {
         FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
         configured = true;
     }
-    int per_sm = 0;
-    FVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, L::bytes));
-    per_sm = std::min(per_sm, (int)(512 / L::tmem_cols));   // never wait in tcgen05.alloc
+    // CTAs per SM from the shared-memory budget (1 KB reserved per CTA) and
+    // the 512 TMEM columns, so that no CTA ever waits in tcgen05.alloc.
+    int smem_sm = 0;
+    FVN_CUDA(ctx, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+    int per_sm = smem_sm / (int)(L::bytes + 1024);
+    per_sm = std::min(per_sm, (int)(512 / L::tmem_cols));
+    per_sm = std::min(per_sm, 16);
     if (per_sm < 1) return set_error(ctx, FVN_ERR_CUDA, "tensor-core conv kernel does not fit on an SM");
     a.tiles_x = (a.Wl + TW - 1) / TW;
     a.ntiles = a.tiles_x * ((a.Hl + TR - 1) / TR);

@@ -101,6 +101,7 @@ extern "C" fvn_status fvn_destroy(fvn_ctx* ctx) {
     cudaFree(ctx->d_error);
     cudaFree(ctx->d_act_scale);
     cudaFree(ctx->d_ticket);
+    cudaFree(ctx->pad_buf);
     cudaFree(ctx->recon_ws.base);
     cudaFree(ctx->render_ws.mask);
     cudaFree(ctx->render_ws.ids);
@@ -128,6 +129,14 @@ extern "C" fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value) {
         case FVN_OPT_MARCH_BLOCKS_PER_SM:
             FVN_CHECK_ARG(ctx, value >= 0 && value <= 16, "blocks per SM must be in [0, 16]");
             ctx->march_blocks_per_sm = value;
+            return FVN_OK;
+        case FVN_OPT_MARCH_REFILL_DENSE:
+            FVN_CHECK_ARG(ctx, value >= 1 && value <= 32, "refill threshold must be in [1, 32]");
+            ctx->march_refill_dense = value;
+            return FVN_OK;
+        case FVN_OPT_MARCH_BLOCKS_PER_SM_DENSE:
+            FVN_CHECK_ARG(ctx, value >= 0 && value <= 16, "blocks per SM must be in [0, 16]");
+            ctx->march_blocks_per_sm_dense = value;
             return FVN_OK;
         default:
             return set_error(ctx, FVN_ERR_ARG, "unknown option %d", option);

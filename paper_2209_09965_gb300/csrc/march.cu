@@ -24,8 +24,15 @@
 
 namespace fvn {
 
+// The march reads a copy of the volume with kPad voxels of clamp-to-edge
+// border on every side: every index of the 32-voxel stencil of a sample in
+// the box is then inside the copy, so the per-sample code has no clamping
+// and no divergent boundary path.
+constexpr int kPad = 2;
+
 struct MarchArgs {
     const void* vol;
+    const void* pvol;                 // padded copy, (nx + 4) x (ny + 4) x (nz + 4)
     int nx, ny, nz;
     int ntf;
     const float4* tf;
@@ -230,13 +237,16 @@ __device__ __forceinline__ bool ray_step(const MarchArgs& a, const T* __restrict
     s.kf += 1.0f;
     const float ux = fmaf(t, s.dx, ux0), uy = fmaf(t, s.dy, uy0), uz = fmaf(t, s.dz, uz0);
     float tx, ty, tz;
-    const int i = floor_frac(ux, tx), j = floor_frac(uy, ty), k = floor_frac(uz, tz);
-    const bool cfast = (i >= 0) & (i <= a.nx - 2) & (j >= 0) & (j <= a.ny - 2) & (k >= 0) & (k <= a.nz - 2);
-    float c[2][2][2], rows[2][2], v;
-    const Vox<T, I, false> vf{vol, vol + ((I)k * a.ny + j) * a.nx + i, a.nx, a.ny, a.nz, i, j, k, sy, sz};
-    const Vox<T, I, true> vc{vol, nullptr, a.nx, a.ny, a.nz, i, j, k, sy, sz};
-    if (cfast) v = cell_value(vf, tx, ty, tz, c, rows);
-    else v = cell_value(vc, tx, ty, tz, c, rows);
+    int i = floor_frac(ux, tx), j = floor_frac(uy, ty), k = floor_frac(uz, tz);
+    // samples lie in the box, so i is in [-1, n - 1]; the clamp only guards
+    // against rounding and keeps every stencil index inside the padded copy
+    i = min(max(i, -1), a.nx - 1);
+    j = min(max(j, -1), a.ny - 1);
+    k = min(max(k, -1), a.nz - 1);
+    float c[2][2][2], rows[2][2];
+    const Vox<T, I, false> vf{vol, vol + ((I)(k + kPad) * sz + (I)(j + kPad) * sy + (i + kPad)), a.nx, a.ny, a.nz,
+                              i, j, k, sy, sz};
+    const float v = cell_value(vf, tx, ty, tz, c, rows);
     const float xi = v * tfmax;
     float fr;
     int ti = floor_frac(xi, fr);
@@ -256,9 +266,7 @@ __device__ __forceinline__ bool ray_step(const MarchArgs& a, const T* __restrict
         float cb = fmaf(fr, c1.z - c0.z, c0.z);
         if (SHADE) {
             float gx, gy, gz;
-            const bool gfast = (i >= 1) & (i <= a.nx - 3) & (j >= 1) & (j <= a.ny - 3) & (k >= 1) & (k <= a.nz - 3);
-            if (gfast) cell_gradient(vf, tx, ty, tz, c, rows, gx, gy, gz);
-            else cell_gradient(vc, tx, ty, tz, c, rows, gx, gy, gz);
+            cell_gradient(vf, tx, ty, tz, c, rows, gx, gy, gz);
             const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
             if (g2 >= 1e-12f) {   // |g| >= 1e-6: shade, otherwise keep the TF colour
                 const float ndl = fabsf(fmaf(gx, s.dx, fmaf(gy, s.dy, gz * s.dz))) * rsqrtf(g2);
@@ -294,13 +302,13 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
     for (int i = threadIdx.x; i < a.ntf; i += blockDim.x) s_tf[i] = a.tf[i];
     __syncthreads();
     const unsigned FULL = 0xffffffffu;
-    const T* __restrict__ vol = static_cast<const T*>(a.vol);
+    const T* __restrict__ vol = static_cast<const T*>(a.pvol);
     const int lane = threadIdx.x & 31;
     const int npix = a.W * a.H;
     // the id list never holds more than one entry per pixel
     const int nrays = a.ids ? min(max(*a.count, 0), npix) : a.n_dense;
     const float tfmax = (float)(a.ntf - 1);
-    const I sy = (I)a.nx, sz = (I)a.nx * a.ny;
+    const I sy = (I)(a.nx + 2 * kPad), sz = sy * (I)(a.ny + 2 * kPad);   // padded strides
     // sample positions are handled in voxel-centre coordinates u = p - 0.5
     const float ux0 = a.ox - 0.5f, uy0 = a.oy - 0.5f, uz0 = a.oz - 0.5f;
     unsigned long long my_samples = 0;
@@ -347,15 +355,38 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
     }
 }
 
+template <typename T>
+__global__ void pad_volume_kernel(const T* __restrict__ src, int nx, int ny, int nz, T* __restrict__ dst) {
+    const int px = nx + 2 * kPad, py = ny + 2 * kPad, pz = nz + 2 * kPad;
+    const long long total = (long long)px * py * pz;
+    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
+         o += (long long)gridDim.x * blockDim.x) {
+        const int x = (int)(o % px);
+        const long long r = o / px;
+        const int y = (int)(r % py), z = (int)(r / py);
+        const int sx = min(max(x - kPad, 0), nx - 1), sy = min(max(y - kPad, 0), ny - 1),
+                  sz = min(max(z - kPad, 0), nz - 1);
+        dst[o] = src[((long long)sz * ny + sy) * nx + sx];
+    }
+}
+
 template <typename T, typename I>
 static fvn_status launch_typed(fvn_ctx* ctx, const MarchArgs& a, bool shade, cudaStream_t st) {
     const size_t smem = (size_t)a.ntf * sizeof(float4);
+    {   // refresh the padded copy of the volume (one pass over it)
+        const long long total = (long long)(a.nx + 2 * kPad) * (a.ny + 2 * kPad) * (a.nz + 2 * kPad);
+        const int grid = (int)std::min<long long>((total + 255) / 256, 64LL * ctx->num_sms);
+        pad_volume_kernel<T><<<grid, 256, 0, st>>>(static_cast<const T*>(a.vol), a.nx, a.ny, a.nz,
+                                                   static_cast<T*>(const_cast<void*>(a.pvol)));
+        FVN_LAUNCH_CHECK(ctx);
+    }
     auto kern = shade ? march_kernel<T, I, true> : march_kernel<T, I, false>;
     if (smem > 48 * 1024)
         FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
     FVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
-    if (ctx->march_blocks_per_sm > 0) per_sm = std::min(per_sm, ctx->march_blocks_per_sm);
+    const int bps = a.ids ? ctx->march_blocks_per_sm : ctx->march_blocks_per_sm_dense;
+    if (bps > 0) per_sm = std::min(per_sm, bps);
     if (per_sm < 1) per_sm = 1;
     const int grid = ctx->num_sms * per_sm;
     kern<<<grid, 128, smem, st>>>(a);
@@ -422,11 +453,24 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
     a.rgbam = rgbam;
     a.plane = (long long)a.W * a.H;
     a.nsamples = nsamples;
-    a.refill_below = ctx->march_refill;
+    a.refill_below = ids ? ctx->march_refill : ctx->march_refill_dense;
     a.ticket = ctx->d_ticket + (ctx->ticket_ring++ & 63);
     if (ids) FVN_CUDA(ctx, cudaMemsetAsync(rgbam, 0, 5 * sizeof(float) * (size_t)a.plane, st));
     FVN_CUDA(ctx, cudaMemsetAsync(a.ticket, 0, sizeof(int), st));
-    const bool big = (unsigned long long)vol->nx * vol->ny * vol->nz >= (1ull << 31);
+    const size_t esize = vol->dtype == FVN_U8 ? 1 : (vol->dtype == FVN_F32 ? 4 : 2);
+    const unsigned long long padded =
+        (unsigned long long)(vol->nx + 2 * kPad) * (vol->ny + 2 * kPad) * (vol->nz + 2 * kPad);
+    if (ctx->pad_bytes < padded * esize) {
+        // growing the padded-volume scratch is a synchronising step
+        FVN_CUDA(ctx, cudaDeviceSynchronize());
+        cudaFree(ctx->pad_buf);
+        ctx->pad_buf = nullptr;
+        ctx->pad_bytes = 0;
+        FVN_CUDA(ctx, cudaMalloc(&ctx->pad_buf, padded * esize));
+        ctx->pad_bytes = padded * esize;
+    }
+    a.pvol = ctx->pad_buf;
+    const bool big = padded >= (1ull << 31);
     const bool shade = mp->shading != 0;
     switch (vol->dtype) {
         case FVN_U8:

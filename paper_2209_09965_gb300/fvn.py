@@ -32,6 +32,7 @@ EXPORTS = (
     "fvn_loss_l1grad", "fvn_adam_step", "fvn_reconstruct_noalloc", "fvn_set_option", "fvn_device_status",
 )
 OPT_CONV_KERNEL, OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 1, 2, 3
+OPT_MARCH_REFILL_DENSE, OPT_MARCH_BLOCKS_PER_SM_DENSE = 4, 5
 CONV_TCGEN05, CONV_MMA_SYNC = 0, 1
 
 
