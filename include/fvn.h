@@ -209,6 +209,19 @@ fvn_status fvn_reconstruct(fvn_ctx* ctx, const float* rgbam, int w, int h, int p
                            void* stream);
 
 /*
+ * fvn_calibrate_fp8 -- activation scales and E4M3 weights for
+ * FVN_PREC_FP8.  Paper: "Model Precision & Optimization" (post-training
+ * reduction of precision; the paper's INT8 path used a calibrating engine
+ * builder).  Runs the FP16 network on the sparse frame rgbam ([5][h][w],
+ * device), takes the largest value of every activation tensor (a running
+ * maximum over calls unless reset != 0), sets each tensor's scale to
+ * amax / 448 and re-quantises the weights to E4M3 with those input scales
+ * folded in and one scale per output channel.  Synchronises the host.
+ * fvn_load_weights discards the FP8 state.
+ */
+fvn_status fvn_calibrate_fp8(fvn_ctx* ctx, const float* rgbam, int w, int h, int reset, void* stream);
+
+/*
  * fvn_reconstruct_noalloc -- fvn_reconstruct without any allocation.
  * The paper has no counterpart: this entry point exists for callers that
  * cannot allocate device memory when they reconstruct a frame, such as code
@@ -244,6 +257,24 @@ fvn_status fvn_reconstruct_noalloc(fvn_ctx* ctx, const float* rgbam, int w, int 
 fvn_status fvn_render(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
                       const fvn_foveation* fov, const fvn_march_params* mp, int precision, float* rgb,
                       float* rgbam_out, void* stream);
+
+/*
+ * fvn_render_adaptive -- fvn_render with a denser-mask fallback (the paper
+ * has no counterpart; this is the frame-quality guard of this library).
+ * After each frame a probe set -- the pixels whose second hash of
+ * (seed ^ 0x9E3779B9, frame, y, x) has its top 24 bits below 2^16 (1/256 of
+ * the frame) and that the mask left out -- is ray-marched too, and the PSNR
+ * of the reconstruction against those probes (RGB clamped to [0, 1]) is the
+ * frame's error estimate.  While the estimate is below min_psnr_db and fewer
+ * than max_levels re-renders were made, the frame is rendered again with
+ * P_b doubled (capped at 1).  level_out / psnr_out (host, optional) receive
+ * the number of re-renders and the last estimate.  Synchronises the host
+ * once per level (it reads the 12-byte error sum).
+ */
+fvn_status fvn_render_adaptive(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
+                               const fvn_foveation* fov, const fvn_march_params* mp, int precision,
+                               float min_psnr_db, int max_levels, float* rgb, int* level_out, float* psnr_out,
+                               void* stream);
 
 /* ------------------------------------------------------------------------
  * Training kernels (FP32, NCHW with batch N).  Paper: "Training" and "Loss"

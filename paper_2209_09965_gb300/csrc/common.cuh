@@ -9,6 +9,7 @@
 #include <stdio.h>
 
 #include <string>
+#include <vector>
 
 #include "../../include/fvn.h"
 
@@ -55,6 +56,20 @@ struct ReconPlan {
 
 enum ConvImpl { CONV_TCGEN05 = 0, CONV_MMA_SYNC = 1 };
 
+// Activation tensors with an FP8 scale (per tensor, from calibration).
+enum Fp8Tensor {
+    FP8_RGBAM = 0, FP8_E0A, FP8_E0, FP8_P0, FP8_E1A, FP8_E1, FP8_P1, FP8_BA, FP8_BT, FP8_D1A, FP8_D1, FP8_D0A,
+    FP8_NT
+};
+
+struct ProbeWorkspace {
+    int w = 0, h = 0;
+    int32_t* ids = nullptr;
+    int32_t* count = nullptr;
+    float* rgbam = nullptr;
+    double* acc = nullptr;
+};
+
 struct RenderWorkspace {
     int w = 0, h = 0;
     uint8_t* mask = nullptr;
@@ -80,6 +95,11 @@ struct fvn_ctx {
     float* head_b32 = nullptr;        // head bias padded to 32
     int* d_error = nullptr;           // device-side error flag (a bounded wait gave up)
     int conv_impl = fvn::CONV_TCGEN05;
+    std::vector<float> host_weights;  // FP32 weights as loaded (re-quantised at FP8 calibration)
+    bool has_fp8 = false;
+    float fp8_amax[fvn::FP8_NT] = {};
+    float fp8_inv_scale[fvn::FP8_NT] = {};
+    float* d_amax = nullptr;          // device amax accumulators [FP8_NT]
     int march_refill = 24;            // sparse march: refill idle lanes once fewer than this many are busy
     int march_blocks_per_sm = 0;      // sparse march CTAs per SM, 0 = occupancy limit
     int march_refill_dense = 1;       // dense march: 1 = whole 32-ray packets only
@@ -89,6 +109,7 @@ struct fvn_ctx {
     float* d_act_scale = nullptr;     // FP8 per-layer activation scales
     fvn::ReconWorkspace recon_ws;
     fvn::RenderWorkspace render_ws;
+    fvn::ProbeWorkspace probe_ws;
 };
 
 namespace fvn {
@@ -131,5 +152,8 @@ fvn_status reconstruct_on(fvn_ctx* ctx, void* workspace, const float* rgbam, int
 size_t recon_workspace_bytes(int w, int h);
 fvn_status reconstruct_tc(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, int w, int h, float* rgb,
                           cudaStream_t st);
+fvn_status reconstruct_tc_fp8(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, int w, int h, float* rgb,
+                              cudaStream_t st);
+fvn_status calibrate_amax(fvn_ctx* ctx, const ReconPlan& B, int w, int h, float* d_amax, cudaStream_t st);
 
 }  // namespace fvn

@@ -1,25 +1,35 @@
 // Reconstruction convolutions on the 5th-generation tensor cores (tcgen05):
 // implicit GEMM with the accumulators in tensor memory (paper: "Reconstruction
-// Network"; the arithmetic is that of recon.cu's layers).
+// Network"; the arithmetic is that of recon.cu's layers), with FP16 operands
+// or FP8 E4M3 operands (paper: "Model Precision & Optimization" runs the
+// network at reduced precision after training).
 //
 // Tile = TR output rows x 128 pixels.  For each row the GEMM is
-// M = 128 pixels, N = COUT, K = 9 taps x CIN, issued as 9 x CIN/16
-// tcgen05.mma (kind::f16, M=128, K=16) by one thread into a TMEM accumulator
-// of COUT columns.  The input halo (TR+2 rows x 130 pixels) is staged in
-// shared memory as planes of 8 channels x 16 bytes per pixel: that is the
-// K-major, non-swizzled core-matrix layout the tensor core reads (8 pixels x
-// 16 bytes contiguous), so the tap shift (dy, dx) is only a start-address
-// offset of the operand descriptor (LBO = one channel plane, SBO = 128 B).
-// Weights stay resident in shared memory in the same layout
-// ([tap][cin/8][cout][8]).  Epilogue: each thread owns one pixel (one TMEM
-// lane): bias, ReLU, FP16, 16-byte NHWC stores; fused 2x2 average pooling;
-// for the last decoder conv a second MMA applies the 1x1 head (16 -> 29,
-// padded to 32) from the activations written back to shared memory, and the
-// thread finishes its pixel with the softmax 5x5 kernel prediction over the
-// sparse samples (staged in shared memory) and the blend.
+// M = 128 pixels, N = COUT, K = 9 taps x CIN, issued as tcgen05.mma
+// (kind::f16 with K = 16, or kind::f8f6f4 with K = 32) by one thread into a
+// TMEM accumulator of COUT columns.  The input halo (TR+2 rows x 130 pixels)
+// is staged in shared memory as planes of 16 bytes per pixel (8 FP16 or 16
+// FP8 channels): that is the K-major, non-swizzled core-matrix layout the
+// tensor core reads (8 pixels x 16 bytes contiguous), so the tap shift
+// (dy, dx) is only a start-address offset of the operand descriptor
+// (LBO = one channel plane, SBO = 128 B).  Weights stay resident in shared
+// memory in the same layout ([tap][cin chunk][cout][16 B]).  Epilogue: each
+// thread owns one pixel (one TMEM lane): scale, bias, ReLU, FP16 / FP8,
+// 16-byte NHWC stores; fused 2x2 average pooling; for the last decoder conv a
+// second MMA applies the 1x1 head (16 -> 29, padded to 32) from the
+// activations written back to shared memory, and the thread finishes its
+// pixel with the softmax 5x5 kernel prediction over the sparse samples
+// (staged in shared memory) and the blend.
+//
+// FP8: an activation tensor t is stored as q = x / s_t (s_t = amax_t / 448
+// from calibration); a layer's weights are stored as e4m3(w s_in / s_w[co])
+// with the input scales folded in per input channel and one scale per output
+// channel, so the accumulator times s_w[co] is the FP32 pre-activation.
+#include <cuda_fp8.h>
 #include <math.h>
 
 #include <algorithm>
+#include <vector>
 
 #include "common.cuh"
 #include "tc.cuh"
@@ -59,26 +69,54 @@ __device__ __forceinline__ void unpack8h(uint4 u, float* v) {
         v[2 * i + 1] = f.y;
     }
 }
+__device__ __forceinline__ uint32_t pack4q(float a, float b, float c, float d) {
+    const uint32_t lo = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+    const uint32_t hi = __nv_cvt_float2_to_fp8x2(make_float2(c, d), __NV_SATFINITE, __NV_E4M3);
+    return lo | (hi << 16);
+}
+__device__ __forceinline__ uint4 pack16q(const float* v) {
+    return make_uint4(pack4q(v[0], v[1], v[2], v[3]), pack4q(v[4], v[5], v[6], v[7]),
+                      pack4q(v[8], v[9], v[10], v[11]), pack4q(v[12], v[13], v[14], v[15]));
+}
+__device__ __forceinline__ void unpack16q(uint4 u, float* v) {
+    const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            const __half2_raw hr =
+                __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((w[i] >> (16 * j)) & 0xFFFFu), __NV_E4M3);
+            const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&hr));
+            v[4 * i + 2 * j] = f.x;
+            v[4 * i + 2 * j + 1] = f.y;
+        }
+    }
+}
 
-template <int CIN, int COUT, int TR, int MODE, int EPI, int CUP>
+// CIN: padded input channels (the GEMM's K per tap); CG: channels of the
+// tensor(s) read from memory (the rest of CIN is zero).
+template <int CIN, int CG, int COUT, int TR, int MODE, int EPI, int CUP, bool F8>
 struct TcLayout {
-    static constexpr int CH = CIN / 8;
+    static constexpr int EB = F8 ? 1 : 2;              // bytes per element
+    static constexpr int CPC = 16 / EB;                // channels per 16-byte chunk
+    static constexpr int CH = CIN / CPC;               // chunks per pixel (K per tap / chunk)
+    static constexpr int CHG = CG / CPC;               // chunks read from memory
     static constexpr int HY = TR + 2;
     static constexpr int CR = TR / 2 + 3, CC = TW / 2 + 3;        // coarse halo (up-sampling)
     static constexpr size_t w_off = 0;
-    static constexpr size_t w_bytes = 9ull * CIN * COUT * 2;
+    static constexpr size_t w_bytes = 9ull * CIN * COUT * EB;
     static constexpr size_t halo_off = w_off + w_bytes;
     static constexpr size_t halo_bytes = (size_t)CH * HY * HXW * 16;
     static constexpr size_t coarse_off = halo_off + halo_bytes;
-    static constexpr size_t coarse_bytes = MODE == TIN_UPCAT ? (size_t)(CUP / 8) * CR * CC * 16 : 0;
+    static constexpr size_t coarse_bytes = MODE == TIN_UPCAT ? (size_t)(CUP / CPC) * CR * CC * 16 : 0;
     static constexpr size_t ha_off = coarse_off + coarse_bytes;     // head operand A: [TR][2][128][8] halves
     static constexpr size_t ha_bytes = EPI == TEPI_HEADKP ? (size_t)TR * 2 * TW * 16 : 0;
     static constexpr size_t hb_off = ha_off + ha_bytes;             // head weights: [2][32][8] halves
     static constexpr size_t hb_bytes = EPI == TEPI_HEADKP ? 2 * 32 * 16 : 0;
     static constexpr size_t sp_off = hb_off + hb_bytes;             // sparse R, G, B, M: [TR+4][TW+4] float4
     static constexpr size_t sp_bytes = EPI == TEPI_HEADKP ? (size_t)(TR + 4) * (TW + 4) * 16 : 0;
-    static constexpr size_t bias_off = sp_off + sp_bytes;
-    static constexpr size_t bias_bytes = (COUT + 32) * 4;
+    static constexpr size_t bias_off = sp_off + sp_bytes;           // bias [COUT], head bias [32], FP8 scales [COUT]
+    static constexpr size_t bias_bytes = (2 * COUT + 32) * 4;
     static constexpr size_t bar_off = bias_off + bias_bytes;
     static constexpr size_t bytes = bar_off + 16;
     static constexpr uint32_t acc_cols = TR * COUT;
@@ -88,27 +126,51 @@ struct TcLayout {
 };
 
 struct TcArgs {
-    const __half* in;        // NHWC input, or the coarse level for up-sampling
-    const __half* skip;      // skip tensor (up-sampling layers)
+    const void* in;          // NHWC input, or the coarse level for up-sampling
+    const void* skip;        // skip tensor (up-sampling layers)
     const float* rgbam;      // sparse frame [5][H0][W0] (first layer, KP)
     int H0, W0;
-    const __half* w;         // [9][CIN/8][COUT][8]
+    const void* w;           // [9][CIN/CPC][COUT][16 B]
     const float* bias;
+    const float* wscale;     // FP8: per output channel weight scale
+    float in_q;              // FP8 first layer: 1 / s of the sparse frame
+    float out_q, pool_q;     // FP8: 1 / s of the output / pooled tensor
     const __half* head_w;    // [2][32][8] halves (KP layer)
     const float* head_b;     // [32]
-    __half* out;             // [Hl][Wl][COUT]
-    __half* pooled;          // [Hl/2][Wl/2][COUT]
+    void* out;               // [Hl][Wl][COUT]
+    void* pooled;            // [Hl/2][Wl/2][COUT]
     float* rgb;              // [3][H0][W0] (KP layer)
     int Hl, Wl;
     int tiles_x, ntiles;
     int* error;              // set when a tensor-core wait gives up
 };
 
-template <int CIN, int COUT, int TR, int MODE, int EPI, int CUP>
+// Store COUT channel values of one pixel (FP16, or FP8 after scaling by q).
+template <int COUT, bool F8>
+__device__ __forceinline__ void store_pixel(void* base, long long pix, const float* v, float q) {
+    if (F8) {
+        uint4* o = reinterpret_cast<uint4*>(static_cast<uint8_t*>(base) + pix * COUT);
+#pragma unroll
+        for (int c = 0; c < COUT; c += 16) {
+            float s[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) s[j] = v[c + j] * q;
+            o[c / 16] = pack16q(s);
+        }
+    } else {
+        uint4* o = reinterpret_cast<uint4*>(static_cast<__half*>(base) + pix * COUT);
+#pragma unroll
+        for (int c = 0; c < COUT; c += 8) o[c / 8] = pack8h(v + c);
+    }
+}
+
+template <int CIN, int CG, int COUT, int TR, int MODE, int EPI, int CUP, bool F8>
 __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
-    using L = TcLayout<CIN, COUT, TR, MODE, EPI, CUP>;
-    constexpr int CH = L::CH, HY = L::HY;
-    static_assert(CIN % 16 == 0 && COUT % 16 == 0 && COUT <= 64, "unsupported conv shape");
+    using L = TcLayout<CIN, CG, COUT, TR, MODE, EPI, CUP, F8>;
+    constexpr int CH = L::CH, CHG = L::CHG, CPC = L::CPC, EB = L::EB, HY = L::HY;
+    constexpr int CUPC = CUP / CPC;                   // up-sampled chunks
+    static_assert(COUT % 16 == 0 && COUT <= 64, "unsupported conv shape");
+    static_assert(CIN % (2 * CPC) == 0, "K per tap must be a multiple of the MMA K");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sW = smem + L::w_off;
     unsigned char* sH = smem + L::halo_off;
@@ -117,6 +179,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
     unsigned char* sHB = smem + L::hb_off;
     float4* sSP = reinterpret_cast<float4*>(smem + L::sp_off);
     float* sBias = reinterpret_cast<float*>(smem + L::bias_off);
+    float* sScale = sBias + COUT + 32;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::bar_off);
     uint32_t* tbase_s = reinterpret_cast<uint32_t*>(smem + L::bar_off + 8);
 
@@ -125,7 +188,10 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
         const uint4* src = reinterpret_cast<const uint4*>(a.w);
         uint4* dst = reinterpret_cast<uint4*>(sW);
         for (int i = tid; i < (int)(L::w_bytes / 16); i += 128) dst[i] = __ldg(src + i);
-        for (int i = tid; i < COUT; i += 128) sBias[i] = __ldg(a.bias + i);
+        for (int i = tid; i < COUT; i += 128) {
+            sBias[i] = __ldg(a.bias + i);
+            sScale[i] = F8 ? __ldg(a.wscale + i) : 1.0f;
+        }
         if (EPI == TEPI_HEADKP) {
             const uint4* hs = reinterpret_cast<const uint4*>(a.head_w);
             for (int i = tid; i < 2 * 32; i += 128) reinterpret_cast<uint4*>(sHB)[i] = __ldg(hs + i);
@@ -140,7 +206,9 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
     tc::fence_after_sync();
     const uint32_t tmem = *tbase_s;
     const uint32_t sW_u = tc::smem_addr(sW), sH_u = tc::smem_addr(sH);
-    constexpr uint32_t idesc = tc::idesc_f16(128, COUT);
+    constexpr uint32_t idesc = F8 ? tc::idesc_e4m3(128, COUT) : tc::idesc_f16(128, COUT);
+    const unsigned char* gin = static_cast<const unsigned char*>(a.in);
+    const unsigned char* gskip = static_cast<const unsigned char*>(a.skip);
     uint32_t phase = 0;
     bool failed = false;
 
@@ -157,28 +225,31 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
             for (int i = tid; i < HY * HXW; i += 128) {
                 const int hy = i / HXW, hx = i - hy * HXW;
                 const int gy = y0 + hy - 1, gx = x0 + hx - 1;
-                float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                float v[16];
+#pragma unroll
+                for (int c = 0; c < 16; ++c) v[c] = 0.f;
                 if (gy >= 0 && gx >= 0 && gy < a.H0 && gx < a.W0) {
                     const float* p = a.rgbam + (long long)gy * a.W0 + gx;
 #pragma unroll
-                    for (int c = 0; c < 5; ++c) v[c] = __ldg(p + c * plane);
+                    for (int c = 0; c < 5; ++c) v[c] = __ldg(p + c * plane) * (F8 ? a.in_q : 1.0f);
                 }
-                *reinterpret_cast<uint4*>(sH + ((0 * HY + hy) * HXW + hx) * 16) = pack8h(v);
+                *reinterpret_cast<uint4*>(sH + ((0 * HY + hy) * HXW + hx) * 16) = F8 ? pack16q(v) : pack8h(v);
 #pragma unroll
                 for (int c = 1; c < CH; ++c)
                     *reinterpret_cast<uint4*>(sH + ((c * HY + hy) * HXW + hx) * 16) = make_uint4(0, 0, 0, 0);
             }
         } else {
-            constexpr int CS0 = MODE == TIN_UPCAT ? CUP / 8 : 0;   // first chunk read from global
+            constexpr int CS0 = MODE == TIN_UPCAT ? CUPC : 0;   // first chunk read from global
             for (int i = tid; i < (CH - CS0) * HY * HXW; i += 128) {
                 const int c = CS0 + i / (HY * HXW);
                 const int rem = i % (HY * HXW);
                 const int hy = rem / HXW, hx = rem - hy * HXW;
                 const int gy = y0 + hy - 1, gx = x0 + hx - 1;
                 unsigned char* dst = sH + ((c * HY + hy) * HXW + hx) * 16;
-                if (gy >= 0 && gx >= 0 && gy < a.Hl && gx < a.Wl) {
-                    if (MODE == TIN_NHWC) cp16(tc::smem_addr(dst), a.in + ((long long)gy * a.Wl + gx) * CIN + c * 8);
-                    else cp16(tc::smem_addr(dst), a.skip + ((long long)gy * a.Wl + gx) * (CIN - CUP) + (c - CS0) * 8);
+                if (c < CHG && gy >= 0 && gx >= 0 && gy < a.Hl && gx < a.Wl) {
+                    const long long pix = (long long)gy * a.Wl + gx;
+                    if (MODE == TIN_NHWC) cp16(tc::smem_addr(dst), gin + (pix * CG + c * CPC) * EB);
+                    else cp16(tc::smem_addr(dst), gskip + (pix * (CG - CUP) + (c - CS0) * CPC) * EB);
                 } else {
                     *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
                 }
@@ -186,13 +257,13 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
             if (MODE == TIN_UPCAT) {   // coarse rows / columns around the tile, clamped to the coarse frame
                 const int Hc = a.Hl >> 1, Wc = a.Wl >> 1;
                 const int cy0 = (y0 >> 1) - 1, cx0 = (x0 >> 1) - 1;
-                for (int i = tid; i < (CUP / 8) * L::CR * L::CC; i += 128) {
+                for (int i = tid; i < CUPC * L::CR * L::CC; i += 128) {
                     const int c = i / (L::CR * L::CC);
                     const int rem = i % (L::CR * L::CC);
                     const int r = rem / L::CC, q = rem - r * L::CC;
                     const int cy = min(max(cy0 + r, 0), Hc - 1), cx = min(max(cx0 + q, 0), Wc - 1);
                     cp16(tc::smem_addr(sC + ((c * L::CR + r) * L::CC + q) * 16),
-                         a.in + ((long long)cy * Wc + cx) * CUP + c * 8);
+                         gin + (((long long)cy * Wc + cx) * CUP + c * CPC) * EB);
                 }
             }
             cp_wait_all();
@@ -200,12 +271,14 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
                 __syncthreads();
                 const int Hc = a.Hl >> 1, Wc = a.Wl >> 1;
                 const int cy0 = (y0 >> 1) - 1, cx0 = (x0 >> 1) - 1;
-                for (int i = tid; i < (CUP / 8) * HY * HXW; i += 128) {
+                for (int i = tid; i < CUPC * HY * HXW; i += 128) {
                     const int c = i / (HY * HXW);
                     const int rem = i % (HY * HXW);
                     const int hy = rem / HXW, hx = rem - hy * HXW;
                     const int gy = y0 + hy - 1, gx = x0 + hx - 1;
-                    float v[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                    float v[16];
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) v[j] = 0.f;
                     if (gy >= 0 && gx >= 0 && gy < a.Hl && gx < a.Wl) {
                         // bilinear x2, half-pixel centres, negative source clamped, upper neighbour clamped
                         const float sy = fmaxf((gy + 0.5f) * 0.5f - 0.5f, 0.f);
@@ -214,19 +287,30 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
                         const float fy = sy - iy0, fx = sx - ix0;
                         const int iy1 = min(iy0 + 1, Hc - 1), ix1 = min(ix0 + 1, Wc - 1);
                         const unsigned char* base = sC + (size_t)c * L::CR * L::CC * 16;
-                        float p00[8], p01[8], p10[8], p11[8];
-                        unpack8h(*reinterpret_cast<const uint4*>(base + ((iy0 - cy0) * L::CC + (ix0 - cx0)) * 16), p00);
-                        unpack8h(*reinterpret_cast<const uint4*>(base + ((iy0 - cy0) * L::CC + (ix1 - cx0)) * 16), p01);
-                        unpack8h(*reinterpret_cast<const uint4*>(base + ((iy1 - cy0) * L::CC + (ix0 - cx0)) * 16), p10);
-                        unpack8h(*reinterpret_cast<const uint4*>(base + ((iy1 - cy0) * L::CC + (ix1 - cx0)) * 16), p11);
+                        const uint4 u00 = *reinterpret_cast<const uint4*>(base + ((iy0 - cy0) * L::CC + (ix0 - cx0)) * 16);
+                        const uint4 u01 = *reinterpret_cast<const uint4*>(base + ((iy0 - cy0) * L::CC + (ix1 - cx0)) * 16);
+                        const uint4 u10 = *reinterpret_cast<const uint4*>(base + ((iy1 - cy0) * L::CC + (ix0 - cx0)) * 16);
+                        const uint4 u11 = *reinterpret_cast<const uint4*>(base + ((iy1 - cy0) * L::CC + (ix1 - cx0)) * 16);
+                        float p00[16], p01[16], p10[16], p11[16];
+                        if (F8) {
+                            unpack16q(u00, p00);
+                            unpack16q(u01, p01);
+                            unpack16q(u10, p10);
+                            unpack16q(u11, p11);
+                        } else {
+                            unpack8h(u00, p00);
+                            unpack8h(u01, p01);
+                            unpack8h(u10, p10);
+                            unpack8h(u11, p11);
+                        }
 #pragma unroll
-                        for (int j = 0; j < 8; ++j) {
+                        for (int j = 0; j < CPC; ++j) {
                             const float top = fmaf(fx, p01[j] - p00[j], p00[j]);
                             const float bot = fmaf(fx, p11[j] - p10[j], p10[j]);
                             v[j] = fmaf(fy, bot - top, top);
                         }
                     }
-                    *reinterpret_cast<uint4*>(sH + ((c * HY + hy) * HXW + hx) * 16) = pack8h(v);
+                    *reinterpret_cast<uint4*>(sH + ((c * HY + hy) * HXW + hx) * 16) = F8 ? pack16q(v) : pack8h(v);
                 }
             }
         }
@@ -261,7 +345,8 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
                         const uint32_t baddr = sW_u + ((tap * CH + 2 * kc) * COUT) * 16;
                         const uint64_t ad = tc::smem_desc(aaddr, HY * HXW * 16, 128);
                         const uint64_t bd = tc::smem_desc(baddr, COUT * 16, 128);
-                        tc::mma_f16(d, ad, bd, idesc, (tap | kc) != 0);
+                        if (F8) tc::mma_e4m3(d, ad, bd, idesc, (tap | kc) != 0);
+                        else tc::mma_f16(d, ad, bd, idesc, (tap | kc) != 0);
                     }
                 }
             }
@@ -288,12 +373,8 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
 #pragma unroll
                 for (int c = 0; c < COUT; c += 16) tc::tmem_ld16(tmem + lane_base + r * COUT + c, v + c);
 #pragma unroll
-                for (int c = 0; c < COUT; ++c) v[c] = fmaxf(v[c] + sBias[c], 0.f);
-                if (y < a.Hl && x < a.Wl) {
-                    uint4* o = reinterpret_cast<uint4*>(a.out + ((long long)y * a.Wl + x) * COUT);
-#pragma unroll
-                    for (int c = 0; c < COUT; c += 8) o[c / 8] = pack8h(v + c);
-                }
+                for (int c = 0; c < COUT; ++c) v[c] = fmaxf(fmaf(v[c], sScale[c], sBias[c]), 0.f);
+                if (y < a.Hl && x < a.Wl) store_pixel<COUT, F8>(a.out, (long long)y * a.Wl + x, v, a.out_q);
                 if (EPI == TEPI_POOL) {
                     if (r & 1) {
                         float s[COUT];
@@ -303,12 +384,8 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
                             s[c] += __shfl_xor_sync(0xffffffffu, s[c], 1);
                             s[c] *= 0.25f;
                         }
-                        if ((lane & 1) == 0 && y < a.Hl && x < a.Wl) {
-                            uint4* o = reinterpret_cast<uint4*>(
-                                a.pooled + ((long long)(y >> 1) * (a.Wl >> 1) + (x >> 1)) * COUT);
-#pragma unroll
-                            for (int c = 0; c < COUT; c += 8) o[c / 8] = pack8h(s + c);
-                        }
+                        if ((lane & 1) == 0 && y < a.Hl && x < a.Wl)
+                            store_pixel<COUT, F8>(a.pooled, (long long)(y >> 1) * (a.Wl >> 1) + (x >> 1), s, a.pool_q);
                     } else {
 #pragma unroll
                         for (int c = 0; c < COUT; ++c) prev[c] = v[c];
@@ -316,13 +393,13 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
                 }
             }
         } else {
-            // activations (bias, ReLU, FP16) -> shared memory as the head's A operand
+            // activations (scale, bias, ReLU, FP16) -> shared memory as the head's A operand
 #pragma unroll 1
             for (int r = 0; r < TR; ++r) {
                 float v[16];
                 tc::tmem_ld16(tmem + lane_base + r * COUT, v);
 #pragma unroll
-                for (int c = 0; c < 16; ++c) v[c] = fmaxf(v[c] + sBias[c], 0.f);
+                for (int c = 0; c < 16; ++c) v[c] = fmaxf(fmaf(v[c], sScale[c], sBias[c]), 0.f);
                 *reinterpret_cast<uint4*>(sHA + ((r * 2 + 0) * TW + px) * 16) = pack8h(v);
                 *reinterpret_cast<uint4*>(sHA + ((r * 2 + 1) * TW + px) * 16) = pack8h(v + 8);
             }
@@ -400,12 +477,22 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
     }
 }
 
+// amax of a non-negative FP16 tensor (calibration of the FP8 scales)
+__global__ void amax_f16_kernel(const __half* __restrict__ x, long long n, float* __restrict__ out) {
+    float m = 0.f;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        m = fmaxf(m, fabsf(__half2float(x[i])));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
+}
+
 }  // namespace
 
-template <int CIN, int COUT, int TR, int MODE, int EPI, int CUP>
+template <int CIN, int CG, int COUT, int TR, int MODE, int EPI, int CUP, bool F8>
 static fvn_status launch_tc(fvn_ctx* ctx, TcArgs a, cudaStream_t st) {
-    using L = TcLayout<CIN, COUT, TR, MODE, EPI, CUP>;
-    auto kern = conv3x3_tc_kernel<CIN, COUT, TR, MODE, EPI, CUP>;
+    using L = TcLayout<CIN, CG, COUT, TR, MODE, EPI, CUP, F8>;
+    auto kern = conv3x3_tc_kernel<CIN, CG, COUT, TR, MODE, EPI, CUP, F8>;
     static bool configured = false;
     if (!configured) {
         FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
@@ -435,35 +522,105 @@ fvn_status reconstruct_tc(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, 
     fvn_status s;
     TcArgs a{};
     a.rgbam = rgbam; a.H0 = h; a.W0 = w; a.w = L[0].w16; a.bias = L[0].bias; a.out = B.e0a; a.Hl = H4; a.Wl = W4;
-    if ((s = launch_tc<16, 16, 4, TIN_RGBAM, TEPI_STORE, 0>(ctx, a, st)) != FVN_OK) return s;
+    if ((s = launch_tc<16, 16, 16, 4, TIN_RGBAM, TEPI_STORE, 0, false>(ctx, a, st)) != FVN_OK) return s;
     a = TcArgs{};
     a.in = B.e0a; a.w = L[1].w16; a.bias = L[1].bias; a.out = B.e0; a.pooled = B.p0; a.Hl = H4; a.Wl = W4;
-    if ((s = launch_tc<16, 16, 4, TIN_NHWC, TEPI_POOL, 0>(ctx, a, st)) != FVN_OK) return s;
+    if ((s = launch_tc<16, 16, 16, 4, TIN_NHWC, TEPI_POOL, 0, false>(ctx, a, st)) != FVN_OK) return s;
     a = TcArgs{};
     a.in = B.p0; a.w = L[2].w16; a.bias = L[2].bias; a.out = B.e1a; a.Hl = H4 / 2; a.Wl = W4 / 2;
-    if ((s = launch_tc<16, 32, 4, TIN_NHWC, TEPI_STORE, 0>(ctx, a, st)) != FVN_OK) return s;
+    if ((s = launch_tc<16, 16, 32, 4, TIN_NHWC, TEPI_STORE, 0, false>(ctx, a, st)) != FVN_OK) return s;
     a = TcArgs{};
     a.in = B.e1a; a.w = L[3].w16; a.bias = L[3].bias; a.out = B.e1; a.pooled = B.p1; a.Hl = H4 / 2; a.Wl = W4 / 2;
-    if ((s = launch_tc<32, 32, 4, TIN_NHWC, TEPI_POOL, 0>(ctx, a, st)) != FVN_OK) return s;
+    if ((s = launch_tc<32, 32, 32, 4, TIN_NHWC, TEPI_POOL, 0, false>(ctx, a, st)) != FVN_OK) return s;
     a = TcArgs{};
     a.in = B.p1; a.w = L[4].w16; a.bias = L[4].bias; a.out = B.ba; a.Hl = H4 / 4; a.Wl = W4 / 4;
-    if ((s = launch_tc<32, 64, 2, TIN_NHWC, TEPI_STORE, 0>(ctx, a, st)) != FVN_OK) return s;
+    if ((s = launch_tc<32, 32, 64, 2, TIN_NHWC, TEPI_STORE, 0, false>(ctx, a, st)) != FVN_OK) return s;
     a = TcArgs{};
     a.in = B.ba; a.w = L[5].w16; a.bias = L[5].bias; a.out = B.bt; a.Hl = H4 / 4; a.Wl = W4 / 4;
-    if ((s = launch_tc<64, 64, 2, TIN_NHWC, TEPI_STORE, 0>(ctx, a, st)) != FVN_OK) return s;
+    if ((s = launch_tc<64, 64, 64, 2, TIN_NHWC, TEPI_STORE, 0, false>(ctx, a, st)) != FVN_OK) return s;
     a = TcArgs{};
     a.in = B.bt; a.skip = B.e1; a.w = L[6].w16; a.bias = L[6].bias; a.out = B.d1a; a.Hl = H4 / 2; a.Wl = W4 / 2;
-    if ((s = launch_tc<96, 32, 2, TIN_UPCAT, TEPI_STORE, 64>(ctx, a, st)) != FVN_OK) return s;
+    if ((s = launch_tc<96, 96, 32, 2, TIN_UPCAT, TEPI_STORE, 64, false>(ctx, a, st)) != FVN_OK) return s;
     a = TcArgs{};
     a.in = B.d1a; a.w = L[7].w16; a.bias = L[7].bias; a.out = B.d1; a.Hl = H4 / 2; a.Wl = W4 / 2;
-    if ((s = launch_tc<32, 32, 4, TIN_NHWC, TEPI_STORE, 0>(ctx, a, st)) != FVN_OK) return s;
+    if ((s = launch_tc<32, 32, 32, 4, TIN_NHWC, TEPI_STORE, 0, false>(ctx, a, st)) != FVN_OK) return s;
     a = TcArgs{};
     a.in = B.d1; a.skip = B.e0; a.w = L[8].w16; a.bias = L[8].bias; a.out = B.d0a; a.Hl = H4; a.Wl = W4;
-    if ((s = launch_tc<48, 16, 4, TIN_UPCAT, TEPI_STORE, 32>(ctx, a, st)) != FVN_OK) return s;
+    if ((s = launch_tc<48, 48, 16, 4, TIN_UPCAT, TEPI_STORE, 32, false>(ctx, a, st)) != FVN_OK) return s;
     a = TcArgs{};
     a.in = B.d0a; a.w = L[9].w16; a.bias = L[9].bias; a.head_w = ctx->head_w16; a.head_b = ctx->head_b32;
     a.rgbam = rgbam; a.H0 = h; a.W0 = w; a.rgb = rgb; a.Hl = H4; a.Wl = W4;
-    return launch_tc<16, 16, 4, TIN_NHWC, TEPI_HEADKP, 0>(ctx, a, st);
+    return launch_tc<16, 16, 16, 4, TIN_NHWC, TEPI_HEADKP, 0, false>(ctx, a, st);
+}
+
+// FP8 network: same buffers (FP8 tensors use half of each FP16 buffer).
+fvn_status reconstruct_tc_fp8(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, int w, int h, float* rgb,
+                              cudaStream_t st) {
+    const int W4 = (w + 3) & ~3, H4 = (h + 3) & ~3;
+    const ConvW* L = ctx->layers;
+    const float* q = ctx->fp8_inv_scale;   // 1 / s per activation tensor
+    fvn_status s;
+    TcArgs a{};
+    a.rgbam = rgbam; a.H0 = h; a.W0 = w; a.w = L[0].w8; a.wscale = L[0].scale8; a.bias = L[0].bias;
+    a.in_q = q[FP8_RGBAM]; a.out_q = q[FP8_E0A]; a.out = B.e0a; a.Hl = H4; a.Wl = W4;
+    if ((s = launch_tc<32, 16, 16, 4, TIN_RGBAM, TEPI_STORE, 0, true>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.e0a; a.w = L[1].w8; a.wscale = L[1].scale8; a.bias = L[1].bias; a.out_q = q[FP8_E0];
+    a.pool_q = q[FP8_P0]; a.out = B.e0; a.pooled = B.p0; a.Hl = H4; a.Wl = W4;
+    if ((s = launch_tc<32, 16, 16, 4, TIN_NHWC, TEPI_POOL, 0, true>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.p0; a.w = L[2].w8; a.wscale = L[2].scale8; a.bias = L[2].bias; a.out_q = q[FP8_E1A];
+    a.out = B.e1a; a.Hl = H4 / 2; a.Wl = W4 / 2;
+    if ((s = launch_tc<32, 16, 32, 4, TIN_NHWC, TEPI_STORE, 0, true>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.e1a; a.w = L[3].w8; a.wscale = L[3].scale8; a.bias = L[3].bias; a.out_q = q[FP8_E1];
+    a.pool_q = q[FP8_P1]; a.out = B.e1; a.pooled = B.p1; a.Hl = H4 / 2; a.Wl = W4 / 2;
+    if ((s = launch_tc<32, 32, 32, 4, TIN_NHWC, TEPI_POOL, 0, true>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.p1; a.w = L[4].w8; a.wscale = L[4].scale8; a.bias = L[4].bias; a.out_q = q[FP8_BA];
+    a.out = B.ba; a.Hl = H4 / 4; a.Wl = W4 / 4;
+    if ((s = launch_tc<32, 32, 64, 2, TIN_NHWC, TEPI_STORE, 0, true>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.ba; a.w = L[5].w8; a.wscale = L[5].scale8; a.bias = L[5].bias; a.out_q = q[FP8_BT];
+    a.out = B.bt; a.Hl = H4 / 4; a.Wl = W4 / 4;
+    if ((s = launch_tc<64, 64, 64, 2, TIN_NHWC, TEPI_STORE, 0, true>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.bt; a.skip = B.e1; a.w = L[6].w8; a.wscale = L[6].scale8; a.bias = L[6].bias; a.out_q = q[FP8_D1A];
+    a.out = B.d1a; a.Hl = H4 / 2; a.Wl = W4 / 2;
+    if ((s = launch_tc<96, 96, 32, 2, TIN_UPCAT, TEPI_STORE, 64, true>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.d1a; a.w = L[7].w8; a.wscale = L[7].scale8; a.bias = L[7].bias; a.out_q = q[FP8_D1];
+    a.out = B.d1; a.Hl = H4 / 2; a.Wl = W4 / 2;
+    if ((s = launch_tc<32, 32, 32, 4, TIN_NHWC, TEPI_STORE, 0, true>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.d1; a.skip = B.e0; a.w = L[8].w8; a.wscale = L[8].scale8; a.bias = L[8].bias; a.out_q = q[FP8_D0A];
+    a.out = B.d0a; a.Hl = H4; a.Wl = W4;
+    if ((s = launch_tc<64, 48, 16, 4, TIN_UPCAT, TEPI_STORE, 32, true>(ctx, a, st)) != FVN_OK) return s;
+    a = TcArgs{};
+    a.in = B.d0a; a.w = L[9].w8; a.wscale = L[9].scale8; a.bias = L[9].bias; a.head_w = ctx->head_w16;
+    a.head_b = ctx->head_b32; a.rgbam = rgbam; a.H0 = h; a.W0 = w; a.rgb = rgb; a.Hl = H4; a.Wl = W4;
+    return launch_tc<32, 16, 16, 4, TIN_NHWC, TEPI_HEADKP, 0, true>(ctx, a, st);
+}
+
+// Reduce the amax of every calibrated activation tensor of the FP16 network
+// into d_amax[FP8_NT] (running maximum).
+fvn_status calibrate_amax(fvn_ctx* ctx, const ReconPlan& B, int w, int h, float* d_amax, cudaStream_t st) {
+    const long long W4 = (w + 3) & ~3, H4 = (h + 3) & ~3;
+    const long long n0 = W4 * H4, n1 = n0 / 4, n2 = n0 / 16;
+    struct T {
+        const __half* p;
+        long long n;
+        int slot;
+    } t[] = {{B.e0a, n0 * 16, FP8_E0A}, {B.e0, n0 * 16, FP8_E0},  {B.p0, n1 * 16, FP8_P0},
+             {B.e1a, n1 * 32, FP8_E1A}, {B.e1, n1 * 32, FP8_E1},  {B.p1, n2 * 32, FP8_P1},
+             {B.ba, n2 * 64, FP8_BA},   {B.bt, n2 * 64, FP8_BT},  {B.d1a, n1 * 32, FP8_D1A},
+             {B.d1, n1 * 32, FP8_D1},   {B.d0a, n0 * 16, FP8_D0A}};
+    for (const auto& x : t) {
+        const int grid = (int)std::min<long long>((x.n + 255) / 256, 8LL * ctx->num_sms);
+        amax_f16_kernel<<<grid, 256, 0, st>>>(x.p, x.n, d_amax + x.slot);
+        FVN_LAUNCH_CHECK(ctx);
+    }
+    return FVN_OK;
 }
 
 }  // namespace fvn

@@ -100,6 +100,7 @@ extern "C" fvn_status fvn_destroy(fvn_ctx* ctx) {
     cudaFree(ctx->head_b32);
     cudaFree(ctx->d_error);
     cudaFree(ctx->d_act_scale);
+    cudaFree(ctx->d_amax);
     cudaFree(ctx->d_ticket);
     cudaFree(ctx->pad_buf);
     cudaFree(ctx->recon_ws.base);
@@ -107,6 +108,10 @@ extern "C" fvn_status fvn_destroy(fvn_ctx* ctx) {
     cudaFree(ctx->render_ws.ids);
     cudaFree(ctx->render_ws.count);
     cudaFree(ctx->render_ws.rgbam);
+    cudaFree(ctx->probe_ws.ids);
+    cudaFree(ctx->probe_ws.count);
+    cudaFree(ctx->probe_ws.rgbam);
+    cudaFree(ctx->probe_ws.acc);
     delete ctx;
     return FVN_OK;
 }

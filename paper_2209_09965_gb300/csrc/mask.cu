@@ -16,6 +16,8 @@
 // range of the id list with one atomic and writes the ids.
 #include <math.h>
 
+#include <algorithm>
+
 #include "common.cuh"
 
 namespace fvn {
@@ -26,14 +28,36 @@ __host__ __device__ __forceinline__ uint32_t pcg_hash(uint32_t v) {
     return (word >> 22u) ^ word;
 }
 
+// Compact Morton (Z-order) index -> 2-D tile coordinates.
+__device__ __forceinline__ void morton_decode(uint32_t m, int& tx, int& ty) {
+    uint32_t x = m & 0x55555555u, y = (m >> 1) & 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0F0F0F0Fu;
+    x = (x | (x >> 4)) & 0x00FF00FFu;
+    x = (x | (x >> 8)) & 0x0000FFFFu;
+    y = (y | (y >> 1)) & 0x33333333u;
+    y = (y | (y >> 2)) & 0x0F0F0F0Fu;
+    y = (y | (y >> 4)) & 0x00FF00FFu;
+    y = (y | (y >> 8)) & 0x0000FFFFu;
+    tx = (int)x;
+    ty = (int)y;
+}
+
+// Each block covers a 16 x 16 pixel tile (tiles in Z-order of blockIdx.x, so
+// that consecutive blocks are neighbours on screen), each warp an 8 x 4
+// sub-tile: the id list comes out in compact screen regions, which keeps the
+// 32 rays of a march packet close together.
 __global__ void __launch_bounds__(256) mask_compact_kernel(int W, int H, uint32_t key, int f2x, int f2y,
                                                            int shift, const uint32_t* __restrict__ lut,
                                                            uint8_t* __restrict__ mask, int32_t* __restrict__ ids,
                                                            int32_t* __restrict__ count) {
     __shared__ int warp_off[8];
     __shared__ int block_base;
+    int tx, ty;
+    morton_decode(blockIdx.x, tx, ty);
+    if (tx * 16 >= W || ty * 16 >= H) return;   // uniform per block: the Z-order domain is a square
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
-    const int x = blockIdx.x * 32 + lane, y = blockIdx.y * 8 + wy;
+    const int x = tx * 16 + (wy & 1) * 8 + (lane & 7), y = ty * 16 + (wy >> 1) * 4 + (lane >> 3);
     const bool valid = x < W && y < H;
     bool m = false;
     if (valid) {
@@ -142,8 +166,11 @@ fvn_status make_mask_impl(fvn_ctx* ctx, const fvn_foveation* fov, int w, int h, 
     f2y = f2y < 0 ? 0 : (f2y > 2 * h ? 2 * h : f2y);
     const uint32_t key = pcg_hash(fov->frame + pcg_hash(fov->seed));
     FVN_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(int32_t), st));
-    dim3 grid((w + 31) / 32, (h + 7) / 8);
-    mask_compact_kernel<<<grid, 256, 0, st>>>(w, h, key, f2x, f2y, lut->shift, lut->d_lut, mask, ids, count);
+    // Z-order over a power-of-two square of 16 x 16 tiles covering the frame
+    const int tiles = std::max((w + 15) / 16, (h + 15) / 16);
+    int side = 1;
+    while (side < tiles) side <<= 1;
+    mask_compact_kernel<<<side * side, 256, 0, st>>>(w, h, key, f2x, f2y, lut->shift, lut->d_lut, mask, ids, count);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
@@ -164,4 +191,124 @@ extern "C" fvn_status fvn_make_mask(fvn_ctx* ctx, const fvn_foveation* fov, int 
                            fov->p_base <= 1.f && isfinite(fov->fovea_radius) && isfinite(fov->falloff_sigma),
                   "foveation radius / falloff must be >= 0 and p_base in [0, 1]");
     return make_mask_impl(ctx, fov, w, h, mask, ids, count, as_stream(stream));
+}
+
+// ---------------------------------------------------------------------------
+// Error estimate for the denser-mask fallback (not in the paper).  A sparse
+// probe set -- pixels whose second hash falls below 1/256 and that the mask
+// left out -- is ray-marched as well; the reconstruction's error at those
+// pixels estimates the frame's PSNR.  When the estimate is below a threshold
+// the frame is rendered again with the periphery density doubled.
+// ---------------------------------------------------------------------------
+namespace fvn {
+
+constexpr uint32_t kProbeSalt = 0x9E3779B9u;     // second, independent hash key
+constexpr uint32_t kProbeThreshold = 1u << 16;   // N2 < 2^24 / 256
+
+__global__ void __launch_bounds__(256) probe_compact_kernel(int W, int H, uint32_t key2,
+                                                            const uint8_t* __restrict__ mask,
+                                                            int32_t* __restrict__ ids, int32_t* __restrict__ count) {
+    __shared__ int warp_off[8];
+    __shared__ int block_base;
+    const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
+    const int x = blockIdx.x * 32 + lane, y = blockIdx.y * 8 + wy;
+    bool m = false;
+    if (x < W && y < H) {
+        const uint32_t h = pcg_hash((uint32_t)x + pcg_hash((uint32_t)y + key2));
+        m = (h >> 8) < kProbeThreshold && mask[(size_t)y * W + x] == 0;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, m);
+    if (lane == 0) warp_off[wy] = __popc(bal);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int tot = 0;
+        for (int i = 0; i < 8; ++i) {
+            int c = warp_off[i];
+            warp_off[i] = tot;
+            tot += c;
+        }
+        block_base = tot ? atomicAdd(count, tot) : 0;
+    }
+    __syncthreads();
+    if (m) ids[block_base + warp_off[wy] + __popc(bal & ((1u << lane) - 1u))] = y * W + x;
+}
+
+// sum over the probes of the squared error of the clamped RGB (double)
+__global__ void probe_error_kernel(const int32_t* __restrict__ ids, const int32_t* __restrict__ count,
+                                   const float* __restrict__ rgb, const float* __restrict__ probe, long long plane,
+                                   double* __restrict__ acc) {
+    const int n = *count;
+    double s = 0.0;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const int p = ids[i];
+        for (int c = 0; c < 3; ++c) {
+            const float d = __saturatef(rgb[c * plane + p]) - __saturatef(probe[c * plane + p]);
+            s += (double)d * d;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(acc, s);
+}
+
+}  // namespace fvn
+
+using namespace fvn;
+
+extern "C" fvn_status fvn_render_adaptive(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf,
+                                          const fvn_camera* cam, const fvn_foveation* fov,
+                                          const fvn_march_params* mp, int precision, float min_psnr_db,
+                                          int max_levels, float* rgb, int* level_out, float* psnr_out,
+                                          void* stream) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    FVN_CHECK_ARG(ctx, fov != nullptr && cam != nullptr && rgb != nullptr, "null argument");
+    FVN_CHECK_ARG(ctx, max_levels >= 0 && max_levels <= 8, "max_levels must be in [0, 8]");
+    FVN_CHECK_ARG(ctx, cam->width >= 1 && cam->height >= 1 && cam->width <= kMaxSide && cam->height <= kMaxSide,
+                  "camera size outside [1, %d]", kMaxSide);
+    cudaStream_t st = as_stream(stream);
+    const int w = cam->width, h = cam->height;
+    const size_t npix = (size_t)w * h;
+    ProbeWorkspace& pw = ctx->probe_ws;
+    if (pw.w != w || pw.h != h) {
+        FVN_CUDA(ctx, cudaDeviceSynchronize());
+        cudaFree(pw.ids);
+        cudaFree(pw.count);
+        cudaFree(pw.rgbam);
+        cudaFree(pw.acc);
+        pw = ProbeWorkspace();
+        FVN_CUDA(ctx, cudaMalloc(&pw.ids, npix * sizeof(int32_t)));
+        FVN_CUDA(ctx, cudaMalloc(&pw.count, sizeof(int32_t)));
+        FVN_CUDA(ctx, cudaMalloc(&pw.rgbam, 5 * npix * sizeof(float)));
+        FVN_CUDA(ctx, cudaMalloc(&pw.acc, sizeof(double)));
+        pw.w = w;
+        pw.h = h;
+    }
+    fvn_foveation f = *fov;
+    const uint32_t key2 = pcg_hash(fov->frame + pcg_hash(fov->seed ^ kProbeSalt));
+    float est = 0.f;
+    int level = 0;
+    for (;; ++level) {
+        fvn_status s = fvn_render(ctx, vol, tf, cam, &f, mp, precision, rgb, nullptr, stream);
+        if (s != FVN_OK) return s;
+        // probes: outside this level's mask
+        FVN_CUDA(ctx, cudaMemsetAsync(pw.count, 0, sizeof(int32_t), st));
+        FVN_CUDA(ctx, cudaMemsetAsync(pw.acc, 0, sizeof(double), st));
+        dim3 grid((w + 31) / 32, (h + 7) / 8);
+        probe_compact_kernel<<<grid, 256, 0, st>>>(w, h, key2, ctx->render_ws.mask, pw.ids, pw.count);
+        FVN_LAUNCH_CHECK(ctx);
+        if ((s = march_impl(ctx, vol, tf, cam, mp, pw.ids, pw.count, pw.rgbam, nullptr, st)) != FVN_OK) return s;
+        probe_error_kernel<<<4 * ctx->num_sms, 256, 0, st>>>(pw.ids, pw.count, rgb, pw.rgbam, (long long)npix, pw.acc);
+        FVN_LAUNCH_CHECK(ctx);
+        double sum = 0.0;
+        int n = 0;
+        FVN_CUDA(ctx, cudaMemcpyAsync(&sum, pw.acc, sizeof(double), cudaMemcpyDeviceToHost, st));
+        FVN_CUDA(ctx, cudaMemcpyAsync(&n, pw.count, sizeof(int), cudaMemcpyDeviceToHost, st));
+        FVN_CUDA(ctx, cudaStreamSynchronize(st));
+        est = (n == 0 || sum == 0.0) ? 99.0f : (float)(-10.0 * log10(sum / (3.0 * n)));
+        if (est >= min_psnr_db || level >= max_levels || f.p_base >= 1.0f) break;
+        f.p_base = std::min(1.0f, 2.0f * f.p_base);
+    }
+    if (level_out) *level_out = level;
+    if (psnr_out) *psnr_out = est;
+    return FVN_OK;
 }

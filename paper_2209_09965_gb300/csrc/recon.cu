@@ -24,6 +24,8 @@
 #include <algorithm>
 #include <vector>
 
+#include <cuda_fp8.h>
+
 #include "common.cuh"
 
 namespace fvn {
@@ -422,8 +424,8 @@ size_t recon_workspace_bytes(int w, int h) {
 
 fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
                             cudaStream_t st) {
-    if (precision != FVN_PREC_FP16)
-        return set_error(ctx, FVN_ERR_UNSUPPORTED, "only FVN_PREC_FP16 is available in this build");
+    if (precision == FVN_PREC_FP8 && !ctx->has_fp8)
+        return set_error(ctx, FVN_ERR_STATE, "FP8 needs calibrated scales (call fvn_calibrate_fp8 first)");
     const int W4 = (w + 3) & ~3, H4 = (h + 3) & ~3;
     ReconWorkspace& ws = ctx->recon_ws;
     if (ws.w != W4 || ws.h != H4) {
@@ -441,11 +443,14 @@ fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, int w, int h, int 
 
 fvn_status reconstruct_on(fvn_ctx* ctx, void* workspace, const float* rgbam, int w, int h, int precision,
                           float* rgb, cudaStream_t st) {
-    if (precision != FVN_PREC_FP16)
-        return set_error(ctx, FVN_ERR_UNSUPPORTED, "only FVN_PREC_FP16 is available in this build");
     const int W4 = (w + 3) & ~3, H4 = (h + 3) & ~3;
     ReconPlan B;
     plan_buffers(W4, H4, &B, static_cast<char*>(workspace));
+    if (precision == FVN_PREC_FP8) {
+        if (!ctx->has_fp8)
+            return set_error(ctx, FVN_ERR_STATE, "FP8 needs calibrated scales (call fvn_calibrate_fp8 first)");
+        return reconstruct_tc_fp8(ctx, B, rgbam, w, h, rgb, st);
+    }
     if (ctx->conv_impl == CONV_TCGEN05) return reconstruct_tc(ctx, B, rgbam, w, h, rgb, st);
     const ConvW* L = ctx->layers;
     fvn_status s;
@@ -505,6 +510,8 @@ extern "C" fvn_status fvn_load_weights(fvn_ctx* ctx, const float* host_w, size_t
     for (size_t i = 0; i < n; ++i)
         FVN_CHECK_ARG(ctx, isfinite(host_w[i]), "weight %zu is not finite", i);
     FVN_CUDA(ctx, cudaDeviceSynchronize());
+    ctx->host_weights.assign(host_w, host_w + n);
+    ctx->has_fp8 = false;   // FP8 weights follow the FP32 weights: calibrate again
     size_t off = 0;
     for (int li = 0; li < kNumLayers; ++li) {
         const LayerSpec& sp = kLayers[li];
@@ -563,4 +570,105 @@ extern "C" fvn_status fvn_reconstruct(fvn_ctx* ctx, const float* rgbam, int w, i
     FVN_CHECK_ARG(ctx, precision == FVN_PREC_FP16 || precision == FVN_PREC_FP8, "unknown precision %d", precision);
     if (!ctx->has_weights) return set_error(ctx, FVN_ERR_STATE, "no weights loaded (call fvn_load_weights)");
     return reconstruct_impl(ctx, rgbam, w, h, precision, rgb, as_stream(stream));
+}
+
+namespace fvn {
+
+// Input tensor of every input channel of a layer, and the layer's output /
+// pooled tensor (FP8 scales; see conv_tc.cu).
+static void fp8_tensors(int layer, int c, int* in_t) {
+    static const int single[kNumLayers] = {FP8_RGBAM, FP8_E0A, FP8_P0, FP8_E1A, FP8_P1, FP8_BA,
+                                           -1,        FP8_D1A, -1,     FP8_D0A, -1};
+    if (layer == 6) *in_t = c < 64 ? FP8_BT : FP8_E1;          // [up(bt), e1]
+    else if (layer == 8) *in_t = c < 32 ? FP8_D1 : FP8_E0;     // [up(d1), e0]
+    else *in_t = single[layer];
+}
+
+// Quantise every 3x3 layer to E4M3 with the activation scales folded in:
+// w' = w s_in(c); s_w[o] = max |w'| / 448; q = e4m3(w' / s_w[o]).  Layout
+// [tap][cin_pad / 16][cout][16 bytes] (cin padded to a multiple of 32).
+static fvn_status build_fp8_weights(fvn_ctx* ctx) {
+    const float* hw = ctx->host_weights.data();
+    float s[FP8_NT];
+    for (int t = 0; t < FP8_NT; ++t) {
+        const float amax = t == FP8_RGBAM ? 1.0f : ctx->fp8_amax[t];
+        s[t] = amax > 0.f ? amax / 448.0f : 1.0f;
+        ctx->fp8_inv_scale[t] = 1.0f / s[t];
+    }
+    size_t off = 0;
+    for (int li = 0; li < kNumLayers; ++li) {
+        const LayerSpec& sp = kLayers[li];
+        const float* W = hw + off;
+        off += (size_t)sp.cout * sp.cin * sp.k * sp.k + sp.cout;
+        if (sp.k != 3) continue;
+        const int cp = (sp.cin + 31) & ~31;
+        std::vector<float> wf((size_t)sp.cout * sp.cin * 9);
+        std::vector<float> sw(sp.cout, 1.0f);
+        for (int o = 0; o < sp.cout; ++o) {
+            float m = 0.f;
+            for (int c = 0; c < sp.cin; ++c) {
+                int t;
+                fp8_tensors(li, c, &t);
+                for (int tap = 0; tap < 9; ++tap) {
+                    const size_t i = ((size_t)o * sp.cin + c) * 9 + tap;
+                    wf[i] = W[i] * s[t];
+                    m = std::max(m, std::fabs(wf[i]));
+                }
+            }
+            sw[o] = m > 0.f ? m / 448.0f : 1.0f;
+        }
+        std::vector<uint8_t> q((size_t)9 * cp * sp.cout, 0);
+        for (int o = 0; o < sp.cout; ++o)
+            for (int c = 0; c < sp.cin; ++c)
+                for (int tap = 0; tap < 9; ++tap) {
+                    const float v = wf[((size_t)o * sp.cin + c) * 9 + tap] / sw[o];
+                    q[(((size_t)tap * (cp / 16) + c / 16) * sp.cout + o) * 16 + (c % 16)] =
+                        (uint8_t)__nv_cvt_float_to_fp8(v, __NV_SATFINITE, __NV_E4M3);
+                }
+        ConvW& L = ctx->layers[li];
+        if (!L.w8) FVN_CUDA(ctx, cudaMalloc(&L.w8, q.size()));
+        if (!L.scale8) FVN_CUDA(ctx, cudaMalloc(&L.scale8, sp.cout * sizeof(float)));
+        FVN_CUDA(ctx, cudaMemcpy(L.w8, q.data(), q.size(), cudaMemcpyHostToDevice));
+        FVN_CUDA(ctx, cudaMemcpy(L.scale8, sw.data(), sp.cout * sizeof(float), cudaMemcpyHostToDevice));
+    }
+    ctx->has_fp8 = true;
+    return FVN_OK;
+}
+
+}  // namespace fvn
+
+extern "C" fvn_status fvn_calibrate_fp8(fvn_ctx* ctx, const float* rgbam, int w, int h, int reset, void* stream) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    FVN_CHECK_ARG(ctx, rgbam != nullptr, "rgbam must be a device pointer");
+    FVN_CHECK_ARG(ctx, w >= 1 && h >= 1 && w <= kMaxSide && h <= kMaxSide, "frame %d x %d outside [1, %d]", w, h,
+                  kMaxSide);
+    if (!ctx->has_weights) return set_error(ctx, FVN_ERR_STATE, "no weights loaded (call fvn_load_weights)");
+    cudaStream_t st = as_stream(stream);
+    // run the FP16 tensor-core network on this frame into the context workspace
+    float* out = nullptr;
+    FVN_CUDA(ctx, cudaMalloc(&out, sizeof(float) * 3 * (size_t)w * h));
+    const int saved = ctx->conv_impl;
+    ctx->conv_impl = CONV_TCGEN05;
+    fvn_status s = reconstruct_impl(ctx, rgbam, w, h, FVN_PREC_FP16, out, st);
+    ctx->conv_impl = saved;
+    if (s != FVN_OK) {
+        cudaFree(out);
+        return s;
+    }
+    if (!ctx->d_amax) FVN_CUDA(ctx, cudaMalloc(&ctx->d_amax, FP8_NT * sizeof(float)));
+    FVN_CUDA(ctx, cudaMemsetAsync(ctx->d_amax, 0, FP8_NT * sizeof(float), st));
+    const int W4 = (w + 3) & ~3, H4 = (h + 3) & ~3;
+    ReconPlan B;
+    plan_buffers(W4, H4, &B, static_cast<char*>(ctx->recon_ws.base));
+    s = calibrate_amax(ctx, B, w, h, ctx->d_amax, st);
+    if (s != FVN_OK) {
+        cudaFree(out);
+        return s;
+    }
+    float amax[FP8_NT];
+    FVN_CUDA(ctx, cudaStreamSynchronize(st));
+    cudaFree(out);
+    FVN_CUDA(ctx, cudaMemcpy(amax, ctx->d_amax, sizeof amax, cudaMemcpyDeviceToHost));
+    for (int t = 0; t < FP8_NT; ++t) ctx->fp8_amax[t] = reset ? amax[t] : std::max(ctx->fp8_amax[t], amax[t]);
+    return build_fp8_weights(ctx);
 }

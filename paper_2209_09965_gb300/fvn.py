@@ -30,6 +30,7 @@ EXPORTS = (
     "fvn_weight_count", "fvn_reconstruct", "fvn_render", "fvn_conv_fwd", "fvn_conv_bwd", "fvn_avgpool2_fwd",
     "fvn_avgpool2_bwd", "fvn_upsample2_fwd", "fvn_upsample2_bwd", "fvn_kp_blend_fwd", "fvn_kp_blend_bwd",
     "fvn_loss_l1grad", "fvn_adam_step", "fvn_reconstruct_noalloc", "fvn_set_option", "fvn_device_status",
+    "fvn_calibrate_fp8", "fvn_render_adaptive",
 )
 OPT_CONV_KERNEL, OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 1, 2, 3
 OPT_MARCH_REFILL_DENSE, OPT_MARCH_BLOCKS_PER_SM_DENSE = 4, 5
@@ -81,6 +82,8 @@ def _load():
         "fvn_reconstruct": [P, P, I, I, I, P, P],
         "fvn_reconstruct_noalloc": [P, P, I, I, I, P, P],
         "fvn_set_option": [P, I, I],
+        "fvn_calibrate_fp8": [P, P, I, I, I, P],
+        "fvn_render_adaptive": [P, P, P, P, P, P, I, F, I, P, P, P, P],
         "fvn_device_status": [P],
         "fvn_render": [P, P, P, P, P, P, I, P, P, P],
         "fvn_conv_fwd": [P, I, P, I, I, I, I, P, P, I, I, I, P, P],
@@ -232,6 +235,22 @@ class Context:
     def reconstruct(self, rgbam, w, h, rgb, precision=PREC_FP16, stream=None):
         self._chk(lib.fvn_reconstruct(self.h, _ptr(rgbam), int(w), int(h), int(precision), _ptr(rgb),
                                       _stream(stream)))
+
+    def render_adaptive(self, vol, tf, cam, fov, mp, rgb, min_psnr_db=35.0, max_levels=3, precision=PREC_FP16,
+                        stream=None):
+        """fvn_render with the denser-mask fallback; returns (levels, PSNR estimate)."""
+        v, t, c, m = volume(vol), transfer_function(tf), camera(cam), march_params(mp)
+        f = foveation(fov)
+        lvl = ctypes.c_int(0)
+        est = ctypes.c_float(0.0)
+        self._chk(lib.fvn_render_adaptive(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c), ctypes.byref(f),
+                                          ctypes.byref(m), int(precision), float(min_psnr_db), int(max_levels),
+                                          _ptr(rgb), ctypes.byref(lvl), ctypes.byref(est), _stream(stream)))
+        return lvl.value, est.value
+
+    def calibrate_fp8(self, rgbam, w, h, reset=True, stream=None):
+        """Set the FP8 activation scales from this sparse frame (synchronises)."""
+        self._chk(lib.fvn_calibrate_fp8(self.h, _ptr(rgbam), int(w), int(h), int(bool(reset)), _stream(stream)))
 
     def reconstruct_noalloc(self, rgbam, w, h, rgb, precision=PREC_FP16, stream=None):
         """fvn_reconstruct on the library's fixed workspace: never allocates

@@ -137,3 +137,33 @@ def test_reconstruct_needs_weights(fvn):
     with pytest.raises(fvn.FvnError, match="expected"):
         c.load_weights(np.zeros(10, np.float32))
     c.close()
+
+
+def test_render_adaptive_follows_oracle_rule(fvn):
+    """Denser-mask fallback: probe ids, estimate and chosen level against the oracle rule."""
+    from oracle import fallback as ofb
+    w, h = 160, 120
+    vol = wl.value_noise_volume(48, seed=6).to(torch.float32).numpy()
+    tf = wl.transfer_function(6, alpha_max=0.1)
+    cam = wl.orbit_camera(6, 2, width=w, height=h, radius_factor=(0.85, 1.75))
+    fov = wl.Foveation(focal_px=(70.0, 60.0), seed=6, frame=2)
+    mp = wl.MarchParams(shading=1)
+    weights = wl.net_weights(3)
+    params = onet.unpack(weights)
+    c = fvn.Context()
+    c.load_weights(weights)
+    dev = torch.device("cuda")
+    v = torch.from_numpy(vol).to(dev)
+    t = torch.from_numpy(tf).to(dev)
+    rgb = torch.zeros(3, h, w, device=dev)
+    lvl0, est0 = c.render_adaptive(v, t, cam, fov, mp, rgb, min_psnr_db=0.0, max_levels=3)
+    ref0, eref0, _ = ofb.render_adaptive(vol, tf, cam, fov, mp, params, 0.0, 3)
+    assert lvl0 == ref0 == 0
+    assert abs(est0 - eref0) < 0.5
+    lvl, est = c.render_adaptive(v, t, cam, fov, mp, rgb, min_psnr_db=200.0, max_levels=3)
+    ref, eref, rgb_ref = ofb.render_adaptive(vol, tf, cam, fov, mp, params, 200.0, 3)
+    assert lvl == ref == 3
+    assert abs(est - eref) < 0.5
+    assert np.abs(rgb.cpu().numpy() - rgb_ref).max() < FP16_TOL
+    c.device_status()
+    c.close()
