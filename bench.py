@@ -41,6 +41,9 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--profile", action="store_true",
                    help="run two untimed frames (mask, sparse march, dense march, reconstruction) for ncu")
+    p.add_argument("--sweep", action="store_true",
+                   help="compaction efficiency: march time vs uniform sample density, compaction vs naive "
+                        "rejection vs the ideal C_max scaling of the dense march")
     return p.parse_args()
 
 
@@ -215,12 +218,72 @@ def run_profile_case():
     print("profile case done", int(count.item()))
 
 
+def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.02, 0.01)):
+    """Frame time of the march vs a uniform sampling density tau (fovea and
+    falloff off, so C_max = tau): mask + compaction + sparse march, mask +
+    naive rejection (full-frame kernel, masked pixels skipped in place), and
+    the ideal tau x dense-march time.  One JSON line per density."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2209_09965_gb300 import fvn
+    from paper_2209_09965_gb300 import workloads as wl
+    dev = torch.device("cuda")
+    vol_np, tf_np, _, _, mp = wl.foveated_1080p_workload(seed=2, frame=0, n=VOL_N)
+    ctx = fvn.Context()
+    vol = torch.from_numpy(vol_np).to(dev)
+    tf = torch.from_numpy(tf_np).to(dev)
+    mask = torch.empty(H, W, dtype=torch.uint8, device=dev)
+    ids = torch.empty(W * H, dtype=torch.int32, device=dev)
+    count = torch.zeros(1, dtype=torch.int32, device=dev)
+    out = torch.empty(5, H, W, device=dev)
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    cams = [wl.orbit_camera(2, f * (ORBIT // nframes), nframes=ORBIT, width=W, height=H,
+                            radius_factor=(0.85, 1.75)) for f in range(nframes)]
+    for cam in cams[:2]:                                    # warm-up
+        ctx.march(vol, tf, cam, mp, out)
+    dense = sum(timed(lambda: ctx.march(vol, tf, cam, mp, out)) for cam in cams)
+    rows = []
+    for tau in densities:
+        comp = rej = 0.0
+        frac = 0.0
+        for i, cam in enumerate(cams):
+            fov = wl.Foveation(focal_px=(W / 2, H / 2), fovea_radius=0.0, falloff_sigma=0.0, p_base=tau, seed=2,
+                               frame=i)
+            comp += timed(lambda: (ctx.make_mask(fov, W, H, mask, ids, count),
+                                   ctx.march(vol, tf, cam, mp, out, ids=ids, count=count)))
+            frac += int(count.item()) / (W * H)
+            rej += timed(lambda: (ctx.make_mask(fov, W, H, mask, ids, count),
+                                  ctx.march_masked(vol, tf, cam, mp, mask, out)))
+        row = {"tau": tau, "sampled_fraction": frac / nframes, "dense_ms": dense / nframes,
+               "compaction_ms": comp / nframes, "rejection_ms": rej / nframes,
+               "ideal_ms": dense / nframes * tau,
+               "compaction_speedup": dense / comp, "rejection_speedup": dense / rej, "ideal_speedup": 1.0 / tau}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    ctx.close()
+    return rows
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
         return run_profile_case()
+    if args.sweep:
+        return run_sweep()
     import numpy as np
     import torch
     rank, world, local = dist_env()

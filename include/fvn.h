@@ -177,6 +177,19 @@ fvn_status fvn_march(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, cons
                      unsigned long long* nsamples, void* stream);
 
 /*
+ * fvn_march_masked -- the naive alternative to compaction.
+ * Paper: "Rendering" (a kernel over the full frame whose invalid pixels are
+ * simply discarded at kernel level, so a warp still waits for its slowest
+ * lane).  Dense ray numbering over the whole frame; pixels whose byte in
+ * mask (device uint8 [h][w]) is 0 are skipped in place and written 0, the
+ * others are marched exactly as fvn_march does.  Kept as the baseline of the
+ * compaction-efficiency measurement.
+ */
+fvn_status fvn_march_masked(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
+                            const fvn_march_params* mp, const uint8_t* mask, float* rgbam,
+                            unsigned long long* nsamples, void* stream);
+
+/*
  * fvn_load_weights -- install reconstruction-network weights.
  * Paper: "Model Precision & Optimization" (train in FP32, run with weights
  * truncated to 16-bit).  host_w: host float32, the flat layer order

@@ -142,7 +142,7 @@ fvn_status make_mask_impl(fvn_ctx* ctx, const fvn_foveation* fov, int w, int h, 
                           int32_t* count, cudaStream_t st);
 fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
                       const fvn_march_params* mp, const int32_t* ids, const int32_t* count, float* rgbam,
-                      unsigned long long* nsamples, cudaStream_t st);
+                      unsigned long long* nsamples, cudaStream_t st, const uint8_t* reject = nullptr);
 fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
                             cudaStream_t st);
 // The network launch sequence on a caller-provided workspace of at least

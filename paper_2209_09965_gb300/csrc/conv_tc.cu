@@ -199,7 +199,12 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
         }
     }
     if (tid == 0) tc::mbar_init(bar, 1);
-    if (warp == 0) tc::tmem_alloc(tbase_s, L::tmem_cols);
+    if (warp == 0) {
+        tc::tmem_alloc(tbase_s, L::tmem_cols);
+        // give up the right to allocate again at once: while a CTA holds it,
+        // no other CTA is scheduled on the SM
+        tc::tmem_relinquish();
+    }
     tc::fence_async_smem();
     tc::fence_before_sync();
     __syncthreads();
@@ -472,7 +477,6 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
     __syncthreads();
     if (warp == 0) {
         tc::fence_after_sync();
-        tc::tmem_relinquish();
         tc::tmem_dealloc(tmem, L::tmem_cols);
     }
 }

@@ -52,6 +52,7 @@ struct MarchArgs {
     unsigned long long* nsamples;
     int* ticket;
     int refill_below;                 // refill idle lanes once fewer than this many are busy
+    const uint8_t* reject;            // dense numbering: skip pixels whose mask byte is 0
 };
 
 template <typename T>
@@ -175,6 +176,7 @@ __device__ __forceinline__ bool start_ray(const MarchArgs& a, int r, int npix, R
         py = ty * 4 + (q >> 3);
         if (px >= a.W || py >= a.H) return false;
         pix = py * a.W + px;
+        if (a.reject && __ldg(a.reject + pix) == 0) return false;   // naive rejection: skip in place
     }
     const float sx = ((px + 0.5f) * a.two_over_w - 1.0f) * a.tan_x;
     const float sy = (1.0f - (py + 0.5f) * a.two_over_h) * a.tan_y;
@@ -396,7 +398,7 @@ static fvn_status launch_typed(fvn_ctx* ctx, const MarchArgs& a, bool shade, cud
 
 fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
                       const fvn_march_params* mp, const int32_t* ids, const int32_t* count, float* rgbam,
-                      unsigned long long* nsamples, cudaStream_t st) {
+                      unsigned long long* nsamples, cudaStream_t st, const uint8_t* reject) {
     MarchArgs a{};
     a.vol = vol->data;
     a.nx = vol->nx;
@@ -455,7 +457,8 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
     a.nsamples = nsamples;
     a.refill_below = ids ? ctx->march_refill : ctx->march_refill_dense;
     a.ticket = ctx->d_ticket + (ctx->ticket_ring++ & 63);
-    if (ids) FVN_CUDA(ctx, cudaMemsetAsync(rgbam, 0, 5 * sizeof(float) * (size_t)a.plane, st));
+    a.reject = ids ? nullptr : reject;
+    if (ids || reject) FVN_CUDA(ctx, cudaMemsetAsync(rgbam, 0, 5 * sizeof(float) * (size_t)a.plane, st));
     FVN_CUDA(ctx, cudaMemsetAsync(a.ticket, 0, sizeof(int), st));
     const size_t esize = vol->dtype == FVN_U8 ? 1 : (vol->dtype == FVN_F32 ? 4 : 2);
     const unsigned long long padded =
@@ -507,4 +510,20 @@ extern "C" fvn_status fvn_march(fvn_ctx* ctx, const fvn_volume* vol, const fvn_t
     FVN_CHECK_ARG(ctx, rgbam != nullptr, "rgbam output is NULL");
     FVN_CHECK_ARG(ctx, (ids == nullptr) == (count == nullptr), "ids and count must both be set or both NULL");
     return march_impl(ctx, vol, tf, cam, mp, ids, count, rgbam, nsamples, as_stream(stream));
+}
+
+extern "C" fvn_status fvn_march_masked(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf,
+                                       const fvn_camera* cam, const fvn_march_params* mp, const uint8_t* mask,
+                                       float* rgbam, unsigned long long* nsamples, void* stream) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    FVN_CHECK_ARG(ctx, mask != nullptr, "mask is NULL");
+    fvn_status st;
+    if ((st = validate_volume(ctx, vol)) != FVN_OK) return st;
+    if ((st = validate_camera(ctx, cam)) != FVN_OK) return st;
+    FVN_CHECK_ARG(ctx, tf && tf->rgba && tf->n >= 2 && tf->n <= 4096, "transfer function needs 2..4096 entries");
+    FVN_CHECK_ARG(ctx, ((uintptr_t)tf->rgba & 15) == 0, "transfer function must be 16-byte aligned");
+    FVN_CHECK_ARG(ctx, mp != nullptr && mp->step_vox > 0.f && mp->term_alpha > 0.f && mp->term_alpha <= 1.f,
+                  "bad march parameters");
+    FVN_CHECK_ARG(ctx, rgbam != nullptr, "rgbam output is NULL");
+    return march_impl(ctx, vol, tf, cam, mp, nullptr, nullptr, rgbam, nsamples, as_stream(stream), mask);
 }

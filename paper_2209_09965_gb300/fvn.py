@@ -30,7 +30,7 @@ EXPORTS = (
     "fvn_weight_count", "fvn_reconstruct", "fvn_render", "fvn_conv_fwd", "fvn_conv_bwd", "fvn_avgpool2_fwd",
     "fvn_avgpool2_bwd", "fvn_upsample2_fwd", "fvn_upsample2_bwd", "fvn_kp_blend_fwd", "fvn_kp_blend_bwd",
     "fvn_loss_l1grad", "fvn_adam_step", "fvn_reconstruct_noalloc", "fvn_set_option", "fvn_device_status",
-    "fvn_calibrate_fp8", "fvn_render_adaptive",
+    "fvn_calibrate_fp8", "fvn_render_adaptive", "fvn_march_masked",
 )
 OPT_CONV_KERNEL, OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 1, 2, 3
 OPT_MARCH_REFILL_DENSE, OPT_MARCH_BLOCKS_PER_SM_DENSE = 4, 5
@@ -83,6 +83,7 @@ def _load():
         "fvn_reconstruct_noalloc": [P, P, I, I, I, P, P],
         "fvn_set_option": [P, I, I],
         "fvn_calibrate_fp8": [P, P, I, I, I, P],
+        "fvn_march_masked": [P, P, P, P, P, P, P, P, P],
         "fvn_render_adaptive": [P, P, P, P, P, P, I, F, I, P, P, P, P],
         "fvn_device_status": [P],
         "fvn_render": [P, P, P, P, P, P, I, P, P, P],
@@ -227,6 +228,13 @@ class Context:
         self._chk(lib.fvn_march(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c), ctypes.byref(m),
                                 _ptr(ids, torch.int32), _ptr(count, torch.int32), _ptr(rgbam),
                                 _ptr(nsamples, torch.int64), _stream(stream)))
+
+    def march_masked(self, vol, tf, cam, mp, mask, rgbam, nsamples=None, stream=None):
+        """Naive rejection: dense ray numbering, pixels with mask 0 skipped in place."""
+        v, t, c, m = volume(vol), transfer_function(tf), camera(cam), march_params(mp)
+        self._chk(lib.fvn_march_masked(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c), ctypes.byref(m),
+                                       _ptr(mask, torch.uint8), _ptr(rgbam), _ptr(nsamples, torch.int64),
+                                       _stream(stream)))
 
     def load_weights(self, flat):
         a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))

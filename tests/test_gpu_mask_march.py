@@ -173,3 +173,25 @@ def test_march_argument_errors(ctx, fvn):
     cam2 = wl.Camera(eye=(1, 1, 1), target=(1, 1, 1), up=(0, 1, 0), fov_y_deg=45, width=8, height=8)
     with pytest.raises(fvn.FvnError, match="eye equals target"):
         ctx.march(v, t, cam2, mp, out)
+
+
+def test_march_masked_equals_sparse_march(ctx):
+    """Naive rejection computes exactly the rays compaction computes."""
+    vol, tf, cam, mp = wl.dense_small_workload(seed=1)
+    cam = wl.Camera(**{**cam.__dict__, "width": 96, "height": 72})
+    fov = wl.Foveation(focal_px=(40.0, 30.0), seed=3, frame=1)
+    dev = torch.device("cuda")
+    v = torch.from_numpy(vol).to(dev)
+    t = torch.from_numpy(tf).to(dev)
+    mask = torch.empty(72, 96, dtype=torch.uint8, device=dev)
+    ids = torch.empty(96 * 72, dtype=torch.int32, device=dev)
+    count = torch.zeros(1, dtype=torch.int32, device=dev)
+    ctx.make_mask(fov, 96, 72, mask, ids, count)
+    a = torch.full((5, 72, 96), 9.0, device=dev)
+    b = torch.full((5, 72, 96), 7.0, device=dev)
+    na = torch.zeros(1, dtype=torch.int64, device=dev)
+    nb = torch.zeros(1, dtype=torch.int64, device=dev)
+    ctx.march(v, t, cam, mp, a, ids=ids, count=count, nsamples=na)
+    ctx.march_masked(v, t, cam, mp, mask, b, nsamples=nb)
+    torch.cuda.synchronize()
+    assert torch.equal(a, b) and int(na.item()) == int(nb.item())
