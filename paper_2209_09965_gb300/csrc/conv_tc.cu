@@ -43,6 +43,9 @@ enum { TEPI_STORE = 0, TEPI_POOL = 1, TEPI_HEADKP = 2 };
 
 constexpr int TW = 128;            // pixels per tile row = MMA M
 constexpr int HXW = TW + 2;        // halo width
+// 8 warps: warps w and w + 4 read the same TMEM lane quadrant (w % 4) and
+// split the tile's rows in the epilogue.
+constexpr int kThreads = 256;
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 __device__ __forceinline__ void cp16(uint32_t dst, const void* src) {
@@ -105,16 +108,24 @@ struct TcLayout {
     static constexpr int CR = TR / 2 + 3, CC = TW / 2 + 3;        // coarse halo (up-sampling)
     static constexpr size_t w_off = 0;
     static constexpr size_t w_bytes = 9ull * CIN * COUT * EB;
+    static constexpr size_t halo_bytes = (size_t)CH * HY * HXW * 16;         // one halo buffer
+    static constexpr size_t sp1_bytes = EPI == TEPI_HEADKP ? (size_t)(TR + 4) * (TW + 4) * 16 : 0;
+    // two halo (and sparse-sample) buffers when they fit: the next tile is
+    // staged while the tensor core works on the current one
+    static constexpr size_t single_bytes = w_bytes + halo_bytes + sp1_bytes +
+        (MODE == TIN_UPCAT ? (size_t)(CUP / CPC) * (TR / 2 + 3) * (TW / 2 + 3) * 16 : 0) +
+        (EPI == TEPI_HEADKP ? (size_t)TR * 2 * TW * 16 + 2 * 32 * 16 : 0) + (2 * COUT + 32) * 4 + 16;
+    // (only while two CTAs still fit on an SM: overlap across CTAs is worth more)
+    static constexpr int NBUF = single_bytes + halo_bytes + sp1_bytes <= 112 * 1024 ? 2 : 1;
     static constexpr size_t halo_off = w_off + w_bytes;
-    static constexpr size_t halo_bytes = (size_t)CH * HY * HXW * 16;
-    static constexpr size_t coarse_off = halo_off + halo_bytes;
+    static constexpr size_t coarse_off = halo_off + NBUF * halo_bytes;
     static constexpr size_t coarse_bytes = MODE == TIN_UPCAT ? (size_t)(CUP / CPC) * CR * CC * 16 : 0;
     static constexpr size_t ha_off = coarse_off + coarse_bytes;     // head operand A: [TR][2][128][8] halves
     static constexpr size_t ha_bytes = EPI == TEPI_HEADKP ? (size_t)TR * 2 * TW * 16 : 0;
     static constexpr size_t hb_off = ha_off + ha_bytes;             // head weights: [2][32][8] halves
     static constexpr size_t hb_bytes = EPI == TEPI_HEADKP ? 2 * 32 * 16 : 0;
     static constexpr size_t sp_off = hb_off + hb_bytes;             // sparse R, G, B, M: [TR+4][TW+4] float4
-    static constexpr size_t sp_bytes = EPI == TEPI_HEADKP ? (size_t)(TR + 4) * (TW + 4) * 16 : 0;
+    static constexpr size_t sp_bytes = NBUF * sp1_bytes;
     static constexpr size_t bias_off = sp_off + sp_bytes;           // bias [COUT], head bias [32], FP8 scales [COUT]
     static constexpr size_t bias_bytes = (2 * COUT + 32) * 4;
     static constexpr size_t bar_off = bias_off + bias_bytes;
@@ -165,7 +176,7 @@ __device__ __forceinline__ void store_pixel(void* base, long long pix, const flo
 }
 
 template <int CIN, int CG, int COUT, int TR, int MODE, int EPI, int CUP, bool F8>
-__global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(TcArgs a) {
     using L = TcLayout<CIN, CG, COUT, TR, MODE, EPI, CUP, F8>;
     constexpr int CH = L::CH, CHG = L::CHG, CPC = L::CPC, EB = L::EB, HY = L::HY;
     constexpr int CUPC = CUP / CPC;                   // up-sampled chunks
@@ -173,11 +184,10 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
     static_assert(CIN % (2 * CPC) == 0, "K per tap must be a multiple of the MMA K");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sW = smem + L::w_off;
-    unsigned char* sH = smem + L::halo_off;
+    unsigned char* sH0 = smem + L::halo_off;        // halo buffer 0 (buffer 1 follows)
     unsigned char* sC = smem + L::coarse_off;
     unsigned char* sHA = smem + L::ha_off;
     unsigned char* sHB = smem + L::hb_off;
-    float4* sSP = reinterpret_cast<float4*>(smem + L::sp_off);
     float* sBias = reinterpret_cast<float*>(smem + L::bias_off);
     float* sScale = sBias + COUT + 32;
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::bar_off);
@@ -187,15 +197,15 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
     {
         const uint4* src = reinterpret_cast<const uint4*>(a.w);
         uint4* dst = reinterpret_cast<uint4*>(sW);
-        for (int i = tid; i < (int)(L::w_bytes / 16); i += 128) dst[i] = __ldg(src + i);
-        for (int i = tid; i < COUT; i += 128) {
+        for (int i = tid; i < (int)(L::w_bytes / 16); i += kThreads) dst[i] = __ldg(src + i);
+        for (int i = tid; i < COUT; i += kThreads) {
             sBias[i] = __ldg(a.bias + i);
             sScale[i] = F8 ? __ldg(a.wscale + i) : 1.0f;
         }
         if (EPI == TEPI_HEADKP) {
             const uint4* hs = reinterpret_cast<const uint4*>(a.head_w);
-            for (int i = tid; i < 2 * 32; i += 128) reinterpret_cast<uint4*>(sHB)[i] = __ldg(hs + i);
-            for (int i = tid; i < 32; i += 128) sBias[COUT + i] = __ldg(a.head_b + i);
+            for (int i = tid; i < 2 * 32; i += kThreads) reinterpret_cast<uint4*>(sHB)[i] = __ldg(hs + i);
+            for (int i = tid; i < 32; i += kThreads) sBias[COUT + i] = __ldg(a.head_b + i);
         }
     }
     if (tid == 0) tc::mbar_init(bar, 1);
@@ -210,24 +220,24 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tbase_s;
-    const uint32_t sW_u = tc::smem_addr(sW), sH_u = tc::smem_addr(sH);
+    const uint32_t sW_u = tc::smem_addr(sW), sH_u = tc::smem_addr(sH0);
     constexpr uint32_t idesc = F8 ? tc::idesc_e4m3(128, COUT) : tc::idesc_f16(128, COUT);
     const unsigned char* gin = static_cast<const unsigned char*>(a.in);
     const unsigned char* gskip = static_cast<const unsigned char*>(a.skip);
     uint32_t phase = 0;
     bool failed = false;
 
-    for (int tile = blockIdx.x; tile < a.ntiles && !failed; tile += gridDim.x) {
+    // Stage the input halo (and the sparse samples of the KP layer) of a tile
+    // into buffer `buf`.  Plain copies are left in flight (cp.async); the
+    // up-sampling layers wait for theirs and interpolate here.
+    auto stage = [&](int tile, int buf) {
         const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
         const int y0 = ty * TR, x0 = tx * TW;
-        tc::fence_before_sync();
-        __syncthreads();   // the previous tile's epilogue is done with TMEM and shared memory
-        tc::fence_after_sync();
-
-        // ---- stage the halo ------------------------------------------------
+        unsigned char* sH = smem + L::halo_off + (size_t)buf * L::halo_bytes;
+        float4* sSP = reinterpret_cast<float4*>(smem + L::sp_off + (size_t)buf * L::sp1_bytes);
         if (MODE == TIN_RGBAM) {
             const long long plane = (long long)a.H0 * a.W0;
-            for (int i = tid; i < HY * HXW; i += 128) {
+            for (int i = tid; i < HY * HXW; i += kThreads) {
                 const int hy = i / HXW, hx = i - hy * HXW;
                 const int gy = y0 + hy - 1, gx = x0 + hx - 1;
                 float v[16];
@@ -245,7 +255,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
             }
         } else {
             constexpr int CS0 = MODE == TIN_UPCAT ? CUPC : 0;   // first chunk read from global
-            for (int i = tid; i < (CH - CS0) * HY * HXW; i += 128) {
+            for (int i = tid; i < (CH - CS0) * HY * HXW; i += kThreads) {
                 const int c = CS0 + i / (HY * HXW);
                 const int rem = i % (HY * HXW);
                 const int hy = rem / HXW, hx = rem - hy * HXW;
@@ -262,7 +272,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
             if (MODE == TIN_UPCAT) {   // coarse rows / columns around the tile, clamped to the coarse frame
                 const int Hc = a.Hl >> 1, Wc = a.Wl >> 1;
                 const int cy0 = (y0 >> 1) - 1, cx0 = (x0 >> 1) - 1;
-                for (int i = tid; i < CUPC * L::CR * L::CC; i += 128) {
+                for (int i = tid; i < CUPC * L::CR * L::CC; i += kThreads) {
                     const int c = i / (L::CR * L::CC);
                     const int rem = i % (L::CR * L::CC);
                     const int r = rem / L::CC, q = rem - r * L::CC;
@@ -271,32 +281,38 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
                          gin + (((long long)cy * Wc + cx) * CUP + c * CPC) * EB);
                 }
             }
-            cp_wait_all();
             if (MODE == TIN_UPCAT) {
+                cp_wait_all();
                 __syncthreads();
                 const int Hc = a.Hl >> 1, Wc = a.Wl >> 1;
                 const int cy0 = (y0 >> 1) - 1, cx0 = (x0 >> 1) - 1;
-                for (int i = tid; i < CUPC * HY * HXW; i += 128) {
-                    const int c = i / (HY * HXW);
-                    const int rem = i % (HY * HXW);
-                    const int hy = rem / HXW, hx = rem - hy * HXW;
+                for (int i = tid; i < HY * HXW; i += kThreads) {
+                    const int hy = i / HXW, hx = i - hy * HXW;
                     const int gy = y0 + hy - 1, gx = x0 + hx - 1;
-                    float v[16];
+                    const bool inside = gy >= 0 && gx >= 0 && gy < a.Hl && gx < a.Wl;
+                    // bilinear x2 with half-pixel centres: fine 2m -> coarse m-1 / m with weights
+                    // 1/4, 3/4 (source clamped to 0 at m = 0), fine 2m+1 -> m / m+1 with 3/4, 1/4;
+                    // the upper neighbour is clamped to the frame
+                    const int my = gy >> 1, mx = gx >> 1;
+                    const int iy0 = (gy & 1) ? my : max(my - 1, 0), ix0 = (gx & 1) ? mx : max(mx - 1, 0);
+                    const float fy = (gy & 1) ? 0.25f : (my > 0 ? 0.75f : 0.0f);
+                    const float fx = (gx & 1) ? 0.25f : (mx > 0 ? 0.75f : 0.0f);
+                    const int iy1 = min(iy0 + 1, Hc - 1), ix1 = min(ix0 + 1, Wc - 1);
+                    const int o00 = ((iy0 - cy0) * L::CC + (ix0 - cx0)) * 16, o01 = ((iy0 - cy0) * L::CC + (ix1 - cx0)) * 16;
+                    const int o10 = ((iy1 - cy0) * L::CC + (ix0 - cx0)) * 16, o11 = ((iy1 - cy0) * L::CC + (ix1 - cx0)) * 16;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) v[j] = 0.f;
-                    if (gy >= 0 && gx >= 0 && gy < a.Hl && gx < a.Wl) {
-                        // bilinear x2, half-pixel centres, negative source clamped, upper neighbour clamped
-                        const float sy = fmaxf((gy + 0.5f) * 0.5f - 0.5f, 0.f);
-                        const float sx = fmaxf((gx + 0.5f) * 0.5f - 0.5f, 0.f);
-                        const int iy0 = (int)sy, ix0 = (int)sx;
-                        const float fy = sy - iy0, fx = sx - ix0;
-                        const int iy1 = min(iy0 + 1, Hc - 1), ix1 = min(ix0 + 1, Wc - 1);
+                    for (int c = 0; c < CUPC; ++c) {
+                        unsigned char* dst = sH + ((c * HY + hy) * HXW + hx) * 16;
+                        if (!inside) {
+                            *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
+                            continue;
+                        }
                         const unsigned char* base = sC + (size_t)c * L::CR * L::CC * 16;
-                        const uint4 u00 = *reinterpret_cast<const uint4*>(base + ((iy0 - cy0) * L::CC + (ix0 - cx0)) * 16);
-                        const uint4 u01 = *reinterpret_cast<const uint4*>(base + ((iy0 - cy0) * L::CC + (ix1 - cx0)) * 16);
-                        const uint4 u10 = *reinterpret_cast<const uint4*>(base + ((iy1 - cy0) * L::CC + (ix0 - cx0)) * 16);
-                        const uint4 u11 = *reinterpret_cast<const uint4*>(base + ((iy1 - cy0) * L::CC + (ix1 - cx0)) * 16);
-                        float p00[16], p01[16], p10[16], p11[16];
+                        const uint4 u00 = *reinterpret_cast<const uint4*>(base + o00);
+                        const uint4 u01 = *reinterpret_cast<const uint4*>(base + o01);
+                        const uint4 u10 = *reinterpret_cast<const uint4*>(base + o10);
+                        const uint4 u11 = *reinterpret_cast<const uint4*>(base + o11);
+                        float v[16], p00[16], p01[16], p10[16], p11[16];
                         if (F8) {
                             unpack16q(u00, p00);
                             unpack16q(u01, p01);
@@ -314,14 +330,14 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
                             const float bot = fmaf(fx, p11[j] - p10[j], p10[j]);
                             v[j] = fmaf(fy, bot - top, top);
                         }
+                        *reinterpret_cast<uint4*>(dst) = F8 ? pack16q(v) : pack8h(v);
                     }
-                    *reinterpret_cast<uint4*>(sH + ((c * HY + hy) * HXW + hx) * 16) = F8 ? pack16q(v) : pack8h(v);
                 }
             }
         }
         if (EPI == TEPI_HEADKP) {   // sparse R, G, B, M around the tile (2-pixel margin)
             const long long plane = (long long)a.H0 * a.W0;
-            for (int i = tid; i < (TR + 4) * (TW + 4); i += 128) {
+            for (int i = tid; i < (TR + 4) * (TW + 4); i += kThreads) {
                 const int r = i / (TW + 4), q = i - r * (TW + 4);
                 const int gy = y0 + r - 2, gx = x0 + q - 2;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -332,12 +348,29 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
                 sSP[i] = v;
             }
         }
+    };
+
+    int buf = 0;
+    int tile = blockIdx.x;
+    if (tile < a.ntiles) {
+        stage(tile, 0);
+        cp_wait_all();
         tc::fence_async_smem();
         __syncthreads();
+    }
+    for (; tile < a.ntiles && !failed; tile += gridDim.x) {
+        const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
+        const int y0 = ty * TR, x0 = tx * TW;
+        const int next = tile + gridDim.x;
+        const float4* sSP = reinterpret_cast<const float4*>(smem + L::sp_off + (size_t)buf * L::sp1_bytes);
 
         // ---- tensor-core main loop: one elected thread issues every MMA ----
         if (tid == 0) {
             tc::fence_after_sync();
+            // descriptors differ only in their start address (bits 0-13, in
+            // 16-byte units, far from overflowing below 228 KB of shared memory)
+            const uint64_t a0 = tc::smem_desc(sH_u + (uint32_t)(buf * L::halo_bytes), HY * HXW * 16, 128);
+            const uint64_t b0 = tc::smem_desc(sW_u, COUT * 16, 128);
 #pragma unroll 1
             for (int r = 0; r < TR; ++r) {
                 const uint32_t d = tmem + (uint32_t)(r * COUT);
@@ -346,10 +379,8 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
                     const int dy = tap / 3, dx = tap - dy * 3;
 #pragma unroll
                     for (int kc = 0; kc < CH / 2; ++kc) {
-                        const uint32_t aaddr = sH_u + (((2 * kc) * HY + r + dy) * HXW + dx) * 16;
-                        const uint32_t baddr = sW_u + ((tap * CH + 2 * kc) * COUT) * 16;
-                        const uint64_t ad = tc::smem_desc(aaddr, HY * HXW * 16, 128);
-                        const uint64_t bd = tc::smem_desc(baddr, COUT * 16, 128);
+                        const uint64_t ad = a0 + (uint64_t)(((2 * kc) * HY + r + dy) * HXW + dx);
+                        const uint64_t bd = b0 + (uint64_t)((tap * CH + 2 * kc) * COUT);
                         if (F8) tc::mma_e4m3(d, ad, bd, idesc, (tap | kc) != 0);
                         else tc::mma_f16(d, ad, bd, idesc, (tap | kc) != 0);
                     }
@@ -357,6 +388,8 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
             }
             tc::mma_commit(bar);
         }
+        // stage the next tile into the other buffer while the MMAs run
+        if (L::NBUF == 2 && next < a.ntiles) stage(next, buf ^ 1);
         if (!tc::mbar_wait(bar, phase, kWaitLimit)) {
             failed = true;
             if (tid == 0) atomicExch(a.error, 1);
@@ -366,13 +399,15 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
         tc::fence_after_sync();
 
         // ---- epilogue: one pixel per thread --------------------------------
-        const int px = warp * 32 + lane;         // TMEM lane = pixel within the tile row
+        const int px = (warp & 3) * 32 + lane;   // TMEM lane = pixel within the tile row
         const int x = x0 + px;
-        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+        const uint32_t lane_base = (uint32_t)((warp & 3) * 32) << 16;
+        // warp group g = warp / 4 handles rows [2g, 2g + 2): the row pairs of the pooling
+        const int r_lo = (warp >> 2) * 2, r_hi = min(TR, r_lo + 2);
         if (EPI != TEPI_HEADKP) {
             float prev[COUT];                    // row r - 1 (pooling pairs rows 2k, 2k+1)
 #pragma unroll 1
-            for (int r = 0; r < TR; ++r) {
+            for (int r = r_lo; r < r_hi; ++r) {
                 const int y = y0 + r;
                 float v[COUT];
 #pragma unroll
@@ -400,7 +435,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
         } else {
             // activations (scale, bias, ReLU, FP16) -> shared memory as the head's A operand
 #pragma unroll 1
-            for (int r = 0; r < TR; ++r) {
+            for (int r = r_lo; r < r_hi; ++r) {
                 float v[16];
                 tc::tmem_ld16(tmem + lane_base + r * COUT, v);
 #pragma unroll
@@ -430,7 +465,7 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
             tc::fence_after_sync();
             const long long plane = (long long)a.H0 * a.W0;
 #pragma unroll 1
-            for (int r = 0; r < TR; ++r) {
+            for (int r = r_lo; r < r_hi; ++r) {
                 const int y = y0 + r;
                 float hd[32];
                 tc::tmem_ld16(tmem + lane_base + r * 32, hd);
@@ -440,25 +475,23 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
                 float mx = hd[3];
 #pragma unroll
                 for (int q = 1; q < 25; ++q) mx = fmaxf(mx, hd[3 + q]);
-                float e[25], es = 0.f;
+                // one pass with the unnormalised softmax weights e_q: the
+                // normalisation cancels in num / den, and den / sum(e) is the
+                // normalised sampled weight the 1e-12 test is defined on
+                float es = 0.f, den = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
 #pragma unroll
                 for (int q = 0; q < 25; ++q) {
-                    e[q] = expf(hd[3 + q] - mx);
-                    es += e[q];
-                }
-                const float inv = 1.0f / es;
-                float den = 0.f, n0 = 0.f, n1 = 0.f, n2 = 0.f;
-#pragma unroll
-                for (int q = 0; q < 25; ++q) {
+                    const float e = expf(hd[3 + q] - mx);
                     const float4 s = sSP[(r + q / 5) * (TW + 4) + px + q % 5];
-                    const float wm = e[q] * inv * s.w;
+                    const float wm = e * s.w;
+                    es += e;
                     den += wm;
                     n0 = fmaf(wm, s.x, n0);
                     n1 = fmaf(wm, s.y, n1);
                     n2 = fmaf(wm, s.z, n2);
                 }
                 float k0 = hd[0], k1 = hd[1], k2 = hd[2];
-                if (den >= 1e-12f) {
+                if (den >= 1e-12f * es) {
                     k0 = n0 / den;
                     k1 = n1 / den;
                     k2 = n2 / den;
@@ -472,7 +505,19 @@ __global__ void __launch_bounds__(128) conv3x3_tc_kernel(TcArgs a) {
                 }
             }
         }
+        // ---- make the next tile's halo ready --------------------------------
+        tc::fence_before_sync();
+        if (L::NBUF == 1) {
+            __syncthreads();   // the epilogue is done with shared memory and TMEM
+            if (next < a.ntiles) stage(next, 0);
+        }
+        cp_wait_all();
+        tc::fence_async_smem();
+        __syncthreads();
+        tc::fence_after_sync();
+        buf ^= L::NBUF - 1;
     }
+    cp_wait_all();   // no copy may still target shared memory when the CTA exits
     tc::fence_before_sync();
     __syncthreads();
     if (warp == 0) {
@@ -508,13 +553,13 @@ static fvn_status launch_tc(fvn_ctx* ctx, TcArgs a, cudaStream_t st) {
     FVN_CUDA(ctx, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
     int per_sm = smem_sm / (int)(L::bytes + 1024);
     per_sm = std::min(per_sm, (int)(512 / L::tmem_cols));
-    per_sm = std::min(per_sm, 16);
+    per_sm = std::min(per_sm, 2048 / kThreads);
     if (per_sm < 1) return set_error(ctx, FVN_ERR_CUDA, "tensor-core conv kernel does not fit on an SM");
     a.tiles_x = (a.Wl + TW - 1) / TW;
     a.ntiles = a.tiles_x * ((a.Hl + TR - 1) / TR);
     const int grid = std::min(a.ntiles, ctx->num_sms * per_sm);
     a.error = ctx->d_error;
-    kern<<<grid, 128, L::bytes, st>>>(a);
+    kern<<<grid, kThreads, L::bytes, st>>>(a);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }

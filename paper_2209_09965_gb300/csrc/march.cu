@@ -2,20 +2,26 @@
 // (paper: "Foveated Rendering" and "Rendering": one ray per valid pixel of the
 // compacted buffer, results written back to their full-frame positions).
 //
-// Persistent kernel: every warp repeatedly takes a packet of 32 rays from a
-// global ticket counter, so lanes stay busy however uneven the ray lengths
-// and however sparse the mask.  Dense rays are numbered in 8 x 4 pixel
-// blocks, sparse rays follow the id list (written tile by tile by the mask
-// kernel), so the 32 rays of a packet are neighbours on screen and their
-// trilinear gathers share cache lines.  The transfer function sits in shared
-// memory; the volume is read through the read-only data path (a 256^3 float
-// volume is 64 MiB and stays resident in the 126 MB L2).
+// Persistent kernel: warps take rays from a global ticket counter; a lane
+// whose ray ends goes idle and the idle lanes of a warp refill together once
+// fewer than a tuned number of lanes are busy (1 = whole 32-ray packets), so
+// lanes stay busy however uneven the ray lengths.  Dense rays are numbered in
+// 8 x 4 pixel blocks, sparse rays follow the id list (written in Z-ordered
+// 16 x 16 tiles of 8 x 4 sub-tiles by the mask kernel), so the rays of a warp
+// are neighbours on screen and their gathers share cache lines.  The
+// transfer function sits in shared memory; the volume is read through the
+// read-only path from a copy with a 2-voxel clamp-to-edge border (a 256^3
+// float volume and its copy stay in the 126 MB L2), so the per-sample code
+// has no boundary branches.
 //
-// Per sample (FP32): trilinear fetch between voxel centres with clamp to
-// edge, TF lookup at v (n - 1), optional Phong headlight shading from central
+// Per sample (FP32): trilinear value between voxel centres (clamp to edge),
+// TF lookup at v (n - 1), optional Phong headlight shading from central
 // differences at +-1 voxel (only for samples with alpha > 0, which are the
 // only ones that contribute), C += (1 - A) a c, A += (1 - A) a, stop once
-// A >= term_alpha.
+// A >= term_alpha.  The 32 voxels a shaded sample needs are loaded in one
+// batch, and two consecutive samples are loaded before the first is
+// composited: the latency chain of a long ray, which bounds sparse frames,
+// is a quarter of the naive one.
 #include <math.h>
 
 #include <algorithm>
@@ -85,72 +91,6 @@ __device__ __forceinline__ int floor_frac(float x, float& frac) {
 }
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
-
-// Voxel access around the cell (i, j, k): fast = unclamped pointer offsets
-// (the whole stencil is inside the volume), otherwise clamp to edge.
-template <typename T, typename I, bool CLAMP>
-struct Vox {
-    const T* __restrict__ vol;
-    const T* b;
-    int nx, ny, nz, i, j, k;
-    I sy, sz;
-    __device__ __forceinline__ float at(int dx, int dy, int dz) const {
-        if (!CLAMP) return load_norm(b + ((I)dz * sz + (I)dy * sy + dx));
-        const int x = min(max(i + dx, 0), nx - 1);
-        const int y = min(max(j + dy, 0), ny - 1);
-        const int z = min(max(k + dz, 0), nz - 1);
-        return load_norm(vol + ((I)z * ny + y) * nx + x);
-    }
-};
-
-// Centre cube c[z][y][x] of the trilinear cell and the x-lerped rows
-// a[z][y]; returns the interpolated value.
-template <class V>
-__device__ __forceinline__ float cell_value(const V& v, float tx, float ty, float tz, float (&c)[2][2][2],
-                                            float (&a)[2][2]) {
-#pragma unroll
-    for (int z = 0; z < 2; ++z)
-#pragma unroll
-        for (int y = 0; y < 2; ++y) {
-            c[z][y][0] = v.at(0, y, z);
-            c[z][y][1] = v.at(1, y, z);
-            a[z][y] = lerpf(c[z][y][0], c[z][y][1], tx);
-        }
-    return lerpf(lerpf(a[0][0], a[0][1], ty), lerpf(a[1][0], a[1][1], ty), tz);
-}
-
-// Central differences of the trilinear field at +-1 voxel along each axis,
-// from the 32-voxel stencil around the cell (the 8 centre voxels plus 24).
-template <class V>
-__device__ __forceinline__ void cell_gradient(const V& v, float tx, float ty, float tz, const float (&c)[2][2][2],
-                                              const float (&a)[2][2], float& gx, float& gy, float& gz) {
-    float d[2][2];
-#pragma unroll
-    for (int z = 0; z < 2; ++z)
-#pragma unroll
-        for (int y = 0; y < 2; ++y) {
-            const float p = lerpf(c[z][y][1], v.at(2, y, z), tx);     // row value at x + 1
-            const float m = lerpf(v.at(-1, y, z), c[z][y][0], tx);    // row value at x - 1
-            d[z][y] = p - m;
-        }
-    gx = 0.5f * lerpf(lerpf(d[0][0], d[0][1], ty), lerpf(d[1][0], d[1][1], ty), tz);
-    float ym[2], yp[2];   // rows j - 1 and j + 2 at z = k, k + 1
-#pragma unroll
-    for (int z = 0; z < 2; ++z) {
-        ym[z] = lerpf(v.at(0, -1, z), v.at(1, -1, z), tx);
-        yp[z] = lerpf(v.at(0, 2, z), v.at(1, 2, z), tx);
-    }
-    gy = 0.5f * lerpf(lerpf(a[0][1], yp[0], ty) - lerpf(ym[0], a[0][0], ty),
-                      lerpf(a[1][1], yp[1], ty) - lerpf(ym[1], a[1][0], ty), tz);
-    float zm[2], zp[2];   // rows k - 1 and k + 2 at y = j, j + 1
-#pragma unroll
-    for (int y = 0; y < 2; ++y) {
-        zm[y] = lerpf(v.at(0, y, -1), v.at(1, y, -1), tx);
-        zp[y] = lerpf(v.at(0, y, 2), v.at(1, y, 2), tx);
-    }
-    gz = 0.5f * lerpf(lerpf(a[1][0], zp[0], tz) - lerpf(zm[0], a[0][0], tz),
-                      lerpf(a[1][1], zp[1], tz) - lerpf(zm[1], a[0][1], tz), ty);
-}
 
 // Ray state of one lane.
 struct Ray {
@@ -230,25 +170,68 @@ __device__ __forceinline__ void finish_ray(const MarchArgs& a, const Ray& s) {
     out[4 * a.plane] = 1.0f;
 }
 
-// One sample of the ray; returns true when the ray is finished.
-template <typename T, typename I, bool SHADE>
-__device__ __forceinline__ bool ray_step(const MarchArgs& a, const T* __restrict__ vol, const float4* s_tf, I sy,
-                                         I sz, float ux0, float uy0, float uz0, float tfmax, Ray& s) {
-    const float t = fmaf(s.kf, a.dt, s.tnear);
-    if (!(t < s.tfar)) return true;
-    s.kf += 1.0f;
-    const float ux = fmaf(t, s.dx, ux0), uy = fmaf(t, s.dy, uy0), uz = fmaf(t, s.dz, uz0);
+// The 32 voxels one shaded sample reads: the trilinear cell c[z][y][x] and
+// the two extra rows each central difference needs, all loaded at once so a
+// sample costs one round trip to the memory system.
+struct Stencil {
+    float c[2][2][2];
+    float xm[2][2], xp[2][2];   // x = -1, +2 at (y, z) of the cell, [z][y]
+    float ym[2][2], yp[2][2];   // y = -1, +2 at (x, z), [z][x]
+    float zm[2][2], zp[2][2];   // z = -1, +2 at (x, y), [y][x]
     float tx, ty, tz;
-    int i = floor_frac(ux, tx), j = floor_frac(uy, ty), k = floor_frac(uz, tz);
+};
+
+template <typename T, typename I, bool SHADE>
+__device__ __forceinline__ void load_stencil(const MarchArgs& a, const T* __restrict__ vol, I sy, I sz, float ux,
+                                             float uy, float uz, Stencil& S) {
+    int i = floor_frac(ux, S.tx), j = floor_frac(uy, S.ty), k = floor_frac(uz, S.tz);
     // samples lie in the box, so i is in [-1, n - 1]; the clamp only guards
     // against rounding and keeps every stencil index inside the padded copy
     i = min(max(i, -1), a.nx - 1);
     j = min(max(j, -1), a.ny - 1);
     k = min(max(k, -1), a.nz - 1);
-    float c[2][2][2], rows[2][2];
-    const Vox<T, I, false> vf{vol, vol + ((I)(k + kPad) * sz + (I)(j + kPad) * sy + (i + kPad)), a.nx, a.ny, a.nz,
-                              i, j, k, sy, sz};
-    const float v = cell_value(vf, tx, ty, tz, c, rows);
+    const T* b = vol + ((I)(k + kPad) * sz + (I)(j + kPad) * sy + (i + kPad));
+#pragma unroll
+    for (int z = 0; z < 2; ++z)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) {
+            const T* r = b + (I)z * sz + (I)y * sy;
+            S.c[z][y][0] = load_norm(r);
+            S.c[z][y][1] = load_norm(r + 1);
+            if (SHADE) {
+                S.xm[z][y] = load_norm(r - 1);
+                S.xp[z][y] = load_norm(r + 2);
+            }
+        }
+    if (SHADE) {
+#pragma unroll
+        for (int z = 0; z < 2; ++z)
+#pragma unroll
+            for (int x = 0; x < 2; ++x) {
+                S.ym[z][x] = load_norm(b + (I)z * sz - sy + x);
+                S.yp[z][x] = load_norm(b + (I)z * sz + 2 * sy + x);
+            }
+#pragma unroll
+        for (int y = 0; y < 2; ++y)
+#pragma unroll
+            for (int x = 0; x < 2; ++x) {
+                S.zm[y][x] = load_norm(b - sz + (I)y * sy + x);
+                S.zp[y][x] = load_norm(b + 2 * sz + (I)y * sy + x);
+            }
+    }
+}
+
+// Classify, shade and composite one loaded sample; returns true once the ray
+// is opaque enough to stop.
+template <bool SHADE>
+__device__ __forceinline__ bool composite_sample(const MarchArgs& a, const float4* s_tf, float tfmax,
+                                                 const Stencil& S, Ray& s) {
+    float rows[2][2];
+#pragma unroll
+    for (int z = 0; z < 2; ++z)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) rows[z][y] = lerpf(S.c[z][y][0], S.c[z][y][1], S.tx);
+    const float v = lerpf(lerpf(rows[0][0], rows[0][1], S.ty), lerpf(rows[1][0], rows[1][1], S.ty), S.tz);
     const float xi = v * tfmax;
     float fr;
     int ti = floor_frac(xi, fr);
@@ -267,8 +250,26 @@ __device__ __forceinline__ bool ray_step(const MarchArgs& a, const T* __restrict
         float cg = fmaf(fr, c1.y - c0.y, c0.y);
         float cb = fmaf(fr, c1.z - c0.z, c0.z);
         if (SHADE) {
-            float gx, gy, gz;
-            cell_gradient(vf, tx, ty, tz, c, rows, gx, gy, gz);
+            // central differences at +-1 voxel of the trilinear field
+            float d[2][2];
+#pragma unroll
+            for (int z = 0; z < 2; ++z)
+#pragma unroll
+                for (int y = 0; y < 2; ++y)
+                    d[z][y] = lerpf(S.c[z][y][1], S.xp[z][y], S.tx) - lerpf(S.xm[z][y], S.c[z][y][0], S.tx);
+            const float gx = 0.5f * lerpf(lerpf(d[0][0], d[0][1], S.ty), lerpf(d[1][0], d[1][1], S.ty), S.tz);
+            float ym[2], yp[2], zm[2], zp[2];
+#pragma unroll
+            for (int q = 0; q < 2; ++q) {
+                ym[q] = lerpf(S.ym[q][0], S.ym[q][1], S.tx);
+                yp[q] = lerpf(S.yp[q][0], S.yp[q][1], S.tx);
+                zm[q] = lerpf(S.zm[q][0], S.zm[q][1], S.tx);
+                zp[q] = lerpf(S.zp[q][0], S.zp[q][1], S.tx);
+            }
+            const float gy = 0.5f * lerpf(lerpf(rows[0][1], yp[0], S.ty) - lerpf(ym[0], rows[0][0], S.ty),
+                                          lerpf(rows[1][1], yp[1], S.ty) - lerpf(ym[1], rows[1][0], S.ty), S.tz);
+            const float gz = 0.5f * lerpf(lerpf(rows[1][0], zp[0], S.tz) - lerpf(zm[0], rows[0][0], S.tz),
+                                          lerpf(rows[1][1], zp[1], S.tz) - lerpf(zm[1], rows[0][1], S.tz), S.ty);
             const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
             if (g2 >= 1e-12f) {   // |g| >= 1e-6: shade, otherwise keep the TF colour
                 const float ndl = fabsf(fmaf(gx, s.dx, fmaf(gy, s.dy, gz * s.dz))) * rsqrtf(g2);
@@ -291,6 +292,27 @@ __device__ __forceinline__ bool ray_step(const MarchArgs& a, const T* __restrict
         s.A += w;
     }
     return s.A >= a.term;
+}
+
+// Up to two samples of the ray with both samples' loads issued before either
+// is composited (the loads do not depend on the compositing), which halves
+// the latency chain a long ray walks.  Returns true when the ray is finished.
+template <typename T, typename I, bool SHADE>
+__device__ __forceinline__ bool ray_step(const MarchArgs& a, const T* __restrict__ vol, const float4* s_tf, I sy,
+                                         I sz, float ux0, float uy0, float uz0, float tfmax, Ray& s) {
+    const float t0 = fmaf(s.kf, a.dt, s.tnear);
+    if (!(t0 < s.tfar)) return true;
+    const float t1 = fmaf(s.kf + 1.0f, a.dt, s.tnear);
+    const bool has1 = t1 < s.tfar;
+    const float t1c = has1 ? t1 : t0;
+    Stencil S0, S1;
+    load_stencil<T, I, SHADE>(a, vol, sy, sz, fmaf(t0, s.dx, ux0), fmaf(t0, s.dy, uy0), fmaf(t0, s.dz, uz0), S0);
+    load_stencil<T, I, SHADE>(a, vol, sy, sz, fmaf(t1c, s.dx, ux0), fmaf(t1c, s.dy, uy0), fmaf(t1c, s.dz, uz0), S1);
+    s.kf += 1.0f;
+    if (composite_sample<SHADE>(a, s_tf, tfmax, S0, s)) return true;
+    if (!has1) return true;
+    s.kf += 1.0f;
+    return composite_sample<SHADE>(a, s_tf, tfmax, S1, s);
 }
 
 // Persistent kernel with per-lane ray refill: a lane whose ray finishes goes
@@ -359,25 +381,22 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
 
 template <typename T>
 __global__ void pad_volume_kernel(const T* __restrict__ src, int nx, int ny, int nz, T* __restrict__ dst) {
-    const int px = nx + 2 * kPad, py = ny + 2 * kPad, pz = nz + 2 * kPad;
-    const long long total = (long long)px * py * pz;
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < total;
-         o += (long long)gridDim.x * blockDim.x) {
-        const int x = (int)(o % px);
-        const long long r = o / px;
-        const int y = (int)(r % py), z = (int)(r / py);
-        const int sx = min(max(x - kPad, 0), nx - 1), sy = min(max(y - kPad, 0), ny - 1),
-                  sz = min(max(z - kPad, 0), nz - 1);
-        dst[o] = src[((long long)sz * ny + sy) * nx + sx];
-    }
+    // one block row per padded (y, z) row: no integer division per element
+    const int px = nx + 2 * kPad, py = ny + 2 * kPad;
+    const int y = blockIdx.y, z = blockIdx.z;
+    const int sy = min(max(y - kPad, 0), ny - 1), sz = min(max(z - kPad, 0), nz - 1);
+    const T* s = src + ((long long)sz * ny + sy) * nx;
+    T* d = dst + ((long long)z * py + y) * px;
+    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < px; x += gridDim.x * blockDim.x)
+        d[x] = s[min(max(x - kPad, 0), nx - 1)];
 }
 
 template <typename T, typename I>
 static fvn_status launch_typed(fvn_ctx* ctx, const MarchArgs& a, bool shade, cudaStream_t st) {
     const size_t smem = (size_t)a.ntf * sizeof(float4);
     {   // refresh the padded copy of the volume (one pass over it)
-        const long long total = (long long)(a.nx + 2 * kPad) * (a.ny + 2 * kPad) * (a.nz + 2 * kPad);
-        const int grid = (int)std::min<long long>((total + 255) / 256, 64LL * ctx->num_sms);
+        const int px = a.nx + 2 * kPad;
+        dim3 grid((px + 255) / 256, a.ny + 2 * kPad, a.nz + 2 * kPad);
         pad_volume_kernel<T><<<grid, 256, 0, st>>>(static_cast<const T*>(a.vol), a.nx, a.ny, a.nz,
                                                    static_cast<T*>(const_cast<void*>(a.pvol)));
         FVN_LAUNCH_CHECK(ctx);
