@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--profile", action="store_true",
                    help="run two untimed frames (mask, sparse march, dense march, reconstruction) for ncu")
+    p.add_argument("--no-multiview", action="store_true",
+                   help="skip the batched 16-view measurement")
     p.add_argument("--sweep", action="store_true",
                    help="compaction efficiency: march time vs uniform sample density, compaction vs naive "
                         "rejection vs the ideal C_max scaling of the dense march")
@@ -276,6 +278,95 @@ def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.
     return rows
 
 
+def run_multiview(ctx, fvn, wl, dev, steps, warmup, flush):
+    """Batched multi-view frames: 16 views (4 stereo pairs at 2064x2208, 4 at
+    1280x720, 4 at 3840x2160) over a 512^3 float16 noise volume and a 1024^3
+    uint8 blob volume, one fvn_render_batch call per frame with the FP8
+    network (scales calibrated on the first frame), an orbit frame per step."""
+    import numpy as np
+    import torch
+    noise, blobs = wl.multiview_volumes(device=dev)
+    vols = [noise, blobs]
+    tfs = [torch.from_numpy(t).to(dev) for t in wl.multiview_transfer_functions()]
+    mp = wl.MarchParams(shading=1)
+    spec0 = wl.multiview_views(frame=0)
+    rgbs = [torch.empty(3, v["h"], v["w"], device=dev) for v in spec0]
+    npix = sum(v["w"] * v["h"] for v in spec0)
+
+    def views(frame, rgbam=None):
+        return [{"vol": vols[v["volume"]], "tf": tfs[v["volume"]], "cam": v["cam"], "fov": v["fov"],
+                 "rgb": rgbs[i], "rgbam": None if rgbam is None else rgbam[i]}
+                for i, v in enumerate(wl.multiview_views(frame=frame))]
+
+    # FP8 scales from the first frame's own sparse frames
+    rgbam = [torch.empty(5, v["h"], v["w"], device=dev) for v in spec0]
+    ctx.render_batch(views(0, rgbam), mp)
+    for i, v in enumerate(spec0):
+        ctx.calibrate_fp8(rgbam[i], v["w"], v["h"], reset=(i == 0))
+    # quality of the FP8 batch on the 1280x720 views against their dense march
+    ctx.render_batch(views(0, rgbam), mp, precision=fvn.PREC_FP8)
+    psnrs = []
+    for i, v in enumerate(spec0):
+        if v["w"] == 1280:
+            dense = torch.empty(5, v["h"], v["w"], device=dev)
+            ctx.march(vols[v["volume"]], tfs[v["volume"]], v["cam"], mp, dense)
+            psnrs.append(psnr_t(rgbs[i], dense[:3]))
+    del rgbam
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    nsamp = torch.zeros(1, dtype=torch.int64, device=dev)
+    for i in range(warmup):
+        ctx.render_batch(views(i), mp, precision=fvn.PREC_FP8)
+    torch.cuda.synchronize()
+    ms = []
+    nsamp.zero_()
+    for i in range(steps):
+        vs = views(i)
+        flush.fill_(float(i))
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        ctx.render_batch(vs, mp, precision=fvn.PREC_FP8, nsamples=nsamp)
+        e1.record(stream)
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = [a.elapsed_time(b) for a, b in ms]
+    samples = int(nsamp.item()) / steps
+    # the same batch captured once in a CUDA graph and replayed
+    graph_ms = None
+    try:
+        vs = views(0)
+        side = torch.cuda.Stream()
+        side.wait_stream(stream)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=side):
+            ctx.render_batch(vs, mp, precision=fvn.PREC_FP8)
+        torch.cuda.synchronize()
+        gm = []
+        for i in range(min(steps, 8)):
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            g.replay()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            gm.append(e0.elapsed_time(e1))
+        graph_ms = float(np.median(gm))
+    except Exception as exc:   # reported, not part of the metric
+        graph_ms = f"capture failed: {str(exc)[:160]}"
+    ctx.device_status()
+    mean_ms = float(np.mean(ms))
+    return {"workload": "16 views (4 stereo pairs 2064x2208, 4x 1280x720, 4x 3840x2160), 512^3 f16 noise + "
+                        "1024^3 u8 blobs, Phong, step 0.5 vox, hash mask r0=0.1 s=0.1 P_b=0.05, FP8 net, "
+                        "one fvn_render_batch per frame",
+            "megapixels_per_batch": npix / 1e6, "batches": steps, "ms_per_batch": mean_ms,
+            "views_per_s": 16 * 1000.0 / mean_ms, "megapixels_per_s": npix / 1e6 * 1000.0 / mean_ms,
+            "gsamples_per_s_end_to_end": samples / (mean_ms / 1000.0) / 1e9, "samples_per_batch": samples,
+            "psnr_720p_views_vs_dense_db": [float(x) for x in psnrs],
+            "graph_ms_per_batch": graph_ms,
+            "launches_per_batch": 14,
+            "note": "launches: 1 mask + compaction, 2 volume padding, 1 persistent march, 10 network layers"}
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -469,6 +560,10 @@ def main():
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_val = world * args.steps / (sum(e2e_ms) / 1000.0)
 
+    multiview = None
+    if not args.no_multiview:
+        multiview = run_multiview(ctx, fvn, wl, dev, min(args.steps, 8), 2, flush)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         c = cpu_oracle_frame_rate()
@@ -512,6 +607,7 @@ def main():
             # head / KP / blend fused on the tcgen05 path; a separate KP kernel otherwise)
             "gpu_launches": (13 if (tuned is None or tuned["conv"]["conv"] == "tcgen05") else 14) * args.steps,
             "cuda_graph": graph_info,
+            "multiview": multiview,
             "clocks": clocks,
         }
         if cpu:

@@ -289,6 +289,41 @@ fvn_status fvn_render_adaptive(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf
                                float min_psnr_db, int max_levels, float* rgb, int* level_out, float* psnr_out,
                                void* stream);
 
+/* Most views one fvn_render_batch call takes. */
+#define FVN_MAX_VIEWS 16
+
+/* One view of a batch.  vol, tf: as for fvn_render (read before the call
+ * returns; views may share them).  cam, fov: the view's camera (its width x
+ * height is the view's size) and foveation.  rgb: device float [3][h][w]
+ * output.  rgbam: optional device float [5][h][w] that receives the view's
+ * sparse frame (NULL: kept in the context's workspace). */
+typedef struct {
+    const fvn_volume* vol;
+    const fvn_tf* tf;
+    fvn_camera cam;
+    fvn_foveation fov;
+    float* rgb;
+    float* rgbam;
+} fvn_view;
+
+/*
+ * fvn_render_batch -- fvn_render for 1..FVN_MAX_VIEWS views of any sizes
+ * (stereo pairs, several resolutions) over up to 4 distinct volumes (of any
+ * voxel types) in one pass: one mask + compaction launch for all views, one
+ * padding launch per distinct volume, ONE persistent march launch over the
+ * rays of every view, and one launch per network layer over the tiles of
+ * every view.  The paper renders one view per frame (Fig. "pipeline"); the
+ * batch is this library's multi-view form of that frame, and each view's rgb
+ * (and rgbam) equals what fvn_render gives for that view alone, bit for bit.
+ * The distinct transfer functions together hold at most 4096 entries.
+ * nsamples: optional device counter, incremented by the samples of all
+ * views.  The context keeps a batch workspace (about 215 B per pixel);
+ * growing it synchronises the device, so capture the call in a CUDA graph
+ * only after one call with the same view sizes.
+ */
+fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int nviews, const fvn_march_params* mp,
+                            int precision, unsigned long long* nsamples, void* stream);
+
 /* ------------------------------------------------------------------------
  * Training kernels (FP32, NCHW with batch N).  Paper: "Training" and "Loss"
  * sections (the network is trained in FP32).  These are the forward and

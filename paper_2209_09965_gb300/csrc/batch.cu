@@ -1,0 +1,184 @@
+// Batched multi-view render: the per-frame path of the paper's pipeline
+// (Fig. "pipeline": sample mask -> compaction -> sparse rendering ->
+// reconstruction) for up to FVN_MAX_VIEWS views of uneven sizes -- stereo
+// pairs, several resolutions, several volumes -- with one launch per stage
+// instead of one per view:
+//
+//   mask + compaction   1 launch over the Z-ordered tiles of every view
+//   volume padding      1 launch per distinct volume
+//   ray march           1 persistent launch over the rays of every view
+//   network             1 launch per layer over the tiles of every view
+//
+// Per view the arithmetic is that of fvn_render, so each view's output is the
+// single-view output bit for bit.  Workspace layout (one device allocation,
+// 256-byte aligned pieces): per view its mask (1 B/px), id list (4 B/px),
+// sparse frame (20 B/px) and activation buffers (188 B/px at 16/32/64
+// channels), then the per-view counts.
+#include <math.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+
+namespace fvn {
+namespace {
+
+struct ViewLayout {
+    size_t mask, ids, rgbam, plan;
+};
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Offsets of every view's pieces; returns the total size.
+size_t batch_layout(const fvn_view* views, int n, ViewLayout* lay) {
+    size_t off = 0;
+    for (int i = 0; i < n; ++i) {
+        const size_t npix = (size_t)views[i].cam.width * views[i].cam.height;
+        lay[i].mask = off;
+        off += align256(npix);
+        lay[i].ids = off;
+        off += align256(npix * sizeof(int32_t));
+        lay[i].rgbam = off;
+        off += align256(5 * npix * sizeof(float));
+        lay[i].plan = off;
+        off += align256(plan_view(views[i].cam.width, views[i].cam.height, nullptr, nullptr));
+    }
+    return off + align256(kMaxViews * sizeof(int32_t));
+}
+
+fvn_status validate_view(fvn_ctx* ctx, const fvn_view& v, int i) {
+    fvn_status st;
+    if ((st = validate_volume(ctx, v.vol)) != FVN_OK) return st;
+    if ((st = validate_camera(ctx, &v.cam)) != FVN_OK) return st;
+    FVN_CHECK_ARG(ctx, v.tf && v.tf->rgba && v.tf->n >= 2 && v.tf->n <= 4096,
+                  "view %d: transfer function needs 2..4096 entries", i);
+    FVN_CHECK_ARG(ctx, ((uintptr_t)v.tf->rgba & 15) == 0, "view %d: transfer function must be 16-byte aligned", i);
+    const fvn_foveation& f = v.fov;
+    FVN_CHECK_ARG(ctx, isfinite(f.focal_px[0]) && isfinite(f.focal_px[1]), "view %d: focal point is not finite", i);
+    FVN_CHECK_ARG(ctx, f.fovea_radius >= 0.f && f.falloff_sigma >= 0.f && f.p_base >= 0.f && f.p_base <= 1.f &&
+                           isfinite(f.fovea_radius) && isfinite(f.falloff_sigma),
+                  "view %d: foveation radius / falloff must be >= 0 and p_base in [0, 1]", i);
+    FVN_CHECK_ARG(ctx, v.rgb != nullptr, "view %d: rgb output is NULL", i);
+    return FVN_OK;
+}
+
+bool same_volume(const fvn_volume* a, const fvn_volume* b) {
+    return a->data == b->data && a->nx == b->nx && a->ny == b->ny && a->nz == b->nz && a->dtype == b->dtype;
+}
+
+}  // namespace
+}  // namespace fvn
+
+using namespace fvn;
+
+extern "C" fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int nviews, const fvn_march_params* mp,
+                                       int precision, unsigned long long* nsamples, void* stream) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    FVN_CHECK_ARG(ctx, views != nullptr, "views is NULL");
+    FVN_CHECK_ARG(ctx, nviews >= 1 && nviews <= kMaxViews, "%d views (1..%d)", nviews, kMaxViews);
+    FVN_CHECK_ARG(ctx, mp && mp->step_vox > 0.f && isfinite(mp->step_vox) && mp->term_alpha > 0.f &&
+                           mp->term_alpha <= 1.f,
+                  "bad march parameters");
+    FVN_CHECK_ARG(ctx, precision == FVN_PREC_FP16 || precision == FVN_PREC_FP8, "unknown precision %d", precision);
+    if (!ctx->has_weights) return set_error(ctx, FVN_ERR_STATE, "no weights loaded (call fvn_load_weights)");
+    if (precision == FVN_PREC_FP8 && !ctx->has_fp8)
+        return set_error(ctx, FVN_ERR_STATE, "FP8 needs calibrated scales (call fvn_calibrate_fp8 first)");
+    // distinct volumes (by pointer, size and type), each padded once
+    const fvn_volume* vols[kMaxBatchVolumes];
+    int nvol = 0, vol_of[kMaxViews];
+    for (int i = 0; i < nviews; ++i) {
+        fvn_status st = validate_view(ctx, views[i], i);
+        if (st != FVN_OK) return st;
+        int k = 0;
+        while (k < nvol && !same_volume(vols[k], views[i].vol)) ++k;
+        if (k == nvol) {
+            FVN_CHECK_ARG(ctx, nvol < kMaxBatchVolumes, "more than %d distinct volumes in one batch",
+                          kMaxBatchVolumes);
+            vols[nvol++] = views[i].vol;
+        }
+        vol_of[i] = k;
+    }
+    int tf_total = 0;   // distinct transfer functions share the march kernel's shared memory
+    for (int i = 0; i < nviews; ++i) {
+        bool seen = false;
+        for (int j = 0; j < i && !seen; ++j)
+            seen = views[j].tf->rgba == views[i].tf->rgba && views[j].tf->n == views[i].tf->n;
+        if (!seen) tf_total += views[i].tf->n;
+    }
+    FVN_CHECK_ARG(ctx, tf_total <= 4096, "the batch's transfer functions hold %d entries (at most 4096)", tf_total);
+
+    // ---- workspace (growing it is the one synchronising step) -------------
+    ViewLayout lay[kMaxViews];
+    const size_t need = batch_layout(views, nviews, lay);
+    BatchWorkspace& ws = ctx->batch_ws;
+    if (ws.bytes < need) {
+        FVN_CUDA(ctx, cudaDeviceSynchronize());
+        cudaFree(ws.base);
+        ws.base = nullptr;
+        ws.bytes = 0;
+        FVN_CUDA(ctx, cudaMalloc(&ws.base, need));
+        ws.bytes = need;
+    }
+    for (int k = 0; k < nvol; ++k) {
+        const size_t pb = padded_volume_bytes(vols[k]);
+        if (ws.pad_bytes[k] < pb) {
+            FVN_CUDA(ctx, cudaDeviceSynchronize());
+            cudaFree(ws.pad[k]);
+            ws.pad[k] = nullptr;
+            ws.pad_bytes[k] = 0;
+            FVN_CUDA(ctx, cudaMalloc(&ws.pad[k], pb));
+            ws.pad_bytes[k] = pb;
+        }
+    }
+    char* base = static_cast<char*>(ws.base);
+    int32_t* counts = reinterpret_cast<int32_t*>(base + need - align256(kMaxViews * sizeof(int32_t)));
+    cudaStream_t st = as_stream(stream);
+
+    // ---- mask + compaction: one launch -------------------------------------
+    const fvn_foveation* fov[kMaxViews];
+    int w[kMaxViews], h[kMaxViews];
+    uint8_t* mask[kMaxViews];
+    int32_t* ids[kMaxViews];
+    float* rgbam[kMaxViews];
+    for (int i = 0; i < nviews; ++i) {
+        fov[i] = &views[i].fov;
+        w[i] = views[i].cam.width;
+        h[i] = views[i].cam.height;
+        mask[i] = reinterpret_cast<uint8_t*>(base + lay[i].mask);
+        ids[i] = reinterpret_cast<int32_t*>(base + lay[i].ids);
+        rgbam[i] = views[i].rgbam ? views[i].rgbam : reinterpret_cast<float*>(base + lay[i].rgbam);
+    }
+    fvn_status s = make_mask_batch_impl(ctx, fov, w, h, mask, ids, counts, nviews, st);
+    if (s != FVN_OK) return s;
+
+    // ---- sparse frames start empty; padded volumes -------------------------
+    for (int i = 0; i < nviews; ++i)
+        FVN_CUDA(ctx, cudaMemsetAsync(rgbam[i], 0, 5 * sizeof(float) * (size_t)w[i] * h[i], st));
+    for (int k = 0; k < nvol; ++k)
+        if ((s = pad_volume_impl(ctx, vols[k], ws.pad[k], st)) != FVN_OK) return s;
+
+    // ---- one persistent march over every view's rays -----------------------
+    BatchMarchView mv[kMaxViews];
+    for (int i = 0; i < nviews; ++i)
+        mv[i] = BatchMarchView{views[i].vol, ws.pad[vol_of[i]], views[i].tf, &views[i].cam, ids[i], counts + i,
+                               rgbam[i]};
+    if ((s = march_batch_impl(ctx, mv, nviews, mp, nsamples, st)) != FVN_OK) return s;
+
+    // ---- network: one launch per layer over every view's tiles ------------
+    if (ctx->conv_impl == CONV_TCGEN05 || precision == FVN_PREC_FP8) {
+        ReconView rv[kMaxViews];
+        for (int i = 0; i < nviews; ++i) {
+            plan_view(w[i], h[i], &rv[i].plan, base + lay[i].plan);
+            rv[i].rgbam = rgbam[i];
+            rv[i].w = w[i];
+            rv[i].h = h[i];
+            rv[i].rgb = views[i].rgb;
+        }
+        return reconstruct_tc_views(ctx, rv, nviews, precision, st);
+    }
+    for (int i = 0; i < nviews; ++i)   // mma.sync convolutions: one network pass per view
+        if ((s = reconstruct_on(ctx, base + lay[i].plan, rgbam[i], w[i], h[i], precision, views[i].rgb, st)) !=
+            FVN_OK)
+            return s;
+    return FVN_OK;
+}

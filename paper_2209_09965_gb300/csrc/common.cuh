@@ -16,9 +16,14 @@
 namespace fvn {
 
 constexpr int kLutBins = 16384;       // threshold-table entries
-constexpr int kLutCache = 8;          // distinct foveation profiles kept per context
+constexpr int kLutCache = 16;         // distinct foveation profiles kept per context
 constexpr int kMaxSide = 16384;       // largest frame side accepted
 constexpr int kMaxVolSide = 4096;     // largest volume side accepted
+constexpr int kMaxViews = FVN_MAX_VIEWS;   // views of one batched render
+constexpr int kMaxBatchVolumes = 4;   // distinct volumes of one batched render
+// a batch's views never evict one another's threshold tables (least recently
+// used eviction only reaches profiles older than the batch)
+static_assert(kLutCache >= kMaxViews, "threshold-table cache smaller than a batch");
 
 struct LutEntry {
     bool valid = false;
@@ -52,6 +57,24 @@ struct ReconWorkspace {
 // Activation buffers of one reconstruction (FP16 NHWC, per level).
 struct ReconPlan {
     __half *e0a, *e0, *p0, *e1a, *e1, *p1, *ba, *bt, *d1a, *d1, *d0a, *d0;
+};
+
+// One view of a batched reconstruction: its activation buffers, sparse
+// frame and output.
+struct ReconView {
+    ReconPlan plan;
+    const float* rgbam;
+    int w, h;
+    float* rgb;
+};
+
+// Workspace of fvn_render_batch, one allocation carved per view.
+struct BatchWorkspace {
+    size_t bytes = 0;
+    void* base = nullptr;
+    int32_t* counts = nullptr;        // per-view sampled-pixel counts
+    void* pad[kMaxBatchVolumes] = {}; // padded volume copies
+    size_t pad_bytes[kMaxBatchVolumes] = {};
 };
 
 enum ConvImpl { CONV_TCGEN05 = 0, CONV_MMA_SYNC = 1 };
@@ -110,6 +133,7 @@ struct fvn_ctx {
     fvn::ReconWorkspace recon_ws;
     fvn::RenderWorkspace render_ws;
     fvn::ProbeWorkspace probe_ws;
+    fvn::BatchWorkspace batch_ws;
 };
 
 namespace fvn {
@@ -145,6 +169,28 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
                       unsigned long long* nsamples, cudaStream_t st, const uint8_t* reject = nullptr);
 fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
                             cudaStream_t st);
+// One view of the batched march: its volume and padded copy, transfer
+// function, camera, compacted ids / count (device) and sparse frame.
+struct BatchMarchView {
+    const fvn_volume* vol;
+    const void* pvol;
+    const fvn_tf* tf;
+    const fvn_camera* cam;
+    const int32_t* ids;
+    const int32_t* count;
+    float* rgbam;
+};
+// Every view's rays in one persistent launch (rgbam must already be zero
+// outside the sampled pixels).
+fvn_status march_batch_impl(fvn_ctx* ctx, const BatchMarchView* views, int n, const fvn_march_params* mp,
+                            unsigned long long* nsamples, cudaStream_t st);
+size_t padded_volume_bytes(const fvn_volume* vol);
+fvn_status pad_volume_impl(fvn_ctx* ctx, const fvn_volume* vol, void* pvol, cudaStream_t st);
+// Masks and id lists of n views in one launch: view i writes mask[i] and its
+// ids at ids[i], its count at counts[i] (counts zeroed here).
+fvn_status make_mask_batch_impl(fvn_ctx* ctx, const fvn_foveation* const* fov, const int* w, const int* h,
+                                uint8_t* const* mask, int32_t* const* ids, int32_t* counts, int n,
+                                cudaStream_t st);
 // The network launch sequence on a caller-provided workspace of at least
 // recon_workspace_bytes(w, h) bytes (256-byte aligned).
 fvn_status reconstruct_on(fvn_ctx* ctx, void* workspace, const float* rgbam, int w, int h, int precision,
@@ -155,5 +201,9 @@ fvn_status reconstruct_tc(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, 
 fvn_status reconstruct_tc_fp8(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, int w, int h, float* rgb,
                               cudaStream_t st);
 fvn_status calibrate_amax(fvn_ctx* ctx, const ReconPlan& B, int w, int h, float* d_amax, cudaStream_t st);
+// The network over n views, one launch per layer for all of them (tcgen05).
+fvn_status reconstruct_tc_views(fvn_ctx* ctx, const ReconView* views, int n, int precision, cudaStream_t st);
+// Activation buffers of one view carved from `base` (nullptr: size only).
+size_t plan_view(int w, int h, ReconPlan* plan, char* base);
 
 }  // namespace fvn

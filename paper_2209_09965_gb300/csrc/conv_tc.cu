@@ -136,11 +136,21 @@ struct TcLayout {
                                         : need_cols <= 256 ? 256 : 512;
 };
 
-struct TcArgs {
+// One image of a batched launch: its tensors and sizes, and the first tile
+// of the launch's tile range that belongs to it.
+struct TcImg {
     const void* in;          // NHWC input, or the coarse level for up-sampling
     const void* skip;        // skip tensor (up-sampling layers)
     const float* rgbam;      // sparse frame [5][H0][W0] (first layer, KP)
+    void* out;               // [Hl][Wl][COUT]
+    void* pooled;            // [Hl/2][Wl/2][COUT]
+    float* rgb;              // [3][H0][W0] (KP layer)
     int H0, W0;
+    int Hl, Wl;
+    int tiles_x, tile0;
+};
+
+struct TcArgs {
     const void* w;           // [9][CIN/CPC][COUT][16 B]
     const float* bias;
     const float* wscale;     // FP8: per output channel weight scale
@@ -148,13 +158,18 @@ struct TcArgs {
     float out_q, pool_q;     // FP8: 1 / s of the output / pooled tensor
     const __half* head_w;    // [2][32][8] halves (KP layer)
     const float* head_b;     // [32]
-    void* out;               // [Hl][Wl][COUT]
-    void* pooled;            // [Hl/2][Wl/2][COUT]
-    float* rgb;              // [3][H0][W0] (KP layer)
-    int Hl, Wl;
-    int tiles_x, ntiles;
+    int ntiles;              // tiles of all images
+    int nimg;
     int* error;              // set when a tensor-core wait gives up
+    TcImg img[kMaxViews];
 };
+
+// Image of tile `tile` (the images' tile ranges are consecutive).
+__device__ __forceinline__ int find_img(const TcArgs& a, int tile) {
+    int i = 0;
+    while (i + 1 < a.nimg && tile >= a.img[i + 1].tile0) ++i;
+    return i;
+}
 
 // Store COUT channel values of one pixel (FP16, or FP8 after scaling by q).
 template <int COUT, bool F8>
@@ -176,7 +191,7 @@ __device__ __forceinline__ void store_pixel(void* base, long long pix, const flo
 }
 
 template <int CIN, int CG, int COUT, int TR, int MODE, int EPI, int CUP, bool F8>
-__global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(TcArgs a) {
+__global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_constant__ TcArgs a) {
     using L = TcLayout<CIN, CG, COUT, TR, MODE, EPI, CUP, F8>;
     constexpr int CH = L::CH, CHG = L::CHG, CPC = L::CPC, EB = L::EB, HY = L::HY;
     constexpr int CUPC = CUP / CPC;                   // up-sampled chunks
@@ -222,29 +237,31 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(TcArgs a) {
     const uint32_t tmem = *tbase_s;
     const uint32_t sW_u = tc::smem_addr(sW), sH_u = tc::smem_addr(sH0);
     constexpr uint32_t idesc = F8 ? tc::idesc_e4m3(128, COUT) : tc::idesc_f16(128, COUT);
-    const unsigned char* gin = static_cast<const unsigned char*>(a.in);
-    const unsigned char* gskip = static_cast<const unsigned char*>(a.skip);
     uint32_t phase = 0;
     bool failed = false;
 
     // Stage the input halo (and the sparse samples of the KP layer) of a tile
     // into buffer `buf`.  Plain copies are left in flight (cp.async); the
     // up-sampling layers wait for theirs and interpolate here.
-    auto stage = [&](int tile, int buf) {
-        const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
+    auto stage = [&](int gtile, int buf) {
+        const TcImg& im = a.img[find_img(a, gtile)];
+        const unsigned char* gin = static_cast<const unsigned char*>(im.in);
+        const unsigned char* gskip = static_cast<const unsigned char*>(im.skip);
+        const int tile = gtile - im.tile0;
+        const int ty = tile / im.tiles_x, tx = tile - ty * im.tiles_x;
         const int y0 = ty * TR, x0 = tx * TW;
         unsigned char* sH = smem + L::halo_off + (size_t)buf * L::halo_bytes;
         float4* sSP = reinterpret_cast<float4*>(smem + L::sp_off + (size_t)buf * L::sp1_bytes);
         if (MODE == TIN_RGBAM) {
-            const long long plane = (long long)a.H0 * a.W0;
+            const long long plane = (long long)im.H0 * im.W0;
             for (int i = tid; i < HY * HXW; i += kThreads) {
                 const int hy = i / HXW, hx = i - hy * HXW;
                 const int gy = y0 + hy - 1, gx = x0 + hx - 1;
                 float v[16];
 #pragma unroll
                 for (int c = 0; c < 16; ++c) v[c] = 0.f;
-                if (gy >= 0 && gx >= 0 && gy < a.H0 && gx < a.W0) {
-                    const float* p = a.rgbam + (long long)gy * a.W0 + gx;
+                if (gy >= 0 && gx >= 0 && gy < im.H0 && gx < im.W0) {
+                    const float* p = im.rgbam + (long long)gy * im.W0 + gx;
 #pragma unroll
                     for (int c = 0; c < 5; ++c) v[c] = __ldg(p + c * plane) * (F8 ? a.in_q : 1.0f);
                 }
@@ -261,8 +278,8 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(TcArgs a) {
                 const int hy = rem / HXW, hx = rem - hy * HXW;
                 const int gy = y0 + hy - 1, gx = x0 + hx - 1;
                 unsigned char* dst = sH + ((c * HY + hy) * HXW + hx) * 16;
-                if (c < CHG && gy >= 0 && gx >= 0 && gy < a.Hl && gx < a.Wl) {
-                    const long long pix = (long long)gy * a.Wl + gx;
+                if (c < CHG && gy >= 0 && gx >= 0 && gy < im.Hl && gx < im.Wl) {
+                    const long long pix = (long long)gy * im.Wl + gx;
                     if (MODE == TIN_NHWC) cp16(tc::smem_addr(dst), gin + (pix * CG + c * CPC) * EB);
                     else cp16(tc::smem_addr(dst), gskip + (pix * (CG - CUP) + (c - CS0) * CPC) * EB);
                 } else {
@@ -270,7 +287,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(TcArgs a) {
                 }
             }
             if (MODE == TIN_UPCAT) {   // coarse rows / columns around the tile, clamped to the coarse frame
-                const int Hc = a.Hl >> 1, Wc = a.Wl >> 1;
+                const int Hc = im.Hl >> 1, Wc = im.Wl >> 1;
                 const int cy0 = (y0 >> 1) - 1, cx0 = (x0 >> 1) - 1;
                 for (int i = tid; i < CUPC * L::CR * L::CC; i += kThreads) {
                     const int c = i / (L::CR * L::CC);
@@ -284,12 +301,12 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(TcArgs a) {
             if (MODE == TIN_UPCAT) {
                 cp_wait_all();
                 __syncthreads();
-                const int Hc = a.Hl >> 1, Wc = a.Wl >> 1;
+                const int Hc = im.Hl >> 1, Wc = im.Wl >> 1;
                 const int cy0 = (y0 >> 1) - 1, cx0 = (x0 >> 1) - 1;
                 for (int i = tid; i < HY * HXW; i += kThreads) {
                     const int hy = i / HXW, hx = i - hy * HXW;
                     const int gy = y0 + hy - 1, gx = x0 + hx - 1;
-                    const bool inside = gy >= 0 && gx >= 0 && gy < a.Hl && gx < a.Wl;
+                    const bool inside = gy >= 0 && gx >= 0 && gy < im.Hl && gx < im.Wl;
                     // bilinear x2 with half-pixel centres: fine 2m -> coarse m-1 / m with weights
                     // 1/4, 3/4 (source clamped to 0 at m = 0), fine 2m+1 -> m / m+1 with 3/4, 1/4;
                     // the upper neighbour is clamped to the frame
@@ -336,13 +353,13 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(TcArgs a) {
             }
         }
         if (EPI == TEPI_HEADKP) {   // sparse R, G, B, M around the tile (2-pixel margin)
-            const long long plane = (long long)a.H0 * a.W0;
+            const long long plane = (long long)im.H0 * im.W0;
             for (int i = tid; i < (TR + 4) * (TW + 4); i += kThreads) {
                 const int r = i / (TW + 4), q = i - r * (TW + 4);
                 const int gy = y0 + r - 2, gx = x0 + q - 2;
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (gy >= 0 && gx >= 0 && gy < a.H0 && gx < a.W0) {
-                    const float* p = a.rgbam + (long long)gy * a.W0 + gx;
+                if (gy >= 0 && gx >= 0 && gy < im.H0 && gx < im.W0) {
+                    const float* p = im.rgbam + (long long)gy * im.W0 + gx;
                     v = make_float4(__ldg(p), __ldg(p + plane), __ldg(p + 2 * plane), __ldg(p + 4 * plane));
                 }
                 sSP[i] = v;
@@ -359,7 +376,9 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(TcArgs a) {
         __syncthreads();
     }
     for (; tile < a.ntiles && !failed; tile += gridDim.x) {
-        const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
+        const TcImg& im = a.img[find_img(a, tile)];
+        const int ltile = tile - im.tile0;
+        const int ty = ltile / im.tiles_x, tx = ltile - ty * im.tiles_x;
         const int y0 = ty * TR, x0 = tx * TW;
         const int next = tile + gridDim.x;
         const float4* sSP = reinterpret_cast<const float4*>(smem + L::sp_off + (size_t)buf * L::sp1_bytes);
@@ -414,7 +433,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(TcArgs a) {
                 for (int c = 0; c < COUT; c += 16) tc::tmem_ld16(tmem + lane_base + r * COUT + c, v + c);
 #pragma unroll
                 for (int c = 0; c < COUT; ++c) v[c] = fmaxf(fmaf(v[c], sScale[c], sBias[c]), 0.f);
-                if (y < a.Hl && x < a.Wl) store_pixel<COUT, F8>(a.out, (long long)y * a.Wl + x, v, a.out_q);
+                if (y < im.Hl && x < im.Wl) store_pixel<COUT, F8>(im.out, (long long)y * im.Wl + x, v, a.out_q);
                 if (EPI == TEPI_POOL) {
                     if (r & 1) {
                         float s[COUT];
@@ -424,8 +443,8 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(TcArgs a) {
                             s[c] += __shfl_xor_sync(0xffffffffu, s[c], 1);
                             s[c] *= 0.25f;
                         }
-                        if ((lane & 1) == 0 && y < a.Hl && x < a.Wl)
-                            store_pixel<COUT, F8>(a.pooled, (long long)(y >> 1) * (a.Wl >> 1) + (x >> 1), s, a.pool_q);
+                        if ((lane & 1) == 0 && y < im.Hl && x < im.Wl)
+                            store_pixel<COUT, F8>(im.pooled, (long long)(y >> 1) * (im.Wl >> 1) + (x >> 1), s, a.pool_q);
                     } else {
 #pragma unroll
                         for (int c = 0; c < COUT; ++c) prev[c] = v[c];
@@ -463,7 +482,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(TcArgs a) {
             }
             phase ^= 1u;
             tc::fence_after_sync();
-            const long long plane = (long long)a.H0 * a.W0;
+            const long long plane = (long long)im.H0 * im.W0;
 #pragma unroll 1
             for (int r = r_lo; r < r_hi; ++r) {
                 const int y = y0 + r;
@@ -497,8 +516,8 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(TcArgs a) {
                     k2 = n2 / den;
                 }
                 const float al = 1.0f / (1.0f + expf(-hd[28]));
-                if (y < a.H0 && x < a.W0) {
-                    float* o = a.rgb + (long long)y * a.W0 + x;
+                if (y < im.H0 && x < im.W0) {
+                    float* o = im.rgb + (long long)y * im.W0 + x;
                     o[0] = fmaf(al, k0 - hd[0], hd[0]);
                     o[plane] = fmaf(al, k1 - hd[1], hd[1]);
                     o[2 * plane] = fmaf(al, k2 - hd[2], hd[2]);
@@ -539,7 +558,7 @@ __global__ void amax_f16_kernel(const __half* __restrict__ x, long long n, float
 }  // namespace
 
 template <int CIN, int CG, int COUT, int TR, int MODE, int EPI, int CUP, bool F8>
-static fvn_status launch_tc(fvn_ctx* ctx, TcArgs a, cudaStream_t st) {
+static fvn_status launch_tc(fvn_ctx* ctx, TcArgs& a, cudaStream_t st) {
     using L = TcLayout<CIN, CG, COUT, TR, MODE, EPI, CUP, F8>;
     auto kern = conv3x3_tc_kernel<CIN, CG, COUT, TR, MODE, EPI, CUP, F8>;
     static bool configured = false;
@@ -555,100 +574,111 @@ static fvn_status launch_tc(fvn_ctx* ctx, TcArgs a, cudaStream_t st) {
     per_sm = std::min(per_sm, (int)(512 / L::tmem_cols));
     per_sm = std::min(per_sm, 2048 / kThreads);
     if (per_sm < 1) return set_error(ctx, FVN_ERR_CUDA, "tensor-core conv kernel does not fit on an SM");
-    a.tiles_x = (a.Wl + TW - 1) / TW;
-    a.ntiles = a.tiles_x * ((a.Hl + TR - 1) / TR);
+    int ntiles = 0;
+    for (int i = 0; i < a.nimg; ++i) {
+        TcImg& m = a.img[i];
+        m.tiles_x = (m.Wl + TW - 1) / TW;
+        m.tile0 = ntiles;
+        ntiles += m.tiles_x * ((m.Hl + TR - 1) / TR);
+    }
+    a.ntiles = ntiles;
     const int grid = std::min(a.ntiles, ctx->num_sms * per_sm);
     a.error = ctx->d_error;
-    kern<<<grid, kThreads, L::bytes, st>>>(a);
-    FVN_LAUNCH_CHECK(ctx);
+    if (grid > 0) {
+        kern<<<grid, kThreads, L::bytes, st>>>(a);
+        FVN_LAUNCH_CHECK(ctx);
+    }
     return FVN_OK;
+}
+
+// Tensors and sizes of layer l (0..9) of the network for one view.
+static TcImg layer_img(int l, const ReconView& v) {
+    const ReconPlan& B = v.plan;
+    const int W4 = (v.w + 3) & ~3, H4 = (v.h + 3) & ~3;
+    TcImg m{};
+    switch (l) {
+        case 0: m.rgbam = v.rgbam; m.H0 = v.h; m.W0 = v.w; m.out = B.e0a; m.Hl = H4; m.Wl = W4; break;
+        case 1: m.in = B.e0a; m.out = B.e0; m.pooled = B.p0; m.Hl = H4; m.Wl = W4; break;
+        case 2: m.in = B.p0; m.out = B.e1a; m.Hl = H4 / 2; m.Wl = W4 / 2; break;
+        case 3: m.in = B.e1a; m.out = B.e1; m.pooled = B.p1; m.Hl = H4 / 2; m.Wl = W4 / 2; break;
+        case 4: m.in = B.p1; m.out = B.ba; m.Hl = H4 / 4; m.Wl = W4 / 4; break;
+        case 5: m.in = B.ba; m.out = B.bt; m.Hl = H4 / 4; m.Wl = W4 / 4; break;
+        case 6: m.in = B.bt; m.skip = B.e1; m.out = B.d1a; m.Hl = H4 / 2; m.Wl = W4 / 2; break;
+        case 7: m.in = B.d1a; m.out = B.d1; m.Hl = H4 / 2; m.Wl = W4 / 2; break;
+        case 8: m.in = B.d1; m.skip = B.e0; m.out = B.d0a; m.Hl = H4; m.Wl = W4; break;
+        default:
+            m.in = B.d0a; m.rgbam = v.rgbam; m.H0 = v.h; m.W0 = v.w; m.rgb = v.rgb; m.Hl = H4; m.Wl = W4;
+            break;
+    }
+    return m;
+}
+
+// The ten launches of the network over every view at once (one launch per
+// layer covers the tiles of all views).  FP16 operands, or FP8 operands with
+// the calibrated scales; FP8 tensors use half of each FP16 buffer.
+template <bool F8>
+static fvn_status run_tc(fvn_ctx* ctx, const ReconView* views, int n, cudaStream_t st) {
+    const ConvW* L = ctx->layers;
+    const float* q = ctx->fp8_inv_scale;   // 1 / s per activation tensor
+    TcArgs a;
+    auto prep = [&](int l) {
+        a = TcArgs{};
+        a.nimg = n;
+        for (int i = 0; i < n; ++i) a.img[i] = layer_img(l, views[i]);
+        a.w = F8 ? static_cast<const void*>(L[l].w8) : static_cast<const void*>(L[l].w16);
+        a.bias = L[l].bias;
+        a.wscale = L[l].scale8;
+    };
+    constexpr int K16 = F8 ? 32 : 16;      // K per tap of the 16-channel layers (FP8 MMA K = 32)
+    fvn_status s;
+    prep(0);
+    a.in_q = q[FP8_RGBAM]; a.out_q = q[FP8_E0A];
+    if ((s = launch_tc<K16, 16, 16, 4, TIN_RGBAM, TEPI_STORE, 0, F8>(ctx, a, st)) != FVN_OK) return s;
+    prep(1);
+    a.out_q = q[FP8_E0]; a.pool_q = q[FP8_P0];
+    if ((s = launch_tc<K16, 16, 16, 4, TIN_NHWC, TEPI_POOL, 0, F8>(ctx, a, st)) != FVN_OK) return s;
+    prep(2);
+    a.out_q = q[FP8_E1A];
+    if ((s = launch_tc<K16, 16, 32, 4, TIN_NHWC, TEPI_STORE, 0, F8>(ctx, a, st)) != FVN_OK) return s;
+    prep(3);
+    a.out_q = q[FP8_E1]; a.pool_q = q[FP8_P1];
+    if ((s = launch_tc<32, 32, 32, 4, TIN_NHWC, TEPI_POOL, 0, F8>(ctx, a, st)) != FVN_OK) return s;
+    prep(4);
+    a.out_q = q[FP8_BA];
+    if ((s = launch_tc<32, 32, 64, 2, TIN_NHWC, TEPI_STORE, 0, F8>(ctx, a, st)) != FVN_OK) return s;
+    prep(5);
+    a.out_q = q[FP8_BT];
+    if ((s = launch_tc<64, 64, 64, 2, TIN_NHWC, TEPI_STORE, 0, F8>(ctx, a, st)) != FVN_OK) return s;
+    prep(6);
+    a.out_q = q[FP8_D1A];
+    if ((s = launch_tc<96, 96, 32, 2, TIN_UPCAT, TEPI_STORE, 64, F8>(ctx, a, st)) != FVN_OK) return s;
+    prep(7);
+    a.out_q = q[FP8_D1];
+    if ((s = launch_tc<32, 32, 32, 4, TIN_NHWC, TEPI_STORE, 0, F8>(ctx, a, st)) != FVN_OK) return s;
+    prep(8);
+    a.out_q = q[FP8_D0A];
+    if ((s = launch_tc<F8 ? 64 : 48, 48, 16, 4, TIN_UPCAT, TEPI_STORE, 32, F8>(ctx, a, st)) != FVN_OK) return s;
+    prep(9);
+    a.head_w = ctx->head_w16;
+    a.head_b = ctx->head_b32;
+    return launch_tc<K16, 16, 16, 4, TIN_NHWC, TEPI_HEADKP, 0, F8>(ctx, a, st);
+}
+
+fvn_status reconstruct_tc_views(fvn_ctx* ctx, const ReconView* views, int n, int precision, cudaStream_t st) {
+    if (n < 1 || n > kMaxViews) return set_error(ctx, FVN_ERR_ARG, "%d views (1..%d)", n, kMaxViews);
+    return precision == FVN_PREC_FP8 ? run_tc<true>(ctx, views, n, st) : run_tc<false>(ctx, views, n, st);
 }
 
 fvn_status reconstruct_tc(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, int w, int h, float* rgb,
                           cudaStream_t st) {
-    const int W4 = (w + 3) & ~3, H4 = (h + 3) & ~3;
-    const ConvW* L = ctx->layers;
-    fvn_status s;
-    TcArgs a{};
-    a.rgbam = rgbam; a.H0 = h; a.W0 = w; a.w = L[0].w16; a.bias = L[0].bias; a.out = B.e0a; a.Hl = H4; a.Wl = W4;
-    if ((s = launch_tc<16, 16, 16, 4, TIN_RGBAM, TEPI_STORE, 0, false>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.e0a; a.w = L[1].w16; a.bias = L[1].bias; a.out = B.e0; a.pooled = B.p0; a.Hl = H4; a.Wl = W4;
-    if ((s = launch_tc<16, 16, 16, 4, TIN_NHWC, TEPI_POOL, 0, false>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.p0; a.w = L[2].w16; a.bias = L[2].bias; a.out = B.e1a; a.Hl = H4 / 2; a.Wl = W4 / 2;
-    if ((s = launch_tc<16, 16, 32, 4, TIN_NHWC, TEPI_STORE, 0, false>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.e1a; a.w = L[3].w16; a.bias = L[3].bias; a.out = B.e1; a.pooled = B.p1; a.Hl = H4 / 2; a.Wl = W4 / 2;
-    if ((s = launch_tc<32, 32, 32, 4, TIN_NHWC, TEPI_POOL, 0, false>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.p1; a.w = L[4].w16; a.bias = L[4].bias; a.out = B.ba; a.Hl = H4 / 4; a.Wl = W4 / 4;
-    if ((s = launch_tc<32, 32, 64, 2, TIN_NHWC, TEPI_STORE, 0, false>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.ba; a.w = L[5].w16; a.bias = L[5].bias; a.out = B.bt; a.Hl = H4 / 4; a.Wl = W4 / 4;
-    if ((s = launch_tc<64, 64, 64, 2, TIN_NHWC, TEPI_STORE, 0, false>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.bt; a.skip = B.e1; a.w = L[6].w16; a.bias = L[6].bias; a.out = B.d1a; a.Hl = H4 / 2; a.Wl = W4 / 2;
-    if ((s = launch_tc<96, 96, 32, 2, TIN_UPCAT, TEPI_STORE, 64, false>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.d1a; a.w = L[7].w16; a.bias = L[7].bias; a.out = B.d1; a.Hl = H4 / 2; a.Wl = W4 / 2;
-    if ((s = launch_tc<32, 32, 32, 4, TIN_NHWC, TEPI_STORE, 0, false>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.d1; a.skip = B.e0; a.w = L[8].w16; a.bias = L[8].bias; a.out = B.d0a; a.Hl = H4; a.Wl = W4;
-    if ((s = launch_tc<48, 48, 16, 4, TIN_UPCAT, TEPI_STORE, 32, false>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.d0a; a.w = L[9].w16; a.bias = L[9].bias; a.head_w = ctx->head_w16; a.head_b = ctx->head_b32;
-    a.rgbam = rgbam; a.H0 = h; a.W0 = w; a.rgb = rgb; a.Hl = H4; a.Wl = W4;
-    return launch_tc<16, 16, 16, 4, TIN_NHWC, TEPI_HEADKP, 0, false>(ctx, a, st);
+    const ReconView v{B, rgbam, w, h, rgb};
+    return run_tc<false>(ctx, &v, 1, st);
 }
 
-// FP8 network: same buffers (FP8 tensors use half of each FP16 buffer).
 fvn_status reconstruct_tc_fp8(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, int w, int h, float* rgb,
                               cudaStream_t st) {
-    const int W4 = (w + 3) & ~3, H4 = (h + 3) & ~3;
-    const ConvW* L = ctx->layers;
-    const float* q = ctx->fp8_inv_scale;   // 1 / s per activation tensor
-    fvn_status s;
-    TcArgs a{};
-    a.rgbam = rgbam; a.H0 = h; a.W0 = w; a.w = L[0].w8; a.wscale = L[0].scale8; a.bias = L[0].bias;
-    a.in_q = q[FP8_RGBAM]; a.out_q = q[FP8_E0A]; a.out = B.e0a; a.Hl = H4; a.Wl = W4;
-    if ((s = launch_tc<32, 16, 16, 4, TIN_RGBAM, TEPI_STORE, 0, true>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.e0a; a.w = L[1].w8; a.wscale = L[1].scale8; a.bias = L[1].bias; a.out_q = q[FP8_E0];
-    a.pool_q = q[FP8_P0]; a.out = B.e0; a.pooled = B.p0; a.Hl = H4; a.Wl = W4;
-    if ((s = launch_tc<32, 16, 16, 4, TIN_NHWC, TEPI_POOL, 0, true>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.p0; a.w = L[2].w8; a.wscale = L[2].scale8; a.bias = L[2].bias; a.out_q = q[FP8_E1A];
-    a.out = B.e1a; a.Hl = H4 / 2; a.Wl = W4 / 2;
-    if ((s = launch_tc<32, 16, 32, 4, TIN_NHWC, TEPI_STORE, 0, true>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.e1a; a.w = L[3].w8; a.wscale = L[3].scale8; a.bias = L[3].bias; a.out_q = q[FP8_E1];
-    a.pool_q = q[FP8_P1]; a.out = B.e1; a.pooled = B.p1; a.Hl = H4 / 2; a.Wl = W4 / 2;
-    if ((s = launch_tc<32, 32, 32, 4, TIN_NHWC, TEPI_POOL, 0, true>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.p1; a.w = L[4].w8; a.wscale = L[4].scale8; a.bias = L[4].bias; a.out_q = q[FP8_BA];
-    a.out = B.ba; a.Hl = H4 / 4; a.Wl = W4 / 4;
-    if ((s = launch_tc<32, 32, 64, 2, TIN_NHWC, TEPI_STORE, 0, true>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.ba; a.w = L[5].w8; a.wscale = L[5].scale8; a.bias = L[5].bias; a.out_q = q[FP8_BT];
-    a.out = B.bt; a.Hl = H4 / 4; a.Wl = W4 / 4;
-    if ((s = launch_tc<64, 64, 64, 2, TIN_NHWC, TEPI_STORE, 0, true>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.bt; a.skip = B.e1; a.w = L[6].w8; a.wscale = L[6].scale8; a.bias = L[6].bias; a.out_q = q[FP8_D1A];
-    a.out = B.d1a; a.Hl = H4 / 2; a.Wl = W4 / 2;
-    if ((s = launch_tc<96, 96, 32, 2, TIN_UPCAT, TEPI_STORE, 64, true>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.d1a; a.w = L[7].w8; a.wscale = L[7].scale8; a.bias = L[7].bias; a.out_q = q[FP8_D1];
-    a.out = B.d1; a.Hl = H4 / 2; a.Wl = W4 / 2;
-    if ((s = launch_tc<32, 32, 32, 4, TIN_NHWC, TEPI_STORE, 0, true>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.d1; a.skip = B.e0; a.w = L[8].w8; a.wscale = L[8].scale8; a.bias = L[8].bias; a.out_q = q[FP8_D0A];
-    a.out = B.d0a; a.Hl = H4; a.Wl = W4;
-    if ((s = launch_tc<64, 48, 16, 4, TIN_UPCAT, TEPI_STORE, 32, true>(ctx, a, st)) != FVN_OK) return s;
-    a = TcArgs{};
-    a.in = B.d0a; a.w = L[9].w8; a.wscale = L[9].scale8; a.bias = L[9].bias; a.head_w = ctx->head_w16;
-    a.head_b = ctx->head_b32; a.rgbam = rgbam; a.H0 = h; a.W0 = w; a.rgb = rgb; a.Hl = H4; a.Wl = W4;
-    return launch_tc<32, 16, 16, 4, TIN_NHWC, TEPI_HEADKP, 0, true>(ctx, a, st);
+    const ReconView v{B, rgbam, w, h, rgb};
+    return run_tc<true>(ctx, &v, 1, st);
 }
 
 // Reduce the amax of every calibrated activation tensor of the FP16 network

@@ -379,28 +379,155 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Batched march: the rays of several views (each with its own camera, frame,
+// compacted id list, output, volume of any voxel type and transfer function)
+// in one persistent launch.  Tickets run over the concatenation of the views'
+// id lists, so a warp takes rays of one view except where two lists meet;
+// per ray the arithmetic is exactly that of march_kernel.
+
+struct MarchBatchView {
+    MarchArgs a;                      // per-view fields (pvol = padded copy of its volume)
+    int dtype;                        // fvn_dtype of the volume
+    int tf_off;                       // first entry of its transfer function in shared memory
+};
+
+struct MarchBatch {
+    int nviews;
+    int ntfs;                         // distinct transfer functions
+    const float4* tf[kMaxViews];
+    int tf_n[kMaxViews], tf_off[kMaxViews];
+    unsigned long long* nsamples;
+    int* ticket;
+    int refill_below;
+    MarchBatchView v[kMaxViews];
+};
+static_assert(sizeof(MarchBatch) <= 4096, "batched march arguments exceed the 4 KB parameter space");
+
+template <typename I, bool SHADE>
+__device__ __forceinline__ bool batch_step(const MarchBatchView& bv, const float4* s_tf, Ray& s) {
+    const MarchArgs& a = bv.a;
+    const I sy = (I)(a.nx + 2 * kPad), sz = sy * (I)(a.ny + 2 * kPad);
+    const float ux0 = a.ox - 0.5f, uy0 = a.oy - 0.5f, uz0 = a.oz - 0.5f;
+    const float tfmax = (float)(a.ntf - 1);
+    const float4* tf = s_tf + bv.tf_off;
+    switch (bv.dtype) {
+        case FVN_U8:
+            return ray_step<uint8_t, I, SHADE>(a, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
+                                               tfmax, s);
+        case FVN_U16:
+            return ray_step<uint16_t, I, SHADE>(a, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0, uy0,
+                                                uz0, tfmax, s);
+        case FVN_F16:
+            return ray_step<__half, I, SHADE>(a, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
+                                              tfmax, s);
+        default:
+            return ray_step<float, I, SHADE>(a, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
+                                             tfmax, s);
+    }
+}
+
+template <typename I, bool SHADE>
+__global__ void __launch_bounds__(128) march_batch_kernel(const __grid_constant__ MarchBatch b) {
+    extern __shared__ float4 s_tf[];
+    __shared__ int s_start[kMaxViews + 1];   // first ticket of each view
+    for (int k = 0; k < b.ntfs; ++k)
+        for (int i = threadIdx.x; i < b.tf_n[k]; i += blockDim.x) s_tf[b.tf_off[k] + i] = b.tf[k][i];
+    if (threadIdx.x == 0) {
+        int acc = 0;
+        for (int v = 0; v < b.nviews; ++v) {
+            s_start[v] = acc;
+            const MarchArgs& a = b.v[v].a;
+            acc += min(max(*a.count, 0), a.W * a.H);
+        }
+        s_start[b.nviews] = acc;
+    }
+    __syncthreads();
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const int nrays = s_start[b.nviews];
+    unsigned long long my_samples = 0;
+    Ray s;
+    s.pix = -1;
+    int view = 0;
+    bool exhausted = false;
+    for (;;) {
+        if (!exhausted) {
+            const unsigned idle = __ballot_sync(FULL, s.pix < 0);
+            if (idle) {
+                const int nidle = __popc(idle);
+                int base = 0;
+                if (lane == 0) base = atomicAdd(b.ticket, nidle);
+                base = __shfl_sync(FULL, base, 0);
+                if (base + nidle >= nrays) exhausted = true;
+                if (s.pix < 0) {
+                    const int r = base + __popc(idle & ((1u << lane) - 1u));
+                    if (r < nrays) {
+                        int v = 0;
+                        while (v + 1 < b.nviews && r >= s_start[v + 1]) ++v;
+                        view = v;
+                        const MarchArgs& a = b.v[v].a;
+                        if (start_ray(a, r - s_start[v], a.W * a.H, s) && !(s.tfar > -INFINITY)) {
+                            finish_ray(a, s);   // missed the box: background, no sample
+                            s.pix = -1;
+                        }
+                    }
+                }
+            }
+        }
+        unsigned busy = __ballot_sync(FULL, s.pix >= 0);
+        if (busy == 0) {
+            if (exhausted) break;
+            continue;
+        }
+        while (busy != 0 && (exhausted || __popc(busy) >= b.refill_below)) {
+            if (s.pix >= 0 && batch_step<I, SHADE>(b.v[view], s_tf, s)) {
+                my_samples += (unsigned long long)s.kf;
+                finish_ray(b.v[view].a, s);
+                s.pix = -1;
+            }
+            busy = __ballot_sync(FULL, s.pix >= 0);
+        }
+        if (exhausted && busy == 0) break;
+    }
+    if (b.nsamples) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) my_samples += __shfl_xor_sync(FULL, my_samples, o);
+        if (lane == 0 && my_samples) atomicAdd(b.nsamples, my_samples);
+    }
+}
+
+// One warp per padded (y, z) row, eight rows per block: few, full blocks and
+// coalesced row copies (clamp-to-edge in x, y and z).
 template <typename T>
-__global__ void pad_volume_kernel(const T* __restrict__ src, int nx, int ny, int nz, T* __restrict__ dst) {
-    // one block row per padded (y, z) row: no integer division per element
-    const int px = nx + 2 * kPad, py = ny + 2 * kPad;
-    const int y = blockIdx.y, z = blockIdx.z;
+__global__ void __launch_bounds__(256) pad_volume_kernel(const T* __restrict__ src, int nx, int ny, int nz,
+                                                         T* __restrict__ dst) {
+    const int px = nx + 2 * kPad, py = ny + 2 * kPad, pz = nz + 2 * kPad;
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= py * pz) return;
+    const int z = row / py, y = row - z * py;
     const int sy = min(max(y - kPad, 0), ny - 1), sz = min(max(z - kPad, 0), nz - 1);
     const T* s = src + ((long long)sz * ny + sy) * nx;
-    T* d = dst + ((long long)z * py + y) * px;
-    for (int x = blockIdx.x * blockDim.x + threadIdx.x; x < px; x += gridDim.x * blockDim.x)
-        d[x] = s[min(max(x - kPad, 0), nx - 1)];
+    T* d = dst + (long long)row * px;
+#pragma unroll 4
+    for (int x = threadIdx.x & 31; x < px; x += 32) d[x] = s[min(max(x - kPad, 0), nx - 1)];
+}
+
+template <typename T>
+static fvn_status pad_volume(fvn_ctx* ctx, const void* vol, int nx, int ny, int nz, void* pvol, cudaStream_t st) {
+    const long long rows = (long long)(ny + 2 * kPad) * (nz + 2 * kPad);
+    pad_volume_kernel<T><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(static_cast<const T*>(vol), nx, ny, nz,
+                                                                       static_cast<T*>(pvol));
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
 }
 
 template <typename T, typename I>
 static fvn_status launch_typed(fvn_ctx* ctx, const MarchArgs& a, bool shade, cudaStream_t st) {
     const size_t smem = (size_t)a.ntf * sizeof(float4);
-    {   // refresh the padded copy of the volume (one pass over it)
-        const int px = a.nx + 2 * kPad;
-        dim3 grid((px + 255) / 256, a.ny + 2 * kPad, a.nz + 2 * kPad);
-        pad_volume_kernel<T><<<grid, 256, 0, st>>>(static_cast<const T*>(a.vol), a.nx, a.ny, a.nz,
-                                                   static_cast<T*>(const_cast<void*>(a.pvol)));
-        FVN_LAUNCH_CHECK(ctx);
-    }
+    // refresh the padded copy of the volume (one pass over it)
+    fvn_status ps = pad_volume<T>(ctx, a.vol, a.nx, a.ny, a.nz, const_cast<void*>(a.pvol), st);
+    if (ps != FVN_OK) return ps;
     auto kern = shade ? march_kernel<T, I, true> : march_kernel<T, I, false>;
     if (smem > 48 * 1024)
         FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -415,9 +542,10 @@ static fvn_status launch_typed(fvn_ctx* ctx, const MarchArgs& a, bool shade, cud
     return FVN_OK;
 }
 
-fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
-                      const fvn_march_params* mp, const int32_t* ids, const int32_t* count, float* rgbam,
-                      unsigned long long* nsamples, cudaStream_t st, const uint8_t* reject) {
+// Per-view fields of the march arguments: volume size, transfer function,
+// camera basis in voxel units, frame size, step and background.
+static MarchArgs view_args(const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
+                           const fvn_march_params* mp) {
     MarchArgs a{};
     a.vol = vol->data;
     a.nx = vol->nx;
@@ -467,12 +595,19 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
     a.bg0 = mp->bg[0];
     a.bg1 = mp->bg[1];
     a.bg2 = mp->bg[2];
-    a.ids = ids;
-    a.count = count;
     a.tiles_x = (a.W + 7) / 8;
     a.n_dense = a.tiles_x * ((a.H + 3) / 4) * 32;
-    a.rgbam = rgbam;
     a.plane = (long long)a.W * a.H;
+    return a;
+}
+
+fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
+                      const fvn_march_params* mp, const int32_t* ids, const int32_t* count, float* rgbam,
+                      unsigned long long* nsamples, cudaStream_t st, const uint8_t* reject) {
+    MarchArgs a = view_args(vol, tf, cam, mp);
+    a.ids = ids;
+    a.count = count;
+    a.rgbam = rgbam;
     a.nsamples = nsamples;
     a.refill_below = ids ? ctx->march_refill : ctx->march_refill_dense;
     a.ticket = ctx->d_ticket + (ctx->ticket_ring++ & 63);
@@ -508,6 +643,71 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
             return big ? launch_typed<float, long long>(ctx, a, shade, st)
                        : launch_typed<float, int>(ctx, a, shade, st);
     }
+}
+
+
+size_t padded_volume_bytes(const fvn_volume* vol) {
+    const size_t esize = vol->dtype == FVN_U8 ? 1 : (vol->dtype == FVN_F32 ? 4 : 2);
+    return esize * (size_t)(vol->nx + 2 * kPad) * (vol->ny + 2 * kPad) * (vol->nz + 2 * kPad);
+}
+
+fvn_status pad_volume_impl(fvn_ctx* ctx, const fvn_volume* vol, void* pvol, cudaStream_t st) {
+    switch (vol->dtype) {
+        case FVN_U8: return pad_volume<uint8_t>(ctx, vol->data, vol->nx, vol->ny, vol->nz, pvol, st);
+        case FVN_U16: return pad_volume<uint16_t>(ctx, vol->data, vol->nx, vol->ny, vol->nz, pvol, st);
+        case FVN_F16: return pad_volume<__half>(ctx, vol->data, vol->nx, vol->ny, vol->nz, pvol, st);
+        default: return pad_volume<float>(ctx, vol->data, vol->nx, vol->ny, vol->nz, pvol, st);
+    }
+}
+
+fvn_status march_batch_impl(fvn_ctx* ctx, const BatchMarchView* views, int n, const fvn_march_params* mp,
+                            unsigned long long* nsamples, cudaStream_t st) {
+    MarchBatch b{};
+    b.nviews = n;
+    b.nsamples = nsamples;
+    b.refill_below = ctx->march_refill;
+    int tf_total = 0;
+    bool big = false;
+    for (int i = 0; i < n; ++i) {
+        const BatchMarchView& v = views[i];
+        MarchBatchView& bv = b.v[i];
+        bv.a = view_args(v.vol, v.tf, v.cam, mp);
+        bv.a.pvol = v.pvol;
+        bv.a.ids = v.ids;
+        bv.a.count = v.count;
+        bv.a.rgbam = v.rgbam;
+        bv.dtype = v.vol->dtype;
+        const unsigned long long voxels =
+            (unsigned long long)(v.vol->nx + 2 * kPad) * (v.vol->ny + 2 * kPad) * (v.vol->nz + 2 * kPad);
+        big = big || voxels >= (1ull << 31);
+        int k = 0;   // transfer functions are shared by pointer
+        while (k < b.ntfs && !(b.tf[k] == bv.a.tf && b.tf_n[k] == bv.a.ntf)) ++k;
+        if (k == b.ntfs) {
+            b.tf[k] = bv.a.tf;
+            b.tf_n[k] = bv.a.ntf;
+            b.tf_off[k] = tf_total;
+            tf_total += bv.a.ntf;
+            ++b.ntfs;
+        }
+        bv.tf_off = b.tf_off[k];
+    }
+    if (tf_total > 4096)
+        return set_error(ctx, FVN_ERR_ARG, "the batch's transfer functions hold %d entries (at most 4096)", tf_total);
+    b.ticket = ctx->d_ticket + (ctx->ticket_ring++ & 63);
+    FVN_CUDA(ctx, cudaMemsetAsync(b.ticket, 0, sizeof(int), st));
+    const bool shade = mp->shading != 0;
+    auto kern = big ? (shade ? march_batch_kernel<long long, true> : march_batch_kernel<long long, false>)
+                    : (shade ? march_batch_kernel<int, true> : march_batch_kernel<int, false>);
+    const size_t smem = (size_t)tf_total * sizeof(float4);
+    if (smem > 48 * 1024)
+        FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    int per_sm = 0;
+    FVN_CUDA(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 128, smem));
+    if (ctx->march_blocks_per_sm > 0) per_sm = std::min(per_sm, ctx->march_blocks_per_sm);
+    if (per_sm < 1) per_sm = 1;
+    kern<<<ctx->num_sms * per_sm, 128, smem, st>>>(b);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
 }
 
 }  // namespace fvn

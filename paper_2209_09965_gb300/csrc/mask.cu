@@ -43,18 +43,17 @@ __device__ __forceinline__ void morton_decode(uint32_t m, int& tx, int& ty) {
     ty = (int)y;
 }
 
-// Each block covers a 16 x 16 pixel tile (tiles in Z-order of blockIdx.x, so
-// that consecutive blocks are neighbours on screen), each warp an 8 x 4
-// sub-tile: the id list comes out in compact screen regions, which keeps the
-// 32 rays of a march packet close together.
-__global__ void __launch_bounds__(256) mask_compact_kernel(int W, int H, uint32_t key, int f2x, int f2y,
-                                                           int shift, const uint32_t* __restrict__ lut,
-                                                           uint8_t* __restrict__ mask, int32_t* __restrict__ ids,
-                                                           int32_t* __restrict__ count) {
+// Each block covers a 16 x 16 pixel tile (tiles in Z-order of the block
+// number, so that consecutive blocks are neighbours on screen), each warp an
+// 8 x 4 sub-tile: the id list comes out in compact screen regions, which keeps
+// the 32 rays of a march packet close together.
+__device__ __forceinline__ void mask_tile(uint32_t block, int W, int H, uint32_t key, int f2x, int f2y, int shift,
+                                          const uint32_t* __restrict__ lut, uint8_t* __restrict__ mask,
+                                          int32_t* __restrict__ ids, int32_t* __restrict__ count) {
     __shared__ int warp_off[8];
     __shared__ int block_base;
     int tx, ty;
-    morton_decode(blockIdx.x, tx, ty);
+    morton_decode(block, tx, ty);
     if (tx * 16 >= W || ty * 16 >= H) return;   // uniform per block: the Z-order domain is a square
     const int lane = threadIdx.x & 31, wy = threadIdx.x >> 5;
     const int x = tx * 16 + (wy & 1) * 8 + (lane & 7), y = ty * 16 + (wy >> 1) * 4 + (lane >> 3);
@@ -81,6 +80,37 @@ __global__ void __launch_bounds__(256) mask_compact_kernel(int W, int H, uint32_
     }
     __syncthreads();
     if (m) ids[block_base + warp_off[wy] + __popc(bal & ((1u << lane) - 1u))] = y * W + x;
+}
+
+__global__ void __launch_bounds__(256) mask_compact_kernel(int W, int H, uint32_t key, int f2x, int f2y,
+                                                           int shift, const uint32_t* __restrict__ lut,
+                                                           uint8_t* __restrict__ mask, int32_t* __restrict__ ids,
+                                                           int32_t* __restrict__ count) {
+    mask_tile(blockIdx.x, W, H, key, f2x, f2y, shift, lut, mask, ids, count);
+}
+
+// Several views in one launch: view i owns blocks [block0, next view's block0).
+struct MaskView {
+    int W, H;
+    uint32_t key;
+    int f2x, f2y, shift;
+    const uint32_t* lut;
+    uint8_t* mask;
+    int32_t* ids;
+    int32_t* count;
+    uint32_t block0;
+};
+struct MaskBatch {
+    int n;
+    MaskView v[kMaxViews];
+};
+static_assert(sizeof(MaskBatch) <= 4096, "batched mask arguments exceed the 4 KB parameter space");
+
+__global__ void __launch_bounds__(256) mask_compact_batch_kernel(const __grid_constant__ MaskBatch b) {
+    int i = 0;
+    while (i + 1 < b.n && blockIdx.x >= b.v[i + 1].block0) ++i;
+    const MaskView& m = b.v[i];
+    mask_tile(blockIdx.x - m.block0, m.W, m.H, m.key, m.f2x, m.f2y, m.shift, m.lut, m.mask, m.ids, m.count);
 }
 
 static int lut_shift(int W, int H) {
@@ -155,22 +185,63 @@ static fvn_status get_lut(fvn_ctx* ctx, int W, int H, float r0, float s, float p
     return FVN_OK;
 }
 
-fvn_status make_mask_impl(fvn_ctx* ctx, const fvn_foveation* fov, int w, int h, uint8_t* mask, int32_t* ids,
-                          int32_t* count, cudaStream_t st) {
+// Per-view launch parameters: threshold table, focal point in half pixels,
+// hash key and the side of the Z-ordered square of 16 x 16 tiles.
+static fvn_status mask_view(fvn_ctx* ctx, const fvn_foveation* fov, int w, int h, cudaStream_t st, MaskView* mv,
+                            int* side_out) {
     const LutEntry* lut = nullptr;
     fvn_status s = get_lut(ctx, w, h, fov->fovea_radius, fov->falloff_sigma, fov->p_base, st, &lut);
     if (s != FVN_OK) return s;
     int f2x = (int)floor(2.0 * (double)fov->focal_px[0] + 0.5);
     int f2y = (int)floor(2.0 * (double)fov->focal_px[1] + 0.5);
-    f2x = f2x < 0 ? 0 : (f2x > 2 * w ? 2 * w : f2x);
-    f2y = f2y < 0 ? 0 : (f2y > 2 * h ? 2 * h : f2y);
-    const uint32_t key = pcg_hash(fov->frame + pcg_hash(fov->seed));
-    FVN_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(int32_t), st));
-    // Z-order over a power-of-two square of 16 x 16 tiles covering the frame
+    mv->f2x = f2x < 0 ? 0 : (f2x > 2 * w ? 2 * w : f2x);
+    mv->f2y = f2y < 0 ? 0 : (f2y > 2 * h ? 2 * h : f2y);
+    mv->key = pcg_hash(fov->frame + pcg_hash(fov->seed));
+    mv->W = w;
+    mv->H = h;
+    mv->shift = lut->shift;
+    mv->lut = lut->d_lut;
     const int tiles = std::max((w + 15) / 16, (h + 15) / 16);
     int side = 1;
     while (side < tiles) side <<= 1;
-    mask_compact_kernel<<<side * side, 256, 0, st>>>(w, h, key, f2x, f2y, lut->shift, lut->d_lut, mask, ids, count);
+    *side_out = side;
+    return FVN_OK;
+}
+
+fvn_status make_mask_impl(fvn_ctx* ctx, const fvn_foveation* fov, int w, int h, uint8_t* mask, int32_t* ids,
+                          int32_t* count, cudaStream_t st) {
+    MaskView mv{};
+    int side = 0;
+    fvn_status s = mask_view(ctx, fov, w, h, st, &mv, &side);
+    if (s != FVN_OK) return s;
+    FVN_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(int32_t), st));
+    // Z-order over a power-of-two square of 16 x 16 tiles covering the frame
+    mask_compact_kernel<<<side * side, 256, 0, st>>>(w, h, mv.key, mv.f2x, mv.f2y, mv.shift, mv.lut, mask, ids,
+                                                     count);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+fvn_status make_mask_batch_impl(fvn_ctx* ctx, const fvn_foveation* const* fov, const int* w, const int* h,
+                                uint8_t* const* mask, int32_t* const* ids, int32_t* counts, int n,
+                                cudaStream_t st) {
+    if (n < 1 || n > kMaxViews) return set_error(ctx, FVN_ERR_ARG, "%d views (1..%d)", n, kMaxViews);
+    MaskBatch b{};
+    b.n = n;
+    unsigned long long blocks = 0;
+    for (int i = 0; i < n; ++i) {
+        int side = 0;
+        fvn_status s = mask_view(ctx, fov[i], w[i], h[i], st, &b.v[i], &side);
+        if (s != FVN_OK) return s;
+        b.v[i].mask = mask[i];
+        b.v[i].ids = ids[i];
+        b.v[i].count = counts + i;
+        b.v[i].block0 = (uint32_t)blocks;
+        blocks += (unsigned long long)side * side;
+    }
+    if (blocks >= (1ull << 31)) return set_error(ctx, FVN_ERR_ARG, "batch too large for one mask launch");
+    FVN_CUDA(ctx, cudaMemsetAsync(counts, 0, n * sizeof(int32_t), st));
+    mask_compact_batch_kernel<<<(unsigned)blocks, 256, 0, st>>>(b);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }

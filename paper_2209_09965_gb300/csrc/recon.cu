@@ -422,6 +422,11 @@ size_t recon_workspace_bytes(int w, int h) {
     return plan_buffers((w + 3) & ~3, (h + 3) & ~3, nullptr, nullptr);
 }
 
+size_t plan_view(int w, int h, ReconPlan* plan, char* base) {
+    ReconPlan tmp;
+    return plan_buffers((w + 3) & ~3, (h + 3) & ~3, plan ? plan : &tmp, base);
+}
+
 fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
                             cudaStream_t st) {
     if (precision == FVN_PREC_FP8 && !ctx->has_fp8)

@@ -30,8 +30,9 @@ EXPORTS = (
     "fvn_weight_count", "fvn_reconstruct", "fvn_render", "fvn_conv_fwd", "fvn_conv_bwd", "fvn_avgpool2_fwd",
     "fvn_avgpool2_bwd", "fvn_upsample2_fwd", "fvn_upsample2_bwd", "fvn_kp_blend_fwd", "fvn_kp_blend_bwd",
     "fvn_loss_l1grad", "fvn_adam_step", "fvn_reconstruct_noalloc", "fvn_set_option", "fvn_device_status",
-    "fvn_calibrate_fp8", "fvn_render_adaptive", "fvn_march_masked",
+    "fvn_calibrate_fp8", "fvn_render_adaptive", "fvn_march_masked", "fvn_render_batch",
 )
+MAX_VIEWS = 16
 OPT_CONV_KERNEL, OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 1, 2, 3
 OPT_MARCH_REFILL_DENSE, OPT_MARCH_BLOCKS_PER_SM_DENSE = 4, 5
 CONV_TCGEN05, CONV_MMA_SYNC = 0, 1
@@ -68,6 +69,11 @@ class MarchParamsC(ctypes.Structure):
                 ("shading", ctypes.c_int)]
 
 
+class ViewC(ctypes.Structure):
+    _fields_ = [("vol", ctypes.POINTER(Volume)), ("tf", ctypes.POINTER(TF)), ("cam", CameraC),
+                ("fov", FoveationC), ("rgb", ctypes.c_void_p), ("rgbam", ctypes.c_void_p)]
+
+
 def _load():
     if not os.path.exists(LIB_PATH):
         raise ImportError(f"libfvn is not built ({LIB_PATH} missing); run __graft_entry__.build()")
@@ -87,6 +93,7 @@ def _load():
         "fvn_render_adaptive": [P, P, P, P, P, P, I, F, I, P, P, P, P],
         "fvn_device_status": [P],
         "fvn_render": [P, P, P, P, P, P, I, P, P, P],
+        "fvn_render_batch": [P, P, I, P, I, P, P],
         "fvn_conv_fwd": [P, I, P, I, I, I, I, P, P, I, I, I, P, P],
         "fvn_conv_bwd": [P, I, P, I, I, I, I, P, I, I, P, P, P, P, P, P, P],
         "fvn_avgpool2_fwd": [P, I, I, I, P, P],
@@ -271,6 +278,35 @@ class Context:
         f = foveation(fov)
         self._chk(lib.fvn_render(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c), ctypes.byref(f),
                                  ctypes.byref(m), int(precision), _ptr(rgb), _ptr(rgbam_out), _stream(stream)))
+
+    def render_batch(self, views, mp, precision=PREC_FP16, nsamples=None, stream=None):
+        """fvn_render for several views in one pass.  ``views`` is a list of
+        dicts with keys vol, tf (CUDA tensors), cam, fov and rgb (CUDA
+        [3, h, w] float32), optionally rgbam (CUDA [5, h, w] float32)."""
+        n = len(views)
+        arr = (ViewC * max(n, 1))()
+        keep = []   # descriptors referenced by pointer must outlive the call
+        vol_desc, tf_desc = {}, {}
+        for i, v in enumerate(views):
+            vt, tt = v["vol"], v["tf"]
+            kv = (vt.data_ptr(), tuple(vt.shape), vt.dtype)
+            if kv not in vol_desc:
+                vol_desc[kv] = volume(vt)
+            kt = (tt.data_ptr(), tuple(tt.shape))
+            if kt not in tf_desc:
+                tf_desc[kt] = transfer_function(tt)
+            vd, td = vol_desc[kv], tf_desc[kt]
+            keep += [vd, td]
+            arr[i].vol = ctypes.pointer(vd)
+            arr[i].tf = ctypes.pointer(td)
+            arr[i].cam = camera(v["cam"])
+            arr[i].fov = foveation(v["fov"])
+            arr[i].rgb = _ptr(v["rgb"])
+            arr[i].rgbam = _ptr(v.get("rgbam"))
+        m = march_params(mp)
+        ns = None if nsamples is None else _ptr(nsamples, torch.int64)
+        self._chk(lib.fvn_render_batch(self.h, arr, int(n), ctypes.byref(m), int(precision), ns,
+                                       _stream(stream)))
 
 
 # --- training kernels (context-free) -----------------------------------------

@@ -20,6 +20,11 @@ Recipes (all seeded, all deterministic on CPU):
   plus implicit end points (0, rgb_0, 0) and (1, rgb_3, alpha_3).
 * ``orbit_camera``: perspective pinhole on a seeded orbit around the volume.
 * ``focal_point``: uniform in the central 50 % of the screen.
+* ``stereo_pair``: two cameras whose eyes sit baseline / 2 to either side of
+  an orbit eye along the image x axis, looking at the same target.
+* ``multiview_views`` / ``multiview_volumes``: 16 views (4 stereo pairs at
+  2064x2208, 4 at 1280x720, 4 at 3840x2160) over a 512^3 float16 noise volume
+  and a 1024^3 uint8 blob volume, alternating between the two.
 * ``net_weights``: Kaiming-uniform weights, zero biases, in the flat order
   given by ``NET_LAYERS``.
 
@@ -253,6 +258,21 @@ def split_weights(flat: np.ndarray, layers=NET_LAYERS) -> dict:
     return out
 
 
+def stereo_pair(cam: Camera, baseline: float = 0.03) -> tuple:
+    """(left, right): the eye moved by -/+ baseline / 2 (world units, the
+    volume's longest side is 1) along the image x axis, same target."""
+    eye = np.array(cam.eye, np.float64)
+    fwd = np.array(cam.target, np.float64) - eye
+    right = np.cross(fwd, np.array(cam.up, np.float64))
+    right /= np.linalg.norm(right)
+    out = []
+    for sgn in (-0.5, 0.5):
+        e = eye + sgn * baseline * right
+        out.append(Camera(eye=tuple(float(v) for v in e), target=cam.target, up=cam.up, fov_y_deg=cam.fov_y_deg,
+                          width=cam.width, height=cam.height))
+    return tuple(out)
+
+
 # ---------------------------------------------------------------------------
 # named workloads
 # ---------------------------------------------------------------------------
@@ -275,3 +295,40 @@ def foveated_1080p_workload(seed: int = 2, frame: int = 0, n: int = 256, width: 
     cam = orbit_camera(seed, frame, width=width, height=height, radius_factor=(0.85, 1.75))
     fov = Foveation(focal_px=focal_point(seed, frame, width, height), seed=seed, frame=frame)
     return vol, tf, cam, fov, MarchParams(shading=1)
+
+
+# 4 stereo pairs at 2064x2208 (8 views), 4 views at 1280x720, 4 at 3840x2160
+MULTIVIEW_SIZES = ((2064, 2208),) * 8 + ((1280, 720),) * 4 + ((3840, 2160),) * 4
+
+
+def multiview_volumes(device="cpu", n_noise: int = 512, n_blobs: int = 1024, seed: int = 50):
+    """(float16 fractal value noise n_noise^3, uint8 Gaussian blobs n_blobs^3)."""
+    noise = value_noise_volume(n_noise, seed + 1, device=device).to(torch.float16)
+    blobs = blob_volume(n_blobs, seed + 2, device=device)
+    blobs = torch.round(blobs.mul_(255.0)).to(torch.uint8)
+    return noise, blobs
+
+
+def multiview_transfer_functions(seed: int = 50):
+    """Transfer functions of the noise and the blob volume."""
+    return transfer_function(seed + 1000, alpha_max=0.08), transfer_function(seed + 2000, alpha_max=0.3)
+
+
+def multiview_views(seed: int = 50, frame: int = 0, sizes=MULTIVIEW_SIZES, nframes: int = 64):
+    """The views of one batched frame: list of dicts with w, h, volume (0 =
+    noise, 1 = blobs), cam and fov.  Views 0-7 are four stereo pairs (pair k
+    renders volume k % 2); the other views alternate between the volumes."""
+    views = []
+    i = 0
+    while i < len(sizes):
+        w, h = sizes[i]
+        k = len(views)
+        paired = i + 1 < len(sizes) and sizes[i + 1] == sizes[i] and i < 8
+        cam = orbit_camera(seed + k, frame, nframes=nframes, width=w, height=h, radius_factor=(0.85, 1.75))
+        cams = stereo_pair(cam) if paired else (cam,)
+        vol = (k // 2) % 2 if paired else k % 2
+        for c in cams:
+            fov = Foveation(focal_px=focal_point(seed + k, frame, w, h), seed=seed + k, frame=frame)
+            views.append({"w": w, "h": h, "volume": vol, "cam": c, "fov": fov})
+        i += len(cams)
+    return views

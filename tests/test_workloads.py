@@ -1,5 +1,6 @@
 """The seeded input generators: shapes, ranges, determinism.  No GPU."""
 import numpy as np
+import torch
 
 from paper_2209_09965_gb300 import workloads as wl
 
@@ -37,3 +38,34 @@ def test_cameras_and_focal_points():
     assert abs(r - 1.8 * np.sqrt(3)) < 1e-9 and cam.width == 1920
     fx, fy = wl.focal_point(2, 5, 1920, 1080)
     assert 480 <= fx <= 1440 and 270 <= fy <= 810
+
+
+def test_stereo_pair_geometry():
+    cam = wl.orbit_camera(4, 3, width=320, height=200)
+    left, right = wl.stereo_pair(cam, baseline=0.05)
+    el, er, e = (np.array(c.eye) for c in (left, right, cam))
+    assert abs(np.linalg.norm(er - el) - 0.05) < 1e-12
+    assert np.allclose((el + er) / 2, e, atol=1e-12)            # centred on the orbit eye
+    fwd = np.array(cam.target) - e
+    assert abs(np.dot(er - el, fwd)) < 1e-12                     # baseline across the view direction
+    assert abs(np.dot(er - el, np.array(cam.up))) < 1e-12
+    assert left.target == cam.target and right.width == 320
+
+
+def test_multiview_views_layout():
+    views = wl.multiview_views(seed=50)
+    sizes = [(v["w"], v["h"]) for v in views]
+    assert sizes == list(wl.MULTIVIEW_SIZES) and len(views) == 16
+    for k in range(4):                                           # four stereo pairs
+        a, b = views[2 * k], views[2 * k + 1]
+        assert a["volume"] == b["volume"] == k % 2
+        assert a["fov"].focal_px == b["fov"].focal_px and a["fov"].seed == b["fov"].seed
+        assert abs(np.linalg.norm(np.array(a["cam"].eye) - np.array(b["cam"].eye)) - 0.03) < 1e-12
+    assert {v["volume"] for v in views[8:]} == {0, 1}
+    assert views == wl.multiview_views(seed=50)                  # seeded
+
+
+def test_multiview_volumes_small():
+    noise, blobs = wl.multiview_volumes(n_noise=16, n_blobs=32, seed=50)
+    assert noise.dtype == torch.float16 and noise.shape == (16, 16, 16)
+    assert blobs.dtype == torch.uint8 and blobs.shape == (32, 32, 32) and int(blobs.max()) > 30
