@@ -100,7 +100,11 @@ fvn_status fvn_create(fvn_ctx** out);
 /* Free a context and everything it owns.  Synchronises the device. */
 fvn_status fvn_destroy(fvn_ctx* ctx);
 
-/* Tuning options (fvn_set_option); the defaults are what the autotuner picked.
+/* Tuning options (fvn_set_option).  Defaults: tcgen05 convolutions, whole
+ * 32-ray packets, no cooperative finish, as many march CTAs as fit; with these
+ * the march is deterministic (each ray's arithmetic is independent of which
+ * rays share its warp).  Every setting computes the same result (the
+ * cooperative finish up to FP32 rounding order); the autotuner times them.
  *  FVN_OPT_CONV_KERNEL: 0 = tcgen05 tensor-core convolutions (TMEM
  *      accumulators), 1 = mma.sync convolutions.
  *  FVN_OPT_MARCH_REFILL: a sparse-march warp refills idle lanes with new
@@ -108,14 +112,20 @@ fvn_status fvn_destroy(fvn_ctx* ctx);
  *      32-ray packets).
  *  FVN_OPT_MARCH_BLOCKS_PER_SM: persistent sparse-march CTAs per SM (0 = as
  *      many as fit).
- *  FVN_OPT_MARCH_REFILL_DENSE, FVN_OPT_MARCH_BLOCKS_PER_SM_DENSE: the same
- *      for the dense march (ids == NULL). */
+ *  FVN_OPT_MARCH_COOP: once at most this many lanes (0..32) of a sparse-march
+ *      warp still hold rays, the warp marches each of them with all 32 lanes
+ *      (32 samples per step, composited by a product scan of the
+ *      transmittances; the same result up to FP32 rounding order); 0 = never.
+ *  FVN_OPT_MARCH_REFILL_DENSE, FVN_OPT_MARCH_BLOCKS_PER_SM_DENSE,
+ *  FVN_OPT_MARCH_COOP_DENSE: the same for the dense march (ids == NULL). */
 enum {
     FVN_OPT_CONV_KERNEL = 1,
     FVN_OPT_MARCH_REFILL = 2,
     FVN_OPT_MARCH_BLOCKS_PER_SM = 3,
     FVN_OPT_MARCH_REFILL_DENSE = 4,
-    FVN_OPT_MARCH_BLOCKS_PER_SM_DENSE = 5
+    FVN_OPT_MARCH_BLOCKS_PER_SM_DENSE = 5,
+    FVN_OPT_MARCH_COOP = 6,
+    FVN_OPT_MARCH_COOP_DENSE = 7
 };
 fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value);
 

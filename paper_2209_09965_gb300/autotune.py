@@ -3,14 +3,15 @@
 Times, with CUDA events on the current stream, the candidate settings of
 
 * the march: the lane-refill threshold of the persistent kernel (how many
-  lanes of a warp must still be busy before idle lanes take new rays) and the
-  number of persistent CTAs per SM;
+  lanes of a warp must still be busy before idle lanes take new rays), the
+  cooperative-finish threshold (how few rays a warp must have left before it
+  marches them with all 32 lanes) and the number of persistent CTAs per SM;
 * the reconstruction convolutions: the tcgen05 (TMEM-accumulator) kernels or
   the mma.sync kernels;
 
 on the caller's own frame, and installs the fastest in the context with
-fvn_set_option.  Every candidate computes the same result; only the time
-differs.
+fvn_set_option.  Every candidate computes the same result (the cooperative
+finish up to FP32 rounding order); only the time differs.
 """
 from __future__ import annotations
 
@@ -35,21 +36,26 @@ def _time(fn, reps=3):
 
 
 def tune_march(ctx: fvn.Context, vol, tf, cam, mp, rgbam, ids=None, count=None,
-               refills=(1, 8, 16, 24, 28), blocks=(0, 4, 6)):
-    """Pick (refill threshold, CTAs per SM) for the march of this frame: the
-    sparse march when ids are given, the dense march otherwise."""
-    o_refill = fvn.OPT_MARCH_REFILL if ids is not None else fvn.OPT_MARCH_REFILL_DENSE
-    o_blocks = fvn.OPT_MARCH_BLOCKS_PER_SM if ids is not None else fvn.OPT_MARCH_BLOCKS_PER_SM_DENSE
+               refills=(1, 8, 16, 24), blocks=(0, 4), coops=(0, 2, 4, 8)):
+    """Pick (refill threshold, cooperative-finish threshold, CTAs per SM) for
+    the march of this frame: the sparse march when ids are given, the dense
+    march otherwise."""
+    sparse = ids is not None
+    o_refill = fvn.OPT_MARCH_REFILL if sparse else fvn.OPT_MARCH_REFILL_DENSE
+    o_blocks = fvn.OPT_MARCH_BLOCKS_PER_SM if sparse else fvn.OPT_MARCH_BLOCKS_PER_SM_DENSE
+    o_coop = fvn.OPT_MARCH_COOP if sparse else fvn.OPT_MARCH_COOP_DENSE
     results = {}
-    for r, b in itertools.product(refills, blocks):
+    for r, c, b in itertools.product(refills, coops, blocks):
         ctx.set_option(o_refill, r)
+        ctx.set_option(o_coop, c)
         ctx.set_option(o_blocks, b)
-        results[(r, b)] = _time(lambda: ctx.march(vol, tf, cam, mp, rgbam, ids=ids, count=count))
+        results[(r, c, b)] = _time(lambda: ctx.march(vol, tf, cam, mp, rgbam, ids=ids, count=count))
     best = min(results, key=results.get)
     ctx.set_option(o_refill, best[0])
-    ctx.set_option(o_blocks, best[1])
-    return {"refill": best[0], "blocks_per_sm": best[1], "ms": results[best],
-            "candidates": {f"{k[0]}/{k[1]}": round(v, 4) for k, v in results.items()}}
+    ctx.set_option(o_coop, best[1])
+    ctx.set_option(o_blocks, best[2])
+    return {"refill": best[0], "coop": best[1], "blocks_per_sm": best[2], "ms": results[best],
+            "candidates": {f"{k[0]}/{k[1]}/{k[2]}": round(v, 4) for k, v in results.items()}}
 
 
 def tune_conv(ctx: fvn.Context, rgbam, w, h, rgb):

@@ -123,10 +123,12 @@ struct fvn_ctx {
     float fp8_amax[fvn::FP8_NT] = {};
     float fp8_inv_scale[fvn::FP8_NT] = {};
     float* d_amax = nullptr;          // device amax accumulators [FP8_NT]
-    int march_refill = 24;            // sparse march: refill idle lanes once fewer than this many are busy
+    int march_refill = 1;             // sparse march: refill idle lanes once fewer than this many are busy
     int march_blocks_per_sm = 0;      // sparse march CTAs per SM, 0 = occupancy limit
     int march_refill_dense = 1;       // dense march: 1 = whole 32-ray packets only
     int march_blocks_per_sm_dense = 0;
+    int march_coop = 0;               // sparse march: finish a warp's rays with the whole warp once at most this many are left
+    int march_coop_dense = 0;
     void* pad_buf = nullptr;          // padded copy of the volume read by the march
     size_t pad_bytes = 0;
     float* d_act_scale = nullptr;     // FP8 per-layer activation scales

@@ -145,6 +145,14 @@ extern "C" fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value) {
             FVN_CHECK_ARG(ctx, value >= 0 && value <= 16, "blocks per SM must be in [0, 16]");
             ctx->march_blocks_per_sm_dense = value;
             return FVN_OK;
+        case FVN_OPT_MARCH_COOP:
+            FVN_CHECK_ARG(ctx, value >= 0 && value <= 32, "cooperative-finish threshold must be in [0, 32]");
+            ctx->march_coop = value;
+            return FVN_OK;
+        case FVN_OPT_MARCH_COOP_DENSE:
+            FVN_CHECK_ARG(ctx, value >= 0 && value <= 32, "cooperative-finish threshold must be in [0, 32]");
+            ctx->march_coop_dense = value;
+            return FVN_OK;
         default:
             return set_error(ctx, FVN_ERR_ARG, "unknown option %d", option);
     }

@@ -58,6 +58,7 @@ struct MarchArgs {
     unsigned long long* nsamples;
     int* ticket;
     int refill_below;                 // refill idle lanes once fewer than this many are busy
+    int coop_below;                   // finish the rays cooperatively once at most this many are busy (0 = never)
     const uint8_t* reject;            // dense numbering: skip pixels whose mask byte is 0
 };
 
@@ -181,16 +182,23 @@ struct Stencil {
     float tx, ty, tz;
 };
 
-template <typename T, typename I, bool SHADE>
-__device__ __forceinline__ void load_stencil(const MarchArgs& a, const T* __restrict__ vol, I sy, I sz, float ux,
-                                             float uy, float uz, Stencil& S) {
+// Cell of a sample position (voxel-centre coordinates): fractions into S
+// and the offset of the cell's first voxel in the padded copy.
+template <typename I>
+__device__ __forceinline__ I stencil_cell(const MarchArgs& a, I sy, I sz, float ux, float uy, float uz, Stencil& S) {
     int i = floor_frac(ux, S.tx), j = floor_frac(uy, S.ty), k = floor_frac(uz, S.tz);
     // samples lie in the box, so i is in [-1, n - 1]; the clamp only guards
     // against rounding and keeps every stencil index inside the padded copy
     i = min(max(i, -1), a.nx - 1);
     j = min(max(j, -1), a.ny - 1);
     k = min(max(k, -1), a.nz - 1);
-    const T* b = vol + ((I)(k + kPad) * sz + (I)(j + kPad) * sy + (i + kPad));
+    return (I)(k + kPad) * sz + (I)(j + kPad) * sy + (i + kPad);
+}
+
+// The voxels of the stencil whose cell starts at vol + b.
+template <typename T, typename I, bool SHADE>
+__device__ __forceinline__ void stencil_fetch(const T* __restrict__ vol, I b0, I sy, I sz, Stencil& S) {
+    const T* b = vol + b0;
 #pragma unroll
     for (int z = 0; z < 2; ++z)
 #pragma unroll
@@ -221,11 +229,20 @@ __device__ __forceinline__ void load_stencil(const MarchArgs& a, const T* __rest
     }
 }
 
-// Classify, shade and composite one loaded sample; returns true once the ray
-// is opaque enough to stop.
+// The 32 voxels one shaded sample reads, loaded at once so a sample costs one
+// round trip to the memory system.
+template <typename T, typename I, bool SHADE>
+__device__ __forceinline__ void load_stencil(const MarchArgs& a, const T* __restrict__ vol, I sy, I sz, float ux,
+                                             float uy, float uz, Stencil& S) {
+    const I b = stencil_cell<I>(a, sy, sz, ux, uy, uz, S);
+    stencil_fetch<T, I, SHADE>(vol, b, sy, sz, S);
+}
+
+// Classify and shade one loaded sample: returns its opacity al and, when
+// al > 0, its (clamped) shaded colour.
 template <bool SHADE>
-__device__ __forceinline__ bool composite_sample(const MarchArgs& a, const float4* s_tf, float tfmax,
-                                                 const Stencil& S, Ray& s) {
+__device__ __forceinline__ float shade_sample(const MarchArgs& a, const float4* s_tf, float tfmax, const Stencil& S,
+                                              float dx, float dy, float dz, float& cr, float& cg, float& cb) {
     float rows[2][2];
 #pragma unroll
     for (int z = 0; z < 2; ++z)
@@ -246,9 +263,9 @@ __device__ __forceinline__ bool composite_sample(const MarchArgs& a, const float
     const float4 c0 = s_tf[ti], c1 = s_tf[ti + 1];
     const float al = fmaf(fr, c1.w - c0.w, c0.w);
     if (al > 0.0f) {
-        float cr = fmaf(fr, c1.x - c0.x, c0.x);
-        float cg = fmaf(fr, c1.y - c0.y, c0.y);
-        float cb = fmaf(fr, c1.z - c0.z, c0.z);
+        cr = fmaf(fr, c1.x - c0.x, c0.x);
+        cg = fmaf(fr, c1.y - c0.y, c0.y);
+        cb = fmaf(fr, c1.z - c0.z, c0.z);
         if (SHADE) {
             // central differences at +-1 voxel of the trilinear field
             float d[2][2];
@@ -272,7 +289,7 @@ __device__ __forceinline__ bool composite_sample(const MarchArgs& a, const float
                                           lerpf(rows[1][1], zp[1], S.tz) - lerpf(zm[1], rows[0][1], S.tz), S.ty);
             const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
             if (g2 >= 1e-12f) {   // |g| >= 1e-6: shade, otherwise keep the TF colour
-                const float ndl = fabsf(fmaf(gx, s.dx, fmaf(gy, s.dy, gz * s.dz))) * rsqrtf(g2);
+                const float ndl = fabsf(fmaf(gx, dx, fmaf(gy, dy, gz * dz))) * rsqrtf(g2);
                 float sp = ndl * ndl;   // ndl^32 by five squarings
                 sp *= sp;
                 sp *= sp;
@@ -285,6 +302,18 @@ __device__ __forceinline__ bool composite_sample(const MarchArgs& a, const float
                 cb = __saturatef(fmaf(cb, diff, spec));
             }
         }
+    }
+    return al;
+}
+
+// Classify, shade and composite one loaded sample; returns true once the ray
+// is opaque enough to stop.
+template <bool SHADE>
+__device__ __forceinline__ bool composite_sample(const MarchArgs& a, const float4* s_tf, float tfmax,
+                                                 const Stencil& S, Ray& s) {
+    float cr, cg, cb;
+    const float al = shade_sample<SHADE>(a, s_tf, tfmax, S, s.dx, s.dy, s.dz, cr, cg, cb);
+    if (al > 0.0f) {
         const float w = (1.0f - s.A) * al;
         s.C0 = fmaf(w, cr, s.C0);
         s.C1 = fmaf(w, cg, s.C1);
@@ -313,6 +342,80 @@ __device__ __forceinline__ bool ray_step(const MarchArgs& a, const T* __restrict
     if (!has1) return true;
     s.kf += 1.0f;
     return composite_sample<SHADE>(a, s_tf, tfmax, S1, s);
+}
+
+// Cooperative march of one ray by the whole warp, for the last few rays of a
+// warp (which otherwise walk their long latency chains with the other lanes
+// idle).  In each chunk lane j takes sample kf + j; the chunk is composited
+// front to back as a product scan of the transmittances (1 - A) over the
+// lanes -- the same recurrence as the sequential march, evaluated in a
+// different order -- and the ray stops at the first sample whose opacity
+// reaches term_alpha, or where it leaves the box.  `r` is the same on every
+// lane on entry and on return.
+template <typename T, typename I, bool SHADE>
+__device__ __forceinline__ void coop_ray(const MarchArgs& a, const T* __restrict__ vol, const float4* s_tf, I sy,
+                                         I sz, float ux0, float uy0, float uz0, float tfmax, Ray& r) {
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    for (;;) {
+        const float t = fmaf(r.kf + (float)lane, a.dt, r.tnear);
+        const bool valid = t < r.tfar;          // a prefix of the lanes
+        const unsigned vb = __ballot_sync(FULL, valid);
+        if (vb == 0) return;
+        float cr = 0.f, cg = 0.f, cb = 0.f, al = 0.f;
+        if (valid) {
+            Stencil S;
+            load_stencil<T, I, SHADE>(a, vol, sy, sz, fmaf(t, r.dx, ux0), fmaf(t, r.dy, uy0), fmaf(t, r.dz, uz0),
+                                      S);
+            al = shade_sample<SHADE>(a, s_tf, tfmax, S, r.dx, r.dy, r.dz, cr, cg, cb);
+            if (!(al > 0.0f)) al = 0.0f;
+        }
+        // incl = prod_{i <= j} (1 - al_i), excl = prod_{i < j} (1 - al_i)
+        float incl = 1.0f - al;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const float v = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl *= v;
+        }
+        float excl = __shfl_up_sync(FULL, incl, 1);
+        if (lane == 0) excl = 1.0f;
+        const float tin = 1.0f - r.A;
+        const float a_after = 1.0f - tin * incl;
+        const unsigned stop = __ballot_sync(FULL, valid && a_after >= a.term);
+        const int last = stop ? __ffs(stop) - 1 : 31 - __clz(vb);
+        const float w = (lane <= last && al > 0.0f) ? tin * excl * al : 0.0f;
+        float c0 = w * cr, c1 = w * cg, c2 = w * cb;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            c0 += __shfl_xor_sync(FULL, c0, o);
+            c1 += __shfl_xor_sync(FULL, c1, o);
+            c2 += __shfl_xor_sync(FULL, c2, o);
+        }
+        r.C0 += c0;
+        r.C1 += c1;
+        r.C2 += c2;
+        r.A = __shfl_sync(FULL, a_after, last);
+        r.kf += (float)(last + 1);
+        if (stop || last < 31) return;
+    }
+}
+
+// The ray of lane `src` on every lane.
+__device__ __forceinline__ Ray shfl_ray(const Ray& s, int src) {
+    const unsigned FULL = 0xffffffffu;
+    Ray r;
+    r.pix = __shfl_sync(FULL, s.pix, src);
+    r.dx = __shfl_sync(FULL, s.dx, src);
+    r.dy = __shfl_sync(FULL, s.dy, src);
+    r.dz = __shfl_sync(FULL, s.dz, src);
+    r.tnear = __shfl_sync(FULL, s.tnear, src);
+    r.tfar = __shfl_sync(FULL, s.tfar, src);
+    r.kf = __shfl_sync(FULL, s.kf, src);
+    r.C0 = __shfl_sync(FULL, s.C0, src);
+    r.C1 = __shfl_sync(FULL, s.C1, src);
+    r.C2 = __shfl_sync(FULL, s.C2, src);
+    r.A = __shfl_sync(FULL, s.A, src);
+    return r;
 }
 
 // Persistent kernel with per-lane ray refill: a lane whose ray finishes goes
@@ -363,6 +466,22 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
             continue;
         }
         while (busy != 0 && (exhausted || __popc(busy) >= a.refill_below)) {
+            if (__popc(busy) <= a.coop_below) {
+                // the warp's last few rays: march each with all 32 lanes
+                do {
+                    const int src = __ffs(busy) - 1;
+                    Ray r = shfl_ray(s, src);
+                    coop_ray<T, I, SHADE>(a, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+                    if (lane == src) {
+                        s = r;
+                        my_samples += (unsigned long long)s.kf;
+                        finish_ray(a, s);
+                        s.pix = -1;
+                    }
+                    busy &= busy - 1u;
+                } while (busy != 0);
+                break;
+            }
             if (s.pix >= 0 && ray_step<T, I, SHADE>(a, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s)) {
                 my_samples += (unsigned long long)s.kf;
                 finish_ray(a, s);
@@ -400,6 +519,7 @@ struct MarchBatch {
     unsigned long long* nsamples;
     int* ticket;
     int refill_below;
+    int coop_below;
     MarchBatchView v[kMaxViews];
 };
 static_assert(sizeof(MarchBatch) <= 4096, "batched march arguments exceed the 4 KB parameter space");
@@ -424,6 +544,30 @@ __device__ __forceinline__ bool batch_step(const MarchBatchView& bv, const float
         default:
             return ray_step<float, I, SHADE>(a, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
                                              tfmax, s);
+    }
+}
+
+template <typename I, bool SHADE>
+__device__ __forceinline__ void batch_coop(const MarchBatchView& bv, const float4* s_tf, Ray& r) {
+    const MarchArgs& a = bv.a;
+    const I sy = (I)(a.nx + 2 * kPad), sz = sy * (I)(a.ny + 2 * kPad);
+    const float ux0 = a.ox - 0.5f, uy0 = a.oy - 0.5f, uz0 = a.oz - 0.5f;
+    const float tfmax = (float)(a.ntf - 1);
+    const float4* tf = s_tf + bv.tf_off;
+    switch (bv.dtype) {
+        case FVN_U8:
+            coop_ray<uint8_t, I, SHADE>(a, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+            break;
+        case FVN_U16:
+            coop_ray<uint16_t, I, SHADE>(a, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax,
+                                         r);
+            break;
+        case FVN_F16:
+            coop_ray<__half, I, SHADE>(a, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+            break;
+        default:
+            coop_ray<float, I, SHADE>(a, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+            break;
     }
 }
 
@@ -481,6 +625,22 @@ __global__ void __launch_bounds__(128) march_batch_kernel(const __grid_constant_
             continue;
         }
         while (busy != 0 && (exhausted || __popc(busy) >= b.refill_below)) {
+            if (__popc(busy) <= b.coop_below) {
+                do {
+                    const int src = __ffs(busy) - 1;
+                    Ray r = shfl_ray(s, src);
+                    const int v = __shfl_sync(FULL, view, src);
+                    batch_coop<I, SHADE>(b.v[v], s_tf, r);
+                    if (lane == src) {
+                        s = r;
+                        my_samples += (unsigned long long)s.kf;
+                        finish_ray(b.v[v].a, s);
+                        s.pix = -1;
+                    }
+                    busy &= busy - 1u;
+                } while (busy != 0);
+                break;
+            }
             if (s.pix >= 0 && batch_step<I, SHADE>(b.v[view], s_tf, s)) {
                 my_samples += (unsigned long long)s.kf;
                 finish_ray(b.v[view].a, s);
@@ -610,6 +770,7 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
     a.rgbam = rgbam;
     a.nsamples = nsamples;
     a.refill_below = ids ? ctx->march_refill : ctx->march_refill_dense;
+    a.coop_below = ids ? ctx->march_coop : ctx->march_coop_dense;
     a.ticket = ctx->d_ticket + (ctx->ticket_ring++ & 63);
     a.reject = ids ? nullptr : reject;
     if (ids || reject) FVN_CUDA(ctx, cudaMemsetAsync(rgbam, 0, 5 * sizeof(float) * (size_t)a.plane, st));
@@ -666,6 +827,7 @@ fvn_status march_batch_impl(fvn_ctx* ctx, const BatchMarchView* views, int n, co
     b.nviews = n;
     b.nsamples = nsamples;
     b.refill_below = ctx->march_refill;
+    b.coop_below = ctx->march_coop;
     int tf_total = 0;
     bool big = false;
     for (int i = 0; i < n; ++i) {

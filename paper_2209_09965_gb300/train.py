@@ -7,7 +7,7 @@ from seeded procedural volumes (the paper trains on renders of its CT and
 simulation datasets, "Dataset" / "Training" sections).  Loss: L1 plus L1 of
 the image gradients (the paper's perceptual and temporal terms, Eq. 4-7,
 need VGG19 weights and optical flow that are not available).  Optimiser:
-Adam, lr 1e-3.
+Adam, lr 1e-3 with cosine decay to ``lr_final``.
 
 Every forward and backward step runs in the library's CUDA kernels, called
 through ``torch.autograd.Function`` shims; parameter gradients are written by
@@ -15,7 +15,12 @@ the backward kernels straight into one flat gradient buffer on which the
 Adam kernel steps.  Assembling a batch (choosing crop windows, slicing the
 rendered frame) uses plain tensor indexing.
 
-    python -m paper_2209_09965_gb300.train --steps 3000 --out weights/fvn_16_32_64.npy
+The shipped weights were made with
+
+    python -m paper_2209_09965_gb300.train --steps 30000 --lr-final 1e-5 --log-every 1000 \
+        --out paper_2209_09965_gb300/weights/fvn_16_32_64.npy
+    python -m paper_2209_09965_gb300.train --steps 8000 --direct-only \
+        --out paper_2209_09965_gb300/weights/fvn_direct_only.npy
 """
 from __future__ import annotations
 
@@ -276,10 +281,13 @@ def main():
     ap.add_argument("--seed", type=int, default=100)
     ap.add_argument("--nvol", type=int, default=64)
     ap.add_argument("--vol-n", type=int, default=512)
+    ap.add_argument("--lr-final", type=float, default=1e-4)
+    ap.add_argument("--log-every", type=int, default=100)
     ap.add_argument("--direct-only", action="store_true")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
-    train(a.steps, a.batch, a.lr, a.seed, a.nvol, a.vol_n, a.out, a.direct_only)
+    train(a.steps, a.batch, a.lr, a.seed, a.nvol, a.vol_n, a.out, a.direct_only, log_every=a.log_every,
+          lr_final=a.lr_final)
 
 
 if __name__ == "__main__":

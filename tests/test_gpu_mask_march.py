@@ -195,3 +195,44 @@ def test_march_masked_equals_sparse_march(ctx):
     ctx.march_masked(v, t, cam, mp, mask, b, nsamples=nb)
     torch.cuda.synchronize()
     assert torch.equal(a, b) and int(na.item()) == int(nb.item())
+
+
+@pytest.mark.parametrize("coop", [1, 4, 32])
+def test_march_cooperative_finish_small(ctx, fvn, coop):
+    """Warp-cooperative finishing of the last rays (32 samples per step,
+    product-scan compositing) matches the oracle like the sequential march;
+    coop = 32 marches every ray cooperatively."""
+    try:
+        ctx.set_option(fvn.OPT_MARCH_COOP_DENSE, coop)
+        ctx.set_option(fvn.OPT_MARCH_COOP, coop)
+        for shading, frame in ((0, 0), (1, 21)):
+            vol, tf, cam, mp = wl.dense_small_workload(seed=1, frame=frame)
+            mp = wl.MarchParams(shading=shading)
+            out, ns = run_march(ctx, vol, tf, cam, mp)
+            _, namb = march_parity(vol, tf, cam, mp, out)
+            _, _, ns_ref = om.march(vol, tf, cam, mp)
+            assert abs(ns - ns_ref) <= 2 * max(1, namb)
+        # no termination (thin TF, opacity stays far below 1): every ray marches to the far side
+        vol, _, cam, _ = wl.dense_small_workload(seed=1)
+        tf = wl.transfer_function(5, alpha_max=0.02)
+        mp = wl.MarchParams(0.5, 1.0, (0.1, 0.2, 0.3), 1)
+        out, _ = run_march(ctx, vol, tf, cam, mp)
+        march_parity(vol, tf, cam, mp, out)
+    finally:
+        ctx.set_option(fvn.OPT_MARCH_COOP_DENSE, 0)
+        ctx.set_option(fvn.OPT_MARCH_COOP, 0)
+
+
+@pytest.mark.parametrize("coop", [4, 32])
+def test_march_cooperative_finish_sparse_1080p(ctx, fvn, coop):
+    vol, tf, cam, fov, mp = wl.foveated_1080p_workload(seed=2, frame=9)
+    _, ids, _ = omask.make_mask(1920, 1080, fov.focal_px, seed=fov.seed, frame=fov.frame)
+    try:
+        ctx.set_option(fvn.OPT_MARCH_COOP, coop)
+        out, ns = run_march(ctx, vol, tf, cam, mp, ids=ids)
+    finally:
+        ctx.set_option(fvn.OPT_MARCH_COOP, 0)
+    sample = np.sort(np.random.default_rng(2).choice(ids, 40000, replace=False)).astype(np.int32)
+    march_parity(vol, tf, cam, mp, out, ids=sample, max_amb_frac=0.05)
+    seq, ns_seq = run_march(ctx, vol, tf, cam, mp, ids=ids)
+    assert abs(ns - ns_seq) <= 0.001 * ns_seq
