@@ -54,9 +54,12 @@ struct ReconWorkspace {
     void* base = nullptr;
 };
 
-// Activation buffers of one reconstruction (FP16 NHWC, per level).
+// Activation buffers of one reconstruction (FP16 NHWC, per level).  u1 and
+// u0 hold the up-sampled inputs of the two decoder convolutions; they alias
+// buffers that are dead by then (u1 = e0a, u0 spans p0 .. d1a).
 struct ReconPlan {
     __half *e0a, *e0, *p0, *e1a, *e1, *p1, *ba, *bt, *d1a, *d1, *d0a, *d0;
+    __half *u1, *u0;
 };
 
 // One view of a batched reconstruction: its activation buffers, sparse

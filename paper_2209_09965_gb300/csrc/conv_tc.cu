@@ -15,7 +15,8 @@
 // (LBO = one channel plane, SBO = 128 B).  Weights stay resident in shared
 // memory in the same layout ([tap][cin chunk][cout][16 B]).  Epilogue: each
 // thread owns one pixel (one TMEM lane): scale, bias, ReLU, FP16 / FP8,
-// 16-byte NHWC stores; fused 2x2 average pooling; for the last decoder conv a
+// 16-byte stores into chunk-planar tensors ([C / chunk][H][W][16 B], one
+// plane per 16-byte channel chunk); fused 2x2 average pooling; for the last decoder conv a
 // second MMA applies the 1x1 head (16 -> 29, padded to 32) from the
 // activations written back to shared memory, and the thread finishes its
 // pixel with the softmax 5x5 kernel prediction over the sparse samples
@@ -38,7 +39,7 @@ namespace fvn {
 
 namespace {
 
-enum { TIN_NHWC = 0, TIN_RGBAM = 1, TIN_UPCAT = 2 };
+enum { TIN_ACT = 0, TIN_RGBAM = 1, TIN_UPCAT = 2 };
 enum { TEPI_STORE = 0, TEPI_POOL = 1, TEPI_HEADKP = 2 };
 
 constexpr int TW = 128;            // pixels per tile row = MMA M
@@ -139,7 +140,7 @@ struct TcLayout {
 // One image of a batched launch: its tensors and sizes, and the first tile
 // of the launch's tile range that belongs to it.
 struct TcImg {
-    const void* in;          // NHWC input, or the coarse level for up-sampling
+    const void* in;          // chunk-planar input, or the coarse level for up-sampling
     const void* skip;        // skip tensor (up-sampling layers)
     const float* rgbam;      // sparse frame [5][H0][W0] (first layer, KP)
     void* out;               // [Hl][Wl][COUT]
@@ -171,22 +172,23 @@ __device__ __forceinline__ int find_img(const TcArgs& a, int tile) {
     return i;
 }
 
-// Store COUT channel values of one pixel (FP16, or FP8 after scaling by q).
+// Store COUT channel values of one pixel (FP16, or FP8 after scaling by q)
+// into a chunk-planar tensor: plane j holds channels [j CPC, (j + 1) CPC) of
+// every pixel as 16-byte vectors ([C / CPC][H][W][16 B]; plane = H W).
 template <int COUT, bool F8>
-__device__ __forceinline__ void store_pixel(void* base, long long pix, const float* v, float q) {
+__device__ __forceinline__ void store_pixel(void* base, long long plane, long long pix, const float* v, float q) {
+    uint4* o = static_cast<uint4*>(base) + pix;
     if (F8) {
-        uint4* o = reinterpret_cast<uint4*>(static_cast<uint8_t*>(base) + pix * COUT);
 #pragma unroll
         for (int c = 0; c < COUT; c += 16) {
             float s[16];
 #pragma unroll
             for (int j = 0; j < 16; ++j) s[j] = v[c + j] * q;
-            o[c / 16] = pack16q(s);
+            o[(c / 16) * plane] = pack16q(s);
         }
     } else {
-        uint4* o = reinterpret_cast<uint4*>(static_cast<__half*>(base) + pix * COUT);
 #pragma unroll
-        for (int c = 0; c < COUT; c += 8) o[c / 8] = pack8h(v + c);
+        for (int c = 0; c < COUT; c += 8) o[(c / 8) * plane] = pack8h(v + c);
     }
 }
 
@@ -280,8 +282,9 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
                 unsigned char* dst = sH + ((c * HY + hy) * HXW + hx) * 16;
                 if (c < CHG && gy >= 0 && gx >= 0 && gy < im.Hl && gx < im.Wl) {
                     const long long pix = (long long)gy * im.Wl + gx;
-                    if (MODE == TIN_NHWC) cp16(tc::smem_addr(dst), gin + (pix * CG + c * CPC) * EB);
-                    else cp16(tc::smem_addr(dst), gskip + (pix * (CG - CUP) + (c - CS0) * CPC) * EB);
+                    const long long plane = (long long)im.Hl * im.Wl;
+                    if (MODE == TIN_ACT) cp16(tc::smem_addr(dst), gin + (c * plane + pix) * 16);
+                    else cp16(tc::smem_addr(dst), gskip + ((c - CS0) * plane + pix) * 16);
                 } else {
                     *reinterpret_cast<uint4*>(dst) = make_uint4(0, 0, 0, 0);
                 }
@@ -295,7 +298,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
                     const int r = rem / L::CC, q = rem - r * L::CC;
                     const int cy = min(max(cy0 + r, 0), Hc - 1), cx = min(max(cx0 + q, 0), Wc - 1);
                     cp16(tc::smem_addr(sC + ((c * L::CR + r) * L::CC + q) * 16),
-                         gin + (((long long)cy * Wc + cx) * CUP + c * CPC) * EB);
+                         gin + (((long long)c * Hc + cy) * Wc + cx) * 16);
                 }
             }
             if (MODE == TIN_UPCAT) {
@@ -433,7 +436,8 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
                 for (int c = 0; c < COUT; c += 16) tc::tmem_ld16(tmem + lane_base + r * COUT + c, v + c);
 #pragma unroll
                 for (int c = 0; c < COUT; ++c) v[c] = fmaxf(fmaf(v[c], sScale[c], sBias[c]), 0.f);
-                if (y < im.Hl && x < im.Wl) store_pixel<COUT, F8>(im.out, (long long)y * im.Wl + x, v, a.out_q);
+                if (y < im.Hl && x < im.Wl)
+                    store_pixel<COUT, F8>(im.out, (long long)im.Hl * im.Wl, (long long)y * im.Wl + x, v, a.out_q);
                 if (EPI == TEPI_POOL) {
                     if (r & 1) {
                         float s[COUT];
@@ -444,7 +448,8 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
                             s[c] *= 0.25f;
                         }
                         if ((lane & 1) == 0 && y < im.Hl && x < im.Wl)
-                            store_pixel<COUT, F8>(im.pooled, (long long)(y >> 1) * (im.Wl >> 1) + (x >> 1), s, a.pool_q);
+                            store_pixel<COUT, F8>(im.pooled, (long long)(im.Hl >> 1) * (im.Wl >> 1),
+                                                  (long long)(y >> 1) * (im.Wl >> 1) + (x >> 1), s, a.pool_q);
                     } else {
 #pragma unroll
                         for (int c = 0; c < COUT; ++c) prev[c] = v[c];
@@ -557,6 +562,12 @@ __global__ void amax_f16_kernel(const __half* __restrict__ x, long long n, float
 
 }  // namespace
 
+}  // namespace fvn
+
+#include "conv_ws.cuh"
+
+namespace fvn {
+
 template <int CIN, int CG, int COUT, int TR, int MODE, int EPI, int CUP, bool F8>
 static fvn_status launch_tc(fvn_ctx* ctx, TcArgs& a, cudaStream_t st) {
     using L = TcLayout<CIN, CG, COUT, TR, MODE, EPI, CUP, F8>;
@@ -591,6 +602,244 @@ static fvn_status launch_tc(fvn_ctx* ctx, TcArgs& a, cudaStream_t st) {
     return FVN_OK;
 }
 
+// ---- TMA tensor maps and the warp-specialised launches ---------------------
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled from the driver (the runtime is linked, not libcuda).
+static EncodeTiledFn encode_tiled() {
+    static const EncodeTiledFn fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            return static_cast<EncodeTiledFn>(nullptr);
+        return reinterpret_cast<EncodeTiledFn>(p);
+    }();
+    return fn;
+}
+
+// Map of a chunk-planar tensor [C / chunk][H][W][16 B] (FP16, or FP8 as
+// bytes) whose box is 16 bytes x 130 pixels x hy rows of one chunk plane:
+// one plane of a stage, read as contiguous 2080-byte rows.
+static fvn_status make_map(fvn_ctx* ctx, CUtensorMap* m, const void* base, int C, int W, int H, int hy, bool f8) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return set_error(ctx, FVN_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t eb = f8 ? 1 : 2, cpc = 16 / eb;
+    const cuuint64_t dims[4] = {cpc, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)C / cpc};
+    const cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16};
+    const cuuint32_t box[4] = {(cuuint32_t)cpc, (cuuint32_t)ws::kHXW, (cuuint32_t)hy, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    const CUresult r = fn(m, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4,
+                          const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return set_error(ctx, FVN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for a %d x %d x %d tensor", (int)r, H,
+                         W, C);
+    return FVN_OK;
+}
+
+// One image of a warp-specialised layer: source 0 (c0 channels) and source 1
+// (c1 channels, may be absent), outputs, size.
+struct WsSpec {
+    const void* in0;
+    int c0;
+    const void* in1;
+    int c1;
+    void* out;
+    void* pooled;
+    int Hl, Wl;
+};
+
+// Stages of the shared-memory ring that fit next to the resident weights.
+template <int CIN, int COUT, int TR, bool F8, bool FUSE>
+constexpr int ws_stages() {
+    using L1 = ws::Layout<CIN, COUT, TR, 1, F8, FUSE>;
+    const long long budget = 227 * 1024 - (long long)L1::bytes + L1::stage;   // bytes for the stages
+    const long long ns = budget / (long long)L1::stage;
+    return ns >= 4 ? 4 : (ns < 1 ? 1 : (int)ns);
+}
+
+template <int CIN, int CHG, int CH0, int COUT, int TR, bool POOL, bool F8, bool FUSE = false>
+static fvn_status launch_ws(fvn_ctx* ctx, const WsSpec* spec, int n, const ConvW& w, float out_q, float pool_q,
+                            cudaStream_t st) {
+    constexpr int NS = ws_stages<CIN, COUT, TR, F8, FUSE>();
+    using L = ws::Layout<CIN, COUT, TR, NS, F8, FUSE>;
+    static_assert(L::bytes <= 227 * 1024, "stage ring does not fit in shared memory");
+    static_assert(sizeof(ws::Args) <= 32764, "kernel arguments exceed the parameter space");
+    auto kern = ws::conv3x3_ws_kernel<CIN, CHG, CH0, COUT, TR, NS, POOL, F8, FUSE>;
+    static bool configured = false;
+    if (!configured) {
+        FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+        configured = true;
+    }
+    int smem_sm = 0;
+    FVN_CUDA(ctx, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+    int per_sm = smem_sm / (int)(L::bytes + 1024);
+    per_sm = std::min(per_sm, (int)(512 / L::tmem_cols));
+    per_sm = std::min(per_sm, 2048 / ws::kThreads);
+    if (per_sm < 1) return set_error(ctx, FVN_ERR_CUDA, "warp-specialised conv kernel does not fit on an SM");
+    constexpr int CPC = L::CPC;
+    ws::Args a{};
+    a.w = F8 ? static_cast<const void*>(w.w8) : static_cast<const void*>(w.w16);
+    a.bias = w.bias;
+    a.wscale = w.scale8;
+    a.out_q = out_q;
+    a.pool_q = pool_q;
+    a.nimg = n;
+    a.error = ctx->d_error;
+    int ntiles = 0;
+    for (int i = 0; i < n; ++i) {
+        const WsSpec& sp = spec[i];
+        ws::Img& m = a.img[i];
+        if (sp.c0 != CH0 * CPC || sp.c0 + sp.c1 != CHG * CPC)
+            return set_error(ctx, FVN_ERR_ARG, "conv layer channels %d + %d do not match the kernel", sp.c0, sp.c1);
+        fvn_status s = make_map(ctx, &m.map0, sp.in0, sp.c0, sp.Wl, sp.Hl, L::HY, F8);
+        if (s != FVN_OK) return s;
+        if (sp.c1 > 0) {
+            if ((s = make_map(ctx, &m.map1, sp.in1, sp.c1, sp.Wl, sp.Hl, L::HY, F8)) != FVN_OK) return s;
+        } else {
+            m.map1 = m.map0;
+        }
+        m.out = sp.out;
+        m.pooled = sp.pooled;
+        m.Hl = sp.Hl;
+        m.Wl = sp.Wl;
+        m.tiles_x = (sp.Wl + ws::kTW - 1) / ws::kTW;
+        m.tile0 = ntiles;
+        ntiles += m.tiles_x * ((sp.Hl + TR - 1) / TR);
+    }
+    a.ntiles = ntiles;
+    const int grid = std::min(ntiles, ctx->num_sms * per_sm);
+    if (grid > 0) {
+        kern<<<grid, ws::kThreads, L::bytes, st>>>(a);
+        FVN_LAUNCH_CHECK(ctx);
+    }
+    return FVN_OK;
+}
+
+// Map of the sparse frame [5][H0][W0] float32 whose box is 136 columns x
+// rows rows of one plane (the kernel-prediction window of a tile).
+static fvn_status make_sparse_map(fvn_ctx* ctx, CUtensorMap* m, const float* base, int W0, int H0, int rows) {
+    const EncodeTiledFn fn = encode_tiled();
+    if (!fn) return set_error(ctx, FVN_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const cuuint64_t dims[3] = {(cuuint64_t)W0, (cuuint64_t)H0, 5};
+    const cuuint64_t strides[2] = {(cuuint64_t)W0 * 4, (cuuint64_t)W0 * H0 * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)ws::kSpW, (cuuint32_t)rows, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<float*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS)
+        return set_error(ctx, FVN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for a %d x %d sparse frame", (int)r,
+                         H0, W0);
+    return FVN_OK;
+}
+
+// Last layer + head + kernel prediction + blend, warp-specialised (frame
+// widths that are multiples of 4, so the sparse frame's rows are 16-byte
+// aligned for TMA).
+template <bool F8>
+static fvn_status launch_ws_headkp(fvn_ctx* ctx, const ReconView* views, int n, cudaStream_t st) {
+    constexpr int CIN = F8 ? 32 : 16, CPC = F8 ? 16 : 8, TR = 4, NS = 4;
+    using L = ws::HkLayout<CIN, TR, NS, F8>;
+    static_assert(L::bytes <= 227 * 1024, "head / kernel-prediction kernel does not fit in shared memory");
+    static_assert(sizeof(ws::HkArgs) <= 32764, "kernel arguments exceed the parameter space");
+    auto kern = ws::conv3x3_ws_headkp_kernel<CIN, 16 / CPC, TR, NS, F8>;
+    static bool configured = false;
+    if (!configured) {
+        FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
+        configured = true;
+    }
+    const ConvW& w = ctx->layers[9];
+    ws::HkArgs h{};
+    ws::Args& a = h.conv;
+    a.w = F8 ? static_cast<const void*>(w.w8) : static_cast<const void*>(w.w16);
+    a.bias = w.bias;
+    a.wscale = w.scale8;
+    a.nimg = n;
+    a.error = ctx->d_error;
+    h.head_w = ctx->head_w16;
+    h.head_b = ctx->head_b32;
+    int ntiles = 0;
+    for (int i = 0; i < n; ++i) {
+        const ReconView& v = views[i];
+        const int Wl = (v.w + 3) & ~3, Hl = (v.h + 3) & ~3;
+        ws::Img& m = a.img[i];
+        fvn_status s = make_map(ctx, &m.map0, v.plan.d0a, 16, Wl, Hl, TR + 2, F8);
+        if (s != FVN_OK) return s;
+        m.map1 = m.map0;
+        if ((s = make_sparse_map(ctx, &h.sp[i], v.rgbam, v.w, v.h, TR + 4)) != FVN_OK) return s;
+        h.rgb[i] = v.rgb;
+        h.H0[i] = v.h;
+        h.W0[i] = v.w;
+        m.Hl = Hl;
+        m.Wl = Wl;
+        m.tiles_x = (Wl + ws::kTW - 1) / ws::kTW;
+        m.tile0 = ntiles;
+        ntiles += m.tiles_x * ((Hl + TR - 1) / TR);
+    }
+    a.ntiles = ntiles;
+    int smem_sm = 0;
+    FVN_CUDA(ctx, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+    int per_sm = std::min(smem_sm / (int)(L::bytes + 1024), (int)(512 / L::tmem_cols));
+    if (per_sm < 1) return set_error(ctx, FVN_ERR_CUDA, "head / kernel-prediction kernel does not fit on an SM");
+    const int grid = std::min(ntiles, ctx->num_sms * per_sm);
+    if (grid > 0) {
+        kern<<<grid, ws::kHkThreads, L::bytes, st>>>(h);
+        FVN_LAUNCH_CHECK(ctx);
+    }
+    return FVN_OK;
+}
+
+// Bilinear x2 up-sampling of the coarse level of every view (one launch, one
+// block per fine row of one chunk plane of one view).
+struct UpArgs {
+    int n, chunks;
+    struct {
+        const void* coarse;
+        void* fine;
+        int Hl, Wl;
+        int row0;                     // first block of this view
+    } im[kMaxViews];
+};
+
+template <bool F8>
+__global__ void __launch_bounds__(256) upsample2_views_kernel(const __grid_constant__ UpArgs u) {
+    int i = 0;
+    while (i + 1 < u.n && (int)blockIdx.x >= u.im[i + 1].row0) ++i;
+    const int r = blockIdx.x - u.im[i].row0;        // chunk * Hl + row
+    const int c = r / u.im[i].Hl, gy = r - c * u.im[i].Hl;
+    ws::upsample2_row<F8>(u.im[i].coarse, u.im[i].fine, u.im[i].Hl, u.im[i].Wl, c, gy);
+}
+
+template <bool F8>
+static fvn_status upsample_views(fvn_ctx* ctx, const void* const* coarse, void* const* fine, const int* Hl,
+                                 const int* Wl, int n, int channels, cudaStream_t st) {
+    UpArgs u{};
+    u.n = n;
+    u.chunks = channels / (F8 ? 16 : 8);
+    long long rows = 0;
+    for (int i = 0; i < n; ++i) {
+        u.im[i].coarse = coarse[i];
+        u.im[i].fine = fine[i];
+        u.im[i].Hl = Hl[i];
+        u.im[i].Wl = Wl[i];
+        u.im[i].row0 = (int)rows;
+        rows += (long long)u.chunks * Hl[i];
+    }
+    if (rows >= (1ll << 31)) return set_error(ctx, FVN_ERR_ARG, "up-sampling grid too large");
+    if (rows > 0) {
+        upsample2_views_kernel<F8><<<(unsigned)rows, 256, 0, st>>>(u);
+        FVN_LAUNCH_CHECK(ctx);
+    }
+    return FVN_OK;
+}
+
 // Tensors and sizes of layer l (0..9) of the network for one view.
 static TcImg layer_img(int l, const ReconView& v) {
     const ReconPlan& B = v.plan;
@@ -613,13 +862,19 @@ static TcImg layer_img(int l, const ReconView& v) {
     return m;
 }
 
-// The ten launches of the network over every view at once (one launch per
-// layer covers the tiles of all views).  FP16 operands, or FP8 operands with
-// the calibrated scales; FP8 tensors use half of each FP16 buffer.
+// The launches of the network over every view at once (one launch per layer
+// covers the tiles of all views).  FP16 operands, or FP8 operands with the
+// calibrated scales; FP8 tensors use half of each FP16 buffer.  The first
+// layer (reading the planar sparse frame) and the last (head, kernel
+// prediction, blend) run conv3x3_tc_kernel; the eight in between run the
+// warp-specialised TMA kernel, the two decoder layers on an up-sampled copy
+// of the coarse level.
 template <bool F8>
 static fvn_status run_tc(fvn_ctx* ctx, const ReconView* views, int n, cudaStream_t st) {
     const ConvW* L = ctx->layers;
     const float* q = ctx->fp8_inv_scale;   // 1 / s per activation tensor
+    constexpr int CPC = F8 ? 16 : 8;
+    constexpr int K16 = F8 ? 32 : 16;      // K per tap of the 16-channel layers (FP8 MMA K = 32)
     TcArgs a;
     auto prep = [&](int l) {
         a = TcArgs{};
@@ -629,39 +884,117 @@ static fvn_status run_tc(fvn_ctx* ctx, const ReconView* views, int n, cudaStream
         a.bias = L[l].bias;
         a.wscale = L[l].scale8;
     };
-    constexpr int K16 = F8 ? 32 : 16;      // K per tap of the 16-channel layers (FP8 MMA K = 32)
+    WsSpec sp[kMaxViews];
+    int Hh[kMaxViews], Wh[kMaxViews], Hf[kMaxViews], Wf[kMaxViews];
+    for (int i = 0; i < n; ++i) {
+        Wf[i] = (views[i].w + 3) & ~3;
+        Hf[i] = (views[i].h + 3) & ~3;
+        Wh[i] = Wf[i] / 2;
+        Hh[i] = Hf[i] / 2;
+    }
+    // spec of layer l for view i: sources, outputs, level size
+    auto spec = [&](const void* in0, int c0, const void* in1, int c1, void* out, void* pooled, int H, int W) {
+        return WsSpec{in0, c0, in1, c1, out, pooled, H, W};
+    };
     fvn_status s;
     prep(0);
     a.in_q = q[FP8_RGBAM]; a.out_q = q[FP8_E0A];
     if ((s = launch_tc<K16, 16, 16, 4, TIN_RGBAM, TEPI_STORE, 0, F8>(ctx, a, st)) != FVN_OK) return s;
-    prep(1);
-    a.out_q = q[FP8_E0]; a.pool_q = q[FP8_P0];
-    if ((s = launch_tc<K16, 16, 16, 4, TIN_NHWC, TEPI_POOL, 0, F8>(ctx, a, st)) != FVN_OK) return s;
-    prep(2);
-    a.out_q = q[FP8_E1A];
-    if ((s = launch_tc<K16, 16, 32, 4, TIN_NHWC, TEPI_STORE, 0, F8>(ctx, a, st)) != FVN_OK) return s;
-    prep(3);
-    a.out_q = q[FP8_E1]; a.pool_q = q[FP8_P1];
-    if ((s = launch_tc<32, 32, 32, 4, TIN_NHWC, TEPI_POOL, 0, F8>(ctx, a, st)) != FVN_OK) return s;
-    prep(4);
-    a.out_q = q[FP8_BA];
-    if ((s = launch_tc<32, 32, 64, 2, TIN_NHWC, TEPI_STORE, 0, F8>(ctx, a, st)) != FVN_OK) return s;
-    prep(5);
-    a.out_q = q[FP8_BT];
-    if ((s = launch_tc<64, 64, 64, 2, TIN_NHWC, TEPI_STORE, 0, F8>(ctx, a, st)) != FVN_OK) return s;
-    prep(6);
-    a.out_q = q[FP8_D1A];
-    if ((s = launch_tc<96, 96, 32, 2, TIN_UPCAT, TEPI_STORE, 64, F8>(ctx, a, st)) != FVN_OK) return s;
-    prep(7);
-    a.out_q = q[FP8_D1];
-    if ((s = launch_tc<32, 32, 32, 4, TIN_NHWC, TEPI_STORE, 0, F8>(ctx, a, st)) != FVN_OK) return s;
-    prep(8);
-    a.out_q = q[FP8_D0A];
-    if ((s = launch_tc<F8 ? 64 : 48, 48, 16, 4, TIN_UPCAT, TEPI_STORE, 32, F8>(ctx, a, st)) != FVN_OK) return s;
-    prep(9);
+    // enc0b (+ pool)
+    for (int i = 0; i < n; ++i) {
+        const ReconPlan& B = views[i].plan;
+        sp[i] = spec(B.e0a, 16, nullptr, 0, B.e0, B.p0, Hf[i], Wf[i]);
+    }
+    if ((s = launch_ws<K16, 16 / CPC, 16 / CPC, 16, 4, true, F8, true>(ctx, sp, n, L[1], q[FP8_E0], q[FP8_P0], st)) !=
+        FVN_OK)
+        return s;
+    // enc1a, enc1b (+ pool)
+    for (int i = 0; i < n; ++i) {
+        const ReconPlan& B = views[i].plan;
+        sp[i] = spec(B.p0, 16, nullptr, 0, B.e1a, nullptr, Hh[i], Wh[i]);
+    }
+    if ((s = launch_ws<K16, 16 / CPC, 16 / CPC, 32, 4, false, F8>(ctx, sp, n, L[2], q[FP8_E1A], 0.f, st)) != FVN_OK)
+        return s;
+    for (int i = 0; i < n; ++i) {
+        const ReconPlan& B = views[i].plan;
+        sp[i] = spec(B.e1a, 32, nullptr, 0, B.e1, B.p1, Hh[i], Wh[i]);
+    }
+    if ((s = launch_ws<32, 32 / CPC, 32 / CPC, 32, 4, true, F8>(ctx, sp, n, L[3], q[FP8_E1], q[FP8_P1], st)) !=
+        FVN_OK)
+        return s;
+    // bottleneck
+    for (int i = 0; i < n; ++i) {
+        const ReconPlan& B = views[i].plan;
+        sp[i] = spec(B.p1, 32, nullptr, 0, B.ba, nullptr, Hf[i] / 4, Wf[i] / 4);
+    }
+    if ((s = launch_ws<32, 32 / CPC, 32 / CPC, 64, 2, false, F8>(ctx, sp, n, L[4], q[FP8_BA], 0.f, st)) != FVN_OK)
+        return s;
+    for (int i = 0; i < n; ++i) {
+        const ReconPlan& B = views[i].plan;
+        sp[i] = spec(B.ba, 64, nullptr, 0, B.bt, nullptr, Hf[i] / 4, Wf[i] / 4);
+    }
+    if ((s = launch_ws<64, 64 / CPC, 64 / CPC, 64, 2, false, F8>(ctx, sp, n, L[5], q[FP8_BT], 0.f, st)) != FVN_OK)
+        return s;
+    // dec1a on [up(bt), e1], dec1b
+    {
+        const void* c[kMaxViews];
+        void* f[kMaxViews];
+        for (int i = 0; i < n; ++i) {
+            c[i] = views[i].plan.bt;
+            f[i] = views[i].plan.u1;
+        }
+        if ((s = upsample_views<F8>(ctx, c, f, Hh, Wh, n, 64, st)) != FVN_OK) return s;
+    }
+    for (int i = 0; i < n; ++i) {
+        const ReconPlan& B = views[i].plan;
+        sp[i] = spec(B.u1, 64, B.e1, 32, B.d1a, nullptr, Hh[i], Wh[i]);
+    }
+    if ((s = launch_ws<96, 96 / CPC, 64 / CPC, 32, 1, false, F8>(ctx, sp, n, L[6], q[FP8_D1A], 0.f, st)) != FVN_OK)
+        return s;
+    for (int i = 0; i < n; ++i) {
+        const ReconPlan& B = views[i].plan;
+        sp[i] = spec(B.d1a, 32, nullptr, 0, B.d1, nullptr, Hh[i], Wh[i]);
+    }
+    if ((s = launch_ws<32, 32 / CPC, 32 / CPC, 32, 4, false, F8>(ctx, sp, n, L[7], q[FP8_D1], 0.f, st)) != FVN_OK)
+        return s;
+    // dec0a on [up(d1), e0]
+    {
+        const void* c[kMaxViews];
+        void* f[kMaxViews];
+        for (int i = 0; i < n; ++i) {
+            c[i] = views[i].plan.d1;
+            f[i] = views[i].plan.u0;
+        }
+        if ((s = upsample_views<F8>(ctx, c, f, Hf, Wf, n, 32, st)) != FVN_OK) return s;
+    }
+    for (int i = 0; i < n; ++i) {
+        const ReconPlan& B = views[i].plan;
+        sp[i] = spec(B.u0, 32, B.e0, 16, B.d0a, nullptr, Hf[i], Wf[i]);
+    }
+    if ((s = launch_ws<F8 ? 64 : 48, 48 / CPC, 32 / CPC, 16, 4, false, F8, true>(ctx, sp, n, L[8], q[FP8_D0A], 0.f,
+                                                                              st)) !=
+        FVN_OK)
+        return s;
+    // dec0b + head + kernel prediction + blend: the warp-specialised kernel for
+    // views whose width is a multiple of 4 (TMA rows of the sparse frame), the
+    // staged kernel for the others -- each view always takes the same kernel
+    ReconView al[kMaxViews], un[kMaxViews];
+    int na = 0, nu = 0;
+    for (int i = 0; i < n; ++i) {
+        if (views[i].w % 4 == 0) al[na++] = views[i];
+        else un[nu++] = views[i];
+    }
+    if (na > 0 && (s = launch_ws_headkp<F8>(ctx, al, na, st)) != FVN_OK) return s;
+    if (nu == 0) return FVN_OK;
+    a = TcArgs{};
+    a.nimg = nu;
+    for (int i = 0; i < nu; ++i) a.img[i] = layer_img(9, un[i]);
+    a.w = F8 ? static_cast<const void*>(L[9].w8) : static_cast<const void*>(L[9].w16);
+    a.bias = L[9].bias;
+    a.wscale = L[9].scale8;
     a.head_w = ctx->head_w16;
     a.head_b = ctx->head_b32;
-    return launch_tc<K16, 16, 16, 4, TIN_NHWC, TEPI_HEADKP, 0, F8>(ctx, a, st);
+    return launch_tc<K16, 16, 16, 4, TIN_ACT, TEPI_HEADKP, 0, F8>(ctx, a, st);
 }
 
 fvn_status reconstruct_tc_views(fvn_ctx* ctx, const ReconView* views, int n, int precision, cudaStream_t st) {

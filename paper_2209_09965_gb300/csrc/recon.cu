@@ -404,7 +404,9 @@ static fvn_status launch_conv(fvn_ctx* ctx, ConvArgs a, cudaStream_t st) {
     return FVN_OK;
 }
 
-static size_t plan_buffers(int W4, int H4, ReconPlan* b, char* base) {
+// separate_up: give the up-sampled decoder inputs buffers of their own
+// (FP8 calibration reads every activation after the pass).
+static size_t plan_buffers(int W4, int H4, ReconPlan* b, char* base, bool separate_up = false) {
     const size_t n0 = (size_t)W4 * H4, n1 = n0 / 4, n2 = n0 / 16;
     const size_t sizes[12] = {n0 * 16, n0 * 16, n1 * 16, n1 * 32, n1 * 32, n2 * 32,
                               n2 * 64, n2 * 64, n1 * 32, n1 * 32, n0 * 16, n0 * 16};
@@ -414,6 +416,20 @@ static size_t plan_buffers(int W4, int H4, ReconPlan* b, char* base) {
     for (int i = 0; i < 12; ++i) {
         if (base) *ptrs[i] = reinterpret_cast<__half*>(base + off);
         off += (sizes[i] * sizeof(__half) + 255) & ~(size_t)255;
+    }
+    // up-sampled decoder inputs on dead buffers: u1 (n1 x 64) on e0a (n0 x 16,
+    // dead after the second layer); u0 (n0 x 32) from p0 on, over p0, e1a,
+    // e1, p1, ba, bt, d1a (n0 x 38 in total, all dead once d1 is written)
+    if (separate_up) {
+        if (base) {
+            b->u1 = reinterpret_cast<__half*>(base + off);
+            b->u0 = reinterpret_cast<__half*>(base + off + ((n1 * 64 * sizeof(__half) + 255) & ~(size_t)255));
+        }
+        return off + ((n1 * 64 * sizeof(__half) + 255) & ~(size_t)255) + ((n0 * 32 * sizeof(__half) + 255) & ~(size_t)255);
+    }
+    if (base) {
+        b->u1 = b->e0a;
+        b->u0 = b->p0;
     }
     return off;
 }
@@ -649,30 +665,34 @@ extern "C" fvn_status fvn_calibrate_fp8(fvn_ctx* ctx, const float* rgbam, int w,
                   kMaxSide);
     if (!ctx->has_weights) return set_error(ctx, FVN_ERR_STATE, "no weights loaded (call fvn_load_weights)");
     cudaStream_t st = as_stream(stream);
-    // run the FP16 tensor-core network on this frame into the context workspace
-    float* out = nullptr;
-    FVN_CUDA(ctx, cudaMalloc(&out, sizeof(float) * 3 * (size_t)w * h));
-    const int saved = ctx->conv_impl;
-    ctx->conv_impl = CONV_TCGEN05;
-    fvn_status s = reconstruct_impl(ctx, rgbam, w, h, FVN_PREC_FP16, out, st);
-    ctx->conv_impl = saved;
-    if (s != FVN_OK) {
-        cudaFree(out);
-        return s;
-    }
-    if (!ctx->d_amax) FVN_CUDA(ctx, cudaMalloc(&ctx->d_amax, FP8_NT * sizeof(float)));
-    FVN_CUDA(ctx, cudaMemsetAsync(ctx->d_amax, 0, FP8_NT * sizeof(float), st));
+    // run the FP16 tensor-core network on this frame into a workspace where
+    // no activation is overwritten, then reduce every activation's amax
     const int W4 = (w + 3) & ~3, H4 = (h + 3) & ~3;
-    ReconPlan B;
-    plan_buffers(W4, H4, &B, static_cast<char*>(ctx->recon_ws.base));
-    s = calibrate_amax(ctx, B, w, h, ctx->d_amax, st);
-    if (s != FVN_OK) {
+    float* out = nullptr;
+    char* wsp = nullptr;
+    FVN_CUDA(ctx, cudaMalloc(&out, sizeof(float) * 3 * (size_t)w * h));
+    if (cudaMalloc(&wsp, plan_buffers(W4, H4, nullptr, nullptr, true)) != cudaSuccess) {
         cudaFree(out);
-        return s;
+        return set_error(ctx, FVN_ERR_OOM, "no memory for the calibration workspace");
     }
-    float amax[FP8_NT];
-    FVN_CUDA(ctx, cudaStreamSynchronize(st));
+    ReconView v;
+    plan_buffers(W4, H4, &v.plan, wsp, true);
+    v.rgbam = rgbam;
+    v.w = w;
+    v.h = h;
+    v.rgb = out;
+    fvn_status s = reconstruct_tc_views(ctx, &v, 1, FVN_PREC_FP16, st);
+    if (s == FVN_OK && !ctx->d_amax && cudaMalloc(&ctx->d_amax, FP8_NT * sizeof(float)) != cudaSuccess)
+        s = set_error(ctx, FVN_ERR_OOM, "no memory for the amax accumulators");
+    if (s == FVN_OK && cudaMemsetAsync(ctx->d_amax, 0, FP8_NT * sizeof(float), st) != cudaSuccess)
+        s = set_error(ctx, FVN_ERR_CUDA, "cudaMemsetAsync failed");
+    if (s == FVN_OK) s = calibrate_amax(ctx, v.plan, w, h, ctx->d_amax, st);
+    const cudaError_t se = cudaStreamSynchronize(st);
     cudaFree(out);
+    cudaFree(wsp);
+    if (s != FVN_OK) return s;
+    if (se != cudaSuccess) return set_error(ctx, FVN_ERR_CUDA, "calibration pass failed: %s", cudaGetErrorString(se));
+    float amax[FP8_NT];
     FVN_CUDA(ctx, cudaMemcpy(amax, ctx->d_amax, sizeof amax, cudaMemcpyDeviceToHost));
     for (int t = 0; t < FP8_NT; ++t) ctx->fp8_amax[t] = reset ? amax[t] : std::max(ctx->fp8_amax[t], amax[t]);
     return build_fp8_weights(ctx);
