@@ -117,7 +117,12 @@ fvn_status fvn_destroy(fvn_ctx* ctx);
  *      (32 samples per step, composited by a product scan of the
  *      transmittances; the same result up to FP32 rounding order); 0 = never.
  *  FVN_OPT_MARCH_REFILL_DENSE, FVN_OPT_MARCH_BLOCKS_PER_SM_DENSE,
- *  FVN_OPT_MARCH_COOP_DENSE: the same for the dense march (ids == NULL). */
+ *  FVN_OPT_MARCH_COOP_DENSE: the same for the dense march (ids == NULL).
+ *  FVN_OPT_MARCH_GRADIENT_VOLUME: 1 (default) = a shaded march first writes a
+ *      gradient volume, (v, dv/dx, dv/dy, dv/dz) as central differences per
+ *      padded voxel (16 bytes each, used when that takes at most 4 GiB), and
+ *      reads 8 of those per sample instead of 32 voxels; 0 = always the
+ *      32-voxel stencil.  Same result up to FP32 rounding order. */
 enum {
     FVN_OPT_CONV_KERNEL = 1,
     FVN_OPT_MARCH_REFILL = 2,
@@ -125,7 +130,8 @@ enum {
     FVN_OPT_MARCH_REFILL_DENSE = 4,
     FVN_OPT_MARCH_BLOCKS_PER_SM_DENSE = 5,
     FVN_OPT_MARCH_COOP = 6,
-    FVN_OPT_MARCH_COOP_DENSE = 7
+    FVN_OPT_MARCH_COOP_DENSE = 7,
+    FVN_OPT_MARCH_GRADIENT_VOLUME = 8
 };
 fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value);
 

@@ -120,7 +120,7 @@ extern "C" fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int 
         ws.bytes = need;
     }
     for (int k = 0; k < nvol; ++k) {
-        const size_t pb = padded_volume_bytes(vols[k]);
+        const size_t pb = march_volume_bytes(ctx, vols[k], mp);
         if (ws.pad_bytes[k] < pb) {
             FVN_CUDA(ctx, cudaDeviceSynchronize());
             cudaFree(ws.pad[k]);
@@ -151,11 +151,11 @@ extern "C" fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int 
     fvn_status s = make_mask_batch_impl(ctx, fov, w, h, mask, ids, counts, nviews, st);
     if (s != FVN_OK) return s;
 
-    // ---- sparse frames start empty; padded volumes -------------------------
+    // ---- sparse frames start empty; the march's copy of each volume --------
     for (int i = 0; i < nviews; ++i)
         FVN_CUDA(ctx, cudaMemsetAsync(rgbam[i], 0, 5 * sizeof(float) * (size_t)w[i] * h[i], st));
     for (int k = 0; k < nvol; ++k)
-        if ((s = pad_volume_impl(ctx, vols[k], ws.pad[k], st)) != FVN_OK) return s;
+        if ((s = march_volume_prepare(ctx, vols[k], mp, ws.pad[k], st)) != FVN_OK) return s;
 
     // ---- one persistent march over every view's rays -----------------------
     BatchMarchView mv[kMaxViews];

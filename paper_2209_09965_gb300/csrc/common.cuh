@@ -132,6 +132,7 @@ struct fvn_ctx {
     int march_blocks_per_sm_dense = 0;
     int march_coop = 0;               // sparse march: finish a warp's rays with the whole warp once at most this many are left
     int march_coop_dense = 0;
+    int march_grad4 = 1;              // shaded marches read a gradient volume when it fits
     void* pad_buf = nullptr;          // padded copy of the volume read by the march
     size_t pad_bytes = 0;
     float* d_act_scale = nullptr;     // FP8 per-layer activation scales
@@ -189,8 +190,13 @@ struct BatchMarchView {
 // outside the sampled pixels).
 fvn_status march_batch_impl(fvn_ctx* ctx, const BatchMarchView* views, int n, const fvn_march_params* mp,
                             unsigned long long* nsamples, cudaStream_t st);
-size_t padded_volume_bytes(const fvn_volume* vol);
-fvn_status pad_volume_impl(fvn_ctx* ctx, const fvn_volume* vol, void* pvol, cudaStream_t st);
+// The march's copy of a volume: a gradient volume for shaded marches that
+// fit (march_uses_grad4), else a padded scalar copy; its size and one pass
+// that writes it.
+bool march_uses_grad4(const fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp);
+size_t march_volume_bytes(const fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp);
+fvn_status march_volume_prepare(fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp, void* buf,
+                                cudaStream_t st);
 // Masks and id lists of n views in one launch: view i writes mask[i] and its
 // ids at ids[i], its count at counts[i] (counts zeroed here).
 fvn_status make_mask_batch_impl(fvn_ctx* ctx, const fvn_foveation* const* fov, const int* w, const int* h,

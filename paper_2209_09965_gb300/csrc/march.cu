@@ -238,17 +238,9 @@ __device__ __forceinline__ void load_stencil(const MarchArgs& a, const T* __rest
     stencil_fetch<T, I, SHADE>(vol, b, sy, sz, S);
 }
 
-// Classify and shade one loaded sample: returns its opacity al and, when
-// al > 0, its (clamped) shaded colour.
-template <bool SHADE>
-__device__ __forceinline__ float shade_sample(const MarchArgs& a, const float4* s_tf, float tfmax, const Stencil& S,
-                                              float dx, float dy, float dz, float& cr, float& cg, float& cb) {
-    float rows[2][2];
-#pragma unroll
-    for (int z = 0; z < 2; ++z)
-#pragma unroll
-        for (int y = 0; y < 2; ++y) rows[z][y] = lerpf(S.c[z][y][0], S.c[z][y][1], S.tx);
-    const float v = lerpf(lerpf(rows[0][0], rows[0][1], S.ty), lerpf(rows[1][0], rows[1][1], S.ty), S.tz);
+// TF lookup at value v: returns the opacity and, when it is > 0, the colour.
+__device__ __forceinline__ float tf_lookup(const MarchArgs& a, const float4* s_tf, float tfmax, float v, float& cr,
+                                           float& cg, float& cb) {
     const float xi = v * tfmax;
     float fr;
     int ti = floor_frac(xi, fr);
@@ -266,53 +258,153 @@ __device__ __forceinline__ float shade_sample(const MarchArgs& a, const float4* 
         cr = fmaf(fr, c1.x - c0.x, c0.x);
         cg = fmaf(fr, c1.y - c0.y, c0.y);
         cb = fmaf(fr, c1.z - c0.z, c0.z);
-        if (SHADE) {
-            // central differences at +-1 voxel of the trilinear field
-            float d[2][2];
-#pragma unroll
-            for (int z = 0; z < 2; ++z)
-#pragma unroll
-                for (int y = 0; y < 2; ++y)
-                    d[z][y] = lerpf(S.c[z][y][1], S.xp[z][y], S.tx) - lerpf(S.xm[z][y], S.c[z][y][0], S.tx);
-            const float gx = 0.5f * lerpf(lerpf(d[0][0], d[0][1], S.ty), lerpf(d[1][0], d[1][1], S.ty), S.tz);
-            float ym[2], yp[2], zm[2], zp[2];
-#pragma unroll
-            for (int q = 0; q < 2; ++q) {
-                ym[q] = lerpf(S.ym[q][0], S.ym[q][1], S.tx);
-                yp[q] = lerpf(S.yp[q][0], S.yp[q][1], S.tx);
-                zm[q] = lerpf(S.zm[q][0], S.zm[q][1], S.tx);
-                zp[q] = lerpf(S.zp[q][0], S.zp[q][1], S.tx);
-            }
-            const float gy = 0.5f * lerpf(lerpf(rows[0][1], yp[0], S.ty) - lerpf(ym[0], rows[0][0], S.ty),
-                                          lerpf(rows[1][1], yp[1], S.ty) - lerpf(ym[1], rows[1][0], S.ty), S.tz);
-            const float gz = 0.5f * lerpf(lerpf(rows[1][0], zp[0], S.tz) - lerpf(zm[0], rows[0][0], S.tz),
-                                          lerpf(rows[1][1], zp[1], S.tz) - lerpf(zm[1], rows[0][1], S.tz), S.ty);
-            const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
-            if (g2 >= 1e-12f) {   // |g| >= 1e-6: shade, otherwise keep the TF colour
-                const float ndl = fabsf(fmaf(gx, dx, fmaf(gy, dy, gz * dz))) * rsqrtf(g2);
-                float sp = ndl * ndl;   // ndl^32 by five squarings
-                sp *= sp;
-                sp *= sp;
-                sp *= sp;
-                sp *= sp;
-                const float diff = fmaf(0.7f, ndl, 0.2f);
-                const float spec = 0.3f * sp;
-                cr = __saturatef(fmaf(cr, diff, spec));
-                cg = __saturatef(fmaf(cg, diff, spec));
-                cb = __saturatef(fmaf(cb, diff, spec));
-            }
-        }
     }
     return al;
 }
 
+// Phong with a headlight from the gradient (gx, gy, gz) and the ray
+// direction; no shading where |g| < 1e-6.
+__device__ __forceinline__ void phong(float gx, float gy, float gz, float dx, float dy, float dz, float& cr, float& cg,
+                                      float& cb) {
+    const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+    if (g2 >= 1e-12f) {   // |g| >= 1e-6: shade, otherwise keep the TF colour
+        const float ndl = fabsf(fmaf(gx, dx, fmaf(gy, dy, gz * dz))) * rsqrtf(g2);
+        float sp = ndl * ndl;   // ndl^32 by five squarings
+        sp *= sp;
+        sp *= sp;
+        sp *= sp;
+        sp *= sp;
+        const float diff = fmaf(0.7f, ndl, 0.2f);
+        const float spec = 0.3f * sp;
+        cr = __saturatef(fmaf(cr, diff, spec));
+        cg = __saturatef(fmaf(cg, diff, spec));
+        cb = __saturatef(fmaf(cb, diff, spec));
+    }
+}
+
+// Classify and shade one loaded sample: returns its opacity al and, when
+// al > 0, its (clamped) shaded colour.
+template <bool SHADE>
+__device__ __forceinline__ float shade_sample(const MarchArgs& a, const float4* s_tf, float tfmax, const Stencil& S,
+                                              float dx, float dy, float dz, float& cr, float& cg, float& cb) {
+    float rows[2][2];
+#pragma unroll
+    for (int z = 0; z < 2; ++z)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) rows[z][y] = lerpf(S.c[z][y][0], S.c[z][y][1], S.tx);
+    const float v = lerpf(lerpf(rows[0][0], rows[0][1], S.ty), lerpf(rows[1][0], rows[1][1], S.ty), S.tz);
+    const float al = tf_lookup(a, s_tf, tfmax, v, cr, cg, cb);
+    if (SHADE && al > 0.0f) {
+        // central differences at +-1 voxel of the trilinear field
+        float d[2][2];
+#pragma unroll
+        for (int z = 0; z < 2; ++z)
+#pragma unroll
+            for (int y = 0; y < 2; ++y)
+                d[z][y] = lerpf(S.c[z][y][1], S.xp[z][y], S.tx) - lerpf(S.xm[z][y], S.c[z][y][0], S.tx);
+        const float gx = 0.5f * lerpf(lerpf(d[0][0], d[0][1], S.ty), lerpf(d[1][0], d[1][1], S.ty), S.tz);
+        float ym[2], yp[2], zm[2], zp[2];
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            ym[q] = lerpf(S.ym[q][0], S.ym[q][1], S.tx);
+            yp[q] = lerpf(S.yp[q][0], S.yp[q][1], S.tx);
+            zm[q] = lerpf(S.zm[q][0], S.zm[q][1], S.tx);
+            zp[q] = lerpf(S.zp[q][0], S.zp[q][1], S.tx);
+        }
+        const float gy = 0.5f * lerpf(lerpf(rows[0][1], yp[0], S.ty) - lerpf(ym[0], rows[0][0], S.ty),
+                                      lerpf(rows[1][1], yp[1], S.ty) - lerpf(ym[1], rows[1][0], S.ty), S.tz);
+        const float gz = 0.5f * lerpf(lerpf(rows[1][0], zp[0], S.tz) - lerpf(zm[0], rows[0][0], S.tz),
+                                      lerpf(rows[1][1], zp[1], S.tz) - lerpf(zm[1], rows[0][1], S.tz), S.ty);
+        phong(gx, gy, gz, dx, dy, dz, cr, cg, cb);
+    }
+    return al;
+}
+
+// Sample source of the scalar padded copy: the 32-voxel stencil.
+template <typename T>
+struct ScalarSrc {
+    using V = T;
+    using St = Stencil;
+    template <typename I, bool SHADE>
+    __device__ static __forceinline__ void load(const MarchArgs& a, const V* __restrict__ vol, I sy, I sz, float ux,
+                                                float uy, float uz, St& S) {
+        load_stencil<T, I, SHADE>(a, vol, sy, sz, ux, uy, uz, S);
+    }
+    template <bool SHADE>
+    __device__ static __forceinline__ float shade(const MarchArgs& a, const float4* s_tf, float tfmax, const St& S,
+                                                  float dx, float dy, float dz, float& cr, float& cg, float& cb) {
+        return shade_sample<SHADE>(a, s_tf, tfmax, S, dx, dy, dz, cr, cg, cb);
+    }
+};
+
+// Sample source of the gradient volume: every padded voxel holds
+// (v, Dx, Dy, Dz) with D = half the difference of its two neighbours along
+// the axis (clamp to edge).  The central difference at +-1 voxel of the
+// trilinear field equals the trilinear interpolation of D (both shifted
+// fields use the sample's own weights), so a shaded sample is 8 float4
+// loads instead of 32 scalar ones.
+struct Stencil4 {
+    float4 c[2][2][2];
+    float tx, ty, tz;
+};
+
+struct Grad4Src {
+    using V = float4;
+    using St = Stencil4;
+    template <typename I, bool SHADE>
+    __device__ static __forceinline__ void load(const MarchArgs& a, const V* __restrict__ vol, I sy, I sz, float ux,
+                                                float uy, float uz, St& S) {
+        int i = floor_frac(ux, S.tx), j = floor_frac(uy, S.ty), k = floor_frac(uz, S.tz);
+        i = min(max(i, -1), a.nx - 1);
+        j = min(max(j, -1), a.ny - 1);
+        k = min(max(k, -1), a.nz - 1);
+        const V* b = vol + ((I)(k + kPad) * sz + (I)(j + kPad) * sy + (i + kPad));
+#pragma unroll
+        for (int z = 0; z < 2; ++z)
+#pragma unroll
+            for (int y = 0; y < 2; ++y) {
+                const V* r = b + (I)z * sz + (I)y * sy;
+                S.c[z][y][0] = __ldg(r);
+                S.c[z][y][1] = __ldg(r + 1);
+            }
+    }
+    template <bool SHADE>
+    __device__ static __forceinline__ float shade(const MarchArgs& a, const float4* s_tf, float tfmax, const St& S,
+                                                  float dx, float dy, float dz, float& cr, float& cg, float& cb) {
+        float rows[2][2];
+#pragma unroll
+        for (int z = 0; z < 2; ++z)
+#pragma unroll
+            for (int y = 0; y < 2; ++y) rows[z][y] = lerpf(S.c[z][y][0].x, S.c[z][y][1].x, S.tx);
+        const float v = lerpf(lerpf(rows[0][0], rows[0][1], S.ty), lerpf(rows[1][0], rows[1][1], S.ty), S.tz);
+        const float al = tf_lookup(a, s_tf, tfmax, v, cr, cg, cb);
+        if (SHADE && al > 0.0f) {
+            float gr[3][2][2];
+#pragma unroll
+            for (int z = 0; z < 2; ++z)
+#pragma unroll
+                for (int y = 0; y < 2; ++y) {
+                    gr[0][z][y] = lerpf(S.c[z][y][0].y, S.c[z][y][1].y, S.tx);
+                    gr[1][z][y] = lerpf(S.c[z][y][0].z, S.c[z][y][1].z, S.tx);
+                    gr[2][z][y] = lerpf(S.c[z][y][0].w, S.c[z][y][1].w, S.tx);
+                }
+            float g[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                g[c] = lerpf(lerpf(gr[c][0][0], gr[c][0][1], S.ty), lerpf(gr[c][1][0], gr[c][1][1], S.ty), S.tz);
+            phong(g[0], g[1], g[2], dx, dy, dz, cr, cg, cb);
+        }
+        return al;
+    }
+};
+
 // Classify, shade and composite one loaded sample; returns true once the ray
 // is opaque enough to stop.
-template <bool SHADE>
+template <typename Src, bool SHADE>
 __device__ __forceinline__ bool composite_sample(const MarchArgs& a, const float4* s_tf, float tfmax,
-                                                 const Stencil& S, Ray& s) {
+                                                 const typename Src::St& S, Ray& s) {
     float cr, cg, cb;
-    const float al = shade_sample<SHADE>(a, s_tf, tfmax, S, s.dx, s.dy, s.dz, cr, cg, cb);
+    const float al = Src::template shade<SHADE>(a, s_tf, tfmax, S, s.dx, s.dy, s.dz, cr, cg, cb);
     if (al > 0.0f) {
         const float w = (1.0f - s.A) * al;
         s.C0 = fmaf(w, cr, s.C0);
@@ -326,22 +418,24 @@ __device__ __forceinline__ bool composite_sample(const MarchArgs& a, const float
 // Up to two samples of the ray with both samples' loads issued before either
 // is composited (the loads do not depend on the compositing), which halves
 // the latency chain a long ray walks.  Returns true when the ray is finished.
-template <typename T, typename I, bool SHADE>
-__device__ __forceinline__ bool ray_step(const MarchArgs& a, const T* __restrict__ vol, const float4* s_tf, I sy,
-                                         I sz, float ux0, float uy0, float uz0, float tfmax, Ray& s) {
+template <typename Src, typename I, bool SHADE>
+__device__ __forceinline__ bool ray_step(const MarchArgs& a, const typename Src::V* __restrict__ vol,
+                                         const float4* s_tf, I sy, I sz, float ux0, float uy0, float uz0,
+                                         float tfmax, Ray& s) {
     const float t0 = fmaf(s.kf, a.dt, s.tnear);
     if (!(t0 < s.tfar)) return true;
     const float t1 = fmaf(s.kf + 1.0f, a.dt, s.tnear);
     const bool has1 = t1 < s.tfar;
     const float t1c = has1 ? t1 : t0;
-    Stencil S0, S1;
-    load_stencil<T, I, SHADE>(a, vol, sy, sz, fmaf(t0, s.dx, ux0), fmaf(t0, s.dy, uy0), fmaf(t0, s.dz, uz0), S0);
-    load_stencil<T, I, SHADE>(a, vol, sy, sz, fmaf(t1c, s.dx, ux0), fmaf(t1c, s.dy, uy0), fmaf(t1c, s.dz, uz0), S1);
+    typename Src::St S0, S1;
+    Src::template load<I, SHADE>(a, vol, sy, sz, fmaf(t0, s.dx, ux0), fmaf(t0, s.dy, uy0), fmaf(t0, s.dz, uz0), S0);
+    Src::template load<I, SHADE>(a, vol, sy, sz, fmaf(t1c, s.dx, ux0), fmaf(t1c, s.dy, uy0), fmaf(t1c, s.dz, uz0),
+                                 S1);
     s.kf += 1.0f;
-    if (composite_sample<SHADE>(a, s_tf, tfmax, S0, s)) return true;
+    if (composite_sample<Src, SHADE>(a, s_tf, tfmax, S0, s)) return true;
     if (!has1) return true;
     s.kf += 1.0f;
-    return composite_sample<SHADE>(a, s_tf, tfmax, S1, s);
+    return composite_sample<Src, SHADE>(a, s_tf, tfmax, S1, s);
 }
 
 // Cooperative march of one ray by the whole warp, for the last few rays of a
@@ -352,9 +446,10 @@ __device__ __forceinline__ bool ray_step(const MarchArgs& a, const T* __restrict
 // different order -- and the ray stops at the first sample whose opacity
 // reaches term_alpha, or where it leaves the box.  `r` is the same on every
 // lane on entry and on return.
-template <typename T, typename I, bool SHADE>
-__device__ __forceinline__ void coop_ray(const MarchArgs& a, const T* __restrict__ vol, const float4* s_tf, I sy,
-                                         I sz, float ux0, float uy0, float uz0, float tfmax, Ray& r) {
+template <typename Src, typename I, bool SHADE>
+__device__ __forceinline__ void coop_ray(const MarchArgs& a, const typename Src::V* __restrict__ vol,
+                                         const float4* s_tf, I sy, I sz, float ux0, float uy0, float uz0, float tfmax,
+                                         Ray& r) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -364,10 +459,10 @@ __device__ __forceinline__ void coop_ray(const MarchArgs& a, const T* __restrict
         if (vb == 0) return;
         float cr = 0.f, cg = 0.f, cb = 0.f, al = 0.f;
         if (valid) {
-            Stencil S;
-            load_stencil<T, I, SHADE>(a, vol, sy, sz, fmaf(t, r.dx, ux0), fmaf(t, r.dy, uy0), fmaf(t, r.dz, uz0),
-                                      S);
-            al = shade_sample<SHADE>(a, s_tf, tfmax, S, r.dx, r.dy, r.dz, cr, cg, cb);
+            typename Src::St S;
+            Src::template load<I, SHADE>(a, vol, sy, sz, fmaf(t, r.dx, ux0), fmaf(t, r.dy, uy0), fmaf(t, r.dz, uz0),
+                                         S);
+            al = Src::template shade<SHADE>(a, s_tf, tfmax, S, r.dx, r.dy, r.dz, cr, cg, cb);
             if (!(al > 0.0f)) al = 0.0f;
         }
         // incl = prod_{i <= j} (1 - al_i), excl = prod_{i < j} (1 - al_i)
@@ -423,13 +518,13 @@ __device__ __forceinline__ Ray shfl_ray(const Ray& s, int src) {
 // idle lanes take new rays from the global queue together (one atomic per
 // warp), so warps neither wait for their longest ray nor for the slowest
 // warp at the end of the queue.
-template <typename T, typename I, bool SHADE>
+template <typename Src, typename I, bool SHADE>
 __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
     extern __shared__ float4 s_tf[];
     for (int i = threadIdx.x; i < a.ntf; i += blockDim.x) s_tf[i] = a.tf[i];
     __syncthreads();
     const unsigned FULL = 0xffffffffu;
-    const T* __restrict__ vol = static_cast<const T*>(a.pvol);
+    const typename Src::V* __restrict__ vol = static_cast<const typename Src::V*>(a.pvol);
     const int lane = threadIdx.x & 31;
     const int npix = a.W * a.H;
     // the id list never holds more than one entry per pixel
@@ -471,7 +566,7 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
                 do {
                     const int src = __ffs(busy) - 1;
                     Ray r = shfl_ray(s, src);
-                    coop_ray<T, I, SHADE>(a, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+                    coop_ray<Src, I, SHADE>(a, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, r);
                     if (lane == src) {
                         s = r;
                         my_samples += (unsigned long long)s.kf;
@@ -482,7 +577,7 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
                 } while (busy != 0);
                 break;
             }
-            if (s.pix >= 0 && ray_step<T, I, SHADE>(a, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s)) {
+            if (s.pix >= 0 && ray_step<Src, I, SHADE>(a, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s)) {
                 my_samples += (unsigned long long)s.kf;
                 finish_ray(a, s);
                 s.pix = -1;
@@ -524,6 +619,10 @@ struct MarchBatch {
 };
 static_assert(sizeof(MarchBatch) <= 4096, "batched march arguments exceed the 4 KB parameter space");
 
+// Volume kinds of a batch view: the fvn_dtype of a scalar padded copy, or
+// kGrad4 for a gradient volume.
+constexpr int kGrad4 = 16;
+
 template <typename I, bool SHADE>
 __device__ __forceinline__ bool batch_step(const MarchBatchView& bv, const float4* s_tf, Ray& s) {
     const MarchArgs& a = bv.a;
@@ -532,18 +631,21 @@ __device__ __forceinline__ bool batch_step(const MarchBatchView& bv, const float
     const float tfmax = (float)(a.ntf - 1);
     const float4* tf = s_tf + bv.tf_off;
     switch (bv.dtype) {
+        case kGrad4:
+            return ray_step<Grad4Src, I, SHADE>(a, static_cast<const float4*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
+                                                tfmax, s);
         case FVN_U8:
-            return ray_step<uint8_t, I, SHADE>(a, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
-                                               tfmax, s);
+            return ray_step<ScalarSrc<uint8_t>, I, SHADE>(a, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0,
+                                                          uy0, uz0, tfmax, s);
         case FVN_U16:
-            return ray_step<uint16_t, I, SHADE>(a, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0, uy0,
-                                                uz0, tfmax, s);
+            return ray_step<ScalarSrc<uint16_t>, I, SHADE>(a, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0,
+                                                           uy0, uz0, tfmax, s);
         case FVN_F16:
-            return ray_step<__half, I, SHADE>(a, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
-                                              tfmax, s);
+            return ray_step<ScalarSrc<__half>, I, SHADE>(a, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0,
+                                                         uz0, tfmax, s);
         default:
-            return ray_step<float, I, SHADE>(a, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
-                                             tfmax, s);
+            return ray_step<ScalarSrc<float>, I, SHADE>(a, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0,
+                                                        uz0, tfmax, s);
     }
 }
 
@@ -555,18 +657,24 @@ __device__ __forceinline__ void batch_coop(const MarchBatchView& bv, const float
     const float tfmax = (float)(a.ntf - 1);
     const float4* tf = s_tf + bv.tf_off;
     switch (bv.dtype) {
+        case kGrad4:
+            coop_ray<Grad4Src, I, SHADE>(a, static_cast<const float4*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+            break;
         case FVN_U8:
-            coop_ray<uint8_t, I, SHADE>(a, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+            coop_ray<ScalarSrc<uint8_t>, I, SHADE>(a, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
+                                                   tfmax, r);
             break;
         case FVN_U16:
-            coop_ray<uint16_t, I, SHADE>(a, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax,
-                                         r);
+            coop_ray<ScalarSrc<uint16_t>, I, SHADE>(a, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0, uy0,
+                                                    uz0, tfmax, r);
             break;
         case FVN_F16:
-            coop_ray<__half, I, SHADE>(a, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+            coop_ray<ScalarSrc<__half>, I, SHADE>(a, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
+                                                  tfmax, r);
             break;
         default:
-            coop_ray<float, I, SHADE>(a, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+            coop_ray<ScalarSrc<float>, I, SHADE>(a, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
+                                                 tfmax, r);
             break;
     }
 }
@@ -682,13 +790,48 @@ static fvn_status pad_volume(fvn_ctx* ctx, const void* vol, int nx, int ny, int 
     return FVN_OK;
 }
 
-template <typename T, typename I>
-static fvn_status launch_typed(fvn_ctx* ctx, const MarchArgs& a, bool shade, cudaStream_t st) {
+__device__ __forceinline__ int clampi(int v, int n) { return min(max(v, 0), n - 1); }
+
+// Gradient volume over the padded box: (v, Dx, Dy, Dz) per voxel with
+// D = (v[+1] - v[-1]) / 2 along each axis (clamp to edge).  One warp per
+// padded (y, z) row, eight rows per block.
+template <typename T>
+__global__ void __launch_bounds__(256) grad4_volume_kernel(const T* __restrict__ src, int nx, int ny, int nz,
+                                                           float4* __restrict__ dst) {
+    const int px = nx + 2 * kPad, py = ny + 2 * kPad, pz = nz + 2 * kPad;
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= py * pz) return;
+    const int z = row / py, y = row - z * py;
+    const int j = y - kPad, k = z - kPad;
+    const long long sxy = (long long)nx * ny;
+    const T* r0 = src + clampi(k, nz) * sxy + (long long)clampi(j, ny) * nx;
+    const T* rym = src + clampi(k, nz) * sxy + (long long)clampi(j - 1, ny) * nx;
+    const T* ryp = src + clampi(k, nz) * sxy + (long long)clampi(j + 1, ny) * nx;
+    const T* rzm = src + clampi(k - 1, nz) * sxy + (long long)clampi(j, ny) * nx;
+    const T* rzp = src + clampi(k + 1, nz) * sxy + (long long)clampi(j, ny) * nx;
+    float4* d = dst + (long long)row * px;
+    for (int x = threadIdx.x & 31; x < px; x += 32) {
+        const int i = x - kPad;
+        const int ic = clampi(i, nx), im = clampi(i - 1, nx), ip = clampi(i + 1, nx);
+        d[x] = make_float4(load_norm(r0 + ic), 0.5f * (load_norm(r0 + ip) - load_norm(r0 + im)),
+                           0.5f * (load_norm(ryp + ic) - load_norm(rym + ic)),
+                           0.5f * (load_norm(rzp + ic) - load_norm(rzm + ic)));
+    }
+}
+
+template <typename T>
+static fvn_status grad4_volume(fvn_ctx* ctx, const void* vol, int nx, int ny, int nz, void* gvol, cudaStream_t st) {
+    const long long rows = (long long)(ny + 2 * kPad) * (nz + 2 * kPad);
+    grad4_volume_kernel<T><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(static_cast<const T*>(vol), nx, ny, nz,
+                                                                          static_cast<float4*>(gvol));
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+template <typename Src, typename I>
+static fvn_status launch_march(fvn_ctx* ctx, const MarchArgs& a, bool shade, cudaStream_t st) {
     const size_t smem = (size_t)a.ntf * sizeof(float4);
-    // refresh the padded copy of the volume (one pass over it)
-    fvn_status ps = pad_volume<T>(ctx, a.vol, a.nx, a.ny, a.nz, const_cast<void*>(a.pvol), st);
-    if (ps != FVN_OK) return ps;
-    auto kern = shade ? march_kernel<T, I, true> : march_kernel<T, I, false>;
+    auto kern = shade ? march_kernel<Src, I, true> : march_kernel<Src, I, false>;
     if (smem > 48 * 1024)
         FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -700,6 +843,10 @@ static fvn_status launch_typed(fvn_ctx* ctx, const MarchArgs& a, bool shade, cud
     kern<<<grid, 128, smem, st>>>(a);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
+}
+
+static unsigned long long padded_voxels(const fvn_volume* vol) {
+    return (unsigned long long)(vol->nx + 2 * kPad) * (vol->ny + 2 * kPad) * (vol->nz + 2 * kPad);
 }
 
 // Per-view fields of the march arguments: volume size, transfer function,
@@ -775,49 +922,66 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
     a.reject = ids ? nullptr : reject;
     if (ids || reject) FVN_CUDA(ctx, cudaMemsetAsync(rgbam, 0, 5 * sizeof(float) * (size_t)a.plane, st));
     FVN_CUDA(ctx, cudaMemsetAsync(a.ticket, 0, sizeof(int), st));
-    const size_t esize = vol->dtype == FVN_U8 ? 1 : (vol->dtype == FVN_F32 ? 4 : 2);
-    const unsigned long long padded =
-        (unsigned long long)(vol->nx + 2 * kPad) * (vol->ny + 2 * kPad) * (vol->nz + 2 * kPad);
-    if (ctx->pad_bytes < padded * esize) {
-        // growing the padded-volume scratch is a synchronising step
+    const size_t bytes = march_volume_bytes(ctx, vol, mp);
+    if (ctx->pad_bytes < bytes) {
+        // growing the volume scratch is a synchronising step
         FVN_CUDA(ctx, cudaDeviceSynchronize());
         cudaFree(ctx->pad_buf);
         ctx->pad_buf = nullptr;
         ctx->pad_bytes = 0;
-        FVN_CUDA(ctx, cudaMalloc(&ctx->pad_buf, padded * esize));
-        ctx->pad_bytes = padded * esize;
+        FVN_CUDA(ctx, cudaMalloc(&ctx->pad_buf, bytes));
+        ctx->pad_bytes = bytes;
     }
     a.pvol = ctx->pad_buf;
-    const bool big = padded >= (1ull << 31);
+    fvn_status ps = march_volume_prepare(ctx, vol, mp, ctx->pad_buf, st);   // one pass over the volume
+    if (ps != FVN_OK) return ps;
+    const bool big = padded_voxels(vol) >= (1ull << 31);
     const bool shade = mp->shading != 0;
+    if (march_uses_grad4(ctx, vol, mp)) return launch_march<Grad4Src, int>(ctx, a, true, st);
     switch (vol->dtype) {
         case FVN_U8:
-            return big ? launch_typed<uint8_t, long long>(ctx, a, shade, st)
-                       : launch_typed<uint8_t, int>(ctx, a, shade, st);
+            return big ? launch_march<ScalarSrc<uint8_t>, long long>(ctx, a, shade, st)
+                       : launch_march<ScalarSrc<uint8_t>, int>(ctx, a, shade, st);
         case FVN_U16:
-            return big ? launch_typed<uint16_t, long long>(ctx, a, shade, st)
-                       : launch_typed<uint16_t, int>(ctx, a, shade, st);
+            return big ? launch_march<ScalarSrc<uint16_t>, long long>(ctx, a, shade, st)
+                       : launch_march<ScalarSrc<uint16_t>, int>(ctx, a, shade, st);
         case FVN_F16:
-            return big ? launch_typed<__half, long long>(ctx, a, shade, st)
-                       : launch_typed<__half, int>(ctx, a, shade, st);
+            return big ? launch_march<ScalarSrc<__half>, long long>(ctx, a, shade, st)
+                       : launch_march<ScalarSrc<__half>, int>(ctx, a, shade, st);
         default:
-            return big ? launch_typed<float, long long>(ctx, a, shade, st)
-                       : launch_typed<float, int>(ctx, a, shade, st);
+            return big ? launch_march<ScalarSrc<float>, long long>(ctx, a, shade, st)
+                       : launch_march<ScalarSrc<float>, int>(ctx, a, shade, st);
     }
 }
 
-
-size_t padded_volume_bytes(const fvn_volume* vol) {
-    const size_t esize = vol->dtype == FVN_U8 ? 1 : (vol->dtype == FVN_F32 ? 4 : 2);
-    return esize * (size_t)(vol->nx + 2 * kPad) * (vol->ny + 2 * kPad) * (vol->nz + 2 * kPad);
+// Shaded marches read a gradient volume (16 bytes per padded voxel) when the
+// option allows it and it takes at most 4 GiB; the others a padded copy.
+bool march_uses_grad4(const fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp) {
+    return mp->shading != 0 && ctx->march_grad4 != 0 && padded_voxels(vol) * 16ull <= (4ull << 30);
 }
 
-fvn_status pad_volume_impl(fvn_ctx* ctx, const fvn_volume* vol, void* pvol, cudaStream_t st) {
+size_t march_volume_bytes(const fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp) {
+    if (march_uses_grad4(ctx, vol, mp)) return 16 * (size_t)padded_voxels(vol);
+    const size_t esize = vol->dtype == FVN_U8 ? 1 : (vol->dtype == FVN_F32 ? 4 : 2);
+    return esize * (size_t)padded_voxels(vol);
+}
+
+fvn_status march_volume_prepare(fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp, void* buf,
+                                cudaStream_t st) {
+    const bool g4 = march_uses_grad4(ctx, vol, mp);
     switch (vol->dtype) {
-        case FVN_U8: return pad_volume<uint8_t>(ctx, vol->data, vol->nx, vol->ny, vol->nz, pvol, st);
-        case FVN_U16: return pad_volume<uint16_t>(ctx, vol->data, vol->nx, vol->ny, vol->nz, pvol, st);
-        case FVN_F16: return pad_volume<__half>(ctx, vol->data, vol->nx, vol->ny, vol->nz, pvol, st);
-        default: return pad_volume<float>(ctx, vol->data, vol->nx, vol->ny, vol->nz, pvol, st);
+        case FVN_U8:
+            return g4 ? grad4_volume<uint8_t>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st)
+                      : pad_volume<uint8_t>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st);
+        case FVN_U16:
+            return g4 ? grad4_volume<uint16_t>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st)
+                      : pad_volume<uint16_t>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st);
+        case FVN_F16:
+            return g4 ? grad4_volume<__half>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st)
+                      : pad_volume<__half>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st);
+        default:
+            return g4 ? grad4_volume<float>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st)
+                      : pad_volume<float>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st);
     }
 }
 
@@ -838,10 +1002,8 @@ fvn_status march_batch_impl(fvn_ctx* ctx, const BatchMarchView* views, int n, co
         bv.a.ids = v.ids;
         bv.a.count = v.count;
         bv.a.rgbam = v.rgbam;
-        bv.dtype = v.vol->dtype;
-        const unsigned long long voxels =
-            (unsigned long long)(v.vol->nx + 2 * kPad) * (v.vol->ny + 2 * kPad) * (v.vol->nz + 2 * kPad);
-        big = big || voxels >= (1ull << 31);
+        bv.dtype = march_uses_grad4(ctx, v.vol, mp) ? kGrad4 : v.vol->dtype;
+        big = big || padded_voxels(v.vol) >= (1ull << 31);
         int k = 0;   // transfer functions are shared by pointer
         while (k < b.ntfs && !(b.tf[k] == bv.a.tf && b.tf_n[k] == bv.a.ntf)) ++k;
         if (k == b.ntfs) {

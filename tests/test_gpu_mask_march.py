@@ -236,3 +236,28 @@ def test_march_cooperative_finish_sparse_1080p(ctx, fvn, coop):
     march_parity(vol, tf, cam, mp, out, ids=sample, max_amb_frac=0.05)
     seq, ns_seq = run_march(ctx, vol, tf, cam, mp, ids=ids)
     assert abs(ns - ns_seq) <= 0.001 * ns_seq
+
+
+@pytest.mark.parametrize("grad_volume", [0, 1])
+@pytest.mark.parametrize("dtype", ["u8", "f16", "f32"])
+def test_march_stencil_and_gradient_volume(ctx, fvn, grad_volume, dtype):
+    """Shaded marches read either the 32-voxel stencil of the padded copy or
+    the gradient volume (value + central differences per voxel); both meet
+    the oracle's bars, on every voxel type, dense and sparse."""
+    base = wl.value_noise_volume(36, seed=9, base_spacing=8).numpy()
+    vol = {"u8": np.round(base * 255).astype(np.uint8), "f16": base.astype(np.float16),
+           "f32": base.astype(np.float32)}[dtype]
+    tf = wl.transfer_function(6, alpha_max=0.2)
+    cam = wl.orbit_camera(5, 3, width=80, height=56, radius_factor=(0.9, 1.3))
+    mp = wl.MarchParams(shading=1)
+    try:
+        ctx.set_option(fvn.OPT_MARCH_GRADIENT_VOLUME, grad_volume)
+        out, ns = run_march(ctx, vol, tf, cam, mp)
+        march_parity(vol, tf, cam, mp, out, max_amb_frac=0.05)
+        ids = np.arange(0, 80 * 56, 3, dtype=np.int32)
+        outs, _ = run_march(ctx, vol, tf, cam, mp, ids=ids)
+        march_parity(vol, tf, cam, mp, outs, ids=ids, max_amb_frac=0.05)
+    finally:
+        ctx.set_option(fvn.OPT_MARCH_GRADIENT_VOLUME, 1)
+    _, _, ns_ref = om.march(vol, tf, cam, mp)
+    assert abs(ns - ns_ref) <= max(2, ns_ref // 10000)
