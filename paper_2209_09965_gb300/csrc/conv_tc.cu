@@ -237,6 +237,9 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tbase_s;
+    // the prologue above only read weights; the activations come from the previous kernel
+    tc::grid_dep_wait();
+    tc::grid_dep_launch();
     const uint32_t sW_u = tc::smem_addr(sW), sH_u = tc::smem_addr(sH0);
     constexpr uint32_t idesc = F8 ? tc::idesc_e4m3(128, COUT) : tc::idesc_f16(128, COUT);
     uint32_t phase = 0;
@@ -568,6 +571,24 @@ __global__ void amax_f16_kernel(const __half* __restrict__ x, long long n, float
 
 namespace fvn {
 
+// Launch with programmatic stream serialisation: the kernel may start (and
+// run its prologue) while the previous kernel in the stream finishes; it
+// waits for that kernel (griddepcontrol.wait) before touching activations.
+template <typename Arg>
+static cudaError_t launch_pdl(void (*kern)(Arg), dim3 grid, dim3 block, size_t smem, cudaStream_t st, const Arg& arg) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kern, arg);
+}
+
 template <int CIN, int CG, int COUT, int TR, int MODE, int EPI, int CUP, bool F8>
 static fvn_status launch_tc(fvn_ctx* ctx, TcArgs& a, cudaStream_t st) {
     using L = TcLayout<CIN, CG, COUT, TR, MODE, EPI, CUP, F8>;
@@ -596,7 +617,7 @@ static fvn_status launch_tc(fvn_ctx* ctx, TcArgs& a, cudaStream_t st) {
     const int grid = std::min(a.ntiles, ctx->num_sms * per_sm);
     a.error = ctx->d_error;
     if (grid > 0) {
-        kern<<<grid, kThreads, L::bytes, st>>>(a);
+        FVN_CUDA(ctx, launch_pdl(kern, dim3(grid), dim3(kThreads), L::bytes, st, a));
         FVN_LAUNCH_CHECK(ctx);
     }
     return FVN_OK;
@@ -716,7 +737,7 @@ static fvn_status launch_ws(fvn_ctx* ctx, const WsSpec* spec, int n, const ConvW
     a.ntiles = ntiles;
     const int grid = std::min(ntiles, ctx->num_sms * per_sm);
     if (grid > 0) {
-        kern<<<grid, ws::kThreads, L::bytes, st>>>(a);
+        FVN_CUDA(ctx, launch_pdl(kern, dim3(grid), dim3(ws::kThreads), L::bytes, st, a));
         FVN_LAUNCH_CHECK(ctx);
     }
     return FVN_OK;
@@ -790,7 +811,7 @@ static fvn_status launch_ws_headkp(fvn_ctx* ctx, const ReconView* views, int n, 
     if (per_sm < 1) return set_error(ctx, FVN_ERR_CUDA, "head / kernel-prediction kernel does not fit on an SM");
     const int grid = std::min(ntiles, ctx->num_sms * per_sm);
     if (grid > 0) {
-        kern<<<grid, ws::kHkThreads, L::bytes, st>>>(h);
+        FVN_CUDA(ctx, launch_pdl(kern, dim3(grid), dim3(ws::kHkThreads), L::bytes, st, h));
         FVN_LAUNCH_CHECK(ctx);
     }
     return FVN_OK;
@@ -810,6 +831,8 @@ struct UpArgs {
 
 template <bool F8>
 __global__ void __launch_bounds__(256) upsample2_views_kernel(const __grid_constant__ UpArgs u) {
+    tc::grid_dep_wait();
+    tc::grid_dep_launch();
     int i = 0;
     while (i + 1 < u.n && (int)blockIdx.x >= u.im[i + 1].row0) ++i;
     const int r = blockIdx.x - u.im[i].row0;        // chunk * Hl + row
@@ -834,7 +857,7 @@ static fvn_status upsample_views(fvn_ctx* ctx, const void* const* coarse, void* 
     }
     if (rows >= (1ll << 31)) return set_error(ctx, FVN_ERR_ARG, "up-sampling grid too large");
     if (rows > 0) {
-        upsample2_views_kernel<F8><<<(unsigned)rows, 256, 0, st>>>(u);
+        FVN_CUDA(ctx, launch_pdl(upsample2_views_kernel<F8>, dim3((unsigned)rows), dim3(256), 0, st, u));
         FVN_LAUNCH_CHECK(ctx);
     }
     return FVN_OK;

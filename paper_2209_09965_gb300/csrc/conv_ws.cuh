@@ -209,6 +209,9 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
+    // the prologue above only read weights; the activations come from the previous kernel
+    tc::grid_dep_wait();
+    tc::grid_dep_launch();
     bool failed = false;
 
     if (warp == 0) {
@@ -467,6 +470,9 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = *tslot;
+    // the prologue above only read weights; the activations come from the previous kernel
+    tc::grid_dep_wait();
+    tc::grid_dep_launch();
     bool failed = false;
 
     if (warp == 0) {
