@@ -644,20 +644,19 @@ static EncodeTiledFn encode_tiled() {
 }
 
 // Map of a chunk-planar tensor [C / chunk][H][W][16 B] (FP16, or FP8 as
-// bytes) whose box is 16 bytes x 130 pixels x hy rows of one chunk plane:
-// one plane of a stage, read as contiguous 2080-byte rows.
+// bytes) seen as 8-byte elements, whose box is one chunk plane's 128 pixels
+// (256 elements, 2048 contiguous bytes) x hy rows: one plane of a stage.
 static fvn_status make_map(fvn_ctx* ctx, CUtensorMap* m, const void* base, int C, int W, int H, int hy, bool f8) {
     const EncodeTiledFn fn = encode_tiled();
     if (!fn) return set_error(ctx, FVN_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
-    const cuuint64_t eb = f8 ? 1 : 2, cpc = 16 / eb;
-    const cuuint64_t dims[4] = {cpc, (cuuint64_t)W, (cuuint64_t)H, (cuuint64_t)C / cpc};
-    const cuuint64_t strides[3] = {16, (cuuint64_t)W * 16, (cuuint64_t)W * H * 16};
-    const cuuint32_t box[4] = {(cuuint32_t)cpc, (cuuint32_t)ws::kHXW, (cuuint32_t)hy, 1};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    const CUresult r = fn(m, f8 ? CU_TENSOR_MAP_DATA_TYPE_UINT8 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 4,
-                          const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const cuuint64_t cpc = f8 ? 16 : 8;
+    const cuuint64_t dims[3] = {(cuuint64_t)W * 2, (cuuint64_t)H, (cuuint64_t)C / cpc};
+    const cuuint64_t strides[2] = {(cuuint64_t)W * 16, (cuuint64_t)W * H * 16};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * ws::kHXW), (cuuint32_t)hy, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS)
         return set_error(ctx, FVN_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d) for a %d x %d x %d tensor", (int)r, H,
                          W, C);
@@ -730,7 +729,7 @@ static fvn_status launch_ws(fvn_ctx* ctx, const WsSpec* spec, int n, const ConvW
         m.pooled = sp.pooled;
         m.Hl = sp.Hl;
         m.Wl = sp.Wl;
-        m.tiles_x = (sp.Wl + ws::kTW - 1) / ws::kTW;
+        m.tiles_x = (sp.Wl + ws::kTO - 1) / ws::kTO;
         m.tile0 = ntiles;
         ntiles += m.tiles_x * ((sp.Hl + TR - 1) / TR);
     }
@@ -800,7 +799,7 @@ static fvn_status launch_ws_headkp(fvn_ctx* ctx, const ReconView* views, int n, 
         h.W0[i] = v.w;
         m.Hl = Hl;
         m.Wl = Wl;
-        m.tiles_x = (Wl + ws::kTW - 1) / ws::kTW;
+        m.tiles_x = (Wl + ws::kTO - 1) / ws::kTO;
         m.tile0 = ntiles;
         ntiles += m.tiles_x * ((Hl + TR - 1) / TR);
     }

@@ -6,17 +6,17 @@
 // level and the skip tensor of a decoder layer).
 //
 // One persistent CTA of 6 warps per SM (or two, when they fit) runs three
-// roles concurrently over its tiles (TR rows x 128 pixels):
-//   warp 0     producer: TMA loads of the tile's halo (one box of 16 bytes x
-//              130 pixels x TR+2 rows per channel chunk, zero-filled outside
-//              the frame) into a ring of NS shared-memory stages;
+// roles concurrently over its tiles (TR rows x 126 pixels):
+//   warp 0     producer: TMA loads of the tile's halo (one box of 128
+//              pixels x 16 bytes x TR+2 rows per channel chunk, zero-filled
+//              outside the frame) into a ring of NS shared-memory stages;
 //   warp 1     MMA issuer: tcgen05.mma per output row into one of two TMEM
 //              accumulators; commits free the stage and hand the accumulator
 //              to the epilogue;
 //   warps 2-5  epilogue: tcgen05.ld of one pixel per thread, scale, bias,
 //              ReLU, FP16 / FP8 stores, pooling.
 // Activations are chunk-planar ([C / chunk][H][W][16 B]), so each TMA box
-// row is 130 contiguous 16-byte vectors.
+// row is 128 contiguous 16-byte vectors.
 // so loads, MMAs and stores of consecutive tiles overlap.  Every mbarrier wait
 // has an iteration limit; a wait that gives up sets the error flag, and every
 // role then leaves its loop, waits (bounded) for its own operations in
@@ -29,18 +29,15 @@ namespace fvn {
 namespace ws {
 
 constexpr int kThreads = 192;
-constexpr int kTW = 128;              // pixels per tile row = MMA M
-constexpr int kHXW = kTW + 2;
+// A tile row is 126 output pixels computed as one MMA of M = 128 (the last
+// two TMEM lanes are not stored), so that its halo row is 128 pixels = 2048
+// contiguous bytes per channel chunk: one TMA box row (256 8-byte elements).
+// Loading rows of 16-byte elements instead runs the copy engine far below
+// its bandwidth.
+constexpr int kTW = 128;              // MMA M = pixels per TMEM accumulator row
+constexpr int kTO = 126;              // output pixels per tile row
+constexpr int kHXW = 128;             // halo pixels per row
 constexpr uint32_t kLimit = 1u << 26;
-
-__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2, int c3,
-                                            uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, %5}], "
-        "[%6];\n" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
-        : "memory");
-}
 
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int c0, int c1, int c2,
                                             uint32_t bar) {
@@ -84,7 +81,9 @@ struct Layout {
     static constexpr int CPC = 16 / EB;                      // channels per 16-byte chunk
     static constexpr int CH = CIN / CPC;                     // chunks per pixel = K per tap / chunk
     static constexpr int HY = TR + 2;
-    static constexpr uint32_t plane = (HY * kHXW * 16 + 127) / 128 * 128;   // one chunk plane of a stage
+    // one chunk plane of a stage; the MMA rows of the two unstored lanes read
+    // 32 bytes past the last halo row, kept zero
+    static constexpr uint32_t plane = (HY * kHXW * 16 + 32 + 127) / 128 * 128;
     static constexpr uint32_t stage = CH * plane;
     static constexpr size_t w_bytes = 9ull * CIN * COUT * EB;
     static constexpr size_t stage_off = (w_bytes + 1023) / 1024 * 1024;
@@ -183,10 +182,14 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
             sBias[i] = __ldg(a.bias + i);
             sScale[i] = F8 ? __ldg(a.wscale + i) : 1.0f;
         }
-        if (CHG < CH) {
-            for (int s = 0; s < NS; ++s)
+        for (int s = 0; s < NS; ++s) {
+            if (CHG < CH)
                 for (int i = tid; i < (int)((CH - CHG) * L::plane / 16); i += kThreads)
                     reinterpret_cast<uint4*>(sStage + (size_t)s * L::stage + CHG * L::plane)[i] = make_uint4(0, 0, 0, 0);
+            constexpr int slack = (int)(L::plane - HY * kHXW * 16) / 16;
+            for (int i = tid; i < CHG * slack; i += kThreads)
+                reinterpret_cast<uint4*>(sStage + (size_t)s * L::stage + (i / slack) * L::plane +
+                                         HY * kHXW * 16)[i % slack] = make_uint4(0, 0, 0, 0);
         }
     }
     if (tid == 0) {
@@ -233,7 +236,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
 #pragma unroll
                 for (int c = 0; c < CHG; ++c) {
                     const bool first = c < CH0;
-                    tma_load_4d(dst + c * L::plane, first ? &im.map0 : &im.map1, 0, tx * kTW - 1, ty * TR - 1,
+                    tma_load_3d(dst + c * L::plane, first ? &im.map0 : &im.map1, 2 * (tx * kTO - 1), ty * TR - 1,
                                 first ? c : c - CH0, full);
                 }
             }
@@ -316,7 +319,8 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
             const Img& im = a.img[find_img(a, tile)];
             const int lt = tile - im.tile0;
             const int ty = lt / im.tiles_x, tx = lt - ty * im.tiles_x;
-            const int x = tx * kTW + px;
+            const int x = tx * kTO + px;
+            const bool xin = px < kTO && x < im.Wl;
             float prev[COUT];
 #pragma unroll 1
             for (int r = 0; r < TR; ++r) {
@@ -328,7 +332,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
                 for (int c = 0; c < COUT; c += 16) tc::tmem_ld16(tmem + lane_base + col + c, v + c);
 #pragma unroll
                 for (int c = 0; c < COUT; ++c) v[c] = fmaxf(fmaf(v[c], sScale[c], sBias[c]), 0.f);
-                if (y < im.Hl && x < im.Wl)
+                if (y < im.Hl && xin)
                     store_px<COUT, F8>(im.out, (long long)im.Hl * im.Wl, (long long)y * im.Wl + x, v, a.out_q);
                 if (POOL) {
                     if (r & 1) {
@@ -339,7 +343,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
                             sum[c] += __shfl_xor_sync(0xffffffffu, sum[c], 1);
                             sum[c] *= 0.25f;
                         }
-                        if ((lane & 1) == 0 && y < im.Hl && x < im.Wl)
+                        if ((lane & 1) == 0 && y < im.Hl && xin)
                             store_px<COUT, F8>(im.pooled, (long long)(im.Hl >> 1) * (im.Wl >> 1),
                                                (long long)(y >> 1) * (im.Wl >> 1) + (x >> 1), sum, a.pool_q);
                     } else {
@@ -376,7 +380,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
 // arithmetic-heavy and needs the warps to hide its latencies.
 constexpr int kHkEpi = 16;
 constexpr int kHkThreads = 64 + 32 * kHkEpi;
-constexpr int kSpW = kTW + 8;         // sparse window columns: x0 - 4 .. x0 + 131 (16-byte aligned start)
+constexpr int kSpW = kTW + 8;         // sparse window columns from (x0 - 2) rounded down to 4 floats
 
 template <int CIN, int TR, int NS, bool F8>
 struct HkLayout {
@@ -443,10 +447,15 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
             sScale[i] = F8 ? __ldg(a.wscale + i) : 1.0f;
         }
         for (int i = tid; i < 32; i += kHkThreads) sHb[i] = __ldg(h.head_b + i);
-        if (CHG < CH)
-            for (int s = 0; s < NS; ++s)
+        for (int s = 0; s < NS; ++s) {
+            if (CHG < CH)
                 for (int i = tid; i < (int)((CH - CHG) * LC::plane / 16); i += kHkThreads)
                     reinterpret_cast<uint4*>(sStage + (size_t)s * L::stage + CHG * LC::plane)[i] = make_uint4(0, 0, 0, 0);
+            constexpr int slack = (int)(LC::plane - HY * kHXW * 16) / 16;
+            for (int i = tid; i < CHG * slack; i += kHkThreads)
+                reinterpret_cast<uint4*>(sStage + (size_t)s * L::stage + (i / slack) * LC::plane +
+                                         HY * kHXW * 16)[i % slack] = make_uint4(0, 0, 0, 0);
+        }
     }
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -493,11 +502,13 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
                 mbar_expect_tx(full, (uint32_t)CHG * HY * kHXW * 16 + 4u * L::SR * kSpW * 4);
                 const uint32_t dst = tc::smem_addr(sStage + (size_t)s * L::stage);
 #pragma unroll
-                for (int c = 0; c < CHG; ++c) tma_load_4d(dst + c * LC::plane, &im.map0, 0, tx * kTW - 1, ty * TR - 1, c, full);
+                for (int c = 0; c < CHG; ++c)
+                    tma_load_3d(dst + c * LC::plane, &im.map0, 2 * (tx * kTO - 1), ty * TR - 1, c, full);
                 const uint32_t sp = dst + LC::stage;
+                const int xs = (tx * kTO - 2) & ~3;   // 16-byte aligned start of the window
 #pragma unroll
                 for (int p = 0; p < 4; ++p)   // planes R, G, B, M (= 4) of the sparse frame
-                    tma_load_3d(sp + p * L::sp_plane, &h.sp[im_i], tx * kTW - 4, ty * TR - 2, p < 3 ? p : 4, full);
+                    tma_load_3d(sp + p * L::sp_plane, &h.sp[im_i], xs, ty * TR - 2, p < 3 ? p : 4, full);
             }
             if (failed)
                 for (int j = (i > NS ? i - NS : 0); j < i; ++j) wait(full0 + 8 * (j % NS), (j / NS) & 1);
@@ -602,7 +613,8 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
             const Img& im = a.img[im_i];
             const int lt = tile - im.tile0;
             const int ty = lt / im.tiles_x, tx = lt - ty * im.tiles_x;
-            const int x = tx * kTW + px;
+            const int x = tx * kTO + px;
+            const int off = (tx * kTO - 2) - ((tx * kTO - 2) & ~3);   // window column of x0 - 2
             const int H0 = h.H0[im_i], W0 = h.W0[im_i];
             const long long plane = (long long)H0 * W0;
             const float* spR = reinterpret_cast<const float*>(sStage + (size_t)s * L::stage + LC::stage);
@@ -623,7 +635,7 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
 #pragma unroll
                 for (int k = 0; k < 25; ++k) {
                     const float e = __expf(hd[3 + k] - mx);
-                    const int o = (r + k / 5) * kSpW + px + 2 + k % 5;
+                    const int o = (r + k / 5) * kSpW + off + px + k % 5;
                     const float wm = e * spR[3 * (L::sp_plane / 4) + o];
                     es += e;
                     den += wm;
@@ -638,7 +650,7 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
                     k2 = n2 / den;
                 }
                 const float al = 1.0f / (1.0f + __expf(-hd[28]));
-                if (y < H0 && x < W0) {
+                if (y < H0 && px < kTO && x < W0) {
                     float* o = h.rgb[im_i] + (long long)y * W0 + x;
                     o[0] = fmaf(al, k0 - hd[0], hd[0]);
                     o[plane] = fmaf(al, k1 - hd[1], hd[1]);
