@@ -541,6 +541,12 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
                     failed = true;
                     break;
                 }
+                // the previous tile's head first: its kernel prediction (the
+                // slow part of the epilogue) then overlaps this tile's conv
+                if (i >= 1 && !head(i - 1)) {
+                    failed = true;
+                    break;
+                }
                 tc::fence_after_sync();
                 const uint64_t a0 = tc::smem_desc(tc::smem_addr(sStage + (size_t)s * L::stage), LC::plane, 128);
                 if (F8) tc::mma_e4m3(tmem + (uint32_t)(acc * LC::acc), z0, b0, idesc_z, 0);
@@ -561,11 +567,6 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
                 }
                 tc::mma_commit(bars + NS + s);
                 tc::mma_commit(bars + 2 * NS + acc);
-                if (i >= 1 && !head(i - 1)) {
-                    failed = true;
-                    ++i;   // the conv of this tile was issued
-                    break;
-                }
             }
             if (!failed && i >= 1 && !head(i - 1)) failed = true;
             // every MMA finished before the TMEM is freed
