@@ -375,9 +375,11 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
 // weights times the sparse samples' mask, normalised by their sum (the
 // direct RGB where no sample is in the window), blend by sigmoid(logit).
 // The sparse R, G, B, M planes around the tile (TR + 4 rows x 136 columns,
-// zero outside the frame) arrive by TMA with the halo.  16 epilogue warps
-// (four per TMEM lane quadrant, one tile row each): the kernel prediction is
-// arithmetic-heavy and needs the warps to hide its latencies.
+// zero outside the frame) arrive by TMA with the halo.  16 epilogue warps in
+// two groups that take alternate tiles (ping-pong: while one group waits for
+// its head MMA the other runs its kernel prediction); within a group two
+// warps per TMEM lane quadrant, each on half of the tile's rows.  Each group
+// has its own conv accumulator, head accumulator and head A buffer.
 constexpr int kHkEpi = 16;
 constexpr int kHkThreads = 64 + 32 * kHkEpi;
 constexpr int kSpW = kTW + 8;         // sparse window columns from (x0 - 2) rounded down to 4 floats
@@ -392,15 +394,16 @@ struct HkLayout {
     static constexpr size_t hb_off = (w_bytes + 127) / 128 * 128;   // head B: [2][32][16 B]
     static constexpr size_t stage_off = (hb_off + 2 * 32 * 16 + 1023) / 1024 * 1024;
     static constexpr size_t zero_off = stage_off + (size_t)NS * stage;
-    static constexpr size_t ha_off = zero_off + 2 * kTW * 16;      // head A: [TR][2][128][16 B]
-    static constexpr size_t bias_off = ha_off + (size_t)TR * 2 * kTW * 16;
+    static constexpr size_t ha_bytes = (size_t)TR * 2 * kTW * 16;   // head A of one group: [TR][2][128][16 B]
+    static constexpr size_t ha_off = zero_off + 2 * kTW * 16;
+    static constexpr size_t bias_off = ha_off + 2 * ha_bytes;
     static constexpr size_t bar_off = bias_off + (16 + 16 + 32) * 4;
-    static constexpr size_t bytes = bar_off + (2 * NS + 6) * 8 + 16;
+    static constexpr size_t bytes = bar_off + (2 * NS + 8) * 8 + 16;
     static constexpr uint32_t acc = C::acc;                         // conv accumulator columns
-    static constexpr uint32_t head_col = 2 * acc;                   // head outputs: TR x 32 columns
-    static constexpr uint32_t tmem_cols = head_col + TR * 32 <= 256 ? 256 : 512;
-    static_assert(head_col + TR * 32 <= 512, "TMEM");
-    static_assert(TR % (kHkEpi / 4) == 0, "rows split evenly over the epilogue warp groups");
+    static constexpr uint32_t head_col = 2 * acc;                   // head outputs: 2 x TR x 32 columns
+    static constexpr uint32_t tmem_cols = head_col + 2 * TR * 32 <= 256 ? 256 : 512;
+    static_assert(head_col + 2 * TR * 32 <= 512, "TMEM");
+    static_assert(TR % (kHkEpi / 8) == 0, "rows split evenly over the warps of a group");
 };
 
 struct HkArgs {
@@ -413,7 +416,7 @@ struct HkArgs {
 };
 
 template <int CIN, int CHG, int TR, int NS, bool F8>
-__global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __grid_constant__ HkArgs h) {
+__global__ void __launch_bounds__(kHkThreads, 1) conv3x3_ws_headkp_kernel(const __grid_constant__ HkArgs h) {
     using L = HkLayout<CIN, TR, NS, F8>;
     using LC = typename L::C;
     constexpr int CH = LC::CH, HY = LC::HY, COUT = 16;
@@ -425,10 +428,10 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
     float* sScale = sBias + 16;
     float* sHb = sBias + 32;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::bar_off);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 6);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 8);
     const uint32_t full0 = tc::smem_addr(bars), empty0 = full0 + 8 * NS;
     const uint32_t tfull0 = full0 + 16 * NS, tempty0 = tfull0 + 16;
-    const uint32_t hready = tempty0 + 16, hdone = hready + 8;
+    const uint32_t hready0 = tempty0 + 16, hdone0 = hready0 + 16;   // per group
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     {
@@ -458,16 +461,17 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
         }
     }
     if (tid == 0) {
+        constexpr int GW = kHkEpi / 2;                 // warps of one epilogue group
         for (int s = 0; s < NS; ++s) {
             tc::mbar_init(bars + s, 1);
-            tc::mbar_init(bars + NS + s, 1 + kHkEpi);  // conv MMAs done + every epilogue warp done with its samples
+            tc::mbar_init(bars + NS + s, 1 + GW);      // conv MMAs done + the tile's group done with its samples
         }
         for (int k = 0; k < 2; ++k) {
             tc::mbar_init(bars + 2 * NS + k, 1);
-            tc::mbar_init(bars + 2 * NS + 2 + k, kHkEpi);
+            tc::mbar_init(bars + 2 * NS + 2 + k, GW);
+            tc::mbar_init(bars + 2 * NS + 4 + k, GW);  // head A of group k written
+            tc::mbar_init(bars + 2 * NS + 6 + k, 1);   // head MMA of group k done
         }
-        tc::mbar_init(bars + 2 * NS + 4, kHkEpi);     // head A written by all epilogue warps
-        tc::mbar_init(bars + 2 * NS + 5, 1);          // head MMA done
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 1) {
@@ -523,15 +527,17 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
             const uint64_t b0 = tc::smem_desc(tc::smem_addr(sW), NB * 16, 128);
             const uint64_t z0 = tc::smem_desc(tc::smem_addr(smem + L::zero_off), kTW * 16, 128);
             const uint64_t hb = tc::smem_desc(tc::smem_addr(smem + L::hb_off), 32 * 16, 128);
-            auto head = [&](int t) -> bool {   // head MMA of the tile with index t
-                if (!wait(hready, t & 1)) return false;
+            auto head = [&](int t) -> bool {   // head MMA of the tile with index t (group t & 1)
+                const int g = t & 1;
+                if (!wait(hready0 + 8 * g, (t >> 1) & 1)) return false;
                 tc::fence_after_sync();
 #pragma unroll 1
                 for (int r = 0; r < TR; ++r) {
-                    const uint64_t ad = tc::smem_desc(tc::smem_addr(smem + L::ha_off + (size_t)r * 2 * kTW * 16), kTW * 16, 128);
-                    tc::mma_f16(tmem + L::head_col + 32 * r, ad, hb, idesc_h, 0);
+                    const uint64_t ad = tc::smem_desc(
+                        tc::smem_addr(smem + L::ha_off + g * L::ha_bytes + (size_t)r * 2 * kTW * 16), kTW * 16, 128);
+                    tc::mma_f16(tmem + L::head_col + g * TR * 32 + 32 * r, ad, hb, idesc_h, 0);
                 }
-                tc::mma_commit(bars + 2 * NS + 5);
+                tc::mma_commit(bars + 2 * NS + 6 + g);
                 return true;
             };
             int i = 0;
@@ -572,18 +578,24 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
             // every MMA finished before the TMEM is freed
             if (i > 0) {
                 wait(tfull0 + 8 * ((i - 1) & 1), ((i - 1) >> 1) & 1);
-                if (!failed) wait(hdone, (i - 1) & 1);
+                if (!failed) wait(hdone0 + 8 * ((i - 1) & 1), ((i - 1) >> 1) & 1);
             }
         }
     } else {
-        // ---- epilogue: warp group g (4 warps, one per lane quadrant) takes rows [g RG, (g + 1) RG) ----
-        constexpr int RG = TR / (kHkEpi / 4);
-        const int q = warp & 3, g = (warp - 2) >> 2;
+        // ---- epilogue: group G (8 warps) takes the tiles i with i % 2 == G; in a
+        // group, sub-group u (4 warps, one per lane quadrant) takes rows [u RG, (u + 1) RG) ----
+        constexpr int RG = TR / (kHkEpi / 8);
+        const int e = warp - 2, G = e >> 3, u = (e >> 2) & 1;
+        const int q = warp & 3;
         const int px = q * 32 + lane;
         const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-        const int r_lo = g * RG, r_hi = r_lo + RG;
+        const int r_lo = u * RG, r_hi = r_lo + RG;
+        const uint32_t hready = hready0 + 8 * G, hdone = hdone0 + 8 * G;
+        unsigned char* ha_base = smem + L::ha_off + G * L::ha_bytes;
+        const uint32_t head_col = L::head_col + G * TR * 32;
         int i = 0;
         for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++i) {
+            if ((i & 1) != G) continue;
             const int s = i % NS, acc = i & 1;
             if (!wait(tfull0 + 8 * acc, (i >> 1) & 1)) {
                 failed = true;
@@ -597,7 +609,7 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
                 tc::tmem_ld16(tmem + lane_base + acc * LC::acc + COUT * (TR + 1 - r), v);
 #pragma unroll
                 for (int c = 0; c < 16; ++c) v[c] = fmaxf(fmaf(v[c], sScale[c], sBias[c]), 0.f);
-                unsigned char* ha = smem + L::ha_off + (size_t)r * 2 * kTW * 16;
+                unsigned char* ha = ha_base + (size_t)r * 2 * kTW * 16;
                 *reinterpret_cast<uint4*>(ha + px * 16) = pack8h(v);
                 *reinterpret_cast<uint4*>(ha + (kTW + px) * 16) = pack8h(v + 8);
             }
@@ -605,7 +617,7 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(hready);
-            if (!wait(hdone, i & 1)) {
+            if (!wait(hdone, (i >> 1) & 1)) {
                 failed = true;
                 break;
             }
@@ -623,8 +635,8 @@ __global__ void __launch_bounds__(kHkThreads) conv3x3_ws_headkp_kernel(const __g
             for (int r = r_lo; r < r_hi; ++r) {
                 const int y = ty * TR + r;
                 float hd[32];
-                tc::tmem_ld16(tmem + lane_base + L::head_col + 32 * r, hd);
-                tc::tmem_ld16(tmem + lane_base + L::head_col + 32 * r + 16, hd + 16);
+                tc::tmem_ld16(tmem + lane_base + head_col + 32 * r, hd);
+                tc::tmem_ld16(tmem + lane_base + head_col + 32 * r + 16, hd + 16);
 #pragma unroll
                 for (int j = 0; j < 29; ++j) hd[j] += sHb[j];
                 float mx = hd[3];
