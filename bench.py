@@ -60,6 +60,9 @@ NET_FLOPS_PER_PX = 2 * 9 * (5 * 16 + 16 * 16 + 48 * 16 + 16 * 16) + 2 * 9 * (16 
     + 2 * 9 * (32 * 64 + 64 * 64) // 16 + 2 * 16 * 29
 # FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+# DRAM bytes (read + write) of one sparse-march launch of this workload, from
+# an ncu capture of the current kernel (python bench.py --profile, second frame)
+MARCH_DRAM_BYTES = 234.66e6 + 19.01e6
 
 
 def dist_env():
@@ -512,6 +515,30 @@ def main():
     net_tflops = NET_FLOPS_PER_PX * W * H / recon_avg_s / 1e12
     mask_gbs = (W * H + 4 * nrays / nq) / mask_avg_s / 1e9
 
+    # ---- the same frames with the FP8 network (scales from frame 0) ----------
+    fp8_info = None
+    try:
+        cam, fov = frames[0]
+        ctx.render(vol, tf, cam, fov, mp, rgb, rgbam_out=rgbam)
+        ctx.calibrate_fp8(rgbam, W, H, reset=True)
+        f8_ms, f8_psnr = [], []
+        for i in range(min(args.steps, ORBIT)):
+            cam, fov = frames[i % ORBIT]
+            flush.fill_(float(i))
+            e0, e1 = ev(), ev()
+            e0.record(stream)
+            ctx.render(vol, tf, cam, fov, mp, rgb, precision=fvn.PREC_FP8)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            f8_ms.append(e0.elapsed_time(e1))
+            ctx.march(vol, tf, cam, mp, dense)
+            f8_psnr.append(psnr_t(rgb, dense[:3]))
+        fp8_info = {"frames_per_s": len(f8_ms) / (sum(f8_ms) / 1000.0), "ms_per_frame": float(np.mean(f8_ms)),
+                    "psnr_vs_dense_db": {"mean": float(np.mean(f8_psnr)), "min": float(np.min(f8_psnr))},
+                    "note": "fvn_render with the FP8 E4M3 network, activation scales calibrated on frame 0"}
+    except Exception as exc:   # reported, not part of the metric
+        fp8_info = {"error": str(exc)[:200]}
+
     # ---- the frame captured once in a CUDA graph and replayed ----------------
     graph_info = None
     try:
@@ -537,7 +564,8 @@ def main():
             torch.cuda.synchronize()
             g_ms.append(e0.elapsed_time(e1))
         graph_info = {"frames": len(g_ms), "ms_per_frame": float(np.median(g_ms)),
-                      "note": "one orbit frame captured with torch.cuda.graph and replayed; L2 written between replays"}
+                      "note": "orbit frame 0 captured with torch.cuda.graph and replayed; L2 written between "
+                              "replays"}
     except Exception as exc:   # capture is an optimisation report, not part of the metric
         graph_info = {"error": str(exc)[:200]}
 
@@ -590,10 +618,13 @@ def main():
             "rays_per_frame": nrays / nq, "sampled_fraction": nrays / nq / (W * H),
             "roofline": {"bound": "alu", "kernel": "march_kernel (sparse)", "achieved": achieved,
                          "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                         "traffic": None,
-                         "note": f"{MARCH_FLOPS_PER_SAMPLE} FP32 flops per shaded sample over the FP32 peak from unit "
-                                 "counts (152 SM x 128 lanes x 2 x 2.07 GHz); the kernel is issue-bound on its "
-                                 "32-voxel gathers (L1-resident volume)"},
+                         "traffic": MARCH_DRAM_BYTES,
+                         "note": f"{MARCH_FLOPS_PER_SAMPLE} FP32 flops per shaded sample (trilinear value, central "
+                                 "differences of the trilinear field, TF, Phong, compositing) over the FP32 peak "
+                                 "from unit counts (152 SM x 128 lanes x 2 x 2.07 GHz); the kernel reads 8 "
+                                 "16-byte gradient-volume voxels per sample and is bound by issuing them (L1 and "
+                                 "issue 60-75 % busy, DRAM < 4 %); traffic = DRAM read + write of one launch "
+                                 "(ncu)"},
             "roofline_stages": {
                 "reconstruct": {"bound": "tensor", "achieved": net_tflops, "peak": tc_peak, "unit": "TFLOP/s",
                                 "frac": net_tflops / tc_peak, "flops_per_px": NET_FLOPS_PER_PX,
@@ -603,10 +634,12 @@ def main():
             "autotune": tuned,
             "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": int(tf_np.nbytes),
                     "d2h_bytes_per_step": int(3 * H * W * 4)},
-            # per frame: mask, volume padding, march, 10 convolutions (the last with the
-            # head / KP / blend fused on the tcgen05 path; a separate KP kernel otherwise)
-            "gpu_launches": (13 if (tuned is None or tuned["conv"]["conv"] == "tcgen05") else 14) * args.steps,
+            # per frame: mask, gradient volume, march, then on the tcgen05 path 10
+            # convolutions + 2 up-sampling passes (head / KP / blend in the last
+            # convolution); on the mma.sync path 10 convolutions + a KP kernel
+            "gpu_launches": (15 if (tuned is None or tuned["conv"]["conv"] == "tcgen05") else 14) * args.steps,
             "cuda_graph": graph_info,
+            "fp8": fp8_info,
             "multiview": multiview,
             "clocks": clocks,
         }
