@@ -366,8 +366,9 @@ def run_multiview(ctx, fvn, wl, dev, steps, warmup, flush):
             "gsamples_per_s_end_to_end": samples / (mean_ms / 1000.0) / 1e9, "samples_per_batch": samples,
             "psnr_720p_views_vs_dense_db": [float(x) for x in psnrs],
             "graph_ms_per_batch": graph_ms,
-            "launches_per_batch": 14,
-            "note": "launches: 1 mask + compaction, 2 volume padding, 1 persistent march, 10 network layers"}
+            "launches_per_batch": 16,
+            "note": "launches: 1 mask + compaction, 2 volume preparations (gradient volume / padded copy), "
+                    "1 persistent march, 10 network layers + 2 up-sampling passes, each over all views"}
 
 
 def main():

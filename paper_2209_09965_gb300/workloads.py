@@ -24,7 +24,8 @@ Recipes (all seeded, all deterministic on CPU):
   an orbit eye along the image x axis, looking at the same target.
 * ``multiview_views`` / ``multiview_volumes``: 16 views (4 stereo pairs at
   2064x2208, 4 at 1280x720, 4 at 3840x2160) over a 512^3 float16 noise volume
-  and a 1024^3 uint8 blob volume, alternating between the two.
+  and a 1024^3 uint8 blob volume, alternating between the two (TF peak
+  opacities 0.08 and 0.15).
 * ``net_weights``: Kaiming-uniform weights, zero biases, in the flat order
   given by ``NET_LAYERS``.
 
@@ -310,8 +311,9 @@ def multiview_volumes(device="cpu", n_noise: int = 512, n_blobs: int = 1024, see
 
 
 def multiview_transfer_functions(seed: int = 50):
-    """Transfer functions of the noise and the blob volume."""
-    return transfer_function(seed + 1000, alpha_max=0.08), transfer_function(seed + 2000, alpha_max=0.3)
+    """Transfer functions of the noise and the blob volume (peak opacities
+    inside the range the network is trained on)."""
+    return transfer_function(seed + 1000, alpha_max=0.08), transfer_function(seed + 2000, alpha_max=0.15)
 
 
 def multiview_views(seed: int = 50, frame: int = 0, sizes=MULTIVIEW_SIZES, nframes: int = 64):
