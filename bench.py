@@ -227,7 +227,8 @@ def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.
     """Frame time of the march vs a uniform sampling density tau (fovea and
     falloff off, so C_max = tau): mask + compaction + sparse march, mask +
     naive rejection (full-frame kernel, masked pixels skipped in place), and
-    the ideal tau x dense-march time.  One JSON line per density."""
+    the ideal tau x dense-march time, each with its launch shapes autotuned.
+    One JSON line per density."""
     import torch
     import __graft_entry__ as ge
     ge.build()
@@ -256,6 +257,8 @@ def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.
 
     cams = [wl.orbit_camera(2, f * (ORBIT // nframes), nframes=ORBIT, width=W, height=H,
                             radius_factor=(0.85, 1.75)) for f in range(nframes)]
+    from paper_2209_09965_gb300 import autotune
+    autotune.tune_march(ctx, vol, tf, cams[0], mp, out)      # dense and naive-rejection launch shapes
     for cam in cams[:2]:                                    # warm-up
         ctx.march(vol, tf, cam, mp, out)
     dense = sum(timed(lambda: ctx.march(vol, tf, cam, mp, out)) for cam in cams)
@@ -263,6 +266,10 @@ def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.
     for tau in densities:
         comp = rej = 0.0
         frac = 0.0
+        fov0 = wl.Foveation(focal_px=(W / 2, H / 2), fovea_radius=0.0, falloff_sigma=0.0, p_base=tau, seed=2,
+                            frame=0)
+        ctx.make_mask(fov0, W, H, mask, ids, count)
+        autotune.tune_march(ctx, vol, tf, cams[0], mp, out, ids=ids, count=count)   # sparse launch shapes
         for i, cam in enumerate(cams):
             fov = wl.Foveation(focal_px=(W / 2, H / 2), fovea_radius=0.0, falloff_sigma=0.0, p_base=tau, seed=2,
                                frame=i)

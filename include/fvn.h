@@ -115,7 +115,8 @@ fvn_status fvn_destroy(fvn_ctx* ctx);
  *  FVN_OPT_MARCH_COOP: once at most this many lanes (0..32) of a sparse-march
  *      warp still hold rays, the warp marches each of them with all 32 lanes
  *      (32 samples per step, composited by a product scan of the
- *      transmittances; the same result up to FP32 rounding order); 0 = never.
+ *      transmittances; the same result up to FP32 rounding order); 0 = never;
+ *      32 = every ray, a warp taking one ray at a time from the queue.
  *  FVN_OPT_MARCH_REFILL_DENSE, FVN_OPT_MARCH_BLOCKS_PER_SM_DENSE,
  *  FVN_OPT_MARCH_COOP_DENSE: the same for the dense march (ids == NULL).
  *  FVN_OPT_MARCH_GRADIENT_VOLUME: 1 (default) = a shaded march first writes a

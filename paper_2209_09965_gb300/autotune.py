@@ -36,7 +36,7 @@ def _time(fn, reps=3):
 
 
 def tune_march(ctx: fvn.Context, vol, tf, cam, mp, rgbam, ids=None, count=None,
-               refills=(1, 8, 16, 24), blocks=(0, 4), coops=(0, 2, 4, 8)):
+               refills=(1, 8, 16, 24), blocks=(0, 4), coops=(0, 2, 4, 8, 16, 32)):
     """Pick (refill threshold, cooperative-finish threshold, CTAs per SM) for
     the march of this frame: the sparse march when ids are given, the dense
     march otherwise."""

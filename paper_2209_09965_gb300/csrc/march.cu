@@ -536,7 +536,24 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
     unsigned long long my_samples = 0;
     Ray s;
     s.pix = -1;
-    bool exhausted = false;   // warp-uniform: the queue has run dry
+    if (a.coop_below >= 32) {
+        // fully cooperative mode (few, long rays): a warp takes one ray at a
+        // time and marches it with all 32 lanes
+        for (;;) {
+            int r = 0;
+            if (lane == 0) r = atomicAdd(a.ticket, 1);
+            r = __shfl_sync(FULL, r, 0);
+            if (r >= nrays) break;
+            if (!start_ray(a, r, npix, s)) continue;   // every lane sets up the same ray
+            if (s.tfar > -INFINITY) coop_ray<Src, I, SHADE>(a, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s);
+            if (lane == 0) {
+                my_samples += (unsigned long long)s.kf;
+                finish_ray(a, s);
+            }
+        }
+        s.pix = -1;
+    }
+    bool exhausted = a.coop_below >= 32;   // warp-uniform: the queue has run dry
     for (;;) {
         if (!exhausted) {
             const unsigned idle = __ballot_sync(FULL, s.pix < 0);
