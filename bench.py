@@ -62,7 +62,7 @@ NET_FLOPS_PER_PX = 2 * 9 * (5 * 16 + 16 * 16 + 48 * 16 + 16 * 16) + 2 * 9 * (16 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one sparse-march launch of this workload, from
 # an ncu capture of the current kernel (python bench.py --profile, second frame)
-MARCH_DRAM_BYTES = 234.66e6 + 19.01e6
+MARCH_DRAM_BYTES = 236.48e6 + 18.86e6
 
 
 def dist_env():
@@ -631,7 +631,7 @@ def main():
                                  "differences of the trilinear field, TF, Phong, compositing) over the FP32 peak "
                                  "from unit counts (152 SM x 128 lanes x 2 x 2.07 GHz); the kernel reads 8 "
                                  "16-byte gradient-volume voxels per sample and is bound by issuing them (L1 and "
-                                 "issue 60-75 % busy, DRAM < 4 %); traffic = DRAM read + write of one launch "
+                                 "issue ~60-70 % busy, DRAM < 4 %); traffic = DRAM read + write of one launch "
                                  "(ncu)"},
             "roofline_stages": {
                 "reconstruct": {"bound": "tensor", "achieved": net_tflops, "peak": tc_peak, "unit": "TFLOP/s",
