@@ -24,10 +24,25 @@
  *    t_k = t_near + k dt for every k >= 0 with t_k < t_far (strict).
  *  - 1-D RGBA transfer function of ntf entries: continuous index v (ntf - 1),
  *    linear between entries.
- *  - Phong with a headlight (L = V = -dir, so H = L): gradient by central
- *    differences of the trilinear field at +-1 voxel, n = -g/|g|,
+ *  - shading 1, Phong with a headlight (L = V = -dir, so H = L): gradient by
+ *    central differences of the trilinear field at +-1 voxel, n = -g/|g|,
  *    c' = clamp(c (0.2 + 0.7 |n.L|) + 0.3 |n.L|^32, 0, 1); |g| < 1e-6 keeps c.
  *    Samples with alpha = 0 contribute nothing and are not shaded.
+ *  - shading 2, the paper's global shadows ("Foveated Rendering": one shadow
+ *    ray per sample towards the light, at a quarter of the main sample
+ *    rate): a directional light along the unit vector L (world and voxel
+ *    space share directions: the box is scaled uniformly).  From a sample
+ *    point p the shadow ray takes samples at s_j = j ds, j = 1, 2, ..., with
+ *    ds = rate dt, while s_j < s_exit (where p + s L leaves the box).  Each
+ *    stands for rate main steps of its TF opacity, the last one for the part
+ *    of its step left inside the box:
+ *        T = prod_j (1 - a_j)^(rate min(1, (s_exit - s_j) / ds)),
+ *    so T is continuous in s_exit.  The shadow ray stops once T < 2^-14 (the
+ *    light it could still carry then moves no output channel by as much).
+ *    H = |L - dir|; with |g| >= 1e-6,
+ *        c' = clamp(c (0.2 + 0.7 T |n.L|) + 0.3 T |n.H|^32, 0, 1),
+ *    otherwise c' = clamp(c (0.2 + 0.7 T), 0, 1); no specular term where
+ *    |L - dir| < 1e-12.
  *  - Front-to-back compositing with non-premultiplied colour:
  *    C += (1 - A) a c', A += (1 - A) a; stop after a sample once A >= term.
  *    Output RGB = C + (1 - A) bg, alpha = A, mask channel = 1.  Rays that miss
@@ -38,7 +53,9 @@
  * bit 2: a shaded sample had |g| < 1e-5) mark pixels where an FP32
  * implementation of the same definition may legitimately take the other side
  * of a discontinuity.  count_shift / term_override let a test compute the
- * alternative result for such pixels.
+ * alternative result for such pixels.  Shadow rays need no flag: T is
+ * continuous in the exit distance, and where FP32 and FP64 disagree on
+ * stopping a shadow ray, T differs by less than the 2^-14 cutoff.
  */
 #include <math.h>
 #include <stdint.h>
@@ -96,6 +113,44 @@ static double trilinear(const or_vol* v, double px, double py, double pz) {
     return acc;
 }
 
+/* TF lookup at value val: col[4] = linear interpolation at index val (ntf - 1). */
+static void tf_sample(const float* tf, int ntf, double val, double* col) {
+    double x = val * (double)(ntf - 1);
+    double fi = floor(x);
+    int i = (int)fi;
+    if (i < 0) i = 0;
+    if (i > ntf - 2) i = ntf - 2;
+    double fr = x - (double)i;
+    for (int ch = 0; ch < 4; ++ch)
+        col[ch] = (double)tf[4 * i + ch] * (1.0 - fr) + (double)tf[4 * (i + 1) + ch] * fr;
+}
+
+#define SHADOW_CUTOFF (1.0 / 16384.0)
+
+/* Transmittance towards a directional light L (unit) from the voxel-space
+ * point p, by the shadow ray defined in the header. */
+static double shadow_transmittance(const or_vol* v, const float* tf, int ntf, const double* p, const double* L,
+                                   double dt, int rate) {
+    double ds = (double)rate * dt;
+    double se = INFINITY;
+    for (int a = 0; a < 3; ++a) {
+        if (L[a] == 0.0) continue;
+        double s = ((L[a] > 0.0 ? (double)v->n[a] : 0.0) - p[a]) / L[a];
+        if (s < se) se = s;
+    }
+    double T = 1.0;
+    for (int64_t j = 1; (double)j * ds < se; ++j) {
+        double s = (double)j * ds;
+        double col[4];
+        tf_sample(tf, ntf, trilinear(v, p[0] + s * L[0], p[1] + s * L[1], p[2] + s * L[2]), col);
+        double e = (se - s) / ds;
+        if (e > 1.0) e = 1.0;
+        if (col[3] > 0.0) T *= pow(1.0 - col[3], (double)rate * e);
+        if (T < SHADOW_CUTOFF) break;
+    }
+    return T;
+}
+
 static void normalize3(double* a) {
     double l = sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
     a[0] /= l; a[1] /= l; a[2] /= l;
@@ -131,9 +186,18 @@ static void setup_camera(const double* cam, int W, int H, const or_vol* v, or_ca
 }
 
 /* One ray; returns the number of classified samples. */
+typedef struct {
+    double dt, term, bg[3];
+    int shading;
+    double L[3];      /* shading 2: unit direction towards the light */
+    int rate;         /* shading 2: shadow step = rate dt */
+} or_mp;
+
 static int64_t march_ray(const or_vol* v, const float* tf, int ntf, const or_cam* c, int px, int py,
-                         double dt, double term, const double* bg, int shading, int count_shift,
-                         double* rgba, int* amb) {
+                         const or_mp* m, double term, int count_shift, double* rgba, int* amb) {
+    const double dt = m->dt;
+    const double* bg = m->bg;
+    const int shading = m->shading;
     double sx = (2.0 * (px + 0.5) / c->W - 1.0) * c->tanh_ * c->aspect;
     double sy = (1.0 - 2.0 * (py + 0.5) / c->H) * c->tanh_;
     double d[3];
@@ -171,16 +235,8 @@ static int64_t march_ray(const or_vol* v, const float* tf, int ntf, const or_cam
     for (k = 0; k < nsamp; ++k) {
         double t = tnear + (double)k * dt;
         double p[3] = {c->o[0] + t * d[0], c->o[1] + t * d[1], c->o[2] + t * d[2]};
-        double val = trilinear(v, p[0], p[1], p[2]);
-        double x = val * (double)(ntf - 1);
-        double fi = floor(x);
-        int i = (int)fi;
-        if (i < 0) i = 0;
-        if (i > ntf - 2) i = ntf - 2;
-        double fr = x - (double)i;
         double col[4];
-        for (int ch = 0; ch < 4; ++ch)
-            col[ch] = (double)tf[4 * i + ch] * (1.0 - fr) + (double)tf[4 * (i + 1) + ch] * fr;
+        tf_sample(tf, ntf, trilinear(v, p[0], p[1], p[2]), col);
         double alpha = col[3];
         if (alpha > 0.0) {
             if (shading) {
@@ -189,12 +245,31 @@ static int64_t march_ray(const or_vol* v, const float* tf, int ntf, const or_cam
                 double gz = 0.5 * (trilinear(v, p[0], p[1], p[2] + 1.0) - trilinear(v, p[0], p[1], p[2] - 1.0));
                 double gn = sqrt(gx * gx + gy * gy + gz * gz);
                 if (gn < 1e-5) *amb |= 4;
-                if (gn >= 1e-6) {
-                    double ndl = fabs(gx * d[0] + gy * d[1] + gz * d[2]) / gn;
-                    double spec = ndl;
-                    for (int s = 0; s < 5; ++s) spec = spec * spec; /* ndl^32 */
-                    for (int ch = 0; ch < 3; ++ch)
-                        col[ch] = clamp01(col[ch] * (0.2 + 0.7 * ndl) + 0.3 * spec);
+                if (shading == 1) {
+                    if (gn >= 1e-6) {
+                        double ndl = fabs(gx * d[0] + gy * d[1] + gz * d[2]) / gn;
+                        double spec = ndl;
+                        for (int s = 0; s < 5; ++s) spec = spec * spec; /* ndl^32 */
+                        for (int ch = 0; ch < 3; ++ch)
+                            col[ch] = clamp01(col[ch] * (0.2 + 0.7 * ndl) + 0.3 * spec);
+                    }
+                } else {
+                    const double* L = m->L;
+                    double T = shadow_transmittance(v, tf, ntf, p, L, dt, m->rate);
+                    if (gn >= 1e-6) {
+                        double ndl = fabs(gx * L[0] + gy * L[1] + gz * L[2]) / gn;
+                        double h[3] = {L[0] - d[0], L[1] - d[1], L[2] - d[2]};
+                        double hn = sqrt(h[0] * h[0] + h[1] * h[1] + h[2] * h[2]);
+                        double spec = 0.0;
+                        if (hn >= 1e-12) {
+                            spec = fabs(gx * h[0] + gy * h[1] + gz * h[2]) / (gn * hn);
+                            for (int s = 0; s < 5; ++s) spec = spec * spec; /* ndh^32 */
+                        }
+                        for (int ch = 0; ch < 3; ++ch)
+                            col[ch] = clamp01(col[ch] * (0.2 + 0.7 * T * ndl) + 0.3 * T * spec);
+                    } else {
+                        for (int ch = 0; ch < 3; ++ch) col[ch] = clamp01(col[ch] * (0.2 + 0.7 * T));
+                    }
                 }
             }
             double w = (1.0 - A) * alpha;
@@ -214,7 +289,8 @@ static int64_t march_ray(const or_vol* v, const float* tf, int ntf, const or_cam
 }
 
 /*
- * mp = {step, term_alpha, bg_r, bg_g, bg_b, shading}
+ * mp = {step, term_alpha, bg_r, bg_g, bg_b, shading, light_x, light_y, light_z, shadow_rate}
+ * (the light direction is normalised here; the last four only matter for shading 2)
  * cam = {eye[3], target[3], up[3], fov_y_deg}
  * ids == NULL: every pixel (dense).  Otherwise only the listed pixel ids
  * y*W + x are marched and every other pixel of out is 0.
@@ -232,6 +308,8 @@ int64_t or_march(const void* data, int dtype, int nx, int ny, int nz, const floa
     memset(out, 0, sizeof(double) * 5 * (size_t)npix);
     if (amb) memset(amb, 0, (size_t)npix);
     const int64_t nrays = ids ? nids : npix;
+    or_mp m = {mp[0], mp[1], {mp[2], mp[3], mp[4]}, (int)mp[5], {mp[6], mp[7], mp[8]}, (int)mp[9]};
+    if (m.shading == 2) normalize3(m.L);
     const double term = term_override > 0.0 ? term_override : mp[1];
     int64_t total = 0;
 #pragma omp parallel for schedule(dynamic, 64) reduction(+ : total)
@@ -240,7 +318,7 @@ int64_t or_march(const void* data, int dtype, int nx, int ny, int nz, const floa
         int px = (int)(pix % W), py = (int)(pix / W);
         double rgba[4];
         int a = 0;
-        total += march_ray(&v, tf, ntf, &c, px, py, mp[0], term, mp + 2, (int)mp[5], count_shift, rgba, &a);
+        total += march_ray(&v, tf, ntf, &c, px, py, &m, term, count_shift, rgba, &a);
         out[0 * npix + pix] = rgba[0];
         out[1 * npix + pix] = rgba[1];
         out[2 * npix + pix] = rgba[2];
@@ -269,4 +347,14 @@ void or_ray(const double* cam, int W, int H, int nx, int ny, int nz, int px, int
     for (int a = 0; a < 3; ++a) d[a] = c.f[a] + sx * c.r[a] + sy * c.u[a];
     normalize3(d);
     for (int a = 0; a < 3; ++a) o[a] = c.o[a];
+}
+
+/* Shadow transmittance (shading 2) at voxel-space points p[n][3] towards the
+ * light direction L[3] (normalised here), for tests. */
+void or_shadow(const void* data, int dtype, int nx, int ny, int nz, const float* tf, int ntf, const double* p,
+               int64_t n, const double* light, double dt, int rate, double* out) {
+    or_vol v = {data, dtype, {nx, ny, nz}};
+    double L[3] = {light[0], light[1], light[2]};
+    normalize3(L);
+    for (int64_t i = 0; i < n; ++i) out[i] = shadow_transmittance(&v, tf, ntf, p + 3 * i, L, dt, rate);
 }

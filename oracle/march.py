@@ -45,6 +45,9 @@ def _load():
         lib.or_trilinear.restype = None
         lib.or_trilinear.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                      ctypes.c_int64, P]
+        lib.or_shadow.restype = None
+        lib.or_shadow.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P,
+                                  ctypes.c_int64, P, ctypes.c_double, ctypes.c_int, P]
         lib.or_ray.restype = None
         lib.or_ray.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int, ctypes.c_int, P, P]
@@ -58,6 +61,13 @@ def _ptr(a):
 
 def _cam_array(cam):
     return np.array(list(cam.eye) + list(cam.target) + list(cam.up) + [cam.fov_y_deg], dtype=np.float64)
+
+
+def _mp_array(mp):
+    light = getattr(mp, "light_dir", (0.0, 1.0, 0.0))
+    rate = getattr(mp, "shadow_rate", 4)
+    return np.array([mp.step_vox, mp.term_alpha, *mp.bg, float(mp.shading), *light, float(rate)],
+                    dtype=np.float64)
 
 
 def _vol_args(vol):
@@ -75,7 +85,7 @@ def march(vol, tf, cam, mp, ids=None, count_shift=0, term_override=0.0):
     vol, dt, nx, ny, nz = _vol_args(vol)
     tf = np.ascontiguousarray(tf, dtype=np.float32)
     camv = _cam_array(cam)
-    mpv = np.array([mp.step_vox, mp.term_alpha, *mp.bg, float(mp.shading)], dtype=np.float64)
+    mpv = _mp_array(mp)
     W, H = cam.width, cam.height
     out = np.empty((5, H, W), dtype=np.float64)
     amb = np.empty((H, W), dtype=np.uint8)
@@ -104,3 +114,15 @@ def ray(cam, dims, px, py):
     nx, ny, nz = dims
     _load().or_ray(_ptr(camv), cam.width, cam.height, nx, ny, nz, px, py, _ptr(o), _ptr(d))
     return o, d
+
+
+def shadow(vol, tf, points, light_dir, step_vox=0.5, rate=4):
+    """Shadow transmittance (shading 2) at voxel-space points towards the light."""
+    vol, dt, nx, ny, nz = _vol_args(vol)
+    tf = np.ascontiguousarray(tf, dtype=np.float32)
+    p = np.ascontiguousarray(points, dtype=np.float64).reshape(-1, 3)
+    L = np.ascontiguousarray(light_dir, dtype=np.float64)
+    out = np.empty(p.shape[0], dtype=np.float64)
+    _load().or_shadow(_ptr(vol), dt, nx, ny, nz, _ptr(tf), tf.shape[0], _ptr(p), p.shape[0], _ptr(L),
+                      float(step_vox), int(rate), _ptr(out))
+    return out

@@ -206,12 +206,21 @@ class Foveation:
     frame: int = 0
 
 
+# Default light of the shadowed shading mode: from above (+y is the orbit's up), off to one side.
+LIGHT_DIR = (0.35, 0.85, 0.40)
+
+
 @dataclass
 class MarchParams:
+    """shading: 0 none, 1 Phong headlight, 2 Phong lit by a directional light
+    along light_dir (world space, towards the light) with one shadow ray per
+    sample at shadow_rate x the main step (the paper's renderer uses 4)."""
     step_vox: float = 0.5
     term_alpha: float = 0.99
     bg: tuple = (0.0, 0.0, 0.0)
     shading: int = 1
+    light_dir: tuple = LIGHT_DIR
+    shadow_rate: int = 4
 
 
 # ---------------------------------------------------------------------------
