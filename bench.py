@@ -41,6 +41,8 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--profile", action="store_true",
                    help="run two untimed frames (mask, sparse march, dense march, reconstruction) for ncu")
+    p.add_argument("--no-shadows", action="store_true",
+                   help="skip the global-shadows block (the paper's renderer setting)")
     p.add_argument("--no-multiview", action="store_true",
                    help="skip the batched 16-view measurement")
     p.add_argument("--sweep", action="store_true",
@@ -286,6 +288,87 @@ def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.
         print(json.dumps(row), flush=True)
     ctx.close()
     return rows
+
+
+def run_shadows(fvn, wl, weights, conv, vol, tf, frames, dev, nframes, flush):
+    """The paper's renderer setting: Phong lit by a directional light with one
+    shadow ray per sample at a quarter of the main sample rate (shading 2),
+    on the same orbit frames as the headline, in a context of its own with
+    its own autotuned march launch shapes.  Foveated fvn_render frames and
+    the dense march of the same frames, PSNR of the reconstruction against
+    the dense render."""
+    import numpy as np
+    import torch
+    from paper_2209_09965_gb300 import autotune
+    c = fvn.Context()
+    try:
+        c.load_weights(weights)
+        c.set_option(fvn.OPT_CONV_KERNEL, fvn.CONV_TCGEN05 if conv == "tcgen05" else fvn.CONV_MMA_SYNC)
+        mp = wl.MarchParams(shading=2, light_dir=wl.LIGHT_DIR, shadow_rate=4)
+        cam0, fov0 = frames[0]
+        rgb = torch.empty(3, H, W, device=dev)
+        rgbam = torch.empty(5, H, W, device=dev)
+        dense = torch.empty(5, H, W, device=dev)
+        mask = torch.empty(H, W, dtype=torch.uint8, device=dev)
+        ids = torch.empty(W * H, dtype=torch.int32, device=dev)
+        count = torch.zeros(1, dtype=torch.int32, device=dev)
+        c.make_mask(fov0, W, H, mask, ids, count)
+        tuned = {"march": autotune.tune_march(c, vol, tf, cam0, mp, rgbam, ids=ids, count=count),
+                 "dense_march": autotune.tune_march(c, vol, tf, cam0, mp, dense)}
+        for k in tuned.values():
+            k.pop("candidates", None)
+        for i in range(3):
+            c.render(vol, tf, frames[i][0], frames[i][1], mp, rgb)
+        torch.cuda.synchronize()
+        stream = torch.cuda.current_stream()
+        fov_ms, dense_ms, march_ms, psnrs = [], [], [], []
+        nsamp = torch.zeros(1, dtype=torch.int64, device=dev)
+        sparse_samples = dense_samples = 0
+        for i in range(nframes):
+            cam, fov = frames[i % len(frames)]
+            e = [torch.cuda.Event(enable_timing=True) for _ in range(6)]
+            flush.fill_(float(i))
+            e[0].record(stream)
+            c.render(vol, tf, cam, fov, mp, rgb)
+            e[1].record(stream)
+            flush.fill_(float(i))
+            nsamp.zero_()
+            e[2].record(stream)
+            c.march(vol, tf, cam, mp, dense, nsamples=nsamp)
+            e[3].record(stream)
+            torch.cuda.synchronize()
+            dense_samples += int(nsamp.item())
+            c.make_mask(fov, W, H, mask, ids, count)
+            nsamp.zero_()
+            flush.fill_(float(i))
+            e[4].record(stream)
+            c.march(vol, tf, cam, mp, rgbam, ids=ids, count=count, nsamples=nsamp)
+            e[5].record(stream)
+            torch.cuda.synchronize()
+            sparse_samples += int(nsamp.item())
+            fov_ms.append(e[0].elapsed_time(e[1]))
+            dense_ms.append(e[2].elapsed_time(e[3]))
+            march_ms.append(e[4].elapsed_time(e[5]))
+            psnrs.append(psnr_t(rgb, dense[:3]))
+        c.device_status()
+        fps = nframes / (sum(fov_ms) / 1000.0)
+        dfps = nframes / (sum(dense_ms) / 1000.0)
+        return {"workload": "foveated-1080p frames with global shadows: directional light "
+                            f"{tuple(round(x, 3) for x in wl.LIGHT_DIR)}, one shadow ray per sample at 1/4 of "
+                            "the sample rate (shading 2)",
+                "frames": nframes, "frames_per_s": fps, "ms_per_frame": float(np.mean(fov_ms)),
+                "dense_march_frames_per_s": dfps, "speedup_vs_dense": fps / dfps,
+                "psnr_vs_dense_db": {"mean": float(np.mean(psnrs)), "min": float(np.min(psnrs))},
+                "stage_ms": {"sparse_march": float(np.mean(march_ms)), "dense_march": float(np.mean(dense_ms))},
+                "gsamples_per_s": {"sparse_march": sparse_samples / (sum(march_ms) / 1000.0) / 1e9,
+                                   "dense_march": dense_samples / (sum(dense_ms) / 1000.0) / 1e9,
+                                   "note": "primary samples only; each shaded sample also marches its "
+                                           "shadow ray"},
+                "autotune": tuned}
+    except Exception as exc:   # reported, not part of the metric
+        return {"error": str(exc)[:200]}
+    finally:
+        c.close()
 
 
 def run_multiview(ctx, fvn, wl, dev, steps, warmup, flush):
@@ -596,6 +679,11 @@ def main():
         e2e_ms.append(e0.elapsed_time(e1))
     e2e_val = world * args.steps / (sum(e2e_ms) / 1000.0)
 
+    shadows = None
+    if not args.no_shadows:
+        shadows = run_shadows(fvn, wl, weights, "tcgen05" if (tuned is None or tuned["conv"]["conv"] == "tcgen05")
+                              else "mma_sync", vol, tf, frames, dev, min(args.steps, 16), flush)
+
     multiview = None
     if not args.no_multiview:
         multiview = run_multiview(ctx, fvn, wl, dev, min(args.steps, 8), 2, flush)
@@ -648,6 +736,7 @@ def main():
             "gpu_launches": (15 if (tuned is None or tuned["conv"]["conv"] == "tcgen05") else 14) * args.steps,
             "cuda_graph": graph_info,
             "fp8": fp8_info,
+            "shadows": shadows,
             "multiview": multiview,
             "clocks": clocks,
         }

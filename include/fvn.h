@@ -86,12 +86,28 @@ typedef struct {
 } fvn_foveation;
 
 /* Ray-march parameters: step in voxels (> 0), early-termination opacity
- * (0, 1], background colour, shading 0 = none, 1 = Phong headlight. */
+ * (0, 1], background colour, and the shading:
+ *   0  none (the TF colour);
+ *   1  Phong with a headlight (light and view along the ray);
+ *   2  Phong lit by a directional light, with global shadows as in the
+ *      paper's renderer ("Foveated Rendering": one shadow ray per sample
+ *      towards the light at a quarter of the main sample rate).  From every
+ *      sample with opacity > 0 a shadow ray takes samples at j * ds,
+ *      j = 1, 2, ..., ds = shadow_rate * step_vox, until it leaves the box;
+ *      each multiplies the light's transmittance T by (1 - a)^shadow_rate
+ *      (a = TF opacity there; the last sample by the power for the part of
+ *      its step inside the box), and the ray stops once T < 2^-14.  The
+ *      shaded colour is clamp(c (0.2 + 0.7 T |n.L|) + 0.3 T |n.H|^32) with
+ *      H = |L - dir|, or clamp(c (0.2 + 0.7 T)) where the gradient is < 1e-6.
+ * light_dir (world space, towards the light; normalised by the library) and
+ * shadow_rate (1..64; the paper uses 4) matter for shading 2 only. */
 typedef struct {
     float step_vox;
     float term_alpha;
     float bg[3];
     int shading;
+    float light_dir[3];
+    int shadow_rate;
 } fvn_march_params;
 
 /* Create a context on the current CUDA device.  Synchronises the host. */

@@ -76,9 +76,8 @@ extern "C" fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int 
     if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
     FVN_CHECK_ARG(ctx, views != nullptr, "views is NULL");
     FVN_CHECK_ARG(ctx, nviews >= 1 && nviews <= kMaxViews, "%d views (1..%d)", nviews, kMaxViews);
-    FVN_CHECK_ARG(ctx, mp && mp->step_vox > 0.f && isfinite(mp->step_vox) && mp->term_alpha > 0.f &&
-                           mp->term_alpha <= 1.f,
-                  "bad march parameters");
+    fvn_status vs = validate_march_params(ctx, mp);
+    if (vs != FVN_OK) return vs;
     FVN_CHECK_ARG(ctx, precision == FVN_PREC_FP16 || precision == FVN_PREC_FP8, "unknown precision %d", precision);
     if (!ctx->has_weights) return set_error(ctx, FVN_ERR_STATE, "no weights loaded (call fvn_load_weights)");
     if (precision == FVN_PREC_FP8 && !ctx->has_fp8)

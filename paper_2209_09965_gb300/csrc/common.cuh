@@ -166,6 +166,7 @@ inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s
 
 fvn_status validate_volume(fvn_ctx* ctx, const fvn_volume* vol);
 fvn_status validate_camera(fvn_ctx* ctx, const fvn_camera* cam);
+fvn_status validate_march_params(fvn_ctx* ctx, const fvn_march_params* mp);
 
 // Stage entry points used by fvn_render (no argument validation).
 fvn_status make_mask_impl(fvn_ctx* ctx, const fvn_foveation* fov, int w, int h, uint8_t* mask, int32_t* ids,

@@ -34,6 +34,24 @@ fvn_status validate_volume(fvn_ctx* ctx, const fvn_volume* vol) {
     return FVN_OK;
 }
 
+fvn_status validate_march_params(fvn_ctx* ctx, const fvn_march_params* mp) {
+    FVN_CHECK_ARG(ctx, mp != nullptr, "march parameters are NULL");
+    FVN_CHECK_ARG(ctx, mp->step_vox > 0.f && isfinite(mp->step_vox), "step_vox must be > 0");
+    FVN_CHECK_ARG(ctx, mp->term_alpha > 0.f && mp->term_alpha <= 1.f, "term_alpha must be in (0, 1]");
+    FVN_CHECK_ARG(ctx, mp->shading >= 0 && mp->shading <= 2, "shading %d (0 none, 1 headlight, 2 shadows)",
+                  mp->shading);
+    if (mp->shading == 2) {
+        const float* l = mp->light_dir;
+        FVN_CHECK_ARG(ctx, isfinite(l[0]) && isfinite(l[1]) && isfinite(l[2]),
+                      "light_dir has a non-finite component");
+        FVN_CHECK_ARG(ctx, (double)l[0] * l[0] + (double)l[1] * l[1] + (double)l[2] * l[2] > 1e-12,
+                      "light_dir is zero");
+        FVN_CHECK_ARG(ctx, mp->shadow_rate >= 1 && mp->shadow_rate <= 64, "shadow_rate %d outside [1, 64]",
+                      mp->shadow_rate);
+    }
+    return FVN_OK;
+}
+
 fvn_status validate_camera(fvn_ctx* ctx, const fvn_camera* cam) {
     FVN_CHECK_ARG(ctx, cam != nullptr, "camera is NULL");
     FVN_CHECK_ARG(ctx, cam->width >= 1 && cam->height >= 1 && cam->width <= kMaxSide && cam->height <= kMaxSide,
@@ -183,8 +201,7 @@ extern "C" fvn_status fvn_render(fvn_ctx* ctx, const fvn_volume* vol, const fvn_
     if ((st = validate_camera(ctx, cam)) != FVN_OK) return st;
     FVN_CHECK_ARG(ctx, tf && tf->rgba && tf->n >= 2 && tf->n <= 4096, "bad transfer function");
     FVN_CHECK_ARG(ctx, fov != nullptr, "foveation is NULL");
-    FVN_CHECK_ARG(ctx, mp && mp->step_vox > 0.f && mp->term_alpha > 0.f && mp->term_alpha <= 1.f,
-                  "bad march parameters");
+    if ((st = validate_march_params(ctx, mp)) != FVN_OK) return st;
     FVN_CHECK_ARG(ctx, rgb != nullptr, "rgb output is NULL");
     FVN_CHECK_ARG(ctx, precision == FVN_PREC_FP16 || precision == FVN_PREC_FP8, "unknown precision %d", precision);
     if (!ctx->has_weights) return set_error(ctx, FVN_ERR_STATE, "no weights loaded (call fvn_load_weights)");

@@ -15,10 +15,12 @@
 // has no boundary branches.
 //
 // Per sample (FP32): trilinear value between voxel centres (clamp to edge),
-// TF lookup at v (n - 1), optional Phong headlight shading from central
-// differences at +-1 voxel (only for samples with alpha > 0, which are the
-// only ones that contribute), C += (1 - A) a c, A += (1 - A) a, stop once
-// A >= term_alpha.  The 32 voxels a shaded sample needs are loaded in one
+// TF lookup at v (n - 1), optional shading from central differences at
+// +-1 voxel (only for samples with alpha > 0, which are the only ones that
+// contribute) -- Phong with a headlight, or, as in the paper's renderer,
+// Phong lit by a directional light whose transmittance a shadow ray towards
+// the light measures at a quarter of the sample rate -- then
+// C += (1 - A) a c, A += (1 - A) a, stop once A >= term_alpha.  The 32 voxels a shaded sample needs are loaded in one
 // batch, and two consecutive samples are loaded before the first is
 // composited: the latency chain of a long ray, which bounds sparse frames,
 // is a quarter of the naive one.
@@ -61,6 +63,19 @@ struct MarchArgs {
     int coop_below;                   // finish the rays cooperatively once at most this many are busy (0 = never)
     const uint8_t* reject;            // dense numbering: skip pixels whose mask byte is 0
 };
+
+// Shading 2: the directional light and the shadow-ray step (the same for
+// every view of a batch: world and voxel space share directions).
+struct Light {
+    float lx, ly, lz;                 // unit direction towards the light
+    float ilx, ily, ilz;              // 1 / l per axis (1 where l = 0)
+    float ds, inv_ds;                 // shadow step (shadow_rate * dt) and its reciprocal
+    int srate;                        // shadow_rate
+};
+
+// A shadow ray stops once the light's transmittance falls below this; the
+// light it could still carry changes no output channel by as much.
+constexpr float kShadowCutoff = 1.0f / 16384.0f;
 
 template <typename T>
 __device__ __forceinline__ float load_norm(const T* p);
@@ -185,14 +200,35 @@ struct Stencil {
 // Cell of a sample position (voxel-centre coordinates): fractions into S
 // and the offset of the cell's first voxel in the padded copy.
 template <typename I>
-__device__ __forceinline__ I stencil_cell(const MarchArgs& a, I sy, I sz, float ux, float uy, float uz, Stencil& S) {
-    int i = floor_frac(ux, S.tx), j = floor_frac(uy, S.ty), k = floor_frac(uz, S.tz);
+__device__ __forceinline__ I cell_base(const MarchArgs& a, I sy, I sz, float ux, float uy, float uz, float& tx,
+                                       float& ty, float& tz) {
+    int i = floor_frac(ux, tx), j = floor_frac(uy, ty), k = floor_frac(uz, tz);
     // samples lie in the box, so i is in [-1, n - 1]; the clamp only guards
     // against rounding and keeps every stencil index inside the padded copy
     i = min(max(i, -1), a.nx - 1);
     j = min(max(j, -1), a.ny - 1);
     k = min(max(k, -1), a.nz - 1);
     return (I)(k + kPad) * sz + (I)(j + kPad) * sy + (i + kPad);
+}
+
+template <typename I>
+__device__ __forceinline__ I stencil_cell(const MarchArgs& a, I sy, I sz, float ux, float uy, float uz, Stencil& S) {
+    return cell_base<I>(a, sy, sz, ux, uy, uz, S.tx, S.ty, S.tz);
+}
+
+// The trilinear cell of a shadow sample (values only).
+struct Cell {
+    float c[2][2][2];
+    float tx, ty, tz;
+};
+
+__device__ __forceinline__ float cell_value(const Cell& C) {
+    float rows[2][2];
+#pragma unroll
+    for (int z = 0; z < 2; ++z)
+#pragma unroll
+        for (int y = 0; y < 2; ++y) rows[z][y] = lerpf(C.c[z][y][0], C.c[z][y][1], C.tx);
+    return lerpf(lerpf(rows[0][0], rows[0][1], C.ty), lerpf(rows[1][0], rows[1][1], C.ty), C.tz);
 }
 
 // The voxels of the stencil whose cell starts at vol + b.
@@ -238,11 +274,9 @@ __device__ __forceinline__ void load_stencil(const MarchArgs& a, const T* __rest
     stencil_fetch<T, I, SHADE>(vol, b, sy, sz, S);
 }
 
-// TF lookup at value v: returns the opacity and, when it is > 0, the colour.
-__device__ __forceinline__ float tf_lookup(const MarchArgs& a, const float4* s_tf, float tfmax, float v, float& cr,
-                                           float& cg, float& cb) {
+// TF entry below value v and the fraction towards the next one.
+__device__ __forceinline__ int tf_index(const MarchArgs& a, float tfmax, float v, float& fr) {
     const float xi = v * tfmax;
-    float fr;
     int ti = floor_frac(xi, fr);
     if (ti > a.ntf - 2) {
         fr += (float)(ti - (a.ntf - 2));
@@ -252,6 +286,22 @@ __device__ __forceinline__ float tf_lookup(const MarchArgs& a, const float4* s_t
         fr += (float)ti;
         ti = 0;
     }
+    return ti;
+}
+
+// TF opacity at value v.
+__device__ __forceinline__ float tf_alpha(const MarchArgs& a, const float4* s_tf, float tfmax, float v) {
+    float fr;
+    const int ti = tf_index(a, tfmax, v, fr);
+    const float a0 = s_tf[ti].w, a1 = s_tf[ti + 1].w;
+    return fmaf(fr, a1 - a0, a0);
+}
+
+// TF lookup at value v: returns the opacity and, when it is > 0, the colour.
+__device__ __forceinline__ float tf_lookup(const MarchArgs& a, const float4* s_tf, float tfmax, float v, float& cr,
+                                           float& cg, float& cb) {
+    float fr;
+    const int ti = tf_index(a, tfmax, v, fr);
     const float4 c0 = s_tf[ti], c1 = s_tf[ti + 1];
     const float al = fmaf(fr, c1.w - c0.w, c0.w);
     if (al > 0.0f) {
@@ -282,42 +332,134 @@ __device__ __forceinline__ void phong(float gx, float gy, float gz, float dx, fl
     }
 }
 
-// Classify and shade one loaded sample: returns its opacity al and, when
-// al > 0, its (clamped) shaded colour.
-template <bool SHADE>
-__device__ __forceinline__ float shade_sample(const MarchArgs& a, const float4* s_tf, float tfmax, const Stencil& S,
-                                              float dx, float dy, float dz, float& cr, float& cg, float& cb) {
-    float rows[2][2];
+// Phong lit by the directional light l, attenuated by the shadow
+// transmittance tr: c' = clamp(c (0.2 + 0.7 tr |n.l|) + 0.3 tr |n.h|^32) with
+// h = |l - dir|; where |g| < 1e-6, c' = clamp(c (0.2 + 0.7 tr)).
+__device__ __forceinline__ void phong_lit(const Light& a, float gx, float gy, float gz, float dx, float dy,
+                                          float dz, float tr, float& cr, float& cg, float& cb) {
+    const float g2 = fmaf(gx, gx, fmaf(gy, gy, gz * gz));
+    float diff, spec = 0.0f;
+    if (g2 >= 1e-12f) {
+        const float ig = rsqrtf(g2);
+        const float ndl = fabsf(fmaf(gx, a.lx, fmaf(gy, a.ly, gz * a.lz))) * ig;
+        const float hx = a.lx - dx, hy = a.ly - dy, hz = a.lz - dz;
+        const float h2 = fmaf(hx, hx, fmaf(hy, hy, hz * hz));
+        if (h2 >= 1e-24f) {   // no half vector when the light shines straight back along the ray
+            float sp = fabsf(fmaf(gx, hx, fmaf(gy, hy, gz * hz))) * ig * rsqrtf(h2);
+            sp *= sp;   // ndh^32 by five squarings
+            sp *= sp;
+            sp *= sp;
+            sp *= sp;
+            sp *= sp;
+            spec = 0.3f * tr * sp;
+        }
+        diff = fmaf(0.7f * tr, ndl, 0.2f);
+    } else {
+        diff = fmaf(0.7f, tr, 0.2f);
+    }
+    cr = __saturatef(fmaf(cr, diff, spec));
+    cg = __saturatef(fmaf(cg, diff, spec));
+    cb = __saturatef(fmaf(cb, diff, spec));
+}
+
+// Light reaching a sample: the shadow ray from the sample point u
+// (voxel-centre coordinates) towards the light, with samples at j ds,
+// j = 1, 2, ..., while inside the box.  Each multiplies the transmittance by
+// (1 - a)^shadow_rate, the last one by the power for the part of its step
+// left inside the box (so the result is continuous in the exit distance);
+// the ray stops once the transmittance falls below kShadowCutoff.  Two
+// samples' loads are issued before either is used.
+// The voxel-centre coordinate of the face a shadow ray along l leaves the
+// box [0, n] by (1e30 where l = 0: that axis never bounds it).
+__device__ __forceinline__ float exit_face(float l, int n) {
+    return l > 0.0f ? (float)n - 0.5f : (l < 0.0f ? -0.5f : 1e30f);
+}
+
+template <typename Src, typename I>
+__device__ __forceinline__ float shadow_ray(const MarchArgs& a, const Light& lt,
+                                            const typename Src::V* __restrict__ vol, const float4* s_tf, float tfmax,
+                                            I sy, I sz, float ux, float uy, float uz) {
+    const float se = fminf(fminf((exit_face(lt.lx, a.nx) - ux) * lt.ilx, (exit_face(lt.ly, a.ny) - uy) * lt.ily),
+                           (exit_face(lt.lz, a.nz) - uz) * lt.ilz);
+    float tr = 1.0f;
+    for (float j = 1.0f;; j += 2.0f) {
+        const float s0 = j * lt.ds;
+        if (!(s0 < se)) break;
+        const float s1 = (j + 1.0f) * lt.ds;
+        const bool has1 = s1 < se;
+        const float s1c = has1 ? s1 : s0;
+        Cell C0, C1;
+        Src::template load_cell<I>(a, vol, sy, sz, fmaf(s0, lt.lx, ux), fmaf(s0, lt.ly, uy), fmaf(s0, lt.lz, uz),
+                                   C0);
+        Src::template load_cell<I>(a, vol, sy, sz, fmaf(s1c, lt.lx, ux), fmaf(s1c, lt.ly, uy), fmaf(s1c, lt.lz, uz),
+                                   C1);
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            const float al = tf_alpha(a, s_tf, tfmax, cell_value(q ? C1 : C0));
+            if (al > 0.0f) {
+                const float base = 1.0f - al;
+                const float e = (se - (q ? s1 : s0)) * lt.inv_ds;   // steps left inside the box
+                float f;
+                if (e >= 1.0f) {
+                    f = base;
+                    for (int i = 1; i < lt.srate; ++i) f *= base;
+                } else {
+                    f = base > 0.0f ? exp2f((float)lt.srate * e * log2f(base)) : 0.0f;
+                }
+                tr *= f;
+            }
+            if (tr < kShadowCutoff || (q == 0 && !has1)) return tr;
+        }
+    }
+    return tr;
+}
+
+// The voxel rows of a stencil interpolated along x, and the trilinear value.
+__device__ __forceinline__ float stencil_value(const Stencil& S, float (&rows)[2][2]) {
 #pragma unroll
     for (int z = 0; z < 2; ++z)
 #pragma unroll
         for (int y = 0; y < 2; ++y) rows[z][y] = lerpf(S.c[z][y][0], S.c[z][y][1], S.tx);
-    const float v = lerpf(lerpf(rows[0][0], rows[0][1], S.ty), lerpf(rows[1][0], rows[1][1], S.ty), S.tz);
-    const float al = tf_lookup(a, s_tf, tfmax, v, cr, cg, cb);
-    if (SHADE && al > 0.0f) {
-        // central differences at +-1 voxel of the trilinear field
-        float d[2][2];
+    return lerpf(lerpf(rows[0][0], rows[0][1], S.ty), lerpf(rows[1][0], rows[1][1], S.ty), S.tz);
+}
+
+// Central differences at +-1 voxel of the trilinear field.
+__device__ __forceinline__ void stencil_gradient(const Stencil& S, const float (&rows)[2][2], float& gx, float& gy,
+                                                 float& gz) {
+    float d[2][2];
 #pragma unroll
-        for (int z = 0; z < 2; ++z)
+    for (int z = 0; z < 2; ++z)
 #pragma unroll
-            for (int y = 0; y < 2; ++y)
-                d[z][y] = lerpf(S.c[z][y][1], S.xp[z][y], S.tx) - lerpf(S.xm[z][y], S.c[z][y][0], S.tx);
-        const float gx = 0.5f * lerpf(lerpf(d[0][0], d[0][1], S.ty), lerpf(d[1][0], d[1][1], S.ty), S.tz);
-        float ym[2], yp[2], zm[2], zp[2];
+        for (int y = 0; y < 2; ++y)
+            d[z][y] = lerpf(S.c[z][y][1], S.xp[z][y], S.tx) - lerpf(S.xm[z][y], S.c[z][y][0], S.tx);
+    gx = 0.5f * lerpf(lerpf(d[0][0], d[0][1], S.ty), lerpf(d[1][0], d[1][1], S.ty), S.tz);
+    float ym[2], yp[2], zm[2], zp[2];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            ym[q] = lerpf(S.ym[q][0], S.ym[q][1], S.tx);
-            yp[q] = lerpf(S.yp[q][0], S.yp[q][1], S.tx);
-            zm[q] = lerpf(S.zm[q][0], S.zm[q][1], S.tx);
-            zp[q] = lerpf(S.zp[q][0], S.zp[q][1], S.tx);
-        }
-        const float gy = 0.5f * lerpf(lerpf(rows[0][1], yp[0], S.ty) - lerpf(ym[0], rows[0][0], S.ty),
-                                      lerpf(rows[1][1], yp[1], S.ty) - lerpf(ym[1], rows[1][0], S.ty), S.tz);
-        const float gz = 0.5f * lerpf(lerpf(rows[1][0], zp[0], S.tz) - lerpf(zm[0], rows[0][0], S.tz),
-                                      lerpf(rows[1][1], zp[1], S.tz) - lerpf(zm[1], rows[0][1], S.tz), S.ty);
-        phong(gx, gy, gz, dx, dy, dz, cr, cg, cb);
+    for (int q = 0; q < 2; ++q) {
+        ym[q] = lerpf(S.ym[q][0], S.ym[q][1], S.tx);
+        yp[q] = lerpf(S.yp[q][0], S.yp[q][1], S.tx);
+        zm[q] = lerpf(S.zm[q][0], S.zm[q][1], S.tx);
+        zp[q] = lerpf(S.zp[q][0], S.zp[q][1], S.tx);
     }
-    return al;
+    gy = 0.5f * lerpf(lerpf(rows[0][1], yp[0], S.ty) - lerpf(ym[0], rows[0][0], S.ty),
+                      lerpf(rows[1][1], yp[1], S.ty) - lerpf(ym[1], rows[1][0], S.ty), S.tz);
+    gz = 0.5f * lerpf(lerpf(rows[1][0], zp[0], S.tz) - lerpf(zm[0], rows[0][0], S.tz),
+                      lerpf(rows[1][1], zp[1], S.tz) - lerpf(zm[1], rows[0][1], S.tz), S.ty);
+}
+
+// Shade a classified sample (al > 0) from its gradient: SHADE 1 headlight,
+// SHADE 2 directional light with the shadow ray from u.
+template <typename Src, int SHADE, typename I>
+__device__ __forceinline__ void light_sample(const MarchArgs& a, const Light& lt,
+                                             const typename Src::V* __restrict__ vol, const float4* s_tf, float tfmax,
+                                             I sy, I sz, float gx, float gy, float gz, float ux, float uy, float uz,
+                                             float dx, float dy, float dz, float& cr, float& cg, float& cb) {
+    if (SHADE == 1) {
+        phong(gx, gy, gz, dx, dy, dz, cr, cg, cb);
+    } else {
+        const float tr = shadow_ray<Src, I>(a, lt, vol, s_tf, tfmax, sy, sz, ux, uy, uz);
+        phong_lit(lt, gx, gy, gz, dx, dy, dz, tr, cr, cg, cb);
+    }
 }
 
 // Sample source of the scalar padded copy: the 32-voxel stencil.
@@ -330,10 +472,35 @@ struct ScalarSrc {
                                                 float uy, float uz, St& S) {
         load_stencil<T, I, SHADE>(a, vol, sy, sz, ux, uy, uz, S);
     }
-    template <bool SHADE>
-    __device__ static __forceinline__ float shade(const MarchArgs& a, const float4* s_tf, float tfmax, const St& S,
-                                                  float dx, float dy, float dz, float& cr, float& cg, float& cb) {
-        return shade_sample<SHADE>(a, s_tf, tfmax, S, dx, dy, dz, cr, cg, cb);
+    template <typename I>
+    __device__ static __forceinline__ void load_cell(const MarchArgs& a, const V* __restrict__ vol, I sy, I sz,
+                                                     float ux, float uy, float uz, Cell& C) {
+        const V* b = vol + cell_base<I>(a, sy, sz, ux, uy, uz, C.tx, C.ty, C.tz);
+#pragma unroll
+        for (int z = 0; z < 2; ++z)
+#pragma unroll
+            for (int y = 0; y < 2; ++y) {
+                const V* r = b + (I)z * sz + (I)y * sy;
+                C.c[z][y][0] = load_norm(r);
+                C.c[z][y][1] = load_norm(r + 1);
+            }
+    }
+    // Classify and shade one loaded sample: returns its opacity al and, when
+    // al > 0, its (clamped) shaded colour.
+    template <int SHADE, typename I>
+    __device__ static __forceinline__ float shade(const MarchArgs& a, const Light& lt, const V* __restrict__ vol,
+                                                  const float4* s_tf, float tfmax, I sy, I sz, const St& S, float ux,
+                                                  float uy, float uz, float dx, float dy, float dz, float& cr,
+                                                  float& cg, float& cb) {
+        float rows[2][2];
+        const float al = tf_lookup(a, s_tf, tfmax, stencil_value(S, rows), cr, cg, cb);
+        if (SHADE != 0 && al > 0.0f) {
+            float gx, gy, gz;
+            stencil_gradient(S, rows, gx, gy, gz);
+            light_sample<ScalarSrc<T>, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, gx, gy, gz, ux, uy, uz, dx, dy,
+                                                 dz, cr, cg, cb);
+        }
+        return al;
     }
 };
 
@@ -354,11 +521,7 @@ struct Grad4Src {
     template <typename I, bool SHADE>
     __device__ static __forceinline__ void load(const MarchArgs& a, const V* __restrict__ vol, I sy, I sz, float ux,
                                                 float uy, float uz, St& S) {
-        int i = floor_frac(ux, S.tx), j = floor_frac(uy, S.ty), k = floor_frac(uz, S.tz);
-        i = min(max(i, -1), a.nx - 1);
-        j = min(max(j, -1), a.ny - 1);
-        k = min(max(k, -1), a.nz - 1);
-        const V* b = vol + ((I)(k + kPad) * sz + (I)(j + kPad) * sy + (i + kPad));
+        const V* b = vol + cell_base<I>(a, sy, sz, ux, uy, uz, S.tx, S.ty, S.tz);
 #pragma unroll
         for (int z = 0; z < 2; ++z)
 #pragma unroll
@@ -368,9 +531,25 @@ struct Grad4Src {
                 S.c[z][y][1] = __ldg(r + 1);
             }
     }
-    template <bool SHADE>
-    __device__ static __forceinline__ float shade(const MarchArgs& a, const float4* s_tf, float tfmax, const St& S,
-                                                  float dx, float dy, float dz, float& cr, float& cg, float& cb) {
+    // values only: the first component of each voxel
+    template <typename I>
+    __device__ static __forceinline__ void load_cell(const MarchArgs& a, const V* __restrict__ vol, I sy, I sz,
+                                                     float ux, float uy, float uz, Cell& C) {
+        const V* b = vol + cell_base<I>(a, sy, sz, ux, uy, uz, C.tx, C.ty, C.tz);
+#pragma unroll
+        for (int z = 0; z < 2; ++z)
+#pragma unroll
+            for (int y = 0; y < 2; ++y) {
+                const float* r = reinterpret_cast<const float*>(b + (I)z * sz + (I)y * sy);
+                C.c[z][y][0] = __ldg(r);
+                C.c[z][y][1] = __ldg(r + 4);
+            }
+    }
+    template <int SHADE, typename I>
+    __device__ static __forceinline__ float shade(const MarchArgs& a, const Light& lt, const V* __restrict__ vol,
+                                                  const float4* s_tf, float tfmax, I sy, I sz, const St& S, float ux,
+                                                  float uy, float uz, float dx, float dy, float dz, float& cr,
+                                                  float& cg, float& cb) {
         float rows[2][2];
 #pragma unroll
         for (int z = 0; z < 2; ++z)
@@ -378,7 +557,7 @@ struct Grad4Src {
             for (int y = 0; y < 2; ++y) rows[z][y] = lerpf(S.c[z][y][0].x, S.c[z][y][1].x, S.tx);
         const float v = lerpf(lerpf(rows[0][0], rows[0][1], S.ty), lerpf(rows[1][0], rows[1][1], S.ty), S.tz);
         const float al = tf_lookup(a, s_tf, tfmax, v, cr, cg, cb);
-        if (SHADE && al > 0.0f) {
+        if (SHADE != 0 && al > 0.0f) {
             float gr[3][2][2];
 #pragma unroll
             for (int z = 0; z < 2; ++z)
@@ -392,7 +571,8 @@ struct Grad4Src {
 #pragma unroll
             for (int c = 0; c < 3; ++c)
                 g[c] = lerpf(lerpf(gr[c][0][0], gr[c][0][1], S.ty), lerpf(gr[c][1][0], gr[c][1][1], S.ty), S.tz);
-            phong(g[0], g[1], g[2], dx, dy, dz, cr, cg, cb);
+            light_sample<Grad4Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, g[0], g[1], g[2], ux, uy, uz, dx, dy,
+                                             dz, cr, cg, cb);
         }
         return al;
     }
@@ -400,11 +580,14 @@ struct Grad4Src {
 
 // Classify, shade and composite one loaded sample; returns true once the ray
 // is opaque enough to stop.
-template <typename Src, bool SHADE>
-__device__ __forceinline__ bool composite_sample(const MarchArgs& a, const float4* s_tf, float tfmax,
-                                                 const typename Src::St& S, Ray& s) {
+template <typename Src, int SHADE, typename I>
+__device__ __forceinline__ bool composite_sample(const MarchArgs& a, const Light& lt,
+                                                 const typename Src::V* __restrict__ vol, const float4* s_tf,
+                                                 float tfmax, I sy, I sz, const typename Src::St& S, float ux,
+                                                 float uy, float uz, Ray& s) {
     float cr, cg, cb;
-    const float al = Src::template shade<SHADE>(a, s_tf, tfmax, S, s.dx, s.dy, s.dz, cr, cg, cb);
+    const float al = Src::template shade<SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S, ux, uy, uz, s.dx, s.dy, s.dz,
+                                                   cr, cg, cb);
     if (al > 0.0f) {
         const float w = (1.0f - s.A) * al;
         s.C0 = fmaf(w, cr, s.C0);
@@ -418,8 +601,8 @@ __device__ __forceinline__ bool composite_sample(const MarchArgs& a, const float
 // Up to two samples of the ray with both samples' loads issued before either
 // is composited (the loads do not depend on the compositing), which halves
 // the latency chain a long ray walks.  Returns true when the ray is finished.
-template <typename Src, typename I, bool SHADE>
-__device__ __forceinline__ bool ray_step(const MarchArgs& a, const typename Src::V* __restrict__ vol,
+template <typename Src, typename I, int SHADE>
+__device__ __forceinline__ bool ray_step(const MarchArgs& a, const Light& lt, const typename Src::V* __restrict__ vol,
                                          const float4* s_tf, I sy, I sz, float ux0, float uy0, float uz0,
                                          float tfmax, Ray& s) {
     const float t0 = fmaf(s.kf, a.dt, s.tnear);
@@ -428,14 +611,15 @@ __device__ __forceinline__ bool ray_step(const MarchArgs& a, const typename Src:
     const bool has1 = t1 < s.tfar;
     const float t1c = has1 ? t1 : t0;
     typename Src::St S0, S1;
-    Src::template load<I, SHADE>(a, vol, sy, sz, fmaf(t0, s.dx, ux0), fmaf(t0, s.dy, uy0), fmaf(t0, s.dz, uz0), S0);
-    Src::template load<I, SHADE>(a, vol, sy, sz, fmaf(t1c, s.dx, ux0), fmaf(t1c, s.dy, uy0), fmaf(t1c, s.dz, uz0),
-                                 S1);
+    const float px0 = fmaf(t0, s.dx, ux0), py0 = fmaf(t0, s.dy, uy0), pz0 = fmaf(t0, s.dz, uz0);
+    const float px1 = fmaf(t1c, s.dx, ux0), py1 = fmaf(t1c, s.dy, uy0), pz1 = fmaf(t1c, s.dz, uz0);
+    Src::template load<I, SHADE != 0>(a, vol, sy, sz, px0, py0, pz0, S0);
+    Src::template load<I, SHADE != 0>(a, vol, sy, sz, px1, py1, pz1, S1);
     s.kf += 1.0f;
-    if (composite_sample<Src, SHADE>(a, s_tf, tfmax, S0, s)) return true;
+    if (composite_sample<Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S0, px0, py0, pz0, s)) return true;
     if (!has1) return true;
     s.kf += 1.0f;
-    return composite_sample<Src, SHADE>(a, s_tf, tfmax, S1, s);
+    return composite_sample<Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S1, px1, py1, pz1, s);
 }
 
 // Cooperative march of one ray by the whole warp, for the last few rays of a
@@ -446,8 +630,8 @@ __device__ __forceinline__ bool ray_step(const MarchArgs& a, const typename Src:
 // different order -- and the ray stops at the first sample whose opacity
 // reaches term_alpha, or where it leaves the box.  `r` is the same on every
 // lane on entry and on return.
-template <typename Src, typename I, bool SHADE>
-__device__ __forceinline__ void coop_ray(const MarchArgs& a, const typename Src::V* __restrict__ vol,
+template <typename Src, typename I, int SHADE>
+__device__ __forceinline__ void coop_ray(const MarchArgs& a, const Light& lt, const typename Src::V* __restrict__ vol,
                                          const float4* s_tf, I sy, I sz, float ux0, float uy0, float uz0, float tfmax,
                                          Ray& r) {
     const unsigned FULL = 0xffffffffu;
@@ -460,9 +644,10 @@ __device__ __forceinline__ void coop_ray(const MarchArgs& a, const typename Src:
         float cr = 0.f, cg = 0.f, cb = 0.f, al = 0.f;
         if (valid) {
             typename Src::St S;
-            Src::template load<I, SHADE>(a, vol, sy, sz, fmaf(t, r.dx, ux0), fmaf(t, r.dy, uy0), fmaf(t, r.dz, uz0),
-                                         S);
-            al = Src::template shade<SHADE>(a, s_tf, tfmax, S, r.dx, r.dy, r.dz, cr, cg, cb);
+            const float px = fmaf(t, r.dx, ux0), py = fmaf(t, r.dy, uy0), pz = fmaf(t, r.dz, uz0);
+            Src::template load<I, SHADE != 0>(a, vol, sy, sz, px, py, pz, S);
+            al = Src::template shade<SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S, px, py, pz, r.dx, r.dy, r.dz, cr,
+                                               cg, cb);
             if (!(al > 0.0f)) al = 0.0f;
         }
         // incl = prod_{i <= j} (1 - al_i), excl = prod_{i < j} (1 - al_i)
@@ -518,8 +703,8 @@ __device__ __forceinline__ Ray shfl_ray(const Ray& s, int src) {
 // idle lanes take new rays from the global queue together (one atomic per
 // warp), so warps neither wait for their longest ray nor for the slowest
 // warp at the end of the queue.
-template <typename Src, typename I, bool SHADE>
-__global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
+template <typename Src, typename I, int SHADE>
+__global__ void __launch_bounds__(128) march_kernel(MarchArgs a, Light lt) {
     extern __shared__ float4 s_tf[];
     for (int i = threadIdx.x; i < a.ntf; i += blockDim.x) s_tf[i] = a.tf[i];
     __syncthreads();
@@ -545,7 +730,7 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
             r = __shfl_sync(FULL, r, 0);
             if (r >= nrays) break;
             if (!start_ray(a, r, npix, s)) continue;   // every lane sets up the same ray
-            if (s.tfar > -INFINITY) coop_ray<Src, I, SHADE>(a, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s);
+            if (s.tfar > -INFINITY) coop_ray<Src, I, SHADE>(a, lt, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s);
             if (lane == 0) {
                 my_samples += (unsigned long long)s.kf;
                 finish_ray(a, s);
@@ -583,7 +768,7 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
                 do {
                     const int src = __ffs(busy) - 1;
                     Ray r = shfl_ray(s, src);
-                    coop_ray<Src, I, SHADE>(a, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+                    coop_ray<Src, I, SHADE>(a, lt, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, r);
                     if (lane == src) {
                         s = r;
                         my_samples += (unsigned long long)s.kf;
@@ -594,7 +779,7 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a) {
                 } while (busy != 0);
                 break;
             }
-            if (s.pix >= 0 && ray_step<Src, I, SHADE>(a, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s)) {
+            if (s.pix >= 0 && ray_step<Src, I, SHADE>(a, lt, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s)) {
                 my_samples += (unsigned long long)s.kf;
                 finish_ray(a, s);
                 s.pix = -1;
@@ -624,6 +809,7 @@ struct MarchBatchView {
 };
 
 struct MarchBatch {
+    Light light;
     int nviews;
     int ntfs;                         // distinct transfer functions
     const float4* tf[kMaxViews];
@@ -640,8 +826,8 @@ static_assert(sizeof(MarchBatch) <= 4096, "batched march arguments exceed the 4 
 // kGrad4 for a gradient volume.
 constexpr int kGrad4 = 16;
 
-template <typename I, bool SHADE>
-__device__ __forceinline__ bool batch_step(const MarchBatchView& bv, const float4* s_tf, Ray& s) {
+template <typename I, int SHADE>
+__device__ __forceinline__ bool batch_step(const MarchBatchView& bv, const Light& lt, const float4* s_tf, Ray& s) {
     const MarchArgs& a = bv.a;
     const I sy = (I)(a.nx + 2 * kPad), sz = sy * (I)(a.ny + 2 * kPad);
     const float ux0 = a.ox - 0.5f, uy0 = a.oy - 0.5f, uz0 = a.oz - 0.5f;
@@ -649,25 +835,25 @@ __device__ __forceinline__ bool batch_step(const MarchBatchView& bv, const float
     const float4* tf = s_tf + bv.tf_off;
     switch (bv.dtype) {
         case kGrad4:
-            return ray_step<Grad4Src, I, SHADE>(a, static_cast<const float4*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
+            return ray_step<Grad4Src, I, SHADE>(a, lt, static_cast<const float4*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
                                                 tfmax, s);
         case FVN_U8:
-            return ray_step<ScalarSrc<uint8_t>, I, SHADE>(a, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0,
+            return ray_step<ScalarSrc<uint8_t>, I, SHADE>(a, lt, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0,
                                                           uy0, uz0, tfmax, s);
         case FVN_U16:
-            return ray_step<ScalarSrc<uint16_t>, I, SHADE>(a, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0,
+            return ray_step<ScalarSrc<uint16_t>, I, SHADE>(a, lt, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0,
                                                            uy0, uz0, tfmax, s);
         case FVN_F16:
-            return ray_step<ScalarSrc<__half>, I, SHADE>(a, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0,
+            return ray_step<ScalarSrc<__half>, I, SHADE>(a, lt, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0,
                                                          uz0, tfmax, s);
         default:
-            return ray_step<ScalarSrc<float>, I, SHADE>(a, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0,
+            return ray_step<ScalarSrc<float>, I, SHADE>(a, lt, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0,
                                                         uz0, tfmax, s);
     }
 }
 
-template <typename I, bool SHADE>
-__device__ __forceinline__ void batch_coop(const MarchBatchView& bv, const float4* s_tf, Ray& r) {
+template <typename I, int SHADE>
+__device__ __forceinline__ void batch_coop(const MarchBatchView& bv, const Light& lt, const float4* s_tf, Ray& r) {
     const MarchArgs& a = bv.a;
     const I sy = (I)(a.nx + 2 * kPad), sz = sy * (I)(a.ny + 2 * kPad);
     const float ux0 = a.ox - 0.5f, uy0 = a.oy - 0.5f, uz0 = a.oz - 0.5f;
@@ -675,28 +861,28 @@ __device__ __forceinline__ void batch_coop(const MarchBatchView& bv, const float
     const float4* tf = s_tf + bv.tf_off;
     switch (bv.dtype) {
         case kGrad4:
-            coop_ray<Grad4Src, I, SHADE>(a, static_cast<const float4*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+            coop_ray<Grad4Src, I, SHADE>(a, lt, static_cast<const float4*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax, r);
             break;
         case FVN_U8:
-            coop_ray<ScalarSrc<uint8_t>, I, SHADE>(a, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
+            coop_ray<ScalarSrc<uint8_t>, I, SHADE>(a, lt, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
                                                    tfmax, r);
             break;
         case FVN_U16:
-            coop_ray<ScalarSrc<uint16_t>, I, SHADE>(a, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0, uy0,
+            coop_ray<ScalarSrc<uint16_t>, I, SHADE>(a, lt, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0, uy0,
                                                     uz0, tfmax, r);
             break;
         case FVN_F16:
-            coop_ray<ScalarSrc<__half>, I, SHADE>(a, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
+            coop_ray<ScalarSrc<__half>, I, SHADE>(a, lt, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
                                                   tfmax, r);
             break;
         default:
-            coop_ray<ScalarSrc<float>, I, SHADE>(a, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
+            coop_ray<ScalarSrc<float>, I, SHADE>(a, lt, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
                                                  tfmax, r);
             break;
     }
 }
 
-template <typename I, bool SHADE>
+template <typename I, int SHADE>
 __global__ void __launch_bounds__(128) march_batch_kernel(const __grid_constant__ MarchBatch b) {
     extern __shared__ float4 s_tf[];
     __shared__ int s_start[kMaxViews + 1];   // first ticket of each view
@@ -755,7 +941,7 @@ __global__ void __launch_bounds__(128) march_batch_kernel(const __grid_constant_
                     const int src = __ffs(busy) - 1;
                     Ray r = shfl_ray(s, src);
                     const int v = __shfl_sync(FULL, view, src);
-                    batch_coop<I, SHADE>(b.v[v], s_tf, r);
+                    batch_coop<I, SHADE>(b.v[v], b.light, s_tf, r);
                     if (lane == src) {
                         s = r;
                         my_samples += (unsigned long long)s.kf;
@@ -766,7 +952,7 @@ __global__ void __launch_bounds__(128) march_batch_kernel(const __grid_constant_
                 } while (busy != 0);
                 break;
             }
-            if (s.pix >= 0 && batch_step<I, SHADE>(b.v[view], s_tf, s)) {
+            if (s.pix >= 0 && batch_step<I, SHADE>(b.v[view], b.light, s_tf, s)) {
                 my_samples += (unsigned long long)s.kf;
                 finish_ray(b.v[view].a, s);
                 s.pix = -1;
@@ -846,9 +1032,9 @@ static fvn_status grad4_volume(fvn_ctx* ctx, const void* vol, int nx, int ny, in
 }
 
 template <typename Src, typename I>
-static fvn_status launch_march(fvn_ctx* ctx, const MarchArgs& a, bool shade, cudaStream_t st) {
+static fvn_status launch_march(fvn_ctx* ctx, const MarchArgs& a, const Light& lt, int shade, cudaStream_t st) {
     const size_t smem = (size_t)a.ntf * sizeof(float4);
-    auto kern = shade ? march_kernel<Src, I, true> : march_kernel<Src, I, false>;
+    auto kern = shade == 2 ? march_kernel<Src, I, 2> : (shade == 1 ? march_kernel<Src, I, 1> : march_kernel<Src, I, 0>);
     if (smem > 48 * 1024)
         FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -857,13 +1043,32 @@ static fvn_status launch_march(fvn_ctx* ctx, const MarchArgs& a, bool shade, cud
     if (bps > 0) per_sm = std::min(per_sm, bps);
     if (per_sm < 1) per_sm = 1;
     const int grid = ctx->num_sms * per_sm;
-    kern<<<grid, 128, smem, st>>>(a);
+    kern<<<grid, 128, smem, st>>>(a, lt);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
 
 static unsigned long long padded_voxels(const fvn_volume* vol) {
     return (unsigned long long)(vol->nx + 2 * kPad) * (vol->ny + 2 * kPad) * (vol->nz + 2 * kPad);
+}
+
+// The light of shading 2 (zero for the other modes).
+static Light make_light(const fvn_march_params* mp) {
+    Light lt{};
+    if (mp->shading != 2) return lt;
+    double l[3] = {mp->light_dir[0], mp->light_dir[1], mp->light_dir[2]};
+    const double ll = sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
+    for (double& x : l) x /= ll;
+    lt.lx = (float)l[0];
+    lt.ly = (float)l[1];
+    lt.lz = (float)l[2];
+    lt.ilx = l[0] != 0.0 ? (float)(1.0 / l[0]) : 1.0f;
+    lt.ily = l[1] != 0.0 ? (float)(1.0 / l[1]) : 1.0f;
+    lt.ilz = l[2] != 0.0 ? (float)(1.0 / l[2]) : 1.0f;
+    lt.srate = mp->shadow_rate;
+    lt.ds = (float)((double)mp->shadow_rate * mp->step_vox);
+    lt.inv_ds = (float)(1.0 / ((double)mp->shadow_rate * mp->step_vox));
+    return lt;
 }
 
 // Per-view fields of the march arguments: volume size, transfer function,
@@ -953,21 +1158,22 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
     fvn_status ps = march_volume_prepare(ctx, vol, mp, ctx->pad_buf, st);   // one pass over the volume
     if (ps != FVN_OK) return ps;
     const bool big = padded_voxels(vol) >= (1ull << 31);
-    const bool shade = mp->shading != 0;
-    if (march_uses_grad4(ctx, vol, mp)) return launch_march<Grad4Src, int>(ctx, a, true, st);
+    const int shade = mp->shading;
+    const Light lt = make_light(mp);
+    if (march_uses_grad4(ctx, vol, mp)) return launch_march<Grad4Src, int>(ctx, a, lt, shade, st);
     switch (vol->dtype) {
         case FVN_U8:
-            return big ? launch_march<ScalarSrc<uint8_t>, long long>(ctx, a, shade, st)
-                       : launch_march<ScalarSrc<uint8_t>, int>(ctx, a, shade, st);
+            return big ? launch_march<ScalarSrc<uint8_t>, long long>(ctx, a, lt, shade, st)
+                       : launch_march<ScalarSrc<uint8_t>, int>(ctx, a, lt, shade, st);
         case FVN_U16:
-            return big ? launch_march<ScalarSrc<uint16_t>, long long>(ctx, a, shade, st)
-                       : launch_march<ScalarSrc<uint16_t>, int>(ctx, a, shade, st);
+            return big ? launch_march<ScalarSrc<uint16_t>, long long>(ctx, a, lt, shade, st)
+                       : launch_march<ScalarSrc<uint16_t>, int>(ctx, a, lt, shade, st);
         case FVN_F16:
-            return big ? launch_march<ScalarSrc<__half>, long long>(ctx, a, shade, st)
-                       : launch_march<ScalarSrc<__half>, int>(ctx, a, shade, st);
+            return big ? launch_march<ScalarSrc<__half>, long long>(ctx, a, lt, shade, st)
+                       : launch_march<ScalarSrc<__half>, int>(ctx, a, lt, shade, st);
         default:
-            return big ? launch_march<ScalarSrc<float>, long long>(ctx, a, shade, st)
-                       : launch_march<ScalarSrc<float>, int>(ctx, a, shade, st);
+            return big ? launch_march<ScalarSrc<float>, long long>(ctx, a, lt, shade, st)
+                       : launch_march<ScalarSrc<float>, int>(ctx, a, lt, shade, st);
     }
 }
 
@@ -1005,6 +1211,7 @@ fvn_status march_volume_prepare(fvn_ctx* ctx, const fvn_volume* vol, const fvn_m
 fvn_status march_batch_impl(fvn_ctx* ctx, const BatchMarchView* views, int n, const fvn_march_params* mp,
                             unsigned long long* nsamples, cudaStream_t st) {
     MarchBatch b{};
+    b.light = make_light(mp);
     b.nviews = n;
     b.nsamples = nsamples;
     b.refill_below = ctx->march_refill;
@@ -1036,9 +1243,11 @@ fvn_status march_batch_impl(fvn_ctx* ctx, const BatchMarchView* views, int n, co
         return set_error(ctx, FVN_ERR_ARG, "the batch's transfer functions hold %d entries (at most 4096)", tf_total);
     b.ticket = ctx->d_ticket + (ctx->ticket_ring++ & 63);
     FVN_CUDA(ctx, cudaMemsetAsync(b.ticket, 0, sizeof(int), st));
-    const bool shade = mp->shading != 0;
-    auto kern = big ? (shade ? march_batch_kernel<long long, true> : march_batch_kernel<long long, false>)
-                    : (shade ? march_batch_kernel<int, true> : march_batch_kernel<int, false>);
+    const int shade = mp->shading;
+    auto kern = big ? (shade == 2 ? march_batch_kernel<long long, 2>
+                                  : (shade == 1 ? march_batch_kernel<long long, 1> : march_batch_kernel<long long, 0>))
+                    : (shade == 2 ? march_batch_kernel<int, 2>
+                                  : (shade == 1 ? march_batch_kernel<int, 1> : march_batch_kernel<int, 0>));
     const size_t smem = (size_t)tf_total * sizeof(float4);
     if (smem > 48 * 1024)
         FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1064,9 +1273,7 @@ extern "C" fvn_status fvn_march(fvn_ctx* ctx, const fvn_volume* vol, const fvn_t
     if ((st = validate_camera(ctx, cam)) != FVN_OK) return st;
     FVN_CHECK_ARG(ctx, tf && tf->rgba && tf->n >= 2 && tf->n <= 4096, "transfer function needs 2..4096 entries");
     FVN_CHECK_ARG(ctx, ((uintptr_t)tf->rgba & 15) == 0, "transfer function must be 16-byte aligned");
-    FVN_CHECK_ARG(ctx, mp != nullptr, "march parameters are NULL");
-    FVN_CHECK_ARG(ctx, mp->step_vox > 0.f && isfinite(mp->step_vox), "step_vox must be > 0");
-    FVN_CHECK_ARG(ctx, mp->term_alpha > 0.f && mp->term_alpha <= 1.f, "term_alpha must be in (0, 1]");
+    if ((st = validate_march_params(ctx, mp)) != FVN_OK) return st;
     FVN_CHECK_ARG(ctx, rgbam != nullptr, "rgbam output is NULL");
     FVN_CHECK_ARG(ctx, (ids == nullptr) == (count == nullptr), "ids and count must both be set or both NULL");
     return march_impl(ctx, vol, tf, cam, mp, ids, count, rgbam, nsamples, as_stream(stream));
@@ -1082,8 +1289,7 @@ extern "C" fvn_status fvn_march_masked(fvn_ctx* ctx, const fvn_volume* vol, cons
     if ((st = validate_camera(ctx, cam)) != FVN_OK) return st;
     FVN_CHECK_ARG(ctx, tf && tf->rgba && tf->n >= 2 && tf->n <= 4096, "transfer function needs 2..4096 entries");
     FVN_CHECK_ARG(ctx, ((uintptr_t)tf->rgba & 15) == 0, "transfer function must be 16-byte aligned");
-    FVN_CHECK_ARG(ctx, mp != nullptr && mp->step_vox > 0.f && mp->term_alpha > 0.f && mp->term_alpha <= 1.f,
-                  "bad march parameters");
+    if ((st = validate_march_params(ctx, mp)) != FVN_OK) return st;
     FVN_CHECK_ARG(ctx, rgbam != nullptr, "rgbam output is NULL");
     return march_impl(ctx, vol, tf, cam, mp, nullptr, nullptr, rgbam, nsamples, as_stream(stream), mask);
 }

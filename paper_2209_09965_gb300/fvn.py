@@ -68,7 +68,7 @@ class FoveationC(ctypes.Structure):
 
 class MarchParamsC(ctypes.Structure):
     _fields_ = [("step_vox", ctypes.c_float), ("term_alpha", ctypes.c_float), ("bg", ctypes.c_float * 3),
-                ("shading", ctypes.c_int)]
+                ("shading", ctypes.c_int), ("light_dir", ctypes.c_float * 3), ("shadow_rate", ctypes.c_int)]
 
 
 class ViewC(ctypes.Structure):
@@ -187,6 +187,8 @@ def march_params(mp) -> MarchParamsC:
     c.step_vox, c.term_alpha = float(mp.step_vox), float(mp.term_alpha)
     c.bg[:] = [float(v) for v in mp.bg]
     c.shading = int(mp.shading)
+    c.light_dir[:] = [float(v) for v in getattr(mp, "light_dir", (0.0, 1.0, 0.0))]
+    c.shadow_rate = int(getattr(mp, "shadow_rate", 4))
     return c
 
 
