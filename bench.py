@@ -313,8 +313,9 @@ def run_shadows(fvn, wl, weights, conv, vol, tf, frames, dev, nframes, flush):
         ids = torch.empty(W * H, dtype=torch.int32, device=dev)
         count = torch.zeros(1, dtype=torch.int32, device=dev)
         c.make_mask(fov0, W, H, mask, ids, count)
-        tuned = {"march": autotune.tune_march(c, vol, tf, cam0, mp, rgbam, ids=ids, count=count),
-                 "dense_march": autotune.tune_march(c, vol, tf, cam0, mp, dense)}
+        grid = dict(refills=(1, 16), coops=(0, 4, 16, 32), blocks=(0,))
+        tuned = {"dense_march": autotune.tune_march(c, vol, tf, cam0, mp, dense, **grid),
+                 "march": autotune.tune_march(c, vol, tf, cam0, mp, rgbam, ids=ids, count=count, **grid)}
         for k in tuned.values():
             k.pop("candidates", None)
         for i in range(3):
@@ -350,6 +351,21 @@ def run_shadows(fvn, wl, weights, conv, vol, tf, frames, dev, nframes, flush):
             dense_ms.append(e[2].elapsed_time(e[3]))
             march_ms.append(e[4].elapsed_time(e[5]))
             psnrs.append(psnr_t(rgb, dense[:3]))
+        # the same marches again with the shadow rays' samples counted too
+        c.set_option(fvn.OPT_MARCH_COUNT_SHADOW, 1)
+        all_sparse = all_dense = 0
+        for i in range(nframes):
+            cam, fov = frames[i % len(frames)]
+            c.make_mask(fov, W, H, mask, ids, count)
+            nsamp.zero_()
+            c.march(vol, tf, cam, mp, rgbam, ids=ids, count=count, nsamples=nsamp)
+            torch.cuda.synchronize()
+            all_sparse += int(nsamp.item())
+            nsamp.zero_()
+            c.march(vol, tf, cam, mp, dense, nsamples=nsamp)
+            torch.cuda.synchronize()
+            all_dense += int(nsamp.item())
+        c.set_option(fvn.OPT_MARCH_COUNT_SHADOW, 0)
         c.device_status()
         fps = nframes / (sum(fov_ms) / 1000.0)
         dfps = nframes / (sum(dense_ms) / 1000.0)
@@ -362,8 +378,11 @@ def run_shadows(fvn, wl, weights, conv, vol, tf, frames, dev, nframes, flush):
                 "stage_ms": {"sparse_march": float(np.mean(march_ms)), "dense_march": float(np.mean(dense_ms))},
                 "gsamples_per_s": {"sparse_march": sparse_samples / (sum(march_ms) / 1000.0) / 1e9,
                                    "dense_march": dense_samples / (sum(dense_ms) / 1000.0) / 1e9,
-                                   "note": "primary samples only; each shaded sample also marches its "
-                                           "shadow ray"},
+                                   "sparse_march_with_shadow_rays": all_sparse / (sum(march_ms) / 1000.0) / 1e9,
+                                   "dense_march_with_shadow_rays": all_dense / (sum(dense_ms) / 1000.0) / 1e9,
+                                   "note": "primary samples, and primary plus shadow-ray samples"},
+                "shadow_samples_per_primary_sample": {"sparse": (all_sparse - sparse_samples) / sparse_samples,
+                                                      "dense": (all_dense - dense_samples) / dense_samples},
                 "autotune": tuned}
     except Exception as exc:   # reported, not part of the metric
         return {"error": str(exc)[:200]}

@@ -139,7 +139,14 @@ fvn_status fvn_destroy(fvn_ctx* ctx);
  *      gradient volume, (v, dv/dx, dv/dy, dv/dz) as central differences per
  *      padded voxel (16 bytes each, used when that takes at most 4 GiB), and
  *      reads 8 of those per sample instead of 32 voxels; 0 = always the
- *      32-voxel stencil.  Same result up to FP32 rounding order. */
+ *      32-voxel stencil.  Same result up to FP32 rounding order.
+ *  FVN_OPT_MARCH_COUNT_SHADOW: 1 = with shading 2, the nsamples counter of a
+ *      march also counts the samples of the shadow rays (default 0: primary
+ *      samples only).
+ * A shadowed march (shading 2) first writes, besides the padded copy, a cell
+ * volume -- per padded voxel the 2 x 2 block of voxels (x..x+1, y..y+1) in
+ * the voxel type -- so that a shadow sample reads two cells instead of
+ * eight voxels; the gradient-volume option does not apply to it. */
 enum {
     FVN_OPT_CONV_KERNEL = 1,
     FVN_OPT_MARCH_REFILL = 2,
@@ -148,7 +155,8 @@ enum {
     FVN_OPT_MARCH_BLOCKS_PER_SM_DENSE = 5,
     FVN_OPT_MARCH_COOP = 6,
     FVN_OPT_MARCH_COOP_DENSE = 7,
-    FVN_OPT_MARCH_GRADIENT_VOLUME = 8
+    FVN_OPT_MARCH_GRADIENT_VOLUME = 8,
+    FVN_OPT_MARCH_COUNT_SHADOW = 9
 };
 fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value);
 

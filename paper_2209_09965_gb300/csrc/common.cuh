@@ -133,6 +133,7 @@ struct fvn_ctx {
     int march_coop = 0;               // sparse march: finish a warp's rays with the whole warp once at most this many are left
     int march_coop_dense = 0;
     int march_grad4 = 1;              // shaded marches read a gradient volume when it fits
+    int march_count_shadow = 0;       // shadowed marches also count the shadow rays' samples
     void* pad_buf = nullptr;          // padded copy of the volume read by the march
     size_t pad_bytes = 0;
     float* d_act_scale = nullptr;     // FP8 per-layer activation scales

@@ -175,6 +175,10 @@ extern "C" fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value) {
             FVN_CHECK_ARG(ctx, value == 0 || value == 1, "gradient-volume option must be 0 or 1");
             ctx->march_grad4 = value;
             return FVN_OK;
+        case FVN_OPT_MARCH_COUNT_SHADOW:
+            FVN_CHECK_ARG(ctx, value == 0 || value == 1, "shadow-sample counting option must be 0 or 1");
+            ctx->march_count_shadow = value;
+            return FVN_OK;
         default:
             return set_error(ctx, FVN_ERR_ARG, "unknown option %d", option);
     }

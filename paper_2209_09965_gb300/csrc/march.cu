@@ -41,6 +41,7 @@ constexpr int kPad = 2;
 struct MarchArgs {
     const void* vol;
     const void* pvol;                 // padded copy, (nx + 4) x (ny + 4) x (nz + 4)
+    const void* svol;                 // shading 2: shadow-ray cells over the padded box (Quad<T> each)
     int nx, ny, nz;
     int ntf;
     const float4* tf;
@@ -71,6 +72,7 @@ struct Light {
     float ilx, ily, ilz;              // 1 / l per axis (1 where l = 0)
     float ds, inv_ds;                 // shadow step (shadow_rate * dt) and its reciprocal
     int srate;                        // shadow_rate
+    int count;                        // add the shadow rays' samples to the sample counter
 };
 
 // A shadow ray stops once the light's transmittance falls below this; the
@@ -95,6 +97,66 @@ template <>
 __device__ __forceinline__ float load_norm<__half>(const __half* p) {
     return __saturatef(__half2float(__ldg(p)));
 }
+
+// Shadow-ray cells (shading 2): per padded voxel (x, y, z) the 2 x 2 block
+// (v(x, y), v(x + 1, y), v(x, y + 1), v(x + 1, y + 1)) at z, in the voxel type,
+// so the 8 voxels of a shadow sample are two vector loads (the cells at z
+// and z + 1) instead of eight scalar ones.
+template <typename T>
+struct Quad;
+template <>
+struct Quad<float> {
+    using type = float4;
+    __device__ static __forceinline__ type make(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
+    __device__ static __forceinline__ void norm(const type& q, float& a, float& b, float& c, float& d) {
+        a = __saturatef(q.x);
+        b = __saturatef(q.y);
+        c = __saturatef(q.z);
+        d = __saturatef(q.w);
+    }
+};
+template <>
+struct Quad<uint16_t> {
+    using type = ushort4;
+    __device__ static __forceinline__ type make(uint16_t a, uint16_t b, uint16_t c, uint16_t d) {
+        return make_ushort4(a, b, c, d);
+    }
+    __device__ static __forceinline__ void norm(const type& q, float& a, float& b, float& c, float& d) {
+        a = (float)q.x * (1.0f / 65535.0f);
+        b = (float)q.y * (1.0f / 65535.0f);
+        c = (float)q.z * (1.0f / 65535.0f);
+        d = (float)q.w * (1.0f / 65535.0f);
+    }
+};
+template <>
+struct Quad<uint8_t> {
+    using type = uchar4;
+    __device__ static __forceinline__ type make(uint8_t a, uint8_t b, uint8_t c, uint8_t d) {
+        return make_uchar4(a, b, c, d);
+    }
+    __device__ static __forceinline__ void norm(const type& q, float& a, float& b, float& c, float& d) {
+        a = (float)q.x * (1.0f / 255.0f);
+        b = (float)q.y * (1.0f / 255.0f);
+        c = (float)q.z * (1.0f / 255.0f);
+        d = (float)q.w * (1.0f / 255.0f);
+    }
+};
+template <>
+struct Quad<__half> {
+    using type = uint2;   // four halves
+    __device__ static __forceinline__ type make(__half a, __half b, __half c, __half d) {
+        const __half2 lo = __halves2half2(a, b), hi = __halves2half2(c, d);
+        return make_uint2(*reinterpret_cast<const unsigned*>(&lo), *reinterpret_cast<const unsigned*>(&hi));
+    }
+    __device__ static __forceinline__ void norm(const type& q, float& a, float& b, float& c, float& d) {
+        const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+        const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+        a = __saturatef(lo.x);
+        b = __saturatef(lo.y);
+        c = __saturatef(hi.x);
+        d = __saturatef(hi.y);
+    }
+};
 
 // floor without conversion instructions (|x| < 2^22): returns i with
 // x - i in [0, 1] (either neighbour at an exact integer, where the trilinear
@@ -289,12 +351,30 @@ __device__ __forceinline__ int tf_index(const MarchArgs& a, float tfmax, float v
     return ti;
 }
 
-// TF opacity at value v.
+// TF opacity at value v, from the table of opacity pairs (a_i, a_i+1) that
+// shadowed marches keep in shared memory right after the TF (one 8-byte
+// read with few bank conflicts, where the .w of two float4 entries would be
+// two reads over a quarter of the banks).
 __device__ __forceinline__ float tf_alpha(const MarchArgs& a, const float4* s_tf, float tfmax, float v) {
     float fr;
     const int ti = tf_index(a, tfmax, v, fr);
-    const float a0 = s_tf[ti].w, a1 = s_tf[ti + 1].w;
-    return fmaf(fr, a1 - a0, a0);
+    const float2 p = reinterpret_cast<const float2*>(s_tf + a.ntf)[ti];
+    return fmaf(fr, p.y - p.x, p.x);
+}
+
+// Shared-memory slots (float4) of a TF of n entries: the entries, and for
+// shadowed marches the opacity pairs after them.
+__host__ __device__ __forceinline__ int tf_slots(int n, int shade) { return shade == 2 ? n + (n + 1) / 2 : n; }
+
+// Copy a TF of n entries into shared memory at s (and its opacity pairs for
+// shadowed marches); the block's threads share the work.
+template <int SHADE>
+__device__ __forceinline__ void load_tf(float4* s, const float4* __restrict__ tf, int n) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = tf[i];
+    if (SHADE == 2) {
+        float2* p = reinterpret_cast<float2*>(s + n);
+        for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = make_float2(tf[i].w, tf[min(i + 1, n - 1)].w);
+    }
 }
 
 // TF lookup at value v: returns the opacity and, when it is > 0, the colour.
@@ -362,53 +442,60 @@ __device__ __forceinline__ void phong_lit(const Light& a, float gx, float gy, fl
     cb = __saturatef(fmaf(cb, diff, spec));
 }
 
-// Light reaching a sample: the shadow ray from the sample point u
-// (voxel-centre coordinates) towards the light, with samples at j ds,
-// j = 1, 2, ..., while inside the box.  Each multiplies the transmittance by
-// (1 - a)^shadow_rate, the last one by the power for the part of its step
-// left inside the box (so the result is continuous in the exit distance);
-// the ray stops once the transmittance falls below kShadowCutoff.  Two
-// samples' loads are issued before either is used.
 // The voxel-centre coordinate of the face a shadow ray along l leaves the
 // box [0, n] by (1e30 where l = 0: that axis never bounds it).
 __device__ __forceinline__ float exit_face(float l, int n) {
     return l > 0.0f ? (float)n - 0.5f : (l < 0.0f ? -0.5f : 1e30f);
 }
 
+// Light reaching a sample: the shadow ray from the sample point u
+// (voxel-centre coordinates) towards the light, with samples at j ds,
+// j = 1, 2, ..., while inside the box.  Each multiplies the transmittance by
+// (1 - a)^shadow_rate, the last one by the power for the part of its step
+// left inside the box (so the result is continuous in the exit distance);
+// the ray stops once the transmittance falls below kShadowCutoff.  The loads
+// of kG consecutive samples are issued before any is used.
 template <typename Src, typename I>
 __device__ __forceinline__ float shadow_ray(const MarchArgs& a, const Light& lt,
                                             const typename Src::V* __restrict__ vol, const float4* s_tf, float tfmax,
-                                            I sy, I sz, float ux, float uy, float uz) {
+                                            I sy, I sz, float ux, float uy, float uz, unsigned& nsh) {
+    constexpr int kG = 4;   // samples whose loads are in flight together
     const float se = fminf(fminf((exit_face(lt.lx, a.nx) - ux) * lt.ilx, (exit_face(lt.ly, a.ny) - uy) * lt.ily),
                            (exit_face(lt.lz, a.nz) - uz) * lt.ilz);
     float tr = 1.0f;
-    for (float j = 1.0f;; j += 2.0f) {
-        const float s0 = j * lt.ds;
-        if (!(s0 < se)) break;
-        const float s1 = (j + 1.0f) * lt.ds;
-        const bool has1 = s1 < se;
-        const float s1c = has1 ? s1 : s0;
-        Cell C0, C1;
-        Src::template load_cell<I>(a, vol, sy, sz, fmaf(s0, lt.lx, ux), fmaf(s0, lt.ly, uy), fmaf(s0, lt.lz, uz),
-                                   C0);
-        Src::template load_cell<I>(a, vol, sy, sz, fmaf(s1c, lt.lx, ux), fmaf(s1c, lt.ly, uy), fmaf(s1c, lt.lz, uz),
-                                   C1);
+    for (float j = 1.0f;; j += (float)kG) {
+        if (!(j * lt.ds < se)) break;
+        Cell C[kG];
+        float sj[kG];
 #pragma unroll
-        for (int q = 0; q < 2; ++q) {
-            const float al = tf_alpha(a, s_tf, tfmax, cell_value(q ? C1 : C0));
+        for (int q = 0; q < kG; ++q) {
+            sj[q] = (j + (float)q) * lt.ds;
+            const float sc = sj[q] < se ? sj[q] : j * lt.ds;   // past the exit: reload the first (unused)
+            Src::template load_cell<I>(a, vol, sy, sz, fmaf(sc, lt.lx, ux), fmaf(sc, lt.ly, uy), fmaf(sc, lt.lz, uz),
+                                       C[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < kG; ++q) {
+            if (!(sj[q] < se)) return tr;
+            ++nsh;
+            const float al = tf_alpha(a, s_tf, tfmax, cell_value(C[q]));
             if (al > 0.0f) {
                 const float base = 1.0f - al;
-                const float e = (se - (q ? s1 : s0)) * lt.inv_ds;   // steps left inside the box
-                float f;
+                const float e = (se - sj[q]) * lt.inv_ds;   // steps left inside the box
+                float f = base;
                 if (e >= 1.0f) {
-                    f = base;
-                    for (int i = 1; i < lt.srate; ++i) f *= base;
+                    if (lt.srate == 4) {
+                        f *= f;
+                        f *= f;
+                    } else {
+                        for (int i = 1; i < lt.srate; ++i) f *= base;
+                    }
                 } else {
                     f = base > 0.0f ? exp2f((float)lt.srate * e * log2f(base)) : 0.0f;
                 }
                 tr *= f;
             }
-            if (tr < kShadowCutoff || (q == 0 && !has1)) return tr;
+            if (tr < kShadowCutoff) return tr;
         }
     }
     return tr;
@@ -453,11 +540,12 @@ template <typename Src, int SHADE, typename I>
 __device__ __forceinline__ void light_sample(const MarchArgs& a, const Light& lt,
                                              const typename Src::V* __restrict__ vol, const float4* s_tf, float tfmax,
                                              I sy, I sz, float gx, float gy, float gz, float ux, float uy, float uz,
-                                             float dx, float dy, float dz, float& cr, float& cg, float& cb) {
-    if (SHADE == 1) {
+                                             float dx, float dy, float dz, float& cr, float& cg, float& cb,
+                                             unsigned& nsh) {
+    if constexpr (SHADE == 1) {
         phong(gx, gy, gz, dx, dy, dz, cr, cg, cb);
-    } else {
-        const float tr = shadow_ray<Src, I>(a, lt, vol, s_tf, tfmax, sy, sz, ux, uy, uz);
+    } else if constexpr (SHADE == 2) {
+        const float tr = shadow_ray<Src, I>(a, lt, vol, s_tf, tfmax, sy, sz, ux, uy, uz, nsh);
         phong_lit(lt, gx, gy, gz, dx, dy, dz, tr, cr, cg, cb);
     }
 }
@@ -472,18 +560,16 @@ struct ScalarSrc {
                                                 float uy, float uz, St& S) {
         load_stencil<T, I, SHADE>(a, vol, sy, sz, ux, uy, uz, S);
     }
+    // the 8 voxels of a shadow sample: two cells of the shadow-ray cell volume
     template <typename I>
-    __device__ static __forceinline__ void load_cell(const MarchArgs& a, const V* __restrict__ vol, I sy, I sz,
-                                                     float ux, float uy, float uz, Cell& C) {
-        const V* b = vol + cell_base<I>(a, sy, sz, ux, uy, uz, C.tx, C.ty, C.tz);
-#pragma unroll
-        for (int z = 0; z < 2; ++z)
-#pragma unroll
-            for (int y = 0; y < 2; ++y) {
-                const V* r = b + (I)z * sz + (I)y * sy;
-                C.c[z][y][0] = load_norm(r);
-                C.c[z][y][1] = load_norm(r + 1);
-            }
+    __device__ static __forceinline__ void load_cell(const MarchArgs& a, const V* __restrict__, I sy, I sz, float ux,
+                                                     float uy, float uz, Cell& C) {
+        using Q = Quad<T>;
+        const typename Q::type* b =
+            static_cast<const typename Q::type*>(a.svol) + cell_base<I>(a, sy, sz, ux, uy, uz, C.tx, C.ty, C.tz);
+        const typename Q::type q0 = __ldg(b), q1 = __ldg(b + sz);
+        Q::norm(q0, C.c[0][0][0], C.c[0][0][1], C.c[0][1][0], C.c[0][1][1]);
+        Q::norm(q1, C.c[1][0][0], C.c[1][0][1], C.c[1][1][0], C.c[1][1][1]);
     }
     // Classify and shade one loaded sample: returns its opacity al and, when
     // al > 0, its (clamped) shaded colour.
@@ -491,14 +577,14 @@ struct ScalarSrc {
     __device__ static __forceinline__ float shade(const MarchArgs& a, const Light& lt, const V* __restrict__ vol,
                                                   const float4* s_tf, float tfmax, I sy, I sz, const St& S, float ux,
                                                   float uy, float uz, float dx, float dy, float dz, float& cr,
-                                                  float& cg, float& cb) {
+                                                  float& cg, float& cb, unsigned& nsh) {
         float rows[2][2];
         const float al = tf_lookup(a, s_tf, tfmax, stencil_value(S, rows), cr, cg, cb);
         if (SHADE != 0 && al > 0.0f) {
             float gx, gy, gz;
             stencil_gradient(S, rows, gx, gy, gz);
             light_sample<ScalarSrc<T>, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, gx, gy, gz, ux, uy, uz, dx, dy,
-                                                 dz, cr, cg, cb);
+                                                 dz, cr, cg, cb, nsh);
         }
         return al;
     }
@@ -531,25 +617,11 @@ struct Grad4Src {
                 S.c[z][y][1] = __ldg(r + 1);
             }
     }
-    // values only: the first component of each voxel
-    template <typename I>
-    __device__ static __forceinline__ void load_cell(const MarchArgs& a, const V* __restrict__ vol, I sy, I sz,
-                                                     float ux, float uy, float uz, Cell& C) {
-        const V* b = vol + cell_base<I>(a, sy, sz, ux, uy, uz, C.tx, C.ty, C.tz);
-#pragma unroll
-        for (int z = 0; z < 2; ++z)
-#pragma unroll
-            for (int y = 0; y < 2; ++y) {
-                const float* r = reinterpret_cast<const float*>(b + (I)z * sz + (I)y * sy);
-                C.c[z][y][0] = __ldg(r);
-                C.c[z][y][1] = __ldg(r + 4);
-            }
-    }
     template <int SHADE, typename I>
     __device__ static __forceinline__ float shade(const MarchArgs& a, const Light& lt, const V* __restrict__ vol,
                                                   const float4* s_tf, float tfmax, I sy, I sz, const St& S, float ux,
                                                   float uy, float uz, float dx, float dy, float dz, float& cr,
-                                                  float& cg, float& cb) {
+                                                  float& cg, float& cb, unsigned& nsh) {
         float rows[2][2];
 #pragma unroll
         for (int z = 0; z < 2; ++z)
@@ -572,7 +644,7 @@ struct Grad4Src {
             for (int c = 0; c < 3; ++c)
                 g[c] = lerpf(lerpf(gr[c][0][0], gr[c][0][1], S.ty), lerpf(gr[c][1][0], gr[c][1][1], S.ty), S.tz);
             light_sample<Grad4Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, g[0], g[1], g[2], ux, uy, uz, dx, dy,
-                                             dz, cr, cg, cb);
+                                             dz, cr, cg, cb, nsh);
         }
         return al;
     }
@@ -584,10 +656,10 @@ template <typename Src, int SHADE, typename I>
 __device__ __forceinline__ bool composite_sample(const MarchArgs& a, const Light& lt,
                                                  const typename Src::V* __restrict__ vol, const float4* s_tf,
                                                  float tfmax, I sy, I sz, const typename Src::St& S, float ux,
-                                                 float uy, float uz, Ray& s) {
+                                                 float uy, float uz, Ray& s, unsigned& nsh) {
     float cr, cg, cb;
     const float al = Src::template shade<SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S, ux, uy, uz, s.dx, s.dy, s.dz,
-                                                   cr, cg, cb);
+                                                   cr, cg, cb, nsh);
     if (al > 0.0f) {
         const float w = (1.0f - s.A) * al;
         s.C0 = fmaf(w, cr, s.C0);
@@ -604,9 +676,18 @@ __device__ __forceinline__ bool composite_sample(const MarchArgs& a, const Light
 template <typename Src, typename I, int SHADE>
 __device__ __forceinline__ bool ray_step(const MarchArgs& a, const Light& lt, const typename Src::V* __restrict__ vol,
                                          const float4* s_tf, I sy, I sz, float ux0, float uy0, float uz0,
-                                         float tfmax, Ray& s) {
+                                         float tfmax, Ray& s, unsigned& nsh) {
     const float t0 = fmaf(s.kf, a.dt, s.tnear);
     if (!(t0 < s.tfar)) return true;
+    if constexpr (SHADE == 2) {
+        // a shadowed sample's time goes into its shadow ray: one sample per
+        // step, so no second stencil stays live across it
+        typename Src::St S0;
+        const float px0 = fmaf(t0, s.dx, ux0), py0 = fmaf(t0, s.dy, uy0), pz0 = fmaf(t0, s.dz, uz0);
+        Src::template load<I, true>(a, vol, sy, sz, px0, py0, pz0, S0);
+        s.kf += 1.0f;
+        return composite_sample<Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S0, px0, py0, pz0, s, nsh);
+    }
     const float t1 = fmaf(s.kf + 1.0f, a.dt, s.tnear);
     const bool has1 = t1 < s.tfar;
     const float t1c = has1 ? t1 : t0;
@@ -616,10 +697,10 @@ __device__ __forceinline__ bool ray_step(const MarchArgs& a, const Light& lt, co
     Src::template load<I, SHADE != 0>(a, vol, sy, sz, px0, py0, pz0, S0);
     Src::template load<I, SHADE != 0>(a, vol, sy, sz, px1, py1, pz1, S1);
     s.kf += 1.0f;
-    if (composite_sample<Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S0, px0, py0, pz0, s)) return true;
+    if (composite_sample<Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S0, px0, py0, pz0, s, nsh)) return true;
     if (!has1) return true;
     s.kf += 1.0f;
-    return composite_sample<Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S1, px1, py1, pz1, s);
+    return composite_sample<Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S1, px1, py1, pz1, s, nsh);
 }
 
 // Cooperative march of one ray by the whole warp, for the last few rays of a
@@ -633,7 +714,7 @@ __device__ __forceinline__ bool ray_step(const MarchArgs& a, const Light& lt, co
 template <typename Src, typename I, int SHADE>
 __device__ __forceinline__ void coop_ray(const MarchArgs& a, const Light& lt, const typename Src::V* __restrict__ vol,
                                          const float4* s_tf, I sy, I sz, float ux0, float uy0, float uz0, float tfmax,
-                                         Ray& r) {
+                                         Ray& r, unsigned& nsh) {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     for (;;) {
@@ -647,7 +728,7 @@ __device__ __forceinline__ void coop_ray(const MarchArgs& a, const Light& lt, co
             const float px = fmaf(t, r.dx, ux0), py = fmaf(t, r.dy, uy0), pz = fmaf(t, r.dz, uz0);
             Src::template load<I, SHADE != 0>(a, vol, sy, sz, px, py, pz, S);
             al = Src::template shade<SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S, px, py, pz, r.dx, r.dy, r.dz, cr,
-                                               cg, cb);
+                                               cg, cb, nsh);
             if (!(al > 0.0f)) al = 0.0f;
         }
         // incl = prod_{i <= j} (1 - al_i), excl = prod_{i < j} (1 - al_i)
@@ -703,10 +784,12 @@ __device__ __forceinline__ Ray shfl_ray(const Ray& s, int src) {
 // idle lanes take new rays from the global queue together (one atomic per
 // warp), so warps neither wait for their longest ray nor for the slowest
 // warp at the end of the queue.
+// Shadowed marches spend their time in independent shadow-ray samples:
+// registers are capped for five CTAs per SM (more warps to hide latency).
 template <typename Src, typename I, int SHADE>
-__global__ void __launch_bounds__(128) march_kernel(MarchArgs a, Light lt) {
+__global__ void __launch_bounds__(128, SHADE == 2 ? 5 : 1) march_kernel(MarchArgs a, Light lt) {
     extern __shared__ float4 s_tf[];
-    for (int i = threadIdx.x; i < a.ntf; i += blockDim.x) s_tf[i] = a.tf[i];
+    load_tf<SHADE>(s_tf, a.tf, a.ntf);
     __syncthreads();
     const unsigned FULL = 0xffffffffu;
     const typename Src::V* __restrict__ vol = static_cast<const typename Src::V*>(a.pvol);
@@ -719,6 +802,7 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a, Light lt) {
     // sample positions are handled in voxel-centre coordinates u = p - 0.5
     const float ux0 = a.ox - 0.5f, uy0 = a.oy - 0.5f, uz0 = a.oz - 0.5f;
     unsigned long long my_samples = 0;
+    unsigned nsh = 0;                 // shadow-ray samples of this lane
     Ray s;
     s.pix = -1;
     if (a.coop_below >= 32) {
@@ -730,7 +814,7 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a, Light lt) {
             r = __shfl_sync(FULL, r, 0);
             if (r >= nrays) break;
             if (!start_ray(a, r, npix, s)) continue;   // every lane sets up the same ray
-            if (s.tfar > -INFINITY) coop_ray<Src, I, SHADE>(a, lt, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s);
+            if (s.tfar > -INFINITY) coop_ray<Src, I, SHADE>(a, lt, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s, nsh);
             if (lane == 0) {
                 my_samples += (unsigned long long)s.kf;
                 finish_ray(a, s);
@@ -768,7 +852,7 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a, Light lt) {
                 do {
                     const int src = __ffs(busy) - 1;
                     Ray r = shfl_ray(s, src);
-                    coop_ray<Src, I, SHADE>(a, lt, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+                    coop_ray<Src, I, SHADE>(a, lt, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, r, nsh);
                     if (lane == src) {
                         s = r;
                         my_samples += (unsigned long long)s.kf;
@@ -779,7 +863,7 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a, Light lt) {
                 } while (busy != 0);
                 break;
             }
-            if (s.pix >= 0 && ray_step<Src, I, SHADE>(a, lt, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s)) {
+            if (s.pix >= 0 && ray_step<Src, I, SHADE>(a, lt, vol, s_tf, sy, sz, ux0, uy0, uz0, tfmax, s, nsh)) {
                 my_samples += (unsigned long long)s.kf;
                 finish_ray(a, s);
                 s.pix = -1;
@@ -789,6 +873,7 @@ __global__ void __launch_bounds__(128) march_kernel(MarchArgs a, Light lt) {
         if (exhausted && busy == 0) break;
     }
     if (a.nsamples) {
+        if (SHADE == 2 && lt.count) my_samples += nsh;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) my_samples += __shfl_xor_sync(FULL, my_samples, o);
         if (lane == 0 && my_samples) atomicAdd(a.nsamples, my_samples);
@@ -827,33 +912,36 @@ static_assert(sizeof(MarchBatch) <= 4096, "batched march arguments exceed the 4 
 constexpr int kGrad4 = 16;
 
 template <typename I, int SHADE>
-__device__ __forceinline__ bool batch_step(const MarchBatchView& bv, const Light& lt, const float4* s_tf, Ray& s) {
+__device__ __forceinline__ bool batch_step(const MarchBatchView& bv, const Light& lt, const float4* s_tf, Ray& s,
+                                           unsigned& nsh) {
     const MarchArgs& a = bv.a;
     const I sy = (I)(a.nx + 2 * kPad), sz = sy * (I)(a.ny + 2 * kPad);
     const float ux0 = a.ox - 0.5f, uy0 = a.oy - 0.5f, uz0 = a.oz - 0.5f;
     const float tfmax = (float)(a.ntf - 1);
     const float4* tf = s_tf + bv.tf_off;
     switch (bv.dtype) {
-        case kGrad4:
-            return ray_step<Grad4Src, I, SHADE>(a, lt, static_cast<const float4*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
-                                                tfmax, s);
+        case kGrad4:   // never with shading 2 (shadowed marches read the padded copy and the cells)
+            if constexpr (SHADE == 2) return true;
+            else return ray_step<Grad4Src, I, SHADE>(a, lt, static_cast<const float4*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
+                                                tfmax, s, nsh);
         case FVN_U8:
             return ray_step<ScalarSrc<uint8_t>, I, SHADE>(a, lt, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0,
-                                                          uy0, uz0, tfmax, s);
+                                                          uy0, uz0, tfmax, s, nsh);
         case FVN_U16:
             return ray_step<ScalarSrc<uint16_t>, I, SHADE>(a, lt, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0,
-                                                           uy0, uz0, tfmax, s);
+                                                           uy0, uz0, tfmax, s, nsh);
         case FVN_F16:
             return ray_step<ScalarSrc<__half>, I, SHADE>(a, lt, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0,
-                                                         uz0, tfmax, s);
+                                                         uz0, tfmax, s, nsh);
         default:
             return ray_step<ScalarSrc<float>, I, SHADE>(a, lt, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0,
-                                                        uz0, tfmax, s);
+                                                        uz0, tfmax, s, nsh);
     }
 }
 
 template <typename I, int SHADE>
-__device__ __forceinline__ void batch_coop(const MarchBatchView& bv, const Light& lt, const float4* s_tf, Ray& r) {
+__device__ __forceinline__ void batch_coop(const MarchBatchView& bv, const Light& lt, const float4* s_tf, Ray& r,
+                                           unsigned& nsh) {
     const MarchArgs& a = bv.a;
     const I sy = (I)(a.nx + 2 * kPad), sz = sy * (I)(a.ny + 2 * kPad);
     const float ux0 = a.ox - 0.5f, uy0 = a.oy - 0.5f, uz0 = a.oz - 0.5f;
@@ -861,33 +949,34 @@ __device__ __forceinline__ void batch_coop(const MarchBatchView& bv, const Light
     const float4* tf = s_tf + bv.tf_off;
     switch (bv.dtype) {
         case kGrad4:
-            coop_ray<Grad4Src, I, SHADE>(a, lt, static_cast<const float4*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax, r);
+            if constexpr (SHADE != 2) coop_ray<Grad4Src, I, SHADE>(a, lt, static_cast<const float4*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax, r, nsh);
             break;
         case FVN_U8:
             coop_ray<ScalarSrc<uint8_t>, I, SHADE>(a, lt, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
-                                                   tfmax, r);
+                                                   tfmax, r, nsh);
             break;
         case FVN_U16:
             coop_ray<ScalarSrc<uint16_t>, I, SHADE>(a, lt, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0, uy0,
-                                                    uz0, tfmax, r);
+                                                    uz0, tfmax, r, nsh);
             break;
         case FVN_F16:
             coop_ray<ScalarSrc<__half>, I, SHADE>(a, lt, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
-                                                  tfmax, r);
+                                                  tfmax, r, nsh);
             break;
         default:
             coop_ray<ScalarSrc<float>, I, SHADE>(a, lt, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
-                                                 tfmax, r);
+                                                 tfmax, r, nsh);
             break;
     }
 }
 
 template <typename I, int SHADE>
-__global__ void __launch_bounds__(128) march_batch_kernel(const __grid_constant__ MarchBatch b) {
+__global__ void __launch_bounds__(128, SHADE == 2 ? 5 : 1)
+    march_batch_kernel(const __grid_constant__ MarchBatch b) {
     extern __shared__ float4 s_tf[];
     __shared__ int s_start[kMaxViews + 1];   // first ticket of each view
     for (int k = 0; k < b.ntfs; ++k)
-        for (int i = threadIdx.x; i < b.tf_n[k]; i += blockDim.x) s_tf[b.tf_off[k] + i] = b.tf[k][i];
+        load_tf<SHADE>(s_tf + b.tf_off[k], b.tf[k], b.tf_n[k]);
     if (threadIdx.x == 0) {
         int acc = 0;
         for (int v = 0; v < b.nviews; ++v) {
@@ -902,6 +991,7 @@ __global__ void __launch_bounds__(128) march_batch_kernel(const __grid_constant_
     const int lane = threadIdx.x & 31;
     const int nrays = s_start[b.nviews];
     unsigned long long my_samples = 0;
+    unsigned nsh = 0;                 // shadow-ray samples of this lane
     Ray s;
     s.pix = -1;
     int view = 0;
@@ -941,7 +1031,7 @@ __global__ void __launch_bounds__(128) march_batch_kernel(const __grid_constant_
                     const int src = __ffs(busy) - 1;
                     Ray r = shfl_ray(s, src);
                     const int v = __shfl_sync(FULL, view, src);
-                    batch_coop<I, SHADE>(b.v[v], b.light, s_tf, r);
+                    batch_coop<I, SHADE>(b.v[v], b.light, s_tf, r, nsh);
                     if (lane == src) {
                         s = r;
                         my_samples += (unsigned long long)s.kf;
@@ -952,7 +1042,7 @@ __global__ void __launch_bounds__(128) march_batch_kernel(const __grid_constant_
                 } while (busy != 0);
                 break;
             }
-            if (s.pix >= 0 && batch_step<I, SHADE>(b.v[view], b.light, s_tf, s)) {
+            if (s.pix >= 0 && batch_step<I, SHADE>(b.v[view], b.light, s_tf, s, nsh)) {
                 my_samples += (unsigned long long)s.kf;
                 finish_ray(b.v[view].a, s);
                 s.pix = -1;
@@ -962,6 +1052,7 @@ __global__ void __launch_bounds__(128) march_batch_kernel(const __grid_constant_
         if (exhausted && busy == 0) break;
     }
     if (b.nsamples) {
+        if (SHADE == 2 && b.light.count) my_samples += nsh;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) my_samples += __shfl_xor_sync(FULL, my_samples, o);
         if (lane == 0 && my_samples) atomicAdd(b.nsamples, my_samples);
@@ -1031,10 +1122,42 @@ static fvn_status grad4_volume(fvn_ctx* ctx, const void* vol, int nx, int ny, in
     return FVN_OK;
 }
 
-template <typename Src, typename I>
+// Shadow-ray cells over the padded box: cell (x, y, z) holds the padded
+// voxels (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1) at z (clamp to edge).
+// One warp per padded (y, z) row, eight rows per block.
+template <typename T>
+__global__ void __launch_bounds__(256) cell_volume_kernel(const T* __restrict__ src, int nx, int ny, int nz,
+                                                          typename Quad<T>::type* __restrict__ dst) {
+    const int px = nx + 2 * kPad, py = ny + 2 * kPad, pz = nz + 2 * kPad;
+    const int row = blockIdx.x * 8 + (threadIdx.x >> 5);
+    if (row >= py * pz) return;
+    const int z = row / py, y = row - z * py;
+    const long long zo = (long long)clampi(z - kPad, nz) * ny;
+    const T* r0 = src + (zo + clampi(y - kPad, ny)) * nx;
+    const T* r1 = src + (zo + clampi(y + 1 - kPad, ny)) * nx;
+    typename Quad<T>::type* d = dst + (long long)row * px;
+    for (int x = threadIdx.x & 31; x < px; x += 32) {
+        const int x0 = clampi(x - kPad, nx), x1 = clampi(x + 1 - kPad, nx);
+        d[x] = Quad<T>::make(r0[x0], r0[x1], r1[x0], r1[x1]);
+    }
+}
+
+template <typename T>
+static fvn_status cell_volume(fvn_ctx* ctx, const void* vol, int nx, int ny, int nz, void* cells, cudaStream_t st) {
+    const long long rows = (long long)(ny + 2 * kPad) * (nz + 2 * kPad);
+    cell_volume_kernel<T><<<(unsigned)((rows + 7) / 8), 256, 0, st>>>(
+        static_cast<const T*>(vol), nx, ny, nz, static_cast<typename Quad<T>::type*>(cells));
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+template <typename Src, typename I, bool SHADOWS = true>
 static fvn_status launch_march(fvn_ctx* ctx, const MarchArgs& a, const Light& lt, int shade, cudaStream_t st) {
-    const size_t smem = (size_t)a.ntf * sizeof(float4);
-    auto kern = shade == 2 ? march_kernel<Src, I, 2> : (shade == 1 ? march_kernel<Src, I, 1> : march_kernel<Src, I, 0>);
+    const size_t smem = (size_t)tf_slots(a.ntf, shade) * sizeof(float4);
+    auto kern = shade == 1 ? march_kernel<Src, I, 1> : march_kernel<Src, I, 0>;
+    if constexpr (SHADOWS) {
+        if (shade == 2) kern = march_kernel<Src, I, 2>;
+    }
     if (smem > 48 * 1024)
         FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;
@@ -1053,9 +1176,10 @@ static unsigned long long padded_voxels(const fvn_volume* vol) {
 }
 
 // The light of shading 2 (zero for the other modes).
-static Light make_light(const fvn_march_params* mp) {
+static Light make_light(const fvn_ctx* ctx, const fvn_march_params* mp) {
     Light lt{};
     if (mp->shading != 2) return lt;
+    lt.count = ctx->march_count_shadow;
     double l[3] = {mp->light_dir[0], mp->light_dir[1], mp->light_dir[2]};
     const double ll = sqrt(l[0] * l[0] + l[1] * l[1] + l[2] * l[2]);
     for (double& x : l) x /= ll;
@@ -1130,6 +1254,9 @@ static MarchArgs view_args(const fvn_volume* vol, const fvn_tf* tf, const fvn_ca
     return a;
 }
 
+static const void* march_cells(const fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp,
+                               const void* buf);
+
 fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
                       const fvn_march_params* mp, const int32_t* ids, const int32_t* count, float* rgbam,
                       unsigned long long* nsamples, cudaStream_t st, const uint8_t* reject) {
@@ -1155,12 +1282,13 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
         ctx->pad_bytes = bytes;
     }
     a.pvol = ctx->pad_buf;
+    a.svol = march_cells(ctx, vol, mp, ctx->pad_buf);
     fvn_status ps = march_volume_prepare(ctx, vol, mp, ctx->pad_buf, st);   // one pass over the volume
     if (ps != FVN_OK) return ps;
     const bool big = padded_voxels(vol) >= (1ull << 31);
     const int shade = mp->shading;
-    const Light lt = make_light(mp);
-    if (march_uses_grad4(ctx, vol, mp)) return launch_march<Grad4Src, int>(ctx, a, lt, shade, st);
+    const Light lt = make_light(ctx, mp);
+    if (march_uses_grad4(ctx, vol, mp)) return launch_march<Grad4Src, int, false>(ctx, a, lt, shade, st);
     switch (vol->dtype) {
         case FVN_U8:
             return big ? launch_march<ScalarSrc<uint8_t>, long long>(ctx, a, lt, shade, st)
@@ -1179,50 +1307,73 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
 
 // Shaded marches read a gradient volume (16 bytes per padded voxel) when the
 // option allows it and it takes at most 4 GiB; the others a padded copy.
+// Shadowed marches (shading 2) read the padded copy for their samples and
+// the shadow-ray cells (4 voxels per padded voxel) for their shadow rays.
 bool march_uses_grad4(const fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp) {
-    return mp->shading != 0 && ctx->march_grad4 != 0 && padded_voxels(vol) * 16ull <= (4ull << 30);
+    return mp->shading == 1 && ctx->march_grad4 != 0 && padded_voxels(vol) * 16ull <= (4ull << 30);
 }
+
+static size_t voxel_bytes(const fvn_volume* vol) {
+    return vol->dtype == FVN_U8 ? 1 : (vol->dtype == FVN_F32 ? 4 : 2);
+}
+
+// Offset of the shadow-ray cells after the padded copy.
+static size_t cells_offset(const fvn_volume* vol) {
+    return (voxel_bytes(vol) * (size_t)padded_voxels(vol) + 255) & ~(size_t)255;
+}
+
+// Shadowed marches read shadow-ray cells.
+static bool uses_cells(const fvn_ctx*, const fvn_march_params* mp) { return mp->shading == 2; }
 
 size_t march_volume_bytes(const fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp) {
     if (march_uses_grad4(ctx, vol, mp)) return 16 * (size_t)padded_voxels(vol);
-    const size_t esize = vol->dtype == FVN_U8 ? 1 : (vol->dtype == FVN_F32 ? 4 : 2);
-    return esize * (size_t)padded_voxels(vol);
+    const size_t pad = voxel_bytes(vol) * (size_t)padded_voxels(vol);
+    return uses_cells(ctx, mp) ? cells_offset(vol) + 4 * pad : pad;
+}
+
+// The shadow-ray cells inside a volume buffer (NULL when the march reads none).
+static const void* march_cells(const fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp,
+                               const void* buf) {
+    return uses_cells(ctx, mp) ? static_cast<const char*>(buf) + cells_offset(vol) : nullptr;
+}
+
+template <typename T>
+static fvn_status prepare_as(fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp, void* buf, bool g4,
+                             cudaStream_t st) {
+    if (g4) return grad4_volume<T>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st);
+    fvn_status s = pad_volume<T>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st);
+    if (s != FVN_OK || !uses_cells(ctx, mp)) return s;
+    return cell_volume<T>(ctx, vol->data, vol->nx, vol->ny, vol->nz, static_cast<char*>(buf) + cells_offset(vol),
+                          st);
 }
 
 fvn_status march_volume_prepare(fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp, void* buf,
                                 cudaStream_t st) {
     const bool g4 = march_uses_grad4(ctx, vol, mp);
     switch (vol->dtype) {
-        case FVN_U8:
-            return g4 ? grad4_volume<uint8_t>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st)
-                      : pad_volume<uint8_t>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st);
-        case FVN_U16:
-            return g4 ? grad4_volume<uint16_t>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st)
-                      : pad_volume<uint16_t>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st);
-        case FVN_F16:
-            return g4 ? grad4_volume<__half>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st)
-                      : pad_volume<__half>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st);
-        default:
-            return g4 ? grad4_volume<float>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st)
-                      : pad_volume<float>(ctx, vol->data, vol->nx, vol->ny, vol->nz, buf, st);
+        case FVN_U8: return prepare_as<uint8_t>(ctx, vol, mp, buf, g4, st);
+        case FVN_U16: return prepare_as<uint16_t>(ctx, vol, mp, buf, g4, st);
+        case FVN_F16: return prepare_as<__half>(ctx, vol, mp, buf, g4, st);
+        default: return prepare_as<float>(ctx, vol, mp, buf, g4, st);
     }
 }
 
 fvn_status march_batch_impl(fvn_ctx* ctx, const BatchMarchView* views, int n, const fvn_march_params* mp,
                             unsigned long long* nsamples, cudaStream_t st) {
     MarchBatch b{};
-    b.light = make_light(mp);
+    b.light = make_light(ctx, mp);
     b.nviews = n;
     b.nsamples = nsamples;
     b.refill_below = ctx->march_refill;
     b.coop_below = ctx->march_coop;
-    int tf_total = 0;
+    int tf_total = 0, tf_slots_total = 0;
     bool big = false;
     for (int i = 0; i < n; ++i) {
         const BatchMarchView& v = views[i];
         MarchBatchView& bv = b.v[i];
         bv.a = view_args(v.vol, v.tf, v.cam, mp);
         bv.a.pvol = v.pvol;
+        bv.a.svol = march_cells(ctx, v.vol, mp, v.pvol);
         bv.a.ids = v.ids;
         bv.a.count = v.count;
         bv.a.rgbam = v.rgbam;
@@ -1233,7 +1384,8 @@ fvn_status march_batch_impl(fvn_ctx* ctx, const BatchMarchView* views, int n, co
         if (k == b.ntfs) {
             b.tf[k] = bv.a.tf;
             b.tf_n[k] = bv.a.ntf;
-            b.tf_off[k] = tf_total;
+            b.tf_off[k] = tf_slots_total;
+            tf_slots_total += tf_slots(bv.a.ntf, mp->shading);
             tf_total += bv.a.ntf;
             ++b.ntfs;
         }
@@ -1248,7 +1400,7 @@ fvn_status march_batch_impl(fvn_ctx* ctx, const BatchMarchView* views, int n, co
                                   : (shade == 1 ? march_batch_kernel<long long, 1> : march_batch_kernel<long long, 0>))
                     : (shade == 2 ? march_batch_kernel<int, 2>
                                   : (shade == 1 ? march_batch_kernel<int, 1> : march_batch_kernel<int, 0>));
-    const size_t smem = (size_t)tf_total * sizeof(float4);
+    const size_t smem = (size_t)tf_slots_total * sizeof(float4);
     if (smem > 48 * 1024)
         FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     int per_sm = 0;

@@ -37,6 +37,7 @@ OPT_CONV_KERNEL, OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 1, 2, 3
 OPT_MARCH_REFILL_DENSE, OPT_MARCH_BLOCKS_PER_SM_DENSE = 4, 5
 OPT_MARCH_COOP, OPT_MARCH_COOP_DENSE = 6, 7
 OPT_MARCH_GRADIENT_VOLUME = 8
+OPT_MARCH_COUNT_SHADOW = 9
 CONV_TCGEN05, CONV_MMA_SYNC = 0, 1
 
 

@@ -1,9 +1,11 @@
 """GPU parity of the shadowed shading mode (shading 2: a directional light,
 one shadow ray per sample at 1 / shadow_rate of the main sample rate) against
 the FP64 oracle, 1e-4 max-abs per channel, through the C ABI: every voxel
-type, both sample sources (stencil of the padded copy and gradient volume),
-the cooperative march modes, sparse 1080p, random lights including
-axis-aligned ones, the batched march, and the argument checks."""
+type (shadow rays read a cell volume of 2 x 2 voxel blocks in the voxel
+type; the gradient-volume option does not apply to them), the cooperative
+march modes, sparse 1080p, random lights including axis-aligned ones, the
+batched march with several transfer functions (whose opacity-pair tables
+share shared memory), and the argument checks."""
 import numpy as np
 import pytest
 import torch
@@ -63,7 +65,7 @@ def test_shadow_dense_small_blobs(ctx, rate):
 
 @pytest.mark.parametrize("grad_volume", [0, 1])
 @pytest.mark.parametrize("dtype", ["u8", "u16", "f16", "f32"])
-def test_shadow_dtypes_and_sample_sources(ctx, fvn, grad_volume, dtype):
+def test_shadow_dtypes(ctx, fvn, grad_volume, dtype):
     base = wl.value_noise_volume(36, seed=9, base_spacing=8).numpy()
     vol = {"u8": np.round(base * 255).astype(np.uint8), "u16": np.round(base * 65535).astype(np.uint16),
            "f16": base.astype(np.float16), "f32": base.astype(np.float32)}[dtype]
@@ -72,7 +74,7 @@ def test_shadow_dtypes_and_sample_sources(ctx, fvn, grad_volume, dtype):
     cam = wl.orbit_camera(5, 3, width=80, height=56, radius_factor=(0.9, 1.3))
     mp = shadow_params(4, light=(-0.5, 0.7, 0.2))
     try:
-        ctx.set_option(fvn.OPT_MARCH_GRADIENT_VOLUME, grad_volume)
+        ctx.set_option(fvn.OPT_MARCH_GRADIENT_VOLUME, grad_volume)    # does not apply to shadowed marches
         out, _ = run_march(ctx, vol_t, tf, cam, mp)
         march_parity(vol, tf, cam, mp, out, max_amb_frac=0.05)
         ids = np.arange(1, 80 * 56, 3, dtype=np.int32)
@@ -128,7 +130,6 @@ def test_shadow_sparse_1080p_sampled(ctx):
     flat = out.reshape(5, -1)
     rest = np.setdiff1d(np.arange(1920 * 1080), ids)
     assert np.all(flat[:, rest] == 0.0) and np.all(flat[4, ids] == 1.0)
-    # shadows darken: never brighter than the same light without occlusion would allow
     assert ns > 0
 
 
@@ -150,13 +151,14 @@ def test_shadow_batch_equals_single_views(fvn):
         u8 = np.round(wl.blob_volume(40, seed=11).numpy() * 255.0).astype(np.uint8)
         f32 = wl.value_noise_volume(32, seed=12, base_spacing=8).numpy().astype(np.float32)
         vols = [torch.from_numpy(u8).to(dev), torch.from_numpy(f32).to(dev)]
-        tf = torch.from_numpy(wl.transfer_function(31, alpha_max=0.3)).to(dev)
+        tfs = [torch.from_numpy(wl.transfer_function(31, alpha_max=0.3)).to(dev),
+               torch.from_numpy(wl.transfer_function(32, alpha_max=0.5, n=77)).to(dev)]
         mp = shadow_params(4, light=(0.2, 0.9, -0.3))
         views = []
         for i, (w, h) in enumerate([(96, 64), (61, 45), (128, 72)]):
             cam = wl.orbit_camera(20 + i, i, width=w, height=h, radius_factor=(1.0, 1.4))
             fov = wl.Foveation(focal_px=wl.focal_point(20 + i, i, w, h), seed=20 + i, frame=i)
-            views.append({"vol": vols[i % 2], "tf": tf, "cam": cam, "fov": fov,
+            views.append({"vol": vols[i % 2], "tf": tfs[(i // 2) % 2], "cam": cam, "fov": fov,
                           "rgb": torch.full((3, h, w), 5.0, device=dev),
                           "rgbam": torch.full((5, h, w), 9.0, device=dev)})
         c.render_batch(views, mp)
@@ -169,12 +171,12 @@ def test_shadow_batch_equals_single_views(fvn):
             assert torch.equal(v["rgbam"], rgbam) and torch.equal(v["rgb"], rgb)
         # the batch's sparse frames against the oracle
         host = [u8, f32]
-        tf_h = tf.cpu().numpy()
         for i, v in enumerate(views):
             f = v["fov"]
             w, h = v["cam"].width, v["cam"].height
             _, ids, _ = omask.make_mask(w, h, f.focal_px, f.fovea_radius, f.falloff_sigma, f.p_base, f.seed, f.frame)
-            march_parity(host[i % 2], tf_h, v["cam"], mp, v["rgbam"].cpu().numpy(), ids=ids, max_amb_frac=0.05)
+            march_parity(host[i % 2], v["tf"].cpu().numpy(), v["cam"], mp, v["rgbam"].cpu().numpy(), ids=ids,
+                         max_amb_frac=0.05)
         c.device_status()
     finally:
         c.close()
@@ -200,3 +202,18 @@ def test_shadow_argument_errors(ctx, fvn):
     a, _ = run_march(ctx, vol, tf, cam, wl.MarchParams(shading=1, light_dir=(0.0, 0.0, 0.0), shadow_rate=0))
     b, _ = run_march(ctx, vol, tf, cam, wl.MarchParams(shading=1))
     assert np.array_equal(a, b)
+
+
+def test_shadow_sample_counting_option(ctx, fvn):
+    vol, tf, cam, _ = wl.dense_small_workload(seed=1, frame=5)
+    mp = shadow_params(4)
+    _, n0 = run_march(ctx, vol, tf, cam, mp)
+    try:
+        ctx.set_option(fvn.OPT_MARCH_COUNT_SHADOW, 1)
+        _, n1 = run_march(ctx, vol, tf, cam, mp)
+        _, h1 = run_march(ctx, vol, tf, cam, wl.MarchParams(shading=1))
+    finally:
+        ctx.set_option(fvn.OPT_MARCH_COUNT_SHADOW, 0)
+    _, h0 = run_march(ctx, vol, tf, cam, wl.MarchParams(shading=1))
+    assert n1 > n0 > 0                      # shadow-ray samples added on top of the primary ones
+    assert h1 == h0                         # no shadow rays without shading 2
