@@ -175,7 +175,8 @@ const char* fvn_last_error(const fvn_ctx* ctx);
  * Paper: "Sample Maps" (M(u, v) = 1 iff N(u, v) < tau(u, v); Eq. 1-2) and
  * "Stream Compaction" (pack the valid pixels into a small buffer).
  *
- * N(u, v) is the top 24 bits of a 32-bit integer hash of (seed, frame, x, y);
+ * N(u, v) is the top 24 bits of a 32-bit integer hash of (seed, frame, x, y),
+ * or, after fvn_set_noise_tiles, the context's noise tile for the frame;
  * tau is taken from a 16384-entry table of floor(tau 2^24) indexed by the
  * squared half-pixel distance to the focal point (built on the host in
  * float64 and cached in the context).  The decision is integer-only and
@@ -190,6 +191,25 @@ const char* fvn_last_error(const fvn_ctx* ctx);
  */
 fvn_status fvn_make_mask(fvn_ctx* ctx, const fvn_foveation* fov, int w, int h, uint8_t* mask,
                          int32_t* ids, int32_t* count, void* stream);
+
+/*
+ * fvn_set_noise_tiles -- the noise of the sample maps from a looping series
+ * of tiles instead of the hash.  Paper: "Noise Patterns" (masks from a
+ * pre-computed series of 64 spatio-temporal blue-noise tiles of 16^2 to
+ * 256^2 pixels, tiled over the frame and looped over the frames).
+ *
+ * tiles : HOST uint32 [frames][tile][tile], every value below 2^24; the
+ *         context keeps its own device copy (the caller's array may be freed).
+ *         NULL reverts to the hash.
+ * tile  : side of a tile, a power of two in [16, 256].
+ * frames: number of tiles, 1..256; frame f of a foveation uses tile f mod frames.
+ * From then on every mask of the context (fvn_make_mask, fvn_render,
+ * fvn_render_batch, fvn_render_adaptive) takes
+ * N(x, y) = tiles[frame mod frames][y mod tile][x mod tile].  Synchronises the
+ * device (masks already queued may read the previous tiles); nothing changes
+ * on error.
+ */
+fvn_status fvn_set_noise_tiles(fvn_ctx* ctx, const uint32_t* tiles, int tile, int frames);
 
 /*
  * fvn_march -- emission-absorption ray march of the volume.

@@ -12,10 +12,15 @@ Follows the paper's "Sample Maps" subsection:
   diagonal R = sqrt(W^2 + H^2) / 2, P_f(d) = 1 for d <= r0 (the fovea) and
   exp(-0.5 ((d - r0) / s)^2) beyond it.
 * M(u, v) = 1 iff N(u, v) < tau(u, v) (strict), N a per-pixel noise value.
-  The paper draws N from pre-computed spatio-temporal blue-noise tiles; here
-  N is the top 24 bits of a stateless 32-bit integer hash of
-  (seed, frame, x, y): the PCG-derived hash evaluated by Jarzynski and Olano,
-  "Hash Functions for GPU Rendering" (JCGT 2020), nested over the four inputs.
+  The paper draws N from a looping series of pre-computed noise tiles
+  ("Noise Patterns": tiles of 16^2 to 256^2 pixels, 64 of them, repeated over
+  the frame and looped over time).  Two sources of N:
+  - by default the top 24 bits of a stateless 32-bit integer hash of
+    (seed, frame, x, y): the PCG-derived hash evaluated by Jarzynski and
+    Olano, "Hash Functions for GPU Rendering" (JCGT 2020), nested over the
+    four inputs;
+  - given a series of K tiles of T x T 24-bit values (an input, like the
+    paper's pre-computed tiles), N(x, y) = tile[frame mod K][y mod T][x mod T].
 * tau is quantised so that CPU and GPU take the decision in integers: the
   squared half-pixel distance q = (2x + 1 - F_x)^2 + (2y + 1 - F_y)^2 (F the
   focal point in half pixels, rounded) selects bin q >> shift of a 16384-entry
@@ -110,16 +115,22 @@ def focal_half_pixels(fx: float, fy: float, width: int, height: int):
 
 
 def make_mask(width: int, height: int, focal_px, fovea_radius=0.10, falloff_sigma=0.10,
-              p_base=0.05, seed=0, frame=0):
-    """Return (mask uint8 [H, W], ids int32 row-major, c_max float)."""
+              p_base=0.05, seed=0, frame=0, noise=None):
+    """Return (mask uint8 [H, W], ids int32 row-major, c_max float).
+    noise: optional uint32 [K, T, T] tile series (values < 2^24) replacing the hash."""
     taus, thr, shift = tau_table(width, height, fovea_radius, falloff_sigma, p_base)
     f2x, f2y = focal_half_pixels(focal_px[0], focal_px[1], width, height)
     ys, xs = np.meshgrid(np.arange(height, dtype=np.int64), np.arange(width, dtype=np.int64),
                          indexing="ij")
     q = (2 * xs + 1 - f2x) ** 2 + (2 * ys + 1 - f2y) ** 2
     b = (q >> shift).astype(np.int64)
-    h = pixel_hash(seed, frame, xs.astype(np.uint32), ys.astype(np.uint32))
-    n24 = (h >> _U32(8)).astype(np.int64)
+    if noise is None:
+        h = pixel_hash(seed, frame, xs.astype(np.uint32), ys.astype(np.uint32))
+        n24 = (h >> _U32(8)).astype(np.int64)
+    else:
+        noise = np.asarray(noise, dtype=np.uint32)
+        k, t = noise.shape[0], noise.shape[1]
+        n24 = noise[int(frame) % k][ys % t, xs % t].astype(np.int64)
     m = (n24 < thr[b].astype(np.int64)).astype(np.uint8)
     ids = np.flatnonzero(m.reshape(-1)).astype(np.int32)
     c_max = float(taus[b].mean())

@@ -134,6 +134,8 @@ struct fvn_ctx {
     int march_coop_dense = 0;
     int march_grad4 = 1;              // shaded marches read a gradient volume when it fits
     int march_count_shadow = 0;       // shadowed marches also count the shadow rays' samples
+    uint32_t* d_noise = nullptr;      // sample-map noise tiles (NULL: the hash), [frames][T][T]
+    int noise_log2 = 0, noise_frames = 0;
     void* pad_buf = nullptr;          // padded copy of the volume read by the march
     size_t pad_bytes = 0;
     float* d_act_scale = nullptr;     // FP8 per-layer activation scales

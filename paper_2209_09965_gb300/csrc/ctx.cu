@@ -121,6 +121,7 @@ extern "C" fvn_status fvn_destroy(fvn_ctx* ctx) {
     cudaFree(ctx->d_amax);
     cudaFree(ctx->d_ticket);
     cudaFree(ctx->pad_buf);
+    cudaFree(ctx->d_noise);
     cudaFree(ctx->recon_ws.base);
     cudaFree(ctx->render_ws.mask);
     cudaFree(ctx->render_ws.ids);

@@ -3,7 +3,10 @@
 //
 // M(x, y) = 1 iff N(x, y) < tau(x, y).  N is the top 24 bits of a nested
 // 32-bit PCG-style integer hash of (seed, frame, y, x) (the "pcg" hash of
-// Jarzynski and Olano, "Hash Functions for GPU Rendering", JCGT 2020).  tau
+// Jarzynski and Olano, "Hash Functions for GPU Rendering", JCGT 2020), or,
+// once the caller has installed a looping series of noise tiles
+// (fvn_set_noise_tiles; the paper's "Noise Patterns" use 64 pre-computed
+// spatio-temporal blue-noise tiles), tile[frame mod K][y mod T][x mod T].  tau
 // comes from a 16384-entry table of floor(tau 2^24) indexed by the squared
 // half-pixel distance to the focal point shifted right so the largest
 // distance of the frame fits; the table is built on the host in float64 from
@@ -48,8 +51,9 @@ __device__ __forceinline__ void morton_decode(uint32_t m, int& tx, int& ty) {
 // 8 x 4 sub-tile: the id list comes out in compact screen regions, which keeps
 // the 32 rays of a march packet close together.
 __device__ __forceinline__ void mask_tile(uint32_t block, int W, int H, uint32_t key, int f2x, int f2y, int shift,
-                                          const uint32_t* __restrict__ lut, uint8_t* __restrict__ mask,
-                                          int32_t* __restrict__ ids, int32_t* __restrict__ count) {
+                                          const uint32_t* __restrict__ lut, const uint32_t* __restrict__ noise,
+                                          int nlog2, uint8_t* __restrict__ mask, int32_t* __restrict__ ids,
+                                          int32_t* __restrict__ count) {
     __shared__ int warp_off[8];
     __shared__ int block_base;
     int tx, ty;
@@ -60,10 +64,12 @@ __device__ __forceinline__ void mask_tile(uint32_t block, int W, int H, uint32_t
     const bool valid = x < W && y < H;
     bool m = false;
     if (valid) {
-        const uint32_t h = pcg_hash((uint32_t)x + pcg_hash((uint32_t)y + key));
+        const int tmask = (1 << nlog2) - 1;
+        const uint32_t n24 = noise ? __ldg(noise + ((y & tmask) << nlog2) + (x & tmask))
+                                   : pcg_hash((uint32_t)x + pcg_hash((uint32_t)y + key)) >> 8;
         const int dx = 2 * x + 1 - f2x, dy = 2 * y + 1 - f2y;
         const uint32_t q = (uint32_t)(dx * dx) + (uint32_t)(dy * dy);
-        m = (h >> 8) < __ldg(lut + (q >> shift));
+        m = n24 < __ldg(lut + (q >> shift));
         mask[(size_t)y * W + x] = (uint8_t)m;
     }
     const unsigned bal = __ballot_sync(0xffffffffu, m);
@@ -84,9 +90,10 @@ __device__ __forceinline__ void mask_tile(uint32_t block, int W, int H, uint32_t
 
 __global__ void __launch_bounds__(256) mask_compact_kernel(int W, int H, uint32_t key, int f2x, int f2y,
                                                            int shift, const uint32_t* __restrict__ lut,
+                                                           const uint32_t* __restrict__ noise, int nlog2,
                                                            uint8_t* __restrict__ mask, int32_t* __restrict__ ids,
                                                            int32_t* __restrict__ count) {
-    mask_tile(blockIdx.x, W, H, key, f2x, f2y, shift, lut, mask, ids, count);
+    mask_tile(blockIdx.x, W, H, key, f2x, f2y, shift, lut, noise, nlog2, mask, ids, count);
 }
 
 // Several views in one launch: view i owns blocks [block0, next view's block0).
@@ -95,6 +102,8 @@ struct MaskView {
     uint32_t key;
     int f2x, f2y, shift;
     const uint32_t* lut;
+    const uint32_t* noise;   // this frame's noise tile, or NULL for the hash
+    int nlog2;               // log2 of the tile side
     uint8_t* mask;
     int32_t* ids;
     int32_t* count;
@@ -110,7 +119,8 @@ __global__ void __launch_bounds__(256) mask_compact_batch_kernel(const __grid_co
     int i = 0;
     while (i + 1 < b.n && blockIdx.x >= b.v[i + 1].block0) ++i;
     const MaskView& m = b.v[i];
-    mask_tile(blockIdx.x - m.block0, m.W, m.H, m.key, m.f2x, m.f2y, m.shift, m.lut, m.mask, m.ids, m.count);
+    mask_tile(blockIdx.x - m.block0, m.W, m.H, m.key, m.f2x, m.f2y, m.shift, m.lut, m.noise, m.nlog2, m.mask, m.ids,
+              m.count);
 }
 
 static int lut_shift(int W, int H) {
@@ -201,6 +211,12 @@ static fvn_status mask_view(fvn_ctx* ctx, const fvn_foveation* fov, int w, int h
     mv->H = h;
     mv->shift = lut->shift;
     mv->lut = lut->d_lut;
+    mv->noise = nullptr;
+    mv->nlog2 = 0;
+    if (ctx->d_noise) {
+        mv->nlog2 = ctx->noise_log2;
+        mv->noise = ctx->d_noise + ((size_t)(fov->frame % (uint32_t)ctx->noise_frames) << (2 * ctx->noise_log2));
+    }
     const int tiles = std::max((w + 15) / 16, (h + 15) / 16);
     int side = 1;
     while (side < tiles) side <<= 1;
@@ -216,8 +232,8 @@ fvn_status make_mask_impl(fvn_ctx* ctx, const fvn_foveation* fov, int w, int h, 
     if (s != FVN_OK) return s;
     FVN_CUDA(ctx, cudaMemsetAsync(count, 0, sizeof(int32_t), st));
     // Z-order over a power-of-two square of 16 x 16 tiles covering the frame
-    mask_compact_kernel<<<side * side, 256, 0, st>>>(w, h, mv.key, mv.f2x, mv.f2y, mv.shift, mv.lut, mask, ids,
-                                                     count);
+    mask_compact_kernel<<<side * side, 256, 0, st>>>(w, h, mv.key, mv.f2x, mv.f2y, mv.shift, mv.lut, mv.noise,
+                                                     mv.nlog2, mask, ids, count);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
@@ -262,6 +278,40 @@ extern "C" fvn_status fvn_make_mask(fvn_ctx* ctx, const fvn_foveation* fov, int 
                            fov->p_base <= 1.f && isfinite(fov->fovea_radius) && isfinite(fov->falloff_sigma),
                   "foveation radius / falloff must be >= 0 and p_base in [0, 1]");
     return make_mask_impl(ctx, fov, w, h, mask, ids, count, as_stream(stream));
+}
+
+extern "C" fvn_status fvn_set_noise_tiles(fvn_ctx* ctx, const uint32_t* tiles, int tile, int frames) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    if (!tiles) {
+        FVN_CUDA(ctx, cudaDeviceSynchronize());   // masks already queued may still read the tiles
+        cudaFree(ctx->d_noise);
+        ctx->d_noise = nullptr;
+        ctx->noise_log2 = ctx->noise_frames = 0;
+        return FVN_OK;
+    }
+    int lg = 0;
+    while ((1 << lg) < tile && lg < 30) ++lg;
+    FVN_CHECK_ARG(ctx, tile >= 16 && tile <= 256 && (1 << lg) == tile, "tile side %d: a power of two in [16, 256]",
+                  tile);
+    FVN_CHECK_ARG(ctx, frames >= 1 && frames <= 256, "%d tiles (1..256)", frames);
+    const size_t n = (size_t)frames * tile * tile;
+    for (size_t i = 0; i < n; ++i)
+        FVN_CHECK_ARG(ctx, tiles[i] < (1u << 24), "noise value %u at %zu is not below 2^24", tiles[i], i);
+    FVN_CUDA(ctx, cudaDeviceSynchronize());
+    cudaFree(ctx->d_noise);
+    ctx->d_noise = nullptr;
+    ctx->noise_log2 = ctx->noise_frames = 0;
+    uint32_t* d = nullptr;
+    FVN_CUDA(ctx, cudaMalloc(&d, n * sizeof(uint32_t)));
+    const cudaError_t e = cudaMemcpy(d, tiles, n * sizeof(uint32_t), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+        cudaFree(d);
+        return set_error(ctx, FVN_ERR_CUDA, "copying the noise tiles: %s", cudaGetErrorString(e));
+    }
+    ctx->d_noise = d;
+    ctx->noise_log2 = lg;
+    ctx->noise_frames = frames;
+    return FVN_OK;
 }
 
 // ---------------------------------------------------------------------------

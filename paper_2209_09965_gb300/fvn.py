@@ -30,7 +30,7 @@ EXPORTS = (
     "fvn_weight_count", "fvn_reconstruct", "fvn_render", "fvn_conv_fwd", "fvn_conv_bwd", "fvn_avgpool2_fwd",
     "fvn_avgpool2_bwd", "fvn_upsample2_fwd", "fvn_upsample2_bwd", "fvn_kp_blend_fwd", "fvn_kp_blend_bwd",
     "fvn_loss_l1grad", "fvn_adam_step", "fvn_reconstruct_noalloc", "fvn_set_option", "fvn_device_status",
-    "fvn_calibrate_fp8", "fvn_render_adaptive", "fvn_march_masked", "fvn_render_batch",
+    "fvn_calibrate_fp8", "fvn_render_adaptive", "fvn_march_masked", "fvn_render_batch", "fvn_set_noise_tiles",
 )
 MAX_VIEWS = 16
 OPT_CONV_KERNEL, OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 1, 2, 3
@@ -97,6 +97,7 @@ def _load():
         "fvn_device_status": [P],
         "fvn_render": [P, P, P, P, P, P, I, P, P, P],
         "fvn_render_batch": [P, P, I, P, I, P, P],
+        "fvn_set_noise_tiles": [P, P, I, I],
         "fvn_conv_fwd": [P, I, P, I, I, I, I, P, P, I, I, I, P, P],
         "fvn_conv_bwd": [P, I, P, I, I, I, I, P, I, I, P, P, P, P, P, P, P],
         "fvn_avgpool2_fwd": [P, I, I, I, P, P],
@@ -231,6 +232,18 @@ class Context:
         _check(st, self.h)
 
     # --- hot path -----------------------------------------------------------
+    def set_noise_tiles(self, tiles):
+        """Install a looping series of sample-map noise tiles (numpy uint32
+        [frames, tile, tile], values < 2^24), or None to go back to the hash."""
+        if tiles is None:
+            self._chk(lib.fvn_set_noise_tiles(self.h, None, 0, 0))
+            return
+        import numpy as np
+        t = np.ascontiguousarray(tiles, dtype=np.uint32)
+        if t.ndim != 3 or t.shape[1] != t.shape[2]:
+            raise ValueError("noise tiles must be [frames, tile, tile]")
+        self._chk(lib.fvn_set_noise_tiles(self.h, t.ctypes.data_as(ctypes.c_void_p), t.shape[1], t.shape[0]))
+
     def make_mask(self, fov, w, h, mask, ids, count, stream=None):
         self._chk(lib.fvn_make_mask(self.h, ctypes.byref(foveation(fov)), int(w), int(h), _ptr(mask, torch.uint8),
                                     _ptr(ids, torch.int32), _ptr(count, torch.int32), _stream(stream)))

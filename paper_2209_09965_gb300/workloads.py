@@ -206,6 +206,82 @@ class Foveation:
     frame: int = 0
 
 
+# ---------------------------------------------------------------------------
+# blue-noise sample-map tiles
+# ---------------------------------------------------------------------------
+
+def blue_noise_ranks(tile: int = 64, seed: int = 0, sigma: float = 1.5, initial: float = 0.1) -> np.ndarray:
+    """Void-and-cluster ranking of a tile x tile torus (Ulichney, "The
+    void-and-cluster method for dither array generation", 1993): a seeded
+    initial pattern of ones relaxed by moving the tightest cluster into the
+    largest void until stable, then ranked by removing tightest clusters
+    (ranks below the initial count) and filling largest voids (ranks above).
+    Cluster / void energies are a toroidal Gaussian filter of the pattern.
+    Returns int64 [tile, tile], a permutation of 0 .. tile^2 - 1."""
+    n = tile * tile
+    d = np.minimum(np.arange(tile), tile - np.arange(tile)).astype(np.float64)
+    kern = np.exp(-(d[:, None] ** 2 + d[None, :] ** 2) / (2.0 * sigma * sigma))   # centred at (0, 0)
+
+    def splat(energy, p, sign):
+        y, x = divmod(int(p), tile)
+        energy += sign * np.roll(np.roll(kern, y, axis=0), x, axis=1)
+
+    rng = np.random.default_rng(seed)
+    ones = np.zeros(n, bool)
+    ones[rng.choice(n, max(1, int(initial * n)), replace=False)] = True
+    energy = np.zeros((tile, tile))
+    for p in np.flatnonzero(ones):
+        splat(energy, p, 1.0)
+    flat = energy.reshape(-1)
+    for _ in range(4 * n):                       # relax: tightest cluster -> largest void
+        c = int(np.argmax(np.where(ones, flat, -np.inf)))
+        ones[c] = False
+        splat(energy, c, -1.0)
+        v = int(np.argmin(np.where(ones, np.inf, flat)))
+        ones[v] = True
+        splat(energy, v, 1.0)
+        if v == c:
+            break
+    ranks = np.full(n, -1, np.int64)
+    n1 = int(ones.sum())
+    pat, e = ones.copy(), energy.copy()
+    ef = e.reshape(-1)
+    for r in range(n1 - 1, -1, -1):              # ranks below n1: remove tightest clusters
+        c = int(np.argmax(np.where(pat, ef, -np.inf)))
+        pat[c] = False
+        splat(e, c, -1.0)
+        ranks[c] = r
+    pat, e = ones.copy(), energy.copy()
+    ef = e.reshape(-1)
+    for r in range(n1, n):                       # ranks from n1: fill largest voids
+        v = int(np.argmin(np.where(pat, np.inf, ef)))
+        pat[v] = True
+        splat(e, v, 1.0)
+        ranks[v] = r
+    return ranks.reshape(tile, tile)
+
+
+GOLDEN = (math.sqrt(5.0) - 1.0) / 2.0
+
+
+def blue_noise_tiles(tile: int = 64, frames: int = 64, seed: int = 0) -> np.ndarray:
+    """A looping series of sample-map noise tiles (the paper draws its masks
+    from a pre-computed series of 64 spatio-temporal blue-noise tiles, which
+    are not available here): frame 0 is the void-and-cluster ranking scaled
+    to 24 bits, frame k adds k times the golden-ratio conjugate modulo 1, so
+    every frame is a rank shift of a blue-noise tile and every pixel's values
+    over the frames form an additive low-discrepancy sequence.  uint32
+    [frames, tile, tile], values < 2^24."""
+    ranks = blue_noise_ranks(tile, seed)
+    n = tile * tile
+    base = ((2 * ranks + 1) << 23) // n                        # (rank + 1/2) / n in 24-bit fixed point
+    out = np.empty((frames, tile, tile), np.uint32)
+    for k in range(frames):
+        off = int(math.floor(math.fmod(k * GOLDEN, 1.0) * (1 << 24)))
+        out[k] = ((base + off) & ((1 << 24) - 1)).astype(np.uint32)
+    return out
+
+
 # Default light of the shadowed shading mode: from above (+y is the orbit's up), off to one side.
 LIGHT_DIR = (0.35, 0.85, 0.40)
 

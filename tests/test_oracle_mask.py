@@ -98,3 +98,48 @@ def test_mask_changes_with_frame():
     a, _, _ = om.make_mask(256, 256, (128.0, 128.0), seed=1, frame=0)
     b, _, _ = om.make_mask(256, 256, (128.0, 128.0), seed=1, frame=1)
     assert (a != b).mean() > 0.05
+
+
+# ---- the tiled noise source (a looping series of pre-computed tiles) -------
+
+def _flat_profile(p):
+    """Profile with tau = p everywhere: no fovea, no falloff (table bins are
+    evaluated at their centres, so even the bin of distance 0 has d > r0 = 0)."""
+    return dict(fovea_radius=0.0, falloff_sigma=0.0, p_base=p)
+
+
+def test_constant_tiles_reduce_to_threshold_only():
+    w, h, fp = 96, 64, (40.3, 27.8)
+    zero = np.zeros((1, 16, 16), np.uint32)
+    m, ids, _ = om.make_mask(w, h, fp, noise=zero)
+    assert m.all() and ids.size == w * h                        # 0 < T everywhere (P_b > 0)
+    top = np.full((1, 16, 16), (1 << 24) - 1, np.uint32)
+    m_top, _, _ = om.make_mask(w, h, fp, noise=top)
+    fovea, _, _ = om.make_mask(w, h, fp, p_base=0.0, falloff_sigma=0.0, seed=5)   # hash, fovea only
+    assert np.array_equal(m_top, fovea) and 0 < m_top.sum() < w * h
+
+
+def test_tiles_repeat_over_the_frame_and_loop_over_frames():
+    rng = np.random.default_rng(3)
+    tiles = rng.integers(0, 1 << 24, (5, 32, 32), dtype=np.uint32)
+    w, h, p = 100, 70, 0.3
+    thr = int(np.floor(float(np.float32(p)) * (1 << 24)))
+    for frame in (0, 3, 7):
+        m, _, _ = om.make_mask(w, h, (10.25, 60.75), frame=frame, noise=tiles, **_flat_profile(p))
+        ys, xs = np.mgrid[0:h, 0:w]
+        expect = tiles[frame % 5][ys % 32, xs % 32] < thr
+        assert np.array_equal(m.astype(bool), expect)
+    a, _, _ = om.make_mask(w, h, (50.0, 35.0), frame=2, noise=tiles)
+    b, _, _ = om.make_mask(w, h, (50.0, 35.0), frame=12, noise=tiles)
+    assert np.array_equal(a, b)                                  # frame mod K
+
+
+def test_blue_noise_tiles_give_the_expected_density():
+    from paper_2209_09965_gb300 import workloads as wl
+    tiles = wl.blue_noise_tiles(32, 6, seed=1)
+    for p in (0.05, 0.1, 0.37):
+        for frame in range(6):
+            m, _, _ = om.make_mask(256, 128, (100.0, 60.0), frame=frame, noise=tiles, **_flat_profile(p))
+            # a rank shift of a permutation: the count of values below the
+            # threshold in each tile is p n to within one
+            assert abs(m.mean() - p) <= 2.0 / (32 * 32)

@@ -69,3 +69,32 @@ def test_multiview_volumes_small():
     noise, blobs = wl.multiview_volumes(n_noise=16, n_blobs=32, seed=50)
     assert noise.dtype == torch.float16 and noise.shape == (16, 16, 16)
     assert blobs.dtype == torch.uint8 and blobs.shape == (32, 32, 32) and int(blobs.max()) > 30
+
+
+def test_blue_noise_tiles_are_blue_permutations():
+    t = 32
+    ranks = wl.blue_noise_ranks(t, seed=4)
+    assert np.array_equal(np.sort(ranks.reshape(-1)), np.arange(t * t))
+    tiles = wl.blue_noise_tiles(t, 8, seed=4)
+    assert tiles.dtype == np.uint32 and tiles.shape == (8, t, t) and int(tiles.max()) < (1 << 24)
+    # frame k is frame 0 shifted by k times the golden-ratio conjugate (mod 2^24)
+    off = (tiles[3].astype(np.int64) - tiles[0].astype(np.int64)) % (1 << 24)
+    assert np.all(off == off.flat[0])
+    assert abs(off.flat[0] / (1 << 24) - (3 * wl.GOLDEN) % 1.0) < 1e-6
+
+    def mean_nn(mask):
+        ys, xs = np.nonzero(mask)
+        p = np.stack([xs, ys], 1).astype(float)
+        d = np.abs(p[:, None] - p[None])
+        d = np.minimum(d, t - d)
+        dd = np.sqrt((d ** 2).sum(-1))
+        np.fill_diagonal(dd, np.inf)
+        return dd.min(1).mean()
+
+    # blue: at 10 % density the sampled pixels keep ~1.5x the nearest-neighbour
+    # distance of white noise, whose expectation is 0.5 / sqrt(0.1) = 1.58 px
+    for k in (0, 3, 7):
+        m = tiles[k] < int(0.1 * (1 << 24))
+        assert mean_nn(m) > 2.1
+    white = np.random.default_rng(0).random((t, t)) < 0.1
+    assert mean_nn(white) < 1.9
