@@ -13,7 +13,6 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import subprocess
 import sys
@@ -129,9 +128,13 @@ def load_weights():
 
 
 def psnr_t(a, b):
-    import torch
-    mse = torch.mean((a.clamp(0, 1) - b.clamp(0, 1)) ** 2).item()
-    return float("inf") if mse == 0 else -10.0 * math.log10(mse)
+    from paper_2209_09965_gb300 import quality
+    return quality.psnr(a, b)
+
+
+def ssim_t(a, b):
+    from paper_2209_09965_gb300 import quality
+    return quality.ssim(a, b)
 
 
 def cpu_oracle_frame_rate(frame_seed=2, budget_s=12.0):
@@ -352,7 +355,7 @@ def run_shadows(fvn, wl, weights, conv, vol, tf, frames, dev, nframes, flush):
             c.render(vol, tf, frames[i][0], frames[i][1], mp, rgb)
         torch.cuda.synchronize()
         stream = torch.cuda.current_stream()
-        fov_ms, dense_ms, march_ms, psnrs = [], [], [], []
+        fov_ms, dense_ms, march_ms, psnrs, ssims = [], [], [], [], []
         nsamp = torch.zeros(1, dtype=torch.int64, device=dev)
         sparse_samples = dense_samples = 0
         for i in range(nframes):
@@ -381,6 +384,7 @@ def run_shadows(fvn, wl, weights, conv, vol, tf, frames, dev, nframes, flush):
             dense_ms.append(e[2].elapsed_time(e[3]))
             march_ms.append(e[4].elapsed_time(e[5]))
             psnrs.append(psnr_t(rgb, dense[:3]))
+            ssims.append(ssim_t(rgb, dense[:3]))
         # the same marches again with the shadow rays' samples counted too
         c.set_option(fvn.OPT_MARCH_COUNT_SHADOW, 1)
         all_sparse = all_dense = 0
@@ -405,6 +409,7 @@ def run_shadows(fvn, wl, weights, conv, vol, tf, frames, dev, nframes, flush):
                 "frames": nframes, "frames_per_s": fps, "ms_per_frame": float(np.mean(fov_ms)),
                 "dense_march_frames_per_s": dfps, "speedup_vs_dense": fps / dfps,
                 "psnr_vs_dense_db": {"mean": float(np.mean(psnrs)), "min": float(np.min(psnrs))},
+                "ssim_vs_dense": {"mean": float(np.mean(ssims)), "min": float(np.min(ssims))},
                 "stage_ms": {"sparse_march": float(np.mean(march_ms)), "dense_march": float(np.mean(dense_ms))},
                 "gsamples_per_s": {"sparse_march": sparse_samples / (sum(march_ms) / 1000.0) / 1e9,
                                    "dense_march": dense_samples / (sum(dense_ms) / 1000.0) / 1e9,
@@ -435,7 +440,7 @@ def run_blue_noise(ctx, wl, vol, tf, mp, frames, dev, nframes, flush):
         for i in range(3):
             ctx.render(vol, tf, frames[i][0], frames[i][1], mp, rgb)
         torch.cuda.synchronize()
-        ms, psnrs = [], []
+        ms, psnrs, ssims = [], [], []
         for i in range(nframes):
             cam, fov = frames[i % len(frames)]
             flush.fill_(float(i))
@@ -447,10 +452,12 @@ def run_blue_noise(ctx, wl, vol, tf, mp, frames, dev, nframes, flush):
             torch.cuda.synchronize()
             ms.append(e0.elapsed_time(e1))
             psnrs.append(psnr_t(rgb, dense[:3]))
+            ssims.append(ssim_t(rgb, dense[:3]))
         return {"workload": "the headline frames, sample maps from 64 blue-noise tiles of 64 x 64 pixels "
                             "(void-and-cluster, golden-ratio animation over the frames)",
                 "frames": nframes, "frames_per_s": nframes / (sum(ms) / 1000.0),
                 "psnr_vs_dense_db": {"mean": float(np.mean(psnrs)), "min": float(np.min(psnrs))},
+                "ssim_vs_dense": {"mean": float(np.mean(ssims)), "min": float(np.min(ssims))},
                 "note": "same network as the headline (trained on hash masks)"}
     except Exception as exc:   # reported, not part of the metric
         return {"error": str(exc)[:200]}
@@ -641,7 +648,7 @@ def main():
 
     # ---- per-stage times, samples and quality on the same frames (untimed for value)
     fov_ms, dense_ms, mask_ms, march_ms, recon_ms = [], [], [], [], []
-    sparse_samples, dense_samples, psnrs = 0, 0, []
+    sparse_samples, dense_samples, psnrs, ssims = 0, 0, [], []
     mask = torch.empty(H, W, dtype=torch.uint8, device=dev)
     ids = torch.empty(W * H, dtype=torch.int32, device=dev)
     count = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -674,6 +681,7 @@ def main():
         dense_ms.append(d0.elapsed_time(d1))
         dense_samples += int(nsamp.item())
         psnrs.append(psnr_t(rgb, dense[:3]))
+        ssims.append(ssim_t(rgb, dense[:3]))
     nq = len(dense_ms)
     dense_fps = nq / (sum(dense_ms) / 1000.0)
     march_s = sum(march_ms) / 1000.0
@@ -797,6 +805,7 @@ def main():
             "dense_march_frames_per_s": dense_fps,
             "speedup_vs_dense": value / world / dense_fps,
             "psnr_vs_dense_db": {"mean": float(np.mean(psnrs)), "min": float(np.min(psnrs))},
+            "ssim_vs_dense": {"mean": float(np.mean(ssims)), "min": float(np.min(ssims))},
             "stage_ms": {"mask": float(np.mean(mask_ms)), "sparse_march": float(np.mean(march_ms)),
                          "reconstruct": float(np.mean(recon_ms)), "dense_march": float(np.mean(dense_ms))},
             "gsamples_per_s": {"sparse_march": sparse_samples / march_s / 1e9,

@@ -283,3 +283,15 @@ def test_psnr_ssim_closed_forms():
     y = np.full((3, 20, 20), 0.6)
     c1 = 0.01 ** 2
     assert abs(metrics.ssim(x, y) - (2 * 0.18 + c1) / (0.09 + 0.36 + c1)) < 1e-12
+
+
+def test_device_quality_metrics_match_the_oracle():
+    """The benchmark's torch PSNR / SSIM equal the oracle's float64 ones."""
+    import torch
+    from paper_2209_09965_gb300 import quality
+    rng = np.random.default_rng(12)
+    a = rng.uniform(-0.1, 1.1, (3, 40, 57))
+    b = np.clip(a + rng.normal(0, 0.05, a.shape), -0.2, 1.2)
+    assert abs(quality.psnr(torch.from_numpy(a), torch.from_numpy(b)) - metrics.psnr(a, b)) < 1e-9
+    assert abs(quality.ssim(torch.from_numpy(a), torch.from_numpy(b)) - metrics.ssim(a, b)) < 1e-12
+    assert abs(quality.ssim(torch.from_numpy(a[0]), torch.from_numpy(b[0])) - metrics.ssim(a[0], b[0])) < 1e-12
