@@ -137,6 +137,25 @@ def ssim_t(a, b):
     return quality.ssim(a, b)
 
 
+class TemporalPsnr:
+    """tPSNR over a sequence of consecutive frames (reconstruction, reference)."""
+
+    def __init__(self):
+        self.prev = None
+        self.values = []
+
+    def add(self, o, y):
+        from paper_2209_09965_gb300 import quality
+        if self.prev is not None:
+            self.values.append(quality.tpsnr(self.prev[0], o, self.prev[1], y))
+        self.prev = (o.clone(), y.clone())
+
+    def summary(self):
+        import numpy as np
+        v = self.values
+        return {"mean": float(np.mean(v)), "min": float(np.min(v)), "pairs": len(v)} if v else None
+
+
 def cpu_oracle_frame_rate(frame_seed=2, budget_s=12.0):
     """Time the CPU oracle on a bounded sample of one frame of the workload and
     extrapolate to frames/s (march of a random subset of the frame's sampled
@@ -356,6 +375,7 @@ def run_shadows(fvn, wl, weights, conv, vol, tf, frames, dev, nframes, flush):
         torch.cuda.synchronize()
         stream = torch.cuda.current_stream()
         fov_ms, dense_ms, march_ms, psnrs, ssims = [], [], [], [], []
+        tps = TemporalPsnr()
         nsamp = torch.zeros(1, dtype=torch.int64, device=dev)
         sparse_samples = dense_samples = 0
         for i in range(nframes):
@@ -385,6 +405,7 @@ def run_shadows(fvn, wl, weights, conv, vol, tf, frames, dev, nframes, flush):
             march_ms.append(e[4].elapsed_time(e[5]))
             psnrs.append(psnr_t(rgb, dense[:3]))
             ssims.append(ssim_t(rgb, dense[:3]))
+            tps.add(rgb, dense[:3])
         # the same marches again with the shadow rays' samples counted too
         c.set_option(fvn.OPT_MARCH_COUNT_SHADOW, 1)
         all_sparse = all_dense = 0
@@ -410,6 +431,7 @@ def run_shadows(fvn, wl, weights, conv, vol, tf, frames, dev, nframes, flush):
                 "dense_march_frames_per_s": dfps, "speedup_vs_dense": fps / dfps,
                 "psnr_vs_dense_db": {"mean": float(np.mean(psnrs)), "min": float(np.min(psnrs))},
                 "ssim_vs_dense": {"mean": float(np.mean(ssims)), "min": float(np.min(ssims))},
+                "tpsnr_vs_dense_db": tps.summary(),
                 "stage_ms": {"sparse_march": float(np.mean(march_ms)), "dense_march": float(np.mean(dense_ms))},
                 "gsamples_per_s": {"sparse_march": sparse_samples / (sum(march_ms) / 1000.0) / 1e9,
                                    "dense_march": dense_samples / (sum(dense_ms) / 1000.0) / 1e9,
@@ -441,6 +463,7 @@ def run_blue_noise(ctx, wl, vol, tf, mp, frames, dev, nframes, flush):
             ctx.render(vol, tf, frames[i][0], frames[i][1], mp, rgb)
         torch.cuda.synchronize()
         ms, psnrs, ssims = [], [], []
+        tps = TemporalPsnr()
         for i in range(nframes):
             cam, fov = frames[i % len(frames)]
             flush.fill_(float(i))
@@ -453,11 +476,13 @@ def run_blue_noise(ctx, wl, vol, tf, mp, frames, dev, nframes, flush):
             ms.append(e0.elapsed_time(e1))
             psnrs.append(psnr_t(rgb, dense[:3]))
             ssims.append(ssim_t(rgb, dense[:3]))
+            tps.add(rgb, dense[:3])
         return {"workload": "the headline frames, sample maps from 64 blue-noise tiles of 64 x 64 pixels "
                             "(void-and-cluster, golden-ratio animation over the frames)",
                 "frames": nframes, "frames_per_s": nframes / (sum(ms) / 1000.0),
                 "psnr_vs_dense_db": {"mean": float(np.mean(psnrs)), "min": float(np.min(psnrs))},
                 "ssim_vs_dense": {"mean": float(np.mean(ssims)), "min": float(np.min(ssims))},
+                "tpsnr_vs_dense_db": tps.summary(),
                 "note": "same network as the headline (trained on hash masks)"}
     except Exception as exc:   # reported, not part of the metric
         return {"error": str(exc)[:200]}
@@ -649,6 +674,7 @@ def main():
     # ---- per-stage times, samples and quality on the same frames (untimed for value)
     fov_ms, dense_ms, mask_ms, march_ms, recon_ms = [], [], [], [], []
     sparse_samples, dense_samples, psnrs, ssims = 0, 0, [], []
+    tps = TemporalPsnr()          # consecutive orbit frames
     mask = torch.empty(H, W, dtype=torch.uint8, device=dev)
     ids = torch.empty(W * H, dtype=torch.int32, device=dev)
     count = torch.zeros(1, dtype=torch.int32, device=dev)
@@ -682,6 +708,7 @@ def main():
         dense_samples += int(nsamp.item())
         psnrs.append(psnr_t(rgb, dense[:3]))
         ssims.append(ssim_t(rgb, dense[:3]))
+        tps.add(rgb, dense[:3])
     nq = len(dense_ms)
     dense_fps = nq / (sum(dense_ms) / 1000.0)
     march_s = sum(march_ms) / 1000.0
@@ -806,6 +833,7 @@ def main():
             "speedup_vs_dense": value / world / dense_fps,
             "psnr_vs_dense_db": {"mean": float(np.mean(psnrs)), "min": float(np.min(psnrs))},
             "ssim_vs_dense": {"mean": float(np.mean(ssims)), "min": float(np.min(ssims))},
+            "tpsnr_vs_dense_db": tps.summary(),
             "stage_ms": {"mask": float(np.mean(mask_ms)), "sparse_march": float(np.mean(march_ms)),
                          "reconstruct": float(np.mean(recon_ms)), "dense_march": float(np.mean(dense_ms))},
             "gsamples_per_s": {"sparse_march": sparse_samples / march_s / 1e9,

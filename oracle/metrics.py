@@ -8,7 +8,8 @@ fixing their conventions.  Readings used here: images are RGB clamped to
 [0, 1]; PSNR with MAX = 1 over all pixels and channels; SSIM after Wang et
 al. 2004 with an 11x11 Gaussian window (sigma 1.5, truncated at radius 5),
 K1 = 0.01, K2 = 0.03, computed per channel over the valid (unpadded) window
-positions and averaged.
+positions and averaged; tPSNR the PSNR (MAX = 1) of the frame-to-frame change
+of the reconstruction against that of the reference, frames clamped first.
 """
 from __future__ import annotations
 
@@ -56,3 +57,12 @@ def ssim(a, b, k1=0.01, k2=0.03):
         s = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
         vals.append(s.mean())
     return float(np.mean(vals))
+
+
+def tpsnr(o_prev, o, y_prev, y):
+    c = lambda t: np.clip(np.asarray(t, np.float64), 0.0, 1.0)   # noqa: E731
+    d = (c(o) - c(o_prev)) - (c(y) - c(y_prev))
+    mse = np.mean(d ** 2)
+    if mse == 0.0:
+        return float("inf")
+    return float(-10.0 * np.log10(mse))

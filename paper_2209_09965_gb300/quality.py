@@ -1,10 +1,12 @@
-"""Image-quality measurements of rendered frames (PSNR, SSIM) on the device,
-for the benchmark's quality figures -- measurement, not part of the render
-path.  Conventions (the paper reports PSNR and SSIM without fixing them):
-RGB clamped to [0, 1]; PSNR with MAX = 1 over all pixels and channels; SSIM
-after Wang et al. 2004, 11 x 11 Gaussian window (sigma 1.5, radius 5),
-K1 = 0.01, K2 = 0.03, over the window positions inside the image, averaged
-over the channels."""
+"""Image-quality measurements of rendered frames (PSNR, SSIM, temporal PSNR)
+on the device, for the benchmark's quality figures -- measurement, not part
+of the render path.  Conventions (the paper reports PSNR, SSIM and tPSNR
+without fixing them): RGB clamped to [0, 1]; PSNR with MAX = 1 over all
+pixels and channels; SSIM after Wang et al. 2004, 11 x 11 Gaussian window
+(sigma 1.5, radius 5), K1 = 0.01, K2 = 0.03, over the window positions
+inside the image, averaged over the channels; tPSNR the PSNR (MAX = 1) of
+the frame-to-frame change of the reconstruction against that of the
+reference, (O_t - O_t-1) vs (Y_t - Y_t-1), the clamped frames differenced."""
 from __future__ import annotations
 
 import math
@@ -45,3 +47,10 @@ def ssim(a: torch.Tensor, b: torch.Tensor, k1=0.01, k2=0.03) -> float:
     c1, c2 = k1 * k1, k2 * k2
     s = ((2 * mx * my + c1) * (2 * sxy + c2)) / ((mx * mx + my * my + c1) * (sxx + syy + c2))
     return float(s.mean(dim=(1, 2)).mean().item())
+
+
+def tpsnr(o_prev: torch.Tensor, o: torch.Tensor, y_prev: torch.Tensor, y: torch.Tensor) -> float:
+    """Temporal PSNR of one frame pair: the reconstruction's change against the reference's."""
+    d = (o.clamp(0, 1) - o_prev.clamp(0, 1)) - (y.clamp(0, 1) - y_prev.clamp(0, 1))
+    mse = torch.mean(d.to(torch.float64) ** 2).item()
+    return float("inf") if mse == 0 else -10.0 * math.log10(mse)

@@ -295,3 +295,20 @@ def test_device_quality_metrics_match_the_oracle():
     assert abs(quality.psnr(torch.from_numpy(a), torch.from_numpy(b)) - metrics.psnr(a, b)) < 1e-9
     assert abs(quality.ssim(torch.from_numpy(a), torch.from_numpy(b)) - metrics.ssim(a, b)) < 1e-12
     assert abs(quality.ssim(torch.from_numpy(a[0]), torch.from_numpy(b[0])) - metrics.ssim(a[0], b[0])) < 1e-12
+
+
+
+def test_tpsnr_closed_form_and_device_metric():
+    import torch
+    from paper_2209_09965_gb300 import quality
+    rng = np.random.default_rng(13)
+    y0, y1 = rng.integers(0, 57, (2, 3, 16, 20)) / 64.0          # dyadic: the differences are exact
+    # a reconstruction off by a constant (inside [0, 1]) changes exactly like the reference
+    assert metrics.tpsnr(y0 + 0.0625, y1 + 0.0625, y0, y1) == float("inf")
+    # a static reconstruction of a changing reference: the error is the reference's change
+    d = y1 - y0
+    assert abs(metrics.tpsnr(y0, y0, y0, y1) - (-10 * np.log10(np.mean(d ** 2)))) < 1e-12
+    o0 = np.clip(y0 + rng.normal(0, 0.03, y0.shape), -0.1, 1.1)
+    o1 = np.clip(y1 + rng.normal(0, 0.03, y1.shape), -0.1, 1.1)
+    t = [torch.from_numpy(v) for v in (o0, o1, y0, y1)]
+    assert abs(quality.tpsnr(*t) - metrics.tpsnr(o0, o1, y0, y1)) < 1e-9
