@@ -38,9 +38,18 @@ per-pixel filter kernels and applies them; the reading used here applies one
 c is the sparse RGB, M the mask channel; neighbours outside the frame count
 as M = 0.
 
+Recurrent variant (the paper's "Recurrence" subsection: D's output is passed
+back to its input layer in the next run, concatenated along the channels):
+enc0 takes 8 channels, the 5 of the sparse frame and the previous frame's
+output RGB clamped to [0, 1] (zeros for the first frame).  The paper's
+recurrent connections between decoder blocks are not part of this variant.
+
 Loss (replaces the paper's Eq. 4-7 perceptual / temporal terms, which need
 VGG19 weights and optical flow): L1 + lambda_g * L1 of forward differences
-along x and y, each term a mean over its own elements, lambda_g = 1.
+along x and y, each term a mean over its own elements, lambda_g = 1.  For
+the recurrent variant the temporal term of Eq. 6 without its optical-flow
+part: L_t = mean |(O_t - O_t-1) - (Y_t - Y_t-1)|, combined as in Eq. 4 with
+lambda_s = 0.8, lambda_t = 1.0.
 Adam: beta = (0.9, 0.999), eps = 1e-8, bias-corrected, no weight decay.
 """
 from __future__ import annotations
@@ -64,11 +73,19 @@ def layer_table(chans=(16, 32, 64), cin=5):
     )
 
 
-def unpack(flat, chans=(16, 32, 64)):
-    """Flat float vector -> {name: (W[co,ci,k,k], b[co])} in float64."""
+def param_count(chans=(16, 32, 64), cin=5):
+    return sum(co * ci * k * k + co for _, ci, co, k in layer_table(chans, cin))
+
+
+def unpack(flat, chans=(16, 32, 64), cin=None):
+    """Flat float vector -> {name: (W[co,ci,k,k], b[co])} in float64.  The
+    input width (5, or 8 for the recurrent variant) follows from the size
+    unless given."""
     flat = np.asarray(flat, dtype=np.float64)
+    if cin is None:
+        cin = 8 if flat.size == param_count(chans, 8) else 5
     out, off = {}, 0
-    for name, ci, co, k in layer_table(chans):
+    for name, ci, co, k in layer_table(chans, cin):
         nw = co * ci * k * k
         out[name] = (flat[off:off + nw].reshape(co, ci, k, k), flat[off + nw:off + nw + co])
         off += nw + co
@@ -79,7 +96,7 @@ def unpack(flat, chans=(16, 32, 64)):
 
 def pack(params, chans=(16, 32, 64)):
     parts = []
-    for name, _, _, _ in layer_table(chans):
+    for name, _, _, _ in layer_table(chans, params["enc0a"][0].shape[1]):
         w, b = params[name]
         parts += [np.asarray(w, np.float64).ravel(), np.asarray(b, np.float64).ravel()]
     return np.concatenate(parts)
@@ -235,14 +252,22 @@ def _pad4(x):
     return xp
 
 
-def forward(params, sparse, return_cache=False):
-    """sparse [N,5,H,W] (or [5,H,W]) float -> rgb [N,3,H,W] (or [3,H,W])."""
+def forward(params, sparse, return_cache=False, prev=None):
+    """sparse [N,5,H,W] (or [5,H,W]) float -> rgb [N,3,H,W] (or [3,H,W]).
+    With recurrent parameters (8 input channels) ``prev`` is the previous
+    output [N,3,H,W] (None: zeros), clamped to [0, 1] as input."""
     single = sparse.ndim == 3
     x_in = np.asarray(sparse, np.float64)
     if single:
         x_in = x_in[None]
     n, _, h, w = x_in.shape
-    x = _pad4(x_in)
+    if params["enc0a"][0].shape[1] == 8:
+        pv = np.zeros((n, 3, h, w)) if prev is None else np.clip(np.asarray(prev, np.float64), 0.0, 1.0)
+        if pv.ndim == 3:
+            pv = pv[None]
+        x = _pad4(np.concatenate([x_in, pv], axis=1))
+    else:
+        x = _pad4(x_in)
     cache = {"x": x}
 
     def cbr(name, inp):
@@ -338,3 +363,10 @@ def adam_step(p, g, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
     mh = m / (1.0 - b1 ** step)
     vh = v / (1.0 - b2 ** step)
     return p - lr * mh / (np.sqrt(vh) + eps), m, v
+
+
+def loss_temporal(o, o_prev, y, y_prev):
+    """(L_t, dL_t/do): mean |(o - o_prev) - (y - y_prev)| (the temporal L1 term
+    without optical flow); o_prev is a constant of the step."""
+    d = (np.asarray(o, np.float64) - o_prev) - (np.asarray(y, np.float64) - y_prev)
+    return float(np.mean(np.abs(d))), np.sign(d) / d.size

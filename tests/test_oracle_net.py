@@ -312,3 +312,82 @@ def test_tpsnr_closed_form_and_device_metric():
     o1 = np.clip(y1 + rng.normal(0, 0.03, y1.shape), -0.1, 1.1)
     t = [torch.from_numpy(v) for v in (o0, o1, y0, y1)]
     assert abs(quality.tpsnr(*t) - metrics.tpsnr(o0, o1, y0, y1)) < 1e-9
+
+
+# ---- recurrent variant: the previous output as three more input channels ----
+
+def _recurrent_from(flat5, rng=None, scale=0.0):
+    """The 8-input network equal to a 5-input one plus prev-channel weights (zero or random)."""
+    p = on.unpack(flat5)
+    w, b = p["enc0a"]
+    extra = np.zeros((w.shape[0], 3, 3, 3)) if rng is None else rng.normal(0, scale, (w.shape[0], 3, 3, 3))
+    p["enc0a"] = (np.concatenate([w, extra], axis=1), b)
+    return p
+
+
+def test_recurrent_with_zero_history_weights_is_the_plain_network():
+    rng = np.random.default_rng(21)
+    flat = wl.net_weights(3)
+    sparse = rng.uniform(0, 1, (2, 5, 12, 18))
+    sparse[:, 4] = (rng.random((2, 12, 18)) < 0.4)
+    prev = rng.uniform(-0.5, 1.5, (2, 3, 12, 18))
+    plain = on.forward(on.unpack(flat), sparse)
+    rec0 = _recurrent_from(flat)
+    assert on.param_count(cin=8) == on.pack(rec0).size
+    assert np.array_equal(on.unpack(on.pack(rec0))["enc0a"][0], rec0["enc0a"][0])
+    assert np.allclose(on.forward(rec0, sparse, prev=prev), plain, atol=1e-13)
+    rec = _recurrent_from(flat, rng, 0.3)
+    # no history is zero history; history outside [0, 1] acts clamped
+    assert np.array_equal(on.forward(rec, sparse), on.forward(rec, sparse, prev=np.zeros((2, 3, 12, 18))))
+    assert np.array_equal(on.forward(rec, sparse, prev=prev), on.forward(rec, sparse, prev=np.clip(prev, 0, 1)))
+    assert not np.allclose(on.forward(rec, sparse, prev=prev), plain, atol=1e-3)
+
+
+def test_recurrent_history_enters_the_first_convolution_linearly():
+    rng = np.random.default_rng(22)
+    rec = _recurrent_from(wl.net_weights(4), rng, 0.3)
+    sparse = rng.uniform(0, 1, (1, 5, 8, 12))
+    prev = rng.uniform(0, 1, (1, 3, 8, 12))
+    _, c1 = on.forward(rec, sparse, return_cache=True, prev=prev)
+    _, c0 = on.forward(rec, sparse, return_cache=True)
+    dz = c1["enc0a"][1] - c0["enc0a"][1]
+    ref = F.conv2d(torch.from_numpy(prev), torch.from_numpy(rec["enc0a"][0][:, 5:]), padding=1).numpy()
+    assert np.max(np.abs(dz - ref)) < 1e-12
+
+
+def test_recurrent_backward_matches_finite_differences():
+    rng = np.random.default_rng(23)
+    rec = _recurrent_from(wl.net_weights(5), rng, 0.3)
+    sparse = rng.uniform(0, 1, (1, 5, 8, 8))
+    sparse[:, 4] = 1.0
+    prev = rng.uniform(0, 1, (1, 3, 8, 8))
+    gout = rng.normal(size=(1, 3, 8, 8))
+    _, cache = on.forward(rec, sparse, return_cache=True, prev=prev)
+    g = on.backward(rec, cache, gout)
+    for (o, c, ky, kx) in [(0, 5, 1, 1), (3, 7, 0, 2), (9, 6, 2, 0)]:      # history-channel weights
+        eps = 1e-6
+        w = rec["enc0a"][0]
+        old = w[o, c, ky, kx]
+        w[o, c, ky, kx] = old + eps
+        fp = np.sum(on.forward(rec, sparse, prev=prev) * gout)
+        w[o, c, ky, kx] = old - eps
+        fm = np.sum(on.forward(rec, sparse, prev=prev) * gout)
+        w[o, c, ky, kx] = old
+        assert abs((fp - fm) / (2 * eps) - g["enc0a"][0][o, c, ky, kx]) < 1e-6 * max(1.0, abs(fp - fm) / eps)
+
+
+def test_temporal_loss_closed_form_and_gradient():
+    rng = np.random.default_rng(24)
+    y0, y1 = rng.uniform(0, 1, (2, 3, 6, 7))
+    o0 = rng.uniform(0, 1, (3, 6, 7))
+    # a reconstruction that follows the reference's change exactly: zero loss
+    l, g = on.loss_temporal(o0 + (y1 - y0), o0, y1, y0)
+    assert l < 1e-15
+    o1 = rng.uniform(0, 1, (3, 6, 7))
+    l, g = on.loss_temporal(o1, o0, y1, y0)
+    assert abs(l - np.mean(np.abs((o1 - o0) - (y1 - y0)))) < 1e-15
+    for idx in [(0, 0, 0), (2, 5, 6), (1, 3, 2)]:
+        e = np.zeros_like(o1)
+        e[idx] = 1e-7
+        fd = (on.loss_temporal(o1 + e, o0, y1, y0)[0] - on.loss_temporal(o1 - e, o0, y1, y0)[0]) / 2e-7
+        assert abs(fd - g[idx]) < 1e-6
