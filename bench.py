@@ -490,6 +490,63 @@ def run_blue_noise(ctx, wl, vol, tf, mp, frames, dev, nframes, flush):
         ctx.set_noise_tiles(None)
 
 
+REC_WEIGHTS = os.path.join(ROOT, "paper_2209_09965_gb300", "weights", "fvn_16_32_64_recurrent.npy")
+
+
+def run_recurrent(fvn, wl, weights, vol, tf, mp, dev, nframes, flush):
+    """The recurrent network (previous output fed back as input) against the
+    plain one on consecutive frames of two orbits -- the benchmark's (64
+    frames per turn) and a slower one (256 per turn) -- PSNR and temporal
+    PSNR against the dense render, and frames/s of fvn_render_recurrent."""
+    import numpy as np
+    import torch
+    if not os.path.exists(REC_WEIGHTS):
+        return None
+    plain, rec = fvn.Context(), fvn.Context()
+    try:
+        plain.load_weights(weights)
+        rec.load_weights(np.load(REC_WEIGHTS).astype(np.float32))
+        bufs = [torch.zeros(3, H, W, device=dev) for _ in range(2)]
+        rgb = torch.empty(3, H, W, device=dev)
+        dense = torch.empty(5, H, W, device=dev)
+        stream = torch.cuda.current_stream()
+        out = {}
+        for per_turn in (ORBIT, 4 * ORBIT):
+            res = {"plain": ([], TemporalPsnr()), "recurrent": ([], TemporalPsnr())}
+            ms = []
+            for i in range(nframes):
+                cam = wl.orbit_camera(2, i, nframes=per_turn, width=W, height=H, radius_factor=(0.85, 1.75))
+                fov = wl.Foveation(focal_px=wl.focal_point(2, i, W, H), seed=2, frame=i)
+                plain.march(vol, tf, cam, mp, dense)
+                plain.render(vol, tf, cam, fov, mp, rgb)
+                cur, prev = bufs[i % 2], bufs[(i + 1) % 2]
+                flush.fill_(float(i))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                rec.render(vol, tf, cam, fov, mp, cur, prev=None if i == 0 else prev)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i >= 2:
+                    ms.append(e0.elapsed_time(e1))
+                for key, img in (("plain", rgb), ("recurrent", cur)):
+                    res[key][0].append(psnr_t(img, dense[:3]))
+                    res[key][1].add(img, dense[:3])
+            out[f"orbit_{per_turn}_frames_per_turn"] = {
+                k: {"psnr_vs_dense_db": float(np.mean(v[0])), "tpsnr_vs_dense_db": v[1].summary()}
+                for k, v in res.items()}
+            out[f"orbit_{per_turn}_frames_per_turn"]["recurrent_frames_per_s"] = len(ms) / (sum(ms) / 1000.0)
+        plain.device_status()
+        rec.device_status()
+        out["workload"] = ("the headline workload on consecutive orbit frames; recurrent network = the plain "
+                           "one fine-tuned with the previous output as input and the temporal loss")
+        return out
+    except Exception as exc:   # reported, not part of the metric
+        return {"error": str(exc)[:200]}
+    finally:
+        plain.close()
+        rec.close()
+
+
 def run_multiview(ctx, fvn, wl, dev, steps, warmup, flush):
     """Batched multi-view frames: 16 views (4 stereo pairs at 2064x2208, 4 at
     1280x720, 4 at 3840x2160) over a 512^3 float16 noise volume and a 1024^3
@@ -809,6 +866,7 @@ def main():
                               else "mma_sync", vol, tf, frames, dev, min(args.steps, 16), flush)
 
     blue = run_blue_noise(ctx, wl, vol, tf, mp, frames, dev, min(args.steps, ORBIT), flush)
+    recurrent = run_recurrent(fvn, wl, weights, vol, tf, mp, dev, min(args.steps, 32), flush)
 
     multiview = None
     if not args.no_multiview:
@@ -866,6 +924,7 @@ def main():
             "fp8": fp8_info,
             "shadows": shadows,
             "blue_noise_mask": blue,
+            "recurrent": recurrent,
             "multiview": multiview,
             "clocks": clocks,
         }

@@ -257,11 +257,16 @@ fvn_status fvn_march_masked(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* t
  * enc0a(5->16) enc0b(16->16) enc1a(16->32) enc1b(32->32) bota(32->64)
  * botb(64->64) dec1a(96->32) dec1b(32->32) dec0a(48->16) dec0b(16->16)
  * head(16->29, 1x1); each layer W[cout][cin][k][k] then b[cout].  n must
- * equal fvn_weight_count().  Converts to the FP16 and FP8 layouts of the
- * kernels.  Synchronises the host.
+ * equal fvn_weight_count(), or fvn_weight_count_recurrent() for the
+ * recurrent network, whose enc0a takes 8 channels: the 5 of the sparse frame
+ * and the previous frame's output RGB (paper: "Recurrence": the output of D
+ * is passed back to its input in the next run, concatenated along the
+ * channels).  Converts to the FP16 and FP8 layouts of the kernels.
+ * Synchronises the host.
  */
 fvn_status fvn_load_weights(fvn_ctx* ctx, const float* host_w, size_t n);
 size_t fvn_weight_count(void);
+size_t fvn_weight_count_recurrent(void);
 
 /*
  * fvn_reconstruct -- full frame from the sparse samples.
@@ -281,6 +286,18 @@ size_t fvn_weight_count(void);
  */
 fvn_status fvn_reconstruct(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
                            void* stream);
+
+/*
+ * fvn_reconstruct_recurrent -- fvn_reconstruct with the recurrent network:
+ * prev_rgb (device float [3][h][w], the previous frame's output, clamped to
+ * [0, 1] as input; NULL reads zeros, for the first frame of a sequence)
+ * enters the first layer beside the sparse frame.  rgb must not alias
+ * prev_rgb.  FVN_ERR_STATE when prev_rgb is set and the loaded weights are
+ * not the recurrent network's.  (fvn_reconstruct with recurrent weights is
+ * this call with prev_rgb = NULL.)
+ */
+fvn_status fvn_reconstruct_recurrent(fvn_ctx* ctx, const float* rgbam, const float* prev_rgb, int w, int h,
+                                     int precision, float* rgb, void* stream);
 
 /*
  * fvn_calibrate_fp8 -- activation scales and E4M3 weights for
@@ -332,6 +349,12 @@ fvn_status fvn_render(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
                       const fvn_foveation* fov, const fvn_march_params* mp, int precision, float* rgb,
                       float* rgbam_out, void* stream);
 
+/* fvn_render with the recurrent network and the previous frame's output
+ * prev_rgb (as fvn_reconstruct_recurrent; rgb must not alias it). */
+fvn_status fvn_render_recurrent(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
+                                const fvn_foveation* fov, const fvn_march_params* mp, int precision,
+                                const float* prev_rgb, float* rgb, float* rgbam_out, void* stream);
+
 /*
  * fvn_render_adaptive -- fvn_render with a denser-mask fallback (the paper
  * has no counterpart; this is the frame-quality guard of this library).
@@ -357,7 +380,9 @@ fvn_status fvn_render_adaptive(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf
  * returns; views may share them).  cam, fov: the view's camera (its width x
  * height is the view's size) and foveation.  rgb: device float [3][h][w]
  * output.  rgbam: optional device float [5][h][w] that receives the view's
- * sparse frame (NULL: kept in the context's workspace). */
+ * sparse frame (NULL: kept in the context's workspace).  prev_rgb: the
+ * view's previous output for the recurrent network (as
+ * fvn_reconstruct_recurrent), or NULL. */
 typedef struct {
     const fvn_volume* vol;
     const fvn_tf* tf;
@@ -365,6 +390,7 @@ typedef struct {
     fvn_foveation fov;
     float* rgb;
     float* rgbam;
+    const float* prev_rgb;
 } fvn_view;
 
 /*

@@ -59,6 +59,8 @@ fvn_status validate_view(fvn_ctx* ctx, const fvn_view& v, int i) {
                            isfinite(f.fovea_radius) && isfinite(f.falloff_sigma),
                   "view %d: foveation radius / falloff must be >= 0 and p_base in [0, 1]", i);
     FVN_CHECK_ARG(ctx, v.rgb != nullptr, "view %d: rgb output is NULL", i);
+    if (v.prev_rgb && !ctx->recurrent)
+        return set_error(ctx, FVN_ERR_STATE, "view %d: a previous frame needs the recurrent network's weights", i);
     return FVN_OK;
 }
 
@@ -172,11 +174,13 @@ extern "C" fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int 
             rv[i].w = w[i];
             rv[i].h = h[i];
             rv[i].rgb = views[i].rgb;
+            rv[i].prev = views[i].prev_rgb;
         }
         return reconstruct_tc_views(ctx, rv, nviews, precision, st);
     }
     for (int i = 0; i < nviews; ++i)   // mma.sync convolutions: one network pass per view
-        if ((s = reconstruct_on(ctx, base + lay[i].plan, rgbam[i], w[i], h[i], precision, views[i].rgb, st)) !=
+        if ((s = reconstruct_on(ctx, base + lay[i].plan, rgbam[i], views[i].prev_rgb, w[i], h[i], precision,
+                                views[i].rgb, st)) !=
             FVN_OK)
             return s;
     return FVN_OK;

@@ -69,6 +69,7 @@ struct ReconView {
     const float* rgbam;
     int w, h;
     float* rgb;
+    const float* prev = nullptr;      // recurrent model: previous output [3][h][w] (NULL: zeros)
 };
 
 // Workspace of fvn_render_batch, one allocation carved per view.
@@ -115,6 +116,7 @@ struct fvn_ctx {
     int* d_ticket = nullptr;          // 64 march work-queue counters (stream-ordered reset)
     unsigned ticket_ring = 0;         // next counter to use, so queued launches do not share one
     bool has_weights = false;
+    bool recurrent = false;           // the loaded weights take the previous output as input
     fvn::ConvW layers[fvn::kNumLayers];
     float* head_w = nullptr;          // FP32 [29][16] + [29] bias for the head / KP stage
     __half* head_w16 = nullptr;       // head weights as a tensor-core operand: [2][32][8] FP16 (rows 29-31 zero)
@@ -177,8 +179,8 @@ fvn_status make_mask_impl(fvn_ctx* ctx, const fvn_foveation* fov, int w, int h, 
 fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
                       const fvn_march_params* mp, const int32_t* ids, const int32_t* count, float* rgbam,
                       unsigned long long* nsamples, cudaStream_t st, const uint8_t* reject = nullptr);
-fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
-                            cudaStream_t st);
+fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, const float* prev, int w, int h, int precision,
+                            float* rgb, cudaStream_t st);
 // One view of the batched march: its volume and padded copy, transfer
 // function, camera, compacted ids / count (device) and sparse frame.
 struct BatchMarchView {
@@ -208,13 +210,13 @@ fvn_status make_mask_batch_impl(fvn_ctx* ctx, const fvn_foveation* const* fov, c
                                 cudaStream_t st);
 // The network launch sequence on a caller-provided workspace of at least
 // recon_workspace_bytes(w, h) bytes (256-byte aligned).
-fvn_status reconstruct_on(fvn_ctx* ctx, void* workspace, const float* rgbam, int w, int h, int precision,
-                          float* rgb, cudaStream_t st);
+fvn_status reconstruct_on(fvn_ctx* ctx, void* workspace, const float* rgbam, const float* prev, int w, int h,
+                          int precision, float* rgb, cudaStream_t st);
 size_t recon_workspace_bytes(int w, int h);
-fvn_status reconstruct_tc(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, int w, int h, float* rgb,
-                          cudaStream_t st);
-fvn_status reconstruct_tc_fp8(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, int w, int h, float* rgb,
-                              cudaStream_t st);
+fvn_status reconstruct_tc(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, const float* prev, int w, int h,
+                          float* rgb, cudaStream_t st);
+fvn_status reconstruct_tc_fp8(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, const float* prev, int w,
+                              int h, float* rgb, cudaStream_t st);
 fvn_status calibrate_amax(fvn_ctx* ctx, const ReconPlan& B, int w, int h, float* d_amax, cudaStream_t st);
 // The network over n views, one launch per layer for all of them (tcgen05).
 fvn_status reconstruct_tc_views(fvn_ctx* ctx, const ReconView* views, int n, int precision, cudaStream_t st);

@@ -143,6 +143,7 @@ struct TcImg {
     const void* in;          // chunk-planar input, or the coarse level for up-sampling
     const void* skip;        // skip tensor (up-sampling layers)
     const float* rgbam;      // sparse frame [5][H0][W0] (first layer, KP)
+    const float* prev;       // first layer, recurrent model: previous output [3][H0][W0] (NULL: zeros)
     void* out;               // [Hl][Wl][COUT]
     void* pooled;            // [Hl/2][Wl/2][COUT]
     float* rgb;              // [3][H0][W0] (KP layer)
@@ -269,6 +270,12 @@ __global__ void __launch_bounds__(kThreads) conv3x3_tc_kernel(const __grid_const
                     const float* p = im.rgbam + (long long)gy * im.W0 + gx;
 #pragma unroll
                     for (int c = 0; c < 5; ++c) v[c] = __ldg(p + c * plane) * (F8 ? a.in_q : 1.0f);
+                    if (im.prev) {   // the previous output, clamped to [0, 1], as channels 5..7
+                        const float* q = im.prev + (long long)gy * im.W0 + gx;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c)
+                            v[5 + c] = __saturatef(__ldg(q + c * plane)) * (F8 ? a.in_q : 1.0f);
+                    }
                 }
                 *reinterpret_cast<uint4*>(sH + ((0 * HY + hy) * HXW + hx) * 16) = F8 ? pack16q(v) : pack8h(v);
 #pragma unroll
@@ -868,7 +875,9 @@ static TcImg layer_img(int l, const ReconView& v) {
     const int W4 = (v.w + 3) & ~3, H4 = (v.h + 3) & ~3;
     TcImg m{};
     switch (l) {
-        case 0: m.rgbam = v.rgbam; m.H0 = v.h; m.W0 = v.w; m.out = B.e0a; m.Hl = H4; m.Wl = W4; break;
+        case 0:
+            m.rgbam = v.rgbam; m.prev = v.prev; m.H0 = v.h; m.W0 = v.w; m.out = B.e0a; m.Hl = H4; m.Wl = W4;
+            break;
         case 1: m.in = B.e0a; m.out = B.e0; m.pooled = B.p0; m.Hl = H4; m.Wl = W4; break;
         case 2: m.in = B.p0; m.out = B.e1a; m.Hl = H4 / 2; m.Wl = W4 / 2; break;
         case 3: m.in = B.e1a; m.out = B.e1; m.pooled = B.p1; m.Hl = H4 / 2; m.Wl = W4 / 2; break;
@@ -1024,15 +1033,15 @@ fvn_status reconstruct_tc_views(fvn_ctx* ctx, const ReconView* views, int n, int
     return precision == FVN_PREC_FP8 ? run_tc<true>(ctx, views, n, st) : run_tc<false>(ctx, views, n, st);
 }
 
-fvn_status reconstruct_tc(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, int w, int h, float* rgb,
-                          cudaStream_t st) {
-    const ReconView v{B, rgbam, w, h, rgb};
+fvn_status reconstruct_tc(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, const float* prev, int w, int h,
+                          float* rgb, cudaStream_t st) {
+    const ReconView v{B, rgbam, w, h, rgb, prev};
     return run_tc<false>(ctx, &v, 1, st);
 }
 
-fvn_status reconstruct_tc_fp8(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, int w, int h, float* rgb,
-                              cudaStream_t st) {
-    const ReconView v{B, rgbam, w, h, rgb};
+fvn_status reconstruct_tc_fp8(fvn_ctx* ctx, const ReconPlan& B, const float* rgbam, const float* prev, int w,
+                              int h, float* rgb, cudaStream_t st) {
+    const ReconView v{B, rgbam, w, h, rgb, prev};
     return run_tc<true>(ctx, &v, 1, st);
 }
 

@@ -197,9 +197,9 @@ extern "C" fvn_status fvn_device_status(fvn_ctx* ctx) {
     return FVN_OK;
 }
 
-extern "C" fvn_status fvn_render(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
-                                 const fvn_foveation* fov, const fvn_march_params* mp, int precision, float* rgb,
-                                 float* rgbam_out, void* stream) {
+static fvn_status render_entry(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
+                               const fvn_foveation* fov, const fvn_march_params* mp, int precision, const float* prev,
+                               float* rgb, float* rgbam_out, void* stream) {
     if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
     fvn_status st;
     if ((st = validate_volume(ctx, vol)) != FVN_OK) return st;
@@ -210,6 +210,8 @@ extern "C" fvn_status fvn_render(fvn_ctx* ctx, const fvn_volume* vol, const fvn_
     FVN_CHECK_ARG(ctx, rgb != nullptr, "rgb output is NULL");
     FVN_CHECK_ARG(ctx, precision == FVN_PREC_FP16 || precision == FVN_PREC_FP8, "unknown precision %d", precision);
     if (!ctx->has_weights) return set_error(ctx, FVN_ERR_STATE, "no weights loaded (call fvn_load_weights)");
+    if (prev && !ctx->recurrent)
+        return set_error(ctx, FVN_ERR_STATE, "a previous frame needs the recurrent network's weights");
     const int w = cam->width, h = cam->height;
     RenderWorkspace& ws = ctx->render_ws;
     if (ws.w != w || ws.h != h) {
@@ -232,5 +234,18 @@ extern "C" fvn_status fvn_render(fvn_ctx* ctx, const fvn_volume* vol, const fvn_
     float* rgbam = rgbam_out ? rgbam_out : ws.rgbam;
     if ((st = make_mask_impl(ctx, fov, w, h, ws.mask, ws.ids, ws.count, s)) != FVN_OK) return st;
     if ((st = march_impl(ctx, vol, tf, cam, mp, ws.ids, ws.count, rgbam, nullptr, s)) != FVN_OK) return st;
-    return reconstruct_impl(ctx, rgbam, w, h, precision, rgb, s);
+    return reconstruct_impl(ctx, rgbam, prev, w, h, precision, rgb, s);
+}
+
+extern "C" fvn_status fvn_render(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
+                                 const fvn_foveation* fov, const fvn_march_params* mp, int precision, float* rgb,
+                                 float* rgbam_out, void* stream) {
+    return render_entry(ctx, vol, tf, cam, fov, mp, precision, nullptr, rgb, rgbam_out, stream);
+}
+
+extern "C" fvn_status fvn_render_recurrent(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf,
+                                           const fvn_camera* cam, const fvn_foveation* fov,
+                                           const fvn_march_params* mp, int precision, const float* prev_rgb,
+                                           float* rgb, float* rgbam_out, void* stream) {
+    return render_entry(ctx, vol, tf, cam, fov, mp, precision, prev_rgb, rgb, rgbam_out, stream);
 }

@@ -70,5 +70,5 @@ extern "C" fvn_status fvn_reconstruct_noalloc(fvn_ctx* ctx, const float* rgbam, 
     void* ws = nullptr;
     fvn_status st = noalloc_workspace(ctx, &ws);
     if (st != FVN_OK) return st;
-    return reconstruct_on(ctx, ws, rgbam, w, h, precision, rgb, as_stream(stream));
+    return reconstruct_on(ctx, ws, rgbam, nullptr, w, h, precision, rgb, as_stream(stream));
 }

@@ -42,9 +42,21 @@ static const LayerSpec kLayers[kNumLayers] = {
 };
 constexpr int kHeadC = 29;
 
-static size_t weight_count() {
+// Layer li of the plain network, or of the recurrent one (paper:
+// "Recurrence": the previous output enters the first layer as three more
+// input channels).
+static LayerSpec layer_spec(bool recurrent, int li) {
+    LayerSpec s = kLayers[li];
+    if (li == 0 && recurrent) s.cin = 8;
+    return s;
+}
+
+static size_t weight_count(bool recurrent = false) {
     size_t n = 0;
-    for (const auto& l : kLayers) n += (size_t)l.cout * l.cin * l.k * l.k + l.cout;
+    for (int li = 0; li < kNumLayers; ++li) {
+        const LayerSpec l = layer_spec(recurrent, li);
+        n += (size_t)l.cout * l.cin * l.k * l.k + l.cout;
+    }
     return n;
 }
 
@@ -111,6 +123,7 @@ struct ConvArgs {
     const __half* in;            // IN_NHWC: [Hl][Wl][CIN]; IN_UPCAT: coarse [Hl/2][Wl/2][CUP]
     const __half* skip;          // IN_UPCAT: [Hl][Wl][CIN - CUP]
     const float* rgbam;          // IN_RGBAM: [5][H0][W0] planar FP32
+    const float* prev;           // IN_RGBAM, recurrent model: previous output [3][H0][W0] (NULL: zeros)
     int H0, W0;                  // IN_RGBAM: unpadded frame
     const __half* w;             // [9][CIN/8][COUT][8]
     const float* bias;           // [COUT]
@@ -171,6 +184,11 @@ __global__ void __launch_bounds__(COUT == 64 ? 256 : 128) conv3x3_f16_kernel(Con
                     const float* p = a.rgbam + (long long)gy * a.W0 + gx;
 #pragma unroll
                     for (int c = 0; c < 5; ++c) v[c] = __ldg(p + c * plane);
+                    if (a.prev) {   // the previous output, clamped to [0, 1], as channels 5..7
+                        const float* q = a.prev + (long long)gy * a.W0 + gx;
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) v[5 + c] = __saturatef(__ldg(q + c * plane));
+                    }
                 }
                 uint4* d0 = reinterpret_cast<uint4*>(sH + ((0 * HY + hy) * HX + hx) * 16);
                 *d0 = pack8(v);
@@ -443,8 +461,8 @@ size_t plan_view(int w, int h, ReconPlan* plan, char* base) {
     return plan_buffers((w + 3) & ~3, (h + 3) & ~3, plan ? plan : &tmp, base);
 }
 
-fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
-                            cudaStream_t st) {
+fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, const float* prev, int w, int h, int precision,
+                            float* rgb, cudaStream_t st) {
     if (precision == FVN_PREC_FP8 && !ctx->has_fp8)
         return set_error(ctx, FVN_ERR_STATE, "FP8 needs calibrated scales (call fvn_calibrate_fp8 first)");
     const int W4 = (w + 3) & ~3, H4 = (h + 3) & ~3;
@@ -459,26 +477,27 @@ fvn_status reconstruct_impl(fvn_ctx* ctx, const float* rgbam, int w, int h, int 
         ws.w = W4;
         ws.h = H4;
     }
-    return reconstruct_on(ctx, ws.base, rgbam, w, h, precision, rgb, st);
+    return reconstruct_on(ctx, ws.base, rgbam, prev, w, h, precision, rgb, st);
 }
 
-fvn_status reconstruct_on(fvn_ctx* ctx, void* workspace, const float* rgbam, int w, int h, int precision,
-                          float* rgb, cudaStream_t st) {
+fvn_status reconstruct_on(fvn_ctx* ctx, void* workspace, const float* rgbam, const float* prev, int w, int h,
+                          int precision, float* rgb, cudaStream_t st) {
     const int W4 = (w + 3) & ~3, H4 = (h + 3) & ~3;
     ReconPlan B;
     plan_buffers(W4, H4, &B, static_cast<char*>(workspace));
     if (precision == FVN_PREC_FP8) {
         if (!ctx->has_fp8)
             return set_error(ctx, FVN_ERR_STATE, "FP8 needs calibrated scales (call fvn_calibrate_fp8 first)");
-        return reconstruct_tc_fp8(ctx, B, rgbam, w, h, rgb, st);
+        return reconstruct_tc_fp8(ctx, B, rgbam, prev, w, h, rgb, st);
     }
-    if (ctx->conv_impl == CONV_TCGEN05) return reconstruct_tc(ctx, B, rgbam, w, h, rgb, st);
+    if (ctx->conv_impl == CONV_TCGEN05) return reconstruct_tc(ctx, B, rgbam, prev, w, h, rgb, st);
     const ConvW* L = ctx->layers;
     fvn_status s;
     ConvArgs a{};
     // level 0: enc0a (sparse frame -> 16), enc0b (16 -> 16, + pool)
     a = ConvArgs{};
-    a.rgbam = rgbam; a.H0 = h; a.W0 = w; a.w = L[0].w16; a.bias = L[0].bias; a.out = B.e0a; a.Hl = H4; a.Wl = W4;
+    a.rgbam = rgbam; a.prev = prev; a.H0 = h; a.W0 = w; a.w = L[0].w16; a.bias = L[0].bias; a.out = B.e0a;
+    a.Hl = H4; a.Wl = W4;
     if ((s = launch_conv<16, 16, IN_RGBAM, false, 0>(ctx, a, st)) != FVN_OK) return s;
     a = ConvArgs{};
     a.in = B.e0a; a.w = L[1].w16; a.bias = L[1].bias; a.out = B.e0; a.pooled = B.p0; a.Hl = H4; a.Wl = W4;
@@ -522,20 +541,26 @@ fvn_status reconstruct_on(fvn_ctx* ctx, void* workspace, const float* rgbam, int
 
 using namespace fvn;
 
-extern "C" size_t fvn_weight_count(void) { return weight_count(); }
+extern "C" size_t fvn_weight_count(void) { return weight_count(false); }
+
+extern "C" size_t fvn_weight_count_recurrent(void) { return weight_count(true); }
 
 extern "C" fvn_status fvn_load_weights(fvn_ctx* ctx, const float* host_w, size_t n) {
     if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
     FVN_CHECK_ARG(ctx, host_w != nullptr, "weights pointer is NULL");
-    FVN_CHECK_ARG(ctx, n == weight_count(), "weight vector has %zu entries, expected %zu", n, weight_count());
+    FVN_CHECK_ARG(ctx, n == weight_count(false) || n == weight_count(true),
+                  "weight vector has %zu entries, expected %zu (or %zu for the recurrent network)", n,
+                  weight_count(false), weight_count(true));
+    const bool recurrent = n == weight_count(true);
     for (size_t i = 0; i < n; ++i)
         FVN_CHECK_ARG(ctx, isfinite(host_w[i]), "weight %zu is not finite", i);
     FVN_CUDA(ctx, cudaDeviceSynchronize());
     ctx->host_weights.assign(host_w, host_w + n);
     ctx->has_fp8 = false;   // FP8 weights follow the FP32 weights: calibrate again
+    ctx->has_weights = false;
     size_t off = 0;
     for (int li = 0; li < kNumLayers; ++li) {
-        const LayerSpec& sp = kLayers[li];
+        const LayerSpec sp = layer_spec(recurrent, li);
         const float* W = host_w + off;
         const float* b = W + (size_t)sp.cout * sp.cin * sp.k * sp.k;
         off += (size_t)sp.cout * sp.cin * sp.k * sp.k + sp.cout;
@@ -578,19 +603,32 @@ extern "C" fvn_status fvn_load_weights(fvn_ctx* ctx, const float* host_w, size_t
         FVN_CUDA(ctx, cudaMemcpy(L.w16, w16.data(), w16.size() * sizeof(__half), cudaMemcpyHostToDevice));
         FVN_CUDA(ctx, cudaMemcpy(L.bias, b, sp.cout * sizeof(float), cudaMemcpyHostToDevice));
     }
+    ctx->recurrent = recurrent;
     ctx->has_weights = true;
     return FVN_OK;
 }
 
-extern "C" fvn_status fvn_reconstruct(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
-                                      void* stream) {
+static fvn_status reconstruct_entry(fvn_ctx* ctx, const float* rgbam, const float* prev, int w, int h,
+                                    int precision, float* rgb, void* stream) {
     if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
     FVN_CHECK_ARG(ctx, rgbam && rgb, "rgbam and rgb must be device pointers");
     FVN_CHECK_ARG(ctx, w >= 1 && h >= 1 && w <= kMaxSide && h <= kMaxSide, "frame %d x %d outside [1, %d]", w, h,
                   kMaxSide);
     FVN_CHECK_ARG(ctx, precision == FVN_PREC_FP16 || precision == FVN_PREC_FP8, "unknown precision %d", precision);
     if (!ctx->has_weights) return set_error(ctx, FVN_ERR_STATE, "no weights loaded (call fvn_load_weights)");
-    return reconstruct_impl(ctx, rgbam, w, h, precision, rgb, as_stream(stream));
+    if (prev && !ctx->recurrent)
+        return set_error(ctx, FVN_ERR_STATE, "a previous frame needs the recurrent network's weights");
+    return reconstruct_impl(ctx, rgbam, prev, w, h, precision, rgb, as_stream(stream));
+}
+
+extern "C" fvn_status fvn_reconstruct(fvn_ctx* ctx, const float* rgbam, int w, int h, int precision, float* rgb,
+                                      void* stream) {
+    return reconstruct_entry(ctx, rgbam, nullptr, w, h, precision, rgb, stream);
+}
+
+extern "C" fvn_status fvn_reconstruct_recurrent(fvn_ctx* ctx, const float* rgbam, const float* prev_rgb, int w,
+                                                int h, int precision, float* rgb, void* stream) {
+    return reconstruct_entry(ctx, rgbam, prev_rgb, w, h, precision, rgb, stream);
 }
 
 namespace fvn {
@@ -618,7 +656,7 @@ static fvn_status build_fp8_weights(fvn_ctx* ctx) {
     }
     size_t off = 0;
     for (int li = 0; li < kNumLayers; ++li) {
-        const LayerSpec& sp = kLayers[li];
+        const LayerSpec sp = layer_spec(ctx->recurrent, li);
         const float* W = hw + off;
         off += (size_t)sp.cout * sp.cin * sp.k * sp.k + sp.cout;
         if (sp.k != 3) continue;

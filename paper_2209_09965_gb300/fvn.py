@@ -31,6 +31,7 @@ EXPORTS = (
     "fvn_avgpool2_bwd", "fvn_upsample2_fwd", "fvn_upsample2_bwd", "fvn_kp_blend_fwd", "fvn_kp_blend_bwd",
     "fvn_loss_l1grad", "fvn_adam_step", "fvn_reconstruct_noalloc", "fvn_set_option", "fvn_device_status",
     "fvn_calibrate_fp8", "fvn_render_adaptive", "fvn_march_masked", "fvn_render_batch", "fvn_set_noise_tiles",
+    "fvn_weight_count_recurrent", "fvn_reconstruct_recurrent", "fvn_render_recurrent",
 )
 MAX_VIEWS = 16
 OPT_CONV_KERNEL, OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 1, 2, 3
@@ -74,7 +75,8 @@ class MarchParamsC(ctypes.Structure):
 
 class ViewC(ctypes.Structure):
     _fields_ = [("vol", ctypes.POINTER(Volume)), ("tf", ctypes.POINTER(TF)), ("cam", CameraC),
-                ("fov", FoveationC), ("rgb", ctypes.c_void_p), ("rgbam", ctypes.c_void_p)]
+                ("fov", FoveationC), ("rgb", ctypes.c_void_p), ("rgbam", ctypes.c_void_p),
+                ("prev_rgb", ctypes.c_void_p)]
 
 
 def _load():
@@ -89,6 +91,8 @@ def _load():
         "fvn_march": [P, P, P, P, P, P, P, P, P, P],
         "fvn_load_weights": [P, P, ctypes.c_size_t],
         "fvn_reconstruct": [P, P, I, I, I, P, P],
+        "fvn_reconstruct_recurrent": [P, P, P, I, I, I, P, P],
+        "fvn_render_recurrent": [P, P, P, P, P, P, I, P, P, P, P],
         "fvn_reconstruct_noalloc": [P, P, I, I, I, P, P],
         "fvn_set_option": [P, I, I],
         "fvn_calibrate_fp8": [P, P, I, I, I, P],
@@ -117,6 +121,8 @@ def _load():
     lib.fvn_last_error.restype = ctypes.c_char_p
     lib.fvn_weight_count.argtypes = []
     lib.fvn_weight_count.restype = ctypes.c_size_t
+    lib.fvn_weight_count_recurrent.argtypes = []
+    lib.fvn_weight_count_recurrent.restype = ctypes.c_size_t
     return lib
 
 
@@ -198,6 +204,10 @@ def weight_count() -> int:
     return int(lib.fvn_weight_count())
 
 
+def weight_count_recurrent() -> int:
+    return int(lib.fvn_weight_count_recurrent())
+
+
 class Context:
     """Owns an fvn_ctx (threshold tables, work-queue counters, weights and
     reconstruction workspace) on the current CUDA device."""
@@ -265,9 +275,14 @@ class Context:
         a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
         self._chk(lib.fvn_load_weights(self.h, a.ctypes.data_as(ctypes.c_void_p), a.size))
 
-    def reconstruct(self, rgbam, w, h, rgb, precision=PREC_FP16, stream=None):
-        self._chk(lib.fvn_reconstruct(self.h, _ptr(rgbam), int(w), int(h), int(precision), _ptr(rgb),
-                                      _stream(stream)))
+    def reconstruct(self, rgbam, w, h, rgb, precision=PREC_FP16, stream=None, prev=None):
+        """prev: the previous output [3, h, w] for the recurrent network (fvn_reconstruct_recurrent)."""
+        if prev is None:
+            self._chk(lib.fvn_reconstruct(self.h, _ptr(rgbam), int(w), int(h), int(precision), _ptr(rgb),
+                                          _stream(stream)))
+        else:
+            self._chk(lib.fvn_reconstruct_recurrent(self.h, _ptr(rgbam), _ptr(prev), int(w), int(h), int(precision),
+                                                    _ptr(rgb), _stream(stream)))
 
     def render_adaptive(self, vol, tf, cam, fov, mp, rgb, min_psnr_db=35.0, max_levels=3, precision=PREC_FP16,
                         stream=None):
@@ -291,16 +306,23 @@ class Context:
         self._chk(lib.fvn_reconstruct_noalloc(self.h, _ptr(rgbam), int(w), int(h), int(precision), _ptr(rgb),
                                               _stream(stream)))
 
-    def render(self, vol, tf, cam, fov, mp, rgb, precision=PREC_FP16, rgbam_out=None, stream=None):
+    def render(self, vol, tf, cam, fov, mp, rgb, precision=PREC_FP16, rgbam_out=None, stream=None, prev=None):
+        """prev: the previous output [3, h, w] for the recurrent network (fvn_render_recurrent)."""
         v, t, c, m = volume(vol), transfer_function(tf), camera(cam), march_params(mp)
         f = foveation(fov)
-        self._chk(lib.fvn_render(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c), ctypes.byref(f),
-                                 ctypes.byref(m), int(precision), _ptr(rgb), _ptr(rgbam_out), _stream(stream)))
+        if prev is None:
+            self._chk(lib.fvn_render(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c), ctypes.byref(f),
+                                     ctypes.byref(m), int(precision), _ptr(rgb), _ptr(rgbam_out), _stream(stream)))
+        else:
+            self._chk(lib.fvn_render_recurrent(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c),
+                                               ctypes.byref(f), ctypes.byref(m), int(precision), _ptr(prev),
+                                               _ptr(rgb), _ptr(rgbam_out), _stream(stream)))
 
     def render_batch(self, views, mp, precision=PREC_FP16, nsamples=None, stream=None):
         """fvn_render for several views in one pass.  ``views`` is a list of
         dicts with keys vol, tf (CUDA tensors), cam, fov and rgb (CUDA
-        [3, h, w] float32), optionally rgbam (CUDA [5, h, w] float32)."""
+        [3, h, w] float32), optionally rgbam (CUDA [5, h, w] float32) and
+        prev (the view's previous output, recurrent network)."""
         n = len(views)
         arr = (ViewC * max(n, 1))()
         keep = []   # descriptors referenced by pointer must outlive the call
@@ -321,6 +343,7 @@ class Context:
             arr[i].fov = foveation(v["fov"])
             arr[i].rgb = _ptr(v["rgb"])
             arr[i].rgbam = _ptr(v.get("rgbam"))
+            arr[i].prev_rgb = _ptr(v.get("prev"))
         m = march_params(mp)
         ns = None if nsamples is None else _ptr(nsamples, torch.int64)
         self._chk(lib.fvn_render_batch(self.h, arr, int(n), ctypes.byref(m), int(precision), ns,

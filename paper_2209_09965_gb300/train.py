@@ -9,6 +9,17 @@ the image gradients (the paper's perceptual and temporal terms, Eq. 4-7,
 need VGG19 weights and optical flow that are not available).  Optimiser:
 Adam, lr 1e-3 with cosine decay to ``lr_final``.
 
+The recurrent network (``--recurrent``; paper: "Recurrence", the output of
+D passed back to its input in the next run) is trained on two-frame
+sequences -- the second frame's camera turned about the target by a small
+random angle, its focal point moved and its mask drawn for the next frame
+index -- with the first frame's output (no gradient) as the second's
+history input, and the loss of Eq. 4 with lambda_s = 0.8 on the spatial
+term above and lambda_t = 1.0 on the temporal term of Eq. 6 without its
+optical-flow part, L1 of (O_1 - O_0) - (Y_1 - Y_0).  It starts from plain
+weights (``--init``) with zero weights on the history channels, so its
+first step is the plain network.
+
 Every forward and backward step runs in the library's CUDA kernels, called
 through ``torch.autograd.Function`` shims; parameter gradients are written by
 the backward kernels straight into one flat gradient buffer on which the
@@ -21,6 +32,9 @@ The shipped weights were made with
         --out paper_2209_09965_gb300/weights/fvn_16_32_64.npy
     python -m paper_2209_09965_gb300.train --steps 8000 --direct-only \
         --out paper_2209_09965_gb300/weights/fvn_direct_only.npy
+    python -m paper_2209_09965_gb300.train --recurrent --steps 6000 --lr 3e-4 --lr-final 1e-5 \
+        --init paper_2209_09965_gb300/weights/fvn_16_32_64.npy --log-every 500 \
+        --out paper_2209_09965_gb300/weights/fvn_16_32_64_recurrent.npy
 """
 from __future__ import annotations
 
@@ -41,15 +55,16 @@ LAYERS = wl.NET_LAYERS
 class Params:
     """Flat FP32 master weights with per-layer views, flat gradient and Adam moments."""
 
-    def __init__(self, flat: np.ndarray, device):
+    def __init__(self, flat: np.ndarray, device, layers=LAYERS):
         self.p = torch.from_numpy(np.ascontiguousarray(flat, np.float32)).to(device).requires_grad_(True)
         self.g = torch.zeros_like(self.p, requires_grad=False)
         self.m = torch.zeros_like(self.g)
         self.v = torch.zeros_like(self.g)
         self.step = 0
+        self.recurrent = layers[0][1] == 8
         self.views = {}
         off = 0
-        for name, ci, co, k in LAYERS:
+        for name, ci, co, k in layers:
             nw = co * ci * k * k
             self.views[name] = (off, nw, (co, ci, k, k))
             off += nw + co
@@ -165,13 +180,20 @@ class _Loss(torch.autograd.Function):
         return (g if float(gl) == 1.0 else g * gl), None, None
 
 
-def forward(P: Params, sparse: torch.Tensor, direct_only: bool = False):
-    """Network forward on [N, 5, H, W] (H, W multiples of 4); returns [N, 3, H, W]."""
+def forward(P: Params, sparse: torch.Tensor, direct_only: bool = False, prev: torch.Tensor = None):
+    """Network forward on [N, 5, H, W] (H, W multiples of 4); returns [N, 3, H, W].
+    The recurrent network also takes prev, the previous output [N, 3, H, W]
+    (None: zeros), clamped to [0, 1]."""
 
     def cbr(name, xa, xb=None):
         return _Conv.apply(xa, xb, P.w(name), P.b(name), True, P.gw(name), P.gb(name))
 
-    e0 = cbr("enc0b", cbr("enc0a", sparse))
+    if P.recurrent:
+        n, _, h, w = sparse.shape
+        hist = torch.zeros(n, 3, h, w, device=sparse.device) if prev is None else prev.detach().clamp(0, 1)
+        e0 = cbr("enc0b", cbr("enc0a", sparse, hist.contiguous()))
+    else:
+        e0 = cbr("enc0b", cbr("enc0a", sparse))
     e1 = cbr("enc1b", cbr("enc1a", _Pool.apply(e0)))
     bt = cbr("botb", cbr("bota", _Pool.apply(e1)))
     d1 = cbr("dec1b", cbr("dec1a", _Up.apply(bt), e1))
@@ -214,49 +236,96 @@ class PairSource:
         yy, xx = torch.meshgrid(torch.arange(crop, device=device), torch.arange(crop, device=device), indexing="ij")
         self.local = (yy * frame_w + xx).reshape(-1).to(torch.int32)
 
-    def sample(self, batch):
+    def _render_crop(self, vol, tf, cam, mp, fov, x0, y0, xs, ys):
+        """Dense march of the crop's pixels (target) and the masked copy (input)."""
         c, W, H = self.crop, self.W, self.H
+        ids = self.local + (y0 * W + x0)
+        cnt = torch.tensor([ids.numel()], dtype=torch.int32, device=self.dev)
+        self.ctx.march(vol, tf, cam, mp, self.rgbam, ids=ids, count=cnt)
+        self.ctx.make_mask(fov, W, H, self.mask, self.ids_all, self.count)
+        win = self.rgbam[:, y0:y0 + c, x0:x0 + c]
+        m = self.mask[y0:y0 + c, x0:x0 + c].to(torch.float32)
+        ys.copy_(win[0:3])
+        xs[0:4] = win[0:4] * m
+        xs[4] = m
+
+    def _draw(self):
+        r, W, H, c = self.rng, self.W, self.H, self.crop
+        vol = self.vols[r.integers(len(self.vols))]
+        tf = torch.from_numpy(wl.transfer_function(int(r.integers(1 << 30)), alpha_max=r.uniform(0.03, 0.2)))
+        cam = wl.random_camera(r, W, H, rmin=0.8, rmax=1.8)
+        mp = wl.MarchParams(shading=int(r.uniform() < 0.85))
+        fov = wl.Foveation(focal_px=(r.uniform(0.0, W), r.uniform(0.0, H)), fovea_radius=r.uniform(0.05, 0.15),
+                           falloff_sigma=r.uniform(0.05, 0.15), p_base=r.uniform(0.03, 0.1),
+                           seed=int(r.integers(1 << 30)), frame=int(r.integers(1 << 20)))
+        # crop window: mostly around the screen centre where the volume is
+        x0 = int(np.clip(r.normal(W / 2, W / 5) - c / 2, 0, W - c))
+        y0 = int(np.clip(r.normal(H / 2, H / 5) - c / 2, 0, H - c))
+        return vol, tf.to(self.dev), cam, mp, fov, x0, y0
+
+    def sample(self, batch):
+        c = self.crop
         xs = torch.empty(batch, 5, c, c, device=self.dev)
         ys = torch.empty(batch, 3, c, c, device=self.dev)
         for b in range(batch):
-            r = self.rng
-            vol = self.vols[r.integers(len(self.vols))]
-            tf = torch.from_numpy(wl.transfer_function(int(r.integers(1 << 30)), alpha_max=r.uniform(0.03, 0.2)))
-            tf = tf.to(self.dev)
-            cam = wl.random_camera(r, W, H, rmin=0.8, rmax=1.8)
-            mp = wl.MarchParams(shading=int(r.uniform() < 0.85))
-            fx, fy = r.uniform(0.0, W), r.uniform(0.0, H)
-            fov = wl.Foveation(focal_px=(fx, fy), fovea_radius=r.uniform(0.05, 0.15),
-                               falloff_sigma=r.uniform(0.05, 0.15), p_base=r.uniform(0.03, 0.1),
-                               seed=int(r.integers(1 << 30)), frame=int(r.integers(1 << 20)))
-            # crop window: mostly around the screen centre where the volume is
-            x0 = int(np.clip(r.normal(W / 2, W / 5) - c / 2, 0, W - c))
-            y0 = int(np.clip(r.normal(H / 2, H / 5) - c / 2, 0, H - c))
-            ids = self.local + (y0 * W + x0)
-            cnt = torch.tensor([ids.numel()], dtype=torch.int32, device=self.dev)
-            self.ctx.march(vol, tf, cam, mp, self.rgbam, ids=ids, count=cnt)
-            self.ctx.make_mask(fov, W, H, self.mask, self.ids_all, self.count)
-            win = self.rgbam[:, y0:y0 + c, x0:x0 + c]
-            m = self.mask[y0:y0 + c, x0:x0 + c].to(torch.float32)
-            ys[b] = win[0:3]
-            xs[b, 0:4] = win[0:4] * m
-            xs[b, 4] = m
+            vol, tf, cam, mp, fov, x0, y0 = self._draw()
+            self._render_crop(vol, tf, cam, mp, fov, x0, y0, xs[b], ys[b])
+        return xs, ys
+
+    def sample_sequence(self, batch, max_angle_deg=6.0):
+        """Two consecutive frames per crop: the second camera turned about the
+        target around the up axis by U[0, max_angle] degrees, the focal point
+        moved by up to 2 % of the width, the mask drawn for the next frame."""
+        c, r = self.crop, self.rng
+        xs = torch.empty(2, batch, 5, c, c, device=self.dev)
+        ys = torch.empty(2, batch, 3, c, c, device=self.dev)
+        for b in range(batch):
+            vol, tf, cam, mp, fov, x0, y0 = self._draw()
+            self._render_crop(vol, tf, cam, mp, fov, x0, y0, xs[0, b], ys[0, b])
+            a = math.radians(r.uniform(0.0, max_angle_deg)) * (1 if r.uniform() < 0.5 else -1)
+            up = np.asarray(cam.up, np.float64) / np.linalg.norm(cam.up)
+            rel = np.asarray(cam.eye, np.float64) - np.asarray(cam.target, np.float64)
+            rel = (rel * math.cos(a) + np.cross(up, rel) * math.sin(a) + up * (up @ rel) * (1 - math.cos(a)))
+            cam1 = wl.Camera(eye=tuple(np.asarray(cam.target) + rel), target=cam.target, up=cam.up,
+                             fov_y_deg=cam.fov_y_deg, width=cam.width, height=cam.height)
+            d = 0.02 * self.W
+            fov1 = wl.Foveation(focal_px=(fov.focal_px[0] + r.uniform(-d, d), fov.focal_px[1] + r.uniform(-d, d)),
+                                fovea_radius=fov.fovea_radius, falloff_sigma=fov.falloff_sigma, p_base=fov.p_base,
+                                seed=fov.seed, frame=fov.frame + 1)
+            self._render_crop(vol, tf, cam1, mp, fov1, x0, y0, xs[1, b], ys[1, b])
         return xs, ys
 
 
+LAMBDA_S, LAMBDA_T = 0.8, 1.0   # Eq. 4 weights of the spatial and temporal terms
+
+
 def train(steps=3000, batch=8, lr=1e-3, seed=100, nvol=64, vol_n=512, out=None, direct_only=False,
-          init_seed=3, log_every=100, device=None, lr_final=1e-4):
+          init_seed=3, log_every=100, device=None, lr_final=1e-4, recurrent=False, init=None, max_angle_deg=6.0):
     device = device or torch.device("cuda")
     ctx = fvn.Context()
     src = PairSource(ctx, device, nvol=nvol, vol_n=vol_n, seed=seed)
-    P = Params(wl.net_weights(init_seed), device)
+    flat = np.load(init).astype(np.float32) if init else wl.net_weights(init_seed)
+    if recurrent:
+        if flat.size == wl.net_param_count():
+            flat = wl.recurrent_weights(flat)
+        P = Params(flat, device, wl.NET_LAYERS_RECURRENT)
+    else:
+        P = Params(flat, device)
     log = []
     t0 = time.time()
     for it in range(1, steps + 1):
-        x, y = src.sample(batch)
         P.g.zero_()
-        pred = forward(P, x, direct_only)
-        loss = _Loss.apply(pred, y, 1.0)
+        if recurrent:
+            x, y = src.sample_sequence(batch, max_angle_deg)
+            with torch.no_grad():
+                o0 = forward(P, x[0])
+            o1 = forward(P, x[1], prev=o0)
+            loss = LAMBDA_S * _Loss.apply(o1, y[1], 1.0) + \
+                LAMBDA_T * _Loss.apply(o1 - o0, (y[1] - y[0]).contiguous(), 0.0)
+        else:
+            x, y = src.sample(batch)
+            pred = forward(P, x, direct_only)
+            loss = _Loss.apply(pred, y, 1.0)
         loss.backward()
         # cosine decay from lr to lr_final over the run
         cur = lr_final + 0.5 * (lr - lr_final) * (1 + math.cos(math.pi * (it - 1) / max(1, steps - 1)))
@@ -284,10 +353,13 @@ def main():
     ap.add_argument("--lr-final", type=float, default=1e-4)
     ap.add_argument("--log-every", type=int, default=100)
     ap.add_argument("--direct-only", action="store_true")
+    ap.add_argument("--recurrent", action="store_true")
+    ap.add_argument("--init", default=None, help="start from these weights (.npy)")
+    ap.add_argument("--max-angle", type=float, default=6.0, help="recurrent: camera turn between frames, degrees")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
     train(a.steps, a.batch, a.lr, a.seed, a.nvol, a.vol_n, a.out, a.direct_only, log_every=a.log_every,
-          lr_final=a.lr_final)
+          lr_final=a.lr_final, recurrent=a.recurrent, init=a.init, max_angle_deg=a.max_angle)
 
 
 if __name__ == "__main__":

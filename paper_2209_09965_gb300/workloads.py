@@ -315,6 +315,24 @@ NET_LAYERS = (
 )
 
 
+# The recurrent network: enc0a also takes the previous output's RGB.
+NET_LAYERS_RECURRENT = (("enc0a", 8, 16, 3),) + NET_LAYERS[1:]
+
+
+def recurrent_weights(flat: np.ndarray, history_scale: float = 0.0, seed: int = 0) -> np.ndarray:
+    """Recurrent weights from plain ones: enc0a's weights for the three
+    history channels are appended (zeros by default, so the recurrent
+    network starts as the plain one; seeded uniform in +-history_scale
+    otherwise)."""
+    parts = split_weights(np.asarray(flat, np.float32))
+    w, b = parts["enc0a"]
+    rng = np.random.default_rng(seed)
+    extra = rng.uniform(-history_scale, history_scale, (w.shape[0], 3) + w.shape[2:]).astype(np.float32)
+    parts["enc0a"] = (np.concatenate([w, extra], axis=1), b)
+    return np.concatenate([np.concatenate([parts[n][0].ravel(), parts[n][1].ravel()])
+                           for n, _, _, _ in NET_LAYERS_RECURRENT]).astype(np.float32)
+
+
 def net_param_count(layers=NET_LAYERS) -> int:
     return sum(co * ci * k * k + co for _, ci, co, k in layers)
 
