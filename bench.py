@@ -46,6 +46,8 @@ def parse():
                    help="skip the global-shadows block (the paper's renderer setting)")
     p.add_argument("--no-multiview", action="store_true",
                    help="skip the batched 16-view measurement")
+    p.add_argument("--sweep-shadows", action="store_true",
+                   help="the compaction sweep with global shadows (the paper's renderer setting)")
     p.add_argument("--sweep", action="store_true",
                    help="compaction efficiency: march time vs uniform sample density, compaction vs naive "
                         "rejection vs the ideal C_max scaling of the dense march")
@@ -277,12 +279,13 @@ def run_profile_shadows():
     print("shadow profile case done")
 
 
-def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.02, 0.01)):
+def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.02, 0.01), shading=1):
     """Frame time of the march vs a uniform sampling density tau (fovea and
     falloff off, so C_max = tau): mask + compaction + sparse march, mask +
     naive rejection (full-frame kernel, masked pixels skipped in place), and
     the ideal tau x dense-march time, each with its launch shapes autotuned.
-    One JSON line per density."""
+    shading 2 runs the paper's renderer setting (global shadows).  One JSON
+    line per density."""
     import torch
     import __graft_entry__ as ge
     ge.build()
@@ -290,6 +293,8 @@ def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.
     from paper_2209_09965_gb300 import workloads as wl
     dev = torch.device("cuda")
     vol_np, tf_np, _, _, mp = wl.foveated_1080p_workload(seed=2, frame=0, n=VOL_N)
+    mp = wl.MarchParams(shading=shading)
+    grid = {} if shading != 2 else dict(refills=(1, 16), coops=(0, 4, 16, 32), blocks=(0,))
     ctx = fvn.Context()
     vol = torch.from_numpy(vol_np).to(dev)
     tf = torch.from_numpy(tf_np).to(dev)
@@ -312,7 +317,7 @@ def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.
     cams = [wl.orbit_camera(2, f * (ORBIT // nframes), nframes=ORBIT, width=W, height=H,
                             radius_factor=(0.85, 1.75)) for f in range(nframes)]
     from paper_2209_09965_gb300 import autotune
-    autotune.tune_march(ctx, vol, tf, cams[0], mp, out)      # dense and naive-rejection launch shapes
+    autotune.tune_march(ctx, vol, tf, cams[0], mp, out, **grid)      # dense and naive-rejection launch shapes
     for cam in cams[:2]:                                    # warm-up
         ctx.march(vol, tf, cam, mp, out)
     dense = sum(timed(lambda: ctx.march(vol, tf, cam, mp, out)) for cam in cams)
@@ -323,7 +328,7 @@ def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.
         fov0 = wl.Foveation(focal_px=(W / 2, H / 2), fovea_radius=0.0, falloff_sigma=0.0, p_base=tau, seed=2,
                             frame=0)
         ctx.make_mask(fov0, W, H, mask, ids, count)
-        autotune.tune_march(ctx, vol, tf, cams[0], mp, out, ids=ids, count=count)   # sparse launch shapes
+        autotune.tune_march(ctx, vol, tf, cams[0], mp, out, ids=ids, count=count, **grid)   # sparse launch shapes
         for i, cam in enumerate(cams):
             fov = wl.Foveation(focal_px=(W / 2, H / 2), fovea_radius=0.0, falloff_sigma=0.0, p_base=tau, seed=2,
                                frame=i)
@@ -332,7 +337,7 @@ def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.
             frac += int(count.item()) / (W * H)
             rej += timed(lambda: (ctx.make_mask(fov, W, H, mask, ids, count),
                                   ctx.march_masked(vol, tf, cam, mp, mask, out)))
-        row = {"tau": tau, "sampled_fraction": frac / nframes, "dense_ms": dense / nframes,
+        row = {"tau": tau, "shading": shading, "sampled_fraction": frac / nframes, "dense_ms": dense / nframes,
                "compaction_ms": comp / nframes, "rejection_ms": rej / nframes,
                "ideal_ms": dense / nframes * tau,
                "compaction_speedup": dense / comp, "rejection_speedup": dense / rej, "ideal_speedup": 1.0 / tau}
@@ -647,6 +652,8 @@ def main():
         return run_profile_shadows()
     if args.sweep:
         return run_sweep()
+    if args.sweep_shadows:
+        return run_sweep(shading=2)
     import numpy as np
     import torch
     rank, world, local = dist_env()

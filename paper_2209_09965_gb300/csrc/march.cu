@@ -921,21 +921,28 @@ __device__ __forceinline__ bool batch_step(const MarchBatchView& bv, const Light
     const float4* tf = s_tf + bv.tf_off;
     switch (bv.dtype) {
         case kGrad4:   // never with shading 2 (shadowed marches read the padded copy and the cells)
-            if constexpr (SHADE == 2) return true;
-            else return ray_step<Grad4Src, I, SHADE>(a, lt, static_cast<const float4*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
-                                                tfmax, s, nsh);
-        case FVN_U8:
-            return ray_step<ScalarSrc<uint8_t>, I, SHADE>(a, lt, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0,
-                                                          uy0, uz0, tfmax, s, nsh);
-        case FVN_U16:
-            return ray_step<ScalarSrc<uint16_t>, I, SHADE>(a, lt, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0,
-                                                           uy0, uz0, tfmax, s, nsh);
-        case FVN_F16:
-            return ray_step<ScalarSrc<__half>, I, SHADE>(a, lt, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0,
-                                                         uz0, tfmax, s, nsh);
-        default:
-            return ray_step<ScalarSrc<float>, I, SHADE>(a, lt, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0,
-                                                        uz0, tfmax, s, nsh);
+            if constexpr (SHADE == 2) {
+                return true;
+            } else {
+                const float4* v = static_cast<const float4*>(a.pvol);
+                return ray_step<Grad4Src, I, SHADE>(a, lt, v, tf, sy, sz, ux0, uy0, uz0, tfmax, s, nsh);
+            }
+        case FVN_U8: {
+            const uint8_t* v = static_cast<const uint8_t*>(a.pvol);
+            return ray_step<ScalarSrc<uint8_t>, I, SHADE>(a, lt, v, tf, sy, sz, ux0, uy0, uz0, tfmax, s, nsh);
+        }
+        case FVN_U16: {
+            const uint16_t* v = static_cast<const uint16_t*>(a.pvol);
+            return ray_step<ScalarSrc<uint16_t>, I, SHADE>(a, lt, v, tf, sy, sz, ux0, uy0, uz0, tfmax, s, nsh);
+        }
+        case FVN_F16: {
+            const __half* v = static_cast<const __half*>(a.pvol);
+            return ray_step<ScalarSrc<__half>, I, SHADE>(a, lt, v, tf, sy, sz, ux0, uy0, uz0, tfmax, s, nsh);
+        }
+        default: {
+            const float* v = static_cast<const float*>(a.pvol);
+            return ray_step<ScalarSrc<float>, I, SHADE>(a, lt, v, tf, sy, sz, ux0, uy0, uz0, tfmax, s, nsh);
+        }
     }
 }
 
@@ -949,24 +956,31 @@ __device__ __forceinline__ void batch_coop(const MarchBatchView& bv, const Light
     const float4* tf = s_tf + bv.tf_off;
     switch (bv.dtype) {
         case kGrad4:
-            if constexpr (SHADE != 2) coop_ray<Grad4Src, I, SHADE>(a, lt, static_cast<const float4*>(a.pvol), tf, sy, sz, ux0, uy0, uz0, tfmax, r, nsh);
+            if constexpr (SHADE != 2) {
+                const float4* v = static_cast<const float4*>(a.pvol);
+                coop_ray<Grad4Src, I, SHADE>(a, lt, v, tf, sy, sz, ux0, uy0, uz0, tfmax, r, nsh);
+            }
             break;
-        case FVN_U8:
-            coop_ray<ScalarSrc<uint8_t>, I, SHADE>(a, lt, static_cast<const uint8_t*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
-                                                   tfmax, r, nsh);
+        case FVN_U8: {
+            const uint8_t* v = static_cast<const uint8_t*>(a.pvol);
+            coop_ray<ScalarSrc<uint8_t>, I, SHADE>(a, lt, v, tf, sy, sz, ux0, uy0, uz0, tfmax, r, nsh);
             break;
-        case FVN_U16:
-            coop_ray<ScalarSrc<uint16_t>, I, SHADE>(a, lt, static_cast<const uint16_t*>(a.pvol), tf, sy, sz, ux0, uy0,
-                                                    uz0, tfmax, r, nsh);
+        }
+        case FVN_U16: {
+            const uint16_t* v = static_cast<const uint16_t*>(a.pvol);
+            coop_ray<ScalarSrc<uint16_t>, I, SHADE>(a, lt, v, tf, sy, sz, ux0, uy0, uz0, tfmax, r, nsh);
             break;
-        case FVN_F16:
-            coop_ray<ScalarSrc<__half>, I, SHADE>(a, lt, static_cast<const __half*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
-                                                  tfmax, r, nsh);
+        }
+        case FVN_F16: {
+            const __half* v = static_cast<const __half*>(a.pvol);
+            coop_ray<ScalarSrc<__half>, I, SHADE>(a, lt, v, tf, sy, sz, ux0, uy0, uz0, tfmax, r, nsh);
             break;
-        default:
-            coop_ray<ScalarSrc<float>, I, SHADE>(a, lt, static_cast<const float*>(a.pvol), tf, sy, sz, ux0, uy0, uz0,
-                                                 tfmax, r, nsh);
+        }
+        default: {
+            const float* v = static_cast<const float*>(a.pvol);
+            coop_ray<ScalarSrc<float>, I, SHADE>(a, lt, v, tf, sy, sz, ux0, uy0, uz0, tfmax, r, nsh);
             break;
+        }
     }
 }
 
