@@ -40,6 +40,8 @@ def parse():
     p.add_argument("--no-autotune", action="store_true")
     p.add_argument("--profile", action="store_true",
                    help="run two untimed frames (mask, sparse march, dense march, reconstruction) for ncu")
+    p.add_argument("--headline-only", action="store_true",
+                   help="only the headline measurement (no shadows, blue-noise, recurrent, batch or CPU blocks)")
     p.add_argument("--profile-shadows", action="store_true",
                    help="two untimed shadowed frames, for ncu")
     p.add_argument("--no-shadows", action="store_true",
@@ -712,6 +714,8 @@ def run_multiview(ctx, fvn, wl, dev, steps, warmup, flush):
 
 def main():
     args = parse()
+    if args.headline_only:
+        args.no_shadows = args.no_multiview = args.no_cpu_baseline = True
     if args.impl == "reference":
         return run_reference(args)
     if args.profile:
@@ -941,8 +945,10 @@ def main():
                               else "mma_sync", vol, tf, frames, dev, min(args.steps, 16), flush)
         paper_settings = run_paper_settings(fvn, wl, weights, vol, tf, dev, min(args.steps, 16), flush)
 
-    blue = run_blue_noise(ctx, wl, vol, tf, mp, frames, dev, min(args.steps, ORBIT), flush)
-    recurrent = run_recurrent(fvn, wl, weights, vol, tf, mp, dev, min(args.steps, 32), flush)
+    blue = recurrent = None
+    if not args.headline_only:
+        blue = run_blue_noise(ctx, wl, vol, tf, mp, frames, dev, min(args.steps, ORBIT), flush)
+        recurrent = run_recurrent(fvn, wl, weights, vol, tf, mp, dev, min(args.steps, 32), flush)
 
     multiview = None
     if not args.no_multiview:
