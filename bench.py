@@ -69,9 +69,7 @@ NET_FLOPS_PER_PX = 2 * 9 * (5 * 16 + 16 * 16 + 48 * 16 + 16 * 16) + 2 * 9 * (16 
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # DRAM bytes (read + write) of one sparse-march launch of this workload, from
 # an ncu capture of the current kernel (python bench.py --profile, second frame)
-MARCH_DRAM_BYTES = 236.48e6 + 18.86e6
-
-
+MARCH_DRAM_BYTES = 236.23e6 + 18.85e6
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
