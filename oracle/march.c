@@ -61,6 +61,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 enum { OR_U8 = 0, OR_U16 = 1, OR_F16 = 2, OR_F32 = 3 };
 
@@ -327,6 +330,15 @@ int64_t or_march(const void* data, int dtype, int nx, int ny, int nz, const floa
         if (amb) amb[pix] = (uint8_t)a;
     }
     return total;
+}
+
+/* Threads of the OpenMP loops (the CPU baseline also times one core). */
+void or_set_threads(int n) {
+#ifdef _OPENMP
+    omp_set_num_threads(n > 0 ? n : 1);
+#else
+    (void)n;
+#endif
 }
 
 /* Normalised trilinear value at voxel-space points p[n][3] (for tests). */

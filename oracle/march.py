@@ -48,6 +48,8 @@ def _load():
         lib.or_shadow.restype = None
         lib.or_shadow.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, P,
                                   ctypes.c_int64, P, ctypes.c_double, ctypes.c_int, P]
+        lib.or_set_threads.restype = None
+        lib.or_set_threads.argtypes = [ctypes.c_int]
         lib.or_ray.restype = None
         lib.or_ray.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                ctypes.c_int, ctypes.c_int, P, P]
@@ -126,3 +128,8 @@ def shadow(vol, tf, points, light_dir, step_vox=0.5, rate=4):
     _load().or_shadow(_ptr(vol), dt, nx, ny, nz, _ptr(tf), tf.shape[0], _ptr(p), p.shape[0], _ptr(L),
                       float(step_vox), int(rate), _ptr(out))
     return out
+
+
+def set_threads(n: int):
+    """Number of OpenMP threads of the marcher."""
+    _load().or_set_threads(int(n))
