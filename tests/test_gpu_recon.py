@@ -167,3 +167,28 @@ def test_render_adaptive_follows_oracle_rule(fvn):
     assert np.abs(rgb.cpu().numpy() - rgb_ref).max() < FP16_TOL
     c.device_status()
     c.close()
+
+
+
+def test_render_cuda_graph_replay(ctx):
+    """fvn_render captured in a CUDA graph replays to the result of the direct call."""
+    vol, tf, cam, fov, mp = wl.foveated_1080p_workload(seed=2, frame=3, n=64, width=320, height=180)
+    dev = torch.device("cuda")
+    v = torch.from_numpy(vol).to(dev)
+    t = torch.from_numpy(tf).to(dev)
+    rgb = torch.empty(3, 180, 320, device=dev)
+    sparse = torch.empty(5, 180, 320, device=dev)
+    ctx.render(v, t, cam, fov, mp, rgb, rgbam_out=sparse)          # sizes the workspaces
+    torch.cuda.synchronize()
+    ref, ref_sparse = rgb.clone(), sparse.clone()
+    side = torch.cuda.Stream()
+    side.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=side):
+        ctx.render(v, t, cam, fov, mp, rgb, rgbam_out=sparse)
+    rgb.fill_(-1.0)
+    sparse.fill_(-1.0)
+    g.replay()
+    g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(rgb, ref) and torch.equal(sparse, ref_sparse)
