@@ -217,3 +217,26 @@ def test_shadow_sample_counting_option(ctx, fvn):
     _, h0 = run_march(ctx, vol, tf, cam, wl.MarchParams(shading=1))
     assert n1 > n0 > 0                      # shadow-ray samples added on top of the primary ones
     assert h1 == h0                         # no shadow rays without shading 2
+
+
+def test_shadow_without_termination_and_empty_volume(ctx, fvn):
+    # a thin TF and term_alpha = 1: every ray and every shadow ray runs to the box's far side
+    vol, _, cam, _ = wl.dense_small_workload(seed=1)
+    tf = wl.transfer_function(5, alpha_max=0.02)
+    mp = shadow_params(4, term=1.0, bg=(0.1, 0.2, 0.3))
+    out, _ = run_march(ctx, vol, tf, cam, mp)
+    march_parity(vol, tf, cam, mp, out)
+    # an empty volume (TF opacity 0 at 0): the background everywhere, no shadow work
+    empty = np.zeros((16, 16, 16), np.float32)
+    tf0 = np.zeros((256, 4), np.float32)
+    tf0[:, :3] = 1.0
+    tf0[1:, 3] = 0.5
+    cam2 = wl.Camera(eye=(0.2, 0.3, 2.0), target=(0, 0, 0), up=(0, 1, 0), fov_y_deg=45.0, width=24, height=16)
+    ctx.set_option(fvn.OPT_MARCH_COUNT_SHADOW, 1)
+    try:
+        out, ns = run_march(ctx, empty, tf0, cam2, mp)
+    finally:
+        ctx.set_option(fvn.OPT_MARCH_COUNT_SHADOW, 0)
+    _, ns_primary = run_march(ctx, empty, tf0, cam2, mp)
+    assert np.all(out[0] == np.float32(0.1)) and np.all(out[2] == np.float32(0.3)) and np.all(out[3] == 0.0)
+    assert ns == ns_primary > 0          # samples, but no shadow-ray samples
