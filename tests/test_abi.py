@@ -34,6 +34,8 @@ def test_every_declared_symbol_is_exported(binding):
 def test_weight_count_matches_layer_table(binding):
     from paper_2209_09965_gb300 import workloads as wl
     assert binding.weight_count() == wl.net_param_count()
+    assert binding.weight_count_recurrent() == wl.net_param_count(wl.NET_LAYERS_RECURRENT)
+    assert wl.recurrent_weights(wl.net_weights(3)).size == binding.weight_count_recurrent()
 
 
 def test_null_context_is_an_argument_error(binding):
