@@ -6,8 +6,11 @@ anything under this directory.  The product path (the CUDA library and its
 Python binding) never does, and shares no code with it.
 
 Modules:
-  mask     -- Eq. 1-3: threshold table, hashed noise, sample mask, C_max, ids
-  march    -- FP64 emission-absorption ray marcher (C, OpenMP), dense / masked
-  net      -- FP64 U-Net forward / backward, kernel prediction + blend, loss, Adam
-  metrics  -- PSNR, SSIM
+  mask     -- Eq. 1-3: threshold table, hashed or tiled noise, sample mask, C_max, ids
+  march    -- FP64 emission-absorption ray marcher (C, OpenMP), dense / masked,
+              headlight Phong or global shadows
+  net      -- FP64 U-Net forward / backward (plain or with the previous output as
+              input), kernel prediction + blend, spatial and temporal losses, Adam
+  metrics  -- PSNR, SSIM, temporal PSNR
+  fallback -- probe set and the denser-mask rule
 """
