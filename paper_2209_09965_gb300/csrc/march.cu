@@ -98,6 +98,36 @@ __device__ __forceinline__ float load_norm<__half>(const __half* p) {
     return __saturatef(__half2float(__ldg(p)));
 }
 
+// The march's copies of the volume (padded copy, shadow-ray cells) hold
+// float and half voxels already clamped to [0, 1], so their loads skip the
+// clamp load_norm applies to the caller's volume (the same values).
+template <typename T>
+__device__ __forceinline__ T prenorm(T v) {
+    return v;
+}
+template <>
+__device__ __forceinline__ float prenorm<float>(float v) {
+    return __saturatef(v);
+}
+template <>
+__device__ __forceinline__ __half prenorm<__half>(__half v) {
+    return __float2half_rn(__saturatef(__half2float(v)));   // exact: a half in [0, 1] converts back unchanged
+}
+
+// Normalised value of a voxel of a copy written through prenorm.
+template <typename T>
+__device__ __forceinline__ float load_pre(const T* p) {
+    return load_norm(p);
+}
+template <>
+__device__ __forceinline__ float load_pre<float>(const float* p) {
+    return __ldg(p);
+}
+template <>
+__device__ __forceinline__ float load_pre<__half>(const __half* p) {
+    return __half2float(__ldg(p));
+}
+
 // Shadow-ray cells (shading 2): per padded voxel (x, y, z) the 2 x 2 block
 // (v(x, y), v(x + 1, y), v(x, y + 1), v(x + 1, y + 1)) at z, in the voxel type,
 // so the 8 voxels of a shadow sample are two vector loads (the cells at z
@@ -109,10 +139,10 @@ struct Quad<float> {
     using type = float4;
     __device__ static __forceinline__ type make(float a, float b, float c, float d) { return make_float4(a, b, c, d); }
     __device__ static __forceinline__ void norm(const type& q, float& a, float& b, float& c, float& d) {
-        a = __saturatef(q.x);
-        b = __saturatef(q.y);
-        c = __saturatef(q.z);
-        d = __saturatef(q.w);
+        a = q.x;   // clamped when the cells were written
+        b = q.y;
+        c = q.z;
+        d = q.w;
     }
 };
 template <>
@@ -149,12 +179,12 @@ struct Quad<__half> {
         return make_uint2(*reinterpret_cast<const unsigned*>(&lo), *reinterpret_cast<const unsigned*>(&hi));
     }
     __device__ static __forceinline__ void norm(const type& q, float& a, float& b, float& c, float& d) {
-        const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+        const float2 lo = __half22float2(*reinterpret_cast<const __half2*>(&q.x));   // clamped when written
         const float2 hi = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
-        a = __saturatef(lo.x);
-        b = __saturatef(lo.y);
-        c = __saturatef(hi.x);
-        d = __saturatef(hi.y);
+        a = lo.x;
+        b = lo.y;
+        c = hi.x;
+        d = hi.y;
     }
 };
 
@@ -302,11 +332,11 @@ __device__ __forceinline__ void stencil_fetch(const T* __restrict__ vol, I b0, I
 #pragma unroll
         for (int y = 0; y < 2; ++y) {
             const T* r = b + (I)z * sz + (I)y * sy;
-            S.c[z][y][0] = load_norm(r);
-            S.c[z][y][1] = load_norm(r + 1);
+            S.c[z][y][0] = load_pre(r);
+            S.c[z][y][1] = load_pre(r + 1);
             if (SHADE) {
-                S.xm[z][y] = load_norm(r - 1);
-                S.xp[z][y] = load_norm(r + 2);
+                S.xm[z][y] = load_pre(r - 1);
+                S.xp[z][y] = load_pre(r + 2);
             }
         }
     if (SHADE) {
@@ -314,15 +344,15 @@ __device__ __forceinline__ void stencil_fetch(const T* __restrict__ vol, I b0, I
         for (int z = 0; z < 2; ++z)
 #pragma unroll
             for (int x = 0; x < 2; ++x) {
-                S.ym[z][x] = load_norm(b + (I)z * sz - sy + x);
-                S.yp[z][x] = load_norm(b + (I)z * sz + 2 * sy + x);
+                S.ym[z][x] = load_pre(b + (I)z * sz - sy + x);
+                S.yp[z][x] = load_pre(b + (I)z * sz + 2 * sy + x);
             }
 #pragma unroll
         for (int y = 0; y < 2; ++y)
 #pragma unroll
             for (int x = 0; x < 2; ++x) {
-                S.zm[y][x] = load_norm(b - sz + (I)y * sy + x);
-                S.zp[y][x] = load_norm(b + 2 * sz + (I)y * sy + x);
+                S.zm[y][x] = load_pre(b - sz + (I)y * sy + x);
+                S.zp[y][x] = load_pre(b + 2 * sz + (I)y * sy + x);
             }
     }
 }
@@ -1086,7 +1116,7 @@ __global__ void __launch_bounds__(256) pad_volume_kernel(const T* __restrict__ s
     const T* s = src + ((long long)sz * ny + sy) * nx;
     T* d = dst + (long long)row * px;
 #pragma unroll 4
-    for (int x = threadIdx.x & 31; x < px; x += 32) d[x] = s[min(max(x - kPad, 0), nx - 1)];
+    for (int x = threadIdx.x & 31; x < px; x += 32) d[x] = prenorm(s[min(max(x - kPad, 0), nx - 1)]);
 }
 
 template <typename T>
@@ -1152,7 +1182,7 @@ __global__ void __launch_bounds__(256) cell_volume_kernel(const T* __restrict__ 
     typename Quad<T>::type* d = dst + (long long)row * px;
     for (int x = threadIdx.x & 31; x < px; x += 32) {
         const int x0 = clampi(x - kPad, nx), x1 = clampi(x + 1 - kPad, nx);
-        d[x] = Quad<T>::make(r0[x0], r0[x1], r1[x0], r1[x1]);
+        d[x] = Quad<T>::make(prenorm(r0[x0]), prenorm(r0[x1]), prenorm(r1[x0]), prenorm(r1[x1]));
     }
 }
 
