@@ -77,6 +77,21 @@ def dist_env():
     return rank, world, local
 
 
+def replica_throughput(local_ms, steps, world, device="cpu"):
+    """Whole-job frames/s of `world` independent replicas (the path has no
+    exchange step): every rank rendered `steps` frames in local_ms of timed
+    region; the job takes the slowest rank's time (max over ranks).
+    Returns (frames/s, job ms)."""
+    total = float(local_ms)
+    if world > 1:
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([total], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total = float(t.item())
+    return world * steps / (total / 1000.0), total
+
+
 class ClockSampler:
     """nvidia-smi SM clock / throttle sampling during the timed region."""
 
@@ -808,12 +823,7 @@ def main():
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = [a.elapsed_time(b) for a, b in step_ms]
-    total_ms = sum(ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * args.steps / (total_ms / 1000.0)
+    value, total_ms = replica_throughput(sum(ms), args.steps, world, dev)
 
     # ---- per-stage times, samples and quality on the same frames (untimed for value)
     fov_ms, dense_ms, mask_ms, march_ms, recon_ms = [], [], [], [], []
