@@ -166,6 +166,14 @@ fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value);
  * remaining work and left its outputs incomplete).  Clears the flag. */
 fvn_status fvn_device_status(fvn_ctx* ctx);
 
+/* Diagnostic of that failure path: launches one kernel that waits, with the
+ * same bounded mbarrier wait the tensor-core kernels use, on a barrier that
+ * nothing completes; after `limit` polls (1..2^20) it gives up and records
+ * the give-up in the context's error flag, so the next fvn_device_status
+ * returns FVN_ERR_TIMEOUT and clears it -- the context stays usable.  No
+ * other work is touched. */
+fvn_status fvn_selftest_wait_timeout(fvn_ctx* ctx, unsigned limit, void* stream);
+
 /* Last error message of this context (or of the calling thread when ctx is
  * NULL); never NULL, "" when there was none. */
 const char* fvn_last_error(const fvn_ctx* ctx);

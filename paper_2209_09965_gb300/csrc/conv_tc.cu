@@ -1067,3 +1067,30 @@ fvn_status calibrate_amax(fvn_ctx* ctx, const ReconPlan& B, int w, int h, float*
 }
 
 }  // namespace fvn
+
+namespace fvn {
+
+// The error path of every bounded tensor-core wait, on its own: an mbarrier
+// that nothing completes, polled `limit` times by one thread, which then
+// records the give-up in the context's error flag and returns.
+__global__ void selftest_wait_kernel(int* error, unsigned limit) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !tc::mbar_wait(&bar, 0, limit)) atomicExch(error, 2);
+}
+
+}  // namespace fvn
+
+using namespace fvn;
+
+extern "C" fvn_status fvn_selftest_wait_timeout(fvn_ctx* ctx, unsigned limit, void* stream) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    FVN_CHECK_ARG(ctx, limit >= 1 && limit <= (1u << 20), "limit %u outside [1, 2^20]", limit);
+    selftest_wait_kernel<<<1, 32, 0, as_stream(stream)>>>(ctx->d_error, limit);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}

@@ -31,7 +31,7 @@ EXPORTS = (
     "fvn_avgpool2_bwd", "fvn_upsample2_fwd", "fvn_upsample2_bwd", "fvn_kp_blend_fwd", "fvn_kp_blend_bwd",
     "fvn_loss_l1grad", "fvn_adam_step", "fvn_reconstruct_noalloc", "fvn_set_option", "fvn_device_status",
     "fvn_calibrate_fp8", "fvn_render_adaptive", "fvn_march_masked", "fvn_render_batch", "fvn_set_noise_tiles",
-    "fvn_weight_count_recurrent", "fvn_reconstruct_recurrent", "fvn_render_recurrent",
+    "fvn_weight_count_recurrent", "fvn_reconstruct_recurrent", "fvn_render_recurrent", "fvn_selftest_wait_timeout",
 )
 MAX_VIEWS = 16
 OPT_CONV_KERNEL, OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 1, 2, 3
@@ -102,6 +102,7 @@ def _load():
         "fvn_render": [P, P, P, P, P, P, I, P, P, P],
         "fvn_render_batch": [P, P, I, P, I, P, P],
         "fvn_set_noise_tiles": [P, P, I, I],
+        "fvn_selftest_wait_timeout": [P, ctypes.c_uint, P],
         "fvn_conv_fwd": [P, I, P, I, I, I, I, P, P, I, I, I, P, P],
         "fvn_conv_bwd": [P, I, P, I, I, I, I, P, I, I, P, P, P, P, P, P, P],
         "fvn_avgpool2_fwd": [P, I, I, I, P, P],
@@ -230,6 +231,10 @@ class Context:
 
     def set_option(self, option, value):
         self._chk(lib.fvn_set_option(self.h, int(option), int(value)))
+
+    def selftest_wait_timeout(self, limit=1000, stream=None):
+        """Run the bounded-wait failure path once (fvn_selftest_wait_timeout)."""
+        self._chk(lib.fvn_selftest_wait_timeout(self.h, int(limit), _stream(stream)))
 
     def device_status(self):
         """Synchronise; raise FvnError(FVN_ERR_TIMEOUT) if a kernel gave up a bounded wait."""
