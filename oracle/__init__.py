@@ -11,6 +11,8 @@ Modules:
               headlight Phong or global shadows
   net      -- FP64 U-Net forward / backward (plain or with the previous output as
               input), kernel prediction + blend, spatial and temporal losses, Adam
+  wnet     -- FP64 two-stage network: direct prediction D, kernel prediction K
+              applied to D's output at several scales in sequence; forward / backward
   metrics  -- PSNR, SSIM, temporal PSNR
   fallback -- probe set and the denser-mask rule
 """
