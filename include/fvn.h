@@ -466,6 +466,80 @@ fvn_status fvn_loss_l1grad(const float* pred, const float* target, int nc, int h
 fvn_status fvn_adam_step(float* p, const float* g, float* m, float* v, size_t n, int step, float lr,
                          float beta1, float beta2, float eps, void* stream);
 
+/* ------------------------------------------------------------------------
+ * Two-stage network (paper: "Reconstruction Network" -- a first U-Net D
+ * predicts a coarse image O_d directly and keeps its decoder's hidden states
+ * H_d; a second U-Net K predicts per-pixel filter kernels from H_d at several
+ * scales, in its encoder and its decoder blocks, and passes O_d through them
+ * in sequence; "Model Configuration": both follow the block plan
+ * e64-e64-e80-d96-d80-d64-d64, D's blocks hold two 3x3 convolutions with
+ * ReLU, K's blocks one 1x1 convolution).  Readings where the paper is
+ * silent: K's blocks take D's decoder state of their own scale (the
+ * encoder blocks also the pooled output of the block above, the decoder
+ * blocks the up-sampled output of the block below); each block's 1x1 heads
+ * give 9 logits of a 3x3 kernel (softmax over the taps inside the frame) and,
+ * in the decoder blocks, one blend logit z; the image is filtered by the
+ * encoder blocks (pooled between scales), by the coarsest block, then, going
+ * up, joined to the encoder image of each scale by
+ * X = J + sigmoid(z) up(Y - pool J) and filtered by that decoder block.
+ * FP32 throughout (CUDA cores), NCHW.
+ * ------------------------------------------------------------------------ */
+
+#define FVN_WNET_MAX_LEVELS 4
+
+/* Block widths: enc[s] / dec[s] of the encoder / decoder block at scale s
+ * (resolution 2^-s), 0 <= s < levels; bot of the block at scale `levels`.
+ * levels 1..4, widths 1..256.  The paper's plan: levels 3, enc {64, 64, 80},
+ * bot 96, dec {64, 64, 80}. */
+typedef struct {
+    int levels;
+    int enc[FVN_WNET_MAX_LEVELS];
+    int bot;
+    int dec[FVN_WNET_MAX_LEVELS];
+} fvn_wnet_config;
+
+/* Number of float weights of a configuration; 0 when it is invalid.  Order
+ * (each layer W[cout][cin][k][k] then b[cout]):
+ *   D: per scale s = 0..L-1 enc_s a (cin -> enc[s], 3x3; cin = 5 at s = 0,
+ *      else enc[s-1]), enc_s b (enc[s] -> enc[s]); bot a (enc[L-1] -> bot),
+ *      bot b; per s = L-1..0 dec_s a ((bot or dec[s+1]) + enc[s] -> dec[s],
+ *      input order [up-sampled, skip]), dec_s b; out (dec[0] -> 3, 1x1).
+ *   K (all 1x1): per s = 0..L-1 enc_s ([pooled K enc_(s-1) (s > 0), D dec_s]
+ *      -> enc[s]), enc_s taps (enc[s] -> 9); bot ([pooled K enc_(L-1), D bot]
+ *      -> bot), bot taps (bot -> 9); per s = L-1..0 dec_s ([up-sampled K
+ *      (bot or dec_(s+1)), D dec_s] -> dec[s]), dec_s taps (dec[s] -> 9),
+ *      dec_s blend (dec[s] -> 1). */
+size_t fvn_wnet_weight_count(const fvn_wnet_config* cfg);
+
+/* Install two-stage weights (host float array of fvn_wnet_weight_count(cfg)
+ * entries; copied, synchronises).  Independent of fvn_load_weights. */
+fvn_status fvn_load_wnet_weights(fvn_ctx* ctx, const fvn_wnet_config* cfg, const float* host_w, size_t n);
+
+/* The two-stage network on one sparse frame: rgbam device float [5][h][w]
+ * (as fvn_reconstruct) -> rgb device float [3][h][w].  The frame is padded
+ * with zeros at the bottom / right to a multiple of 2^levels and cropped
+ * back.  Uses a context workspace (reallocated, with a device
+ * synchronisation, when the frame size changes).  FVN_ERR_STATE without
+ * fvn_load_wnet_weights. */
+fvn_status fvn_reconstruct_wnet(fvn_ctx* ctx, const float* rgbam, int w, int h, float* rgb, void* stream);
+
+/* Training pieces of the two-stage network (FP32, NCHW, device pointers).
+ * fvn_filter3_fwd: out[n][c] (p) = sum_q w_q(p) img[n][c](p + q), c < 3,
+ * w = softmax of logits[n][0..8](p) over the taps q = (q/3 - 1, q%3 - 1)
+ * with p + q inside the h x w frame.  fvn_filter3_bwd: dL/dimg and
+ * dL/dlogits (overwritten) from dL/dout. */
+fvn_status fvn_filter3_fwd(const float* img, const float* logits, int n, int h, int w_, float* out, void* stream);
+fvn_status fvn_filter3_bwd(const float* img, const float* logits, int n, int h, int w_, const float* gout,
+                           float* gimg, float* glogits, void* stream);
+
+/* fvn_wnet_join_fwd: x = j + sigmoid(z) up(y - pool j), j / x [N][3][h][w],
+ * y [N][3][h/2][w/2], z [N][1][h][w]; h, w even.  fvn_wnet_join_bwd: dL/dj,
+ * dL/dy and dL/dz (overwritten) from dL/dx. */
+fvn_status fvn_wnet_join_fwd(const float* j, const float* y, const float* z, int n, int h, int w_, float* x,
+                             void* stream);
+fvn_status fvn_wnet_join_bwd(const float* j, const float* y, const float* z, int n, int h, int w_,
+                             const float* gx, float* gj, float* gy, float* gz, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -81,6 +81,18 @@ struct BatchWorkspace {
     size_t pad_bytes[kMaxBatchVolumes] = {};
 };
 
+// Two-stage network: configuration, FP32 weights on the device (the flat
+// layout of fvn_wnet_weight_count) and an activation workspace for one frame
+// size.
+struct WnetState {
+    fvn_wnet_config cfg{};
+    float* d_w = nullptr;
+    size_t n = 0;
+    void* ws = nullptr;
+    size_t ws_bytes = 0;
+    int ws_w = 0, ws_h = 0;           // padded frame the workspace was carved for
+};
+
 enum ConvImpl { CONV_TCGEN05 = 0, CONV_MMA_SYNC = 1 };
 
 // Activation tensors with an FP8 scale (per tensor, from calibration).
@@ -145,6 +157,7 @@ struct fvn_ctx {
     fvn::RenderWorkspace render_ws;
     fvn::ProbeWorkspace probe_ws;
     fvn::BatchWorkspace batch_ws;
+    fvn::WnetState wnet;
 };
 
 namespace fvn {

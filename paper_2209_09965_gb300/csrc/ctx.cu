@@ -132,6 +132,8 @@ extern "C" fvn_status fvn_destroy(fvn_ctx* ctx) {
     cudaFree(ctx->probe_ws.rgbam);
     cudaFree(ctx->probe_ws.acc);
     cudaFree(ctx->batch_ws.base);
+    cudaFree(ctx->wnet.d_w);
+    cudaFree(ctx->wnet.ws);
     for (void* p : ctx->batch_ws.pad) cudaFree(p);
     delete ctx;
     return FVN_OK;

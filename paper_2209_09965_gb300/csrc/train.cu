@@ -17,6 +17,7 @@
 #include <algorithm>
 
 #include "common.cuh"
+#include "resample.cuh"
 
 namespace fvn {
 
@@ -203,15 +204,6 @@ __global__ void avgpool2_bwd_kernel(const float* __restrict__ gy, long long nc, 
     }
 }
 
-// weight of coarse index i in fine sample o of the x2 bilinear up-sampling
-// (source (o + 0.5)/2 - 0.5 clamped at 0, upper neighbour clamped to n - 1)
-__device__ __forceinline__ void up_src(int o, int n, int& i0, int& i1, float& t) {
-    float s = fmaxf((o + 0.5f) * 0.5f - 0.5f, 0.f);
-    i0 = (int)s;
-    t = s - i0;
-    i1 = min(i0 + 1, n - 1);
-}
-
 __global__ void upsample2_fwd_kernel(const float* __restrict__ x, long long nc, int h, int w_, float* __restrict__ y) {
     const int H2 = 2 * h, W2 = 2 * w_;
     const long long total = nc * H2 * W2;
@@ -228,13 +220,6 @@ __global__ void upsample2_fwd_kernel(const float* __restrict__ x, long long nc, 
         const float bot = (1.f - tx) * p[y1 * w_ + x0] + tx * p[y1 * w_ + x1];
         y[i] = (1.f - ty) * top + ty * bot;
     }
-}
-
-__device__ __forceinline__ float up_weight(int o, int i, int n) {
-    int i0, i1;
-    float t;
-    up_src(o, n, i0, i1, t);
-    return (i0 == i ? 1.f - t : 0.f) + (i1 == i ? t : 0.f);
 }
 
 __global__ void upsample2_bwd_kernel(const float* __restrict__ gy, long long nc, int h, int w_, float* __restrict__ gx) {

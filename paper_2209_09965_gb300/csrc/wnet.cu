@@ -1,0 +1,553 @@
+// Two-stage reconstruction network (paper: "Reconstruction Network", Fig.
+// "network architecture", "Model Configuration"): a U-Net D of 3x3
+// convolutions predicts a coarse image O_d and keeps its decoder's states;
+// a U-Net K of 1x1 convolutions predicts, per block, a 3x3 kernel per pixel
+// (and, in its decoder blocks, a blend weight) and passes O_d through those
+// kernels in sequence: filtered by the encoder blocks with pooling between
+// scales, by the coarsest block, then joined to each scale's encoder image
+// (X = J + sigmoid(z) up(Y - pool J)) and filtered by the decoder blocks.
+//
+// FP32, NCHW.  The convolutions, pooling and up-sampling are the FP32
+// training kernels; this file adds the per-pixel filter, the join (forward
+// and backward) and the whole-frame forward pass behind
+// fvn_reconstruct_wnet.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <vector>
+
+#include "common.cuh"
+#include "resample.cuh"
+
+namespace fvn {
+namespace {
+
+constexpr int kTaps = 9;
+constexpr int kMaxWidth = 256;
+
+int sm_count() {
+    static int n = [] {
+        int dev = 0, v = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        return v > 0 ? v : 148;
+    }();
+    return n;
+}
+
+int grid_of(long long total) {
+    return (int)std::max(1LL, std::min((total + 255) / 256, 16LL * sm_count()));
+}
+
+__device__ __forceinline__ bool tap_inside(int q, int y, int x, int h, int w) {
+    const int yy = y + q / 3 - 1, xx = x + q % 3 - 1;
+    return yy >= 0 && yy < h && xx >= 0 && xx < w;
+}
+
+// Softmax of the 9 logits at pixel (y, x) over the taps inside the frame;
+// lg points at logit 0 of the pixel, logits are hw apart.
+__device__ __forceinline__ void tap_weights(const float* __restrict__ lg, long long hw, int h, int w, int y, int x,
+                                            float wq[kTaps]) {
+    float m = -INFINITY;
+#pragma unroll
+    for (int q = 0; q < kTaps; ++q) {
+        wq[q] = tap_inside(q, y, x, h, w) ? __ldg(lg + q * hw) : 0.f;
+        if (tap_inside(q, y, x, h, w)) m = fmaxf(m, wq[q]);
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int q = 0; q < kTaps; ++q) {
+        wq[q] = tap_inside(q, y, x, h, w) ? expf(wq[q] - m) : 0.f;
+        s += wq[q];
+    }
+    const float inv = 1.f / s;   // s >= 1: the largest in-frame term is exp(0)
+#pragma unroll
+    for (int q = 0; q < kTaps; ++q) wq[q] *= inv;
+}
+
+__global__ void filter3_fwd_kernel(const float* __restrict__ img, const float* __restrict__ logits, int n, int h,
+                                   int w, float* __restrict__ out) {
+    const long long hw = (long long)h * w, total = n * hw;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / hw, p = i - b * hw;
+        const int y = (int)(p / w), x = (int)(p - (long long)y * w);
+        float wq[kTaps];
+        tap_weights(logits + b * kTaps * hw + p, hw, h, w, y, x, wq);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float* im = img + (b * 3 + c) * hw + p;
+            float acc = 0.f;
+#pragma unroll
+            for (int q = 0; q < kTaps; ++q)
+                if (tap_inside(q, y, x, h, w)) acc = fmaf(wq[q], __ldg(im + (q / 3 - 1) * w + (q % 3 - 1)), acc);
+            out[(b * 3 + c) * hw + p] = acc;
+        }
+    }
+}
+
+// dL/dlogit_q(p) = w_q (sum_c g_c(p) (img_c(p + q) - out_c(p))), zero outside
+__global__ void filter3_bwd_logits_kernel(const float* __restrict__ img, const float* __restrict__ logits, int n,
+                                          int h, int w, const float* __restrict__ gout, float* __restrict__ glog) {
+    const long long hw = (long long)h * w, total = n * hw;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / hw, p = i - b * hw;
+        const int y = (int)(p / w), x = (int)(p - (long long)y * w);
+        float wq[kTaps], d[kTaps];
+        tap_weights(logits + b * kTaps * hw + p, hw, h, w, y, x, wq);
+#pragma unroll
+        for (int q = 0; q < kTaps; ++q) d[q] = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float* im = img + (b * 3 + c) * hw + p;
+            float v[kTaps], o = 0.f;
+#pragma unroll
+            for (int q = 0; q < kTaps; ++q) {
+                v[q] = tap_inside(q, y, x, h, w) ? __ldg(im + (q / 3 - 1) * w + (q % 3 - 1)) : 0.f;
+                o = fmaf(wq[q], v[q], o);
+            }
+            const float g = __ldg(gout + (b * 3 + c) * hw + p);
+#pragma unroll
+            for (int q = 0; q < kTaps; ++q) d[q] = fmaf(g, v[q] - o, d[q]);
+        }
+#pragma unroll
+        for (int q = 0; q < kTaps; ++q)
+            glog[(b * kTaps + q) * hw + p] = tap_inside(q, y, x, h, w) ? wq[q] * d[q] : 0.f;
+    }
+}
+
+// dL/dimg_c(r) = sum over taps q with p = r - q in the frame of w_q(p) g_c(p)
+__global__ void filter3_bwd_img_kernel(const float* __restrict__ logits, int n, int h, int w,
+                                       const float* __restrict__ gout, float* __restrict__ gimg) {
+    const long long hw = (long long)h * w, total = n * hw;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / hw, r = i - b * hw;
+        const int ry = (int)(r / w), rx = (int)(r - (long long)ry * w);
+        float acc[3] = {0.f, 0.f, 0.f};
+        for (int q = 0; q < kTaps; ++q) {
+            const int py = ry - (q / 3 - 1), px = rx - (q % 3 - 1);
+            if (py < 0 || py >= h || px < 0 || px >= w) continue;
+            const long long p = (long long)py * w + px;
+            float wq[kTaps];
+            tap_weights(logits + b * kTaps * hw + p, hw, h, w, py, px, wq);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) acc[c] = fmaf(wq[q], __ldg(gout + (b * 3 + c) * hw + p), acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) gimg[(b * 3 + c) * hw + r] = acc[c];
+    }
+}
+
+__device__ __forceinline__ float sigmoidf_(float z) { return 1.f / (1.f + expf(-z)); }
+
+// up(Y - pool J) at fine pixel (y, x) of channel plane jc / yc
+__device__ __forceinline__ float join_detail(const float* __restrict__ jc, const float* __restrict__ yc, int w,
+                                             int hc, int wc, int y, int x) {
+    int y0, y1, x0, x1;
+    float ty, tx;
+    up_src(y, hc, y0, y1, ty);
+    up_src(x, wc, x0, x1, tx);
+    auto d = [&](int cy, int cx) {
+        const float* q = jc + (long long)(2 * cy) * w + 2 * cx;
+        return __ldg(yc + (long long)cy * wc + cx) - 0.25f * (__ldg(q) + __ldg(q + 1) + __ldg(q + w) + __ldg(q + w + 1));
+    };
+    const float top = (1.f - tx) * d(y0, x0) + tx * d(y0, x1);
+    const float bot = (1.f - tx) * d(y1, x0) + tx * d(y1, x1);
+    return (1.f - ty) * top + ty * bot;
+}
+
+__global__ void join_fwd_kernel(const float* __restrict__ j, const float* __restrict__ yv,
+                                const float* __restrict__ z, int n, int h, int w, float* __restrict__ xo) {
+    const long long hw = (long long)h * w, total = n * hw;
+    const int hc = h / 2, wc = w / 2;
+    const long long hwc = (long long)hc * wc;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / hw, p = i - b * hw;
+        const int y = (int)(p / w), x = (int)(p - (long long)y * w);
+        const float a = sigmoidf_(__ldg(z + b * hw + p));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float* jc = j + (b * 3 + c) * hw;
+            const float u = join_detail(jc, yv + (b * 3 + c) * hwc, w, hc, wc, y, x);
+            xo[(b * 3 + c) * hw + p] = __ldg(jc + p) + a * u;
+        }
+    }
+}
+
+// dL/dY = up^T(sigmoid(z) gx) at every coarse pixel (the up-sampling's adjoint)
+__global__ void join_bwd_coarse_kernel(const float* __restrict__ z, const float* __restrict__ gx, int n, int h,
+                                       int w, float* __restrict__ gy) {
+    const int hc = h / 2, wc = w / 2;
+    const long long hw = (long long)h * w, hwc = (long long)hc * wc, total = n * 3 * hwc;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long bc = i / hwc, r = i - bc * hwc;
+        const long long b = bc / 3;
+        const int iy = (int)(r / wc), ix = (int)(r - (long long)iy * wc);
+        const float* g = gx + bc * hw;
+        const float* zb = z + b * hw;
+        float s = 0.f;
+        for (int oy = max(2 * iy - 1, 0); oy <= min(2 * iy + 2, h - 1); ++oy) {
+            const float wy = up_weight(oy, iy, hc);
+            if (wy == 0.f) continue;
+            for (int ox = max(2 * ix - 1, 0); ox <= min(2 * ix + 2, w - 1); ++ox) {
+                const float wx = up_weight(ox, ix, wc);
+                if (wx == 0.f) continue;
+                const long long o = (long long)oy * w + ox;
+                s += wy * wx * sigmoidf_(__ldg(zb + o)) * __ldg(g + o);
+            }
+        }
+        gy[i] = s;
+    }
+}
+
+// dL/dJ = gx - pool^T(dL/dY);  dL/dz = sigmoid'(z) sum_c gx_c up(Y - pool J)_c
+__global__ void join_bwd_fine_kernel(const float* __restrict__ j, const float* __restrict__ yv,
+                                     const float* __restrict__ z, int n, int h, int w, const float* __restrict__ gx,
+                                     const float* __restrict__ gy, float* __restrict__ gj, float* __restrict__ gz) {
+    const long long hw = (long long)h * w, total = n * hw;
+    const int hc = h / 2, wc = w / 2;
+    const long long hwc = (long long)hc * wc;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long b = i / hw, p = i - b * hw;
+        const int y = (int)(p / w), x = (int)(p - (long long)y * w);
+        const float a = sigmoidf_(__ldg(z + b * hw + p));
+        float sz = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const long long bc = b * 3 + c;
+            const float g = __ldg(gx + bc * hw + p);
+            const float u = join_detail(j + bc * hw, yv + bc * hwc, w, hc, wc, y, x);
+            sz = fmaf(g, u, sz);
+            gj[bc * hw + p] = g - 0.25f * __ldg(gy + bc * hwc + (long long)(y / 2) * wc + x / 2);
+        }
+        gz[b * hw + p] = sz * a * (1.f - a);
+    }
+}
+
+// dst[c][y][x] = src[c][y][x] inside src's sw x sh frame, 0 outside; dst is dw x dh
+__global__ void window_copy_kernel(const float* __restrict__ src, int sw, int sh, float* __restrict__ dst, int dw,
+                                   int dh, int nc) {
+    const long long dhw = (long long)dw * dh, total = nc * dhw;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long c = i / dhw, p = i - c * dhw;
+        const int y = (int)(p / dw), x = (int)(p - (long long)y * dw);
+        dst[i] = (y < sh && x < sw) ? __ldg(src + (c * sh + y) * (long long)sw + x) : 0.f;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// layer table (the flat weight order of fvn_wnet_weight_count)
+// ---------------------------------------------------------------------------
+struct WLayer {
+    int cin, cout, k;
+    size_t off;   // W[cout][cin][k][k] at off, bias after it
+};
+
+struct WTable {
+    int d_enc_a[FVN_WNET_MAX_LEVELS], d_enc_b[FVN_WNET_MAX_LEVELS], d_bot_a, d_bot_b;
+    int d_dec_a[FVN_WNET_MAX_LEVELS], d_dec_b[FVN_WNET_MAX_LEVELS], d_out;
+    int k_enc[FVN_WNET_MAX_LEVELS], k_enc_taps[FVN_WNET_MAX_LEVELS], k_bot, k_bot_taps;
+    int k_dec[FVN_WNET_MAX_LEVELS], k_dec_taps[FVN_WNET_MAX_LEVELS], k_dec_blend[FVN_WNET_MAX_LEVELS];
+    std::vector<WLayer> L;
+    size_t total = 0;
+
+    int add(int cin, int cout, int k) {
+        L.push_back({cin, cout, k, total});
+        total += (size_t)cout * cin * k * k + cout;
+        return (int)L.size() - 1;
+    }
+};
+
+bool config_ok(const fvn_wnet_config* c) {
+    if (!c || c->levels < 1 || c->levels > FVN_WNET_MAX_LEVELS) return false;
+    if (c->bot < 1 || c->bot > kMaxWidth) return false;
+    for (int s = 0; s < c->levels; ++s)
+        if (c->enc[s] < 1 || c->enc[s] > kMaxWidth || c->dec[s] < 1 || c->dec[s] > kMaxWidth) return false;
+    return true;
+}
+
+WTable make_table(const fvn_wnet_config& c) {
+    WTable t;
+    const int L = c.levels;
+    int ci = 5;
+    for (int s = 0; s < L; ++s) {
+        t.d_enc_a[s] = t.add(ci, c.enc[s], 3);
+        t.d_enc_b[s] = t.add(c.enc[s], c.enc[s], 3);
+        ci = c.enc[s];
+    }
+    t.d_bot_a = t.add(c.enc[L - 1], c.bot, 3);
+    t.d_bot_b = t.add(c.bot, c.bot, 3);
+    int prev = c.bot;
+    for (int s = L - 1; s >= 0; --s) {
+        t.d_dec_a[s] = t.add(prev + c.enc[s], c.dec[s], 3);
+        t.d_dec_b[s] = t.add(c.dec[s], c.dec[s], 3);
+        prev = c.dec[s];
+    }
+    t.d_out = t.add(c.dec[0], 3, 1);
+    for (int s = 0; s < L; ++s) {
+        t.k_enc[s] = t.add((s ? c.enc[s - 1] : 0) + c.dec[s], c.enc[s], 1);
+        t.k_enc_taps[s] = t.add(c.enc[s], kTaps, 1);
+    }
+    t.k_bot = t.add(c.enc[L - 1] + c.bot, c.bot, 1);
+    t.k_bot_taps = t.add(c.bot, kTaps, 1);
+    prev = c.bot;
+    for (int s = L - 1; s >= 0; --s) {
+        t.k_dec[s] = t.add(prev + c.dec[s], c.dec[s], 1);
+        t.k_dec_taps[s] = t.add(c.dec[s], kTaps, 1);
+        t.k_dec_blend[s] = t.add(c.dec[s], 1, 1);
+        prev = c.dec[s];
+    }
+    return t;
+}
+
+// ---------------------------------------------------------------------------
+// activation buffers of one frame (padded to a multiple of 2^levels)
+// ---------------------------------------------------------------------------
+struct WPlan {
+    float* x;                                        // [5] padded sparse frame
+    float *T[FVN_WNET_MAX_LEVELS], *E[FVN_WNET_MAX_LEVELS], *U[FVN_WNET_MAX_LEVELS];
+    float *UPD[FVN_WNET_MAX_LEVELS], *P[FVN_WNET_MAX_LEVELS + 1];
+    float *G[FVN_WNET_MAX_LEVELS], *PG[FVN_WNET_MAX_LEVELS + 1], *LE[FVN_WNET_MAX_LEVELS];
+    float *GD[FVN_WNET_MAX_LEVELS], *UPK[FVN_WNET_MAX_LEVELS], *LD[FVN_WNET_MAX_LEVELS], *ZD[FVN_WNET_MAX_LEVELS];
+    float *I[FVN_WNET_MAX_LEVELS + 1], *J[FVN_WNET_MAX_LEVELS], *X[FVN_WNET_MAX_LEVELS];
+    float *Y[FVN_WNET_MAX_LEVELS + 1];
+    float *TB, *B, *GB, *LB;
+};
+
+// Carve the buffers from base (nullptr: size only); returns the bytes used.
+size_t plan_wnet(const fvn_wnet_config& c, int Wp, int Hp, WPlan* pl, char* base) {
+    size_t off = 0;
+    auto take = [&](int ch, int s) -> float* {
+        const size_t bytes = ((size_t)ch * (size_t)(Hp >> s) * (size_t)(Wp >> s) * sizeof(float) + 255) & ~(size_t)255;
+        float* p = base ? reinterpret_cast<float*>(base + off) : nullptr;
+        off += bytes;
+        return p;
+    };
+    const int L = c.levels;
+    pl->x = take(5, 0);
+    for (int s = 0; s < L; ++s) {
+        const int up = s == L - 1 ? c.bot : c.dec[s + 1];
+        pl->T[s] = take(std::max(c.enc[s], c.dec[s]), s);
+        pl->E[s] = take(c.enc[s], s);
+        pl->U[s] = take(c.dec[s], s);
+        pl->UPD[s] = take(up, s);
+        pl->G[s] = take(c.enc[s], s);
+        pl->LE[s] = take(kTaps, s);
+        pl->GD[s] = take(c.dec[s], s);
+        pl->UPK[s] = take(up, s);
+        pl->LD[s] = take(kTaps, s);
+        pl->ZD[s] = take(1, s);
+        pl->I[s] = take(3, s);
+        pl->J[s] = take(3, s);
+        pl->X[s] = take(3, s);
+        pl->Y[s] = take(3, s);
+    }
+    for (int s = 1; s <= L; ++s) {
+        pl->P[s] = take(c.enc[s - 1], s);
+        pl->PG[s] = take(c.enc[s - 1], s);
+    }
+    pl->I[L] = take(3, L);
+    pl->Y[L] = take(3, L);
+    pl->TB = take(c.bot, L);
+    pl->B = take(c.bot, L);
+    pl->GB = take(c.bot, L);
+    pl->LB = take(kTaps, L);
+    return off;
+}
+
+}  // namespace
+}  // namespace fvn
+
+using namespace fvn;
+
+// error text of a context-free call, moved to the context
+#define WN(call)                                                                       \
+    do {                                                                               \
+        const fvn_status s_ = (call);                                                  \
+        if (s_ != FVN_OK) return set_error(ctx, s_, "%s", fvn_last_error(nullptr));    \
+    } while (0)
+
+extern "C" size_t fvn_wnet_weight_count(const fvn_wnet_config* cfg) {
+    return config_ok(cfg) ? make_table(*cfg).total : 0;
+}
+
+extern "C" fvn_status fvn_load_wnet_weights(fvn_ctx* ctx, const fvn_wnet_config* cfg, const float* host_w,
+                                            size_t n) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    FVN_CHECK_ARG(ctx, config_ok(cfg), "invalid two-stage configuration (levels 1..%d, widths 1..%d)",
+                  FVN_WNET_MAX_LEVELS, kMaxWidth);
+    FVN_CHECK_ARG(ctx, host_w != nullptr, "weights pointer is NULL");
+    const size_t want = make_table(*cfg).total;
+    FVN_CHECK_ARG(ctx, n == want, "weight vector has %zu entries, expected %zu", n, want);
+    for (size_t i = 0; i < n; ++i) FVN_CHECK_ARG(ctx, isfinite(host_w[i]), "weight %zu is not finite", i);
+    FVN_CUDA(ctx, cudaDeviceSynchronize());
+    WnetState& S = ctx->wnet;
+    if (S.n != n) {
+        cudaFree(S.d_w);
+        S.d_w = nullptr;
+        S.n = 0;
+        FVN_CUDA(ctx, cudaMalloc(&S.d_w, n * sizeof(float)));
+    }
+    FVN_CUDA(ctx, cudaMemcpy(S.d_w, host_w, n * sizeof(float), cudaMemcpyHostToDevice));
+    S.n = n;
+    if (memcmp(&S.cfg, cfg, sizeof(*cfg)) != 0) {   // buffers are planned for the widths
+        cudaFree(S.ws);
+        S.ws = nullptr;
+        S.ws_bytes = 0;
+        S.ws_w = S.ws_h = 0;
+    }
+    S.cfg = *cfg;
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_reconstruct_wnet(fvn_ctx* ctx, const float* rgbam, int w, int h, float* rgb,
+                                           void* stream) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    FVN_CHECK_ARG(ctx, rgbam && rgb, "null buffer");
+    FVN_CHECK_ARG(ctx, w >= 1 && h >= 1 && w <= kMaxSide && h <= kMaxSide, "bad frame size %d x %d", w, h);
+    WnetState& S = ctx->wnet;
+    if (!S.d_w) return set_error(ctx, FVN_ERR_STATE, "no two-stage weights (call fvn_load_wnet_weights first)");
+    const fvn_wnet_config& c = S.cfg;
+    const int L = c.levels, m = 1 << L;
+    const int Wp = (w + m - 1) / m * m, Hp = (h + m - 1) / m * m;
+    cudaStream_t st = as_stream(stream);
+    if (S.ws_w != Wp || S.ws_h != Hp) {
+        FVN_CUDA(ctx, cudaDeviceSynchronize());
+        cudaFree(S.ws);
+        S.ws = nullptr;
+        S.ws_w = S.ws_h = 0;
+        WPlan tmp;
+        const size_t bytes = plan_wnet(c, Wp, Hp, &tmp, nullptr);
+        FVN_CUDA(ctx, cudaMalloc(&S.ws, bytes));
+        S.ws_bytes = bytes;
+        S.ws_w = Wp;
+        S.ws_h = Hp;
+    }
+    WPlan B;
+    plan_wnet(c, Wp, Hp, &B, static_cast<char*>(S.ws));
+    const WTable t = make_table(c);
+    auto Wt = [&](int li) { return S.d_w + t.L[li].off; };
+    auto Bs = [&](int li) { return S.d_w + t.L[li].off + (size_t)t.L[li].cout * t.L[li].cin * t.L[li].k * t.L[li].k; };
+    auto conv = [&](const float* xa, int ca, const float* xb, int cb, int s, int li, int relu, float* y) {
+        return fvn_conv_fwd(xa, ca, xb, cb, 1, Hp >> s, Wp >> s, Wt(li), Bs(li), t.L[li].cout, t.L[li].k, relu, y,
+                            stream);
+    };
+    auto hs = [&](int s) { return Hp >> s; };
+    auto ws = [&](int s) { return Wp >> s; };
+
+    window_copy_kernel<<<grid_of(5LL * Wp * Hp), 256, 0, st>>>(rgbam, w, h, B.x, Wp, Hp, 5);
+    FVN_LAUNCH_CHECK(ctx);
+    // D: encoder, coarsest block, decoder, output layer
+    const float* in = B.x;
+    int cin = 5;
+    for (int s = 0; s < L; ++s) {
+        WN(conv(in, cin, nullptr, 0, s, t.d_enc_a[s], 1, B.T[s]));
+        WN(conv(B.T[s], c.enc[s], nullptr, 0, s, t.d_enc_b[s], 1, B.E[s]));
+        WN(fvn_avgpool2_fwd(B.E[s], c.enc[s], hs(s), ws(s), B.P[s + 1], stream));
+        in = B.P[s + 1];
+        cin = c.enc[s];
+    }
+    WN(conv(B.P[L], c.enc[L - 1], nullptr, 0, L, t.d_bot_a, 1, B.TB));
+    WN(conv(B.TB, c.bot, nullptr, 0, L, t.d_bot_b, 1, B.B));
+    const float* prev = B.B;
+    int pc = c.bot;
+    for (int s = L - 1; s >= 0; --s) {
+        WN(fvn_upsample2_fwd(prev, pc, hs(s + 1), ws(s + 1), B.UPD[s], stream));
+        WN(conv(B.UPD[s], pc, B.E[s], c.enc[s], s, t.d_dec_a[s], 1, B.T[s]));
+        WN(conv(B.T[s], c.dec[s], nullptr, 0, s, t.d_dec_b[s], 1, B.U[s]));
+        prev = B.U[s];
+        pc = c.dec[s];
+    }
+    WN(conv(B.U[0], c.dec[0], nullptr, 0, 0, t.d_out, 0, B.I[0]));
+    // K: encoder blocks, coarsest block, decoder blocks (features and heads)
+    for (int s = 0; s < L; ++s) {
+        if (s == 0) {
+            WN(conv(B.U[0], c.dec[0], nullptr, 0, 0, t.k_enc[0], 1, B.G[0]));
+        } else {
+            WN(fvn_avgpool2_fwd(B.G[s - 1], c.enc[s - 1], hs(s - 1), ws(s - 1), B.PG[s], stream));
+            WN(conv(B.PG[s], c.enc[s - 1], B.U[s], c.dec[s], s, t.k_enc[s], 1, B.G[s]));
+        }
+        WN(conv(B.G[s], c.enc[s], nullptr, 0, s, t.k_enc_taps[s], 0, B.LE[s]));
+    }
+    WN(fvn_avgpool2_fwd(B.G[L - 1], c.enc[L - 1], hs(L - 1), ws(L - 1), B.PG[L], stream));
+    WN(conv(B.PG[L], c.enc[L - 1], B.B, c.bot, L, t.k_bot, 1, B.GB));
+    WN(conv(B.GB, c.bot, nullptr, 0, L, t.k_bot_taps, 0, B.LB));
+    prev = B.GB;
+    pc = c.bot;
+    for (int s = L - 1; s >= 0; --s) {
+        WN(fvn_upsample2_fwd(prev, pc, hs(s + 1), ws(s + 1), B.UPK[s], stream));
+        WN(conv(B.UPK[s], pc, B.U[s], c.dec[s], s, t.k_dec[s], 1, B.GD[s]));
+        WN(conv(B.GD[s], c.dec[s], nullptr, 0, s, t.k_dec_taps[s], 0, B.LD[s]));
+        WN(conv(B.GD[s], c.dec[s], nullptr, 0, s, t.k_dec_blend[s], 0, B.ZD[s]));
+        prev = B.GD[s];
+        pc = c.dec[s];
+    }
+    // image path: O_d through the encoder kernels, the coarsest, then the
+    // decoder joins and kernels
+    for (int s = 0; s < L; ++s) {
+        WN(fvn_filter3_fwd(B.I[s], B.LE[s], 1, hs(s), ws(s), B.J[s], stream));
+        WN(fvn_avgpool2_fwd(B.J[s], 3, hs(s), ws(s), B.I[s + 1], stream));
+    }
+    WN(fvn_filter3_fwd(B.I[L], B.LB, 1, hs(L), ws(L), B.Y[L], stream));
+    for (int s = L - 1; s >= 0; --s) {
+        WN(fvn_wnet_join_fwd(B.J[s], B.Y[s + 1], B.ZD[s], 1, hs(s), ws(s), B.X[s], stream));
+        WN(fvn_filter3_fwd(B.X[s], B.LD[s], 1, hs(s), ws(s), B.Y[s], stream));
+    }
+    window_copy_kernel<<<grid_of(3LL * w * h), 256, 0, st>>>(B.Y[0], Wp, Hp, rgb, w, h, 3);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_filter3_fwd(const float* img, const float* logits, int n, int h, int w_, float* out,
+                                      void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, img && logits && out && n >= 1 && h >= 1 && w_ >= 1, "bad filter arguments");
+    filter3_fwd_kernel<<<grid_of((long long)n * h * w_), 256, 0, as_stream(stream)>>>(img, logits, n, h, w_, out);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_filter3_bwd(const float* img, const float* logits, int n, int h, int w_,
+                                      const float* gout, float* gimg, float* glogits, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, img && logits && gout && gimg && glogits && n >= 1 && h >= 1 && w_ >= 1,
+                  "bad filter arguments");
+    const int g = grid_of((long long)n * h * w_);
+    filter3_bwd_logits_kernel<<<g, 256, 0, as_stream(stream)>>>(img, logits, n, h, w_, gout, glogits);
+    FVN_LAUNCH_CHECK(ctx);
+    filter3_bwd_img_kernel<<<g, 256, 0, as_stream(stream)>>>(logits, n, h, w_, gout, gimg);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_wnet_join_fwd(const float* j, const float* y, const float* z, int n, int h, int w_,
+                                        float* x, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, j && y && z && x && n >= 1 && h >= 2 && w_ >= 2 && h % 2 == 0 && w_ % 2 == 0,
+                  "bad join arguments");
+    join_fwd_kernel<<<grid_of((long long)n * h * w_), 256, 0, as_stream(stream)>>>(j, y, z, n, h, w_, x);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_wnet_join_bwd(const float* j, const float* y, const float* z, int n, int h, int w_,
+                                        const float* gx, float* gj, float* gy, float* gz, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, j && y && z && gx && gj && gy && gz && n >= 1 && h >= 2 && w_ >= 2 && h % 2 == 0 &&
+                           w_ % 2 == 0,
+                  "bad join arguments");
+    join_bwd_coarse_kernel<<<grid_of((long long)n * 3 * (h / 2) * (w_ / 2)), 256, 0, as_stream(stream)>>>(
+        z, gx, n, h, w_, gy);
+    FVN_LAUNCH_CHECK(ctx);
+    join_bwd_fine_kernel<<<grid_of((long long)n * h * w_), 256, 0, as_stream(stream)>>>(j, y, z, n, h, w_, gx, gy,
+                                                                                        gj, gz);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}

@@ -32,7 +32,10 @@ EXPORTS = (
     "fvn_loss_l1grad", "fvn_adam_step", "fvn_reconstruct_noalloc", "fvn_set_option", "fvn_device_status",
     "fvn_calibrate_fp8", "fvn_render_adaptive", "fvn_march_masked", "fvn_render_batch", "fvn_set_noise_tiles",
     "fvn_weight_count_recurrent", "fvn_reconstruct_recurrent", "fvn_render_recurrent", "fvn_selftest_wait_timeout",
+    "fvn_wnet_weight_count", "fvn_load_wnet_weights", "fvn_reconstruct_wnet", "fvn_filter3_fwd", "fvn_filter3_bwd",
+    "fvn_wnet_join_fwd", "fvn_wnet_join_bwd",
 )
+WNET_MAX_LEVELS = 4
 MAX_VIEWS = 16
 OPT_CONV_KERNEL, OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 1, 2, 3
 OPT_MARCH_REFILL_DENSE, OPT_MARCH_BLOCKS_PER_SM_DENSE = 4, 5
@@ -71,6 +74,23 @@ class FoveationC(ctypes.Structure):
 class MarchParamsC(ctypes.Structure):
     _fields_ = [("step_vox", ctypes.c_float), ("term_alpha", ctypes.c_float), ("bg", ctypes.c_float * 3),
                 ("shading", ctypes.c_int), ("light_dir", ctypes.c_float * 3), ("shadow_rate", ctypes.c_int)]
+
+
+class WnetConfigC(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("enc", ctypes.c_int * WNET_MAX_LEVELS), ("bot", ctypes.c_int),
+                ("dec", ctypes.c_int * WNET_MAX_LEVELS)]
+
+
+def wnet_config(cfg) -> WnetConfigC:
+    """(enc widths, bottom width, dec widths), dec indexed by scale like enc."""
+    enc, bot, dec = cfg
+    c = WnetConfigC()
+    c.levels = len(enc)
+    for s in range(len(enc)):
+        c.enc[s] = int(enc[s])
+        c.dec[s] = int(dec[s])
+    c.bot = int(bot)
+    return c
 
 
 class ViewC(ctypes.Structure):
@@ -113,6 +133,12 @@ def _load():
         "fvn_kp_blend_bwd": [P, P, P, I, I, I, P, P],
         "fvn_loss_l1grad": [P, P, I, I, I, F, P, P, P],
         "fvn_adam_step": [P, P, P, P, ctypes.c_size_t, I, F, F, F, F, P],
+        "fvn_load_wnet_weights": [P, P, P, ctypes.c_size_t],
+        "fvn_reconstruct_wnet": [P, P, I, I, P, P],
+        "fvn_filter3_fwd": [P, P, I, I, I, P, P],
+        "fvn_filter3_bwd": [P, P, I, I, I, P, P, P, P],
+        "fvn_wnet_join_fwd": [P, P, P, I, I, I, P, P],
+        "fvn_wnet_join_bwd": [P, P, P, I, I, I, P, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -124,6 +150,8 @@ def _load():
     lib.fvn_weight_count.restype = ctypes.c_size_t
     lib.fvn_weight_count_recurrent.argtypes = []
     lib.fvn_weight_count_recurrent.restype = ctypes.c_size_t
+    lib.fvn_wnet_weight_count.argtypes = [P]
+    lib.fvn_wnet_weight_count.restype = ctypes.c_size_t
     return lib
 
 
@@ -280,6 +308,15 @@ class Context:
         a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
         self._chk(lib.fvn_load_weights(self.h, a.ctypes.data_as(ctypes.c_void_p), a.size))
 
+    def load_wnet_weights(self, cfg, flat):
+        """Two-stage network weights for widths cfg = (enc, bot, dec)."""
+        a = np.ascontiguousarray(np.asarray(flat, dtype=np.float32))
+        c = wnet_config(cfg)
+        self._chk(lib.fvn_load_wnet_weights(self.h, ctypes.byref(c), a.ctypes.data_as(ctypes.c_void_p), a.size))
+
+    def reconstruct_wnet(self, rgbam, w, h, rgb, stream=None):
+        self._chk(lib.fvn_reconstruct_wnet(self.h, _ptr(rgbam), int(w), int(h), _ptr(rgb), _stream(stream)))
+
     def reconstruct(self, rgbam, w, h, rgb, precision=PREC_FP16, stream=None, prev=None):
         """prev: the previous output [3, h, w] for the recurrent network (fvn_reconstruct_recurrent)."""
         if prev is None:
@@ -406,6 +443,33 @@ def loss_l1grad(pred, target, lam, loss, gpred, stream=None):
     n, c, h, w = pred.shape
     _check(lib.fvn_loss_l1grad(_ptr(pred), _ptr(target), n * c, h, w, float(lam), _ptr(loss), _ptr(gpred),
                                _stream(stream)))
+
+
+def wnet_weight_count(cfg) -> int:
+    c = wnet_config(cfg)
+    return int(lib.fvn_wnet_weight_count(ctypes.byref(c)))
+
+
+def filter3_fwd(img, logits, out, stream=None):
+    n, _, h, w = img.shape
+    _check(lib.fvn_filter3_fwd(_ptr(img), _ptr(logits), n, h, w, _ptr(out), _stream(stream)))
+
+
+def filter3_bwd(img, logits, gout, gimg, glogits, stream=None):
+    n, _, h, w = img.shape
+    _check(lib.fvn_filter3_bwd(_ptr(img), _ptr(logits), n, h, w, _ptr(gout), _ptr(gimg), _ptr(glogits),
+                               _stream(stream)))
+
+
+def wnet_join_fwd(j, y, z, x, stream=None):
+    n, _, h, w = j.shape
+    _check(lib.fvn_wnet_join_fwd(_ptr(j), _ptr(y), _ptr(z), n, h, w, _ptr(x), _stream(stream)))
+
+
+def wnet_join_bwd(j, y, z, gx, gj, gy, gz, stream=None):
+    n, _, h, w = j.shape
+    _check(lib.fvn_wnet_join_bwd(_ptr(j), _ptr(y), _ptr(z), n, h, w, _ptr(gx), _ptr(gj), _ptr(gy), _ptr(gz),
+                                 _stream(stream)))
 
 
 def adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):

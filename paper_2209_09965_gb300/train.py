@@ -165,6 +165,38 @@ class _KP(torch.autograd.Function):
         return gh, None
 
 
+class _Filter3(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, img, logits):
+        out = torch.empty_like(img)
+        fvn.filter3_fwd(img, logits, out)
+        ctx.save_for_backward(img, logits)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        img, logits = ctx.saved_tensors
+        gimg, glog = torch.empty_like(img), torch.empty_like(logits)
+        fvn.filter3_bwd(img, logits, gout.contiguous(), gimg, glog)
+        return gimg, glog
+
+
+class _Join(torch.autograd.Function):
+    @staticmethod
+    def forward(ctx, j, y, z):
+        x = torch.empty_like(j)
+        fvn.wnet_join_fwd(j, y, z, x)
+        ctx.save_for_backward(j, y, z)
+        return x
+
+    @staticmethod
+    def backward(ctx, gx):
+        j, y, z = ctx.saved_tensors
+        gj, gy, gz = torch.empty_like(j), torch.empty_like(y), torch.empty_like(z)
+        fvn.wnet_join_bwd(j, y, z, gx.contiguous(), gj, gy, gz)
+        return gj, gy, gz
+
+
 class _Loss(torch.autograd.Function):
     @staticmethod
     def forward(ctx, pred, target, lam):
@@ -202,6 +234,49 @@ def forward(P: Params, sparse: torch.Tensor, direct_only: bool = False, prev: to
     if direct_only:
         return head[:, 0:3].contiguous()
     return _KP.apply(head, sparse)
+
+
+def wnet_forward(P: Params, sparse: torch.Tensor, cfg):
+    """The two-stage network (fvn_reconstruct_wnet's layer sequence) on
+    [N, 5, H, W], H and W multiples of 2^levels: D's direct prediction O_d and
+    decoder states, K's per-block kernels and blend logits, then O_d through
+    K's kernels in order.  Returns [N, 3, H, W]."""
+    enc, _, _ = cfg
+    n_lv = len(enc)
+
+    def conv(name, xa, xb=None, relu=True):
+        return _Conv.apply(xa, xb, P.w(name), P.b(name), relu, P.gw(name), P.gb(name))
+
+    e, t = [], sparse
+    for s in range(n_lv):
+        e.append(conv(f"d_enc{s}b", conv(f"d_enc{s}a", t)))
+        t = _Pool.apply(e[s])
+    bt = conv("d_botb", conv("d_bota", t))
+    u, below = [None] * n_lv, bt
+    for s in reversed(range(n_lv)):
+        u[s] = conv(f"d_dec{s}b", conv(f"d_dec{s}a", _Up.apply(below), e[s]))
+        below = u[s]
+    o_d = conv("d_out", u[0], relu=False)
+    g, taps_e = [], []
+    for s in range(n_lv):
+        g.append(conv("k_enc0", u[0]) if s == 0 else conv(f"k_enc{s}", _Pool.apply(g[s - 1]), u[s]))
+        taps_e.append(conv(f"k_enc{s}_taps", g[s], relu=False))
+    gb = conv("k_bot", _Pool.apply(g[-1]), bt)
+    taps_b = conv("k_bot_taps", gb, relu=False)
+    taps_d, blend_d, below = [None] * n_lv, [None] * n_lv, gb
+    for s in reversed(range(n_lv)):
+        gd = conv(f"k_dec{s}", _Up.apply(below), u[s])
+        taps_d[s] = conv(f"k_dec{s}_taps", gd, relu=False)
+        blend_d[s] = conv(f"k_dec{s}_blend", gd, relu=False)
+        below = gd
+    j, img = [], o_d
+    for s in range(n_lv):
+        j.append(_Filter3.apply(img, taps_e[s]))
+        img = _Pool.apply(j[s])
+    y = _Filter3.apply(img, taps_b)
+    for s in reversed(range(n_lv)):
+        y = _Filter3.apply(_Join.apply(j[s], y, blend_d[s]), taps_d[s])
+    return y
 
 
 # ---------------------------------------------------------------------------
@@ -300,12 +375,19 @@ LAMBDA_S, LAMBDA_T = 0.8, 1.0   # Eq. 4 weights of the spatial and temporal term
 
 
 def train(steps=3000, batch=8, lr=1e-3, seed=100, nvol=64, vol_n=512, out=None, direct_only=False,
-          init_seed=3, log_every=100, device=None, lr_final=1e-4, recurrent=False, init=None, max_angle_deg=6.0):
+          init_seed=3, log_every=100, device=None, lr_final=1e-4, recurrent=False, init=None, max_angle_deg=6.0,
+          wnet=None):
+    """wnet: widths (enc, bot, dec) to train the two-stage network instead."""
     device = device or torch.device("cuda")
     ctx = fvn.Context()
     src = PairSource(ctx, device, nvol=nvol, vol_n=vol_n, seed=seed)
-    flat = np.load(init).astype(np.float32) if init else wl.net_weights(init_seed)
-    if recurrent:
+    if wnet is not None:
+        flat = np.load(init).astype(np.float32) if init else wl.wnet_weights(wnet, init_seed)
+    else:
+        flat = np.load(init).astype(np.float32) if init else wl.net_weights(init_seed)
+    if wnet is not None:
+        P = Params(flat, device, wl.wnet_layers(wnet))
+    elif recurrent:
         if flat.size == wl.net_param_count():
             flat = wl.recurrent_weights(flat)
         P = Params(flat, device, wl.NET_LAYERS_RECURRENT)
@@ -324,7 +406,7 @@ def train(steps=3000, batch=8, lr=1e-3, seed=100, nvol=64, vol_n=512, out=None, 
                 LAMBDA_T * _Loss.apply(o1 - o0, (y[1] - y[0]).contiguous(), 0.0)
         else:
             x, y = src.sample(batch)
-            pred = forward(P, x, direct_only)
+            pred = wnet_forward(P, x, wnet) if wnet is not None else forward(P, x, direct_only)
             loss = _Loss.apply(pred, y, 1.0)
         loss.backward()
         # cosine decay from lr to lr_final over the run
@@ -356,10 +438,13 @@ def main():
     ap.add_argument("--recurrent", action="store_true")
     ap.add_argument("--init", default=None, help="start from these weights (.npy)")
     ap.add_argument("--max-angle", type=float, default=6.0, help="recurrent: camera turn between frames, degrees")
+    ap.add_argument("--wnet", choices=("slim", "paper"), default=None,
+                    help="train the two-stage network with the single network's widths or the paper's")
     ap.add_argument("--out", default=None)
     a = ap.parse_args()
+    cfg = {"slim": wl.WNET_SLIM, "paper": wl.WNET_PAPER}.get(a.wnet)
     train(a.steps, a.batch, a.lr, a.seed, a.nvol, a.vol_n, a.out, a.direct_only, log_every=a.log_every,
-          lr_final=a.lr_final, recurrent=a.recurrent, init=a.init, max_angle_deg=a.max_angle)
+          lr_final=a.lr_final, recurrent=a.recurrent, init=a.init, max_angle_deg=a.max_angle, wnet=cfg)
 
 
 if __name__ == "__main__":

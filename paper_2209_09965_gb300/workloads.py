@@ -333,6 +333,53 @@ def recurrent_weights(flat: np.ndarray, history_scale: float = 0.0, seed: int = 
                            for n, _, _, _ in NET_LAYERS_RECURRENT]).astype(np.float32)
 
 
+# The two-stage network (direct prediction D, then kernel prediction K on D's
+# output): block widths (encoder per scale, coarsest block, decoder per
+# scale), and its layers in the flat weight order of fvn_wnet_weight_count.
+WNET_PAPER = ((64, 64, 80), 96, (64, 64, 80))   # the paper's e64-e64-e80-d96-d80-d64-d64
+WNET_SLIM = ((16, 32), 64, (16, 32))            # the single network's widths
+
+
+def wnet_layers(cfg) -> tuple:
+    enc, bot, dec = cfg
+    n = len(enc)
+    d_enc = []
+    for s in range(n):
+        d_enc += [(f"d_enc{s}a", 5 if s == 0 else enc[s - 1], enc[s], 3), (f"d_enc{s}b", enc[s], enc[s], 3)]
+    d_dec = []
+    for s in range(n - 1, -1, -1):
+        below = bot if s == n - 1 else dec[s + 1]
+        d_dec += [(f"d_dec{s}a", below + enc[s], dec[s], 3), (f"d_dec{s}b", dec[s], dec[s], 3)]
+    k_enc = []
+    for s in range(n):
+        k_enc += [(f"k_enc{s}", dec[s] + (enc[s - 1] if s > 0 else 0), enc[s], 1), (f"k_enc{s}_taps", enc[s], 9, 1)]
+    k_dec = []
+    for s in range(n - 1, -1, -1):
+        below = bot if s == n - 1 else dec[s + 1]
+        k_dec += [(f"k_dec{s}", below + dec[s], dec[s], 1), (f"k_dec{s}_taps", dec[s], 9, 1),
+                  (f"k_dec{s}_blend", dec[s], 1, 1)]
+    return tuple(d_enc + [("d_bota", enc[-1], bot, 3), ("d_botb", bot, bot, 3)] + d_dec + [("d_out", dec[0], 3, 1)]
+                 + k_enc + [("k_bot", enc[-1] + bot, bot, 1), ("k_bot_taps", bot, 9, 1)] + k_dec)
+
+
+def wnet_weights(cfg, seed: int = 3) -> np.ndarray:
+    """Seeded initial weights of the two-stage network: Kaiming-uniform for
+    the convolutions, small weights on the tap and blend heads, tap biases
+    that favour the centre tap (every kernel starts close to the identity,
+    so the first output is close to D's), zero other biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for name, ci, co, k in wnet_layers(cfg):
+        bound = math.sqrt(6.0 / (ci * k * k))
+        head = name.endswith("_taps") or name.endswith("_blend")
+        parts.append(rng.uniform(-bound, bound, co * ci * k * k) * (0.1 if head else 1.0))
+        b = np.zeros(co)
+        if name.endswith("_taps"):
+            b[4] = 3.0
+        parts.append(b)
+    return np.concatenate(parts).astype(np.float32)
+
+
 def net_param_count(layers=NET_LAYERS) -> int:
     return sum(co * ci * k * k + co for _, ci, co, k in layers)
 

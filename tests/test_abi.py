@@ -60,3 +60,27 @@ def test_training_entry_points_validate_before_launch(binding):
     assert lib.fvn_adam_step(None, None, None, None, 0, 1, ctypes.c_float(1e-3), ctypes.c_float(0.9),
                              ctypes.c_float(0.999), ctypes.c_float(1e-8), None) == -1
     assert b"bad" in lib.fvn_last_error(None) or b"null" in lib.fvn_last_error(None)
+
+
+def test_two_stage_weight_count_and_argument_checks(binding):
+    from oracle import wnet as W
+    from paper_2209_09965_gb300 import workloads as wl
+    for cfg in (wl.WNET_PAPER, wl.WNET_SLIM, ((3, 5), 6, (4, 5)), ((8,), 4, (6,)), ((4, 5, 6, 7), 9, (3, 4, 5, 6))):
+        assert binding.wnet_weight_count(cfg) == W.param_count(cfg) == wl.net_param_count(wl.wnet_layers(cfg))
+    assert binding.wnet_weight_count(wl.WNET_PAPER) == 862741
+    for bad in (((), 4, ()), ((4,) * 5, 4, (4,) * 5), ((0, 4), 4, (4, 4)), ((4, 4), 257, (4, 4))):
+        c = binding.WnetConfigC()
+        c.levels = len(bad[0])
+        for s in range(min(len(bad[0]), 4)):
+            c.enc[s], c.dec[s] = bad[0][s], bad[2][s]
+        c.bot = bad[1]
+        assert binding.lib.fvn_wnet_weight_count(ctypes.byref(c)) == 0
+    lib = binding.lib
+    assert lib.fvn_load_wnet_weights(None, None, None, 0) == -1
+    assert lib.fvn_reconstruct_wnet(None, None, 4, 4, None, None) == -1
+    assert lib.fvn_filter3_fwd(None, None, 1, 4, 4, None, None) == -1
+    assert lib.fvn_filter3_bwd(None, None, 1, 4, 4, None, None, None, None) == -1
+    assert lib.fvn_wnet_join_fwd(None, None, None, 1, 4, 4, None, None) == -1
+    p = ctypes.c_void_p(16)   # never dereferenced: the odd size is rejected first
+    assert lib.fvn_wnet_join_fwd(p, p, p, 1, 5, 4, p, None) == -1
+    assert lib.fvn_wnet_join_bwd(p, p, p, 1, 4, 3, p, p, p, p, None) == -1
