@@ -50,6 +50,8 @@ def parse():
                    help="skip the batched 16-view measurement")
     p.add_argument("--sweep-shadows", action="store_true",
                    help="the compaction sweep with global shadows (the paper's renderer setting)")
+    p.add_argument("--two-stage-only", action="store_true",
+                   help="only the two-stage network comparison (prints its JSON)")
     p.add_argument("--sweep", action="store_true",
                    help="compaction efficiency: march time vs uniform sample density, compaction vs naive "
                         "rejection vs the ideal C_max scaling of the dense march")
@@ -643,6 +645,110 @@ def run_recurrent(fvn, wl, weights, vol, tf, mp, dev, nframes, flush):
         rec.close()
 
 
+WDIR = os.path.join(ROOT, "paper_2209_09965_gb300", "weights")
+# equal-budget ablation of the reconstruction (same data stream, steps and
+# schedule): the single network (one 5x5 kernel on the sparse samples), its
+# direct prediction alone, and the two-stage network (kernels on D's output)
+# with the single network's widths and with the paper's
+ABLATION = {"single_kp_on_sparse": "fvn_16_32_64_4k.npy", "direct_only": "fvn_direct_only_4k.npy",
+            "two_stage_slim": "fvn_wnet_slim_4k.npy", "two_stage_paper": "fvn_wnet_paper_4k.npy"}
+
+
+def wnet_flops_per_px(wl, cfg):
+    """Algorithmic FLOPs per full-resolution pixel of the two-stage pass:
+    2 cin cout k^2 per convolution at its scale (4^-s of the pixels), and
+    3 x 9 multiply-adds per filtered pixel."""
+    n_lv = len(cfg[0])
+    scale = {}
+    for s in range(n_lv):
+        for pre in (f"d_enc{s}", f"d_dec{s}", f"k_enc{s}", f"k_dec{s}"):
+            scale[pre] = s
+    f = 0.0
+    for name, ci, co, k in wl.wnet_layers(cfg):
+        s = n_lv if name.startswith(("d_bot", "k_bot")) else 0 if name == "d_out" else scale[name[:6]]
+        f += 2.0 * ci * co * k * k / 4 ** s
+    filt = sum(2 * 4 ** -s for s in range(n_lv)) + 4 ** -n_lv
+    return f + filt * 3 * 9 * 2
+
+
+def run_two_stage(fvn, wl, weights, vol, tf, mp, dev, nframes, flush):
+    """The paper's two-stage reconstruction (D's direct prediction, then K's
+    kernels applied to it at several scales) against the single network with
+    one kernel on the sparse samples, on the headline frames: PSNR / SSIM
+    against the dense render for the equal-budget ablation and the shipped
+    single network, and the time of fvn_reconstruct_wnet at 1080p."""
+    import numpy as np
+    import torch
+    paths = {k: os.path.join(WDIR, v) for k, v in ABLATION.items()}
+    if not all(os.path.exists(p) for p in paths.values()):
+        return None
+    cfgs = {"two_stage_slim": wl.WNET_SLIM, "two_stage_paper": wl.WNET_PAPER}
+    ctxs = {}
+    try:
+        for key, path in paths.items():
+            c = fvn.Context()
+            ctxs[key] = c
+            wts = np.load(path).astype(np.float32)
+            if key in cfgs:
+                c.load_wnet_weights(cfgs[key], wts)
+            else:
+                if key == "direct_only":   # the blend forced to the direct prediction
+                    parts = wl.split_weights(wts)
+                    parts["head"][0][28] = 0.0
+                    parts["head"][1][28] = -1e4
+                c.load_weights(wts)
+        ctxs["single_kp_on_sparse_shipped"] = fvn.Context()
+        ctxs["single_kp_on_sparse_shipped"].load_weights(weights)
+        sp = torch.empty(5, H, W, device=dev)
+        dense = torch.empty(5, H, W, device=dev)
+        rgb = torch.empty(3, H, W, device=dev)
+        base = ctxs["single_kp_on_sparse_shipped"]
+        stream = torch.cuda.current_stream()
+        scores = {k: ([], []) for k in ctxs}
+        ms = {k: [] for k in cfgs}
+        for i in range(nframes):
+            cam = wl.orbit_camera(2, i, nframes=ORBIT, width=W, height=H, radius_factor=(0.85, 1.75))
+            fov = wl.Foveation(focal_px=wl.focal_point(2, i, W, H), seed=2, frame=i)
+            base.march(vol, tf, cam, mp, dense)
+            base.render(vol, tf, cam, fov, mp, rgb, rgbam_out=sp)
+            for key, c in ctxs.items():
+                flush.fill_(float(i))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                if key in cfgs:
+                    c.reconstruct_wnet(sp, W, H, rgb)
+                else:
+                    c.reconstruct(sp, W, H, rgb)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if key in cfgs and i >= 1:
+                    ms[key].append(e0.elapsed_time(e1))
+                scores[key][0].append(psnr_t(rgb, dense[:3]))
+                scores[key][1].append(ssim_t(rgb, dense[:3]))
+        for c in ctxs.values():
+            c.device_status()
+        out = {"workload": f"the headline frames ({nframes} orbit frames, 1920x1080, hash mask P_b=0.05); each "
+                           "model trained for 4000 steps on the same data stream and schedule, plus the "
+                           "shipped single network (30000 steps)",
+               "psnr_vs_dense_db": {k: float(np.mean(v[0])) for k, v in scores.items()},
+               "ssim_vs_dense": {k: float(np.mean(v[1])) for k, v in scores.items()}}
+        timing = {}
+        for key, cfg in cfgs.items():
+            t = float(np.mean(ms[key])) if ms[key] else float("nan")
+            fl = wnet_flops_per_px(wl, cfg)
+            timing[key] = {"ms_per_1080p_frame": t, "flops_per_px": fl,
+                           "achieved_tflops": fl * W * H / (t / 1000.0) / 1e12,
+                           "peak_tflops": FP32_PEAK_TFLOPS, "bound": "alu",
+                           "note": "FP32 CUDA-core convolutions (the training kernels)"}
+        out["reconstruct"] = timing
+        return out
+    except Exception as exc:   # reported, not part of the metric
+        return {"error": str(exc)[:200]}
+    finally:
+        for c in ctxs.values():
+            c.close()
+
+
 def run_multiview(ctx, fvn, wl, dev, steps, warmup, flush):
     """Batched multi-view frames: 16 views (4 stereo pairs at 2064x2208, 4 at
     1280x720, 4 at 3840x2160) over a 512^3 float16 noise volume and a 1024^3
@@ -763,6 +869,12 @@ def main():
     from paper_2209_09965_gb300 import workloads as wl
 
     weights, wkind = load_weights()
+    if args.two_stage_only:
+        vol_np, tf_np, _, _, mp = wl.foveated_1080p_workload(seed=2, frame=0, n=VOL_N)
+        flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
+        print(json.dumps(run_two_stage(fvn, wl, weights, torch.from_numpy(vol_np).to(dev),
+                                       torch.from_numpy(tf_np).to(dev), mp, dev, 16, flush)))
+        return
     ctx = fvn.Context()
     ctx.load_weights(weights)
     vol_np, tf_np, _, _, mp = wl.foveated_1080p_workload(seed=2, frame=0, n=VOL_N)
@@ -963,10 +1075,11 @@ def main():
                               else "mma_sync", vol, tf, frames, dev, min(args.steps, 16), flush)
         paper_settings = run_paper_settings(fvn, wl, weights, vol, tf, dev, min(args.steps, 16), flush)
 
-    blue = recurrent = None
+    blue = recurrent = two_stage = None
     if not args.headline_only:
         blue = run_blue_noise(ctx, wl, vol, tf, mp, frames, dev, min(args.steps, ORBIT), flush)
         recurrent = run_recurrent(fvn, wl, weights, vol, tf, mp, dev, min(args.steps, 32), flush)
+        two_stage = run_two_stage(fvn, wl, weights, vol, tf, mp, dev, min(args.steps, 8), flush)
 
     multiview = None
     if not args.no_multiview:
@@ -1026,6 +1139,7 @@ def main():
             "paper_settings": paper_settings,
             "blue_noise_mask": blue,
             "recurrent": recurrent,
+            "two_stage": two_stage,
             "multiview": multiview,
             "clocks": clocks,
         }

@@ -85,8 +85,8 @@ def wnet_config(cfg) -> WnetConfigC:
     """(enc widths, bottom width, dec widths), dec indexed by scale like enc."""
     enc, bot, dec = cfg
     c = WnetConfigC()
-    c.levels = len(enc)
-    for s in range(len(enc)):
+    c.levels = len(enc)     # more than WNET_MAX_LEVELS: the library rejects it
+    for s in range(min(len(enc), WNET_MAX_LEVELS)):
         c.enc[s] = int(enc[s])
         c.dec[s] = int(dec[s])
     c.bot = int(bot)

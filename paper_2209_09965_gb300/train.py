@@ -20,6 +20,11 @@ optical-flow part, L1 of (O_1 - O_0) - (Y_1 - Y_0).  It starts from plain
 weights (``--init``) with zero weights on the history channels, so its
 first step is the plain network.
 
+The two-stage network (``--wnet slim|paper``; paper: "Reconstruction
+Network", D's direct prediction refined by K's kernels at several scales)
+trains with the same loss on the same pairs; its initial kernels are close
+to the identity, so it starts from D's output.
+
 Every forward and backward step runs in the library's CUDA kernels, called
 through ``torch.autograd.Function`` shims; parameter gradients are written by
 the backward kernels straight into one flat gradient buffer on which the
@@ -35,6 +40,16 @@ The shipped weights were made with
     python -m paper_2209_09965_gb300.train --recurrent --steps 6000 --lr 3e-4 --lr-final 1e-5 \
         --init paper_2209_09965_gb300/weights/fvn_16_32_64.npy --log-every 500 \
         --out paper_2209_09965_gb300/weights/fvn_16_32_64_recurrent.npy
+
+and the equal-budget ablation of the reconstruction with
+
+    python -m paper_2209_09965_gb300.train --steps 4000 --direct-only \
+        --out paper_2209_09965_gb300/weights/fvn_direct_only_4k.npy
+    python -m paper_2209_09965_gb300.train --steps 4000 --out paper_2209_09965_gb300/weights/fvn_16_32_64_4k.npy
+    python -m paper_2209_09965_gb300.train --steps 4000 --wnet slim \
+        --out paper_2209_09965_gb300/weights/fvn_wnet_slim_4k.npy
+    python -m paper_2209_09965_gb300.train --steps 4000 --wnet paper \
+        --out paper_2209_09965_gb300/weights/fvn_wnet_paper_4k.npy
 """
 from __future__ import annotations
 
