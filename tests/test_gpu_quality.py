@@ -104,3 +104,48 @@ def test_trained_network_beats_baselines(fvn):
     assert mean["trained"] > mean["direct_only"]
     assert mean["trained"] > mean["untrained"] + 10
     assert mean["trained"] >= 35.0
+
+
+def test_two_stage_beats_kernels_on_the_sparse_samples(fvn):
+    """The paper's argument for its second stage ("Kernel Prediction": kernels
+    applied to the sparse frame itself left blotches, applied to D's coarse
+    reconstruction they refine it): at an equal training budget and the same
+    widths, the two-stage network beats the single network whose one kernel
+    filters the sparse samples, and the paper's widths beat the slim ones."""
+    files = {k: os.path.join(WDIR, v) for k, v in (
+        ("single", "fvn_16_32_64_4k.npy"), ("slim", "fvn_wnet_slim_4k.npy"), ("paper", "fvn_wnet_paper_4k.npy"))}
+    if not all(os.path.exists(p) for p in files.values()):
+        pytest.skip("ablation weights not present")
+    W, H = 1920, 1080
+    vol_np, tf_np, _, _, mp = wl.foveated_1080p_workload(seed=7, frame=0)
+    dev = torch.device("cuda")
+    vol = torch.from_numpy(vol_np).to(dev)
+    tf = torch.from_numpy(tf_np).to(dev)
+    ctx = {k: fvn.Context() for k in files}
+    try:
+        ctx["single"].load_weights(np.load(files["single"]).astype(np.float32))
+        ctx["slim"].load_wnet_weights(wl.WNET_SLIM, np.load(files["slim"]).astype(np.float32))
+        ctx["paper"].load_wnet_weights(wl.WNET_PAPER, np.load(files["paper"]).astype(np.float32))
+        scores = {k: [] for k in files}
+        dense = torch.empty(5, H, W, device=dev)
+        sp = torch.empty(5, H, W, device=dev)
+        out = torch.empty(3, H, W, device=dev)
+        for f in (0, 16, 40):
+            cam = wl.orbit_camera(7, f, width=W, height=H, radius_factor=(0.85, 1.75))
+            fov = wl.Foveation(focal_px=wl.focal_point(7, f, W, H), seed=7, frame=f)
+            ctx["single"].march(vol, tf, cam, mp, dense)
+            ctx["single"].render(vol, tf, cam, fov, mp, out, rgbam_out=sp)
+            for k, c in ctx.items():
+                if k == "single":
+                    c.reconstruct(sp, W, H, out)
+                else:
+                    c.reconstruct_wnet(sp, W, H, out)
+                torch.cuda.synchronize()
+                scores[k].append(psnr(out, dense[0:3]))
+        mean = {k: float(np.mean(v)) for k, v in scores.items()}
+        print("PSNR dB", mean)
+        assert mean["slim"] > mean["single"] + 1.0
+        assert mean["paper"] > mean["slim"]
+    finally:
+        for c in ctx.values():
+            c.close()
