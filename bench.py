@@ -50,6 +50,8 @@ def parse():
                    help="skip the batched 16-view measurement")
     p.add_argument("--sweep-shadows", action="store_true",
                    help="the compaction sweep with global shadows (the paper's renderer setting)")
+    p.add_argument("--profile-two-stage", action="store_true",
+                   help="two untimed two-stage passes at 1080p (paper widths), for ncu")
     p.add_argument("--two-stage-only", action="store_true",
                    help="only the two-stage network comparison (prints its JSON)")
     p.add_argument("--sweep", action="store_true",
@@ -304,6 +306,37 @@ def run_profile_shadows():
         ctx.render(vol, tf, cam, fov, mp, rgb)
     ctx.device_status()
     print("shadow profile case done")
+
+
+def run_profile_two_stage():
+    """Two untimed passes of the two-stage network with the paper's widths
+    (the trained equal-budget weights when present) over the sparse 1080p
+    headline frame of orbit frame 16, for an ncu capture."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2209_09965_gb300 import fvn
+    from paper_2209_09965_gb300 import workloads as wl
+    dev = torch.device("cuda")
+    weights, _ = load_weights()
+    vol_np, tf_np, _, _, mp = wl.foveated_1080p_workload(seed=2, frame=0, n=VOL_N)
+    ctx = fvn.Context()
+    ctx.load_weights(weights)
+    path = os.path.join(WDIR, ABLATION["two_stage_paper"])
+    wts = np.load(path).astype(np.float32) if os.path.exists(path) else wl.wnet_weights(wl.WNET_PAPER, 3)
+    ctx.load_wnet_weights(wl.WNET_PAPER, wts)
+    vol = torch.from_numpy(vol_np).to(dev)
+    tf = torch.from_numpy(tf_np).to(dev)
+    rgb = torch.empty(3, H, W, device=dev)
+    sp = torch.empty(5, H, W, device=dev)
+    cam = wl.orbit_camera(2, 16, nframes=ORBIT, width=W, height=H, radius_factor=(0.85, 1.75))
+    fov = wl.Foveation(focal_px=wl.focal_point(2, 16, W, H), seed=2, frame=16)
+    ctx.render(vol, tf, cam, fov, mp, rgb, rgbam_out=sp)
+    for _ in range(2):
+        ctx.reconstruct_wnet(sp, W, H, rgb)
+    ctx.device_status()
+    print("two-stage profile case done")
 
 
 def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.02, 0.01), shading=1):
@@ -851,6 +884,8 @@ def main():
         return run_profile_case()
     if args.profile_shadows:
         return run_profile_shadows()
+    if args.profile_two_stage:
+        return run_profile_two_stage()
     if args.sweep:
         return run_sweep()
     if args.sweep_shadows:

@@ -28,84 +28,125 @@ constexpr int CO_T = 16;        // output channels per CTA
 // FWD:  W(co, ci, tap) = w[co][ci][tap], x = xa ++ xb, epilogue bias / ReLU.
 // DGRAD: x = gy masked by (y_relu > 0), W(co', ci', tap) = w[ci'][co'][flip(tap)],
 //        output split into gxa / gxb.
+// A CTA computes a TH x TW pixel tile for CO_T output channels; each thread
+// four consecutive pixels of one row for all CO_T channels, so every weight
+// read from shared memory (a broadcast) feeds four FMAs and every input read
+// sixteen.  Input channels are staged CI_T at a time.
+constexpr int TH = 16, TW = 64, CI_T = 4;
+constexpr int TWS = TW + 4;     // staged row stride: 16-byte aligned rows
+
 template <int K, bool DGRAD>
-__global__ void __launch_bounds__(CT* CT) conv_f32_kernel(const float* __restrict__ xa, int ca,
+__global__ void __launch_bounds__(256, 2) conv_f32_kernel(const float* __restrict__ xa, int ca,
                                                           const float* __restrict__ xb, int cb,
                                                           const float* __restrict__ mask_src, int n_in, int h,
                                                           int w_, const float* __restrict__ wt,
                                                           const float* __restrict__ bias, int n_out, int relu,
                                                           float* __restrict__ ya, int ya_c, float* __restrict__ yb,
                                                           int tiles_x) {
-    constexpr int R = K / 2, HT = CT + 2 * R;
-    __shared__ float s_in[HT][HT + 1];
-    __shared__ float s_w[CO_T][K * K];
+    constexpr int R = K / 2, HH = TH + 2 * R, HW = TW + 2 * R, KK = K * K;
+    __shared__ __align__(16) float s_in[CI_T][HH][TWS];
+    __shared__ __align__(16) float s_w[CI_T][KK][CO_T];
     const int tile = blockIdx.x;
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     const int co0 = blockIdx.y * CO_T;
     const int n = blockIdx.z;
-    const int lx = threadIdx.x % CT, ly = threadIdx.x / CT;
-    const int x = tx * CT + lx, y = ty * CT + ly;
+    const int tc = threadIdx.x % (TW / 4), tr = threadIdx.x / (TW / 4);
+    const int y = ty * TH + tr, x0 = tx * TW + 4 * tc;
     const long long hw = (long long)h * w_;
-    float acc[CO_T];
+    float acc[4][CO_T];
 #pragma unroll
-    for (int j = 0; j < CO_T; ++j) acc[j] = 0.f;
-    for (int ci = 0; ci < n_in; ++ci) {
-        const float* src;
-        const float* msk = nullptr;
-        if (!DGRAD) {
-            src = ci < ca ? xa + ((long long)n * ca + ci) * hw : xb + ((long long)n * cb + (ci - ca)) * hw;
-        } else {
-            src = xa + ((long long)n * n_in + ci) * hw;
-            if (mask_src) msk = mask_src + ((long long)n * n_in + ci) * hw;
-        }
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int j = 0; j < CO_T; ++j) acc[p][j] = 0.f;
+    for (int ci0 = 0; ci0 < n_in; ci0 += CI_T) {
         __syncthreads();
-        for (int i = threadIdx.x; i < HT * HT; i += CT * CT) {
-            const int hy = i / HT, hx = i - hy * HT;
-            const int gy = ty * CT + hy - R, gx = tx * CT + hx - R;
+        for (int i = threadIdx.x; i < CI_T * HH * HW; i += 256) {
+            const int c = i / (HH * HW), r = i - c * (HH * HW);
+            const int hy = r / HW, hx = r - hy * HW;
+            const int ci = ci0 + c;
+            const int gy = ty * TH + hy - R, gx = tx * TW + hx - R;
             float v = 0.f;
-            if (gy >= 0 && gx >= 0 && gy < h && gx < w_) {
+            if (ci < n_in && gy >= 0 && gx >= 0 && gy < h && gx < w_) {
                 const long long o = (long long)gy * w_ + gx;
-                v = __ldg(src + o);
-                if (msk && !(__ldg(msk + o) > 0.f)) v = 0.f;
+                if (!DGRAD) {
+                    const float* src = ci < ca ? xa + ((long long)n * ca + ci) * hw
+                                               : xb + ((long long)n * cb + (ci - ca)) * hw;
+                    v = __ldg(src + o);
+                } else {
+                    const long long base = ((long long)n * n_in + ci) * hw;
+                    v = __ldg(xa + base + o);
+                    if (mask_src && !(__ldg(mask_src + base + o) > 0.f)) v = 0.f;
+                }
             }
-            s_in[hy][hx] = v;
+            s_in[c][hy][hx] = v;
         }
-        for (int i = threadIdx.x; i < CO_T * K * K; i += CT * CT) {
-            const int j = i / (K * K), tap = i - j * K * K;
-            const int co = co0 + j;
+        for (int i = threadIdx.x; i < CI_T * KK * CO_T; i += 256) {
+            const int c = i / (KK * CO_T), r = i - c * (KK * CO_T);
+            const int tap = r / CO_T, j = r - tap * CO_T;
+            const int ci = ci0 + c, co = co0 + j;
             float v = 0.f;
-            if (co < n_out) {
-                if (!DGRAD) v = __ldg(wt + ((long long)co * n_in + ci) * K * K + tap);
-                else v = __ldg(wt + ((long long)ci * n_out + co) * K * K + (K * K - 1 - tap));
+            if (ci < n_in && co < n_out) {
+                if (!DGRAD) v = __ldg(wt + ((long long)co * n_in + ci) * KK + tap);
+                else v = __ldg(wt + ((long long)ci * n_out + co) * KK + (KK - 1 - tap));
             }
-            s_w[j][tap] = v;
+            s_w[c][tap][j] = v;
         }
         __syncthreads();
 #pragma unroll
-        for (int ky = 0; ky < K; ++ky)
+        for (int c = 0; c < CI_T; ++c) {
 #pragma unroll
-            for (int kx = 0; kx < K; ++kx) {
-                const float v = s_in[ly + ky][lx + kx];
+            for (int ky = 0; ky < K; ++ky) {
+                float v[4 + 2 * R];
+                const float4 a = *reinterpret_cast<const float4*>(&s_in[c][tr + ky][4 * tc]);
+                v[0] = a.x;
+                v[1] = a.y;
+                v[2] = a.z;
+                v[3] = a.w;
+                if constexpr (R > 0) {
+                    const float2 b = *reinterpret_cast<const float2*>(&s_in[c][tr + ky][4 * tc + 4]);
+                    v[4] = b.x;
+                    v[5] = b.y;
+                }
 #pragma unroll
-                for (int j = 0; j < CO_T; ++j) acc[j] = fmaf(s_w[j][ky * K + kx], v, acc[j]);
+                for (int kx = 0; kx < K; ++kx) {
+                    const float4* wp = reinterpret_cast<const float4*>(&s_w[c][ky * K + kx][0]);
+#pragma unroll
+                    for (int q = 0; q < CO_T / 4; ++q) {
+                        const float4 wv = wp[q];
+#pragma unroll
+                        for (int p = 0; p < 4; ++p) {
+                            const float xv = v[p + kx];
+                            acc[p][4 * q + 0] = fmaf(wv.x, xv, acc[p][4 * q + 0]);
+                            acc[p][4 * q + 1] = fmaf(wv.y, xv, acc[p][4 * q + 1]);
+                            acc[p][4 * q + 2] = fmaf(wv.z, xv, acc[p][4 * q + 2]);
+                            acc[p][4 * q + 3] = fmaf(wv.w, xv, acc[p][4 * q + 3]);
+                        }
+                    }
+                }
             }
+        }
     }
-    if (x >= w_ || y >= h) return;
-    const long long p = (long long)y * w_ + x;
+    if (y >= h) return;
 #pragma unroll
-    for (int j = 0; j < CO_T; ++j) {
-        const int co = co0 + j;
-        if (co >= n_out) break;
-        float v = acc[j];
-        if (!DGRAD) {
-            v += __ldg(bias + co);
-            if (relu) v = fmaxf(v, 0.f);
-            ya[((long long)n * n_out + co) * hw + p] = v;
-        } else {
-            if (co < ya_c) {
-                if (ya) ya[((long long)n * ya_c + co) * hw + p] = v;
-            } else if (yb) {
-                yb[((long long)n * (n_out - ya_c) + (co - ya_c)) * hw + p] = v;
+    for (int p = 0; p < 4; ++p) {
+        const int x = x0 + p;
+        if (x >= w_) break;
+        const long long pix = (long long)y * w_ + x;
+#pragma unroll
+        for (int j = 0; j < CO_T; ++j) {
+            const int co = co0 + j;
+            if (co >= n_out) break;
+            float v = acc[p][j];
+            if (!DGRAD) {
+                v += __ldg(bias + co);
+                if (relu) v = fmaxf(v, 0.f);
+                ya[((long long)n * n_out + co) * hw + pix] = v;
+            } else {
+                if (co < ya_c) {
+                    if (ya) ya[((long long)n * ya_c + co) * hw + pix] = v;
+                } else if (yb) {
+                    yb[((long long)n * (n_out - ya_c) + (co - ya_c)) * hw + pix] = v;
+                }
             }
         }
     }
@@ -400,13 +441,13 @@ extern "C" fvn_status fvn_conv_fwd(const float* xa, int ca, const float* xb, int
     FVN_CHECK_ARG(ctx, xa && w && b && y && (cb == 0 || xb), "null tensor");
     FVN_CHECK_ARG(ctx, ca >= 1 && cb >= 0 && n >= 1 && h >= 1 && w_ >= 1 && cout >= 1, "bad sizes");
     FVN_CHECK_ARG(ctx, k == 1 || k == 3, "k must be 1 or 3");
-    const int tiles_x = (w_ + CT - 1) / CT;
-    dim3 grid(tiles_x * ((h + CT - 1) / CT), (cout + CO_T - 1) / CO_T, n);
+    const int tiles_x = (w_ + TW - 1) / TW;
+    dim3 grid(tiles_x * ((h + TH - 1) / TH), (cout + CO_T - 1) / CO_T, n);
     if (k == 3)
-        conv_f32_kernel<3, false><<<grid, CT * CT, 0, as_stream(stream)>>>(xa, ca, xb, cb, nullptr, ca + cb, h, w_, w,
+        conv_f32_kernel<3, false><<<grid, 256, 0, as_stream(stream)>>>(xa, ca, xb, cb, nullptr, ca + cb, h, w_, w,
                                                                            b, cout, relu, y, cout, nullptr, tiles_x);
     else
-        conv_f32_kernel<1, false><<<grid, CT * CT, 0, as_stream(stream)>>>(xa, ca, xb, cb, nullptr, ca + cb, h, w_, w,
+        conv_f32_kernel<1, false><<<grid, 256, 0, as_stream(stream)>>>(xa, ca, xb, cb, nullptr, ca + cb, h, w_, w,
                                                                            b, cout, relu, y, cout, nullptr, tiles_x);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
@@ -422,16 +463,17 @@ extern "C" fvn_status fvn_conv_bwd(const float* xa, int ca, const float* xb, int
     FVN_CHECK_ARG(ctx, ca >= 1 && cb >= 0 && n >= 1 && h >= 1 && w_ >= 1 && cout >= 1, "bad sizes");
     FVN_CHECK_ARG(ctx, k == 1 || k == 3, "k must be 1 or 3");
     const int cin = ca + cb;
-    const int tiles_x = (w_ + CT - 1) / CT;
+    const int tiles_x = (w_ + CT - 1) / CT;            // wgrad tiles
     const int tiles = tiles_x * ((h + CT - 1) / CT);
     if (gxa || gxb) {
-        dim3 grid(tiles, (cin + CO_T - 1) / CO_T, n);
+        const int dtx = (w_ + TW - 1) / TW;
+        dim3 grid(dtx * ((h + TH - 1) / TH), (cin + CO_T - 1) / CO_T, n);
         if (k == 3)
-            conv_f32_kernel<3, true><<<grid, CT * CT, 0, st>>>(gy, cout, nullptr, 0, y_relu, cout, h, w_, w, nullptr,
-                                                               cin, 0, gxa, ca, gxb, tiles_x);
+            conv_f32_kernel<3, true><<<grid, 256, 0, st>>>(gy, cout, nullptr, 0, y_relu, cout, h, w_, w, nullptr,
+                                                           cin, 0, gxa, ca, gxb, dtx);
         else
-            conv_f32_kernel<1, true><<<grid, CT * CT, 0, st>>>(gy, cout, nullptr, 0, y_relu, cout, h, w_, w, nullptr,
-                                                               cin, 0, gxa, ca, gxb, tiles_x);
+            conv_f32_kernel<1, true><<<grid, 256, 0, st>>>(gy, cout, nullptr, 0, y_relu, cout, h, w_, w, nullptr,
+                                                           cin, 0, gxa, ca, gxb, dtx);
         FVN_LAUNCH_CHECK(ctx);
     }
     if (gw) {
