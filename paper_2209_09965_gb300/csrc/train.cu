@@ -152,6 +152,126 @@ __global__ void __launch_bounds__(256, 2) conv_f32_kernel(const float* __restric
     }
 }
 
+// 1x1 convolution (FWD / DGRAD as above with K = 1) as a skinny GEMM over
+// pixel strips: a CTA takes PW x 128 consecutive pixels of one image and up
+// to 8 groups of 16 output channels (blockIdx.z selects the groups when
+// there are more), so each input value is read from memory once per 128
+// output channels; warp w handles sub-strip w / ncog (128 pixels, 4 per
+// lane) and group w % ncog.  Input channels are staged P1_CI at a time.
+constexpr int P1_CI = 8;
+
+__global__ void __launch_bounds__(256) conv1x1_f32_kernel(const float* __restrict__ xa, int ca,
+                                                          const float* __restrict__ xb, int cb,
+                                                          const float* __restrict__ mask_src, int n_in, long long hw,
+                                                          const float* __restrict__ wt,
+                                                          const float* __restrict__ bias, int n_out, int relu,
+                                                          float* __restrict__ ya, int ya_c, float* __restrict__ yb,
+                                                          int ncog, int pw, bool dgrad) {
+    extern __shared__ __align__(16) float smem1[];
+    const int px = 128 * pw;                           // pixels of the strip
+    float* s_in = smem1;                               // [P1_CI][px]
+    float* s_w = smem1 + P1_CI * px;                   // [P1_CI][ncog * 16]
+    const int cop = ncog * CO_T;
+    const int co_base = blockIdx.z * cop;
+    const long long p0 = (long long)blockIdx.x * px;
+    const int n = blockIdx.y;
+    const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+    const int sub = warp / ncog, cog = warp - sub * ncog;
+    const int lp = sub * 128 + 4 * lane;               // first pixel of this lane within the strip
+    float acc[4][CO_T];
+#pragma unroll
+    for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int j = 0; j < CO_T; ++j) acc[p][j] = 0.f;
+    for (int ci0 = 0; ci0 < n_in; ci0 += P1_CI) {
+        __syncthreads();
+        for (int i = threadIdx.x; i < P1_CI * px; i += blockDim.x) {
+            const int c = i / px, q = i - c * px;
+            const int ci = ci0 + c;
+            const long long pix = p0 + q;
+            float v = 0.f;
+            if (ci < n_in && pix < hw) {
+                if (!dgrad) {
+                    const float* src = ci < ca ? xa + ((long long)n * ca + ci) * hw
+                                               : xb + ((long long)n * cb + (ci - ca)) * hw;
+                    v = __ldg(src + pix);
+                } else {
+                    const long long o = ((long long)n * n_in + ci) * hw + pix;
+                    v = __ldg(xa + o);
+                    if (mask_src && !(__ldg(mask_src + o) > 0.f)) v = 0.f;
+                }
+            }
+            s_in[i] = v;
+        }
+        for (int i = threadIdx.x; i < P1_CI * cop; i += blockDim.x) {
+            const int c = i / cop, co = co_base + (i - c * cop);
+            const int ci = ci0 + c;
+            float v = 0.f;
+            if (ci < n_in && co < n_out)
+                v = dgrad ? __ldg(wt + (long long)ci * n_out + co) : __ldg(wt + (long long)co * n_in + ci);
+            s_w[i] = v;
+        }
+        __syncthreads();
+        if (sub < pw) {
+#pragma unroll
+            for (int c = 0; c < P1_CI; ++c) {
+                const float4 xv = *reinterpret_cast<const float4*>(s_in + c * px + lp);
+                const float x4[4] = {xv.x, xv.y, xv.z, xv.w};
+                const float4* wp = reinterpret_cast<const float4*>(s_w + c * cop + cog * CO_T);
+#pragma unroll
+                for (int q = 0; q < CO_T / 4; ++q) {
+                    const float4 wv = wp[q];
+#pragma unroll
+                    for (int p = 0; p < 4; ++p) {
+                        acc[p][4 * q + 0] = fmaf(wv.x, x4[p], acc[p][4 * q + 0]);
+                        acc[p][4 * q + 1] = fmaf(wv.y, x4[p], acc[p][4 * q + 1]);
+                        acc[p][4 * q + 2] = fmaf(wv.z, x4[p], acc[p][4 * q + 2]);
+                        acc[p][4 * q + 3] = fmaf(wv.w, x4[p], acc[p][4 * q + 3]);
+                    }
+                }
+            }
+        }
+    }
+    if (sub >= pw) return;
+#pragma unroll
+    for (int p = 0; p < 4; ++p) {
+        const long long pix = p0 + lp + p;
+        if (pix >= hw) break;
+#pragma unroll
+        for (int j = 0; j < CO_T; ++j) {
+            const int co = co_base + cog * CO_T + j;
+            if (co >= n_out) break;
+            float v = acc[p][j];
+            if (!dgrad) {
+                v += __ldg(bias + co);
+                if (relu) v = fmaxf(v, 0.f);
+                ya[((long long)n * n_out + co) * hw + pix] = v;
+            } else if (co < ya_c) {
+                if (ya) ya[((long long)n * ya_c + co) * hw + pix] = v;
+            } else if (yb) {
+                yb[((long long)n * (n_out - ya_c) + (co - ya_c)) * hw + pix] = v;
+            }
+        }
+    }
+}
+
+// launch shape of conv1x1_f32_kernel for n_out output channels: groups of
+// 16 channels per CTA (at most 8), CTAs over the groups (nz), sub-strips
+struct Conv1Shape {
+    int ncog, nz, pw, threads;
+    size_t smem;
+};
+inline Conv1Shape conv1_shape(int n_out) {
+    Conv1Shape s;
+    const int groups = (n_out + CO_T - 1) / CO_T;
+    s.nz = (groups + 7) / 8;
+    s.ncog = (groups + s.nz - 1) / s.nz;
+    s.pw = std::max(1, 8 / s.ncog);
+    s.threads = 32 * s.ncog * s.pw;
+    s.smem = sizeof(float) * (size_t)P1_CI * (128 * s.pw + s.ncog * CO_T);
+    return s;
+}
+
 // dL/dw[co][ci][tap] and dL/db[co]: each CTA reduces a 16 x 16 (co, ci) block
 // over a range of 16 x 16 pixel tiles and adds its partial sums atomically.
 template <int K>
@@ -443,12 +563,17 @@ extern "C" fvn_status fvn_conv_fwd(const float* xa, int ca, const float* xb, int
     FVN_CHECK_ARG(ctx, k == 1 || k == 3, "k must be 1 or 3");
     const int tiles_x = (w_ + TW - 1) / TW;
     dim3 grid(tiles_x * ((h + TH - 1) / TH), (cout + CO_T - 1) / CO_T, n);
-    if (k == 3)
+    if (k == 3) {
         conv_f32_kernel<3, false><<<grid, 256, 0, as_stream(stream)>>>(xa, ca, xb, cb, nullptr, ca + cb, h, w_, w,
-                                                                           b, cout, relu, y, cout, nullptr, tiles_x);
-    else
-        conv_f32_kernel<1, false><<<grid, 256, 0, as_stream(stream)>>>(xa, ca, xb, cb, nullptr, ca + cb, h, w_, w,
-                                                                           b, cout, relu, y, cout, nullptr, tiles_x);
+                                                                       b, cout, relu, y, cout, nullptr, tiles_x);
+    } else {
+        const Conv1Shape sh = conv1_shape(cout);
+        const long long hw = (long long)h * w_;
+        dim3 g1((unsigned)((hw + 128 * sh.pw - 1) / (128 * sh.pw)), n, sh.nz);
+        conv1x1_f32_kernel<<<g1, sh.threads, sh.smem, as_stream(stream)>>>(xa, ca, xb, cb, nullptr, ca + cb, hw, w, b,
+                                                                          cout, relu, y, cout, nullptr, sh.ncog,
+                                                                          sh.pw, false);
+    }
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
@@ -468,12 +593,16 @@ extern "C" fvn_status fvn_conv_bwd(const float* xa, int ca, const float* xb, int
     if (gxa || gxb) {
         const int dtx = (w_ + TW - 1) / TW;
         dim3 grid(dtx * ((h + TH - 1) / TH), (cin + CO_T - 1) / CO_T, n);
-        if (k == 3)
+        if (k == 3) {
             conv_f32_kernel<3, true><<<grid, 256, 0, st>>>(gy, cout, nullptr, 0, y_relu, cout, h, w_, w, nullptr,
                                                            cin, 0, gxa, ca, gxb, dtx);
-        else
-            conv_f32_kernel<1, true><<<grid, 256, 0, st>>>(gy, cout, nullptr, 0, y_relu, cout, h, w_, w, nullptr,
-                                                           cin, 0, gxa, ca, gxb, dtx);
+        } else {
+            const Conv1Shape sh = conv1_shape(cin);
+            const long long hw = (long long)h * w_;
+            dim3 g1((unsigned)((hw + 128 * sh.pw - 1) / (128 * sh.pw)), n, sh.nz);
+            conv1x1_f32_kernel<<<g1, sh.threads, sh.smem, st>>>(gy, cout, nullptr, 0, y_relu, cout, hw, w, nullptr, cin,
+                                                               0, gxa, ca, gxb, sh.ncog, sh.pw, true);
+        }
         FVN_LAUNCH_CHECK(ctx);
     }
     if (gw) {
