@@ -60,6 +60,7 @@ __global__ void __launch_bounds__(256, 2) conv_f32_kernel(const float* __restric
         for (int j = 0; j < CO_T; ++j) acc[p][j] = 0.f;
     for (int ci0 = 0; ci0 < n_in; ci0 += CI_T) {
         __syncthreads();
+#pragma unroll 4
         for (int i = threadIdx.x; i < CI_T * HH * HW; i += 256) {
             const int c = i / (HH * HW), r = i - c * (HH * HW);
             const int hy = r / HW, hx = r - hy * HW;
@@ -183,25 +184,57 @@ __global__ void __launch_bounds__(256) conv1x1_f32_kernel(const float* __restric
     for (int p = 0; p < 4; ++p)
 #pragma unroll
         for (int j = 0; j < CO_T; ++j) acc[p][j] = 0.f;
+    // planes whose length is a multiple of 4 (and 16-byte aligned tensors)
+    // are staged with 16-byte loads
+    const bool vec = (hw & 3) == 0 && ((reinterpret_cast<uintptr_t>(xa) | reinterpret_cast<uintptr_t>(xb) |
+                                        reinterpret_cast<uintptr_t>(mask_src)) & 15) == 0;
     for (int ci0 = 0; ci0 < n_in; ci0 += P1_CI) {
         __syncthreads();
-        for (int i = threadIdx.x; i < P1_CI * px; i += blockDim.x) {
-            const int c = i / px, q = i - c * px;
-            const int ci = ci0 + c;
-            const long long pix = p0 + q;
-            float v = 0.f;
-            if (ci < n_in && pix < hw) {
-                if (!dgrad) {
-                    const float* src = ci < ca ? xa + ((long long)n * ca + ci) * hw
-                                               : xb + ((long long)n * cb + (ci - ca)) * hw;
-                    v = __ldg(src + pix);
-                } else {
-                    const long long o = ((long long)n * n_in + ci) * hw + pix;
-                    v = __ldg(xa + o);
-                    if (mask_src && !(__ldg(mask_src + o) > 0.f)) v = 0.f;
+        if (vec) {
+#pragma unroll 8
+            for (int i = threadIdx.x; i < P1_CI * px / 4; i += blockDim.x) {
+                const int c = (4 * i) / px, q = 4 * i - c * px;
+                const int ci = ci0 + c;
+                const long long pix = p0 + q;
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (ci < n_in && pix < hw) {
+                    if (!dgrad) {
+                        const float* src = ci < ca ? xa + ((long long)n * ca + ci) * hw
+                                                   : xb + ((long long)n * cb + (ci - ca)) * hw;
+                        v = __ldg(reinterpret_cast<const float4*>(src + pix));
+                    } else {
+                        const long long o = ((long long)n * n_in + ci) * hw + pix;
+                        v = __ldg(reinterpret_cast<const float4*>(xa + o));
+                        if (mask_src) {
+                            const float4 m = __ldg(reinterpret_cast<const float4*>(mask_src + o));
+                            v.x = m.x > 0.f ? v.x : 0.f;
+                            v.y = m.y > 0.f ? v.y : 0.f;
+                            v.z = m.z > 0.f ? v.z : 0.f;
+                            v.w = m.w > 0.f ? v.w : 0.f;
+                        }
+                    }
                 }
+                *reinterpret_cast<float4*>(s_in + 4 * i) = v;
             }
-            s_in[i] = v;
+        } else {
+            for (int i = threadIdx.x; i < P1_CI * px; i += blockDim.x) {
+                const int c = i / px, q = i - c * px;
+                const int ci = ci0 + c;
+                const long long pix = p0 + q;
+                float v = 0.f;
+                if (ci < n_in && pix < hw) {
+                    if (!dgrad) {
+                        const float* src = ci < ca ? xa + ((long long)n * ca + ci) * hw
+                                                   : xb + ((long long)n * cb + (ci - ca)) * hw;
+                        v = __ldg(src + pix);
+                    } else {
+                        const long long o = ((long long)n * n_in + ci) * hw + pix;
+                        v = __ldg(xa + o);
+                        if (mask_src && !(__ldg(mask_src + o) > 0.f)) v = 0.f;
+                    }
+                }
+                s_in[i] = v;
+            }
         }
         for (int i = threadIdx.x; i < P1_CI * cop; i += blockDim.x) {
             const int c = i / cop, co = co_base + (i - c * cop);
