@@ -31,9 +31,19 @@ constexpr int CO_T = 16;        // output channels per CTA
 // A CTA computes a TH x TW pixel tile for CO_T output channels; each thread
 // four consecutive pixels of one row for all CO_T channels, so every weight
 // read from shared memory (a broadcast) feeds four FMAs and every input read
-// sixteen.  Input channels are staged CI_T at a time.
+// sixteen.  Input channels are staged CI_T at a time; the forward pass
+// copies the next group asynchronously (cp.async, double-buffered) while
+// it computes on the current one.
 constexpr int TH = 16, TW = 64, CI_T = 4;
 constexpr int TWS = TW + 4;     // staged row stride: 16-byte aligned rows
+
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
 template <int K, bool DGRAD>
 __global__ void __launch_bounds__(256, 2) conv_f32_kernel(const float* __restrict__ xa, int ca,
@@ -44,8 +54,8 @@ __global__ void __launch_bounds__(256, 2) conv_f32_kernel(const float* __restric
                                                           float* __restrict__ ya, int ya_c, float* __restrict__ yb,
                                                           int tiles_x) {
     constexpr int R = K / 2, HH = TH + 2 * R, HW = TW + 2 * R, KK = K * K;
-    __shared__ __align__(16) float s_in[CI_T][HH][TWS];
-    __shared__ __align__(16) float s_w[CI_T][KK][CO_T];
+    __shared__ __align__(16) float s_in[2][CI_T][HH][TWS];
+    __shared__ __align__(16) float s_w[2][CI_T][KK][CO_T];
     const int tile = blockIdx.x;
     const int ty = tile / tiles_x, tx = tile - ty * tiles_x;
     const int co0 = blockIdx.y * CO_T;
@@ -58,59 +68,26 @@ __global__ void __launch_bounds__(256, 2) conv_f32_kernel(const float* __restric
     for (int p = 0; p < 4; ++p)
 #pragma unroll
         for (int j = 0; j < CO_T; ++j) acc[p][j] = 0.f;
-    for (int ci0 = 0; ci0 < n_in; ci0 += CI_T) {
-        __syncthreads();
-#pragma unroll 4
-        for (int i = threadIdx.x; i < CI_T * HH * HW; i += 256) {
-            const int c = i / (HH * HW), r = i - c * (HH * HW);
-            const int hy = r / HW, hx = r - hy * HW;
-            const int ci = ci0 + c;
-            const int gy = ty * TH + hy - R, gx = tx * TW + hx - R;
-            float v = 0.f;
-            if (ci < n_in && gy >= 0 && gx >= 0 && gy < h && gx < w_) {
-                const long long o = (long long)gy * w_ + gx;
-                if (!DGRAD) {
-                    const float* src = ci < ca ? xa + ((long long)n * ca + ci) * hw
-                                               : xb + ((long long)n * cb + (ci - ca)) * hw;
-                    v = __ldg(src + o);
-                } else {
-                    const long long base = ((long long)n * n_in + ci) * hw;
-                    v = __ldg(xa + base + o);
-                    if (mask_src && !(__ldg(mask_src + base + o) > 0.f)) v = 0.f;
-                }
-            }
-            s_in[c][hy][hx] = v;
-        }
-        for (int i = threadIdx.x; i < CI_T * KK * CO_T; i += 256) {
-            const int c = i / (KK * CO_T), r = i - c * (KK * CO_T);
-            const int tap = r / CO_T, j = r - tap * CO_T;
-            const int ci = ci0 + c, co = co0 + j;
-            float v = 0.f;
-            if (ci < n_in && co < n_out) {
-                if (!DGRAD) v = __ldg(wt + ((long long)co * n_in + ci) * KK + tap);
-                else v = __ldg(wt + ((long long)ci * n_out + co) * KK + (KK - 1 - tap));
-            }
-            s_w[c][tap][j] = v;
-        }
-        __syncthreads();
+
+    auto accumulate = [&](int buf) {
 #pragma unroll
         for (int c = 0; c < CI_T; ++c) {
 #pragma unroll
             for (int ky = 0; ky < K; ++ky) {
                 float v[4 + 2 * R];
-                const float4 a = *reinterpret_cast<const float4*>(&s_in[c][tr + ky][4 * tc]);
+                const float4 a = *reinterpret_cast<const float4*>(&s_in[buf][c][tr + ky][4 * tc]);
                 v[0] = a.x;
                 v[1] = a.y;
                 v[2] = a.z;
                 v[3] = a.w;
                 if constexpr (R > 0) {
-                    const float2 b = *reinterpret_cast<const float2*>(&s_in[c][tr + ky][4 * tc + 4]);
+                    const float2 b = *reinterpret_cast<const float2*>(&s_in[buf][c][tr + ky][4 * tc + 4]);
                     v[4] = b.x;
                     v[5] = b.y;
                 }
 #pragma unroll
                 for (int kx = 0; kx < K; ++kx) {
-                    const float4* wp = reinterpret_cast<const float4*>(&s_w[c][ky * K + kx][0]);
+                    const float4* wp = reinterpret_cast<const float4*>(&s_w[buf][c][ky * K + kx][0]);
 #pragma unroll
                     for (int q = 0; q < CO_T / 4; ++q) {
                         const float4 wv = wp[q];
@@ -125,6 +102,70 @@ __global__ void __launch_bounds__(256, 2) conv_f32_kernel(const float* __restric
                     }
                 }
             }
+        }
+    };
+
+    if constexpr (!DGRAD) {
+        // zero-filled copies read nothing; their source is any valid address
+        auto stage = [&](int buf, int ci0) {
+            for (int i = threadIdx.x; i < CI_T * HH * HW; i += 256) {
+                const int c = i / (HH * HW), r = i - c * (HH * HW);
+                const int hy = r / HW, hx = r - hy * HW;
+                const int ci = ci0 + c;
+                const int gy = ty * TH + hy - R, gx = tx * TW + hx - R;
+                const bool ok = ci < n_in && gy >= 0 && gx >= 0 && gy < h && gx < w_;
+                const float* src = xa;
+                if (ok)
+                    src = (ci < ca ? xa + ((long long)n * ca + ci) * hw : xb + ((long long)n * cb + (ci - ca)) * hw) +
+                          (long long)gy * w_ + gx;
+                cp_async4(&s_in[buf][c][hy][hx], src, ok);
+            }
+            for (int i = threadIdx.x; i < CI_T * KK * CO_T; i += 256) {
+                const int c = i / (KK * CO_T), r = i - c * (KK * CO_T);
+                const int tap = r / CO_T, j = r - tap * CO_T;
+                const int ci = ci0 + c, co = co0 + j;
+                const bool ok = ci < n_in && co < n_out;
+                cp_async4(&s_w[buf][c][tap][j], ok ? wt + ((long long)co * n_in + ci) * KK + tap : wt, ok);
+            }
+        };
+        const int nch = (n_in + CI_T - 1) / CI_T;
+        stage(0, 0);
+        cp_async_commit();
+        for (int k = 0; k < nch; ++k) {
+            if (k + 1 < nch) stage((k + 1) & 1, (k + 1) * CI_T);
+            cp_async_commit();
+            cp_async_wait_1();          // this thread's copies of group k have landed
+            __syncthreads();            // ... and every thread's
+            accumulate(k & 1);
+            __syncthreads();            // buffer k & 1 is free for group k + 2
+        }
+    } else {
+        for (int ci0 = 0; ci0 < n_in; ci0 += CI_T) {
+            __syncthreads();
+#pragma unroll 4
+            for (int i = threadIdx.x; i < CI_T * HH * HW; i += 256) {
+                const int c = i / (HH * HW), r = i - c * (HH * HW);
+                const int hy = r / HW, hx = r - hy * HW;
+                const int ci = ci0 + c;
+                const int gy = ty * TH + hy - R, gx = tx * TW + hx - R;
+                float v = 0.f;
+                if (ci < n_in && gy >= 0 && gx >= 0 && gy < h && gx < w_) {
+                    const long long base = ((long long)n * n_in + ci) * hw + (long long)gy * w_ + gx;
+                    v = __ldg(xa + base);
+                    if (mask_src && !(__ldg(mask_src + base) > 0.f)) v = 0.f;
+                }
+                s_in[0][c][hy][hx] = v;
+            }
+            for (int i = threadIdx.x; i < CI_T * KK * CO_T; i += 256) {
+                const int c = i / (KK * CO_T), r = i - c * (KK * CO_T);
+                const int tap = r / CO_T, j = r - tap * CO_T;
+                const int ci = ci0 + c, co = co0 + j;
+                s_w[0][c][tap][j] = (ci < n_in && co < n_out)
+                                        ? __ldg(wt + ((long long)ci * n_out + co) * KK + (KK - 1 - tap))
+                                        : 0.f;
+            }
+            __syncthreads();
+            accumulate(0);
         }
     }
     if (y >= h) return;
