@@ -774,12 +774,90 @@ def run_two_stage(fvn, wl, weights, vol, tf, mp, dev, nframes, flush):
                            "peak_tflops": FP32_PEAK_TFLOPS, "bound": "alu",
                            "note": "FP32 CUDA-core convolutions (the training kernels)"}
         out["reconstruct"] = timing
+        # the FP64 oracle beside it: the same network on a 96 x 96 crop of the
+        # sparse frame, on the host, scaled to the frame's pixels
+        from oracle import wnet as ownet
+        crop = sp[:, 500:596, 900:996].double().cpu().numpy()
+        params = ownet.unpack(np.load(paths["two_stage_paper"]).astype(np.float64), wl.WNET_PAPER)
+        t0 = time.perf_counter()
+        ownet.forward(params, wl.WNET_PAPER, crop)
+        t_crop = time.perf_counter() - t0
+        out["cpu_oracle"] = {"kind": "oracle", "s_per_1080p_frame": t_crop * W * H / (96 * 96),
+                             "sample": "FP64 two-stage forward (paper widths) of a 96 x 96 crop, scaled by pixels",
+                             "threads": "numpy"}
         return out
     except Exception as exc:   # reported, not part of the metric
         return {"error": str(exc)[:200]}
     finally:
         for c in ctxs.values():
             c.close()
+
+
+def run_training(fvn, wl, weights, vol, tf, mp, dev, steps=20, warmup=3, batch=8, crop=256):
+    """Training throughput (paper: "Training", "Model Precision &
+    Optimization": FP32): one optimiser step = forward, loss, backward and
+    Adam through the library's FP32 kernels, on a fixed batch of 256 x 256
+    crops of the headline frames (sparse input, dense target), timed with
+    CUDA events; for the single network and the two-stage network with the
+    paper's widths.  Algorithmic work: 3 x the forward flops per pixel
+    (forward, data gradient, weight gradient)."""
+    import numpy as np
+    import torch
+    from paper_2209_09965_gb300 import train
+    ctx = fvn.Context()
+    try:
+        ctx.load_weights(weights)
+        sp = torch.empty(5, H, W, device=dev)
+        dense = torch.empty(5, H, W, device=dev)
+        rgb = torch.empty(3, H, W, device=dev)
+        xs = torch.empty(batch, 5, crop, crop, device=dev)
+        ys = torch.empty(batch, 3, crop, crop, device=dev)
+        rng = np.random.default_rng(5)
+        for b in range(batch):
+            cam = wl.orbit_camera(2, 8 * b, nframes=ORBIT, width=W, height=H, radius_factor=(0.85, 1.75))
+            fov = wl.Foveation(focal_px=wl.focal_point(2, 8 * b, W, H), seed=2, frame=8 * b)
+            ctx.march(vol, tf, cam, mp, dense)
+            ctx.render(vol, tf, cam, fov, mp, rgb, rgbam_out=sp)
+            y0 = int(rng.integers(H // 4, 3 * H // 4 - crop))
+            x0 = int(rng.integers(W // 4, 3 * W // 4 - crop))
+            xs[b].copy_(sp[:, y0:y0 + crop, x0:x0 + crop])
+            ys[b].copy_(dense[0:3, y0:y0 + crop, x0:x0 + crop])
+        torch.cuda.synchronize()
+        out = {"workload": f"one optimiser step (forward, L1 + gradient loss, backward, Adam) on {batch} crops of "
+                           f"{crop} x {crop} from the headline frames, FP32 training kernels"}
+        px = batch * crop * crop
+        models = {"single": (weights, wl.NET_LAYERS, None, NET_FLOPS_PER_PX),
+                  "two_stage_paper": (wl.wnet_weights(wl.WNET_PAPER, 3), wl.wnet_layers(wl.WNET_PAPER),
+                                      wl.WNET_PAPER, wnet_flops_per_px(wl, wl.WNET_PAPER))}
+        stream = torch.cuda.current_stream()
+        for key, (flat, layers, cfg, fpp) in models.items():
+            P = train.Params(np.array(flat, np.float32), dev, layers)
+
+            def step():
+                P.g.zero_()
+                pred = train.wnet_forward(P, xs, cfg) if cfg else train.forward(P, xs)
+                train._Loss.apply(pred, ys, 1.0).backward()
+                P.adam(1e-4)
+            for _ in range(warmup):
+                step()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / steps
+            ach = 3.0 * fpp * px / (ms / 1000.0) / 1e12
+            out[key] = {"ms_per_step": ms, "steps_per_s": 1000.0 / ms, "pixels_per_s": px * 1000.0 / ms,
+                        "flops_per_step": 3.0 * fpp * px, "achieved_tflops": ach, "bound": "alu",
+                        "peak_tflops": FP32_PEAK_TFLOPS, "frac": ach / FP32_PEAK_TFLOPS}
+        ctx.device_status()
+        return out
+    except Exception as exc:   # reported, not part of the metric
+        return {"error": str(exc)[:200]}
+    finally:
+        ctx.close()
 
 
 def run_multiview(ctx, fvn, wl, dev, steps, warmup, flush):
@@ -907,8 +985,9 @@ def main():
     if args.two_stage_only:
         vol_np, tf_np, _, _, mp = wl.foveated_1080p_workload(seed=2, frame=0, n=VOL_N)
         flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device=dev)
-        print(json.dumps(run_two_stage(fvn, wl, weights, torch.from_numpy(vol_np).to(dev),
-                                       torch.from_numpy(tf_np).to(dev), mp, dev, 16, flush)))
+        vol, tf = torch.from_numpy(vol_np).to(dev), torch.from_numpy(tf_np).to(dev)
+        print(json.dumps({"two_stage": run_two_stage(fvn, wl, weights, vol, tf, mp, dev, 16, flush),
+                          "training": run_training(fvn, wl, weights, vol, tf, mp, dev)}))
         return
     ctx = fvn.Context()
     ctx.load_weights(weights)
@@ -1110,11 +1189,12 @@ def main():
                               else "mma_sync", vol, tf, frames, dev, min(args.steps, 16), flush)
         paper_settings = run_paper_settings(fvn, wl, weights, vol, tf, dev, min(args.steps, 16), flush)
 
-    blue = recurrent = two_stage = None
+    blue = recurrent = two_stage = training = None
     if not args.headline_only:
         blue = run_blue_noise(ctx, wl, vol, tf, mp, frames, dev, min(args.steps, ORBIT), flush)
         recurrent = run_recurrent(fvn, wl, weights, vol, tf, mp, dev, min(args.steps, 32), flush)
         two_stage = run_two_stage(fvn, wl, weights, vol, tf, mp, dev, min(args.steps, 8), flush)
+        training = run_training(fvn, wl, weights, vol, tf, mp, dev)
 
     multiview = None
     if not args.no_multiview:
@@ -1175,6 +1255,7 @@ def main():
             "blue_noise_mask": blue,
             "recurrent": recurrent,
             "two_stage": two_stage,
+            "training": training,
             "multiview": multiview,
             "clocks": clocks,
         }
