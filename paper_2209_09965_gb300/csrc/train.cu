@@ -348,6 +348,13 @@ inline Conv1Shape conv1_shape(int n_out) {
 
 // dL/dw[co][ci][tap] and dL/db[co]: each CTA reduces a 16 x 16 (co, ci) block
 // over a range of 16 x 16 pixel tiles and adds its partial sums atomically.
+// Thread t takes output channels 4 (t >> 6) .. + 3, input channel (t >> 2) & 15
+// and the tile rows r = 4 i + (t & 3); per step four pixels of a row: four
+// 16-byte loads of dL/dy and one 16- and one 8-byte load per tap row of x
+// feed 4 x 4 x K^2 FMAs.  The four row subsets of a (co, ci) pair sit in
+// consecutive lanes and are summed by shuffles before the atomics.
+constexpr int WG_XS = CT + 4;   // staged x row stride (16-byte aligned rows)
+
 template <int K>
 __global__ void __launch_bounds__(256) conv_wgrad_kernel(const float* __restrict__ xa, int ca,
                                                          const float* __restrict__ xb, int cb,
@@ -355,17 +362,19 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(const float* __restrict
                                                          const float* __restrict__ y_relu, int n, int h, int w_,
                                                          int cout, float* __restrict__ gw, float* __restrict__ gb,
                                                          int tiles_x, int tiles_per_img, int tiles_per_cta) {
-    constexpr int R = K / 2, HT = CT + 2 * R;
-    __shared__ float s_g[16][CT * CT];
-    __shared__ float s_x[16][HT * HT];
+    constexpr int R = K / 2, HT = CT + 2 * R, KK = K * K;
+    __shared__ __align__(16) float s_g[16][CT * CT];
+    __shared__ __align__(16) float s_x[16][HT][WG_XS];
     const int cin = ca + cb;
     const int co0 = blockIdx.x * 16, ci0 = blockIdx.y * 16;
-    const int tco = threadIdx.x / 16, tci = threadIdx.x % 16;
+    const int cg = threadIdx.x >> 6, tci = (threadIdx.x >> 2) & 15, sub = threadIdx.x & 3;
     const long long hw = (long long)h * w_;
-    float acc[K * K];
+    float acc[4][KK];
 #pragma unroll
-    for (int i = 0; i < K * K; ++i) acc[i] = 0.f;
-    float accb = 0.f;
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int i = 0; i < KK; ++i) acc[j][i] = 0.f;
+    float accb[4] = {0.f, 0.f, 0.f, 0.f};
     const int total_tiles = n * tiles_per_img;
     const int t_begin = blockIdx.z * tiles_per_cta;
     const int t_end = std::min(total_tiles, t_begin + tiles_per_cta);
@@ -387,7 +396,8 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(const float* __restrict
         }
         for (int i = threadIdx.x; i < 16 * HT * HT; i += 256) {
             const int j = i / (HT * HT), pp = i - j * HT * HT;
-            const int yy = ty * CT + pp / HT - R, xx = tx * CT + pp % HT - R;
+            const int hy = pp / HT, hx = pp - hy * HT;
+            const int yy = ty * CT + hy - R, xx = tx * CT + hx - R;
             const int ci = ci0 + j;
             float v = 0.f;
             if (ci < cin && yy >= 0 && xx >= 0 && yy < h && xx < w_) {
@@ -395,25 +405,71 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(const float* __restrict
                                            : xb + ((long long)img * cb + (ci - ca)) * hw;
                 v = __ldg(src + (long long)yy * w_ + xx);
             }
-            s_x[j][pp] = v;
+            s_x[j][hy][hx] = v;
         }
         __syncthreads();
-        for (int pp = 0; pp < CT * CT; ++pp) {
-            const float g = s_g[tco][pp];
-            const int py = pp / CT, px = pp % CT;
-            accb += g;
+#pragma unroll 1
+        for (int rr = 0; rr < CT / 4; ++rr) {
+            const int r = 4 * rr + sub;
 #pragma unroll
-            for (int ky = 0; ky < K; ++ky)
+            for (int k4 = 0; k4 < CT / 4; ++k4) {
+                float g[4][4];
 #pragma unroll
-                for (int kx = 0; kx < K; ++kx) acc[ky * K + kx] = fmaf(g, s_x[tci][(py + ky) * HT + px + kx], acc[ky * K + kx]);
+                for (int j = 0; j < 4; ++j) {
+                    const float4 gv = *reinterpret_cast<const float4*>(&s_g[4 * cg + j][r * CT + 4 * k4]);
+                    g[j][0] = gv.x;
+                    g[j][1] = gv.y;
+                    g[j][2] = gv.z;
+                    g[j][3] = gv.w;
+                    accb[j] += (gv.x + gv.y) + (gv.z + gv.w);
+                }
+#pragma unroll
+                for (int ky = 0; ky < K; ++ky) {
+                    float xv[4 + 2 * R];
+                    const float4 a = *reinterpret_cast<const float4*>(&s_x[tci][r + ky][4 * k4]);
+                    xv[0] = a.x;
+                    xv[1] = a.y;
+                    xv[2] = a.z;
+                    xv[3] = a.w;
+                    if constexpr (R > 0) {
+                        const float2 b = *reinterpret_cast<const float2*>(&s_x[tci][r + ky][4 * k4 + 4]);
+                        xv[4] = b.x;
+                        xv[5] = b.y;
+                    }
+#pragma unroll
+                    for (int kx = 0; kx < K; ++kx)
+#pragma unroll
+                        for (int j = 0; j < 4; ++j)
+#pragma unroll
+                            for (int p = 0; p < 4; ++p)
+                                acc[j][ky * K + kx] = fmaf(g[j][p], xv[p + kx], acc[j][ky * K + kx]);
+                }
+            }
         }
     }
-    const int co = co0 + tco, ci = ci0 + tci;
-    if (co < cout && ci < cin) {
+    // sum the four row subsets (consecutive lanes), then one atomic per entry
 #pragma unroll
-        for (int i = 0; i < K * K; ++i) atomicAdd(gw + ((long long)co * cin + ci) * K * K + i, acc[i]);
+    for (int j = 0; j < 4; ++j) {
+#pragma unroll
+        for (int i = 0; i < KK; ++i) {
+            acc[j][i] += __shfl_xor_sync(0xffffffffu, acc[j][i], 1);
+            acc[j][i] += __shfl_xor_sync(0xffffffffu, acc[j][i], 2);
+        }
+        accb[j] += __shfl_xor_sync(0xffffffffu, accb[j], 1);
+        accb[j] += __shfl_xor_sync(0xffffffffu, accb[j], 2);
     }
-    if (blockIdx.y == 0 && tci == 0 && co < cout) atomicAdd(gb + co, accb);
+    const int ci = ci0 + tci;
+    if (sub == 0) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int co = co0 + 4 * cg + j;
+            if (co < cout && ci < cin) {
+#pragma unroll
+                for (int i = 0; i < KK; ++i) atomicAdd(gw + ((long long)co * cin + ci) * KK + i, acc[j][i]);
+            }
+            if (blockIdx.y == 0 && tci == 0 && co < cout) atomicAdd(gb + co, accb[j]);
+        }
+    }
 }
 
 __global__ void avgpool2_fwd_kernel(const float* __restrict__ x, long long nc, int h, int w_, float* __restrict__ y) {
