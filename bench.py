@@ -52,6 +52,7 @@ def parse():
                    help="the compaction sweep with global shadows (the paper's renderer setting)")
     p.add_argument("--profile-two-stage", action="store_true",
                    help="two untimed two-stage passes at 1080p (paper widths), for ncu")
+    p.add_argument("--profile-size", default="1920x1080", help="frame size of --profile-two-stage")
     p.add_argument("--two-stage-only", action="store_true",
                    help="only the two-stage network comparison (prints its JSON)")
     p.add_argument("--sweep", action="store_true",
@@ -308,10 +309,11 @@ def run_profile_shadows():
     print("shadow profile case done")
 
 
-def run_profile_two_stage():
+def run_profile_two_stage(size="1920x1080"):
     """Two untimed passes of the two-stage network with the paper's widths
-    (the trained equal-budget weights when present) over the sparse 1080p
-    headline frame of orbit frame 16, for an ncu capture."""
+    (the trained equal-budget weights when present) over the sparse headline
+    frame of orbit frame 16 (1920 x 1080, or the top-left window of the
+    given size), for an ncu capture."""
     import numpy as np
     import torch
     import __graft_entry__ as ge
@@ -333,8 +335,13 @@ def run_profile_two_stage():
     cam = wl.orbit_camera(2, 16, nframes=ORBIT, width=W, height=H, radius_factor=(0.85, 1.75))
     fov = wl.Foveation(focal_px=wl.focal_point(2, 16, W, H), seed=2, frame=16)
     ctx.render(vol, tf, cam, fov, mp, rgb, rgbam_out=sp)
+    pw, ph = (int(v) for v in size.lower().split("x"))
+    if not (1 <= pw <= W and 1 <= ph <= H):
+        raise SystemExit(f"--profile-size must be within {W}x{H}")
+    win = sp[:, :ph, :pw].contiguous()
+    out = torch.empty(3, ph, pw, device=dev)
     for _ in range(2):
-        ctx.reconstruct_wnet(sp, W, H, rgb)
+        ctx.reconstruct_wnet(win, pw, ph, out)
     ctx.device_status()
     print("two-stage profile case done")
 
@@ -963,7 +970,7 @@ def main():
     if args.profile_shadows:
         return run_profile_shadows()
     if args.profile_two_stage:
-        return run_profile_two_stage()
+        return run_profile_two_stage(args.profile_size)
     if args.sweep:
         return run_sweep()
     if args.sweep_shadows:
