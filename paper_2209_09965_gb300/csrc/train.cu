@@ -108,17 +108,26 @@ __global__ void __launch_bounds__(256, 2) conv_f32_kernel(const float* __restric
     if constexpr (!DGRAD) {
         // zero-filled copies read nothing; their source is any valid address
         auto stage = [&](int buf, int ci0) {
-            for (int i = threadIdx.x; i < CI_T * HH * HW; i += 256) {
-                const int c = i / (HH * HW), r = i - c * (HH * HW);
-                const int hy = r / HW, hx = r - hy * HW;
+            // each thread copies fixed tile positions of all CI_T channels:
+            // the position arithmetic is done once per position
+            const float* plane[CI_T];
+#pragma unroll
+            for (int c = 0; c < CI_T; ++c) {
                 const int ci = ci0 + c;
+                plane[c] = ci >= n_in ? nullptr
+                           : ci < ca  ? xa + ((long long)n * ca + ci) * hw
+                                      : xb + ((long long)n * cb + (ci - ca)) * hw;
+            }
+            for (int pos = threadIdx.x; pos < HH * HW; pos += 256) {
+                const int hy = pos / HW, hx = pos - hy * HW;
                 const int gy = ty * TH + hy - R, gx = tx * TW + hx - R;
-                const bool ok = ci < n_in && gy >= 0 && gx >= 0 && gy < h && gx < w_;
-                const float* src = xa;
-                if (ok)
-                    src = (ci < ca ? xa + ((long long)n * ca + ci) * hw : xb + ((long long)n * cb + (ci - ca)) * hw) +
-                          (long long)gy * w_ + gx;
-                cp_async4(&s_in[buf][c][hy][hx], src, ok);
+                const bool in = gy >= 0 && gx >= 0 && gy < h && gx < w_;
+                const long long off = in ? (long long)gy * w_ + gx : 0;
+#pragma unroll
+                for (int c = 0; c < CI_T; ++c) {
+                    const bool ok = in && plane[c] != nullptr;
+                    cp_async4(&s_in[buf][c][hy][hx], ok ? plane[c] + off : xa, ok);
+                }
             }
             for (int i = threadIdx.x; i < CI_T * KK * CO_T; i += 256) {
                 const int c = i / (KK * CO_T), r = i - c * (KK * CO_T);
@@ -142,19 +151,24 @@ __global__ void __launch_bounds__(256, 2) conv_f32_kernel(const float* __restric
     } else {
         for (int ci0 = 0; ci0 < n_in; ci0 += CI_T) {
             __syncthreads();
-#pragma unroll 4
-            for (int i = threadIdx.x; i < CI_T * HH * HW; i += 256) {
-                const int c = i / (HH * HW), r = i - c * (HH * HW);
-                const int hy = r / HW, hx = r - hy * HW;
-                const int ci = ci0 + c;
+            for (int pos = threadIdx.x; pos < HH * HW; pos += 256) {
+                const int hy = pos / HW, hx = pos - hy * HW;
                 const int gy = ty * TH + hy - R, gx = tx * TW + hx - R;
-                float v = 0.f;
-                if (ci < n_in && gy >= 0 && gx >= 0 && gy < h && gx < w_) {
-                    const long long base = ((long long)n * n_in + ci) * hw + (long long)gy * w_ + gx;
-                    v = __ldg(xa + base);
-                    if (mask_src && !(__ldg(mask_src + base) > 0.f)) v = 0.f;
+                const bool in = gy >= 0 && gx >= 0 && gy < h && gx < w_;
+                const long long off = (long long)gy * w_ + gx;
+                float v[CI_T];
+#pragma unroll
+                for (int c = 0; c < CI_T; ++c) {
+                    const int ci = ci0 + c;
+                    v[c] = 0.f;
+                    if (in && ci < n_in) {
+                        const long long base = ((long long)n * n_in + ci) * hw + off;
+                        v[c] = __ldg(xa + base);
+                        if (mask_src && !(__ldg(mask_src + base) > 0.f)) v[c] = 0.f;
+                    }
                 }
-                s_in[0][c][hy][hx] = v;
+#pragma unroll
+                for (int c = 0; c < CI_T; ++c) s_in[0][c][hy][hx] = v[c];
             }
             for (int i = threadIdx.x; i < CI_T * KK * CO_T; i += 256) {
                 const int c = i / (KK * CO_T), r = i - c * (KK * CO_T);
