@@ -42,6 +42,11 @@ __device__ __forceinline__ void cp_async4(float* dst, const float* src, bool val
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 4 : 0)
                  : "memory");
 }
+__device__ __forceinline__ void cp_async16(float* dst, const float* src, bool valid) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(valid ? 16 : 0)
+                 : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 
@@ -213,7 +218,9 @@ __global__ void __launch_bounds__(256, 2) conv_f32_kernel(const float* __restric
 // to 8 groups of 16 output channels (blockIdx.z selects the groups when
 // there are more), so each input value is read from memory once per 128
 // output channels; warp w handles sub-strip w / ncog (128 pixels, 4 per
-// lane) and group w % ncog.  Input channels are staged P1_CI at a time.
+// lane) and group w % ncog.  Input channels are staged P1_CI at a time; the
+// forward pass on 16-byte aligned planes copies the next group with cp.async
+// into a second buffer while it computes on the current one.
 constexpr int P1_CI = 8;
 
 __global__ void __launch_bounds__(256) conv1x1_f32_kernel(const float* __restrict__ xa, int ca,
@@ -225,9 +232,9 @@ __global__ void __launch_bounds__(256) conv1x1_f32_kernel(const float* __restric
                                                           int ncog, int pw, bool dgrad) {
     extern __shared__ __align__(16) float smem1[];
     const int px = 128 * pw;                           // pixels of the strip
-    float* s_in = smem1;                               // [P1_CI][px]
-    float* s_w = smem1 + P1_CI * px;                   // [P1_CI][ncog * 16]
     const int cop = ncog * CO_T;
+    float* s_in = smem1;                               // [2][P1_CI][px]
+    float* s_w = smem1 + 2 * P1_CI * px;               // [2][P1_CI][cop]
     const int co_base = blockIdx.z * cop;
     const long long p0 = (long long)blockIdx.x * px;
     const int n = blockIdx.y;
@@ -239,25 +246,78 @@ __global__ void __launch_bounds__(256) conv1x1_f32_kernel(const float* __restric
     for (int p = 0; p < 4; ++p)
 #pragma unroll
         for (int j = 0; j < CO_T; ++j) acc[p][j] = 0.f;
+    auto accumulate = [&](int buf) {
+        if (sub >= pw) return;
+        const float* si = s_in + buf * P1_CI * px;
+        const float* sw = s_w + buf * P1_CI * cop;
+#pragma unroll
+        for (int c = 0; c < P1_CI; ++c) {
+            const float4 xv = *reinterpret_cast<const float4*>(si + c * px + lp);
+            const float x4[4] = {xv.x, xv.y, xv.z, xv.w};
+            const float4* wp = reinterpret_cast<const float4*>(sw + c * cop + cog * CO_T);
+#pragma unroll
+            for (int q = 0; q < CO_T / 4; ++q) {
+                const float4 wv = wp[q];
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    acc[p][4 * q + 0] = fmaf(wv.x, x4[p], acc[p][4 * q + 0]);
+                    acc[p][4 * q + 1] = fmaf(wv.y, x4[p], acc[p][4 * q + 1]);
+                    acc[p][4 * q + 2] = fmaf(wv.z, x4[p], acc[p][4 * q + 2]);
+                    acc[p][4 * q + 3] = fmaf(wv.w, x4[p], acc[p][4 * q + 3]);
+                }
+            }
+        }
+    };
     // planes whose length is a multiple of 4 (and 16-byte aligned tensors)
-    // are staged with 16-byte loads
+    // are staged with 16-byte copies
     const bool vec = (hw & 3) == 0 && ((reinterpret_cast<uintptr_t>(xa) | reinterpret_cast<uintptr_t>(xb) |
                                         reinterpret_cast<uintptr_t>(mask_src)) & 15) == 0;
-    for (int ci0 = 0; ci0 < n_in; ci0 += P1_CI) {
-        __syncthreads();
-        if (vec) {
-#pragma unroll 8
+    if (!dgrad && vec) {
+        // forward: the next channel group is copied asynchronously
+        // (double-buffered) while the current one is used
+        auto stage = [&](int buf, int ci0) {
+            float* si = s_in + buf * P1_CI * px;
             for (int i = threadIdx.x; i < P1_CI * px / 4; i += blockDim.x) {
                 const int c = (4 * i) / px, q = 4 * i - c * px;
                 const int ci = ci0 + c;
                 const long long pix = p0 + q;
-                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (ci < n_in && pix < hw) {
-                    if (!dgrad) {
-                        const float* src = ci < ca ? xa + ((long long)n * ca + ci) * hw
-                                                   : xb + ((long long)n * cb + (ci - ca)) * hw;
-                        v = __ldg(reinterpret_cast<const float4*>(src + pix));
-                    } else {
+                const bool ok = ci < n_in && pix < hw;
+                const float* src = xa;
+                if (ok)
+                    src = (ci < ca ? xa + ((long long)n * ca + ci) * hw : xb + ((long long)n * cb + (ci - ca)) * hw) +
+                          pix;
+                cp_async16(si + 4 * i, src, ok);
+            }
+            float* sw = s_w + buf * P1_CI * cop;
+            for (int i = threadIdx.x; i < P1_CI * cop; i += blockDim.x) {
+                const int c = i / cop, co = co_base + (i - c * cop);
+                const int ci = ci0 + c;
+                const bool ok = ci < n_in && co < n_out;
+                cp_async4(sw + i, ok ? wt + (long long)co * n_in + ci : wt, ok);
+            }
+        };
+        const int nch = (n_in + P1_CI - 1) / P1_CI;
+        stage(0, 0);
+        cp_async_commit();
+        for (int k = 0; k < nch; ++k) {
+            if (k + 1 < nch) stage((k + 1) & 1, (k + 1) * P1_CI);
+            cp_async_commit();
+            cp_async_wait_1();
+            __syncthreads();
+            accumulate(k & 1);
+            __syncthreads();
+        }
+    } else {
+        for (int ci0 = 0; ci0 < n_in; ci0 += P1_CI) {
+            __syncthreads();
+            if (vec) {
+#pragma unroll 8
+                for (int i = threadIdx.x; i < P1_CI * px / 4; i += blockDim.x) {
+                    const int c = (4 * i) / px, q = 4 * i - c * px;
+                    const int ci = ci0 + c;
+                    const long long pix = p0 + q;
+                    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                    if (ci < n_in && pix < hw) {
                         const long long o = ((long long)n * n_in + ci) * hw + pix;
                         v = __ldg(reinterpret_cast<const float4*>(xa + o));
                         if (mask_src) {
@@ -268,56 +328,38 @@ __global__ void __launch_bounds__(256) conv1x1_f32_kernel(const float* __restric
                             v.w = m.w > 0.f ? v.w : 0.f;
                         }
                     }
+                    *reinterpret_cast<float4*>(s_in + 4 * i) = v;
                 }
-                *reinterpret_cast<float4*>(s_in + 4 * i) = v;
+            } else {
+                for (int i = threadIdx.x; i < P1_CI * px; i += blockDim.x) {
+                    const int c = i / px, q = i - c * px;
+                    const int ci = ci0 + c;
+                    const long long pix = p0 + q;
+                    float v = 0.f;
+                    if (ci < n_in && pix < hw) {
+                        if (!dgrad) {
+                            const float* src = ci < ca ? xa + ((long long)n * ca + ci) * hw
+                                                       : xb + ((long long)n * cb + (ci - ca)) * hw;
+                            v = __ldg(src + pix);
+                        } else {
+                            const long long o = ((long long)n * n_in + ci) * hw + pix;
+                            v = __ldg(xa + o);
+                            if (mask_src && !(__ldg(mask_src + o) > 0.f)) v = 0.f;
+                        }
+                    }
+                    s_in[i] = v;
+                }
             }
-        } else {
-            for (int i = threadIdx.x; i < P1_CI * px; i += blockDim.x) {
-                const int c = i / px, q = i - c * px;
+            for (int i = threadIdx.x; i < P1_CI * cop; i += blockDim.x) {
+                const int c = i / cop, co = co_base + (i - c * cop);
                 const int ci = ci0 + c;
-                const long long pix = p0 + q;
                 float v = 0.f;
-                if (ci < n_in && pix < hw) {
-                    if (!dgrad) {
-                        const float* src = ci < ca ? xa + ((long long)n * ca + ci) * hw
-                                                   : xb + ((long long)n * cb + (ci - ca)) * hw;
-                        v = __ldg(src + pix);
-                    } else {
-                        const long long o = ((long long)n * n_in + ci) * hw + pix;
-                        v = __ldg(xa + o);
-                        if (mask_src && !(__ldg(mask_src + o) > 0.f)) v = 0.f;
-                    }
-                }
-                s_in[i] = v;
+                if (ci < n_in && co < n_out)
+                    v = dgrad ? __ldg(wt + (long long)ci * n_out + co) : __ldg(wt + (long long)co * n_in + ci);
+                s_w[i] = v;
             }
-        }
-        for (int i = threadIdx.x; i < P1_CI * cop; i += blockDim.x) {
-            const int c = i / cop, co = co_base + (i - c * cop);
-            const int ci = ci0 + c;
-            float v = 0.f;
-            if (ci < n_in && co < n_out)
-                v = dgrad ? __ldg(wt + (long long)ci * n_out + co) : __ldg(wt + (long long)co * n_in + ci);
-            s_w[i] = v;
-        }
-        __syncthreads();
-        if (sub < pw) {
-#pragma unroll
-            for (int c = 0; c < P1_CI; ++c) {
-                const float4 xv = *reinterpret_cast<const float4*>(s_in + c * px + lp);
-                const float x4[4] = {xv.x, xv.y, xv.z, xv.w};
-                const float4* wp = reinterpret_cast<const float4*>(s_w + c * cop + cog * CO_T);
-#pragma unroll
-                for (int q = 0; q < CO_T / 4; ++q) {
-                    const float4 wv = wp[q];
-#pragma unroll
-                    for (int p = 0; p < 4; ++p) {
-                        acc[p][4 * q + 0] = fmaf(wv.x, x4[p], acc[p][4 * q + 0]);
-                        acc[p][4 * q + 1] = fmaf(wv.y, x4[p], acc[p][4 * q + 1]);
-                        acc[p][4 * q + 2] = fmaf(wv.z, x4[p], acc[p][4 * q + 2]);
-                        acc[p][4 * q + 3] = fmaf(wv.w, x4[p], acc[p][4 * q + 3]);
-                    }
-                }
-            }
+            __syncthreads();
+            accumulate(0);
         }
     }
     if (sub >= pw) return;
@@ -354,9 +396,9 @@ inline Conv1Shape conv1_shape(int n_out) {
     const int groups = (n_out + CO_T - 1) / CO_T;
     s.nz = (groups + 7) / 8;
     s.ncog = (groups + s.nz - 1) / s.nz;
-    s.pw = std::max(1, 8 / s.ncog);
+    s.pw = std::max(1, std::min(4, 8 / s.ncog));
     s.threads = 32 * s.ncog * s.pw;
-    s.smem = sizeof(float) * (size_t)P1_CI * (128 * s.pw + s.ncog * CO_T);
+    s.smem = sizeof(float) * 2 * (size_t)P1_CI * (128 * s.pw + s.ncog * CO_T);   // two buffers
     return s;
 }
 
