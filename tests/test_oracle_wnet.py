@@ -177,3 +177,37 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
         return out, dict(wq=wq, nb=nb, out=out)
     monkeypatch.setattr(W, "filter3", bad_filter)
     assert np.abs(W.forward(P, TINY, sp) - np.array([0.3, 0.55, 0.8])[None, :, None, None]).max() > 1e-3
+
+
+@pytest.mark.parametrize("cfg", [((5,), 4, (6,)), ((3, 4, 5), 6, (4, 3, 5))])
+def test_constant_image_at_other_depths(cfg):
+    """The image-path invariant with one and three levels (ragged frame)."""
+    P = rand_params(cfg, 13)
+    set_layer(P, "d_out", 0.0, [0.1, 0.2, 0.9])
+    sp = np.random.default_rng(14).uniform(size=(1, 5, 11, 19))
+    out = W.forward(P, cfg, sp)
+    assert np.abs(out - np.array([0.1, 0.2, 0.9])[None, :, None, None]).max() < 1e-12
+
+
+def test_flops_of_the_benchmark_roofline():
+    """The two-stage roofline numerator: every convolution's 2 cin cout k^2 at
+    its scale (4^-s of the pixels), plus 2 x 27 flops per filtered pixel at
+    each of the image path's filters."""
+    import os
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    from paper_2209_09965_gb300 import workloads as wl
+    enc, bot, dec = W.PAPER
+    conv = 0.0
+    scale = {"d_out": 0}
+    for s in range(3):
+        for pre in ("d_enc", "d_dec", "k_enc", "k_dec"):
+            scale[f"{pre}{s}"] = s
+    for name, ci, co, k in W.layer_table(W.PAPER):
+        key = name if name == "d_out" else name[:6]
+        s = 3 if "bot" in name else scale[key]
+        conv += 2 * ci * co * k * k / 4 ** s
+    filters = (1 + 1 / 4 + 1 / 16) * 2 + 1 / 64        # encoder and decoder filters per scale, the coarsest
+    assert bench.wnet_flops_per_px(wl, W.PAPER) == pytest.approx(conv + filters * 54, rel=1e-12)
+    assert 470e3 < conv < 480e3
