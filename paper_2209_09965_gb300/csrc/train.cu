@@ -12,6 +12,8 @@
 //  - 2x2 average pooling, bilinear x2 up-sampling and their adjoints;
 //  - the kernel-prediction blend forward / backward;
 //  - the L1 + image-gradient loss and Adam.
+// The same convolutions run the two-stage network's inference pass
+// (fvn_reconstruct_wnet, wnet.cu).
 #include <math.h>
 
 #include <algorithm>
