@@ -75,6 +75,7 @@ def test_two_stage_weight_count_and_argument_checks(binding):
             c.enc[s], c.dec[s] = bad[0][s], bad[2][s]
         c.bot = bad[1]
         assert binding.lib.fvn_wnet_weight_count(ctypes.byref(c)) == 0
+    assert binding.wnet_weight_count(((4,) * 5, 4, (4,) * 5)) == 0    # too deep: marshalled, then rejected
     lib = binding.lib
     assert lib.fvn_load_wnet_weights(None, None, None, 0) == -1
     assert lib.fvn_reconstruct_wnet(None, None, 4, 4, None, None) == -1
