@@ -512,7 +512,9 @@ typedef struct {
 size_t fvn_wnet_weight_count(const fvn_wnet_config* cfg);
 
 /* Install two-stage weights (host float array of fvn_wnet_weight_count(cfg)
- * entries; copied, synchronises).  Independent of fvn_load_weights. */
+ * entries, all finite; copied, synchronises).  Independent of
+ * fvn_load_weights.  An argument error (FVN_ERR_ARG) keeps the weights
+ * installed before; a CUDA error during the copy leaves none installed. */
 fvn_status fvn_load_wnet_weights(fvn_ctx* ctx, const fvn_wnet_config* cfg, const float* host_w, size_t n);
 
 /* The two-stage network on one sparse frame: rgbam device float [5][h][w]

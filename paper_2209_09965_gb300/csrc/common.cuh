@@ -87,7 +87,8 @@ struct BatchWorkspace {
 struct WnetState {
     fvn_wnet_config cfg{};
     float* d_w = nullptr;
-    size_t n = 0;
+    size_t n = 0, cap = 0;            // weights in use / floats allocated
+    bool loaded = false;              // a complete set of weights is in place
     void* ws = nullptr;
     size_t ws_bytes = 0;
     int ws_w = 0, ws_h = 0;           // padded frame the workspace was carved for

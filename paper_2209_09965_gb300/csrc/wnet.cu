@@ -389,11 +389,13 @@ extern "C" fvn_status fvn_load_wnet_weights(fvn_ctx* ctx, const fvn_wnet_config*
     for (size_t i = 0; i < n; ++i) FVN_CHECK_ARG(ctx, isfinite(host_w[i]), "weight %zu is not finite", i);
     FVN_CUDA(ctx, cudaDeviceSynchronize());
     WnetState& S = ctx->wnet;
-    if (S.n != n) {
+    S.loaded = false;                  // until the new set is complete
+    if (S.cap < n) {
         cudaFree(S.d_w);
         S.d_w = nullptr;
-        S.n = 0;
+        S.cap = 0;
         FVN_CUDA(ctx, cudaMalloc(&S.d_w, n * sizeof(float)));
+        S.cap = n;
     }
     FVN_CUDA(ctx, cudaMemcpy(S.d_w, host_w, n * sizeof(float), cudaMemcpyHostToDevice));
     S.n = n;
@@ -404,6 +406,7 @@ extern "C" fvn_status fvn_load_wnet_weights(fvn_ctx* ctx, const fvn_wnet_config*
         S.ws_w = S.ws_h = 0;
     }
     S.cfg = *cfg;
+    S.loaded = true;
     return FVN_OK;
 }
 
@@ -413,7 +416,7 @@ extern "C" fvn_status fvn_reconstruct_wnet(fvn_ctx* ctx, const float* rgbam, int
     FVN_CHECK_ARG(ctx, rgbam && rgb, "null buffer");
     FVN_CHECK_ARG(ctx, w >= 1 && h >= 1 && w <= kMaxSide && h <= kMaxSide, "bad frame size %d x %d", w, h);
     WnetState& S = ctx->wnet;
-    if (!S.d_w) return set_error(ctx, FVN_ERR_STATE, "no two-stage weights (call fvn_load_wnet_weights first)");
+    if (!S.loaded) return set_error(ctx, FVN_ERR_STATE, "no two-stage weights (call fvn_load_wnet_weights first)");
     const fvn_wnet_config& c = S.cfg;
     const int L = c.levels, m = 1 << L;
     const int Wp = (w + m - 1) / m * m, Hp = (h + m - 1) / m * m;
