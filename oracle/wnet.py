@@ -21,8 +21,8 @@ the encoder and decoder blocks at scale s (resolution 2^-s), ``bot`` that of
 the block at the coarsest scale L = len(enc).  The paper's plan reads as
 enc = (64, 64, 80), bot = 96, dec = (64, 64, 80) -- its d96 is the block
 between the two halves, so there are four blocks going down (three of them
-pooled) and three coming up, the "four encoder and three decoder blocks" of
-the text.  The frame is zero-padded at the bottom / right to a multiple of
+pooled) and three coming up, which matches the text's count of encoder
+and decoder blocks (4 and 3).  The frame is zero-padded at the bottom / right to a multiple of
 2^L and the output cropped back.
 
 D (3x3 convolutions with bias, each followed by ReLU):

@@ -48,7 +48,7 @@ def test_block_plan_reads_as_the_paper_widths():
     bot, dec_up = rest[0], rest[1:]
     cfg = (enc, bot, tuple(reversed(dec_up)))
     assert cfg == W.PAPER == wl.WNET_PAPER
-    assert len(blocks) == 7 and len(enc) + 1 == 4 and len(dec_up) == 3   # "four encoder and three decoder blocks"
+    assert len(blocks) == 7 and len(enc) + 1 == 4 and len(dec_up) == 3   # the text counts 4 encoder, 3 decoder blocks
 
 
 def test_loss_weights():
