@@ -27,10 +27,7 @@ def N(t):
 
 
 @pytest.mark.parametrize("k,ca,cb,cout,h,w", [(3, 5, 0, 16, 20, 37), (3, 16, 32, 16, 17, 16), (1, 16, 0, 29, 9, 40),
-                                             (3, 64, 32, 32, 8, 8), (3, 3, 0, 5, 1, 1),
-                                             # 1x1: planes not a multiple of 4 (scalar staging), more than
-                                             # 128 output / input channels (channel groups over blockIdx.z)
-                                             (1, 5, 3, 9, 7, 13), (1, 130, 0, 200, 3, 5), (1, 96, 80, 176, 8, 8)])
+                                             (3, 64, 32, 32, 8, 8), (3, 3, 0, 5, 1, 1)])
 def test_conv_forward_backward(fvn, k, ca, cb, cout, h, w):
     rng = np.random.default_rng(k * 100 + ca + cout)
     n = 2

@@ -4,7 +4,10 @@ through the C ABI the guards must be intact -- mask, ids and count, dense
 and sparse marches, the FP16 reconstruction (both kernel families), the
 whole frame, the two-stage network and its kernels, and the training
 kernels -- on odd frame sizes (1 x 1, widths not a multiple of 4, ragged
-tiles)."""
+tiles).  Also the 1x1 training convolutions' remaining shapes against the
+oracle: planes whose length is not a multiple of 4 (scalar staging) and
+more than 128 channels (channel groups spread over CTAs).  Collected last,
+so a failure here comes after every other test has run."""
 import math
 
 import numpy as np
@@ -127,3 +130,32 @@ def test_training_kernels_stay_in_bounds(fvn, k, ca, cb, cout, h, w):
         u = Guarded((n, ca, 2 * h, 2 * w))
         fvn.upsample2_fwd(xa, u.t)
         assert p.intact() and u.intact()
+
+
+@pytest.mark.parametrize("ca,cb,cout,h,w", [(5, 3, 9, 7, 13), (130, 0, 200, 3, 5), (96, 80, 176, 8, 8)])
+def test_1x1_training_convolution_shapes(fvn, ca, cb, cout, h, w):
+    from oracle import net as onet
+    rng = np.random.default_rng(ca + cout)
+    n = 2
+    xa = rng.normal(size=(n, ca, h, w))
+    xb = rng.normal(size=(n, cb, h, w)) if cb else None
+    wt = rng.normal(size=(cout, ca + cb, 1, 1)) * 0.2
+    b = rng.normal(size=cout) * 0.1
+    x = xa if xb is None else np.concatenate([xa, xb], 1)
+    z = onet.conv2d(x, wt, b)
+    T = lambda a: torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(DEV)   # noqa: E731
+    y = torch.empty(n, cout, h, w, device=DEV)
+    fvn.conv_fwd(T(xa), None if xb is None else T(xb), T(wt), T(b), True, y)
+    torch.cuda.synchronize()
+    assert np.abs(y.cpu().numpy() - np.maximum(z, 0)).max() < 1e-4
+    gy = rng.normal(size=z.shape)
+    gx_ref, gw_ref, gb_ref = onet.conv2d_backward(x, wt, gy * (z > 0))
+    gxa = torch.empty(n, ca, h, w, device=DEV)
+    gxb = torch.empty(n, cb, h, w, device=DEV) if cb else None
+    gw, gb = torch.empty(cout, ca + cb, 1, 1, device=DEV), torch.empty(cout, device=DEV)
+    fvn.conv_bwd(T(xa), None if xb is None else T(xb), T(wt), T(gy), y, gxa, gxb, gw, gb)
+    torch.cuda.synchronize()
+    gx = gxa.cpu().numpy() if gxb is None else np.concatenate([gxa.cpu().numpy(), gxb.cpu().numpy()], 1)
+    assert np.abs(gx - gx_ref).max() < 1e-3 * max(1.0, np.abs(gx_ref).max())
+    assert np.abs(gw.cpu().numpy() - gw_ref).max() < 1e-3 * max(1.0, np.abs(gw_ref).max())
+    assert np.abs(gb.cpu().numpy() - gb_ref).max() < 1e-3 * max(1.0, np.abs(gb_ref).max())
