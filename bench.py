@@ -441,7 +441,7 @@ def run_sweep(nframes=8, densities=(1.0, 0.7, 0.5, 0.3, 0.2, 0.1, 0.05, 0.03, 0.
     return rows
 
 
-def run_shadows(fvn, wl, weights, conv, vol, tf, frames, dev, nframes, flush):
+def run_shadows(fvn, wl, weights, vol, tf, frames, dev, nframes, flush):
     """The paper's renderer setting: Phong lit by a directional light with one
     shadow ray per sample at a quarter of the main sample rate (shading 2),
     on the same orbit frames as the headline, in a context of its own with
@@ -454,7 +454,6 @@ def run_shadows(fvn, wl, weights, conv, vol, tf, frames, dev, nframes, flush):
     c = fvn.Context()
     try:
         c.load_weights(weights)
-        c.set_option(fvn.OPT_CONV_KERNEL, fvn.CONV_TCGEN05 if conv == "tcgen05" else fvn.CONV_MMA_SYNC)
         mp = wl.MarchParams(shading=2, light_dir=wl.LIGHT_DIR, shadow_rate=4)
         cam0, fov0 = frames[0]
         rgb = torch.empty(3, H, W, device=dev)
@@ -1052,8 +1051,7 @@ def main():
         c0 = torch.zeros(1, dtype=torch.int32, device=dev)
         ctx.make_mask(fov, W, H, m0, i0, c0)
         tuned = {"march": autotune.tune_march(ctx, vol, tf, cam, mp, rgbam, ids=i0, count=c0),
-                 "dense_march": autotune.tune_march(ctx, vol, tf, cam, mp, dense),
-                 "conv": autotune.tune_conv(ctx, rgbam, W, H, rgb)}
+                 "dense_march": autotune.tune_march(ctx, vol, tf, cam, mp, dense)}
         ctx.device_status()
 
     # ---- warm-up ---------------------------------------------------------
@@ -1219,8 +1217,7 @@ def main():
 
     shadows = paper_settings = None
     if not args.no_shadows:
-        shadows = run_shadows(fvn, wl, weights, "tcgen05" if (tuned is None or tuned["conv"]["conv"] == "tcgen05")
-                              else "mma_sync", vol, tf, frames, dev, min(args.steps, 16), flush)
+        shadows = run_shadows(fvn, wl, weights, vol, tf, frames, dev, min(args.steps, 16), flush)
         paper_settings = run_paper_settings(fvn, wl, weights, vol, tf, dev, min(args.steps, 16), flush)
 
     blue = recurrent = two_stage = training = None
@@ -1279,10 +1276,9 @@ def main():
             "autotune": tuned,
             "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": int(tf_np.nbytes),
                     "d2h_bytes_per_step": int(3 * H * W * 4)},
-            # per frame: mask, gradient volume, march, then on the tcgen05 path 10
-            # convolutions + 2 up-sampling passes (head / KP / blend in the last
-            # convolution); on the mma.sync path 10 convolutions + a KP kernel
-            "gpu_launches": (15 if (tuned is None or tuned["conv"]["conv"] == "tcgen05") else 14) * args.steps,
+            # per frame: mask, gradient volume, march, then 10 convolutions + 2
+            # up-sampling passes (head / KP / blend in the last convolution)
+            "gpu_launches": 15 * args.steps,
             "cuda_graph": graph_info,
             "fp8": fp8_info,
             "shadows": shadows,

@@ -49,11 +49,19 @@ typedef enum { FVN_PREC_FP16 = 0, FVN_PREC_FP8 = 1 } fvn_precision;
 
 typedef struct fvn_ctx fvn_ctx;
 
-/* Scalar volume; data is a device pointer, 1 <= nx, ny, nz <= 4096. */
+/* Scalar volume; data is a device pointer, 1 <= nx, ny, nz <= 4096.
+ * generation: 0 = the library makes its working copy of the volume (padded
+ * copy, gradient volume or shadow cells, one pass over the volume) on every
+ * march; any other value lets a context reuse the copy it made last for the
+ * same data pointer, sizes, voxel type, generation and kind of copy, so a
+ * static volume is prepared once.  The caller must then change generation
+ * whenever it changes the voxels, and order its calls on the device (one
+ * stream, or events) so that a reuse follows the pass that made the copy. */
 typedef struct {
     const void* data;
     int nx, ny, nz;
     int dtype;                 /* fvn_dtype */
+    uint32_t generation;
 } fvn_volume;
 
 /* 1-D RGBA transfer function: device pointer to n entries of float RGBA
@@ -116,13 +124,11 @@ fvn_status fvn_create(fvn_ctx** out);
 /* Free a context and everything it owns.  Synchronises the device. */
 fvn_status fvn_destroy(fvn_ctx* ctx);
 
-/* Tuning options (fvn_set_option).  Defaults: tcgen05 convolutions, whole
- * 32-ray packets, no cooperative finish, as many march CTAs as fit; with these
- * the march is deterministic (each ray's arithmetic is independent of which
- * rays share its warp).  Every setting computes the same result (the
- * cooperative finish up to FP32 rounding order); the autotuner times them.
- *  FVN_OPT_CONV_KERNEL: 0 = tcgen05 tensor-core convolutions (TMEM
- *      accumulators), 1 = mma.sync convolutions.
+/* Tuning options (fvn_set_option).  Defaults: whole 32-ray packets, no
+ * cooperative finish, as many march CTAs as fit; with these the march is
+ * deterministic (each ray's arithmetic is independent of which rays share
+ * its warp).  Every setting computes the same result (the cooperative finish
+ * up to FP32 rounding order); the autotuner times them.
  *  FVN_OPT_MARCH_REFILL: a sparse-march warp refills idle lanes with new
  *      rays once fewer than this many lanes (1..32) are busy (1 = only whole
  *      32-ray packets).
@@ -148,7 +154,6 @@ fvn_status fvn_destroy(fvn_ctx* ctx);
  * the voxel type -- so that a shadow sample reads two cells instead of
  * eight voxels; the gradient-volume option does not apply to it. */
 enum {
-    FVN_OPT_CONV_KERNEL = 1,
     FVN_OPT_MARCH_REFILL = 2,
     FVN_OPT_MARCH_BLOCKS_PER_SM = 3,
     FVN_OPT_MARCH_REFILL_DENSE = 4,

@@ -49,10 +49,14 @@
  *    the box give bg, A = 0, mask = 1.
  *
  * Ambiguity flags (bit 0: the sample count (t_far - t_near)/dt lies within
- * 2e-3 of an integer; bit 1: A came within 2e-6 of the termination threshold;
+ * 1e-3 of an integer; bit 1: A came within 1e-6 of the termination threshold;
  * bit 2: a shaded sample had |g| < 1e-5) mark pixels where an FP32
  * implementation of the same definition may legitimately take the other side
- * of a discontinuity.  count_shift / term_override let a test compute the
+ * of a discontinuity.  The windows are a few times the largest FP32 / FP64
+ * difference of these quantities met on a foveated 1080p frame (1.6e-4
+ * samples for the count, 4.0e-7 for A): FP32 ray geometry at a few hundred
+ * voxels from the eye, and FP32 compositing over hundreds of steps, cannot
+ * resolve them more finely.  count_shift / term_override let a test compute the
  * alternative result for such pixels.  Shadow rays need no flag: T is
  * continuous in the exit distance, and where FP32 and FP64 disagree on
  * stopping a shadow ray, T differs by less than the 2^-14 cutoff.
@@ -197,7 +201,7 @@ typedef struct {
 } or_mp;
 
 static int64_t march_ray(const or_vol* v, const float* tf, int ntf, const or_cam* c, int px, int py,
-                         const or_mp* m, double term, int count_shift, double* rgba, int* amb) {
+                         const or_mp* m, double term, int count_shift, double* rgba, int* amb, double* mg) {
     const double dt = m->dt;
     const double* bg = m->bg;
     const int shading = m->shading;
@@ -207,6 +211,7 @@ static int64_t march_ray(const or_vol* v, const float* tf, int ntf, const or_cam
     for (int a = 0; a < 3; ++a) d[a] = c->f[a] + sx * c->r[a] + sy * c->u[a];
     normalize3(d);
     *amb = 0;
+    if (mg) mg[0] = mg[1] = INFINITY;
     rgba[0] = bg[0]; rgba[1] = bg[1]; rgba[2] = bg[2]; rgba[3] = 0.0;
 
     double tn = -INFINITY, tfar = INFINITY;
@@ -225,7 +230,8 @@ static int64_t march_ray(const or_vol* v, const float* tf, int ntf, const or_cam
     if (!(tnear < tfar)) return 0;
 
     double span = (tfar - tnear) / dt;
-    if (fabs(span - nearbyint(span)) < 2e-3) *amb |= 1;
+    if (fabs(span - nearbyint(span)) < 1e-3) *amb |= 1;
+    if (mg) mg[0] = fabs(span - nearbyint(span));
     /* number of k >= 0 with tnear + k dt < tfar */
     int64_t nsamp = (int64_t)ceil(span);
     while (nsamp > 0 && tnear + (double)(nsamp - 1) * dt >= tfar) --nsamp;
@@ -281,7 +287,8 @@ static int64_t march_ray(const or_vol* v, const float* tf, int ntf, const or_cam
             C[2] += w * col[2];
             A += w;
         }
-        if (fabs(A - term) < 2e-6) *amb |= 2;
+        if (fabs(A - term) < 1e-6) *amb |= 2;
+        if (mg && fabs(A - term) < mg[1]) mg[1] = fabs(A - term);
         if (A >= term) { ++k; break; }
     }
     rgba[0] = C[0] + (1.0 - A) * bg[0];
@@ -298,12 +305,16 @@ static int64_t march_ray(const or_vol* v, const float* tf, int ntf, const or_cam
  * ids == NULL: every pixel (dense).  Otherwise only the listed pixel ids
  * y*W + x are marched and every other pixel of out is 0.
  * out: [5][H][W] float64 (R, G, B, A, M).  amb: [H*W] or NULL.
+ * margin: [H*W][2] or NULL; per marched pixel the distances behind its
+ * ambiguity flags: |(t_far - t_near) / dt - nearest integer| and the
+ * smallest |A - term| over its composited steps (INFINITY where none);
+ * a diagnostic of the flags, not part of the rendering.
  * term_override > 0 replaces mp's termination threshold.
  * Returns the total number of classified samples.
  */
 int64_t or_march(const void* data, int dtype, int nx, int ny, int nz, const float* tf, int ntf,
                  const double* cam, int W, int H, const double* mp, const int32_t* ids, int64_t nids,
-                 int count_shift, double term_override, double* out, uint8_t* amb) {
+                 int count_shift, double term_override, double* out, uint8_t* amb, double* margin) {
     or_vol v = {data, dtype, {nx, ny, nz}};
     or_cam c;
     setup_camera(cam, W, H, &v, &c);
@@ -321,7 +332,8 @@ int64_t or_march(const void* data, int dtype, int nx, int ny, int nz, const floa
         int px = (int)(pix % W), py = (int)(pix / W);
         double rgba[4];
         int a = 0;
-        total += march_ray(&v, tf, ntf, &c, px, py, &m, term, count_shift, rgba, &a);
+        total += march_ray(&v, tf, ntf, &c, px, py, &m, term, count_shift, rgba, &a,
+                           margin ? margin + 2 * pix : NULL);
         out[0 * npix + pix] = rgba[0];
         out[1 * npix + pix] = rgba[1];
         out[2 * npix + pix] = rgba[2];

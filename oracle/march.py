@@ -41,7 +41,7 @@ def _load():
         lib.or_march.restype = ctypes.c_int64
         lib.or_march.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P, ctypes.c_int,
                                  P, ctypes.c_int, ctypes.c_int, P, P, ctypes.c_int64, ctypes.c_int,
-                                 ctypes.c_double, P, P]
+                                 ctypes.c_double, P, P, P]
         lib.or_trilinear.restype = None
         lib.or_trilinear.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                      ctypes.c_int64, P]
@@ -82,8 +82,11 @@ def _vol_args(vol):
     return vol, DTYPES[vol.dtype], nx, ny, nz
 
 
-def march(vol, tf, cam, mp, ids=None, count_shift=0, term_override=0.0):
-    """Return (out [5, H, W] float64, amb [H, W] uint8, nsamples)."""
+def march(vol, tf, cam, mp, ids=None, count_shift=0, term_override=0.0, margins=False):
+    """Return (out [5, H, W] float64, amb [H, W] uint8, nsamples), and with
+    margins=True also margin [2, H, W]: per marched pixel the distance of the
+    sample count (t_far - t_near) / dt to the nearest integer and the smallest
+    |A - term| over its steps -- the quantities the ambiguity flags test."""
     vol, dt, nx, ny, nz = _vol_args(vol)
     tf = np.ascontiguousarray(tf, dtype=np.float32)
     camv = _cam_array(cam)
@@ -96,8 +99,12 @@ def march(vol, tf, cam, mp, ids=None, count_shift=0, term_override=0.0):
         idp, nids = _ptr(ids), ids.size
     else:
         idp, nids = None, 0
+    mg = np.full((H * W, 2), np.inf, dtype=np.float64) if margins else None
     ns = _load().or_march(_ptr(vol), dt, nx, ny, nz, _ptr(tf), tf.shape[0], _ptr(camv), W, H, _ptr(mpv),
-                          idp, nids, int(count_shift), float(term_override), _ptr(out), _ptr(amb))
+                          idp, nids, int(count_shift), float(term_override), _ptr(out), _ptr(amb),
+                          _ptr(mg) if margins else None)
+    if margins:
+        return out, amb, int(ns), mg.T.reshape(2, H, W).copy()
     return out, amb, int(ns)
 
 

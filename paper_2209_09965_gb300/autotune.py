@@ -6,8 +6,6 @@ Times, with CUDA events on the current stream, the candidate settings of
   lanes of a warp must still be busy before idle lanes take new rays), the
   cooperative-finish threshold (how few rays a warp must have left before it
   marches them with all 32 lanes) and the number of persistent CTAs per SM;
-* the reconstruction convolutions: the tcgen05 (TMEM-accumulator) kernels or
-  the mma.sync kernels;
 
 on the caller's own frame, and installs the fastest in the context with
 fvn_set_option.  Every candidate computes the same result (the cooperative
@@ -56,14 +54,3 @@ def tune_march(ctx: fvn.Context, vol, tf, cam, mp, rgbam, ids=None, count=None,
     ctx.set_option(o_blocks, best[2])
     return {"refill": best[0], "coop": best[1], "blocks_per_sm": best[2], "ms": results[best],
             "candidates": {f"{k[0]}/{k[1]}/{k[2]}": round(v, 4) for k, v in results.items()}}
-
-
-def tune_conv(ctx: fvn.Context, rgbam, w, h, rgb):
-    """Pick the convolution kernels (tcgen05 or mma.sync) for this frame size."""
-    results = {}
-    for name, impl in (("tcgen05", fvn.CONV_TCGEN05), ("mma_sync", fvn.CONV_MMA_SYNC)):
-        ctx.set_option(fvn.OPT_CONV_KERNEL, impl)
-        results[name] = _time(lambda: ctx.reconstruct(rgbam, w, h, rgb))
-    best = min(results, key=results.get)
-    ctx.set_option(fvn.OPT_CONV_KERNEL, fvn.CONV_TCGEN05 if best == "tcgen05" else fvn.CONV_MMA_SYNC)
-    return {"conv": best, "ms": {k: round(v, 4) for k, v in results.items()}}

@@ -127,6 +127,7 @@ extern "C" fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int 
             cudaFree(ws.pad[k]);
             ws.pad[k] = nullptr;
             ws.pad_bytes[k] = 0;
+            ws.pad_key[k] = PreparedKey();
             FVN_CUDA(ctx, cudaMalloc(&ws.pad[k], pb));
             ws.pad_bytes[k] = pb;
         }
@@ -156,7 +157,7 @@ extern "C" fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int 
     for (int i = 0; i < nviews; ++i)
         FVN_CUDA(ctx, cudaMemsetAsync(rgbam[i], 0, 5 * sizeof(float) * (size_t)w[i] * h[i], st));
     for (int k = 0; k < nvol; ++k)
-        if ((s = march_volume_prepare(ctx, vols[k], mp, ws.pad[k], st)) != FVN_OK) return s;
+        if ((s = march_volume_prepare_cached(ctx, vols[k], mp, ws.pad[k], ws.pad_key[k], st)) != FVN_OK) return s;
 
     // ---- one persistent march over every view's rays -----------------------
     BatchMarchView mv[kMaxViews];
@@ -166,22 +167,14 @@ extern "C" fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int 
     if ((s = march_batch_impl(ctx, mv, nviews, mp, nsamples, st)) != FVN_OK) return s;
 
     // ---- network: one launch per layer over every view's tiles ------------
-    if (ctx->conv_impl == CONV_TCGEN05 || precision == FVN_PREC_FP8) {
-        ReconView rv[kMaxViews];
-        for (int i = 0; i < nviews; ++i) {
-            plan_view(w[i], h[i], &rv[i].plan, base + lay[i].plan);
-            rv[i].rgbam = rgbam[i];
-            rv[i].w = w[i];
-            rv[i].h = h[i];
-            rv[i].rgb = views[i].rgb;
-            rv[i].prev = views[i].prev_rgb;
-        }
-        return reconstruct_tc_views(ctx, rv, nviews, precision, st);
+    ReconView rv[kMaxViews];
+    for (int i = 0; i < nviews; ++i) {
+        plan_view(w[i], h[i], &rv[i].plan, base + lay[i].plan);
+        rv[i].rgbam = rgbam[i];
+        rv[i].w = w[i];
+        rv[i].h = h[i];
+        rv[i].rgb = views[i].rgb;
+        rv[i].prev = views[i].prev_rgb;
     }
-    for (int i = 0; i < nviews; ++i)   // mma.sync convolutions: one network pass per view
-        if ((s = reconstruct_on(ctx, base + lay[i].plan, rgbam[i], views[i].prev_rgb, w[i], h[i], precision,
-                                views[i].rgb, st)) !=
-            FVN_OK)
-            return s;
-    return FVN_OK;
+    return reconstruct_tc_views(ctx, rv, nviews, precision, st);
 }

@@ -8,6 +8,7 @@
 #include <stdint.h>
 #include <stdio.h>
 
+#include <atomic>
 #include <string>
 #include <vector>
 
@@ -72,6 +73,19 @@ struct ReconView {
     const float* prev = nullptr;      // recurrent model: previous output [3][h][w] (NULL: zeros)
 };
 
+// The source of a prepared volume copy (padded copy, gradient volume or
+// shadow cells): the copy is reused while a volume with a non-zero
+// generation names the same data, sizes, voxel type, generation and kind.
+struct PreparedKey {
+    const void* data = nullptr;
+    int nx = 0, ny = 0, nz = 0, dtype = -1, kind = -1;
+    uint32_t generation = 0;          // 0: nothing reusable
+    bool matches(const fvn_volume* v, int k) const {
+        return generation != 0 && v->generation == generation && v->data == data && v->nx == nx &&
+               v->ny == ny && v->nz == nz && v->dtype == dtype && k == kind;
+    }
+};
+
 // Workspace of fvn_render_batch, one allocation carved per view.
 struct BatchWorkspace {
     size_t bytes = 0;
@@ -79,6 +93,7 @@ struct BatchWorkspace {
     int32_t* counts = nullptr;        // per-view sampled-pixel counts
     void* pad[kMaxBatchVolumes] = {}; // padded volume copies
     size_t pad_bytes[kMaxBatchVolumes] = {};
+    PreparedKey pad_key[kMaxBatchVolumes];
 };
 
 // Two-stage network: configuration, FP32 weights on the device (the flat
@@ -93,8 +108,6 @@ struct WnetState {
     size_t ws_bytes = 0;
     int ws_w = 0, ws_h = 0;           // padded frame the workspace was carved for
 };
-
-enum ConvImpl { CONV_TCGEN05 = 0, CONV_MMA_SYNC = 1 };
 
 // Activation tensors with an FP8 scale (per tensor, from calibration).
 enum Fp8Tensor {
@@ -131,11 +144,9 @@ struct fvn_ctx {
     bool has_weights = false;
     bool recurrent = false;           // the loaded weights take the previous output as input
     fvn::ConvW layers[fvn::kNumLayers];
-    float* head_w = nullptr;          // FP32 [29][16] + [29] bias for the head / KP stage
     __half* head_w16 = nullptr;       // head weights as a tensor-core operand: [2][32][8] FP16 (rows 29-31 zero)
     float* head_b32 = nullptr;        // head bias padded to 32
     int* d_error = nullptr;           // device-side error flag (a bounded wait gave up)
-    int conv_impl = fvn::CONV_TCGEN05;
     std::vector<float> host_weights;  // FP32 weights as loaded (re-quantised at FP8 calibration)
     bool has_fp8 = false;
     float fp8_amax[fvn::FP8_NT] = {};
@@ -153,6 +164,7 @@ struct fvn_ctx {
     int noise_log2 = 0, noise_frames = 0;
     void* pad_buf = nullptr;          // padded copy of the volume read by the march
     size_t pad_bytes = 0;
+    fvn::PreparedKey pad_key;         // what pad_buf holds
     float* d_act_scale = nullptr;     // FP8 per-layer activation scales
     fvn::ReconWorkspace recon_ws;
     fvn::RenderWorkspace render_ws;
@@ -162,6 +174,19 @@ struct fvn_ctx {
 };
 
 namespace fvn {
+
+// A kernel that uses more than 48 KB of dynamic shared memory must opt in,
+// once per device (the attribute belongs to the device's copy of the
+// kernel).  `done` is the kernel's own record of the devices already set up
+// (bit d for device d < 64; higher device indices set it on every call).
+template <typename K>
+inline cudaError_t opt_in_smem(const fvn_ctx* ctx, K kern, int bytes, std::atomic<unsigned long long>& done) {
+    const unsigned long long bit = ctx->device < 64 ? 1ull << ctx->device : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
+    return e;
+}
 
 fvn_status set_error(fvn_ctx* ctx, fvn_status st, const char* fmt, ...);
 
@@ -217,6 +242,10 @@ bool march_uses_grad4(const fvn_ctx* ctx, const fvn_volume* vol, const fvn_march
 size_t march_volume_bytes(const fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp);
 fvn_status march_volume_prepare(fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp, void* buf,
                                 cudaStream_t st);
+// march_volume_prepare unless `key` says buf already holds that copy (the
+// volume's generation is non-zero and unchanged); records the new source.
+fvn_status march_volume_prepare_cached(fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp, void* buf,
+                                       PreparedKey& key, cudaStream_t st);
 // Masks and id lists of n views in one launch: view i writes mask[i] and its
 // ids at ids[i], its count at counts[i] (counts zeroed here).
 fvn_status make_mask_batch_impl(fvn_ctx* ctx, const fvn_foveation* const* fov, const int* w, const int* h,

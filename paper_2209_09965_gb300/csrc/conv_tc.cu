@@ -600,11 +600,8 @@ template <int CIN, int CG, int COUT, int TR, int MODE, int EPI, int CUP, bool F8
 static fvn_status launch_tc(fvn_ctx* ctx, TcArgs& a, cudaStream_t st) {
     using L = TcLayout<CIN, CG, COUT, TR, MODE, EPI, CUP, F8>;
     auto kern = conv3x3_tc_kernel<CIN, CG, COUT, TR, MODE, EPI, CUP, F8>;
-    static bool configured = false;
-    if (!configured) {
-        FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};
+    FVN_CUDA(ctx, opt_in_smem(ctx, kern, (int)L::bytes, configured));
     // CTAs per SM from the shared-memory budget (1 KB reserved per CTA) and
     // the 512 TMEM columns, so that no CTA ever waits in tcgen05.alloc.
     int smem_sm = 0;
@@ -699,11 +696,8 @@ static fvn_status launch_ws(fvn_ctx* ctx, const WsSpec* spec, int n, const ConvW
     static_assert(L::bytes <= 227 * 1024, "stage ring does not fit in shared memory");
     static_assert(sizeof(ws::Args) <= 32764, "kernel arguments exceed the parameter space");
     auto kern = ws::conv3x3_ws_kernel<CIN, CHG, CH0, COUT, TR, NS, POOL, F8, FUSE>;
-    static bool configured = false;
-    if (!configured) {
-        FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};
+    FVN_CUDA(ctx, opt_in_smem(ctx, kern, (int)L::bytes, configured));
     int smem_sm = 0;
     FVN_CUDA(ctx, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
     int per_sm = smem_sm / (int)(L::bytes + 1024);
@@ -777,11 +771,8 @@ static fvn_status launch_ws_headkp(fvn_ctx* ctx, const ReconView* views, int n, 
     static_assert(L::bytes <= 227 * 1024, "head / kernel-prediction kernel does not fit in shared memory");
     static_assert(sizeof(ws::HkArgs) <= 32764, "kernel arguments exceed the parameter space");
     auto kern = ws::conv3x3_ws_headkp_kernel<CIN, 16 / CPC, TR, NS, F8>;
-    static bool configured = false;
-    if (!configured) {
-        FVN_CUDA(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes));
-        configured = true;
-    }
+    static std::atomic<unsigned long long> configured{0};
+    FVN_CUDA(ctx, opt_in_smem(ctx, kern, (int)L::bytes, configured));
     const ConvW& w = ctx->layers[9];
     ws::HkArgs h{};
     ws::Args& a = h.conv;

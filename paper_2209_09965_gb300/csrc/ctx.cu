@@ -113,7 +113,6 @@ extern "C" fvn_status fvn_destroy(fvn_ctx* ctx) {
         cudaFree(L.scale8);
         cudaFree(L.bias);
     }
-    cudaFree(ctx->head_w);
     cudaFree(ctx->head_w16);
     cudaFree(ctx->head_b32);
     cudaFree(ctx->d_error);
@@ -146,10 +145,6 @@ extern "C" const char* fvn_last_error(const fvn_ctx* ctx) {
 extern "C" fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value) {
     if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
     switch (option) {
-        case FVN_OPT_CONV_KERNEL:
-            FVN_CHECK_ARG(ctx, value == CONV_TCGEN05 || value == CONV_MMA_SYNC, "conv kernel must be 0 or 1");
-            ctx->conv_impl = value;
-            return FVN_OK;
         case FVN_OPT_MARCH_REFILL:
             FVN_CHECK_ARG(ctx, value >= 1 && value <= 32, "refill threshold must be in [1, 32]");
             ctx->march_refill = value;

@@ -1322,12 +1322,14 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
         cudaFree(ctx->pad_buf);
         ctx->pad_buf = nullptr;
         ctx->pad_bytes = 0;
+        ctx->pad_key = PreparedKey();
         FVN_CUDA(ctx, cudaMalloc(&ctx->pad_buf, bytes));
         ctx->pad_bytes = bytes;
     }
     a.pvol = ctx->pad_buf;
     a.svol = march_cells(ctx, vol, mp, ctx->pad_buf);
-    fvn_status ps = march_volume_prepare(ctx, vol, mp, ctx->pad_buf, st);   // one pass over the volume
+    // one pass over the volume, skipped while a non-zero generation says the copy is current
+    fvn_status ps = march_volume_prepare_cached(ctx, vol, mp, ctx->pad_buf, ctx->pad_key, st);
     if (ps != FVN_OK) return ps;
     const bool big = padded_voxels(vol) >= (1ull << 31);
     const int shade = mp->shading;
@@ -1400,6 +1402,29 @@ fvn_status march_volume_prepare(fvn_ctx* ctx, const fvn_volume* vol, const fvn_m
         case FVN_F16: return prepare_as<__half>(ctx, vol, mp, buf, g4, st);
         default: return prepare_as<float>(ctx, vol, mp, buf, g4, st);
     }
+}
+
+// Kind of copy a march reads: 0 padded copy, 1 gradient volume, 2 padded
+// copy + shadow cells.
+static int volume_kind(const fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp) {
+    return march_uses_grad4(ctx, vol, mp) ? 1 : (uses_cells(ctx, mp) ? 2 : 0);
+}
+
+fvn_status march_volume_prepare_cached(fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp, void* buf,
+                                       PreparedKey& key, cudaStream_t st) {
+    const int kind = volume_kind(ctx, vol, mp);
+    if (key.matches(vol, kind)) return FVN_OK;
+    key = PreparedKey();
+    const fvn_status s = march_volume_prepare(ctx, vol, mp, buf, st);
+    if (s != FVN_OK || vol->generation == 0) return s;
+    key.data = vol->data;
+    key.nx = vol->nx;
+    key.ny = vol->ny;
+    key.nz = vol->nz;
+    key.dtype = vol->dtype;
+    key.kind = kind;
+    key.generation = vol->generation;
+    return FVN_OK;
 }
 
 fvn_status march_batch_impl(fvn_ctx* ctx, const BatchMarchView* views, int n, const fvn_march_params* mp,

@@ -37,12 +37,11 @@ EXPORTS = (
 )
 WNET_MAX_LEVELS = 4
 MAX_VIEWS = 16
-OPT_CONV_KERNEL, OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 1, 2, 3
+OPT_MARCH_REFILL, OPT_MARCH_BLOCKS_PER_SM = 2, 3
 OPT_MARCH_REFILL_DENSE, OPT_MARCH_BLOCKS_PER_SM_DENSE = 4, 5
 OPT_MARCH_COOP, OPT_MARCH_COOP_DENSE = 6, 7
 OPT_MARCH_GRADIENT_VOLUME = 8
 OPT_MARCH_COUNT_SHADOW = 9
-CONV_TCGEN05, CONV_MMA_SYNC = 0, 1
 
 
 class FvnError(RuntimeError):
@@ -53,7 +52,7 @@ class FvnError(RuntimeError):
 
 class Volume(ctypes.Structure):
     _fields_ = [("data", ctypes.c_void_p), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
-                ("dtype", ctypes.c_int)]
+                ("dtype", ctypes.c_int), ("generation", ctypes.c_uint32)]
 
 
 class TF(ctypes.Structure):
@@ -187,12 +186,14 @@ if hasattr(torch, "uint16"):
     _DTYPE[torch.uint16] = U16
 
 
-def volume(t: torch.Tensor) -> Volume:
-    """Descriptor of a [nz, ny, nx] CUDA volume (uint16 may be carried as int16)."""
+def volume(t: torch.Tensor, generation: int = 0) -> Volume:
+    """Descriptor of a [nz, ny, nx] CUDA volume (uint16 may be carried as
+    int16).  generation != 0 lets the library reuse its prepared copy of an
+    unchanged volume (change it whenever the voxels change)."""
     if t.dim() != 3 or t.dtype not in _DTYPE:
         raise ValueError("volume must be a 3-D uint8 / uint16 / float16 / float32 CUDA tensor")
     nz, ny, nx = t.shape
-    return Volume(_ptr(t, None), nx, ny, nz, _DTYPE[t.dtype])
+    return Volume(_ptr(t, None), nx, ny, nz, _DTYPE[t.dtype], int(generation) & 0xFFFFFFFF)
 
 
 def transfer_function(t: torch.Tensor) -> TF:
@@ -291,15 +292,15 @@ class Context:
         self._chk(lib.fvn_make_mask(self.h, ctypes.byref(foveation(fov)), int(w), int(h), _ptr(mask, torch.uint8),
                                     _ptr(ids, torch.int32), _ptr(count, torch.int32), _stream(stream)))
 
-    def march(self, vol, tf, cam, mp, rgbam, ids=None, count=None, nsamples=None, stream=None):
-        v, t, c, m = volume(vol), transfer_function(tf), camera(cam), march_params(mp)
+    def march(self, vol, tf, cam, mp, rgbam, ids=None, count=None, nsamples=None, stream=None, generation=0):
+        v, t, c, m = volume(vol, generation), transfer_function(tf), camera(cam), march_params(mp)
         self._chk(lib.fvn_march(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c), ctypes.byref(m),
                                 _ptr(ids, torch.int32), _ptr(count, torch.int32), _ptr(rgbam),
                                 _ptr(nsamples, torch.int64), _stream(stream)))
 
-    def march_masked(self, vol, tf, cam, mp, mask, rgbam, nsamples=None, stream=None):
+    def march_masked(self, vol, tf, cam, mp, mask, rgbam, nsamples=None, stream=None, generation=0):
         """Naive rejection: dense ray numbering, pixels with mask 0 skipped in place."""
-        v, t, c, m = volume(vol), transfer_function(tf), camera(cam), march_params(mp)
+        v, t, c, m = volume(vol, generation), transfer_function(tf), camera(cam), march_params(mp)
         self._chk(lib.fvn_march_masked(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c), ctypes.byref(m),
                                        _ptr(mask, torch.uint8), _ptr(rgbam), _ptr(nsamples, torch.int64),
                                        _stream(stream)))
@@ -327,9 +328,9 @@ class Context:
                                                     _ptr(rgb), _stream(stream)))
 
     def render_adaptive(self, vol, tf, cam, fov, mp, rgb, min_psnr_db=35.0, max_levels=3, precision=PREC_FP16,
-                        stream=None):
+                        stream=None, generation=0):
         """fvn_render with the denser-mask fallback; returns (levels, PSNR estimate)."""
-        v, t, c, m = volume(vol), transfer_function(tf), camera(cam), march_params(mp)
+        v, t, c, m = volume(vol, generation), transfer_function(tf), camera(cam), march_params(mp)
         f = foveation(fov)
         lvl = ctypes.c_int(0)
         est = ctypes.c_float(0.0)
@@ -348,9 +349,11 @@ class Context:
         self._chk(lib.fvn_reconstruct_noalloc(self.h, _ptr(rgbam), int(w), int(h), int(precision), _ptr(rgb),
                                               _stream(stream)))
 
-    def render(self, vol, tf, cam, fov, mp, rgb, precision=PREC_FP16, rgbam_out=None, stream=None, prev=None):
-        """prev: the previous output [3, h, w] for the recurrent network (fvn_render_recurrent)."""
-        v, t, c, m = volume(vol), transfer_function(tf), camera(cam), march_params(mp)
+    def render(self, vol, tf, cam, fov, mp, rgb, precision=PREC_FP16, rgbam_out=None, stream=None, prev=None,
+               generation=0):
+        """prev: the previous output [3, h, w] for the recurrent network (fvn_render_recurrent).
+        generation != 0: reuse the prepared copy of an unchanged volume (fvn_volume.generation)."""
+        v, t, c, m = volume(vol, generation), transfer_function(tf), camera(cam), march_params(mp)
         f = foveation(fov)
         if prev is None:
             self._chk(lib.fvn_render(self.h, ctypes.byref(v), ctypes.byref(t), ctypes.byref(c), ctypes.byref(f),
@@ -363,8 +366,9 @@ class Context:
     def render_batch(self, views, mp, precision=PREC_FP16, nsamples=None, stream=None):
         """fvn_render for several views in one pass.  ``views`` is a list of
         dicts with keys vol, tf (CUDA tensors), cam, fov and rgb (CUDA
-        [3, h, w] float32), optionally rgbam (CUDA [5, h, w] float32) and
-        prev (the view's previous output, recurrent network)."""
+        [3, h, w] float32), optionally rgbam (CUDA [5, h, w] float32),
+        prev (the view's previous output, recurrent network) and generation
+        (of the view's volume, see fvn_volume)."""
         n = len(views)
         arr = (ViewC * max(n, 1))()
         keep = []   # descriptors referenced by pointer must outlive the call
@@ -373,7 +377,7 @@ class Context:
             vt, tt = v["vol"], v["tf"]
             kv = (vt.data_ptr(), tuple(vt.shape), vt.dtype)
             if kv not in vol_desc:
-                vol_desc[kv] = volume(vt)
+                vol_desc[kv] = volume(vt, v.get("generation", 0))
             kt = (tt.data_ptr(), tuple(tt.shape))
             if kt not in tf_desc:
                 tf_desc[kt] = transfer_function(tt)

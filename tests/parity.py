@@ -5,16 +5,22 @@ from oracle import march as om
 
 MARCH_TOL = 1e-4          # max-abs per channel, FP32 march vs FP64 oracle
 GRAD_TOL = 1e-3           # pixels whose shading saw a near-zero gradient
+AMB_FRAC = 0.02           # flagged rays allowed: 2 % of the compared rays ...
+AMB_MIN = 6               # ... or 6 rays when fewer than 300 are compared
 
 
-def march_parity(vol, tf, cam, mp, gpu_rgbam, ids=None, tol=MARCH_TOL, max_amb_frac=0.01):
+def march_parity(vol, tf, cam, mp, gpu_rgbam, ids=None, tol=MARCH_TOL):
     """Compare a GPU march with the oracle at ``ids`` (all pixels if None).
 
     Unflagged pixels must agree within ``tol``.  Pixels where the oracle
-    flags a discrete FP32/FP64 ambiguity (sample count at an integer,
-    termination at the threshold; bits 0-1) may take either side and must
-    then match one of the oracle's alternative results; they may be at most
-    ``max_amb_frac`` of the pixels.  Pixels flagged only for a near-zero
+    flags a discrete FP32/FP64 ambiguity (sample count within 1e-3 of an
+    integer, termination within 1e-6 of the threshold; bits 0-1) may take
+    either side and must then match one of the oracle's alternative results;
+    they may be at most 2 % of the compared pixels (at least 6 allowed, so
+    small comparisons have a floor against counting noise).  On a foveated
+    1080p frame the windows flag about 1.3 % of the rays (0.16 % by the count,
+    1.1 % by termination), of which 0.06 % take the other side, with margins
+    of at most 1.6e-4 and 4.0e-7 (test_march_ambiguity_margins_1080p).  Pixels flagged only for a near-zero
     gradient (bit 2: the shading normal is ill-conditioned, or exactly zero in
     flat regions) must agree within GRAD_TOL.
     Returns (max error over unflagged pixels, number of discrete-ambiguous pixels).
@@ -33,7 +39,7 @@ def march_parity(vol, tf, cam, mp, gpu_rgbam, ids=None, tol=MARCH_TOL, max_amb_f
     assert clean_err < tol, f"march error {clean_err} at unambiguous pixels"
     if grad.any():
         assert err[grad].max() < GRAD_TOL, f"march error {err[grad].max()} at near-zero-gradient pixels"
-    assert disc.mean() <= max_amb_frac, f"{disc.mean():.4f} of pixels ambiguous"
+    assert disc.sum() <= max(AMB_FRAC * disc.size, AMB_MIN), f"{disc.mean():.4f} of pixels ambiguous"
     bad = sel[(err >= tol) & disc]
     if bad.size:
         bad32 = bad.astype(np.int32)

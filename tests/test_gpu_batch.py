@@ -24,10 +24,9 @@ def fvn():
     return f
 
 
-@pytest.fixture(scope="module", params=["tcgen05", "mma_sync"])
-def ctx(fvn, request):
+@pytest.fixture(scope="module")
+def ctx(fvn):
     c = fvn.Context()
-    c.set_option(fvn.OPT_CONV_KERNEL, fvn.CONV_TCGEN05 if request.param == "tcgen05" else fvn.CONV_MMA_SYNC)
     c.load_weights(wl.net_weights(3))
     yield c
     c.device_status()
@@ -114,7 +113,7 @@ def test_batch_sparse_frames_match_oracle(ctx, fvn):
         assert np.array_equal(got[4].reshape(-1) != 0, m.reshape(-1) != 0), "batch mask differs from the oracle"
         unsampled = m.reshape(-1) == 0
         assert np.all(got.reshape(5, -1)[:, unsampled] == 0.0)
-        march_parity(host[vi], tfs[ti], v["cam"], mp, got, ids=ids, max_amb_frac=0.05)
+        march_parity(host[vi], tfs[ti], v["cam"], mp, got, ids=ids)
 
 
 def test_batch_fp8_equals_single_views(ctx, fvn):

@@ -104,7 +104,7 @@ def test_render_and_batch_with_tiles(fvn):
                                         f.frame, noise=tiles)
             got = rgbam.cpu().numpy()
             assert np.array_equal(got[4] != 0, m != 0)
-            march_parity(vol_np, tf_np, v["cam"], mp, got, ids=ids, max_amb_frac=0.05)
+            march_parity(vol_np, tf_np, v["cam"], mp, got, ids=ids)
         c.device_status()
     finally:
         c.close()

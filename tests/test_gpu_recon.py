@@ -22,10 +22,9 @@ def fvn():
     return f
 
 
-@pytest.fixture(scope="module", params=["tcgen05", "mma_sync"])
-def ctx(fvn, request):
+@pytest.fixture(scope="module")
+def ctx(fvn):
     c = fvn.Context()
-    c.set_option(fvn.OPT_CONV_KERNEL, fvn.CONV_TCGEN05 if request.param == "tcgen05" else fvn.CONV_MMA_SYNC)
     c.load_weights(wl.net_weights(3))
     yield c
     c.device_status()          # no bounded tensor-core wait gave up
@@ -61,10 +60,8 @@ def test_recon_fp16_matches_oracle(ctx, h, w, seed):
     assert np.abs(out - ref).max() < FP16_TOL
 
 
-@pytest.mark.parametrize("impl", [0, 1])
-def test_recon_other_weights(fvn, impl):
+def test_recon_other_weights(fvn):
     c = fvn.Context()
-    c.set_option(fvn.OPT_CONV_KERNEL, impl)
     w = wl.net_weights(11)
     rng = np.random.default_rng(12)
     w = (w + rng.normal(size=w.size).astype(np.float32) * 0.02).astype(np.float32)   # non-zero biases too

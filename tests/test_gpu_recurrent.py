@@ -28,10 +28,9 @@ def rec_weights(seed=3, scale=0.3):
     return wl.recurrent_weights(wl.net_weights(seed), history_scale=scale, seed=seed + 100)
 
 
-@pytest.fixture(scope="module", params=["tcgen05", "mma_sync"])
-def ctx(fvn, request):
+@pytest.fixture(scope="module")
+def ctx(fvn):
     c = fvn.Context()
-    c.set_option(fvn.OPT_CONV_KERNEL, fvn.CONV_TCGEN05 if request.param == "tcgen05" else fvn.CONV_MMA_SYNC)
     c.load_weights(rec_weights())
     yield c
     c.device_status()

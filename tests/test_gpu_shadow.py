@@ -76,10 +76,10 @@ def test_shadow_dtypes(ctx, fvn, grad_volume, dtype):
     try:
         ctx.set_option(fvn.OPT_MARCH_GRADIENT_VOLUME, grad_volume)    # does not apply to shadowed marches
         out, _ = run_march(ctx, vol_t, tf, cam, mp)
-        march_parity(vol, tf, cam, mp, out, max_amb_frac=0.05)
+        march_parity(vol, tf, cam, mp, out)
         ids = np.arange(1, 80 * 56, 3, dtype=np.int32)
         outs, _ = run_march(ctx, vol_t, tf, cam, mp, ids=ids)
-        march_parity(vol, tf, cam, mp, outs, ids=ids, max_amb_frac=0.05)
+        march_parity(vol, tf, cam, mp, outs, ids=ids)
     finally:
         ctx.set_option(fvn.OPT_MARCH_GRADIENT_VOLUME, 1)
 
@@ -100,7 +100,7 @@ def test_shadow_tiny_grids_random_cameras_and_lights(ctx, n, seed):
         cam = wl.Camera(eye=eye, target=(0.02, -0.03, 0.01), up=(0, 1, 0), fov_y_deg=60.0, width=13, height=9)
         mp = shadow_params([4, 1, 2, 4][k], light=lights[k], term=0.95, bg=(0.1, 0.2, 0.3))
         out, _ = run_march(ctx, vol, tf, cam, mp)
-        march_parity(vol, tf, cam, mp, out, max_amb_frac=0.05)
+        march_parity(vol, tf, cam, mp, out)
 
 
 @pytest.mark.parametrize("coop", [4, 32])
@@ -126,7 +126,7 @@ def test_shadow_sparse_1080p_sampled(ctx):
     _, ids, _ = omask.make_mask(1920, 1080, fov.focal_px, seed=fov.seed, frame=fov.frame)
     out, ns = run_march(ctx, vol, tf, cam, mp, ids=ids)
     sample = np.sort(np.random.default_rng(4).choice(ids, 4000, replace=False)).astype(np.int32)
-    march_parity(vol, tf, cam, mp, out, ids=sample, max_amb_frac=0.05)
+    march_parity(vol, tf, cam, mp, out, ids=sample)
     flat = out.reshape(5, -1)
     rest = np.setdiff1d(np.arange(1920 * 1080), ids)
     assert np.all(flat[:, rest] == 0.0) and np.all(flat[4, ids] == 1.0)
@@ -175,8 +175,7 @@ def test_shadow_batch_equals_single_views(fvn):
             f = v["fov"]
             w, h = v["cam"].width, v["cam"].height
             _, ids, _ = omask.make_mask(w, h, f.focal_px, f.fovea_radius, f.falloff_sigma, f.p_base, f.seed, f.frame)
-            march_parity(host[i % 2], v["tf"].cpu().numpy(), v["cam"], mp, v["rgbam"].cpu().numpy(), ids=ids,
-                         max_amb_frac=0.05)
+            march_parity(host[i % 2], v["tf"].cpu().numpy(), v["cam"], mp, v["rgbam"].cpu().numpy(), ids=ids)
         c.device_status()
     finally:
         c.close()

@@ -13,8 +13,6 @@ from paper_2209_09965_gb300 import workloads as wl
 
 pytestmark = pytest.mark.gpu
 
-FP16_TOL = 2e-2     # the tolerance of the reconstruction parity tests
-
 
 @pytest.fixture(scope="module")
 def fvn():
@@ -33,22 +31,32 @@ def sparse(h, w, seed, density=0.2):
     return torch.from_numpy(sp).cuda()
 
 
-def test_noalloc_matches_reconstruct_on_two_calls(fvn):
-    ctx = fvn.Context()
-    ctx.load_weights(wl.net_weights(3))
+def _noalloc(fvn, ctx, x, w, h, out, precision):
     lib = fvn.lib
     stream = ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    st = lib.fvn_reconstruct_noalloc(ctx.h, ctypes.c_void_p(x.data_ptr()), w, h, precision,
+                                     ctypes.c_void_p(out.data_ptr()), stream)
+    assert st == 0, lib.fvn_last_error(ctx.h)
+
+
+@pytest.mark.parametrize("precision", ["fp16", "fp8"])
+def test_noalloc_matches_reconstruct_on_two_calls(fvn, precision):
+    """Same kernels and weights as fvn_reconstruct, only another workspace:
+    the outputs must be identical bit for bit, on two calls in a row (the
+    second reuses the array the first left behind)."""
+    ctx = fvn.Context()
+    ctx.load_weights(wl.net_weights(3))
+    prec = fvn.PREC_FP16 if precision == "fp16" else fvn.PREC_FP8
+    if prec == fvn.PREC_FP8:
+        ctx.calibrate_fp8(sparse(256, 320, 9), 320, 256)
     for call, (h, w, seed) in enumerate([(120, 200, 1), (512, 512, 2)]):
         x = sparse(h, w, seed)
         ref = torch.empty(3, h, w, device="cuda")
         out = torch.full((3, h, w), float("nan"), device="cuda")
-        ctx.reconstruct(x, w, h, ref)
-        st = lib.fvn_reconstruct_noalloc(ctx.h, ctypes.c_void_p(x.data_ptr()), w, h, fvn.PREC_FP16,
-                                         ctypes.c_void_p(out.data_ptr()), stream)
-        assert st == 0, lib.fvn_last_error(ctx.h)
+        ctx.reconstruct(x, w, h, ref, precision=prec)
+        _noalloc(fvn, ctx, x, w, h, out, prec)
         torch.cuda.synchronize()
-        err = (out - ref).abs().max().item()
-        assert err < FP16_TOL, (call, err)
+        assert torch.equal(out, ref), (precision, call, (out - ref).abs().max().item())
     ctx.close()
 
 
