@@ -200,6 +200,31 @@ __device__ __forceinline__ int floor_frac(float x, float& frac) {
 
 __device__ __forceinline__ float lerpf(float a, float b, float t) { return fmaf(t, b - a, a); }
 
+// Packed FP32 pairs (the f32x2 instructions of this architecture): one
+// instruction computes both lanes with the same IEEE operations as two
+// scalar ones, so lerp2 gives bit for bit the two lerpf results.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) {
+    float2 d;
+    asm("{\n.reg .b64 ra, rb, rc, rd;\n"
+        "mov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\nmov.b64 rc, {%6, %7};\n"
+        "fma.rn.f32x2 rd, ra, rb, rc;\nmov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y), "f"(c.x), "f"(c.y));
+    return d;
+}
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) {
+    float2 d;
+    asm("{\n.reg .b64 ra, rb, rd;\n"
+        "mov.b64 ra, {%2, %3};\nmov.b64 rb, {%4, %5};\n"
+        "sub.rn.f32x2 rd, ra, rb;\nmov.b64 {%0, %1}, rd;\n}"
+        : "=f"(d.x), "=f"(d.y)
+        : "f"(a.x), "f"(a.y), "f"(b.x), "f"(b.y));
+    return d;
+}
+__device__ __forceinline__ float2 lerp2(float2 a, float2 b, float2 t) { return fma2(t, sub2(b, a), a); }
+__device__ __forceinline__ float2 lo2(const float4& v) { return make_float2(v.x, v.y); }
+__device__ __forceinline__ float2 hi2(const float4& v) { return make_float2(v.z, v.w); }
+
 // Ray state of one lane.
 struct Ray {
     int pix;                     // pixel id, < 0 when the lane is idle
@@ -647,38 +672,57 @@ struct Grad4Src {
                 S.c[z][y][1] = __ldg(r + 1);
             }
     }
+    // The trilinear interpolation of all four channels (value and the three
+    // half differences) as packed pairs, in the order of the scalar
+    // definition (x, then y, then z); the TF colour and opacity likewise.  No
+    // branch depends on the sample, so the two samples of a step interleave.
     template <int SHADE, typename I>
     __device__ static __forceinline__ float shade(const MarchArgs& a, const Light& lt, const V* __restrict__ vol,
                                                   const float4* s_tf, float tfmax, I sy, I sz, const St& S, float ux,
                                                   float uy, float uz, float dx, float dy, float dz, float& cr,
                                                   float& cg, float& cb, unsigned& nsh) {
-        float rows[2][2];
+        const float2 tx = make_float2(S.tx, S.tx), ty = make_float2(S.ty, S.ty), tz = make_float2(S.tz, S.tz);
+        float2 lo[2][2], hi[2][2];
 #pragma unroll
         for (int z = 0; z < 2; ++z)
 #pragma unroll
-            for (int y = 0; y < 2; ++y) rows[z][y] = lerpf(S.c[z][y][0].x, S.c[z][y][1].x, S.tx);
-        const float v = lerpf(lerpf(rows[0][0], rows[0][1], S.ty), lerpf(rows[1][0], rows[1][1], S.ty), S.tz);
-        const float al = tf_lookup(a, s_tf, tfmax, v, cr, cg, cb);
-        if (SHADE != 0 && al > 0.0f) {
-            float gr[3][2][2];
-#pragma unroll
-            for (int z = 0; z < 2; ++z)
-#pragma unroll
-                for (int y = 0; y < 2; ++y) {
-                    gr[0][z][y] = lerpf(S.c[z][y][0].y, S.c[z][y][1].y, S.tx);
-                    gr[1][z][y] = lerpf(S.c[z][y][0].z, S.c[z][y][1].z, S.tx);
-                    gr[2][z][y] = lerpf(S.c[z][y][0].w, S.c[z][y][1].w, S.tx);
-                }
-            float g[3];
-#pragma unroll
-            for (int c = 0; c < 3; ++c)
-                g[c] = lerpf(lerpf(gr[c][0][0], gr[c][0][1], S.ty), lerpf(gr[c][1][0], gr[c][1][1], S.ty), S.tz);
-            light_sample<Grad4Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, g[0], g[1], g[2], ux, uy, uz, dx, dy,
-                                             dz, cr, cg, cb, nsh);
+            for (int y = 0; y < 2; ++y) {
+                lo[z][y] = lerp2(lo2(S.c[z][y][0]), lo2(S.c[z][y][1]), tx);   // (v, Dx)
+                hi[z][y] = lerp2(hi2(S.c[z][y][0]), hi2(S.c[z][y][1]), tx);   // (Dy, Dz)
+            }
+        const float2 vx = lerp2(lerp2(lo[0][0], lo[0][1], ty), lerp2(lo[1][0], lo[1][1], ty), tz);
+        const float2 yz = lerp2(lerp2(hi[0][0], hi[0][1], ty), lerp2(hi[1][0], hi[1][1], ty), tz);
+        float fr;
+        const int ti = tf_index(a, tfmax, vx.x, fr);
+        const float4 c0 = s_tf[ti], c1 = s_tf[ti + 1];
+        const float2 f2 = make_float2(fr, fr);
+        const float2 rg = lerp2(lo2(c0), lo2(c1), f2), ba = lerp2(hi2(c0), hi2(c1), f2);
+        cr = rg.x;
+        cg = rg.y;
+        cb = ba.x;
+        if constexpr (SHADE == 1) {
+            phong(vx.y, yz.x, yz.y, dx, dy, dz, cr, cg, cb);
+        } else if constexpr (SHADE != 0) {
+            if (ba.y > 0.0f)
+                light_sample<Grad4Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, vx.y, yz.x, yz.y, ux, uy, uz, dx,
+                                                 dy, dz, cr, cg, cb, nsh);
         }
-        return al;
+        return ba.y;
     }
 };
+
+// Composite one classified sample (opacity al, shaded colour c); returns
+// true once the ray is opaque enough to stop.
+__device__ __forceinline__ bool composite(const MarchArgs& a, float al, float cr, float cg, float cb, Ray& s) {
+    if (al > 0.0f) {
+        const float w = (1.0f - s.A) * al;
+        s.C0 = fmaf(w, cr, s.C0);
+        s.C1 = fmaf(w, cg, s.C1);
+        s.C2 = fmaf(w, cb, s.C2);
+        s.A += w;
+    }
+    return s.A >= a.term;
+}
 
 // Classify, shade and composite one loaded sample; returns true once the ray
 // is opaque enough to stop.
@@ -690,14 +734,7 @@ __device__ __forceinline__ bool composite_sample(const MarchArgs& a, const Light
     float cr, cg, cb;
     const float al = Src::template shade<SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S, ux, uy, uz, s.dx, s.dy, s.dz,
                                                    cr, cg, cb, nsh);
-    if (al > 0.0f) {
-        const float w = (1.0f - s.A) * al;
-        s.C0 = fmaf(w, cr, s.C0);
-        s.C1 = fmaf(w, cg, s.C1);
-        s.C2 = fmaf(w, cb, s.C2);
-        s.A += w;
-    }
-    return s.A >= a.term;
+    return composite(a, al, cr, cg, cb, s);
 }
 
 // Up to two samples of the ray with both samples' loads issued before either
@@ -726,11 +763,19 @@ __device__ __forceinline__ bool ray_step(const MarchArgs& a, const Light& lt, co
     const float px1 = fmaf(t1c, s.dx, ux0), py1 = fmaf(t1c, s.dy, uy0), pz1 = fmaf(t1c, s.dz, uz0);
     Src::template load<I, SHADE != 0>(a, vol, sy, sz, px0, py0, pz0, S0);
     Src::template load<I, SHADE != 0>(a, vol, sy, sz, px1, py1, pz1, S1);
+    // both samples are classified and shaded before either is composited
+    // (independent work the scheduler can interleave; the second is wasted
+    // only on a ray's last step)
+    float r0, g0, b0, r1, g1, b1;
+    const float al0 = Src::template shade<SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S0, px0, py0, pz0, s.dx, s.dy,
+                                                    s.dz, r0, g0, b0, nsh);
+    const float al1 = Src::template shade<SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S1, px1, py1, pz1, s.dx, s.dy,
+                                                    s.dz, r1, g1, b1, nsh);
     s.kf += 1.0f;
-    if (composite_sample<Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S0, px0, py0, pz0, s, nsh)) return true;
+    if (composite(a, al0, r0, g0, b0, s)) return true;
     if (!has1) return true;
     s.kf += 1.0f;
-    return composite_sample<Src, SHADE, I>(a, lt, vol, s_tf, tfmax, sy, sz, S1, px1, py1, pz1, s, nsh);
+    return composite(a, al1, r1, g1, b1, s);
 }
 
 // Cooperative march of one ray by the whole warp, for the last few rays of a
