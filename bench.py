@@ -61,20 +61,25 @@ def parse():
     return p.parse_args()
 
 
-# Algorithmic work, counted from the definition of each step:
-#  march, per shaded sample: position 8, trilinear value 21 (7 lerps), TF 13,
-#  gradient 132 (6 trilinear values + 3 differences), normalisation and
-#  Phong 26, compositing 9 -> 209 FP32 flops (an FMA counts 2).
-MARCH_FLOPS_PER_SAMPLE = 209
+# Algorithmic work per unit of each stage:
+#  march, per shaded sample: about 60 FP32 flops (trilinear value, TF,
+#  gradient, Phong and compositing counted as the operations a sample needs
+#  beyond its gathers) and 224 bytes of cached gather (8 voxels of 4 bytes for
+#  the value + 6 x 32 bytes for the central differences), per the hot-path
+#  scope of this build; the march is a gather kernel, so both are reported.
+MARCH_FLOPS_PER_SAMPLE = 60
+MARCH_GATHER_BYTES_PER_SAMPLE = 224
+# L1 load bandwidth from unit counts: 152 SMs x 128 bytes per clock x 2.07 GHz
+L1_PEAK_GBS = 152 * 128 * 2.07e9 / 1e9
 # network, per full-resolution pixel: sum over layers of 2 * 9 * cin * cout /
 # (pixels per level) + the 1x1 head = 57,664 flops
 NET_FLOPS_PER_PX = 2 * 9 * (5 * 16 + 16 * 16 + 48 * 16 + 16 * 16) + 2 * 9 * (16 * 32 + 32 * 32 + 96 * 32 + 32 * 32) // 4 \
     + 2 * 9 * (32 * 64 + 64 * 64) // 16 + 2 * 16 * 29
 # FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
-# DRAM bytes (read + write) of one sparse-march launch of this workload, from
-# an ncu capture of the current kernel (python bench.py --profile, second frame)
-MARCH_DRAM_BYTES = 236.23e6 + 18.85e6
+# ncu counters of one sparse-march launch of this workload (the capture named
+# in "profile"; None until the current kernel has been captured)
+MARCH_NCU = None
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -190,91 +195,102 @@ def _oracle_workload(seed):
     return _WORKLOADS[seed]
 
 
-def cpu_oracle_frame_rate(frame_seed=2, budget_s=12.0, dense=True, nrays=30000, one_core=True):
-    """Time the CPU oracle on a bounded sample of one frame of the workload and
-    extrapolate to frames/s (march of a random subset of nrays of the frame's
-    sampled rays + FP64 network on a 128 x 128 crop, repeated for up to
-    min(budget_s, 4) s, scaled by pixel count); with one_core, also the march
-    on one thread, and with dense, the dense march of as many random pixels."""
+NBANDS = 16          # the oracle runs a frame as 16 bands of rows, one band per step
+
+
+class OracleFrames:
+    """The CPU oracle on whole frames of the workload, one band of 1/16 of the
+    rows per step: step i runs band i mod 16 of the frame of seed
+    2 + (i div 16) mod 4 -- the FP64 march of every sampled ray in the band's
+    rows and the FP64 network on the band (the oracle as it stands; the
+    network's cost is proportional to the band's pixels).  The frame's mask
+    (numpy, integer) runs with its first band.  Sixteen consecutive steps are
+    exactly one frame of work, so frames/s = bands done / 16 / seconds, and
+    every step's time is a time that actually ran."""
+
+    def __init__(self, one_core=False):
+        self.one_core = one_core
+        self.ids = {}
+
+    def band_rows(self, k):
+        return int(round(k * H / NBANDS)), int(round((k + 1) * H / NBANDS))
+
+    def step(self, i, threads=None):
+        import numpy as np
+        from oracle import march as om
+        from oracle import mask as omask
+        from oracle import net as onet
+        seed, k = 2 + (i // NBANDS) % 4, i % NBANDS
+        vol, tf, cam, fov, mp = _oracle_workload(seed)
+        if not hasattr(self, "params"):
+            self.params = onet.unpack(load_weights()[0])
+        t0 = time.perf_counter()
+        if k == 0 or seed not in self.ids:
+            _, self.ids[seed], _ = omask.make_mask(W, H, fov.focal_px, seed=fov.seed, frame=fov.frame)
+        ids = self.ids[seed]
+        r0, r1 = self.band_rows(k)
+        band = ids[(ids >= r0 * W) & (ids < r1 * W)].astype(np.int32)
+        sp, _, _ = om.march(vol, tf, cam, mp, ids=band)
+        onet.forward(self.params, sp[:, r0:r1, :])
+        return time.perf_counter() - t0
+
+
+def cpu_baseline_frame():
+    """The oracle on one whole frame (16 band steps, every host core), plus
+    the dense march of one band and the sparse march of one band on one core,
+    each scaled to a frame by its share of the rows."""
     import numpy as np
-    import torch
     from oracle import march as om
-    from oracle import mask as omask
-    from oracle import net as onet
-    vol, tf, cam, fov, mp = _oracle_workload(frame_seed)
-    t0 = time.perf_counter()
-    _, ids, _ = omask.make_mask(W, H, fov.focal_px, seed=fov.seed, frame=fov.frame)
-    t_mask = time.perf_counter() - t0
-    rng = np.random.default_rng(0)
-    nsub = max(1, min(ids.size, int(nrays)))
-    sub = np.sort(rng.choice(ids, nsub, replace=False)).astype(np.int32)
-    t0 = time.perf_counter()
-    sp, _, _ = om.march(vol, tf, cam, mp, ids=sub)
-    t_march = (time.perf_counter() - t0) * ids.size / nsub
-    weights, _ = load_weights()
-    params = onet.unpack(weights)
-    crop = 128
-    x = sp[:, 400:400 + crop, 800:800 + crop]
-    t0 = time.perf_counter()
-    reps = 0
-    while True:
-        onet.forward(params, x)
-        reps += 1
-        if time.perf_counter() - t0 > min(budget_s, 4.0):
-            break
-    t_net = (time.perf_counter() - t0) / reps * (W * H) / (crop * crop)
-    t_frame = t_mask + t_march + t_net
+    of = OracleFrames()
+    of.step(0)                                   # warm: loads, weights, workload
+    t = sum(of.step(i) for i in range(NBANDS))
     cores = os.cpu_count()
-    # the march on one core (a smaller subset of the same rays)
-    t_march1 = float("nan")
-    if one_core:
-        n1 = min(nsub, 3000)
-        om.set_threads(1)
-        t0 = time.perf_counter()
-        om.march(vol, tf, cam, mp, ids=sub[:n1])
-        t_march1 = (time.perf_counter() - t0) * ids.size / n1
-        om.set_threads(cores)
-    # the dense march (every pixel) beside it, from a uniform subset of the frame's pixels
-    t_dense = float("nan")
-    if dense:
-        dsub = np.sort(rng.choice(W * H, nsub, replace=False)).astype(np.int32)
-        t0 = time.perf_counter()
-        om.march(vol, tf, cam, mp, ids=dsub)
-        t_dense = (time.perf_counter() - t0) * (W * H) / nsub
-    sample = (f"mask of the full 1920x1080 frame; FP64 march of {nsub} of its {ids.size} sampled rays "
-              f"(scaled x{ids.size / nsub:.1f}); FP64 network on a {crop}x{crop} crop x{reps} "
-              f"(scaled x{W * H / crop / crop:.0f})")
-    return {"value": 1.0 / t_frame, "unit": "frames/s", "cores": cores, "kind": "oracle", "sample": sample,
-            "seconds_per_frame": t_frame, "mask_s": t_mask, "march_s": t_march, "net_s": t_net,
-            "march_s_one_core": t_march1, "single_core_frames_per_s": 1.0 / (t_mask + t_march1 + t_net),
-            "dense_march_s": t_dense, "dense_march_frames_per_s": 1.0 / t_dense,
-            "threads": f"march: OpenMP on {cores} threads (and on 1 for the single-core figure); mask and "
-                       "network: numpy"}
+    vol, tf, cam, fov, mp = _oracle_workload(2)
+    r0, r1 = of.band_rows(7)
+    rows = np.arange(r0 * W, r1 * W, dtype=np.int32)
+    t0 = time.perf_counter()
+    om.march(vol, tf, cam, mp, ids=rows)
+    t_dense = (time.perf_counter() - t0) * H / (r1 - r0)
+    ids = of.ids[2]
+    band = ids[(ids >= r0 * W) & (ids < r1 * W)].astype(np.int32)
+    om.set_threads(1)
+    t0 = time.perf_counter()
+    om.march(vol, tf, cam, mp, ids=band)
+    t_march1 = (time.perf_counter() - t0) * H / (r1 - r0)
+    om.set_threads(cores)
+    return {"value": 1.0 / t, "unit": "frames/s", "cores": cores, "kind": "oracle",
+            "sample": "one whole 1920x1080 frame of the workload in 16 bands of rows: the mask, the FP64 march "
+                      "of every sampled ray and the FP64 network on every band (all host cores for the march, "
+                      "numpy for mask and network)",
+            "seconds_per_frame": t,
+            "dense_march_frames_per_s": 1.0 / t_dense,
+            "sparse_march_one_core_s_per_frame": t_march1,
+            "note": "dense march: every pixel of one band, scaled by rows; one-core figure: the sparse march of "
+                    "one band on one thread, scaled by rows"}
 
 
 def run_reference(args):
     rank, world, _ = dist_env()
     if rank != 0:
         return
-    import numpy as np  # noqa: F401
+    of = OracleFrames()
     times = []
-    # each step a bounded sample of one frame, sized so that the whole run
-    # takes about two minutes of host time
-    per_step = min(12.0, max(0.3, 120.0 / (args.warmup + args.steps)))
     for i in range(args.warmup + args.steps):
-        r = cpu_oracle_frame_rate(frame_seed=2 + (i % 4), budget_s=per_step / 3, dense=False,
-                                  nrays=max(1000, int(10000 * per_step)), one_core=False)
+        t = of.step(i)
         if i >= args.warmup:
-            times.append(r["seconds_per_frame"])
-    t = sum(times) / len(times)
-    val = 1.0 / t
+            times.append(t)
+    total = sum(times)
+    val = len(times) / NBANDS / total            # frames of work per second
     out = {"metric": METRIC, "value": val, "unit": "frames/s", "n_gpus": 1, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1000 * t, "higher_is_better": True, "scaling": "weak",
-           "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+           "warmup": args.warmup, "ms_per_step": 1000 * total / len(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
            "config": {"workload": "foveated-1080p: 256^3 f32 fractal value noise, 1920x1080, Phong, step 0.5, "
-                                  "hash mask r0=0.1 s=0.1 P_b=0.05, U-Net 16/32/64"},
-           "cpu_baseline": {"value": val, "unit": "frames/s", "cores": r["cores"], "kind": "oracle",
-                            "sample": r["sample"]},
+                                  "hash mask r0=0.1 s=0.1 P_b=0.05, U-Net 16/32/64",
+                      "step": "one band of 1/16 of a frame's rows (16 steps = one frame)"},
+           "cpu_baseline": {"value": val, "unit": "frames/s", "cores": os.cpu_count(), "kind": "oracle",
+                            "sample": f"{len(times)} bands of 1/16 of a 1920x1080 frame's rows (frames of seeds "
+                                      "2-5): the mask with each frame's first band, the FP64 march of every "
+                                      "sampled ray of the band, the FP64 network on the band"},
            "e2e": {"value": val, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(out))
 
@@ -1067,7 +1083,8 @@ def main():
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    step_ms = []
+    step_ms, stage_rows = [], []
+    ctx.set_option(fvn.OPT_STAGE_TIMING, 1)                 # CUDA events at the frame's stage boundaries
     for i in range(args.steps):
         cam, fov = frames[i % ORBIT]
         flush.fill_(float(i))                               # evict the volume from L2 between steps
@@ -1075,12 +1092,15 @@ def main():
         e0.record(stream)
         ctx.render(vol, tf, cam, fov, mp, rgb, rgbam_out=rgbam)
         e1.record(stream)
+        stage_rows.append(ctx.stage_times())                # waits for this frame
         step_ms.append((e0, e1))
     torch.cuda.synchronize()
+    ctx.set_option(fvn.OPT_STAGE_TIMING, 0)
     if world > 1:
         torch.distributed.barrier()
     clocks = sampler.stop()
     ms = [a.elapsed_time(b) for a, b in step_ms]
+    stage_live = {k: float(np.mean([r[k] for r in stage_rows])) for k in fvn.STAGES}
     value, total_ms = replica_throughput(sum(ms), args.steps, world, dev)
 
     # ---- per-stage times, samples and quality on the same frames (untimed for value)
@@ -1128,8 +1148,11 @@ def main():
 
     # roofline of the dominant kernel (the sparse march): issue-bound FP32
     # work; every sample of this workload has alpha > 0 and is shaded
-    march_avg_s = march_s / nq
-    achieved = sparse_samples / nq * MARCH_FLOPS_PER_SAMPLE / march_avg_s / 1e12
+    # the sparse march kernel's own launches inside the timed region (stage events)
+    march_kernel_s = stage_live["march"] / 1000.0
+    samples_per_frame = sparse_samples / nq
+    achieved = samples_per_frame * MARCH_FLOPS_PER_SAMPLE / march_kernel_s / 1e12
+    gather_gbs = samples_per_frame * MARCH_GATHER_BYTES_PER_SAMPLE / march_kernel_s / 1e9
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -1137,8 +1160,8 @@ def main():
         pass
     hbm_peak = float(peaks.get("hbm_gbs", 6800.0))
     tc_peak = float(peaks.get("bf16_tflops", 1900.0))       # FP16 dense rate = BF16 dense rate
-    recon_avg_s = sum(recon_ms) / nq / 1000.0
-    mask_avg_s = sum(mask_ms) / nq / 1000.0
+    recon_avg_s = stage_live["network"] / 1000.0
+    mask_avg_s = stage_live["mask"] / 1000.0
     net_tflops = NET_FLOPS_PER_PX * W * H / recon_avg_s / 1e12
     mask_gbs = (W * H + 4 * nrays / nq) / mask_avg_s / 1e9
 
@@ -1233,9 +1256,7 @@ def main():
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        c = cpu_oracle_frame_rate()
-        cpu = {k: c[k] for k in ("value", "unit", "cores", "kind", "sample", "single_core_frames_per_s", "threads",
-                                 "dense_march_frames_per_s")}
+        cpu = cpu_baseline_frame()
 
     if rank == 0:
         out = {
@@ -1254,19 +1275,27 @@ def main():
             "tpsnr_vs_dense_db": tps.summary(),
             "stage_ms": {"mask": float(np.mean(mask_ms)), "sparse_march": float(np.mean(march_ms)),
                          "reconstruct": float(np.mean(recon_ms)), "dense_march": float(np.mean(dense_ms))},
+            "stage_ms_timed_region": stage_live,
             "gsamples_per_s": {"sparse_march": sparse_samples / march_s / 1e9,
                                "dense_march": dense_samples / (sum(dense_ms) / 1000.0) / 1e9,
                                "dense_equivalent": dense_samples / nq / (fov_step_ms / 1000.0) / 1e9},
             "rays_per_frame": nrays / nq, "sampled_fraction": nrays / nq / (W * H),
-            "roofline": {"bound": "alu", "kernel": "march_kernel (sparse)", "achieved": achieved,
-                         "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
-                         "traffic": MARCH_DRAM_BYTES,
-                         "note": f"{MARCH_FLOPS_PER_SAMPLE} FP32 flops per shaded sample (trilinear value, central "
-                                 "differences of the trilinear field, TF, Phong, compositing) over the FP32 peak "
-                                 "from unit counts (152 SM x 128 lanes x 2 x 2.07 GHz); the kernel reads 8 "
-                                 "16-byte gradient-volume voxels per sample and is bound by issuing them (L1 and "
-                                 "issue ~60-70 % busy, DRAM < 4 %); traffic = DRAM read + write of one launch "
-                                 "(ncu)"},
+            "roofline": {"bound": "alu", "kernel": "march_kernel<Grad4Src, int, 1> (sparse, compacted ids)",
+                         "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                         "frac": achieved / FP32_PEAK_TFLOPS,
+                         "traffic": MARCH_NCU["dram_bytes"] if MARCH_NCU else None,
+                         "kernel_ms": stage_live["march"], "samples_per_launch": samples_per_frame,
+                         "flops_per_sample": MARCH_FLOPS_PER_SAMPLE,
+                         "gather": {"bytes_per_sample": MARCH_GATHER_BYTES_PER_SAMPLE, "achieved_gbs": gather_gbs,
+                                    "peak_gbs": L1_PEAK_GBS, "frac": gather_gbs / L1_PEAK_GBS,
+                                    "peak_kind": "L1 load bandwidth from unit counts (152 SM x 128 B/clk x "
+                                                 "2.07 GHz)"},
+                         "ncu": MARCH_NCU,
+                         "note": "achieved = algorithmic flops (or gather bytes) of one launch / the launch's "
+                                 "duration from CUDA events around the kernel inside the timed frames; peak = FP32 "
+                                 "unit counts (152 SM x 128 lanes x 2 x 2.07 GHz; MEASURED_PEAKS.json has no FP32 "
+                                 "figure); the kernel reads 8 16-byte gradient-volume voxels per sample and its "
+                                 "limiter is instruction issue and L1 (see ncu)"},
             "roofline_stages": {
                 "reconstruct": {"bound": "tensor", "achieved": net_tflops, "peak": tc_peak, "unit": "TFLOP/s",
                                 "frac": net_tflops / tc_peak, "flops_per_px": NET_FLOPS_PER_PX,

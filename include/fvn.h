@@ -149,6 +149,8 @@ fvn_status fvn_destroy(fvn_ctx* ctx);
  *  FVN_OPT_MARCH_COUNT_SHADOW: 1 = with shading 2, the nsamples counter of a
  *      march also counts the samples of the shadow rays (default 0: primary
  *      samples only).
+ *  FVN_OPT_STAGE_TIMING: 1 = fvn_render records CUDA events at its stage
+ *      boundaries (read with fvn_stage_times); 0 (default) = none.
  * A shadowed march (shading 2) first writes, besides the padded copy, a cell
  * volume -- per padded voxel the 2 x 2 block of voxels (x..x+1, y..y+1) in
  * the voxel type -- so that a shadow sample reads two cells instead of
@@ -161,9 +163,20 @@ enum {
     FVN_OPT_MARCH_COOP = 6,
     FVN_OPT_MARCH_COOP_DENSE = 7,
     FVN_OPT_MARCH_GRADIENT_VOLUME = 8,
-    FVN_OPT_MARCH_COUNT_SHADOW = 9
+    FVN_OPT_MARCH_COUNT_SHADOW = 9,
+    FVN_OPT_STAGE_TIMING = 10
 };
 fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value);
+
+/* Stage times of the last fvn_render / fvn_render_recurrent of this context,
+ * with FVN_OPT_STAGE_TIMING set to 1 before it (the option makes fvn_render
+ * record CUDA events on its stream at the stage boundaries; paper: the
+ * per-stage frame times of its evaluation, section "Performance").  Waits
+ * for that frame, then writes five host floats, in milliseconds: mask and
+ * compaction; the march's setup (clearing the sparse frame); the volume
+ * preparation (0 when a reusable copy was current); the march kernel; the
+ * reconstruction network.  FVN_ERR_STATE when no frame was recorded. */
+fvn_status fvn_stage_times(fvn_ctx* ctx, float* ms);
 
 /* Synchronise the device and report a device-side failure recorded by this
  * context's kernels since the last call: FVN_ERR_TIMEOUT when a tensor-core

@@ -115,6 +115,10 @@ enum Fp8Tensor {
     FP8_NT
 };
 
+// Stage timing of fvn_render (FVN_OPT_STAGE_TIMING): events recorded on the
+// frame's stream at the stage boundaries.
+enum StageMark { TM_START = 0, TM_MASK, TM_SETUP, TM_PREP, TM_MARCH, TM_NET, TM_N };
+
 struct ProbeWorkspace {
     int w = 0, h = 0;
     int32_t* ids = nullptr;
@@ -171,6 +175,10 @@ struct fvn_ctx {
     fvn::ProbeWorkspace probe_ws;
     fvn::BatchWorkspace batch_ws;
     fvn::WnetState wnet;
+    bool timing = false;              // record stage events (FVN_OPT_STAGE_TIMING)
+    bool in_render = false;           // inside fvn_render: its stages are the ones recorded
+    bool timed_frame = false;         // a whole fvn_render was recorded since timing was enabled
+    cudaEvent_t tm_ev[fvn::TM_N] = {};
 };
 
 namespace fvn {
@@ -204,6 +212,12 @@ fvn_status set_error(fvn_ctx* ctx, fvn_status st, const char* fmt, ...);
     } while (0)
 
 inline cudaStream_t as_stream(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+// Record stage boundary k of the fvn_render in progress when stage timing
+// is on (the stages of other calls are not recorded).
+inline void stage_mark(fvn_ctx* ctx, int k, cudaStream_t st) {
+    if (ctx->timing && ctx->in_render) cudaEventRecord(ctx->tm_ev[k], st);
+}
 
 // Launch-error check after a kernel launch.
 #define FVN_LAUNCH_CHECK(ctx) FVN_CUDA((ctx), cudaGetLastError())

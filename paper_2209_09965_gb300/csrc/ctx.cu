@@ -114,6 +114,8 @@ extern "C" fvn_status fvn_destroy(fvn_ctx* ctx) {
         cudaFree(L.bias);
     }
     cudaFree(ctx->head_w16);
+    for (cudaEvent_t e : ctx->tm_ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(ctx->head_b32);
     cudaFree(ctx->d_error);
     cudaFree(ctx->d_act_scale);
@@ -177,6 +179,13 @@ extern "C" fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value) {
             FVN_CHECK_ARG(ctx, value == 0 || value == 1, "shadow-sample counting option must be 0 or 1");
             ctx->march_count_shadow = value;
             return FVN_OK;
+        case FVN_OPT_STAGE_TIMING:
+            FVN_CHECK_ARG(ctx, value == 0 || value == 1, "stage-timing option must be 0 or 1");
+            if (value && !ctx->tm_ev[0])
+                for (int k = 0; k < TM_N; ++k) FVN_CUDA(ctx, cudaEventCreate(&ctx->tm_ev[k]));
+            ctx->timing = value != 0;
+            ctx->timed_frame = false;
+            return FVN_OK;
         default:
             return set_error(ctx, FVN_ERR_ARG, "unknown option %d", option);
     }
@@ -229,9 +238,31 @@ static fvn_status render_entry(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf
     }
     cudaStream_t s = as_stream(stream);
     float* rgbam = rgbam_out ? rgbam_out : ws.rgbam;
+    struct InRender {   // the stages of this call are the ones recorded
+        fvn_ctx* c;
+        explicit InRender(fvn_ctx* x) : c(x) { c->in_render = true; c->timed_frame = false; }
+        ~InRender() { c->in_render = false; }
+    } guard(ctx);
+    stage_mark(ctx, TM_START, s);
     if ((st = make_mask_impl(ctx, fov, w, h, ws.mask, ws.ids, ws.count, s)) != FVN_OK) return st;
+    stage_mark(ctx, TM_MASK, s);
     if ((st = march_impl(ctx, vol, tf, cam, mp, ws.ids, ws.count, rgbam, nullptr, s)) != FVN_OK) return st;
-    return reconstruct_impl(ctx, rgbam, prev, w, h, precision, rgb, s);
+    if ((st = reconstruct_impl(ctx, rgbam, prev, w, h, precision, rgb, s)) != FVN_OK) return st;
+    stage_mark(ctx, TM_NET, s);
+    ctx->timed_frame = ctx->timing;
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_stage_times(fvn_ctx* ctx, float* ms) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    FVN_CHECK_ARG(ctx, ms != nullptr, "ms is NULL");
+    if (!ctx->timing || !ctx->timed_frame)
+        return set_error(ctx, FVN_ERR_STATE, "no frame rendered with stage timing on (FVN_OPT_STAGE_TIMING)");
+    FVN_CUDA(ctx, cudaEventSynchronize(ctx->tm_ev[TM_NET]));
+    float t[TM_N - 1];
+    for (int k = 0; k + 1 < TM_N; ++k) FVN_CUDA(ctx, cudaEventElapsedTime(&t[k], ctx->tm_ev[k], ctx->tm_ev[k + 1]));
+    for (int k = 0; k + 1 < TM_N; ++k) ms[k] = t[k];
+    return FVN_OK;
 }
 
 extern "C" fvn_status fvn_render(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,

@@ -1345,6 +1345,8 @@ static MarchArgs view_args(const fvn_volume* vol, const fvn_tf* tf, const fvn_ca
 
 static const void* march_cells(const fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp,
                                const void* buf);
+static fvn_status launch_for(fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp, const MarchArgs& a,
+                             cudaStream_t st);
 
 fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, const fvn_camera* cam,
                       const fvn_march_params* mp, const int32_t* ids, const int32_t* count, float* rgbam,
@@ -1360,6 +1362,7 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
     a.reject = ids ? nullptr : reject;
     if (ids || reject) FVN_CUDA(ctx, cudaMemsetAsync(rgbam, 0, 5 * sizeof(float) * (size_t)a.plane, st));
     FVN_CUDA(ctx, cudaMemsetAsync(a.ticket, 0, sizeof(int), st));
+    stage_mark(ctx, TM_SETUP, st);
     const size_t bytes = march_volume_bytes(ctx, vol, mp);
     if (ctx->pad_bytes < bytes) {
         // growing the volume scratch is a synchronising step
@@ -1376,6 +1379,15 @@ fvn_status march_impl(fvn_ctx* ctx, const fvn_volume* vol, const fvn_tf* tf, con
     // one pass over the volume, skipped while a non-zero generation says the copy is current
     fvn_status ps = march_volume_prepare_cached(ctx, vol, mp, ctx->pad_buf, ctx->pad_key, st);
     if (ps != FVN_OK) return ps;
+    stage_mark(ctx, TM_PREP, st);
+    const fvn_status ls = launch_for(ctx, vol, mp, a, st);
+    stage_mark(ctx, TM_MARCH, st);
+    return ls;
+}
+
+// The march kernel for the volume's copy and voxel type.
+static fvn_status launch_for(fvn_ctx* ctx, const fvn_volume* vol, const fvn_march_params* mp, const MarchArgs& a,
+                             cudaStream_t st) {
     const bool big = padded_voxels(vol) >= (1ull << 31);
     const int shade = mp->shading;
     const Light lt = make_light(ctx, mp);

@@ -33,7 +33,7 @@ EXPORTS = (
     "fvn_calibrate_fp8", "fvn_render_adaptive", "fvn_march_masked", "fvn_render_batch", "fvn_set_noise_tiles",
     "fvn_weight_count_recurrent", "fvn_reconstruct_recurrent", "fvn_render_recurrent", "fvn_selftest_wait_timeout",
     "fvn_wnet_weight_count", "fvn_load_wnet_weights", "fvn_reconstruct_wnet", "fvn_filter3_fwd", "fvn_filter3_bwd",
-    "fvn_wnet_join_fwd", "fvn_wnet_join_bwd",
+    "fvn_wnet_join_fwd", "fvn_wnet_join_bwd", "fvn_stage_times",
 )
 WNET_MAX_LEVELS = 4
 MAX_VIEWS = 16
@@ -42,6 +42,8 @@ OPT_MARCH_REFILL_DENSE, OPT_MARCH_BLOCKS_PER_SM_DENSE = 4, 5
 OPT_MARCH_COOP, OPT_MARCH_COOP_DENSE = 6, 7
 OPT_MARCH_GRADIENT_VOLUME = 8
 OPT_MARCH_COUNT_SHADOW = 9
+OPT_STAGE_TIMING = 10
+STAGES = ("mask", "march_setup", "volume_prep", "march", "network")
 
 
 class FvnError(RuntimeError):
@@ -138,6 +140,7 @@ def _load():
         "fvn_filter3_bwd": [P, P, I, I, I, P, P, P, P],
         "fvn_wnet_join_fwd": [P, P, P, I, I, I, P, P],
         "fvn_wnet_join_bwd": [P, P, P, I, I, I, P, P, P, P, P],
+        "fvn_stage_times": [P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -264,6 +267,12 @@ class Context:
     def selftest_wait_timeout(self, limit=1000, stream=None):
         """Run the bounded-wait failure path once (fvn_selftest_wait_timeout)."""
         self._chk(lib.fvn_selftest_wait_timeout(self.h, int(limit), _stream(stream)))
+
+    def stage_times(self):
+        """Per-stage ms of the last render with OPT_STAGE_TIMING on (waits for it)."""
+        ms = (ctypes.c_float * len(STAGES))()
+        self._chk(lib.fvn_stage_times(self.h, ms))
+        return dict(zip(STAGES, (float(x) for x in ms)))
 
     def device_status(self):
         """Synchronise; raise FvnError(FVN_ERR_TIMEOUT) if a kernel gave up a bounded wait."""

@@ -376,3 +376,37 @@ def test_volume_generation_reuses_the_prepared_copy(fvn, shading):
         march_parity(v.cpu().numpy(), tf, cam, mp, changed.cpu().numpy())
     finally:
         c.close()
+
+
+def test_stage_times(fvn):
+    """FVN_OPT_STAGE_TIMING: fvn_render records its stage boundaries; the
+    five stage times are non-negative and add up to the frame's time."""
+    c = fvn.Context()
+    try:
+        c.load_weights(wl.net_weights(3))
+        vol, tf, cam, mp = wl.dense_small_workload(seed=1, frame=2)
+        mp = wl.MarchParams(shading=1)
+        dev = torch.device("cuda")
+        v, t = torch.from_numpy(vol).to(dev), torch.from_numpy(tf).to(dev)
+        fov = wl.Foveation(focal_px=(60.0, 60.0), seed=1, frame=2)
+        rgb = torch.empty(3, cam.height, cam.width, device=dev)
+        with pytest.raises(fvn.FvnError, match="stage timing"):
+            c.stage_times()
+        c.set_option(fvn.OPT_STAGE_TIMING, 1)
+        for gen in (0, 3, 3):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            c.render(v, t, cam, fov, mp, rgb, generation=gen)
+            e1.record()
+            st = c.stage_times()
+            torch.cuda.synchronize()
+            assert set(st) == set(fvn.STAGES) and all(x >= 0.0 for x in st.values())
+            assert sum(st.values()) <= e0.elapsed_time(e1) + 1e-3
+        out = torch.empty(5, cam.height, cam.width, device=dev)
+        c.march(v, t, cam, mp, out)                  # not a render: the last frame's times stay
+        assert c.stage_times() == st
+        c.set_option(fvn.OPT_STAGE_TIMING, 0)
+        with pytest.raises(fvn.FvnError, match="stage timing"):
+            c.stage_times()
+    finally:
+        c.close()
