@@ -650,13 +650,14 @@ static EncodeTiledFn encode_tiled() {
 // Map of a chunk-planar tensor [C / chunk][H][W][16 B] (FP16, or FP8 as
 // bytes) seen as 8-byte elements, whose box is one chunk plane's 128 pixels
 // (256 elements, 2048 contiguous bytes) x hy rows: one plane of a stage.
-static fvn_status make_map(fvn_ctx* ctx, CUtensorMap* m, const void* base, int C, int W, int H, int hy, bool f8) {
+static fvn_status make_map(fvn_ctx* ctx, CUtensorMap* m, const void* base, int C, int W, int H, int hy, bool f8,
+                           int box_px = ws::kHXW) {
     const EncodeTiledFn fn = encode_tiled();
     if (!fn) return set_error(ctx, FVN_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
     const cuuint64_t cpc = f8 ? 16 : 8;
     const cuuint64_t dims[3] = {(cuuint64_t)W * 2, (cuuint64_t)H, (cuuint64_t)C / cpc};
     const cuuint64_t strides[2] = {(cuuint64_t)W * 16, (cuuint64_t)W * H * 16};
-    const cuuint32_t box[3] = {(cuuint32_t)(2 * ws::kHXW), (cuuint32_t)hy, 1};
+    const cuuint32_t box[3] = {(cuuint32_t)(2 * box_px), (cuuint32_t)hy, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<void*>(base), dims, strides, box, estr,
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
@@ -680,29 +681,32 @@ struct WsSpec {
 };
 
 // Stages of the shared-memory ring that fit next to the resident weights.
-template <int CIN, int COUT, int TR, bool F8, bool FUSE>
+template <int CIN, int COUT, int TR, bool F8, bool FUSE, int UPC = 0>
 constexpr int ws_stages() {
-    using L1 = ws::Layout<CIN, COUT, TR, 1, F8, FUSE>;
-    const long long budget = 227 * 1024 - (long long)L1::bytes + L1::stage;   // bytes for the stages
-    const long long ns = budget / (long long)L1::stage;
+    using L1 = ws::Layout<CIN, COUT, TR, 1, F8, FUSE, UPC>;
+    const long long per = (long long)L1::stage + L1::coarse + 8 * (UPC ? 3 : 2);   // bytes of one stage
+    const long long budget = 227 * 1024 - (long long)L1::bytes + per;             // bytes for the stages
+    const long long ns = budget / per;
     return ns >= 4 ? 4 : (ns < 1 ? 1 : (int)ns);
 }
 
-template <int CIN, int CHG, int CH0, int COUT, int TR, bool POOL, bool F8, bool FUSE = false>
+// A warp-specialised layer; UPC > 0: source 0 is the coarse level, whose
+// bilinear x2 up-sampling (UPC chunks) the kernel computes itself.
+template <int CIN, int CHG, int CH0, int COUT, int TR, bool POOL, bool F8, bool FUSE = false, int UPC = 0>
 static fvn_status launch_ws(fvn_ctx* ctx, const WsSpec* spec, int n, const ConvW& w, float out_q, float pool_q,
                             cudaStream_t st) {
-    constexpr int NS = ws_stages<CIN, COUT, TR, F8, FUSE>();
-    using L = ws::Layout<CIN, COUT, TR, NS, F8, FUSE>;
+    constexpr int NS = ws_stages<CIN, COUT, TR, F8, FUSE, UPC>();
+    using L = ws::Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>;
     static_assert(L::bytes <= 227 * 1024, "stage ring does not fit in shared memory");
     static_assert(sizeof(ws::Args) <= 32764, "kernel arguments exceed the parameter space");
-    auto kern = ws::conv3x3_ws_kernel<CIN, CHG, CH0, COUT, TR, NS, POOL, F8, FUSE>;
+    auto kern = ws::conv3x3_ws_kernel<CIN, CHG, CH0, COUT, TR, NS, POOL, F8, FUSE, UPC>;
     static std::atomic<unsigned long long> configured{0};
     FVN_CUDA(ctx, opt_in_smem(ctx, kern, (int)L::bytes, configured));
     int smem_sm = 0;
     FVN_CUDA(ctx, cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
     int per_sm = smem_sm / (int)(L::bytes + 1024);
     per_sm = std::min(per_sm, (int)(512 / L::tmem_cols));
-    per_sm = std::min(per_sm, 2048 / ws::kThreads);
+    per_sm = std::min(per_sm, 2048 / L::threads);
     if (per_sm < 1) return set_error(ctx, FVN_ERR_CUDA, "warp-specialised conv kernel does not fit on an SM");
     constexpr int CPC = L::CPC;
     ws::Args a{};
@@ -719,7 +723,8 @@ static fvn_status launch_ws(fvn_ctx* ctx, const WsSpec* spec, int n, const ConvW
         ws::Img& m = a.img[i];
         if (sp.c0 != CH0 * CPC || sp.c0 + sp.c1 != CHG * CPC)
             return set_error(ctx, FVN_ERR_ARG, "conv layer channels %d + %d do not match the kernel", sp.c0, sp.c1);
-        fvn_status s = make_map(ctx, &m.map0, sp.in0, sp.c0, sp.Wl, sp.Hl, L::HY, F8);
+        fvn_status s = UPC ? make_map(ctx, &m.map0, sp.in0, sp.c0, sp.Wl / 2, sp.Hl / 2, L::CR, F8, L::CC)
+                           : make_map(ctx, &m.map0, sp.in0, sp.c0, sp.Wl, sp.Hl, L::HY, F8);
         if (s != FVN_OK) return s;
         if (sp.c1 > 0) {
             if ((s = make_map(ctx, &m.map1, sp.in1, sp.c1, sp.Wl, sp.Hl, L::HY, F8)) != FVN_OK) return s;
@@ -737,7 +742,7 @@ static fvn_status launch_ws(fvn_ctx* ctx, const WsSpec* spec, int n, const ConvW
     a.ntiles = ntiles;
     const int grid = std::min(ntiles, ctx->num_sms * per_sm);
     if (grid > 0) {
-        FVN_CUDA(ctx, launch_pdl(kern, dim3(grid), dim3(ws::kThreads), L::bytes, st, a));
+        FVN_CUDA(ctx, launch_pdl(kern, dim3(grid), dim3(L::threads), L::bytes, st, a));
         FVN_LAUNCH_CHECK(ctx);
     }
     return FVN_OK;
@@ -979,23 +984,13 @@ static fvn_status run_tc(fvn_ctx* ctx, const ReconView* views, int n, cudaStream
     }
     if ((s = launch_ws<32, 32 / CPC, 32 / CPC, 32, 4, false, F8>(ctx, sp, n, L[7], q[FP8_D1], 0.f, st)) != FVN_OK)
         return s;
-    // dec0a on [up(d1), e0]
-    {
-        const void* c[kMaxViews];
-        void* f[kMaxViews];
-        for (int i = 0; i < n; ++i) {
-            c[i] = views[i].plan.d1;
-            f[i] = views[i].plan.u0;
-        }
-        if ((s = upsample_views<F8>(ctx, c, f, Hf, Wf, n, 32, st)) != FVN_OK) return s;
-    }
+    // dec0a on [up(d1), e0], the up-sampling computed inside the layer from d1
     for (int i = 0; i < n; ++i) {
         const ReconPlan& B = views[i].plan;
-        sp[i] = spec(B.u0, 32, B.e0, 16, B.d0a, nullptr, Hf[i], Wf[i]);
+        sp[i] = spec(B.d1, 32, B.e0, 16, B.d0a, nullptr, Hf[i], Wf[i]);
     }
-    if ((s = launch_ws<F8 ? 64 : 48, 48 / CPC, 32 / CPC, 16, 4, false, F8, true>(ctx, sp, n, L[8], q[FP8_D0A], 0.f,
-                                                                              st)) !=
-        FVN_OK)
+    if ((s = launch_ws<F8 ? 64 : 48, 48 / CPC, 32 / CPC, 16, 4, false, F8, true, 32 / CPC>(
+             ctx, sp, n, L[8], q[FP8_D0A], 0.f, st)) != FVN_OK)
         return s;
     // dec0b + head + kernel prediction + blend: the warp-specialised kernel for
     // views whose width is a multiple of 4 (TMA rows of the sparse frame), the

@@ -75,7 +75,13 @@ __device__ __forceinline__ bool wait(uint32_t bar, uint32_t parity) {
 // that those three are adjacent (output row r at column COUT (TR + 1 - r)),
 // which halves the operand reads of the tensor core at TR = 4.  The weights
 // are then kept as [dx][chunk][dy][COUT][16 B].
-template <int CIN, int COUT, int TR, int NS, bool F8, bool FUSE = false>
+//
+// UPC > 0 (decoder layers): the first UPC chunks of the input are the
+// bilinear x2 up-sampling of a coarse tensor, computed in the kernel: the
+// producer loads the coarse rows / columns under the tile (CR x CC pixels
+// per chunk) next to each stage, and up-sampling warps interpolate them into
+// the stage's first UPC chunk planes before the MMAs read it.
+template <int CIN, int COUT, int TR, int NS, bool F8, bool FUSE = false, int UPC = 0>
 struct Layout {
     static constexpr int EB = F8 ? 1 : 2;
     static constexpr int CPC = 16 / EB;                      // channels per 16-byte chunk
@@ -85,13 +91,22 @@ struct Layout {
     // 32 bytes past the last halo row, kept zero
     static constexpr uint32_t plane = (HY * kHXW * 16 + 32 + 127) / 128 * 128;
     static constexpr uint32_t stage = CH * plane;
+    // coarse rows and columns under the HY x 128 fine halo of a tile
+    static constexpr int CR = (TR + 1) / 2 + 2, CC = kHXW / 2 + 1;
+    static constexpr uint32_t cchunk = (CR * CC * 16 + 127) / 128 * 128;     // one coarse chunk (TMA target)
+    static constexpr uint32_t coarse = UPC * cchunk;                          // per stage
     static constexpr size_t w_bytes = 9ull * CIN * COUT * EB;
     static constexpr size_t stage_off = (w_bytes + 1023) / 1024 * 1024;
     static constexpr size_t zero_off = stage_off + (size_t)NS * stage;   // zero A operand (FUSE)
     static constexpr size_t zero_bytes = FUSE ? 2 * kTW * 16 : 0;
-    static constexpr size_t bias_off = zero_off + zero_bytes;
+    static constexpr size_t coarse_off = zero_off + zero_bytes;
+    static constexpr size_t bias_off = coarse_off + (size_t)NS * coarse;
     static constexpr size_t bar_off = bias_off + 2 * COUT * 4;
-    static constexpr size_t bytes = bar_off + (2 * NS + 4) * 8 + 16;
+    static constexpr int nbar = 2 * NS + 4 + (UPC ? NS : 0);          // full, empty, tfull, tempty, ready
+    static constexpr size_t bytes = bar_off + nbar * 8 + 16;
+    static constexpr int up_warps = 8;                                 // up-sampling warps (UPC > 0)
+    static constexpr int threads = 64 + 32 * 4 + (UPC ? 32 * up_warps : 0);
+    static_assert(UPC == 0 || 2 * CC <= 256, "coarse box wider than a TMA box");
     static constexpr uint32_t acc = (FUSE ? TR + 4 : TR) * COUT;   // TMEM columns of one accumulator
     static constexpr uint32_t tmem_cols = 2 * acc <= 32 ? 32 : 2 * acc <= 64 ? 64 : 2 * acc <= 128 ? 128
                                         : 2 * acc <= 256 ? 256 : 512;
@@ -147,21 +162,43 @@ __device__ __forceinline__ void store_px(void* base, long long plane, long long 
     }
 }
 
+// One coarse row of a chunk interpolated along x at a fine column: the
+// coarse pixels lx0, lx1 of `row` (16-byte chunks) with weight fx on lx1.
+template <bool F8>
+__device__ __forceinline__ void coarse_hlerp(const uint4* row, int lx0, int lx1, float fx, float* h) {
+    constexpr int CPC = F8 ? 16 : 8;
+    float p0[16], p1[16];
+    const uint4 u0 = row[lx0], u1 = row[lx1];
+    if (F8) {
+        unpack16q(u0, p0);
+        unpack16q(u1, p1);
+    } else {
+        unpack8h(u0, p0);
+        unpack8h(u1, p1);
+    }
+#pragma unroll
+    for (int j = 0; j < CPC; ++j) h[j] = fmaf(fx, p1[j] - p0[j], p0[j]);
+}
+
 // CIN: K per tap (padded); CHG: chunks read from memory (the others stay
-// zero); CH0: chunks from source 0.
-template <int CIN, int CHG, int CH0, int COUT, int TR, int NS, bool POOL, bool F8, bool FUSE>
-__global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_constant__ Args a) {
-    using L = Layout<CIN, COUT, TR, NS, F8, FUSE>;
-    constexpr int CH = L::CH, HY = L::HY;
+// zero); CH0: chunks from source 0 (UPC > 0: CH0 == UPC chunks up-sampled
+// from the coarse tensor of source 0).
+template <int CIN, int CHG, int CH0, int COUT, int TR, int NS, bool POOL, bool F8, bool FUSE, int UPC = 0>
+__global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>::threads)
+    conv3x3_ws_kernel(const __grid_constant__ Args a) {
+    using L = Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>;
+    constexpr int CH = L::CH, HY = L::HY, kThreads = L::threads;
+    static_assert(UPC == 0 || UPC == CH0, "up-sampled chunks are source 0");
     extern __shared__ __align__(1024) unsigned char smem[];
     unsigned char* sW = smem;
     unsigned char* sStage = smem + L::stage_off;
     float* sBias = reinterpret_cast<float*>(smem + L::bias_off);
     float* sScale = sBias + COUT;
     uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::bar_off);
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + 2 * NS + 4);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + L::nbar);
     const uint32_t full0 = tc::smem_addr(bars), empty0 = full0 + 8 * NS;
     const uint32_t tfull0 = full0 + 16 * NS, tempty0 = tfull0 + 16;
+    const uint32_t ready0 = tempty0 + 16;   // UPC: stage's up-sampled planes written
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     {   // resident weights, bias, scales; chunks never loaded stay zero
@@ -201,6 +238,8 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
             tc::mbar_init(bars + 2 * NS + k, 1);
             tc::mbar_init(bars + 2 * NS + 2 + k, 4);
         }
+        if (UPC)
+            for (int k = 0; k < NS; ++k) tc::mbar_init(bars + 2 * NS + 4 + k, L::up_warps);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 1) {
@@ -231,13 +270,27 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
                 const int lt = tile - im.tile0;
                 const int ty = lt / im.tiles_x, tx = lt - ty * im.tiles_x;
                 const uint32_t full = full0 + 8 * s;
-                mbar_expect_tx(full, (uint32_t)CHG * HY * kHXW * 16);
                 const uint32_t dst = tc::smem_addr(sStage + (size_t)s * L::stage);
+                if constexpr (UPC > 0) {
+                    // the coarse rows / columns under the tile (source 0), then
+                    // the fine chunks of source 1 straight into the stage
+                    mbar_expect_tx(full, (uint32_t)(CHG - UPC) * HY * kHXW * 16 + (uint32_t)UPC * L::CR * L::CC * 16);
+                    const uint32_t cdst = tc::smem_addr(smem + L::coarse_off + (size_t)s * L::coarse);
 #pragma unroll
-                for (int c = 0; c < CHG; ++c) {
-                    const bool first = c < CH0;
-                    tma_load_3d(dst + c * L::plane, first ? &im.map0 : &im.map1, 2 * (tx * kTO - 1), ty * TR - 1,
-                                first ? c : c - CH0, full);
+                    for (int c = 0; c < UPC; ++c)
+                        tma_load_3d(cdst + c * L::cchunk, &im.map0, 2 * (((tx * kTO) >> 1) - 1), ((ty * TR) >> 1) - 1,
+                                    c, full);
+#pragma unroll
+                    for (int c = UPC; c < CHG; ++c)
+                        tma_load_3d(dst + c * L::plane, &im.map1, 2 * (tx * kTO - 1), ty * TR - 1, c - UPC, full);
+                } else {
+                    mbar_expect_tx(full, (uint32_t)CHG * HY * kHXW * 16);
+#pragma unroll
+                    for (int c = 0; c < CHG; ++c) {
+                        const bool first = c < CH0;
+                        tma_load_3d(dst + c * L::plane, first ? &im.map0 : &im.map1, 2 * (tx * kTO - 1),
+                                    ty * TR - 1, first ? c : c - CH0, full);
+                    }
                 }
             }
             // on failure, let the loads already issued land before the CTA exits
@@ -255,7 +308,9 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
             int i = 0;
             for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++i) {
                 const int s = i % NS, acc = i & 1;
-                if (!wait(full0 + 8 * s, (i / NS) & 1) || (i >= 2 && !wait(tempty0 + 8 * acc, ((i >> 1) - 1) & 1))) {
+                // UPC: the stage is complete once the up-sampling warps have written their planes
+                const uint32_t in_bar = UPC ? ready0 + 8 * s : full0 + 8 * s;
+                if (!wait(in_bar, (i / NS) & 1) || (i >= 2 && !wait(tempty0 + 8 * acc, ((i >> 1) - 1) & 1))) {
                     failed = true;
                     break;
                 }
@@ -281,16 +336,19 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
                         }
                     }
                 } else {
+                    // rows innermost: consecutive MMAs accumulate into
+                    // different rows' accumulators, so they do not wait on
+                    // one another
 #pragma unroll 1
-                    for (int r = 0; r < TR; ++r) {
-                        const uint32_t d = tmem + (uint32_t)(acc * L::acc + r * COUT);
-#pragma unroll 1
-                        for (int tap = 0; tap < 9; ++tap) {
-                            const int dy = tap / 3, dx = tap - dy * 3;
+                    for (int tap = 0; tap < 9; ++tap) {
+                        const int dy = tap / 3, dx = tap - dy * 3;
 #pragma unroll
-                            for (int kc = 0; kc < CH / 2; ++kc) {
+                        for (int kc = 0; kc < CH / 2; ++kc) {
+                            const uint64_t bd = b0 + (uint64_t)((tap * CH + 2 * kc) * COUT);
+#pragma unroll
+                            for (int r = 0; r < TR; ++r) {
+                                const uint32_t d = tmem + (uint32_t)(acc * L::acc + r * COUT);
                                 const uint64_t ad = a0 + (uint64_t)((2 * kc) * (L::plane >> 4) + (r + dy) * kHXW + dx);
-                                const uint64_t bd = b0 + (uint64_t)((tap * CH + 2 * kc) * COUT);
                                 if (F8) tc::mma_e4m3(d, ad, bd, idesc, (tap | kc) != 0);
                                 else tc::mma_f16(d, ad, bd, idesc, (tap | kc) != 0);
                             }
@@ -303,7 +361,7 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
             // every MMA issued must finish before the TMEM is freed
             if (i > 0) wait(tfull0 + 8 * ((i - 1) & 1), ((i - 1) >> 1) & 1);
         }
-    } else {
+    } else if (warp < 6) {
         // ---- epilogue: warps 2-5, one pixel (TMEM lane) per thread ---------
         const int q = warp & 3;                 // TMEM lane quadrant of this warp
         const int px = q * 32 + lane;
@@ -355,6 +413,85 @@ __global__ void __launch_bounds__(kThreads) conv3x3_ws_kernel(const __grid_const
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) mbar_arrive(tempty0 + 8 * acc);
+        }
+    } else if constexpr (UPC > 0) {
+        // ---- up-sampling: warps 6.. write the stage's first UPC chunk planes
+        // as the bilinear x2 up-sampling (half-pixel centres, edge clamp) of
+        // the coarse rows the producer loaded, zero outside the fine frame.
+        // Thread t takes (chunk, fine halo column) items t, t + 32 up_warps, ..;
+        // along a column it interpolates each coarse row along x once and
+        // slides a pair of rows down the HY fine rows. ----
+        constexpr int CPC = L::CPC;
+        const int t = tid - 192;
+        int i = 0;
+        for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++i) {
+            const int s = i % NS;
+            if (!wait(full0 + 8 * s, (i / NS) & 1)) {
+                failed = true;
+                break;
+            }
+            const Img& im = a.img[find_img(a, tile)];
+            const int lt = tile - im.tile0;
+            const int ty = lt / im.tiles_x, tx = lt - ty * im.tiles_x;
+            const int x0 = tx * kTO, y0 = ty * TR;
+            const int Hc = im.Hl >> 1, Wc = im.Wl >> 1;
+            const int cy0 = (y0 >> 1) - 1, cx0 = (x0 >> 1) - 1;   // coarse origin of the loaded block
+            unsigned char* stg = sStage + (size_t)s * L::stage;
+            const unsigned char* cbuf = smem + L::coarse_off + (size_t)s * L::coarse;
+            for (int item = t; item < UPC * kHXW; item += 32 * L::up_warps) {
+                const int c = item / kHXW, p = item - c * kHXW;
+                uint4* dst = reinterpret_cast<uint4*>(stg + (size_t)c * L::plane) + p;
+                const int gx = x0 - 1 + p;
+                if (gx < 0 || gx >= im.Wl) {
+#pragma unroll
+                    for (int j = 0; j < HY; ++j) dst[j * kHXW] = make_uint4(0, 0, 0, 0);
+                    continue;
+                }
+                const int mx = gx >> 1;
+                const int ix0 = (gx & 1) ? mx : max(mx - 1, 0), ix1 = min(ix0 + 1, Wc - 1);
+                const float fx = (gx & 1) ? 0.25f : (mx > 0 ? 0.75f : 0.0f);
+                const int lx0 = ix0 - cx0, lx1 = ix1 - cx0;
+                const uint4* crows = reinterpret_cast<const uint4*>(cbuf + (size_t)c * L::cchunk);
+                float ha[CPC], hb[CPC];
+                int ra = -1, rb = -1;                   // coarse rows held in ha / hb
+#pragma unroll
+                for (int j = 0; j < HY; ++j) {
+                    const int gy = y0 - 1 + j;
+                    if (gy < 0 || gy >= im.Hl) {
+                        dst[j * kHXW] = make_uint4(0, 0, 0, 0);
+                        continue;
+                    }
+                    const int my = gy >> 1;
+                    const int iy0 = (gy & 1) ? my : max(my - 1, 0), iy1 = min(iy0 + 1, Hc - 1);
+                    const float fy = (gy & 1) ? 0.25f : (my > 0 ? 0.75f : 0.0f);
+                    const int ly0 = iy0 - cy0, ly1 = iy1 - cy0;
+                    if (ly0 != ra) {
+                        if (ly0 == rb) {
+#pragma unroll
+                            for (int k = 0; k < CPC; ++k) ha[k] = hb[k];
+                        } else {
+                            coarse_hlerp<F8>(crows + ly0 * L::CC, lx0, lx1, fx, ha);
+                        }
+                        ra = ly0;
+                    }
+                    if (ly1 != rb) {
+                        if (ly1 == ra) {
+#pragma unroll
+                            for (int k = 0; k < CPC; ++k) hb[k] = ha[k];
+                        } else {
+                            coarse_hlerp<F8>(crows + ly1 * L::CC, lx0, lx1, fx, hb);
+                        }
+                        rb = ly1;
+                    }
+                    float v[CPC];
+#pragma unroll
+                    for (int k = 0; k < CPC; ++k) v[k] = fmaf(fy, hb[k] - ha[k], ha[k]);
+                    dst[j * kHXW] = F8 ? pack16q(v) : pack8h(v);
+                }
+            }
+            tc::fence_async_smem();   // generic-proxy writes, read next by the tensor core
+            __syncwarp();
+            if (lane == 0) mbar_arrive(ready0 + 8 * s);
         }
     }
     if (failed) atomicExch(a.error, 1);
