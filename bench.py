@@ -924,9 +924,10 @@ def run_multiview(ctx, fvn, wl, dev, steps, warmup, flush):
     rgbs = [torch.empty(3, v["h"], v["w"], device=dev) for v in spec0]
     npix = sum(v["w"] * v["h"] for v in spec0)
 
-    def views(frame, rgbam=None):
+    def views(frame, rgbam=None, generation=0):
         return [{"vol": vols[v["volume"]], "tf": tfs[v["volume"]], "cam": v["cam"], "fov": v["fov"],
-                 "rgb": rgbs[i], "rgbam": None if rgbam is None else rgbam[i]}
+                 "rgb": rgbs[i], "rgbam": None if rgbam is None else rgbam[i],
+                 "generation": generation and generation + v["volume"]}
                 for i, v in enumerate(wl.multiview_views(frame=frame))]
 
     # FP8 scales from the first frame's own sparse frames
@@ -934,15 +935,23 @@ def run_multiview(ctx, fvn, wl, dev, steps, warmup, flush):
     ctx.render_batch(views(0, rgbam), mp)
     for i, v in enumerate(spec0):
         ctx.calibrate_fp8(rgbam[i], v["w"], v["h"], reset=(i == 0))
-    # quality of the batch on the 1280x720 views against their dense march (FP16, then FP8)
-    psnrs16, psnrs = [], []
-    for prec, acc in ((fvn.PREC_FP16, psnrs16), (fvn.PREC_FP8, psnrs)):
-        ctx.render_batch(views(0, rgbam), mp, precision=prec)
+    # quality of the batch on the 1280x720 views against their dense march
+    # (FP16, then FP8), without and with the per-view denser-mask fallback
+    psnrs16, psnrs, ad16, ad8, levels = [], [], [], [], {}
+
+    def q720(acc):
         for i, v in enumerate(spec0):
             if v["w"] == 1280:
                 dense = torch.empty(5, v["h"], v["w"], device=dev)
                 ctx.march(vols[v["volume"]], tfs[v["volume"]], v["cam"], mp, dense)
                 acc.append(psnr_t(rgbs[i], dense[:3]))
+
+    for prec, acc, acc_ad, name in ((fvn.PREC_FP16, psnrs16, ad16, "fp16"), (fvn.PREC_FP8, psnrs, ad8, "fp8")):
+        ctx.render_batch(views(0, rgbam), mp, precision=prec)
+        q720(acc)
+        lv, est = ctx.render_batch_adaptive(views(0), mp, min_psnr_db=35.0, max_levels=3, precision=prec)
+        q720(acc_ad)
+        levels[name] = {"levels": lv, "estimates_db": [round(x, 2) for x in est]}
     del rgbam
     torch.cuda.synchronize()
     stream = torch.cuda.current_stream()
@@ -950,23 +959,32 @@ def run_multiview(ctx, fvn, wl, dev, steps, warmup, flush):
     for i in range(warmup):
         ctx.render_batch(views(i), mp, precision=fvn.PREC_FP8)
     torch.cuda.synchronize()
-    ms = []
-    nsamp.zero_()
-    for i in range(steps):
-        vs = views(i)
-        flush.fill_(float(i))
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        ctx.render_batch(vs, mp, precision=fvn.PREC_FP8, nsamples=nsamp)
-        e1.record(stream)
-        ms.append((e0, e1))
-    torch.cuda.synchronize()
-    ms = [a.elapsed_time(b) for a, b in ms]
-    samples = int(nsamp.item()) / steps
+    def timed(gen, adaptive=False):
+        out = []
+        nsamp.zero_()
+        for i in range(steps):
+            vs = views(i, generation=gen)
+            flush.fill_(float(i))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            if adaptive:
+                ctx.render_batch_adaptive(vs, mp, min_psnr_db=35.0, max_levels=3, precision=fvn.PREC_FP8,
+                                          nsamples=nsamp)
+            else:
+                ctx.render_batch(vs, mp, precision=fvn.PREC_FP8, nsamples=nsamp)
+            e1.record(stream)
+            out.append((e0, e1))
+        torch.cuda.synchronize()
+        return [a.elapsed_time(b) for a, b in out], int(nsamp.item()) / steps
+
+    ms_prep, _ = timed(0)                           # volume copies prepared in every batch
+    ctx.render_batch(views(0, generation=1), mp, precision=fvn.PREC_FP8)
+    ms, samples = timed(1)                           # static volumes: their copies reused
+    ms_ad, samples_ad = timed(1, adaptive=True)
     # the same batch captured once in a CUDA graph and replayed
     graph_ms = None
     try:
-        vs = views(0)
+        vs = views(0, generation=1)
         side = torch.cuda.Stream()
         side.wait_stream(stream)
         g = torch.cuda.CUDAGraph()
@@ -993,12 +1011,20 @@ def run_multiview(ctx, fvn, wl, dev, steps, warmup, flush):
             "megapixels_per_batch": npix / 1e6, "batches": steps, "ms_per_batch": mean_ms,
             "views_per_s": 16 * 1000.0 / mean_ms, "megapixels_per_s": npix / 1e6 * 1000.0 / mean_ms,
             "gsamples_per_s_end_to_end": samples / (mean_ms / 1000.0) / 1e9, "samples_per_batch": samples,
-            "psnr_720p_views_vs_dense_db": [float(x) for x in psnrs],
-            "psnr_720p_views_vs_dense_db_fp16": [float(x) for x in psnrs16],
+            "ms_per_batch_preparing_volumes": float(np.mean(ms_prep)),
+            "psnr_720p_views_vs_dense_db": [float(x) for x in ad8],
+            "psnr_720p_views_vs_dense_db_fp16": [float(x) for x in ad16],
+            "psnr_720p_views_no_fallback_db": [float(x) for x in psnrs],
+            "psnr_720p_views_no_fallback_db_fp16": [float(x) for x in psnrs16],
+            "fallback": {"rule": "fvn_render_batch_adaptive: per view, probe PSNR < 35 dB -> P_b doubled, up to 3 "
+                                 "times", "frame0": levels, "ms_per_batch": float(np.mean(ms_ad)),
+                         "samples_per_batch": samples_ad},
             "graph_ms_per_batch": graph_ms,
-            "launches_per_batch": 16,
-            "note": "launches: 1 mask + compaction, 2 volume preparations (gradient volume / padded copy), "
-                    "1 persistent march, 10 network layers + 2 up-sampling passes, each over all views"}
+            "launches_per_batch": 13,
+            "note": "launches: 1 mask + compaction, 1 persistent march, 9 convolution layers + the last layer "
+                    "with head / kernel prediction + 1 up-sampling pass, each over all views; the 2 volume "
+                    "preparations (gradient volume / padded copy) run once for static volumes "
+                    "(fvn_volume.generation), in every batch otherwise (ms_per_batch_preparing_volumes)"}
 
 
 def main():
@@ -1305,9 +1331,10 @@ def main():
             "autotune": tuned,
             "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": int(tf_np.nbytes),
                     "d2h_bytes_per_step": int(3 * H * W * 4)},
-            # per frame: mask, gradient volume, march, then 10 convolutions + 2
-            # up-sampling passes (head / KP / blend in the last convolution)
-            "gpu_launches": 15 * args.steps,
+            # per frame: mask, gradient volume, march, then 10 convolutions + 1
+            # up-sampling pass (head / KP / blend in the last convolution; the
+            # full-resolution up-sampling inside the decoder convolution)
+            "gpu_launches": 14 * args.steps,
             "cuda_graph": graph_info,
             "fp8": fp8_info,
             "shadows": shadows,

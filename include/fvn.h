@@ -437,6 +437,24 @@ typedef struct {
 fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int nviews, const fvn_march_params* mp,
                             int precision, unsigned long long* nsamples, void* stream);
 
+/*
+ * fvn_render_batch_adaptive -- fvn_render_batch with the denser-mask
+ * fallback of fvn_render_adaptive applied to every view (the paper has no
+ * counterpart; this is the library's frame-quality guard).  After each
+ * batch, every view's probes (its second hash below 1/256, outside its mask)
+ * are ray-marched in one launch and the PSNR of its reconstruction there
+ * estimates the view's PSNR; the views below min_psnr_db that have made
+ * fewer than max_levels (0..8) re-renders and whose P_b is below 1 are
+ * rendered again, together, with P_b doubled (capped at 1).  Each view ends
+ * with the output fvn_render_adaptive gives for it alone.  levels_out /
+ * psnr_out: optional host arrays of nviews entries (re-renders, last
+ * estimate).  nsamples counts the samples of every batch pass.  Synchronises
+ * the host once per pass; keeps a probe workspace of 24 bytes per pixel.
+ */
+fvn_status fvn_render_batch_adaptive(fvn_ctx* ctx, const fvn_view* views, int nviews, const fvn_march_params* mp,
+                                     int precision, float min_psnr_db, int max_levels, unsigned long long* nsamples,
+                                     int* levels_out, float* psnr_out, void* stream);
+
 /* ------------------------------------------------------------------------
  * Training kernels (FP32, NCHW with batch N).  Paper: "Training" and "Loss"
  * sections (the network is trained in FP32).  These are the forward and

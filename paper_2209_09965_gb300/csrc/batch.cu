@@ -71,10 +71,13 @@ bool same_volume(const fvn_volume* a, const fvn_volume* b) {
 }  // namespace
 }  // namespace fvn
 
-using namespace fvn;
+namespace fvn {
+namespace {
 
-extern "C" fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int nviews, const fvn_march_params* mp,
-                                       int precision, unsigned long long* nsamples, void* stream) {
+// The batch; leaves every view's mask and volume copy in
+// ctx->batch_ws.view_mask / view_pvol.
+fvn_status render_batch_impl(fvn_ctx* ctx, const fvn_view* views, int nviews, const fvn_march_params* mp,
+                             int precision, unsigned long long* nsamples, void* stream) {
     if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
     FVN_CHECK_ARG(ctx, views != nullptr, "views is NULL");
     FVN_CHECK_ARG(ctx, nviews >= 1 && nviews <= kMaxViews, "%d views (1..%d)", nviews, kMaxViews);
@@ -165,6 +168,10 @@ extern "C" fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int 
         mv[i] = BatchMarchView{views[i].vol, ws.pad[vol_of[i]], views[i].tf, &views[i].cam, ids[i], counts + i,
                                rgbam[i]};
     if ((s = march_batch_impl(ctx, mv, nviews, mp, nsamples, st)) != FVN_OK) return s;
+    for (int i = 0; i < nviews; ++i) {
+        ws.view_mask[i] = mask[i];
+        ws.view_pvol[i] = ws.pad[vol_of[i]];
+    }
 
     // ---- network: one launch per layer over every view's tiles ------------
     ReconView rv[kMaxViews];
@@ -177,4 +184,111 @@ extern "C" fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int 
         rv[i].prev = views[i].prev_rgb;
     }
     return reconstruct_tc_views(ctx, rv, nviews, precision, st);
+}
+
+}  // namespace
+}  // namespace fvn
+
+using namespace fvn;
+
+extern "C" fvn_status fvn_render_batch(fvn_ctx* ctx, const fvn_view* views, int nviews, const fvn_march_params* mp,
+                                       int precision, unsigned long long* nsamples, void* stream) {
+    return render_batch_impl(ctx, views, nviews, mp, precision, nsamples, stream);
+}
+
+extern "C" fvn_status fvn_render_batch_adaptive(fvn_ctx* ctx, const fvn_view* views, int nviews,
+                                                const fvn_march_params* mp, int precision, float min_psnr_db,
+                                                int max_levels, unsigned long long* nsamples, int* levels_out,
+                                                float* psnr_out, void* stream) {
+    if (!ctx) return set_error(nullptr, FVN_ERR_ARG, "ctx is NULL");
+    FVN_CHECK_ARG(ctx, views != nullptr, "views is NULL");
+    FVN_CHECK_ARG(ctx, nviews >= 1 && nviews <= kMaxViews, "%d views (1..%d)", nviews, kMaxViews);
+    FVN_CHECK_ARG(ctx, max_levels >= 0 && max_levels <= 8, "max_levels must be in [0, 8]");
+    FVN_CHECK_ARG(ctx, isfinite(min_psnr_db), "min_psnr_db is not finite");
+    cudaStream_t st = as_stream(stream);
+    // probe workspace: per view ids (4 B / px) and samples (20 B / px), then
+    // the counts and the error sums
+    size_t off[kMaxViews], need = 0;
+    for (int i = 0; i < nviews; ++i) {
+        FVN_CHECK_ARG(ctx, views[i].cam.width >= 1 && views[i].cam.height >= 1 && views[i].cam.width <= kMaxSide &&
+                               views[i].cam.height <= kMaxSide,
+                      "view %d: camera size outside [1, %d]", i, kMaxSide);
+        off[i] = need;
+        need += align256((size_t)views[i].cam.width * views[i].cam.height * 24);
+    }
+    const size_t cnt_off = need;
+    need += align256(kMaxViews * sizeof(int32_t)) + kMaxViews * sizeof(double);
+    BatchWorkspace& ws = ctx->batch_ws;
+    fvn_view cur[kMaxViews];
+    int orig[kMaxViews], level[kMaxViews];
+    float est[kMaxViews];
+    int n = nviews;
+    for (int i = 0; i < nviews; ++i) {
+        cur[i] = views[i];
+        orig[i] = i;
+        level[i] = 0;
+        est[i] = 0.f;
+    }
+    for (;;) {
+        fvn_status s = render_batch_impl(ctx, cur, n, mp, precision, nsamples, stream);
+        if (s != FVN_OK) return s;
+        if (ws.probe_bytes < need) {   // after the first batch: its arguments are validated
+            FVN_CUDA(ctx, cudaDeviceSynchronize());
+            cudaFree(ws.probe);
+            ws.probe = nullptr;
+            ws.probe_bytes = 0;
+            FVN_CUDA(ctx, cudaMalloc(&ws.probe, need));
+            ws.probe_bytes = need;
+        }
+        char* pb = static_cast<char*>(ws.probe);
+        int32_t* counts = reinterpret_cast<int32_t*>(pb + cnt_off);
+        double* sums = reinterpret_cast<double*>(pb + cnt_off + align256(kMaxViews * sizeof(int32_t)));
+        FVN_CUDA(ctx, cudaMemsetAsync(counts, 0, kMaxViews * sizeof(int32_t), st));
+        FVN_CUDA(ctx, cudaMemsetAsync(sums, 0, kMaxViews * sizeof(double), st));
+        // probes outside each view's mask, marched in one launch, errors per view
+        BatchMarchView mv[kMaxViews];
+        for (int a = 0; a < n; ++a) {
+            const int i = orig[a];
+            const fvn_view& v = cur[a];
+            const int w = v.cam.width, h = v.cam.height;
+            int32_t* pids = reinterpret_cast<int32_t*>(pb + off[i]);
+            float* prgbam = reinterpret_cast<float*>(pb + off[i] + (size_t)w * h * 4);
+            if ((s = probe_compact(ctx, w, h, probe_key(&v.fov), ws.view_mask[a], pids, counts + i, st)) != FVN_OK)
+                return s;
+            mv[a] = BatchMarchView{v.vol, ws.view_pvol[a], v.tf, &v.cam, pids, counts + i, prgbam};
+        }
+        if ((s = march_batch_impl(ctx, mv, n, mp, nullptr, st)) != FVN_OK) return s;
+        for (int a = 0; a < n; ++a) {
+            const int i = orig[a];
+            const long long plane = (long long)cur[a].cam.width * cur[a].cam.height;
+            if ((s = probe_error(ctx, mv[a].ids, mv[a].count, cur[a].rgb, mv[a].rgbam, plane, sums + i, st)) !=
+                FVN_OK)
+                return s;
+        }
+        int hc[kMaxViews];
+        double hs[kMaxViews];
+        FVN_CUDA(ctx, cudaMemcpyAsync(hc, counts, sizeof hc, cudaMemcpyDeviceToHost, st));
+        FVN_CUDA(ctx, cudaMemcpyAsync(hs, sums, sizeof hs, cudaMemcpyDeviceToHost, st));
+        FVN_CUDA(ctx, cudaStreamSynchronize(st));
+        // the views below the threshold go again with their periphery density doubled
+        int m = 0;
+        for (int a = 0; a < n; ++a) {
+            const int i = orig[a];
+            est[i] = (hc[i] == 0 || hs[i] == 0.0) ? 99.0f : (float)(-10.0 * log10(hs[i] / (3.0 * hc[i])));
+            if (est[i] >= min_psnr_db || level[i] >= max_levels || cur[a].fov.p_base >= 1.0f) continue;
+            fvn_view nv = cur[a];
+            nv.fov.p_base = std::min(1.0f, 2.0f * nv.fov.p_base);
+            ++level[i];
+            cur[m] = nv;
+            orig[m] = i;
+            ++m;
+        }
+        if (m == 0) break;
+        n = m;
+    }
+    for (int i = 0; i < nviews; ++i) {
+        if (levels_out) levels_out[i] = level[i];
+        if (psnr_out) psnr_out[i] = est[i];
+    }
+    return FVN_OK;
 }

@@ -94,6 +94,12 @@ struct BatchWorkspace {
     void* pad[kMaxBatchVolumes] = {}; // padded volume copies
     size_t pad_bytes[kMaxBatchVolumes] = {};
     PreparedKey pad_key[kMaxBatchVolumes];
+    uint8_t* view_mask[kMaxViews] = {};      // the last batch's masks and volume copies, per view
+    const void* view_pvol[kMaxViews] = {};
+    // probes of fvn_render_batch_adaptive: per view ids and samples (24 B per
+    // pixel), then counts and error sums
+    void* probe = nullptr;
+    size_t probe_bytes = 0;
 };
 
 // Two-stage network: configuration, FP32 weights on the device (the flat
@@ -265,6 +271,14 @@ fvn_status march_volume_prepare_cached(fvn_ctx* ctx, const fvn_volume* vol, cons
 fvn_status make_mask_batch_impl(fvn_ctx* ctx, const fvn_foveation* const* fov, const int* w, const int* h,
                                 uint8_t* const* mask, int32_t* const* ids, int32_t* counts, int n,
                                 cudaStream_t st);
+// Error-estimate probes of the denser-mask fallback: the key of a frame's
+// second hash, the compaction of the probe pixels (second hash below 1/256,
+// outside the mask) and the sum of squared errors of the clamped RGB at them.
+uint32_t probe_key(const fvn_foveation* f);
+fvn_status probe_compact(fvn_ctx* ctx, int w, int h, uint32_t key2, const uint8_t* mask, int32_t* ids,
+                         int32_t* count, cudaStream_t st);
+fvn_status probe_error(fvn_ctx* ctx, const int32_t* ids, const int32_t* count, const float* rgb, const float* probe,
+                       long long plane, double* acc, cudaStream_t st);
 // The network launch sequence on a caller-provided workspace of at least
 // recon_workspace_bytes(w, h) bytes (256-byte aligned).
 fvn_status reconstruct_on(fvn_ctx* ctx, void* workspace, const float* rgbam, const float* prev, int w, int h,

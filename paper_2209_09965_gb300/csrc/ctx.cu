@@ -136,6 +136,7 @@ extern "C" fvn_status fvn_destroy(fvn_ctx* ctx) {
     cudaFree(ctx->wnet.d_w);
     cudaFree(ctx->wnet.ws);
     for (void* p : ctx->batch_ws.pad) cudaFree(p);
+    cudaFree(ctx->batch_ws.probe);
     delete ctx;
     return FVN_OK;
 }

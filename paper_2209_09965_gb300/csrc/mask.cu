@@ -372,6 +372,23 @@ __global__ void probe_error_kernel(const int32_t* __restrict__ ids, const int32_
     if ((threadIdx.x & 31) == 0 && s != 0.0) atomicAdd(acc, s);
 }
 
+uint32_t probe_key(const fvn_foveation* f) { return pcg_hash(f->frame + pcg_hash(f->seed ^ kProbeSalt)); }
+
+fvn_status probe_compact(fvn_ctx* ctx, int w, int h, uint32_t key2, const uint8_t* mask, int32_t* ids,
+                         int32_t* count, cudaStream_t st) {
+    dim3 grid((w + 31) / 32, (h + 7) / 8);
+    probe_compact_kernel<<<grid, 256, 0, st>>>(w, h, key2, mask, ids, count);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+fvn_status probe_error(fvn_ctx* ctx, const int32_t* ids, const int32_t* count, const float* rgb, const float* probe,
+                       long long plane, double* acc, cudaStream_t st) {
+    probe_error_kernel<<<4 * ctx->num_sms, 256, 0, st>>>(ids, count, rgb, probe, plane, acc);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
 }  // namespace fvn
 
 using namespace fvn;
@@ -405,7 +422,7 @@ extern "C" fvn_status fvn_render_adaptive(fvn_ctx* ctx, const fvn_volume* vol, c
         pw.h = h;
     }
     fvn_foveation f = *fov;
-    const uint32_t key2 = pcg_hash(fov->frame + pcg_hash(fov->seed ^ kProbeSalt));
+    const uint32_t key2 = probe_key(fov);
     float est = 0.f;
     int level = 0;
     for (;; ++level) {
@@ -414,12 +431,9 @@ extern "C" fvn_status fvn_render_adaptive(fvn_ctx* ctx, const fvn_volume* vol, c
         // probes: outside this level's mask
         FVN_CUDA(ctx, cudaMemsetAsync(pw.count, 0, sizeof(int32_t), st));
         FVN_CUDA(ctx, cudaMemsetAsync(pw.acc, 0, sizeof(double), st));
-        dim3 grid((w + 31) / 32, (h + 7) / 8);
-        probe_compact_kernel<<<grid, 256, 0, st>>>(w, h, key2, ctx->render_ws.mask, pw.ids, pw.count);
-        FVN_LAUNCH_CHECK(ctx);
+        if ((s = probe_compact(ctx, w, h, key2, ctx->render_ws.mask, pw.ids, pw.count, st)) != FVN_OK) return s;
         if ((s = march_impl(ctx, vol, tf, cam, mp, pw.ids, pw.count, pw.rgbam, nullptr, st)) != FVN_OK) return s;
-        probe_error_kernel<<<4 * ctx->num_sms, 256, 0, st>>>(pw.ids, pw.count, rgb, pw.rgbam, (long long)npix, pw.acc);
-        FVN_LAUNCH_CHECK(ctx);
+        if ((s = probe_error(ctx, pw.ids, pw.count, rgb, pw.rgbam, (long long)npix, pw.acc, st)) != FVN_OK) return s;
         double sum = 0.0;
         int n = 0;
         FVN_CUDA(ctx, cudaMemcpyAsync(&sum, pw.acc, sizeof(double), cudaMemcpyDeviceToHost, st));

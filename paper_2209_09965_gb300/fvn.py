@@ -33,7 +33,7 @@ EXPORTS = (
     "fvn_calibrate_fp8", "fvn_render_adaptive", "fvn_march_masked", "fvn_render_batch", "fvn_set_noise_tiles",
     "fvn_weight_count_recurrent", "fvn_reconstruct_recurrent", "fvn_render_recurrent", "fvn_selftest_wait_timeout",
     "fvn_wnet_weight_count", "fvn_load_wnet_weights", "fvn_reconstruct_wnet", "fvn_filter3_fwd", "fvn_filter3_bwd",
-    "fvn_wnet_join_fwd", "fvn_wnet_join_bwd", "fvn_stage_times",
+    "fvn_wnet_join_fwd", "fvn_wnet_join_bwd", "fvn_stage_times", "fvn_render_batch_adaptive",
 )
 WNET_MAX_LEVELS = 4
 MAX_VIEWS = 16
@@ -141,6 +141,7 @@ def _load():
         "fvn_wnet_join_fwd": [P, P, P, I, I, I, P, P],
         "fvn_wnet_join_bwd": [P, P, P, I, I, I, P, P, P, P, P],
         "fvn_stage_times": [P, P],
+        "fvn_render_batch_adaptive": [P, P, I, P, I, F, I, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -372,12 +373,7 @@ class Context:
                                                ctypes.byref(f), ctypes.byref(m), int(precision), _ptr(prev),
                                                _ptr(rgb), _ptr(rgbam_out), _stream(stream)))
 
-    def render_batch(self, views, mp, precision=PREC_FP16, nsamples=None, stream=None):
-        """fvn_render for several views in one pass.  ``views`` is a list of
-        dicts with keys vol, tf (CUDA tensors), cam, fov and rgb (CUDA
-        [3, h, w] float32), optionally rgbam (CUDA [5, h, w] float32),
-        prev (the view's previous output, recurrent network) and generation
-        (of the view's volume, see fvn_volume)."""
+    def _batch_views(self, views):
         n = len(views)
         arr = (ViewC * max(n, 1))()
         keep = []   # descriptors referenced by pointer must outlive the call
@@ -399,10 +395,34 @@ class Context:
             arr[i].rgb = _ptr(v["rgb"])
             arr[i].rgbam = _ptr(v.get("rgbam"))
             arr[i].prev_rgb = _ptr(v.get("prev"))
+        return arr, keep
+
+    def render_batch(self, views, mp, precision=PREC_FP16, nsamples=None, stream=None):
+        """fvn_render for several views in one pass.  ``views`` is a list of
+        dicts with keys vol, tf (CUDA tensors), cam, fov and rgb (CUDA
+        [3, h, w] float32), optionally rgbam (CUDA [5, h, w] float32),
+        prev (the view's previous output, recurrent network) and generation
+        (of the view's volume, see fvn_volume)."""
+        arr, keep = self._batch_views(views)
         m = march_params(mp)
         ns = None if nsamples is None else _ptr(nsamples, torch.int64)
-        self._chk(lib.fvn_render_batch(self.h, arr, int(n), ctypes.byref(m), int(precision), ns,
+        self._chk(lib.fvn_render_batch(self.h, arr, len(views), ctypes.byref(m), int(precision), ns,
                                        _stream(stream)))
+
+    def render_batch_adaptive(self, views, mp, min_psnr_db=35.0, max_levels=3, precision=PREC_FP16, nsamples=None,
+                              stream=None):
+        """render_batch with the per-view denser-mask fallback; returns
+        (levels, PSNR estimates), one entry per view."""
+        arr, keep = self._batch_views(views)
+        m = march_params(mp)
+        n = len(views)
+        lv = (ctypes.c_int * n)()
+        est = (ctypes.c_float * n)()
+        ns = None if nsamples is None else _ptr(nsamples, torch.int64)
+        self._chk(lib.fvn_render_batch_adaptive(self.h, arr, n, ctypes.byref(m), int(precision), float(min_psnr_db),
+                                                int(max_levels), ns, lv, est, _stream(stream)))
+        return list(lv), [float(x) for x in est]
+
 
 
 # --- training kernels (context-free) -----------------------------------------

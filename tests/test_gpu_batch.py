@@ -186,3 +186,44 @@ def test_batch_argument_errors(ctx, fvn):
     views[0]["rgb"] = None
     with pytest.raises((fvn.FvnError, ValueError)):
         ctx.render_batch(views, mp)
+
+
+@pytest.mark.parametrize("mode", ["all", "some"])
+def test_batch_adaptive_equals_single_view_fallback(ctx, fvn, mode):
+    """fvn_render_batch_adaptive applies the denser-mask fallback to every
+    view: each view ends with the output, level and estimate that
+    fvn_render_adaptive gives for it alone -- with a threshold every view
+    misses (all re-render up to max_levels), and with one between the views'
+    first estimates (some re-render, the others keep their first frame)."""
+    dev, host, vols_d, tfs, tfs_d = _setup()
+    mp = wl.MarchParams(shading=1)
+    single = []
+    first = []
+    for v in _views(SPECS, vols_d, tfs_d, dev):
+        lvl, est = ctx.render_adaptive(v["vol"], v["tf"], v["cam"], v["fov"], mp, v["rgb"], min_psnr_db=-1.0,
+                                       max_levels=0)
+        first.append(est)
+    thr = 99.5 if mode == "all" else float(np.median(first))
+    for v in _views(SPECS, vols_d, tfs_d, dev):
+        lvl, est = ctx.render_adaptive(v["vol"], v["tf"], v["cam"], v["fov"], mp, v["rgb"], min_psnr_db=thr,
+                                       max_levels=2)
+        torch.cuda.synchronize()
+        single.append((lvl, est, v["rgb"].clone()))
+    views = _views(SPECS, vols_d, tfs_d, dev)
+    levels, ests = ctx.render_batch_adaptive(views, mp, min_psnr_db=thr, max_levels=2)
+    torch.cuda.synchronize()
+    for (lvl, est, rgb), v, bl, be in zip(single, views, levels, ests):
+        assert bl == lvl and be == est
+        assert torch.equal(v["rgb"], rgb)
+    if mode == "all":
+        assert all(x == 2 for x in levels)
+    else:
+        assert 0 < sum(1 for x in levels if x > 0) < len(levels)
+
+
+def test_batch_adaptive_argument_errors(ctx, fvn):
+    dev, host, vols_d, tfs, tfs_d = _setup()
+    views = _views(SPECS[:2], vols_d, tfs_d, dev)
+    with pytest.raises(fvn.FvnError, match="max_levels"):
+        ctx.render_batch_adaptive(views, wl.MarchParams(shading=1), max_levels=9)
+    assert float(views[0]["rgb"].min()) == 5.0           # nothing was enqueued
