@@ -1094,6 +1094,8 @@ def main():
         ctx.make_mask(fov, W, H, m0, i0, c0)
         tuned = {"march": autotune.tune_march(ctx, vol, tf, cam, mp, rgbam, ids=i0, count=c0),
                  "dense_march": autotune.tune_march(ctx, vol, tf, cam, mp, dense)}
+        ctx.march(vol, tf, cam, mp, rgbam, ids=i0, count=c0)
+        tuned["conv_tiles"] = autotune.tune_conv_tiles(ctx, rgbam, W, H, rgb)
         ctx.device_status()
 
     # ---- warm-up ---------------------------------------------------------

@@ -151,6 +151,13 @@ fvn_status fvn_destroy(fvn_ctx* ctx);
  *      samples only).
  *  FVN_OPT_STAGE_TIMING: 1 = fvn_render records CUDA events at its stage
  *      boundaries (read with fvn_stage_times); 0 (default) = none.
+ *  FVN_OPT_CONV_ROWS_HALF (2 or 4, default 4), FVN_OPT_CONV_ROWS_QUARTER
+ *      (1, 2 or 4, default 2), FVN_OPT_CONV_ROWS_DEC1 (1 or 2, default 1):
+ *      output rows per tile of the network's half-resolution 32-channel
+ *      convolutions, of its quarter-resolution bottleneck convolutions and of
+ *      its first decoder convolution (96 input channels).  Every setting
+ *      computes the same result bit for bit (each output pixel's sums are
+ *      formed in the same order).
  * A shadowed march (shading 2) first writes, besides the padded copy, a cell
  * volume -- per padded voxel the 2 x 2 block of voxels (x..x+1, y..y+1) in
  * the voxel type -- so that a shadow sample reads two cells instead of
@@ -164,7 +171,10 @@ enum {
     FVN_OPT_MARCH_COOP_DENSE = 7,
     FVN_OPT_MARCH_GRADIENT_VOLUME = 8,
     FVN_OPT_MARCH_COUNT_SHADOW = 9,
-    FVN_OPT_STAGE_TIMING = 10
+    FVN_OPT_STAGE_TIMING = 10,
+    FVN_OPT_CONV_ROWS_HALF = 11,
+    FVN_OPT_CONV_ROWS_QUARTER = 12,
+    FVN_OPT_CONV_ROWS_DEC1 = 13
 };
 fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value);
 

@@ -6,6 +6,8 @@ Times, with CUDA events on the current stream, the candidate settings of
   lanes of a warp must still be busy before idle lanes take new rays), the
   cooperative-finish threshold (how few rays a warp must have left before it
   marches them with all 32 lanes) and the number of persistent CTAs per SM;
+* the network: the output rows per tile of its half-resolution,
+  quarter-resolution and first decoder convolutions;
 
 on the caller's own frame, and installs the fastest in the context with
 fvn_set_option.  Every candidate computes the same result (the cooperative
@@ -53,4 +55,25 @@ def tune_march(ctx: fvn.Context, vol, tf, cam, mp, rgbam, ids=None, count=None,
     ctx.set_option(o_coop, best[1])
     ctx.set_option(o_blocks, best[2])
     return {"refill": best[0], "coop": best[1], "blocks_per_sm": best[2], "ms": results[best],
+            "candidates": {f"{k[0]}/{k[1]}/{k[2]}": round(v, 4) for k, v in results.items()}}
+
+
+def tune_conv_tiles(ctx: fvn.Context, rgbam, w, h, rgb, precision=fvn.PREC_FP16, halves=(2, 4), quarters=(1, 2, 4),
+                    dec1=(1, 2)):
+    """Pick the network's tile shapes for this frame size: output rows per tile
+    of the half-resolution 32-channel convolutions, of the quarter-resolution
+    bottleneck and of the first decoder convolution (every choice gives the
+    same output bit for bit; fewer rows per tile mean more, smaller tiles for
+    the persistent CTAs, more rows less halo re-reading)."""
+    results = {}
+    for a, b, c in itertools.product(halves, quarters, dec1):
+        ctx.set_option(fvn.OPT_CONV_ROWS_HALF, a)
+        ctx.set_option(fvn.OPT_CONV_ROWS_QUARTER, b)
+        ctx.set_option(fvn.OPT_CONV_ROWS_DEC1, c)
+        results[(a, b, c)] = _time(lambda: ctx.reconstruct(rgbam, w, h, rgb, precision=precision), reps=5)
+    best = min(results, key=results.get)
+    ctx.set_option(fvn.OPT_CONV_ROWS_HALF, best[0])
+    ctx.set_option(fvn.OPT_CONV_ROWS_QUARTER, best[1])
+    ctx.set_option(fvn.OPT_CONV_ROWS_DEC1, best[2])
+    return {"rows_half": best[0], "rows_quarter": best[1], "rows_dec1": best[2], "ms": results[best],
             "candidates": {f"{k[0]}/{k[1]}/{k[2]}": round(v, 4) for k, v in results.items()}}

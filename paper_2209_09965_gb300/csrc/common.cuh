@@ -170,6 +170,9 @@ struct fvn_ctx {
     int march_coop_dense = 0;
     int march_grad4 = 1;              // shaded marches read a gradient volume when it fits
     int march_count_shadow = 0;       // shadowed marches also count the shadow rays' samples
+    int conv_rows_half = 4;           // output rows per tile of the half-resolution 32-channel layers
+    int conv_rows_quarter = 2;        // ... of the quarter-resolution bottleneck layers
+    int conv_rows_dec1 = 1;           // ... of the first decoder layer (96 input channels)
     uint32_t* d_noise = nullptr;      // sample-map noise tiles (NULL: the hash), [frames][T][T]
     int noise_log2 = 0, noise_frames = 0;
     void* pad_buf = nullptr;          // padded copy of the volume read by the march

@@ -940,27 +940,42 @@ static fvn_status run_tc(fvn_ctx* ctx, const ReconView* views, int n, cudaStream
         const ReconPlan& B = views[i].plan;
         sp[i] = spec(B.p0, 16, nullptr, 0, B.e1a, nullptr, Hh[i], Wh[i]);
     }
-    if ((s = launch_ws<K16, 16 / CPC, 16 / CPC, 32, 4, false, F8>(ctx, sp, n, L[2], q[FP8_E1A], 0.f, st)) != FVN_OK)
+    s = ctx->conv_rows_half == 2
+            ? launch_ws<K16, 16 / CPC, 16 / CPC, 32, 2, false, F8>(ctx, sp, n, L[2], q[FP8_E1A], 0.f, st)
+            : launch_ws<K16, 16 / CPC, 16 / CPC, 32, 4, false, F8>(ctx, sp, n, L[2], q[FP8_E1A], 0.f, st);
+    if (s != FVN_OK)
         return s;
     for (int i = 0; i < n; ++i) {
         const ReconPlan& B = views[i].plan;
         sp[i] = spec(B.e1a, 32, nullptr, 0, B.e1, B.p1, Hh[i], Wh[i]);
     }
-    if ((s = launch_ws<32, 32 / CPC, 32 / CPC, 32, 4, true, F8>(ctx, sp, n, L[3], q[FP8_E1], q[FP8_P1], st)) !=
-        FVN_OK)
+    s = ctx->conv_rows_half == 2
+            ? launch_ws<32, 32 / CPC, 32 / CPC, 32, 2, true, F8>(ctx, sp, n, L[3], q[FP8_E1], q[FP8_P1], st)
+            : launch_ws<32, 32 / CPC, 32 / CPC, 32, 4, true, F8>(ctx, sp, n, L[3], q[FP8_E1], q[FP8_P1], st);
+    if (s != FVN_OK)
         return s;
     // bottleneck
     for (int i = 0; i < n; ++i) {
         const ReconPlan& B = views[i].plan;
         sp[i] = spec(B.p1, 32, nullptr, 0, B.ba, nullptr, Hf[i] / 4, Wf[i] / 4);
     }
-    if ((s = launch_ws<32, 32 / CPC, 32 / CPC, 64, 2, false, F8>(ctx, sp, n, L[4], q[FP8_BA], 0.f, st)) != FVN_OK)
+    s = ctx->conv_rows_quarter == 1
+            ? launch_ws<32, 32 / CPC, 32 / CPC, 64, 1, false, F8>(ctx, sp, n, L[4], q[FP8_BA], 0.f, st)
+            : ctx->conv_rows_quarter == 4
+                  ? launch_ws<32, 32 / CPC, 32 / CPC, 64, 4, false, F8>(ctx, sp, n, L[4], q[FP8_BA], 0.f, st)
+                  : launch_ws<32, 32 / CPC, 32 / CPC, 64, 2, false, F8>(ctx, sp, n, L[4], q[FP8_BA], 0.f, st);
+    if (s != FVN_OK)
         return s;
     for (int i = 0; i < n; ++i) {
         const ReconPlan& B = views[i].plan;
         sp[i] = spec(B.ba, 64, nullptr, 0, B.bt, nullptr, Hf[i] / 4, Wf[i] / 4);
     }
-    if ((s = launch_ws<64, 64 / CPC, 64 / CPC, 64, 2, false, F8>(ctx, sp, n, L[5], q[FP8_BT], 0.f, st)) != FVN_OK)
+    s = ctx->conv_rows_quarter == 1
+            ? launch_ws<64, 64 / CPC, 64 / CPC, 64, 1, false, F8>(ctx, sp, n, L[5], q[FP8_BT], 0.f, st)
+            : ctx->conv_rows_quarter == 4
+                  ? launch_ws<64, 64 / CPC, 64 / CPC, 64, 4, false, F8>(ctx, sp, n, L[5], q[FP8_BT], 0.f, st)
+                  : launch_ws<64, 64 / CPC, 64 / CPC, 64, 2, false, F8>(ctx, sp, n, L[5], q[FP8_BT], 0.f, st);
+    if (s != FVN_OK)
         return s;
     // dec1a on [up(bt), e1], dec1b
     {
@@ -976,13 +991,19 @@ static fvn_status run_tc(fvn_ctx* ctx, const ReconView* views, int n, cudaStream
         const ReconPlan& B = views[i].plan;
         sp[i] = spec(B.u1, 64, B.e1, 32, B.d1a, nullptr, Hh[i], Wh[i]);
     }
-    if ((s = launch_ws<96, 96 / CPC, 64 / CPC, 32, 1, false, F8>(ctx, sp, n, L[6], q[FP8_D1A], 0.f, st)) != FVN_OK)
+    s = ctx->conv_rows_dec1 == 2
+            ? launch_ws<96, 96 / CPC, 64 / CPC, 32, 2, false, F8>(ctx, sp, n, L[6], q[FP8_D1A], 0.f, st)
+            : launch_ws<96, 96 / CPC, 64 / CPC, 32, 1, false, F8>(ctx, sp, n, L[6], q[FP8_D1A], 0.f, st);
+    if (s != FVN_OK)
         return s;
     for (int i = 0; i < n; ++i) {
         const ReconPlan& B = views[i].plan;
         sp[i] = spec(B.d1a, 32, nullptr, 0, B.d1, nullptr, Hh[i], Wh[i]);
     }
-    if ((s = launch_ws<32, 32 / CPC, 32 / CPC, 32, 4, false, F8>(ctx, sp, n, L[7], q[FP8_D1], 0.f, st)) != FVN_OK)
+    s = ctx->conv_rows_half == 2
+            ? launch_ws<32, 32 / CPC, 32 / CPC, 32, 2, false, F8>(ctx, sp, n, L[7], q[FP8_D1], 0.f, st)
+            : launch_ws<32, 32 / CPC, 32 / CPC, 32, 4, false, F8>(ctx, sp, n, L[7], q[FP8_D1], 0.f, st);
+    if (s != FVN_OK)
         return s;
     // dec0a on [up(d1), e0], the up-sampling computed inside the layer from d1
     for (int i = 0; i < n; ++i) {

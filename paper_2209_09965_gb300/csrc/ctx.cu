@@ -180,6 +180,18 @@ extern "C" fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value) {
             FVN_CHECK_ARG(ctx, value == 0 || value == 1, "shadow-sample counting option must be 0 or 1");
             ctx->march_count_shadow = value;
             return FVN_OK;
+        case FVN_OPT_CONV_ROWS_HALF:
+            FVN_CHECK_ARG(ctx, value == 2 || value == 4, "half-resolution tile rows must be 2 or 4");
+            ctx->conv_rows_half = value;
+            return FVN_OK;
+        case FVN_OPT_CONV_ROWS_QUARTER:
+            FVN_CHECK_ARG(ctx, value == 1 || value == 2 || value == 4, "quarter-resolution tile rows must be 1, 2 or 4");
+            ctx->conv_rows_quarter = value;
+            return FVN_OK;
+        case FVN_OPT_CONV_ROWS_DEC1:
+            FVN_CHECK_ARG(ctx, value == 1 || value == 2, "first decoder layer tile rows must be 1 or 2");
+            ctx->conv_rows_dec1 = value;
+            return FVN_OK;
         case FVN_OPT_STAGE_TIMING:
             FVN_CHECK_ARG(ctx, value == 0 || value == 1, "stage-timing option must be 0 or 1");
             if (value && !ctx->tm_ev[0])

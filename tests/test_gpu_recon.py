@@ -189,3 +189,35 @@ def test_render_cuda_graph_replay(ctx):
     g.replay()
     torch.cuda.synchronize()
     assert torch.equal(rgb, ref) and torch.equal(sparse, ref_sparse)
+
+
+@pytest.mark.parametrize("h,w", [(1080, 1920), (130, 67)])
+def test_recon_tile_rows_are_bit_identical(fvn, h, w):
+    """The tile-shape options (output rows per tile of the half-resolution,
+    quarter-resolution and first decoder convolutions) change the launch
+    shape, not the arithmetic: every combination gives the same frame, FP16
+    and FP8."""
+    c = fvn.Context()
+    try:
+        c.load_weights(wl.net_weights(3))
+        x = torch.from_numpy(sparse_input(h, w, 9)).cuda()
+        c.calibrate_fp8(x, w, h)
+        for prec in (fvn.PREC_FP16, fvn.PREC_FP8):
+            ref = torch.empty(3, h, w, device="cuda")
+            c.reconstruct(x, w, h, ref, precision=prec)
+            for a, b, d in ((2, 1, 2), (2, 4, 1), (4, 4, 2), (2, 2, 1)):
+                c.set_option(fvn.OPT_CONV_ROWS_HALF, a)
+                c.set_option(fvn.OPT_CONV_ROWS_QUARTER, b)
+                c.set_option(fvn.OPT_CONV_ROWS_DEC1, d)
+                out = torch.full((3, h, w), 7.0, device="cuda")
+                c.reconstruct(x, w, h, out, precision=prec)
+                torch.cuda.synchronize()
+                assert torch.equal(out, ref), (prec, a, b, d)
+            c.set_option(fvn.OPT_CONV_ROWS_HALF, 4)
+            c.set_option(fvn.OPT_CONV_ROWS_QUARTER, 2)
+            c.set_option(fvn.OPT_CONV_ROWS_DEC1, 1)
+        with pytest.raises(fvn.FvnError, match="tile rows"):
+            c.set_option(fvn.OPT_CONV_ROWS_HALF, 3)
+        c.device_status()
+    finally:
+        c.close()
