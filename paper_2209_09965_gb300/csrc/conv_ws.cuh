@@ -162,22 +162,58 @@ __device__ __forceinline__ void store_px(void* base, long long plane, long long 
     }
 }
 
+// The up-sampling of the decoder input works on half2 pairs (the operands
+// the tensor core reads are FP16 / FP8 anyway): a 16-byte chunk is NP = 4
+// (FP16) or 8 (FP8, widened from E4M3) pairs.
+template <bool F8>
+__device__ __forceinline__ void chunk_to_h2(uint4 u, __half2* h) {
+    if (F8) {
+        const uint32_t w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 2; ++j) {
+                const __half2_raw r =
+                    __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)((w[i] >> (16 * j)) & 0xFFFFu), __NV_E4M3);
+                h[2 * i + j] = *reinterpret_cast<const __half2*>(&r);
+            }
+    } else {
+        const __half2* p = reinterpret_cast<const __half2*>(&u);
+#pragma unroll
+        for (int i = 0; i < 4; ++i) h[i] = p[i];
+    }
+}
+template <bool F8>
+__device__ __forceinline__ uint4 h2_to_chunk(const __half2* h) {
+    if (F8) {
+        uint32_t w[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const uint32_t lo = __nv_cvt_halfraw2_to_fp8x2(*reinterpret_cast<const __half2_raw*>(&h[2 * i]),
+                                                           __NV_SATFINITE, __NV_E4M3);
+            const uint32_t hi = __nv_cvt_halfraw2_to_fp8x2(*reinterpret_cast<const __half2_raw*>(&h[2 * i + 1]),
+                                                           __NV_SATFINITE, __NV_E4M3);
+            w[i] = lo | (hi << 16);
+        }
+        return make_uint4(w[0], w[1], w[2], w[3]);
+    }
+    uint4 u;
+    __half2* p = reinterpret_cast<__half2*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) p[i] = h[i];
+    return u;
+}
+
 // One coarse row of a chunk interpolated along x at a fine column: the
 // coarse pixels lx0, lx1 of `row` (16-byte chunks) with weight fx on lx1.
 template <bool F8>
-__device__ __forceinline__ void coarse_hlerp(const uint4* row, int lx0, int lx1, float fx, float* h) {
-    constexpr int CPC = F8 ? 16 : 8;
-    float p0[16], p1[16];
-    const uint4 u0 = row[lx0], u1 = row[lx1];
-    if (F8) {
-        unpack16q(u0, p0);
-        unpack16q(u1, p1);
-    } else {
-        unpack8h(u0, p0);
-        unpack8h(u1, p1);
-    }
+__device__ __forceinline__ void coarse_hlerp(const uint4* row, int lx0, int lx1, __half2 fx, __half2* h) {
+    constexpr int NP = F8 ? 8 : 4;
+    __half2 p0[NP], p1[NP];
+    chunk_to_h2<F8>(row[lx0], p0);
+    chunk_to_h2<F8>(row[lx1], p1);
 #pragma unroll
-    for (int j = 0; j < CPC; ++j) h[j] = fmaf(fx, p1[j] - p0[j], p0[j]);
+    for (int j = 0; j < NP; ++j) h[j] = __hfma2(fx, __hsub2(p1[j], p0[j]), p0[j]);
 }
 
 // CIN: K per tap (padded); CHG: chunks read from memory (the others stay
@@ -417,7 +453,8 @@ __global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>::thre
     } else if constexpr (UPC > 0) {
         // ---- up-sampling: warps 6.. write the stage's first UPC chunk planes
         // as the bilinear x2 up-sampling (half-pixel centres, edge clamp) of
-        // the coarse rows the producer loaded, zero outside the fine frame.
+        // the coarse rows the producer loaded, zero outside the fine frame
+        // (half2 arithmetic: the interpolated values are FP16 / FP8 operands).
         // Thread t takes (chunk, fine halo column) items t, t + 32 up_warps, ..;
         // along a column it interpolates each coarse row along x once and
         // slides a pair of rows down the HY fine rows. ----
@@ -449,10 +486,11 @@ __global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>::thre
                 }
                 const int mx = gx >> 1;
                 const int ix0 = (gx & 1) ? mx : max(mx - 1, 0), ix1 = min(ix0 + 1, Wc - 1);
-                const float fx = (gx & 1) ? 0.25f : (mx > 0 ? 0.75f : 0.0f);
+                const __half2 fx = __float2half2_rn((gx & 1) ? 0.25f : (mx > 0 ? 0.75f : 0.0f));
                 const int lx0 = ix0 - cx0, lx1 = ix1 - cx0;
                 const uint4* crows = reinterpret_cast<const uint4*>(cbuf + (size_t)c * L::cchunk);
-                float ha[CPC], hb[CPC];
+                constexpr int NP = CPC / 2;
+                __half2 ha[NP], hb[NP];
                 int ra = -1, rb = -1;                   // coarse rows held in ha / hb
 #pragma unroll
                 for (int j = 0; j < HY; ++j) {
@@ -463,12 +501,12 @@ __global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>::thre
                     }
                     const int my = gy >> 1;
                     const int iy0 = (gy & 1) ? my : max(my - 1, 0), iy1 = min(iy0 + 1, Hc - 1);
-                    const float fy = (gy & 1) ? 0.25f : (my > 0 ? 0.75f : 0.0f);
+                    const __half2 fy = __float2half2_rn((gy & 1) ? 0.25f : (my > 0 ? 0.75f : 0.0f));
                     const int ly0 = iy0 - cy0, ly1 = iy1 - cy0;
                     if (ly0 != ra) {
                         if (ly0 == rb) {
 #pragma unroll
-                            for (int k = 0; k < CPC; ++k) ha[k] = hb[k];
+                            for (int k = 0; k < NP; ++k) ha[k] = hb[k];
                         } else {
                             coarse_hlerp<F8>(crows + ly0 * L::CC, lx0, lx1, fx, ha);
                         }
@@ -477,16 +515,16 @@ __global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>::thre
                     if (ly1 != rb) {
                         if (ly1 == ra) {
 #pragma unroll
-                            for (int k = 0; k < CPC; ++k) hb[k] = ha[k];
+                            for (int k = 0; k < NP; ++k) hb[k] = ha[k];
                         } else {
                             coarse_hlerp<F8>(crows + ly1 * L::CC, lx0, lx1, fx, hb);
                         }
                         rb = ly1;
                     }
-                    float v[CPC];
+                    __half2 v[NP];
 #pragma unroll
-                    for (int k = 0; k < CPC; ++k) v[k] = fmaf(fy, hb[k] - ha[k], ha[k]);
-                    dst[j * kHXW] = F8 ? pack16q(v) : pack8h(v);
+                    for (int k = 0; k < NP; ++k) v[k] = __hfma2(fy, __hsub2(hb[k], ha[k]), ha[k]);
+                    dst[j * kHXW] = h2_to_chunk<F8>(v);
                 }
             }
             tc::fence_async_smem();   // generic-proxy writes, read next by the tensor core
