@@ -158,6 +158,10 @@ fvn_status fvn_destroy(fvn_ctx* ctx);
  *      its first decoder convolution (96 input channels).  Every setting
  *      computes the same result bit for bit (each output pixel's sums are
  *      formed in the same order).
+ *  FVN_OPT_CONV_FUSE_UP_DEC1: 1 = the first decoder convolution up-samples
+ *      the bottleneck output itself instead of reading a pass's up-sampled
+ *      copy (0, default); the in-kernel up-sampling interpolates in half
+ *      precision, so the two differ by FP16 rounding.
  * A shadowed march (shading 2) first writes, besides the padded copy, a cell
  * volume -- per padded voxel the 2 x 2 block of voxels (x..x+1, y..y+1) in
  * the voxel type -- so that a shadow sample reads two cells instead of
@@ -174,7 +178,8 @@ enum {
     FVN_OPT_STAGE_TIMING = 10,
     FVN_OPT_CONV_ROWS_HALF = 11,
     FVN_OPT_CONV_ROWS_QUARTER = 12,
-    FVN_OPT_CONV_ROWS_DEC1 = 13
+    FVN_OPT_CONV_ROWS_DEC1 = 13,
+    FVN_OPT_CONV_FUSE_UP_DEC1 = 14
 };
 fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value);
 

@@ -59,21 +59,25 @@ def tune_march(ctx: fvn.Context, vol, tf, cam, mp, rgbam, ids=None, count=None,
 
 
 def tune_conv_tiles(ctx: fvn.Context, rgbam, w, h, rgb, precision=fvn.PREC_FP16, halves=(2, 4), quarters=(1, 2, 4),
-                    dec1=(1, 2)):
+                    dec1=(1, 2), fuse_up=(0, 1)):
     """Pick the network's tile shapes for this frame size: output rows per tile
     of the half-resolution 32-channel convolutions, of the quarter-resolution
     bottleneck and of the first decoder convolution (every choice gives the
     same output bit for bit; fewer rows per tile mean more, smaller tiles for
-    the persistent CTAs, more rows less halo re-reading)."""
+    the persistent CTAs, more rows less halo re-reading), and whether the first
+    decoder convolution up-samples its input itself (the same result up to
+    FP16 rounding of the interpolation)."""
     results = {}
-    for a, b, c in itertools.product(halves, quarters, dec1):
+    for a, b, c, f in itertools.product(halves, quarters, dec1, fuse_up):
         ctx.set_option(fvn.OPT_CONV_ROWS_HALF, a)
         ctx.set_option(fvn.OPT_CONV_ROWS_QUARTER, b)
         ctx.set_option(fvn.OPT_CONV_ROWS_DEC1, c)
-        results[(a, b, c)] = _time(lambda: ctx.reconstruct(rgbam, w, h, rgb, precision=precision), reps=5)
+        ctx.set_option(fvn.OPT_CONV_FUSE_UP_DEC1, f)
+        results[(a, b, c, f)] = _time(lambda: ctx.reconstruct(rgbam, w, h, rgb, precision=precision), reps=5)
     best = min(results, key=results.get)
     ctx.set_option(fvn.OPT_CONV_ROWS_HALF, best[0])
     ctx.set_option(fvn.OPT_CONV_ROWS_QUARTER, best[1])
     ctx.set_option(fvn.OPT_CONV_ROWS_DEC1, best[2])
-    return {"rows_half": best[0], "rows_quarter": best[1], "rows_dec1": best[2], "ms": results[best],
-            "candidates": {f"{k[0]}/{k[1]}/{k[2]}": round(v, 4) for k, v in results.items()}}
+    ctx.set_option(fvn.OPT_CONV_FUSE_UP_DEC1, best[3])
+    return {"rows_half": best[0], "rows_quarter": best[1], "rows_dec1": best[2], "fuse_up_dec1": best[3],
+            "ms": results[best], "candidates": {"/".join(map(str, k)): round(v, 4) for k, v in results.items()}}

@@ -173,6 +173,7 @@ struct fvn_ctx {
     int conv_rows_half = 4;           // output rows per tile of the half-resolution 32-channel layers
     int conv_rows_quarter = 2;        // ... of the quarter-resolution bottleneck layers
     int conv_rows_dec1 = 1;           // ... of the first decoder layer (96 input channels)
+    int conv_fuse_up_dec1 = 0;        // first decoder layer computes its up-sampled input itself
     uint32_t* d_noise = nullptr;      // sample-map noise tiles (NULL: the hash), [frames][T][T]
     int noise_log2 = 0, noise_frames = 0;
     void* pad_buf = nullptr;          // padded copy of the volume read by the march

@@ -977,8 +977,19 @@ static fvn_status run_tc(fvn_ctx* ctx, const ReconView* views, int n, cudaStream
                   : launch_ws<64, 64 / CPC, 64 / CPC, 64, 2, false, F8>(ctx, sp, n, L[5], q[FP8_BT], 0.f, st);
     if (s != FVN_OK)
         return s;
-    // dec1a on [up(bt), e1], dec1b
-    {
+    // dec1a on [up(bt), e1]: the up-sampling of bt in its own pass, or
+    // inside the convolution (FVN_OPT_CONV_FUSE_UP_DEC1), then dec1b
+    if (ctx->conv_fuse_up_dec1) {
+        for (int i = 0; i < n; ++i) {
+            const ReconPlan& B = views[i].plan;
+            sp[i] = spec(B.bt, 64, B.e1, 32, B.d1a, nullptr, Hh[i], Wh[i]);
+        }
+        s = ctx->conv_rows_dec1 == 2
+                ? launch_ws<96, 96 / CPC, 64 / CPC, 32, 2, false, F8, false, 64 / CPC>(ctx, sp, n, L[6],
+                                                                                    q[FP8_D1A], 0.f, st)
+                : launch_ws<96, 96 / CPC, 64 / CPC, 32, 1, false, F8, false, 64 / CPC>(ctx, sp, n, L[6],
+                                                                                    q[FP8_D1A], 0.f, st);
+    } else {
         const void* c[kMaxViews];
         void* f[kMaxViews];
         for (int i = 0; i < n; ++i) {
@@ -986,16 +997,15 @@ static fvn_status run_tc(fvn_ctx* ctx, const ReconView* views, int n, cudaStream
             f[i] = views[i].plan.u1;
         }
         if ((s = upsample_views<F8>(ctx, c, f, Hh, Wh, n, 64, st)) != FVN_OK) return s;
+        for (int i = 0; i < n; ++i) {
+            const ReconPlan& B = views[i].plan;
+            sp[i] = spec(B.u1, 64, B.e1, 32, B.d1a, nullptr, Hh[i], Wh[i]);
+        }
+        s = ctx->conv_rows_dec1 == 2
+                ? launch_ws<96, 96 / CPC, 64 / CPC, 32, 2, false, F8>(ctx, sp, n, L[6], q[FP8_D1A], 0.f, st)
+                : launch_ws<96, 96 / CPC, 64 / CPC, 32, 1, false, F8>(ctx, sp, n, L[6], q[FP8_D1A], 0.f, st);
     }
-    for (int i = 0; i < n; ++i) {
-        const ReconPlan& B = views[i].plan;
-        sp[i] = spec(B.u1, 64, B.e1, 32, B.d1a, nullptr, Hh[i], Wh[i]);
-    }
-    s = ctx->conv_rows_dec1 == 2
-            ? launch_ws<96, 96 / CPC, 64 / CPC, 32, 2, false, F8>(ctx, sp, n, L[6], q[FP8_D1A], 0.f, st)
-            : launch_ws<96, 96 / CPC, 64 / CPC, 32, 1, false, F8>(ctx, sp, n, L[6], q[FP8_D1A], 0.f, st);
-    if (s != FVN_OK)
-        return s;
+    if (s != FVN_OK) return s;
     for (int i = 0; i < n; ++i) {
         const ReconPlan& B = views[i].plan;
         sp[i] = spec(B.d1a, 32, nullptr, 0, B.d1, nullptr, Hh[i], Wh[i]);

@@ -192,6 +192,10 @@ extern "C" fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value) {
             FVN_CHECK_ARG(ctx, value == 1 || value == 2, "first decoder layer tile rows must be 1 or 2");
             ctx->conv_rows_dec1 = value;
             return FVN_OK;
+        case FVN_OPT_CONV_FUSE_UP_DEC1:
+            FVN_CHECK_ARG(ctx, value == 0 || value == 1, "decoder up-sampling option must be 0 or 1");
+            ctx->conv_fuse_up_dec1 = value;
+            return FVN_OK;
         case FVN_OPT_STAGE_TIMING:
             FVN_CHECK_ARG(ctx, value == 0 || value == 1, "stage-timing option must be 0 or 1");
             if (value && !ctx->tm_ev[0])

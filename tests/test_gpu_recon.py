@@ -221,3 +221,29 @@ def test_recon_tile_rows_are_bit_identical(fvn, h, w):
         c.device_status()
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("h,w,seed", [(64, 128, 0), (45, 70, 2), (4, 4, 3), (130, 67, 5), (1080, 1920, 6)])
+def test_recon_fused_decoder_upsampling_matches_oracle(fvn, h, w, seed):
+    """FVN_OPT_CONV_FUSE_UP_DEC1: the first decoder convolution up-samples the
+    bottleneck output itself (half precision); the frame still meets the FP16
+    bar against the oracle, for every tile-row setting of that layer."""
+    c = fvn.Context()
+    try:
+        c.load_weights(wl.net_weights(3))
+        c.set_option(fvn.OPT_CONV_FUSE_UP_DEC1, 1)
+        sp = sparse_input(h, w, seed)
+        ref = onet.forward(onet.unpack(wl.net_weights(3)), sp) if h * w < 100000 else None
+        outs = []
+        for rows in (1, 2):
+            c.set_option(fvn.OPT_CONV_ROWS_DEC1, rows)
+            outs.append(gpu_recon(c, sp))
+        assert np.array_equal(outs[0], outs[1])
+        c.set_option(fvn.OPT_CONV_FUSE_UP_DEC1, 0)
+        sep = gpu_recon(c, sp)
+        assert np.abs(outs[0] - sep).max() < 1e-2
+        if ref is not None:
+            assert np.abs(outs[0] - ref).max() < FP16_TOL
+        c.device_status()
+    finally:
+        c.close()
