@@ -413,21 +413,25 @@ __device__ __forceinline__ int tf_index(const MarchArgs& a, float tfmax, float v
 __device__ __forceinline__ float tf_alpha(const MarchArgs& a, const float4* s_tf, float tfmax, float v) {
     float fr;
     const int ti = tf_index(a, tfmax, v, fr);
-    const float2 p = reinterpret_cast<const float2*>(s_tf + a.ntf)[ti];
+    const float2 p = reinterpret_cast<const float2*>(s_tf + a.ntf + 1)[ti];
     return fmaf(fr, p.y - p.x, p.x);
 }
 
-// Shared-memory slots (float4) of a TF of n entries: the entries, and for
+// Shared-memory slots (float4) of a TF of n entries: the entries and a copy
+// of the last one (so an index at the top end needs no clamp), and for
 // shadowed marches the opacity pairs after them.
-__host__ __device__ __forceinline__ int tf_slots(int n, int shade) { return shade == 2 ? n + (n + 1) / 2 : n; }
+__host__ __device__ __forceinline__ int tf_slots(int n, int shade) {
+    return shade == 2 ? n + 1 + (n + 1) / 2 : n + 1;
+}
 
-// Copy a TF of n entries into shared memory at s (and its opacity pairs for
-// shadowed marches); the block's threads share the work.
+// Copy a TF of n entries (and its last entry once more) into shared memory
+// at s, and for shadowed marches its opacity pairs; the block's threads
+// share the work.
 template <int SHADE>
 __device__ __forceinline__ void load_tf(float4* s, const float4* __restrict__ tf, int n) {
-    for (int i = threadIdx.x; i < n; i += blockDim.x) s[i] = tf[i];
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) s[i] = tf[min(i, n - 1)];
     if (SHADE == 2) {
-        float2* p = reinterpret_cast<float2*>(s + n);
+        float2* p = reinterpret_cast<float2*>(s + n + 1);
         for (int i = threadIdx.x; i < n; i += blockDim.x) p[i] = make_float2(tf[i].w, tf[min(i + 1, n - 1)].w);
     }
 }
@@ -692,8 +696,11 @@ struct Grad4Src {
             }
         const float2 vx = lerp2(lerp2(lo[0][0], lo[0][1], ty), lerp2(lo[1][0], lo[1][1], ty), tz);
         const float2 yz = lerp2(lerp2(hi[0][0], hi[0][1], ty), lerp2(hi[1][0], hi[1][1], ty), tz);
+        // v is in [0, 1] up to rounding (the copy holds clamped values): the
+        // entry below v (n - 1) needs only a floor at 0 and a cap at n - 1,
+        // the padded last entry covers ti + 1 = n
         float fr;
-        const int ti = tf_index(a, tfmax, vx.x, fr);
+        const int ti = min(floor_frac(fmaxf(vx.x * tfmax, 0.0f), fr), a.ntf - 1);
         const float4 c0 = s_tf[ti], c1 = s_tf[ti + 1];
         const float2 f2 = make_float2(fr, fr);
         const float2 rg = lerp2(lo2(c0), lo2(c1), f2), ba = lerp2(hi2(c0), hi2(c1), f2);
