@@ -78,8 +78,13 @@ NET_FLOPS_PER_PX = 2 * 9 * (5 * 16 + 16 * 16 + 48 * 16 + 16 * 16) + 2 * 9 * (16 
 # FP32 peak from unit counts: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # ncu counters of one sparse-march launch of this workload (the capture named
-# in "profile"; None until the current kernel has been captured)
-MARCH_NCU = None
+# in "profile": caches flushed before the replay, so its duration is above the
+# live one)
+MARCH_NCU = {"dram_bytes": 262.6e6, "dram_read_bytes": 244.2e6, "dram_write_bytes": 18.4e6,
+             "l2_to_l1_read_bytes": 749.6e6, "l2_to_l1_gbs": 962.1, "l1_throughput_pct": 74.0,
+             "l2_throughput_pct": 7.3, "dram_throughput_pct": 4.3, "l1_hit_pct": 86.7, "l2_hit_pct": 60.6,
+             "issue_active_pct": 51.0, "ncu_duration_us": 779.1,
+             "profile": "profiles/march_kernel_foveated1080p.md"}
 def dist_env():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -307,6 +312,7 @@ def run_profile_case():
     vol_np, tf_np, cam, fov, mp = wl.foveated_1080p_workload(seed=2, frame=0, n=VOL_N)
     ctx = fvn.Context()
     ctx.load_weights(weights)
+    ctx.set_option(fvn.OPT_MARCH_COOP, 4)     # the launch shape the autotuner picks for this frame
     vol = torch.from_numpy(vol_np).to(dev)
     tf = torch.from_numpy(tf_np).to(dev)
     mask = torch.empty(H, W, dtype=torch.uint8, device=dev)
