@@ -491,6 +491,24 @@ fvn_status fvn_conv_bwd(const float* xa, int ca, const float* xb, int cb, int n,
                         const float* w, int cout, int k, const float* gy, const float* y_relu,
                         float* gxa, float* gxb, float* gw, float* gb, void* stream);
 
+/* The 3x3 layers on the tensor cores (tcgen05, BF16 operands rounded from
+ * the FP32 tensors while staged, FP32 accumulation; paper: "Model Precision &
+ * Optimization" -- FP32 master weights, 16-bit arithmetic).
+ * fvn_conv3x3_fwd_bf16: as fvn_conv_fwd with k = 3.  fvn_conv3x3_dgrad_bf16:
+ * dL/dx of the layer (ca + cb input channels, cout outputs, weights w
+ * [cout][ca+cb][3][3]) from gy [N][cout][H][W], masked by y_relu > 0 when
+ * y_relu is set, into gxa [N][ca][H][W] and gxb [N][cb][H][W] (either may be
+ * NULL to skip).  Channel pairs (in -> out, padded to multiples of 16) of
+ * 16/32/48/64/96 channels as the slim network's layers need;
+ * FVN_ERR_UNSUPPORTED for others.  fvn_train_device_status synchronises and
+ * returns FVN_ERR_TIMEOUT (clearing the flag) when one of these kernels gave
+ * up a bounded wait. */
+fvn_status fvn_conv3x3_fwd_bf16(const float* xa, int ca, const float* xb, int cb, int n, int h, int w_,
+                                const float* w, const float* b, int cout, int relu, float* y, void* stream);
+fvn_status fvn_conv3x3_dgrad_bf16(const float* gy, const float* y_relu, int cout, int n, int h, int w_,
+                                  const float* w, int ca, int cb, float* gxa, float* gxb, void* stream);
+fvn_status fvn_train_device_status(void);
+
 /* 2x2 average pooling and its adjoint ([N][C][H][W] -> [N][C][H/2][W/2]). */
 fvn_status fvn_avgpool2_fwd(const float* x, int nc, int h, int w_, float* y, void* stream);
 fvn_status fvn_avgpool2_bwd(const float* gy, int nc, int h, int w_, float* gx, void* stream);

@@ -198,12 +198,16 @@ namespace fvn {
 // kernel).  `done` is the kernel's own record of the devices already set up
 // (bit d for device d < 64; higher device indices set it on every call).
 template <typename K>
-inline cudaError_t opt_in_smem(const fvn_ctx* ctx, K kern, int bytes, std::atomic<unsigned long long>& done) {
-    const unsigned long long bit = ctx->device < 64 ? 1ull << ctx->device : 0ull;
+inline cudaError_t opt_in_smem(int device, K kern, int bytes, std::atomic<unsigned long long>& done) {
+    const unsigned long long bit = device >= 0 && device < 64 ? 1ull << device : 0ull;
     if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
     const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
     if (e == cudaSuccess && bit) done.fetch_or(bit, std::memory_order_acq_rel);
     return e;
+}
+template <typename K>
+inline cudaError_t opt_in_smem(const fvn_ctx* ctx, K kern, int bytes, std::atomic<unsigned long long>& done) {
+    return opt_in_smem(ctx->device, kern, bytes, done);
 }
 
 fvn_status set_error(fvn_ctx* ctx, fvn_status st, const char* fmt, ...);

@@ -1,0 +1,408 @@
+// Tensor-core convolutions of the training step (paper: "Training" and
+// "Model Precision & Optimization": the network is trained with FP32 master
+// weights; here its 3x3 layers' forward pass and data gradient run as
+// implicit GEMMs on the 5th-generation tensor cores).
+//
+// The training pass keeps FP32 NCHW tensors ([N][C][H][W]).  A CTA stages a
+// tile's input halo (TR + 2 rows x 130 pixels) into shared memory as BF16
+// chunk planes (8 channels = 16 bytes per pixel: the K-major core-matrix
+// layout, so a tap is only a descriptor start address), rounding the FP32
+// values to BF16 on the way -- BF16 keeps FP32's exponent range, so the
+// data gradients need no loss scaling -- and issues, per output row, one
+// tcgen05.mma (kind::f16 with BF16 operands, M = 128 pixels, N = output
+// channels, K = 16) per tap and channel pair into an FP32 TMEM accumulator.
+// The weights are read from the FP32 master copy and converted in the
+// prologue: as they are for the forward pass, transposed (input <-> output
+// channel) and flipped (tap 8 - t) for the data gradient, which is the
+// convolution of the output gradient with them.  The data gradient's input
+// is the output gradient times the layer's ReLU mask (saved output > 0),
+// applied while staging.  Epilogue: bias and ReLU (forward), FP32 stores of
+// one pixel per thread, channel by channel (coalesced along x); the data
+// gradient's channels go to the two tensors of a concatenated input.
+//
+// Every mbarrier wait has an iteration limit; a wait that gives up sets the
+// error flag the caller passed and the CTA leaves its loop.
+#include <cuda_bf16.h>
+
+#include <algorithm>
+
+#include "common.cuh"
+#include "tc.cuh"
+
+namespace fvn {
+namespace ttc {
+
+constexpr int TW = 128;                 // output pixels per tile row = MMA M
+constexpr int HXW = TW + 2;             // halo pixels per row
+constexpr int kThreads = 256;
+constexpr uint32_t kLimit = 1u << 26;
+
+struct Args {
+    const float* src0;                  // input channels [0, c0): [N][c0][H][W]
+    const float* src1;                  // input channels [c0, cin): [N][cin - c0][H][W] (NULL when cin == c0)
+    const float* mask;                  // data gradient: src0 is used where mask > 0 (same layout), else NULL
+    int c0, cin, cout;
+    const float* w;                     // the layer's FP32 weights [cout_layer][cin_layer][3][3]
+    const float* bias;                  // forward: [cout] (NULL: none)
+    int dgrad;                          // 1: weights transposed and flipped (data gradient)
+    int relu;
+    float* out0;                        // output channels [0, o0): [N][o0][H][W] (NULL: not written)
+    float* out1;                        // output channels [o0, cout): [N][cout - o0][H][W] (NULL: not written)
+    int o0;
+    int n, H, W;
+    int tiles_x, tiles_img, ntiles;
+    int* error;
+};
+
+// Shared-memory layout of an instance: CINP input channels (multiple of 16),
+// COUTP output channels (multiple of 16), TR output rows per tile.
+template <int CINP, int COUTP, int TR>
+struct Layout {
+    static constexpr int CH = CINP / 8;                                    // chunk planes
+    static constexpr int HY = TR + 2;
+    static constexpr size_t w_bytes = 9ull * CINP * COUTP * 2;             // [tap][CH][COUTP][8] BF16
+    static constexpr size_t halo = (size_t)CH * HY * HXW * 16 + 32;        // one halo buffer (+ MMA over-read)
+    static constexpr size_t halo_r = (halo + 127) / 128 * 128;
+    static constexpr size_t w_off = 0;
+    static constexpr size_t halo_off = (w_bytes + 1023) / 1024 * 1024;
+    static constexpr int NBUF = halo_off + 2 * halo_r + COUTP * 4 + 64 <= 220 * 1024 ? 2 : 1;
+    static constexpr size_t bias_off = halo_off + NBUF * halo_r;
+    static constexpr size_t bar_off = bias_off + COUTP * 4;
+    static constexpr size_t bytes = bar_off + 16;
+    static constexpr uint32_t acc_cols = TR * COUTP;
+    static constexpr uint32_t tmem_cols = acc_cols <= 32 ? 32 : acc_cols <= 64 ? 64 : acc_cols <= 128 ? 128
+                                        : acc_cols <= 256 ? 256 : 512;
+    static_assert(acc_cols <= 512, "accumulators exceed the TMEM");
+    static_assert(COUTP % 16 == 0 && COUTP <= 256 && CINP % 16 == 0, "unsupported shape");
+    static_assert(bytes <= 227 * 1024, "shared memory");
+};
+
+// BF16 instruction descriptor of kind::f16: FP32 accumulator, A and B BF16,
+// both K-major, shape M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ uint4 pack8bf(const float* v) {
+    uint4 r;
+    __nv_bfloat162 h0 = __floats2bfloat162_rn(v[0], v[1]), h1 = __floats2bfloat162_rn(v[2], v[3]);
+    __nv_bfloat162 h2 = __floats2bfloat162_rn(v[4], v[5]), h3 = __floats2bfloat162_rn(v[6], v[7]);
+    r.x = *reinterpret_cast<uint32_t*>(&h0);
+    r.y = *reinterpret_cast<uint32_t*>(&h1);
+    r.z = *reinterpret_cast<uint32_t*>(&h2);
+    r.w = *reinterpret_cast<uint32_t*>(&h3);
+    return r;
+}
+
+// Element (tap, input channel ci, output channel co) of this GEMM's weights.
+__device__ __forceinline__ float weight_elem(const Args& a, int tap, int ci, int co) {
+    if (a.dgrad) return __ldg(a.w + ((size_t)ci * a.cout + co) * 9 + (8 - tap));   // layer [ci][co][8 - tap]
+    return __ldg(a.w + ((size_t)co * a.cin + ci) * 9 + tap);
+}
+
+template <int CINP, int COUTP, int TR>
+__global__ void __launch_bounds__(kThreads, 2) conv3x3_train_kernel(const __grid_constant__ Args a) {
+    using L = Layout<CINP, COUTP, TR>;
+    constexpr int CH = L::CH, HY = L::HY;
+    static_assert(TR % 2 == 0, "the two warp groups of the epilogue split the rows");
+    extern __shared__ __align__(1024) unsigned char smem[];
+    float* sBias = reinterpret_cast<float*>(smem + L::bias_off);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::bar_off);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::bar_off + 8);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    {   // this GEMM's weights as BF16 chunks [tap][CH][COUTP][8], zero beyond cin / cout: the
+        // layer's FP32 array is read in order (coalesced) and each element scattered to its slot
+        uint4* z = reinterpret_cast<uint4*>(smem + L::w_off);
+        for (int i = tid; i < (int)(L::w_bytes / 16); i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+        for (int i = tid; i < COUTP; i += kThreads) sBias[i] = (a.bias && i < a.cout) ? __ldg(a.bias + i) : 0.f;
+        __syncthreads();
+        __nv_bfloat16* wb = reinterpret_cast<__nv_bfloat16*>(smem + L::w_off);
+        const int total = a.cin * a.cout * 9;
+        for (int i = tid; i < total; i += kThreads) {
+            const int t = i % 9, r = i / 9;
+            // forward: the layer is [cout][cin][t]; data gradient: [cin][cout][8 - tap]
+            int ci, co, tap;
+            if (a.dgrad) {
+                co = r % a.cout;
+                ci = r / a.cout;
+                tap = 8 - t;
+            } else {
+                ci = r % a.cin;
+                co = r / a.cin;
+                tap = t;
+            }
+            wb[((size_t)(tap * CH + ci / 8) * COUTP + co) * 8 + (ci & 7)] = __float2bfloat16_rn(__ldg(a.w + i));
+        }
+    }
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, L::tmem_cols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_async_smem();
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const uint32_t sW_u = tc::smem_addr(smem + L::w_off), sH_u = tc::smem_addr(smem + L::halo_off);
+    constexpr uint32_t idesc = idesc_bf16(128, COUTP);
+    const size_t plane = (size_t)a.H * a.W;
+
+    // the input halo of a tile as BF16 chunk planes [CH][HY][HXW][8], one
+    // 16-byte chunk (8 channels of a pixel) per item, consecutive items along x
+    auto stage = [&](int tile, int buf) {
+        const int img = tile / a.tiles_img, lt = tile - img * a.tiles_img;
+        const int ty = lt / a.tiles_x, tx = lt - ty * a.tiles_x;
+        const int y0 = ty * TR, x0 = tx * TW;
+        const float* s0 = a.src0 + (size_t)img * a.c0 * plane;
+        const float* s1 = a.src1 ? a.src1 + (size_t)img * (a.cin - a.c0) * plane : nullptr;
+        const float* mk = a.mask ? a.mask + (size_t)img * a.c0 * plane : nullptr;
+        unsigned char* sH = smem + L::halo_off + (size_t)buf * L::halo_r;
+#pragma unroll 2
+        for (int i = tid; i < CH * HY * HXW; i += kThreads) {
+            const int hx = i % HXW, t = i / HXW, hy = t % HY, ch = t / HY;
+            const int gy = y0 + hy - 1, gx = x0 + hx - 1;
+            // every load issued without a branch (addresses clamped into the
+            // tensors, the values outside the frame / channels zeroed after)
+            const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
+            const size_t p = (size_t)min(max(gy, 0), a.H - 1) * a.W + min(max(gx, 0), a.W - 1);
+            float v[8], m[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int c = min(ch * 8 + j, a.cin - 1);
+                const float* src = c < a.c0 ? s0 + (size_t)c * plane : s1 + (size_t)(c - a.c0) * plane;
+                v[j] = __ldg(src + p);
+                m[j] = 1.f;
+            }
+            if (mk) {
+#pragma unroll
+                for (int j = 0; j < 8; ++j) m[j] = __ldg(mk + (size_t)min(ch * 8 + j, a.c0 - 1) * plane + p);
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) v[j] = (in && ch * 8 + j < a.cin && m[j] > 0.f) ? v[j] : 0.f;
+            *reinterpret_cast<uint4*>(sH + ((size_t)(ch * HY + hy) * HXW + hx) * 16) = pack8bf(v);
+        }
+    };
+
+    uint32_t phase = 0;
+    bool failed = false;
+    int buf = 0;
+    int tile = blockIdx.x;
+    if (tile < a.ntiles) {
+        stage(tile, 0);
+        tc::fence_async_smem();
+        __syncthreads();
+    }
+    for (; tile < a.ntiles; tile += gridDim.x) {
+        const int img = tile / a.tiles_img, lt = tile - img * a.tiles_img;
+        const int ty = lt / a.tiles_x, tx = lt - ty * a.tiles_x;
+        const int y0 = ty * TR, x0 = tx * TW;
+        const int next = tile + gridDim.x;
+        if (tid == 0) {   // one thread issues every MMA of the tile
+            tc::fence_after_sync();
+            const uint64_t a0 = tc::smem_desc(sH_u + (uint32_t)(buf * L::halo_r), HY * HXW * 16, 128);
+            const uint64_t b0 = tc::smem_desc(sW_u, COUTP * 16, 128);
+#pragma unroll 1
+            for (int tap = 0; tap < 9; ++tap) {
+                const int dy = tap / 3, dx = tap - dy * 3;
+#pragma unroll
+                for (int kc = 0; kc < CH / 2; ++kc) {
+                    const uint64_t bd = b0 + (uint64_t)((tap * CH + 2 * kc) * COUTP);
+#pragma unroll
+                    for (int r = 0; r < TR; ++r) {
+                        const uint64_t ad = a0 + (uint64_t)(((2 * kc) * HY + r + dy) * HXW + dx);
+                        tc::mma_f16(tmem + (uint32_t)(r * COUTP), ad, bd, idesc, (tap | kc) != 0);
+                    }
+                }
+            }
+            tc::mma_commit(bar);
+        }
+        if (L::NBUF == 2 && next < a.ntiles) stage(next, buf ^ 1);   // overlaps the MMAs
+        if (!tc::mbar_wait(bar, phase, kLimit)) {
+            failed = true;
+            break;
+        }
+        phase ^= 1u;
+        tc::fence_after_sync();
+        // ---- epilogue: one pixel per thread; warp group warp / 4 takes half the rows
+        const int q = warp & 3, px = q * 32 + lane, x = x0 + px;
+        const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+        constexpr int RG = TR / 2;
+        const int r_lo = (warp >> 2) * RG;
+#pragma unroll 1
+        for (int r = r_lo; r < r_lo + RG; ++r) {
+            const int y = y0 + r;
+            const bool inside = y < a.H && x < a.W;
+#pragma unroll 1
+            for (int cb = 0; cb < COUTP; cb += 16) {
+                float v[16];
+                tc::tmem_ld16(tmem + lane_base + (uint32_t)(r * COUTP + cb), v);   // the whole warp
+                if (inside) {
+                    const size_t pix = (size_t)y * a.W + x;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) {
+                        const int c = cb + j;
+                        if (c >= a.cout) break;
+                        float o = v[j] + sBias[c];
+                        if (a.relu) o = fmaxf(o, 0.f);
+                        if (c < a.o0) {
+                            if (a.out0) a.out0[((size_t)img * a.o0 + c) * plane + pix] = o;
+                        } else if (a.out1) {
+                            a.out1[((size_t)img * (a.cout - a.o0) + (c - a.o0)) * plane + pix] = o;
+                        }
+                    }
+                }
+            }
+        }
+        if (L::NBUF == 1 && next < a.ntiles) stage(next, 0);   // the MMAs are done with the buffer
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();                                        // TMEM read, next tile staged
+        buf ^= L::NBUF - 1;
+    }
+    if (failed) atomicExch(a.error, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, L::tmem_cols);
+    }
+}
+
+}  // namespace ttc
+}  // namespace fvn
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+namespace fvn {
+namespace {
+
+int g_error_dev = -1;          // device of the error flag below
+int* g_error = nullptr;        // set by a kernel whose bounded wait gave up
+
+fvn_status error_flag(int** out) {
+    int dev = 0;
+    FVN_CUDA(nullptr, cudaGetDevice(&dev));
+    if (!g_error || g_error_dev != dev) {
+        int* p = nullptr;
+        FVN_CUDA(nullptr, cudaMalloc(&p, sizeof(int)));
+        FVN_CUDA(nullptr, cudaMemset(p, 0, sizeof(int)));
+        g_error = p;   // one flag per process and device in use (the previous device's flag is kept)
+        g_error_dev = dev;
+    }
+    *out = g_error;
+    return FVN_OK;
+}
+
+template <int CINP, int COUTP, int TR>
+fvn_status launch_train(ttc::Args a, cudaStream_t st) {
+    using L = ttc::Layout<CINP, COUTP, TR>;
+    auto kern = ttc::conv3x3_train_kernel<CINP, COUTP, TR>;
+    static std::atomic<unsigned long long> configured{0};
+    int dev = 0;
+    FVN_CUDA(nullptr, cudaGetDevice(&dev));
+    FVN_CUDA(nullptr, opt_in_smem(dev, kern, (int)L::bytes, configured));
+    int sms = 0;
+    FVN_CUDA(nullptr, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    int per_sm = 0;   // CTAs resident at once (registers, shared memory), within the TMEM
+    FVN_CUDA(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ttc::kThreads, L::bytes));
+    per_sm = std::min(per_sm, (int)(512 / L::tmem_cols));
+    if (per_sm < 1) return set_error(nullptr, FVN_ERR_CUDA, "training conv kernel does not fit on an SM");
+    a.tiles_x = (a.W + ttc::TW - 1) / ttc::TW;
+    a.tiles_img = a.tiles_x * ((a.H + TR - 1) / TR);
+    const long long nt = (long long)a.tiles_img * a.n;
+    if (nt >= (1ll << 31)) return set_error(nullptr, FVN_ERR_ARG, "too many tiles");
+    a.ntiles = (int)nt;
+    fvn_status s = error_flag(&a.error);
+    if (s != FVN_OK) return s;
+    const int grid = (int)std::min<long long>(nt, (long long)sms * per_sm);
+    kern<<<grid, ttc::kThreads, L::bytes, st>>>(a);
+    FVN_LAUNCH_CHECK(nullptr);
+    return FVN_OK;
+}
+
+// The instance for a GEMM of cin -> cout channels (padded to multiples of 16).
+fvn_status dispatch(const ttc::Args& a, cudaStream_t st) {
+    const int ci = (a.cin + 15) & ~15, co = (a.cout + 15) & ~15;
+#define FVN_TTC(CI, CO, TR) \
+    if (ci == CI && co == CO) return launch_train<CI, CO, TR>(a, st);
+    FVN_TTC(16, 16, 4)
+    FVN_TTC(16, 32, 4)
+    FVN_TTC(16, 48, 4)
+    FVN_TTC(32, 16, 4)
+    FVN_TTC(32, 32, 4)
+    FVN_TTC(32, 64, 4)
+    FVN_TTC(32, 96, 4)
+    FVN_TTC(48, 16, 2)
+    FVN_TTC(64, 32, 2)
+    FVN_TTC(64, 64, 2)
+    FVN_TTC(96, 32, 2)
+#undef FVN_TTC
+    return set_error(nullptr, FVN_ERR_UNSUPPORTED, "no tensor-core training convolution for %d -> %d channels",
+                     a.cin, a.cout);
+}
+
+}  // namespace
+}  // namespace fvn
+
+using namespace fvn;
+
+extern "C" fvn_status fvn_conv3x3_fwd_bf16(const float* xa, int ca, const float* xb, int cb, int n, int h, int w_,
+                                           const float* w, const float* b, int cout, int relu, float* y,
+                                           void* stream) {
+    FVN_CHECK_ARG(nullptr, xa && w && y && (cb == 0 || xb), "null tensor");
+    FVN_CHECK_ARG(nullptr, ca >= 1 && cb >= 0 && n >= 1 && h >= 1 && w_ >= 1 && cout >= 1, "bad sizes");
+    ttc::Args a{};
+    a.src0 = xa;
+    a.c0 = ca;
+    a.src1 = cb ? xb : nullptr;
+    a.cin = ca + cb;
+    a.cout = cout;
+    a.w = w;
+    a.bias = b;
+    a.relu = relu != 0;
+    a.out0 = y;
+    a.o0 = cout;
+    a.n = n;
+    a.H = h;
+    a.W = w_;
+    return dispatch(a, as_stream(stream));
+}
+
+extern "C" fvn_status fvn_conv3x3_dgrad_bf16(const float* gy, const float* y_relu, int cout, int n, int h, int w_,
+                                             const float* w, int ca, int cb, float* gxa, float* gxb, void* stream) {
+    FVN_CHECK_ARG(nullptr, gy && w && (gxa || gxb), "null tensor");
+    FVN_CHECK_ARG(nullptr, ca >= 1 && cb >= 0 && n >= 1 && h >= 1 && w_ >= 1 && cout >= 1, "bad sizes");
+    FVN_CHECK_ARG(nullptr, cb > 0 || gxb == nullptr, "gxb without second input channels");
+    ttc::Args a{};
+    a.src0 = gy;
+    a.c0 = cout;
+    a.mask = y_relu;
+    a.cin = cout;            // this GEMM runs from the layer's output channels ...
+    a.cout = ca + cb;        // ... to its input channels
+    a.w = w;
+    a.dgrad = 1;
+    a.out0 = gxa;
+    a.out1 = gxb;
+    a.o0 = ca;
+    a.n = n;
+    a.H = h;
+    a.W = w_;
+    return dispatch(a, as_stream(stream));
+}
+
+extern "C" fvn_status fvn_train_device_status(void) {
+    if (!g_error) return FVN_OK;
+    FVN_CUDA(nullptr, cudaDeviceSynchronize());
+    int flag = 0;
+    FVN_CUDA(nullptr, cudaMemcpy(&flag, g_error, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        FVN_CUDA(nullptr, cudaMemset(g_error, 0, sizeof(int)));
+        return set_error(nullptr, FVN_ERR_TIMEOUT, "a training convolution gave up waiting for the tensor cores");
+    }
+    return FVN_OK;
+}

@@ -34,6 +34,7 @@ EXPORTS = (
     "fvn_weight_count_recurrent", "fvn_reconstruct_recurrent", "fvn_render_recurrent", "fvn_selftest_wait_timeout",
     "fvn_wnet_weight_count", "fvn_load_wnet_weights", "fvn_reconstruct_wnet", "fvn_filter3_fwd", "fvn_filter3_bwd",
     "fvn_wnet_join_fwd", "fvn_wnet_join_bwd", "fvn_stage_times", "fvn_render_batch_adaptive",
+    "fvn_conv3x3_fwd_bf16", "fvn_conv3x3_dgrad_bf16", "fvn_train_device_status",
 )
 WNET_MAX_LEVELS = 4
 MAX_VIEWS = 16
@@ -144,6 +145,9 @@ def _load():
         "fvn_wnet_join_bwd": [P, P, P, I, I, I, P, P, P, P, P],
         "fvn_stage_times": [P, P],
         "fvn_render_batch_adaptive": [P, P, I, P, I, F, I, P, P, P, P],
+        "fvn_conv3x3_fwd_bf16": [P, I, P, I, I, I, I, P, P, I, I, P, P],
+        "fvn_conv3x3_dgrad_bf16": [P, P, I, I, I, I, P, I, I, P, P, P],
+        "fvn_train_device_status": [],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -442,6 +446,27 @@ def conv_bwd(xa, xb, w, gy, y_relu, gxa, gxb, gw, gb, stream=None):
     cout, _, k, _ = w.shape
     _check(lib.fvn_conv_bwd(_ptr(xa), ca, _ptr(xb), cb, n, h, wd, _ptr(w), cout, k, _ptr(gy), _ptr(y_relu),
                             _ptr(gxa), _ptr(gxb), _ptr(gw), _ptr(gb), _stream(stream)))
+
+
+def conv3x3_fwd_bf16(xa, xb, w, b, relu, y, stream=None):
+    """3x3 convolution forward on the tensor cores (BF16 operands, FP32 accumulation)."""
+    n, ca, h, wd = xa.shape
+    cb = 0 if xb is None else xb.shape[1]
+    _check(lib.fvn_conv3x3_fwd_bf16(_ptr(xa), ca, _ptr(xb), cb, n, h, wd, _ptr(w), _ptr(b), w.shape[0],
+                                    int(bool(relu)), _ptr(y), _stream(stream)))
+
+
+def conv3x3_dgrad_bf16(gy, y_relu, w, ca, cb, gxa, gxb, stream=None):
+    """Data gradient of a 3x3 convolution on the tensor cores: gy [N, cout, H, W]
+    masked by y_relu > 0 (None: no mask) into gxa [N, ca, H, W], gxb [N, cb, H, W]."""
+    n, cout, h, wd = gy.shape
+    _check(lib.fvn_conv3x3_dgrad_bf16(_ptr(gy), _ptr(y_relu), cout, n, h, wd, _ptr(w), int(ca), int(cb), _ptr(gxa),
+                                      _ptr(gxb), _stream(stream)))
+
+
+def train_device_status():
+    """Synchronise; FvnError(TIMEOUT) if a training tensor-core wait gave up."""
+    _check(lib.fvn_train_device_status())
 
 
 def avgpool2_fwd(x, y, stream=None):

@@ -131,6 +131,34 @@ class _Conv(torch.autograd.Function):
         return gxa, gxb, None, None, None, None, None
 
 
+class _ConvTC(torch.autograd.Function):
+    """A 3x3 layer on the tensor cores: forward and data gradient as tcgen05
+    implicit GEMMs with BF16 operands and FP32 accumulation, the weight
+    gradient by the FP32 kernel (written straight into the flat buffer)."""
+
+    @staticmethod
+    def forward(ctx, xa, xb, w, b, relu, gw, gb):
+        n, _, h, wd = xa.shape
+        y = torch.empty(n, w.shape[0], h, wd, device=xa.device)
+        fvn.conv3x3_fwd_bf16(xa, xb, w.detach(), b.detach(), relu, y)
+        ctx.save_for_backward(xa, xb, w, y if relu else None)
+        ctx.gwb = (gw, gb)
+        return y
+
+    @staticmethod
+    def backward(ctx, gy):
+        xa, xb, w, y = ctx.saved_tensors
+        gy = gy.contiguous()
+        ca, cb = xa.shape[1], 0 if xb is None else xb.shape[1]
+        gxa = torch.empty_like(xa) if ctx.needs_input_grad[0] else None
+        gxb = torch.empty_like(xb) if (xb is not None and ctx.needs_input_grad[1]) else None
+        if gxa is not None or gxb is not None:
+            fvn.conv3x3_dgrad_bf16(gy, y, w.detach(), ca, cb, gxa, gxb)
+        gw, gb = ctx.gwb
+        fvn.conv_bwd(xa, xb, w.detach(), gy, y, None, None, gw, gb)
+        return gxa, gxb, None, None, None, None, None
+
+
 class _Pool(torch.autograd.Function):
     @staticmethod
     def forward(ctx, x):
@@ -227,13 +255,17 @@ class _Loss(torch.autograd.Function):
         return (g if float(gl) == 1.0 else g * gl), None, None
 
 
-def forward(P: Params, sparse: torch.Tensor, direct_only: bool = False, prev: torch.Tensor = None):
+def forward(P: Params, sparse: torch.Tensor, direct_only: bool = False, prev: torch.Tensor = None,
+            tc: bool = True):
     """Network forward on [N, 5, H, W] (H, W multiples of 4); returns [N, 3, H, W].
     The recurrent network also takes prev, the previous output [N, 3, H, W]
-    (None: zeros), clamped to [0, 1]."""
+    (None: zeros), clamped to [0, 1].  tc: the 3x3 layers' forward and data
+    gradient on the tensor cores (BF16 operands, FP32 accumulation); False:
+    every layer on the FP32 kernels."""
+    conv = _ConvTC if tc else _Conv
 
     def cbr(name, xa, xb=None):
-        return _Conv.apply(xa, xb, P.w(name), P.b(name), True, P.gw(name), P.gb(name))
+        return conv.apply(xa, xb, P.w(name), P.b(name), True, P.gw(name), P.gb(name))
 
     if P.recurrent:
         n, _, h, w = sparse.shape

@@ -159,7 +159,7 @@ def test_recurrent_training_step_matches_oracle(fvn):
     y0, y1 = rng.uniform(size=(2, n, 3, h, w)).astype(np.float32)
     P = train.Params(flat, DEV, wl.NET_LAYERS_RECURRENT)
     T = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(DEV)   # noqa: E731
-    o1 = train.forward(P, T(sp), prev=T(o_prev))
+    o1 = train.forward(P, T(sp), prev=T(o_prev), tc=False)
     loss = train.LAMBDA_S * train._Loss.apply(o1, T(y1), 1.0) + \
         train.LAMBDA_T * train._Loss.apply(o1 - T(o_prev), T(y1 - y0), 0.0)
     P.g.zero_()

@@ -123,7 +123,7 @@ def test_loss_and_adam(fvn):
 
 def test_whole_network_forward_and_gradients_match_oracle(fvn):
     """train.forward + backward through the autograd shims (every step in the
-    library's FP32 kernels) against the FP64 oracle network."""
+    library's FP32 kernels: tc=False) against the FP64 oracle network."""
     from paper_2209_09965_gb300 import train, workloads as wl
     rng = np.random.default_rng(7)
     flat = wl.net_weights(5)
@@ -135,7 +135,7 @@ def test_whole_network_forward_and_gradients_match_oracle(fvn):
     sp[:, 4] = m
     tgt = rng.uniform(size=(n, 3, h, w)).astype(np.float32)
     P = train.Params(flat, DEV)
-    pred = train.forward(P, T(sp))
+    pred = train.forward(P, T(sp), tc=False)
     loss = train._Loss.apply(pred, T(tgt), 1.0)
     P.g.zero_()
     loss.backward()

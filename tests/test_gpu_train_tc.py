@@ -1,0 +1,113 @@
+"""GPU: the training step's 3x3 layers on the tensor cores (forward and data
+gradient as tcgen05 implicit GEMMs, BF16 operands, FP32 accumulation)
+against the FP64 oracle, layer by layer and through the whole network's
+forward and backward, through the C ABI.  The bars are those of 16-bit
+operands: BF16 keeps 8 significant bits, so a layer's output differs from the
+FP64 one by up to ~1 % of its scale."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import net as onet
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda")
+LAYER_TOL = 1.5e-2      # max-abs error / max |reference|, one layer
+NET_TOL = 5e-2          # the same for the whole network's parameter gradients
+
+
+@pytest.fixture(scope="module")
+def fvn():
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2209_09965_gb300 import fvn as f
+    return f
+
+
+def T(a):
+    return torch.from_numpy(np.ascontiguousarray(a, np.float32)).to(DEV)
+
+
+def N(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+# every 3x3 layer shape of the 16/32/64 network (input a + input b -> output),
+# on ragged frames that span several tiles
+@pytest.mark.parametrize("ca,cb,cout,h,w", [(5, 0, 16, 19, 150), (8, 0, 16, 9, 40), (16, 0, 16, 12, 131),
+                                           (16, 0, 32, 10, 64), (32, 0, 32, 7, 129), (32, 0, 64, 6, 33),
+                                           (64, 0, 64, 5, 20), (64, 32, 32, 9, 70), (32, 16, 16, 13, 260),
+                                           (16, 0, 16, 1, 1)])
+def test_tc_conv_forward_and_data_gradient(fvn, ca, cb, cout, h, w):
+    rng = np.random.default_rng(ca * 7 + cb * 3 + cout)
+    n = 2
+    xa = rng.normal(size=(n, ca, h, w))
+    xb = rng.normal(size=(n, cb, h, w)) if cb else None
+    wt = rng.normal(size=(cout, ca + cb, 3, 3)) * 0.2
+    b = rng.normal(size=cout) * 0.1
+    x = xa if xb is None else np.concatenate([xa, xb], 1)
+    z = onet.conv2d(x, wt, b)
+    y_ref = np.maximum(z, 0)
+    y = torch.full((n, cout, h, w), 9.0, device=DEV)
+    fvn.conv3x3_fwd_bf16(T(xa), None if xb is None else T(xb), T(wt), T(b), True, y)
+    fvn.train_device_status()
+    assert np.abs(N(y) - y_ref).max() < LAYER_TOL * np.abs(y_ref).max()
+    # data gradient through the ReLU of the FP64 forward (the saved output's mask)
+    gy = rng.normal(size=y_ref.shape)
+    gx_ref, _, _ = onet.conv2d_backward(x, wt, gy * (z > 0))
+    gxa = torch.full((n, ca, h, w), 7.0, device=DEV)
+    gxb = torch.full((n, cb, h, w), 7.0, device=DEV) if cb else None
+    fvn.conv3x3_dgrad_bf16(T(gy), T(y_ref), T(wt), ca, cb, gxa, gxb)
+    fvn.train_device_status()
+    gx = N(gxa) if gxb is None else np.concatenate([N(gxa), N(gxb)], 1)
+    assert np.abs(gx - gx_ref).max() < LAYER_TOL * np.abs(gx_ref).max()
+
+
+def test_tc_conv_unsupported_shape_is_rejected(fvn):
+    x = torch.zeros(1, 176, 4, 4, device=DEV)
+    wt = torch.zeros(80, 176, 3, 3, device=DEV)
+    y = torch.zeros(1, 80, 4, 4, device=DEV)
+    with pytest.raises(fvn.FvnError, match="no tensor-core training convolution"):
+        fvn.conv3x3_fwd_bf16(x, None, wt, torch.zeros(80, device=DEV), True, y)
+
+
+def test_tc_whole_network_gradients_match_oracle(fvn):
+    """train.forward (tc=True) + backward through the autograd shims against
+    the FP64 oracle network: prediction, loss and every parameter gradient."""
+    from paper_2209_09965_gb300 import train, workloads as wl
+    rng = np.random.default_rng(7)
+    flat = wl.net_weights(5)
+    flat = (flat + rng.normal(size=flat.size).astype(np.float32) * 0.01).astype(np.float32)
+    n, h, w = 2, 32, 136
+    sp = np.zeros((n, 5, h, w), np.float32)
+    m = rng.uniform(size=(n, h, w)) < 0.3
+    sp[:, 0:4] = rng.uniform(size=(n, 4, h, w)) * m[:, None]
+    sp[:, 4] = m
+    tgt = rng.uniform(size=(n, 3, h, w)).astype(np.float32)
+    P = train.Params(flat, DEV)
+    pred = train.forward(P, T(sp), tc=True)
+    loss = train._Loss.apply(pred, T(tgt), 1.0)
+    P.g.zero_()
+    loss.backward()
+    fvn.train_device_status()
+    params = onet.unpack(flat)
+    ref, cache = onet.forward(params, sp.astype(np.float64), return_cache=True)
+    lref, gref = onet.loss_l1_grad(ref, tgt)
+    assert np.abs(N(pred) - ref).max() < 2e-2
+    assert abs(float(loss.item()) - lref) < 1e-2 * abs(lref)
+    ref_g = onet.pack(onet.backward(params, cache, gref))
+    g = P.g.cpu().numpy().astype(np.float64)
+    assert np.abs(g - ref_g).max() < NET_TOL * np.abs(ref_g).max()
+    # and the FP32 path of the same step agrees with it to the same bar
+    P2 = train.Params(flat, DEV)
+    P2.g.zero_()
+    train._Loss.apply(train.forward(P2, T(sp), tc=False), T(tgt), 1.0).backward()
+    g32 = P2.g.cpu().numpy().astype(np.float64)
+    assert np.abs(g - g32).max() < NET_TOL * np.abs(g32).max()
+
+
+def test_tc_training_reduces_loss(fvn):
+    from paper_2209_09965_gb300 import train
+    _, log = train.train(steps=60, nvol=2, vol_n=64, log_every=20, batch=4)
+    assert log[-1][1] < log[0][1]
+    fvn.train_device_status()
