@@ -508,6 +508,12 @@ fvn_status fvn_conv3x3_fwd_bf16(const float* xa, int ca, const float* xb, int cb
 fvn_status fvn_conv3x3_dgrad_bf16(const float* gy, const float* y_relu, int cout, int n, int h, int w_,
                                   const float* w, int ca, int cb, float* gxa, float* gxb, void* stream);
 fvn_status fvn_train_device_status(void);
+/* dL/dw [cout][ca+cb][3][3] and dL/db [cout] (overwritten) of a 3x3 layer on
+ * the tensor cores: the sum over images and pixels of gy (masked by
+ * y_relu > 0 when set) times the shifted inputs xa / xb, as a GEMM over the
+ * pixels with BF16 operands and FP32 accumulation (cout up to 96). */
+fvn_status fvn_conv3x3_wgrad_bf16(const float* xa, int ca, const float* xb, int cb, int n, int h, int w_,
+                                  const float* gy, const float* y_relu, int cout, float* gw, float* gb, void* stream);
 
 /* 2x2 average pooling and its adjoint ([N][C][H][W] -> [N][C][H/2][W/2]). */
 fvn_status fvn_avgpool2_fwd(const float* x, int nc, int h, int w_, float* y, void* stream);

@@ -20,6 +20,8 @@
 // one pixel per thread, channel by channel (coalesced along x); the data
 // gradient's channels go to the two tensors of a concatenated input.
 //
+// The weight gradient is a GEMM over the pixels (see conv3x3_wgrad_kernel).
+//
 // Every mbarrier wait has an iteration limit; a wait that gives up sets the
 // error flag the caller passed and the CTA leaves its loop.
 #include <cuda_bf16.h>
@@ -272,6 +274,248 @@ __global__ void __launch_bounds__(kThreads, 2) conv3x3_train_kernel(const __grid
     }
 }
 
+// ---------------------------------------------------------------------------
+// Weight gradient on the tensor cores: dL/dW[co][ci][t] =
+// sum over images and pixels p of dz[co](p) x[ci](p + shift(t)), with dz the
+// output gradient times the ReLU mask, and dL/db[co] = sum of dz[co].  As a
+// GEMM: rows R = 9 ci + t (and one more row of ones, R = 9 cin, for the
+// bias; R is then the flat index of W[co] itself), columns co, K = pixels.
+// A CTA owns 128 rows (an M block: at most 16 input channels) and a range of
+// K tiles -- 128-pixel segments of image rows, y fastest, so that the CTA
+// walks down a column of segments -- and accumulates D[R][co] in TMEM
+// (M = 128, N = COUTP, K = 16 per MMA, BF16 operands, both K-major).
+// Per K tile the needed input rows and dz are stored coalesced into FP32
+// shared memory (a rolling window of three input rows: one new row per tile
+// down the column) from registers loaded during the previous tile, and the
+// BF16 operands are built from there: row R of A is the segment of x[ci]
+// shifted by tap t, B is dz with the ReLU mask applied.  The next tile's
+// loads are in flight while a tile is built.  At the end the CTA adds D to the
+// FP32 gradients with atomics (the M blocks and K ranges of the grid
+// partition the sum).
+struct WgArgs {
+    const float* xa;                    // layer input channels [0, ca): [N][ca][H][W]
+    const float* xb;                    // [ca, cin): [N][cin - ca][H][W] (NULL when cin == ca)
+    const float* gy;                    // [N][cout][H][W]
+    const float* y;                     // ReLU output of the layer (NULL: no ReLU)
+    int ca, cin, cout;
+    float* gw;                          // [cout][cin][3][3], accumulated into (zeroed by the caller)
+    float* gb;                          // [cout], accumulated into
+    int n, H, W;
+    int segs_x, ktiles, kper;           // row segments per image row, K tiles, K tiles per CTA
+    int* error;
+};
+
+constexpr int kWgRS = 132;              // FP32 row stride of the staged rows (130 used: x0 - 1 .. x0 + 128)
+constexpr int kWgCh = 16;               // input channels 128 consecutive rows R = 9 ci + t touch at most
+
+template <int COUTP>
+struct WgLayout {
+    static constexpr size_t a_bytes = 16ull * 128 * 16;                 // [16 chunks][128 rows][8 px] BF16
+    static constexpr size_t b_bytes = 16ull * COUTP * 16;               // [16 chunks][COUTP][8 px]
+    static constexpr size_t x_off = a_bytes + b_bytes;                  // [kWgCh][3 slots][kWgRS] FP32
+    static constexpr size_t g_off = x_off + 4ull * kWgCh * 3 * kWgRS;   // dz: [COUTP][kWgRS] FP32
+    static constexpr size_t bar_off = g_off + 4ull * COUTP * kWgRS;
+    static constexpr size_t bytes = bar_off + 16;
+    static constexpr uint32_t tmem_cols = COUTP <= 32 ? 32 : COUTP <= 64 ? 64 : COUTP <= 128 ? 128 : 256;
+    static constexpr int row_per = (kWgCh * 130 + kThreads - 1) / kThreads;   // row values per thread
+    static constexpr int dz_per = COUTP * 128 / kThreads;                    // dz values per thread
+};
+
+template <int COUTP>
+__global__ void __launch_bounds__(kThreads, COUTP <= 32 ? 3 : COUTP <= 64 ? 2 : 1)
+conv3x3_wgrad_kernel(const __grid_constant__ WgArgs a) {
+    using L = WgLayout<COUTP>;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::bar_off);
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::bar_off + 8);
+    unsigned char* sA = smem;
+    unsigned char* sB = smem + L::a_bytes;
+    float* xs = reinterpret_cast<float*>(smem + L::x_off);
+    float* gs = reinterpret_cast<float*>(smem + L::g_off);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mblock = blockIdx.y;
+    const int rows = 9 * a.cin + 1;                      // weight rows + the bias row
+    const int ci_lo = min(mblock * 128 / 9, a.cin);
+    const int nch = min(a.cin, (mblock * 128 + 127) / 9 + 1) - ci_lo;   // 0 .. kWgCh
+    const size_t plane = (size_t)a.H * a.W;
+    if (tid == 0) {
+        tc::mbar_init(bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(tslot, L::tmem_cols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = *tslot;
+    const int k0 = blockIdx.x * a.kper, k1 = min(a.ktiles, k0 + a.kper);
+
+    // Registers that carry one tile's global loads to the next iteration's
+    // shared-memory stores: one input row of this M block's channels
+    // (segment x0 - 1 .. x0 + 128) and the tile's dz (ReLU mask applied).
+    float rv[L::row_per], gv[L::dz_per];
+    auto coords = [&](int kt, int& img, int& x0, int& y) {
+        y = kt % a.H;
+        const int r = kt / a.H;
+        x0 = (r % a.segs_x) * 128;
+        img = r / a.segs_x;
+    };
+    auto load_row = [&](int img, int x0, int yy) {      // zero outside the image
+        const bool row_in = yy >= 0 && yy < a.H;
+        const size_t roff = (size_t)min(max(yy, 0), a.H - 1) * a.W;
+#pragma unroll
+        for (int k = 0; k < L::row_per; ++k) {
+            const int i = tid + k * kThreads;
+            rv[k] = 0.f;
+            if (i < nch * 130) {
+                const int cl = i / 130, px = i - cl * 130;
+                const int ci = ci_lo + cl, xx = x0 - 1 + px;
+                const float* src = ci < a.ca ? a.xa + ((size_t)img * a.ca + ci) * plane
+                                             : a.xb + ((size_t)img * (a.cin - a.ca) + (ci - a.ca)) * plane;
+                if (row_in && xx >= 0 && xx < a.W) rv[k] = __ldg(src + roff + xx);   // predicated: no wait here
+            }
+        }
+    };
+    auto store_row = [&](int yy) {                      // into slot (yy + 3) % 3
+        const int slot = (yy + 3) % 3;
+#pragma unroll
+        for (int k = 0; k < L::row_per; ++k) {
+            const int i = tid + k * kThreads;
+            if (i < nch * 130) {
+                const int cl = i / 130, px = i - cl * 130;
+                xs[(cl * 3 + slot) * kWgRS + px] = rv[k];
+            }
+        }
+    };
+    float mv[L::dz_per];
+    auto load_dz = [&](int img, int x0, int y) {        // zero past the edge and for padded channels
+        const size_t goff = ((size_t)img * a.cout * a.H + y) * a.W;
+#pragma unroll
+        for (int k = 0; k < L::dz_per; ++k) {
+            const int i = tid + k * kThreads, co = i >> 7, px = i & 127;
+            const size_t off = goff + (size_t)co * plane + (x0 + px);
+            gv[k] = 0.f;
+            mv[k] = 1.f;
+            if (co < a.cout && x0 + px < a.W) {         // predicated: no wait here
+                gv[k] = __ldg(a.gy + off);
+                if (a.y) mv[k] = __ldg(a.y + off);
+            }
+        }
+    };
+    auto store_dz = [&]() {                             // the ReLU mask applied
+#pragma unroll
+        for (int k = 0; k < L::dz_per; ++k) {
+            const int i = tid + k * kThreads;
+            gs[(i >> 7) * kWgRS + (i & 127)] = mv[k] > 0.f ? gv[k] : 0.f;
+        }
+    };
+
+    constexpr uint32_t idesc = idesc_bf16(128, COUTP);
+    uint32_t phase = 0;
+    bool failed = false;
+    int img = 0, x0 = 0, y = 0;
+    bool rolled = false;                                 // rv holds row y + 1 of this tile
+    if (k0 < k1) {
+        coords(k0, img, x0, y);
+        load_dz(img, x0, y);
+    }
+    for (int kt = k0; kt < k1; ++kt) {
+        // ---- this tile's rows and dz into shared memory (the previous tile's build is done with them)
+        store_dz();
+        if (rolled) {
+            store_row(y + 1);                            // the window moves down one row
+        } else {
+            for (int d = -1; d <= 1; ++d) {
+                load_row(img, x0, y + d);
+                store_row(y + d);
+            }
+        }
+        // the previous tile's MMAs must be done with the BF16 operands before they are rebuilt
+        if (kt > k0) {
+            if (!tc::mbar_wait(bar, phase, kLimit)) failed = true;
+            phase ^= 1u;
+        }
+        if (__syncthreads_or(failed)) break;
+        // ---- the next tile's loads, in flight while this one is built
+        int nimg = img, nx0 = x0, ny = y;
+        rolled = false;
+        if (kt + 1 < k1) {
+            coords(kt + 1, nimg, nx0, ny);
+            rolled = nimg == img && nx0 == x0 && ny == y + 1;
+            if (rolled) load_row(nimg, nx0, ny + 1);
+            load_dz(nimg, nx0, ny);
+        }
+        // ---- BF16 operands: A row R = x[ci] shifted by tap t; B = dz
+        for (int i = tid; i < 128 * 16; i += kThreads) {   // (row r, chunk c), r fastest
+            const int c = i >> 7, r = i & 127;
+            const int R = mblock * 128 + r;
+            float v[8];
+            if (R < rows - 1) {
+                const int ci = R / 9, t = R - ci * 9, ty = t / 3, tx = t - ty * 3;
+                const float* src = xs + ((ci - ci_lo) * 3 + (y + ty + 2) % 3) * kWgRS + c * 8 + tx;
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = src[j];
+            } else {
+                const float one = R == rows - 1 ? 1.f : 0.f;   // dz is zero past the edge
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = one;
+            }
+            *reinterpret_cast<uint4*>(sA + ((size_t)c * 128 + r) * 16) = pack8bf(v);
+        }
+        for (int i = tid; i < COUTP * 16; i += kThreads) {   // (output channel co, chunk c), co fastest
+            const int c = i / COUTP, co = i - c * COUTP;
+            const float4 p = *reinterpret_cast<const float4*>(gs + co * kWgRS + c * 8);
+            const float4 q = *reinterpret_cast<const float4*>(gs + co * kWgRS + c * 8 + 4);
+            const float v[8] = {p.x, p.y, p.z, p.w, q.x, q.y, q.z, q.w};
+            *reinterpret_cast<uint4*>(sB + ((size_t)c * COUTP + co) * 16) = pack8bf(v);
+        }
+        tc::fence_async_smem();
+        tc::fence_before_sync();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint64_t ad = tc::smem_desc(tc::smem_addr(sA), 128 * 16, 128);
+            const uint64_t bd = tc::smem_desc(tc::smem_addr(sB), COUTP * 16, 128);
+#pragma unroll
+            for (int s = 0; s < 8; ++s)   // K = 16 pixels = chunks 2s, 2s + 1
+                tc::mma_f16(tmem, ad + (uint64_t)(2 * s * 128), bd + (uint64_t)(2 * s * COUTP), idesc,
+                            (kt > k0 || s > 0) ? 1u : 0u);
+            tc::mma_commit(bar);
+        }
+        img = nimg, x0 = nx0, y = ny;
+    }
+    if (!failed && k0 < k1 && !tc::mbar_wait(bar, phase, kLimit)) failed = true;   // the last tile's MMAs
+    tc::fence_after_sync();
+    // ---- D[R][co] -> the gradients: warps 0-3, one TMEM lane (row) per thread
+    if (!__syncthreads_or(failed) && k0 < k1 && warp < 4) {
+        const int r = warp * 32 + lane, R = mblock * 128 + r;
+        const uint32_t lane_base = (uint32_t)(warp * 32) << 16;
+#pragma unroll 1
+        for (int cb = 0; cb < COUTP; cb += 16) {
+            float v[16];
+            tc::tmem_ld16(tmem + lane_base + (uint32_t)cb, v);
+            if (R < rows) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j) {
+                    const int co = cb + j;
+                    if (co >= a.cout) break;
+                    if (R == rows - 1) atomicAdd(a.gb + co, v[j]);
+                    else atomicAdd(a.gw + (size_t)co * (rows - 1) + R, v[j]);   // W[co] flat = 9 ci + t
+                }
+            }
+        }
+    }
+    if (failed) atomicExch(a.error, 1);
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) {
+        tc::fence_after_sync();
+        tc::tmem_dealloc(tmem, L::tmem_cols);
+    }
+}
+
 }  // namespace ttc
 }  // namespace fvn
 
@@ -298,6 +542,40 @@ fvn_status error_flag(int** out) {
     return FVN_OK;
 }
 
+// Shared memory opted in and the largest shared-memory carveout preferred,
+// once per device: the occupancy query (and the launch) then count every CTA
+// that the SM's shared memory holds, not only those of the default L1 split.
+template <typename K>
+cudaError_t configure_train(int dev, K kern, int bytes, std::atomic<unsigned long long>& done) {
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0ull;
+    if (bit && (done.load(std::memory_order_acquire) & bit)) return cudaSuccess;
+    const cudaError_t e =
+        cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+    if (e != cudaSuccess) return e;
+    return opt_in_smem(dev, kern, bytes, done);
+}
+
+// CTAs of `kern` (kThreads threads, `bytes` of dynamic shared memory) one SM
+// holds at once, from its registers and shared memory (the largest carveout,
+// which the launch takes; the occupancy query counts the default split).
+template <typename K>
+cudaError_t resident_ctas(int dev, K kern, int bytes, int& per_sm) {
+    cudaFuncAttributes fa{};
+    cudaError_t e = cudaFuncGetAttributes(&fa, kern);
+    int smem_sm = 0, reserved = 0, regs_sm = 0, threads_sm = 0;
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&threads_sm, cudaDevAttrMaxThreadsPerMultiProcessor, dev);
+    if (e != cudaSuccess) return e;
+    const int warps = ttc::kThreads / 32;
+    const int warp_regs = (fa.numRegs * 32 + 255) / 256 * 256;       // allocated per warp in 256-register units
+    const int by_smem = smem_sm / std::max(1, bytes + (int)fa.sharedSizeBytes + reserved);
+    const int by_regs = regs_sm / std::max(1, warp_regs * warps);
+    per_sm = std::min({by_smem, by_regs, threads_sm / ttc::kThreads});
+    return cudaSuccess;
+}
+
 template <int CINP, int COUTP, int TR>
 fvn_status launch_train(ttc::Args a, cudaStream_t st) {
     using L = ttc::Layout<CINP, COUTP, TR>;
@@ -305,11 +583,11 @@ fvn_status launch_train(ttc::Args a, cudaStream_t st) {
     static std::atomic<unsigned long long> configured{0};
     int dev = 0;
     FVN_CUDA(nullptr, cudaGetDevice(&dev));
-    FVN_CUDA(nullptr, opt_in_smem(dev, kern, (int)L::bytes, configured));
+    FVN_CUDA(nullptr, configure_train(dev, kern, (int)L::bytes, configured));
     int sms = 0;
     FVN_CUDA(nullptr, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     int per_sm = 0;   // CTAs resident at once (registers, shared memory), within the TMEM
-    FVN_CUDA(nullptr, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, ttc::kThreads, L::bytes));
+    FVN_CUDA(nullptr, resident_ctas(dev, kern, (int)L::bytes, per_sm));
     per_sm = std::min(per_sm, (int)(512 / L::tmem_cols));
     if (per_sm < 1) return set_error(nullptr, FVN_ERR_CUDA, "training conv kernel does not fit on an SM");
     a.tiles_x = (a.W + ttc::TW - 1) / ttc::TW;
@@ -346,10 +624,69 @@ fvn_status dispatch(const ttc::Args& a, cudaStream_t st) {
                      a.cin, a.cout);
 }
 
+template <int COUTP>
+fvn_status launch_wgrad(ttc::WgArgs a, cudaStream_t st) {
+    using L = ttc::WgLayout<COUTP>;
+    auto kern = ttc::conv3x3_wgrad_kernel<COUTP>;
+    static std::atomic<unsigned long long> configured{0};
+    int dev = 0;
+    FVN_CUDA(nullptr, cudaGetDevice(&dev));
+    FVN_CUDA(nullptr, configure_train(dev, kern, (int)L::bytes, configured));
+    int sms = 0, per_sm = 0;
+    FVN_CUDA(nullptr, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    FVN_CUDA(nullptr, resident_ctas(dev, kern, (int)L::bytes, per_sm));
+    per_sm = std::min(per_sm, (int)(512 / L::tmem_cols));
+    if (per_sm < 1) return set_error(nullptr, FVN_ERR_CUDA, "weight-gradient kernel does not fit on an SM");
+    a.segs_x = (a.W + 127) / 128;
+    const long long kt = (long long)a.n * a.H * a.segs_x;
+    if (kt >= (1ll << 31)) return set_error(nullptr, FVN_ERR_ARG, "too many pixels");
+    a.ktiles = (int)kt;
+    const int mb = (9 * a.cin + 1 + 127) / 128;
+    // split K so that the grid fills the resident CTAs once
+    const int splits = (int)std::max(1ll, std::min(kt, (long long)sms * per_sm / mb));
+    a.kper = (int)((kt + splits - 1) / splits);
+    const int gx = (int)((kt + a.kper - 1) / a.kper);
+    fvn_status s = error_flag(&a.error);
+    if (s != FVN_OK) return s;
+    FVN_CUDA(nullptr, cudaMemsetAsync(a.gw, 0, sizeof(float) * 9 * (size_t)a.cin * a.cout, st));
+    FVN_CUDA(nullptr, cudaMemsetAsync(a.gb, 0, sizeof(float) * (size_t)a.cout, st));
+    kern<<<dim3(gx, mb), ttc::kThreads, L::bytes, st>>>(a);
+    FVN_LAUNCH_CHECK(nullptr);
+    return FVN_OK;
+}
+
 }  // namespace
 }  // namespace fvn
 
 using namespace fvn;
+
+extern "C" fvn_status fvn_conv3x3_wgrad_bf16(const float* xa, int ca, const float* xb, int cb, int n, int h, int w_,
+                                             const float* gy, const float* y_relu, int cout, float* gw, float* gb,
+                                             void* stream) {
+    FVN_CHECK_ARG(nullptr, xa && gy && gw && gb && (cb == 0 || xb), "null tensor");
+    FVN_CHECK_ARG(nullptr, ca >= 1 && cb >= 0 && n >= 1 && h >= 1 && w_ >= 1 && cout >= 1, "bad sizes");
+    ttc::WgArgs a{};
+    a.xa = xa;
+    a.xb = cb ? xb : nullptr;
+    a.gy = gy;
+    a.y = y_relu;
+    a.ca = ca;
+    a.cin = ca + cb;
+    a.cout = cout;
+    a.gw = gw;
+    a.gb = gb;
+    a.n = n;
+    a.H = h;
+    a.W = w_;
+    const int cp = (cout + 15) & ~15;
+    cudaStream_t st = as_stream(stream);
+    if (cp == 16) return launch_wgrad<16>(a, st);
+    if (cp == 32) return launch_wgrad<32>(a, st);
+    if (cp == 48) return launch_wgrad<48>(a, st);
+    if (cp == 64) return launch_wgrad<64>(a, st);
+    if (cp == 96) return launch_wgrad<96>(a, st);
+    return set_error(nullptr, FVN_ERR_UNSUPPORTED, "no tensor-core weight gradient for %d output channels", cout);
+}
 
 extern "C" fvn_status fvn_conv3x3_fwd_bf16(const float* xa, int ca, const float* xb, int cb, int n, int h, int w_,
                                            const float* w, const float* b, int cout, int relu, float* y,

@@ -34,7 +34,7 @@ EXPORTS = (
     "fvn_weight_count_recurrent", "fvn_reconstruct_recurrent", "fvn_render_recurrent", "fvn_selftest_wait_timeout",
     "fvn_wnet_weight_count", "fvn_load_wnet_weights", "fvn_reconstruct_wnet", "fvn_filter3_fwd", "fvn_filter3_bwd",
     "fvn_wnet_join_fwd", "fvn_wnet_join_bwd", "fvn_stage_times", "fvn_render_batch_adaptive",
-    "fvn_conv3x3_fwd_bf16", "fvn_conv3x3_dgrad_bf16", "fvn_train_device_status",
+    "fvn_conv3x3_fwd_bf16", "fvn_conv3x3_dgrad_bf16", "fvn_train_device_status", "fvn_conv3x3_wgrad_bf16",
 )
 WNET_MAX_LEVELS = 4
 MAX_VIEWS = 16
@@ -148,6 +148,7 @@ def _load():
         "fvn_conv3x3_fwd_bf16": [P, I, P, I, I, I, I, P, P, I, I, P, P],
         "fvn_conv3x3_dgrad_bf16": [P, P, I, I, I, I, P, I, I, P, P, P],
         "fvn_train_device_status": [],
+        "fvn_conv3x3_wgrad_bf16": [P, I, P, I, I, I, I, P, P, I, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -462,6 +463,14 @@ def conv3x3_dgrad_bf16(gy, y_relu, w, ca, cb, gxa, gxb, stream=None):
     n, cout, h, wd = gy.shape
     _check(lib.fvn_conv3x3_dgrad_bf16(_ptr(gy), _ptr(y_relu), cout, n, h, wd, _ptr(w), int(ca), int(cb), _ptr(gxa),
                                       _ptr(gxb), _stream(stream)))
+
+
+def conv3x3_wgrad_bf16(xa, xb, gy, y_relu, gw, gb, stream=None):
+    """Weight and bias gradients of a 3x3 layer on the tensor cores (overwritten)."""
+    n, ca, h, wd = xa.shape
+    cb = 0 if xb is None else xb.shape[1]
+    _check(lib.fvn_conv3x3_wgrad_bf16(_ptr(xa), ca, _ptr(xb), cb, n, h, wd, _ptr(gy), _ptr(y_relu), gy.shape[1],
+                                      _ptr(gw), _ptr(gb), _stream(stream)))
 
 
 def train_device_status():

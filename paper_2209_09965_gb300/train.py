@@ -134,7 +134,8 @@ class _Conv(torch.autograd.Function):
 class _ConvTC(torch.autograd.Function):
     """A 3x3 layer on the tensor cores: forward and data gradient as tcgen05
     implicit GEMMs with BF16 operands and FP32 accumulation, the weight
-    gradient by the FP32 kernel (written straight into the flat buffer)."""
+    gradient as a tcgen05 GEMM over the pixels (written straight into the
+    flat buffer)."""
 
     @staticmethod
     def forward(ctx, xa, xb, w, b, relu, gw, gb):
@@ -155,7 +156,7 @@ class _ConvTC(torch.autograd.Function):
         if gxa is not None or gxb is not None:
             fvn.conv3x3_dgrad_bf16(gy, y, w.detach(), ca, cb, gxa, gxb)
         gw, gb = ctx.gwb
-        fvn.conv_bwd(xa, xb, w.detach(), gy, y, None, None, gw, gb)
+        fvn.conv3x3_wgrad_bf16(xa, xb, gy, y, gw, gb)
         return gxa, gxb, None, None, None, None, None
 
 

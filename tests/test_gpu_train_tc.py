@@ -111,3 +111,32 @@ def test_tc_training_reduces_loss(fvn):
     _, log = train.train(steps=60, nvol=2, vol_n=64, log_every=20, batch=4)
     assert log[-1][1] < log[0][1]
     fvn.train_device_status()
+
+
+# weight and bias gradients (a GEMM over the pixels): every layer shape, ragged
+# widths across several 128-pixel segments, and the ReLU mask from the forward
+@pytest.mark.parametrize("ca,cb,cout,h,w", [(5, 0, 16, 19, 150), (16, 0, 32, 10, 64), (32, 0, 64, 6, 33),
+                                           (64, 0, 64, 5, 20), (64, 32, 32, 9, 70), (32, 16, 16, 13, 260),
+                                           (48, 0, 48, 7, 129), (32, 0, 96, 4, 300), (16, 0, 16, 1, 1)])
+def test_tc_conv_weight_gradient(fvn, ca, cb, cout, h, w):
+    rng = np.random.default_rng(ca * 5 + cb + cout * 11)
+    n = 2
+    xa = rng.normal(size=(n, ca, h, w))
+    xb = rng.normal(size=(n, cb, h, w)) if cb else None
+    x = xa if xb is None else np.concatenate([xa, xb], 1)
+    z = rng.normal(size=(n, cout, h, w))
+    gy = rng.normal(size=z.shape)
+    y = np.maximum(z, 0)
+    _, gw_ref, gb_ref = onet.conv2d_backward(x, np.zeros((cout, ca + cb, 3, 3)), gy * (z > 0))
+    gw = torch.full((cout, ca + cb, 3, 3), 5.0, device=DEV)
+    gb = torch.full((cout,), 5.0, device=DEV)
+    fvn.conv3x3_wgrad_bf16(T(xa), None if xb is None else T(xb), T(gy), T(y), gw, gb)
+    fvn.train_device_status()
+    assert np.abs(N(gw) - gw_ref).max() < LAYER_TOL * np.abs(gw_ref).max()
+    assert np.abs(N(gb) - gb_ref).max() < LAYER_TOL * max(np.abs(gb_ref).max(), 1e-6)
+    # without a ReLU mask
+    _, gw2, gb2 = onet.conv2d_backward(x, np.zeros((cout, ca + cb, 3, 3)), gy)
+    fvn.conv3x3_wgrad_bf16(T(xa), None if xb is None else T(xb), T(gy), None, gw, gb)
+    fvn.train_device_status()
+    assert np.abs(N(gw) - gw2).max() < LAYER_TOL * np.abs(gw2).max()
+    assert np.abs(N(gb) - gb2).max() < LAYER_TOL * max(np.abs(gb2).max(), 1e-6)
