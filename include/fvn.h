@@ -531,6 +531,18 @@ fvn_status fvn_kp_blend_fwd(const float* head, const float* sparse, int n, int h
 fvn_status fvn_kp_blend_bwd(const float* head, const float* sparse, const float* gout, int n, int h,
                             int w_, float* ghead, void* stream);
 
+/* The 1x1 head and the kernel-prediction blend fused (the paper's "Kernel
+ * Prediction" subsection).  Forward: head = w x + b ([N][16][H][W] ->
+ * [N][29][H][W], written for the backward pass; w [29][16], b [29]) and
+ * out [N][3][H][W] as fvn_kp_blend_fwd computes it from head.  Backward:
+ * from dL/dout, dL/dx (overwritten) and the head's dL/dw, dL/db
+ * (overwritten); dL/dhead is not stored.  FP32 throughout; the weight
+ * gradients are summed with atomics (order not fixed). */
+fvn_status fvn_head_kp_fwd(const float* x, int n, int h, int w_, const float* w, const float* b,
+                           const float* sparse, float* head, float* out, void* stream);
+fvn_status fvn_head_kp_bwd(const float* x, const float* head, const float* sparse, const float* w,
+                           const float* gout, int n, int h, int w_, float* gx, float* gw, float* gb, void* stream);
+
 /* L1 + lam * (L1 of x / y forward differences), each a mean over its own
  * elements, over pred / target [N][C][H][W].  loss: device float scalar
  * (overwritten); gpred: dL/dpred (overwritten). */

@@ -530,65 +530,91 @@ __global__ void __launch_bounds__(256) conv_wgrad_kernel(const float* __restrict
     }
 }
 
+// The resampling kernels run on a 2-D grid: blockIdx.y walks the planes
+// (image x channel), blockIdx.x x 256 + threadIdx.x the pixels of one plane,
+// so the index arithmetic stays 32-bit and one division per element.
+// VEC: the fine tensor is 8-byte aligned (w_ is even, so every pixel pair
+// 2 xx, 2 xx + 1 is too) and is accessed as float2
+template <bool VEC>
 __global__ void avgpool2_fwd_kernel(const float* __restrict__ x, long long nc, int h, int w_, float* __restrict__ y) {
-    const int ho = h / 2, wo = w_ / 2;
-    const long long total = nc * ho * wo;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const long long c = i / ((long long)ho * wo);
-        const int r = (int)(i - c * ho * wo);
-        const int yy = r / wo, xx = r - yy * wo;
+    const int ho = h / 2, wo = w_ / 2, r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ho * wo) return;
+    const int yy = r / wo, xx = r - yy * wo;
+#pragma unroll 4
+    for (long long c = blockIdx.y; c < nc; c += gridDim.y) {
         const float* p = x + c * h * w_ + (long long)(2 * yy) * w_ + 2 * xx;
-        y[i] = 0.25f * (p[0] + p[1] + p[w_] + p[w_ + 1]);
+        float2 a, b;
+        if (VEC) {
+            a = __ldg(reinterpret_cast<const float2*>(p));
+            b = __ldg(reinterpret_cast<const float2*>(p + w_));
+        } else {
+            a = make_float2(__ldg(p), __ldg(p + 1));
+            b = make_float2(__ldg(p + w_), __ldg(p + w_ + 1));
+        }
+        y[c * ho * wo + r] = 0.25f * (a.x + a.y + b.x + b.y);
     }
 }
 
+template <bool VEC>
 __global__ void avgpool2_bwd_kernel(const float* __restrict__ gy, long long nc, int h, int w_, float* __restrict__ gx) {
-    const int ho = h / 2, wo = w_ / 2;
-    const long long total = nc * h * w_;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const long long c = i / ((long long)h * w_);
-        const int r = (int)(i - c * h * w_);
-        const int yy = r / w_, xx = r - yy * w_;
-        gx[i] = 0.25f * gy[c * ho * wo + (long long)(yy / 2) * wo + xx / 2];
+    const int ho = h / 2, wo = w_ / 2, r = blockIdx.x * blockDim.x + threadIdx.x;   // one coarse pixel
+    if (r >= ho * wo) return;
+    const int yy = r / wo, xx = r - yy * wo;
+#pragma unroll 4
+    for (long long c = blockIdx.y; c < nc; c += gridDim.y) {
+        const float v = 0.25f * __ldg(gy + c * ho * wo + r);
+        float* q = gx + c * h * w_ + (long long)(2 * yy) * w_ + 2 * xx;
+        if (VEC) {
+            *reinterpret_cast<float2*>(q) = make_float2(v, v);
+            *reinterpret_cast<float2*>(q + w_) = make_float2(v, v);
+        } else {
+            q[0] = q[1] = q[w_] = q[w_ + 1] = v;
+        }
     }
 }
 
 __global__ void upsample2_fwd_kernel(const float* __restrict__ x, long long nc, int h, int w_, float* __restrict__ y) {
-    const int H2 = 2 * h, W2 = 2 * w_;
-    const long long total = nc * H2 * W2;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const long long c = i / ((long long)H2 * W2);
-        const int r = (int)(i - c * H2 * W2);
-        const int oy = r / W2, ox = r - oy * W2;
-        int y0, y1, x0, x1;
-        float ty, tx;
-        up_src(oy, h, y0, y1, ty);
-        up_src(ox, w_, x0, x1, tx);
+    const int H2 = 2 * h, W2 = 2 * w_, r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= H2 * W2) return;
+    const int oy = r / W2, ox = r - oy * W2;
+    int y0, y1, x0, x1;
+    float ty, tx;
+    up_src(oy, h, y0, y1, ty);
+    up_src(ox, w_, x0, x1, tx);
+#pragma unroll 4
+    for (long long c = blockIdx.y; c < nc; c += gridDim.y) {
         const float* p = x + c * h * w_;
-        const float top = (1.f - tx) * p[y0 * w_ + x0] + tx * p[y0 * w_ + x1];
-        const float bot = (1.f - tx) * p[y1 * w_ + x0] + tx * p[y1 * w_ + x1];
-        y[i] = (1.f - ty) * top + ty * bot;
+        const float top = (1.f - tx) * __ldg(p + y0 * w_ + x0) + tx * __ldg(p + y0 * w_ + x1);
+        const float bot = (1.f - tx) * __ldg(p + y1 * w_ + x0) + tx * __ldg(p + y1 * w_ + x1);
+        y[c * H2 * W2 + r] = (1.f - ty) * top + ty * bot;
     }
 }
 
 __global__ void upsample2_bwd_kernel(const float* __restrict__ gy, long long nc, int h, int w_, float* __restrict__ gx) {
-    const int H2 = 2 * h, W2 = 2 * w_;
-    const long long total = nc * h * w_;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const long long c = i / ((long long)h * w_);
-        const int r = (int)(i - c * h * w_);
-        const int iy = r / w_, ix = r - iy * w_;
+    const int H2 = 2 * h, W2 = 2 * w_, r = blockIdx.x * blockDim.x + threadIdx.x;   // one coarse pixel
+    if (r >= h * w_) return;
+    const int iy = r / w_, ix = r - iy * w_;
+    const int oy0 = max(2 * iy - 1, 0), oy1 = min(2 * iy + 2, H2 - 1);
+    const int ox0 = max(2 * ix - 1, 0), ox1 = min(2 * ix + 2, W2 - 1);
+    float wy[4], wx[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        wy[k] = oy0 + k <= oy1 ? up_weight(oy0 + k, iy, h) : 0.f;
+        wx[k] = ox0 + k <= ox1 ? up_weight(ox0 + k, ix, w_) : 0.f;
+    }
+#pragma unroll 4
+    for (long long c = blockIdx.y; c < nc; c += gridDim.y) {
         const float* g = gy + c * H2 * W2;
         float s = 0.f;
-        for (int oy = max(2 * iy - 1, 0); oy <= min(2 * iy + 2, H2 - 1); ++oy) {
-            const float wy = up_weight(oy, iy, h);
-            if (wy == 0.f) continue;
-            for (int ox = max(2 * ix - 1, 0); ox <= min(2 * ix + 2, W2 - 1); ++ox) {
-                const float wx = up_weight(ox, ix, w_);
-                if (wx != 0.f) s += wy * wx * g[(long long)oy * W2 + ox];
-            }
+#pragma unroll
+        for (int a = 0; a < 4; ++a) {
+            if (wy[a] == 0.f) continue;
+            const float* row = g + (long long)(oy0 + a) * W2;
+#pragma unroll
+            for (int b = 0; b < 4; ++b)
+                if (wx[b] != 0.f) s += wy[a] * wx[b] * __ldg(row + ox0 + b);
         }
-        gx[i] = s;
+        gx[c * h * w_ + r] = s;
     }
 }
 
@@ -672,38 +698,50 @@ __global__ void kp_blend_kernel(const float* __restrict__ head, const float* __r
     }
 }
 
-// L1 + lam (L1 of forward differences), gradient and (atomically summed) loss
+// L1 + lam (L1 of forward differences), gradient and loss.  Blocks walk the
+// image rows (grid-stride), threads the pixels of a row; the loss is reduced
+// in the block and added with one atomic per block.
 __global__ void loss_kernel(const float* __restrict__ p, const float* __restrict__ t, long long nc, int h, int w_,
                             float lam, float* __restrict__ loss, float* __restrict__ g) {
-    const long long hw = (long long)h * w_;
-    const long long total = nc * hw;
-    const double n1 = (double)total, nx = (double)nc * h * (w_ - 1), ny = (double)nc * (h - 1) * w_;
+    __shared__ float red[32];
+    const long long rows = nc * h;
+    const double n1 = (double)rows * w_, nx = (double)rows * (w_ - 1), ny = (double)nc * (h - 1) * w_;
     const float i1 = (float)(1.0 / n1), ix = nx > 0 ? (float)(lam / nx) : 0.f, iy = ny > 0 ? (float)(lam / ny) : 0.f;
+    auto sgn = [](float v) { return (float)((v > 0.f) - (v < 0.f)); };
     float part = 0.f;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total; i += (long long)gridDim.x * blockDim.x) {
-        const int r = (int)(i % hw);
-        const int y = r / w_, x = r - y * w_;
-        const float d = p[i] - t[i];
-        auto sgn = [](float v) { return (float)((v > 0.f) - (v < 0.f)); };
-        float gi = sgn(d) * i1;
-        part += fabsf(d) * i1;
-        if (x + 1 < w_) {
-            const float dx = (p[i + 1] - t[i + 1]) - d;
-            gi -= sgn(dx) * ix;
-            part += fabsf(dx) * ix;
+    for (long long row = blockIdx.x; row < rows; row += gridDim.x) {
+        const int y = (int)(row % h);
+        for (int x = threadIdx.x; x < w_; x += blockDim.x) {
+            const long long i = row * w_ + x;
+            const float d = __ldg(p + i) - __ldg(t + i);
+            float gi = sgn(d) * i1;
+            part += fabsf(d) * i1;
+            if (x + 1 < w_) {
+                const float dx = (__ldg(p + i + 1) - __ldg(t + i + 1)) - d;
+                gi -= sgn(dx) * ix;
+                part += fabsf(dx) * ix;
+            }
+            if (x > 0) gi += sgn(d - (__ldg(p + i - 1) - __ldg(t + i - 1))) * ix;
+            if (y + 1 < h) {
+                const float dy = (__ldg(p + i + w_) - __ldg(t + i + w_)) - d;
+                gi -= sgn(dy) * iy;
+                part += fabsf(dy) * iy;
+            }
+            if (y > 0) gi += sgn(d - (__ldg(p + i - w_) - __ldg(t + i - w_))) * iy;
+            g[i] = gi;
         }
-        if (x > 0) gi += sgn(d - (p[i - 1] - t[i - 1])) * ix;
-        if (y + 1 < h) {
-            const float dy = (p[i + w_] - t[i + w_]) - d;
-            gi -= sgn(dy) * iy;
-            part += fabsf(dy) * iy;
-        }
-        if (y > 0) gi += sgn(d - (p[i - w_] - t[i - w_])) * iy;
-        g[i] = gi;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(loss, part);
+    const int warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    if ((threadIdx.x & 31) == 0) red[warp] = part;
+    __syncthreads();
+    if (warp == 0) {
+        part = (int)threadIdx.x < nw ? red[threadIdx.x] : 0.f;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+        if (threadIdx.x == 0) atomicAdd(loss, part);
+    }
 }
 
 __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
@@ -717,6 +755,15 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
         v[i] = vi;
         p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
     }
+}
+
+// grid of the resampling kernels: pixels of a plane x planes, about 8192
+// CTAs in all -- each thread loops over the planes gridDim.y apart, so that
+// the CTAs are not so small that their scheduling is the limit
+static dim3 plane_grid(long long plane, long long nc) {
+    const long long gx = (plane + 255) / 256;
+    const long long gy = std::max(1LL, std::min(nc, 8192 / std::max(1LL, gx)));
+    return dim3((unsigned)gx, (unsigned)std::min(gy, 65535LL));
 }
 
 static int grid_for(fvn_ctx* ctx, long long total) {
@@ -818,7 +865,9 @@ extern "C" fvn_status fvn_conv_bwd(const float* xa, int ca, const float* xb, int
 extern "C" fvn_status fvn_avgpool2_fwd(const float* x, int nc, int h, int w_, float* y, void* stream) {
     fvn_ctx* ctx = nullptr;
     FVN_CHECK_ARG(ctx, x && y && nc >= 1 && h >= 2 && w_ >= 2 && h % 2 == 0 && w_ % 2 == 0, "bad pool arguments");
-    avgpool2_fwd_kernel<<<grid_for(train_ctx(), (long long)nc * h * w_ / 4), 256, 0, as_stream(stream)>>>(x, nc, h, w_, y);
+    const dim3 grid = plane_grid((long long)(h / 2) * (w_ / 2), nc);
+    if (((uintptr_t)x & 7) == 0) avgpool2_fwd_kernel<true><<<grid, 256, 0, as_stream(stream)>>>(x, nc, h, w_, y);
+    else avgpool2_fwd_kernel<false><<<grid, 256, 0, as_stream(stream)>>>(x, nc, h, w_, y);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
@@ -826,7 +875,9 @@ extern "C" fvn_status fvn_avgpool2_fwd(const float* x, int nc, int h, int w_, fl
 extern "C" fvn_status fvn_avgpool2_bwd(const float* gy, int nc, int h, int w_, float* gx, void* stream) {
     fvn_ctx* ctx = nullptr;
     FVN_CHECK_ARG(ctx, gx && gy && nc >= 1 && h >= 2 && w_ >= 2 && h % 2 == 0 && w_ % 2 == 0, "bad pool arguments");
-    avgpool2_bwd_kernel<<<grid_for(train_ctx(), (long long)nc * h * w_), 256, 0, as_stream(stream)>>>(gy, nc, h, w_, gx);
+    const dim3 grid = plane_grid((long long)(h / 2) * (w_ / 2), nc);
+    if (((uintptr_t)gx & 7) == 0) avgpool2_bwd_kernel<true><<<grid, 256, 0, as_stream(stream)>>>(gy, nc, h, w_, gx);
+    else avgpool2_bwd_kernel<false><<<grid, 256, 0, as_stream(stream)>>>(gy, nc, h, w_, gx);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
@@ -834,7 +885,7 @@ extern "C" fvn_status fvn_avgpool2_bwd(const float* gy, int nc, int h, int w_, f
 extern "C" fvn_status fvn_upsample2_fwd(const float* x, int nc, int h, int w_, float* y, void* stream) {
     fvn_ctx* ctx = nullptr;
     FVN_CHECK_ARG(ctx, x && y && nc >= 1 && h >= 1 && w_ >= 1, "bad upsample arguments");
-    upsample2_fwd_kernel<<<grid_for(train_ctx(), (long long)nc * h * w_ * 4), 256, 0, as_stream(stream)>>>(x, nc, h, w_, y);
+    upsample2_fwd_kernel<<<plane_grid(4ll * h * w_, nc), 256, 0, as_stream(stream)>>>(x, nc, h, w_, y);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
@@ -842,7 +893,7 @@ extern "C" fvn_status fvn_upsample2_fwd(const float* x, int nc, int h, int w_, f
 extern "C" fvn_status fvn_upsample2_bwd(const float* gy, int nc, int h, int w_, float* gx, void* stream) {
     fvn_ctx* ctx = nullptr;
     FVN_CHECK_ARG(ctx, gx && gy && nc >= 1 && h >= 1 && w_ >= 1, "bad upsample arguments");
-    upsample2_bwd_kernel<<<grid_for(train_ctx(), (long long)nc * h * w_), 256, 0, as_stream(stream)>>>(gy, nc, h, w_, gx);
+    upsample2_bwd_kernel<<<plane_grid((long long)h * w_, nc), 256, 0, as_stream(stream)>>>(gy, nc, h, w_, gx);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
@@ -872,8 +923,10 @@ extern "C" fvn_status fvn_loss_l1grad(const float* pred, const float* target, in
     fvn_ctx* ctx = nullptr;
     FVN_CHECK_ARG(ctx, pred && target && loss && gpred && nc >= 1 && h >= 1 && w_ >= 1, "bad loss arguments");
     FVN_CUDA(ctx, cudaMemsetAsync(loss, 0, sizeof(float), as_stream(stream)));
-    loss_kernel<<<grid_for(train_ctx(), (long long)nc * h * w_), 256, 0, as_stream(stream)>>>(pred, target, nc, h, w_,
-                                                                                               lam, loss, gpred);
+    const fvn_ctx* tc = train_ctx();
+    const long long rows = (long long)nc * h;
+    const int grid = (int)std::min<long long>(rows, 4LL * (tc->num_sms > 0 ? tc->num_sms : 148));
+    loss_kernel<<<grid, 256, 0, as_stream(stream)>>>(pred, target, nc, h, w_, lam, loss, gpred);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }

@@ -35,6 +35,7 @@ EXPORTS = (
     "fvn_wnet_weight_count", "fvn_load_wnet_weights", "fvn_reconstruct_wnet", "fvn_filter3_fwd", "fvn_filter3_bwd",
     "fvn_wnet_join_fwd", "fvn_wnet_join_bwd", "fvn_stage_times", "fvn_render_batch_adaptive",
     "fvn_conv3x3_fwd_bf16", "fvn_conv3x3_dgrad_bf16", "fvn_train_device_status", "fvn_conv3x3_wgrad_bf16",
+    "fvn_head_kp_fwd", "fvn_head_kp_bwd",
 )
 WNET_MAX_LEVELS = 4
 MAX_VIEWS = 16
@@ -149,6 +150,8 @@ def _load():
         "fvn_conv3x3_dgrad_bf16": [P, P, I, I, I, I, P, I, I, P, P, P],
         "fvn_train_device_status": [],
         "fvn_conv3x3_wgrad_bf16": [P, I, P, I, I, I, I, P, P, I, P, P, P],
+        "fvn_head_kp_fwd": [P, I, I, I, P, P, P, P, P, P],
+        "fvn_head_kp_bwd": [P, P, P, P, P, I, I, I, P, P, P, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -471,6 +474,20 @@ def conv3x3_wgrad_bf16(xa, xb, gy, y_relu, gw, gb, stream=None):
     cb = 0 if xb is None else xb.shape[1]
     _check(lib.fvn_conv3x3_wgrad_bf16(_ptr(xa), ca, _ptr(xb), cb, n, h, wd, _ptr(gy), _ptr(y_relu), gy.shape[1],
                                       _ptr(gw), _ptr(gb), _stream(stream)))
+
+
+def head_kp_fwd(x, w, b, sparse, head, out, stream=None):
+    """The 1x1 head (x [N][16][H][W] -> head [N][29][H][W]) and the kernel-prediction blend -> out [N][3][H][W]."""
+    n, _, h, wd = x.shape
+    _check(lib.fvn_head_kp_fwd(_ptr(x), n, h, wd, _ptr(w), _ptr(b), _ptr(sparse), _ptr(head), _ptr(out),
+                               _stream(stream)))
+
+
+def head_kp_bwd(x, head, sparse, w, gout, gx, gw, gb, stream=None):
+    """dL/dx, and the head's dL/dw, dL/db (overwritten), from dL/dout of the blend."""
+    n, _, h, wd = x.shape
+    _check(lib.fvn_head_kp_bwd(_ptr(x), _ptr(head), _ptr(sparse), _ptr(w), _ptr(gout), n, h, wd, _ptr(gx),
+                               _ptr(gw), _ptr(gb), _stream(stream)))
 
 
 def train_device_status():

@@ -209,6 +209,30 @@ class _KP(torch.autograd.Function):
         return gh, None
 
 
+class _HeadKP(torch.autograd.Function):
+    """The 1x1 head and the kernel-prediction blend fused: one kernel forward
+    (the head's output kept for the backward pass), one backward (dL/dx and
+    the head's weight gradients, written straight into the flat buffer)."""
+
+    @staticmethod
+    def forward(ctx, x, sparse, w, b, gw, gb):
+        n, _, h, wd = x.shape
+        head = torch.empty(n, 29, h, wd, device=x.device)
+        out = torch.empty(n, 3, h, wd, device=x.device)
+        fvn.head_kp_fwd(x, w.detach(), b.detach(), sparse, head, out)
+        ctx.save_for_backward(x, head, sparse, w)
+        ctx.gwb = (gw, gb)
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        x, head, sparse, w = ctx.saved_tensors
+        gx = torch.empty_like(x)
+        gw, gb = ctx.gwb
+        fvn.head_kp_bwd(x, head, sparse, w.detach(), gout.contiguous(), gx, gw, gb)
+        return gx, None, None, None, None, None
+
+
 class _Filter3(torch.autograd.Function):
     @staticmethod
     def forward(ctx, img, logits):
@@ -260,9 +284,9 @@ def forward(P: Params, sparse: torch.Tensor, direct_only: bool = False, prev: to
             tc: bool = True):
     """Network forward on [N, 5, H, W] (H, W multiples of 4); returns [N, 3, H, W].
     The recurrent network also takes prev, the previous output [N, 3, H, W]
-    (None: zeros), clamped to [0, 1].  tc: the 3x3 layers' forward and data
-    gradient on the tensor cores (BF16 operands, FP32 accumulation); False:
-    every layer on the FP32 kernels."""
+    (None: zeros), clamped to [0, 1].  tc: the 3x3 layers on the tensor cores
+    (BF16 operands, FP32 accumulation) and the head fused with the blend;
+    False: every layer on the FP32 kernels."""
     conv = _ConvTC if tc else _Conv
 
     def cbr(name, xa, xb=None):
@@ -278,6 +302,8 @@ def forward(P: Params, sparse: torch.Tensor, direct_only: bool = False, prev: to
     bt = cbr("botb", cbr("bota", _Pool.apply(e1)))
     d1 = cbr("dec1b", cbr("dec1a", _Up.apply(bt), e1))
     d0 = cbr("dec0b", cbr("dec0a", _Up.apply(d1), e0))
+    if tc and not direct_only:
+        return _HeadKP.apply(d0, sparse, P.w("head"), P.b("head"), P.gw("head"), P.gb("head"))
     head = _Conv.apply(d0, None, P.w("head"), P.b("head"), False, P.gw("head"), P.gb("head"))
     if direct_only:
         return head[:, 0:3].contiguous()

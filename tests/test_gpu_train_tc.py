@@ -140,3 +140,34 @@ def test_tc_conv_weight_gradient(fvn, ca, cb, cout, h, w):
     fvn.train_device_status()
     assert np.abs(N(gw) - gw2).max() < LAYER_TOL * np.abs(gw2).max()
     assert np.abs(N(gb) - gb2).max() < LAYER_TOL * max(np.abs(gb2).max(), 1e-6)
+
+
+# the 1x1 head fused with the kernel-prediction blend, forward and backward
+# (FP32 throughout): sparse masks thin enough that some 5x5 neighbourhoods
+# are empty (the direct-prediction branch), ragged frames across several
+# 256-pixel tiles
+@pytest.mark.parametrize("n,h,w,density", [(2, 37, 300, 0.05), (1, 8, 8, 0.5), (3, 1, 1, 1.0), (1, 64, 96, 0.0)])
+def test_fused_head_and_blend(fvn, n, h, w, density):
+    rng = np.random.default_rng(h * 31 + w)
+    x = rng.normal(size=(n, 16, h, w))
+    wt = rng.normal(size=(29, 16, 1, 1)) * 0.3
+    b = rng.normal(size=29) * 0.1
+    sparse = rng.uniform(size=(n, 5, h, w))
+    sparse[:, 4] = (rng.uniform(size=(n, h, w)) < density).astype(np.float64)
+    sparse[:, 0:4] *= sparse[:, 4:5]
+    head_ref = onet.conv2d(x, wt, b)
+    out_ref, cache = onet.kp_blend(head_ref, sparse)
+    gout = rng.normal(size=out_ref.shape)
+    gh = onet.kp_blend_backward(gout, cache)
+    gx_ref, gw_ref, gb_ref = onet.conv2d_backward(x, wt, gh)
+    head = torch.full((n, 29, h, w), 3.0, device=DEV)
+    out = torch.full((n, 3, h, w), 3.0, device=DEV)
+    fvn.head_kp_fwd(T(x), T(wt), T(b), T(sparse), head, out)
+    gx = torch.full((n, 16, h, w), 3.0, device=DEV)
+    gw = torch.full((29, 16, 1, 1), 3.0, device=DEV)
+    gb = torch.full((29,), 3.0, device=DEV)
+    fvn.head_kp_bwd(T(x), head, T(sparse), T(wt), T(gout), gx, gw, gb)
+    torch.cuda.synchronize()
+    tol = 1e-4
+    for got, ref in ((head, head_ref), (out, out_ref), (gx, gx_ref), (gw, gw_ref), (gb, gb_ref)):
+        assert np.abs(N(got) - ref).max() <= tol * max(np.abs(ref).max(), 1.0)
