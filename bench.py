@@ -900,24 +900,32 @@ def run_training(fvn, wl, weights, vol, tf, mp, dev, steps=20, warmup=3, batch=8
                 pred = train.wnet_forward(P, xs, cfg) if cfg else train.forward(P, xs, tc=tc)
                 train._Loss.apply(pred, ys, 1.0).backward()
                 P.adam(1e-4)
-            for _ in range(warmup):
-                step()
-            torch.cuda.synchronize()
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(steps):
-                step()
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ms = e0.elapsed_time(e1) / steps
+
+            def timed(fn):
+                for _ in range(warmup):
+                    fn()
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                for _ in range(steps):
+                    fn()
+                e1.record(stream)
+                torch.cuda.synchronize()
+                return e0.elapsed_time(e1) / steps
+            eager_ms = timed(step)
+            ms = eager_ms
+            if tc:   # the step as one CUDA graph (the batch copied into its inputs every step)
+                gstep = train.GraphedStep(P, xs, ys, lambda P_, x: train.forward(P_, x, tc=True), lr=1e-4)
+                ms = timed(lambda: gstep(xs, ys))
             ach = 3.0 * fpp * px / (ms / 1000.0) / 1e12
             out[key] = {"ms_per_step": ms, "steps_per_s": 1000.0 / ms, "pixels_per_s": px * 1000.0 / ms,
-                        "flops_per_step": 3.0 * fpp * px, "achieved_tflops": ach}
+                        "flops_per_step": 3.0 * fpp * px, "achieved_tflops": ach, "cuda_graph": bool(tc),
+                        "eager_ms_per_step": eager_ms}
             if tc:
                 out[key].update({"bound": "tensor", "peak_tflops": tc_peak, "frac": ach / tc_peak,
-                                 "arithmetic": "3x3 forward and data gradient on tcgen05 (BF16 operands, FP32 "
-                                               "accumulation); weight gradient, head, pooling, kernel prediction, "
-                                               "loss and Adam on the FP32 kernels",
+                                 "arithmetic": "3x3 forward, data and weight gradients on tcgen05 (BF16 operands, "
+                                               "FP32 accumulation); head fused with the kernel-prediction blend, "
+                                               "pooling, up-sampling, loss and Adam on FP32 kernels",
                                  "peak_kind": "measured bf16 burst"})
             else:
                 out[key].update({"bound": "alu", "peak_tflops": FP32_PEAK_TFLOPS, "frac": ach / FP32_PEAK_TFLOPS,

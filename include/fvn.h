@@ -552,6 +552,10 @@ fvn_status fvn_loss_l1grad(const float* pred, const float* target, int nc, int h
 /* One bias-corrected Adam step on n parameters (step >= 1). */
 fvn_status fvn_adam_step(float* p, const float* g, float* m, float* v, size_t n, int step, float lr,
                          float beta1, float beta2, float eps, void* stream);
+/* The same with the step count (int, >= 1) read from device memory when the
+ * kernel runs, so that a step captured in a CUDA graph can be replayed. */
+fvn_status fvn_adam_step_dev(float* p, const float* g, float* m, float* v, size_t n, const int* step, float lr,
+                             float beta1, float beta2, float eps, void* stream);
 
 /* ------------------------------------------------------------------------
  * Two-stage network (paper: "Reconstruction Network" -- a first U-Net D

@@ -757,6 +757,23 @@ __global__ void adam_kernel(float* __restrict__ p, const float* __restrict__ g, 
     }
 }
 
+// Adam with the step count read from device memory (a step replayed from a
+// CUDA graph): the bias corrections 1 - beta^step in double, as on the host.
+__global__ void adam_dev_kernel(float* __restrict__ p, const float* __restrict__ g, float* __restrict__ m,
+                                float* __restrict__ v, size_t n, const int* __restrict__ step, float lr, float b1,
+                                float b2, float eps) {
+    const int t = max(__ldg(step), 1);
+    const float c1 = (float)(1.0 - pow((double)b1, t)), c2 = (float)(1.0 - pow((double)b2, t));
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const float gi = g[i];
+        const float mi = b1 * m[i] + (1.f - b1) * gi;
+        const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+        m[i] = mi;
+        v[i] = vi;
+        p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+    }
+}
+
 // grid of the resampling kernels: pixels of a plane x planes, about 8192
 // CTAs in all -- each thread loops over the planes gridDim.y apart, so that
 // the CTAs are not so small that their scheduling is the limit
@@ -939,6 +956,16 @@ extern "C" fvn_status fvn_adam_step(float* p, const float* g, float* m, float* v
     const float c2 = (float)(1.0 - pow((double)beta2, step));
     adam_kernel<<<grid_for(train_ctx(), (long long)n), 256, 0, as_stream(stream)>>>(p, g, m, v, n, lr, beta1, beta2,
                                                                                     eps, c1, c2);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+extern "C" fvn_status fvn_adam_step_dev(float* p, const float* g, float* m, float* v, size_t n, const int* step,
+                                        float lr, float beta1, float beta2, float eps, void* stream) {
+    fvn_ctx* ctx = nullptr;
+    FVN_CHECK_ARG(ctx, p && g && m && v && step && n >= 1, "bad adam arguments");
+    adam_dev_kernel<<<grid_for(train_ctx(), (long long)n), 256, 0, as_stream(stream)>>>(p, g, m, v, n, step, lr,
+                                                                                        beta1, beta2, eps);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }

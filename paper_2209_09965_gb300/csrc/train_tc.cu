@@ -96,12 +96,6 @@ __device__ __forceinline__ uint4 pack8bf(const float* v) {
     return r;
 }
 
-// Element (tap, input channel ci, output channel co) of this GEMM's weights.
-__device__ __forceinline__ float weight_elem(const Args& a, int tap, int ci, int co) {
-    if (a.dgrad) return __ldg(a.w + ((size_t)ci * a.cout + co) * 9 + (8 - tap));   // layer [ci][co][8 - tap]
-    return __ldg(a.w + ((size_t)co * a.cin + ci) * 9 + tap);
-}
-
 template <int CINP, int COUTP, int TR>
 __global__ void __launch_bounds__(kThreads, 2) conv3x3_train_kernel(const __grid_constant__ Args a) {
     using L = Layout<CINP, COUTP, TR>;
@@ -112,28 +106,26 @@ __global__ void __launch_bounds__(kThreads, 2) conv3x3_train_kernel(const __grid
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + L::bar_off);
     uint32_t* tslot = reinterpret_cast<uint32_t*>(smem + L::bar_off + 8);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    {   // this GEMM's weights as BF16 chunks [tap][CH][COUTP][8], zero beyond cin / cout: the
-        // layer's FP32 array is read in order (coalesced) and each element scattered to its slot
-        uint4* z = reinterpret_cast<uint4*>(smem + L::w_off);
-        for (int i = tid; i < (int)(L::w_bytes / 16); i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
+    {   // this GEMM's weights as BF16 chunks [tap][CH][COUTP][8], zero beyond cin / cout: one
+        // 16-byte chunk per item, its 8 input channels gathered by independent loads
         for (int i = tid; i < COUTP; i += kThreads) sBias[i] = (a.bias && i < a.cout) ? __ldg(a.bias + i) : 0.f;
-        __syncthreads();
-        __nv_bfloat16* wb = reinterpret_cast<__nv_bfloat16*>(smem + L::w_off);
-        const int total = a.cin * a.cout * 9;
-        for (int i = tid; i < total; i += kThreads) {
-            const int t = i % 9, r = i / 9;
-            // forward: the layer is [cout][cin][t]; data gradient: [cin][cout][8 - tap]
-            int ci, co, tap;
-            if (a.dgrad) {
-                co = r % a.cout;
-                ci = r / a.cout;
-                tap = 8 - t;
-            } else {
-                ci = r % a.cin;
-                co = r / a.cin;
-                tap = t;
+        uint4* wz = reinterpret_cast<uint4*>(smem + L::w_off);
+        constexpr int items = 9 * CH * COUTP;
+#pragma unroll 4
+        for (int i = tid; i < items; i += kThreads) {
+            const int co = i % COUTP, t = i / COUTP, ch = t % CH, tap = t / CH;
+            float v[8];
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const int ci = ch * 8 + j;
+                const bool ok = ci < a.cin && co < a.cout;
+                // forward: the layer is [cout][cin][tap]; data gradient: [cin][cout][8 - tap]
+                const size_t off = a.dgrad ? ((size_t)min(ci, a.cin - 1) * a.cout + min(co, a.cout - 1)) * 9 + (8 - tap)
+                                           : ((size_t)min(co, a.cout - 1) * a.cin + min(ci, a.cin - 1)) * 9 + tap;
+                const float w = __ldg(a.w + off);
+                v[j] = ok ? w : 0.f;
             }
-            wb[((size_t)(tap * CH + ci / 8) * COUTP + co) * 8 + (ci & 7)] = __float2bfloat16_rn(__ldg(a.w + i));
+            wz[i] = pack8bf(v);
         }
     }
     if (tid == 0) {
@@ -163,29 +155,42 @@ __global__ void __launch_bounds__(kThreads, 2) conv3x3_train_kernel(const __grid
         const float* s1 = a.src1 ? a.src1 + (size_t)img * (a.cin - a.c0) * plane : nullptr;
         const float* mk = a.mask ? a.mask + (size_t)img * a.c0 * plane : nullptr;
         unsigned char* sH = smem + L::halo_off + (size_t)buf * L::halo_r;
-#pragma unroll 2
-        for (int i = tid; i < CH * HY * HXW; i += kThreads) {
-            const int hx = i % HXW, t = i / HXW, hy = t % HY, ch = t / HY;
+        // chunks never straddle the two sources nor run past cin: one base
+        // pointer per chunk, one add per channel
+        const bool aligned = a.c0 % 8 == 0 && a.cin % 8 == 0;
+        for (int i = tid; i < HY * HXW; i += kThreads) {   // one halo pixel, all its chunks
+            const int hy = i / HXW, hx = i - hy * HXW;
             const int gy = y0 + hy - 1, gx = x0 + hx - 1;
             // every load issued without a branch (addresses clamped into the
             // tensors, the values outside the frame / channels zeroed after)
             const bool in = gy >= 0 && gy < a.H && gx >= 0 && gx < a.W;
             const size_t p = (size_t)min(max(gy, 0), a.H - 1) * a.W + min(max(gx, 0), a.W - 1);
-            float v[8], m[8];
+            unsigned char* dst = sH + (size_t)i * 16;
+#pragma unroll 4
+            for (int ch = 0; ch < CH; ++ch) {
+                float v[8], m[8];
+                if (aligned) {
+                    const int c = min(ch * 8, a.cin - 8);
+                    const float* src = (c < a.c0 ? s0 + (size_t)c * plane : s1 + (size_t)(c - a.c0) * plane) + p;
+                    const float* ms = mk ? mk + (size_t)min(c, a.c0 - 8) * plane + p : nullptr;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                const int c = min(ch * 8 + j, a.cin - 1);
-                const float* src = c < a.c0 ? s0 + (size_t)c * plane : s1 + (size_t)(c - a.c0) * plane;
-                v[j] = __ldg(src + p);
-                m[j] = 1.f;
+                    for (int j = 0; j < 8; ++j) {
+                        v[j] = __ldg(src + (size_t)j * plane);
+                        m[j] = ms ? __ldg(ms + (size_t)j * plane) : 1.f;
+                    }
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 8; ++j) {
+                        const int c = min(ch * 8 + j, a.cin - 1);
+                        const float* src = c < a.c0 ? s0 + (size_t)c * plane : s1 + (size_t)(c - a.c0) * plane;
+                        v[j] = __ldg(src + p);
+                        m[j] = mk ? __ldg(mk + (size_t)min(ch * 8 + j, a.c0 - 1) * plane + p) : 1.f;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < 8; ++j) v[j] = (in && ch * 8 + j < a.cin && m[j] > 0.f) ? v[j] : 0.f;
+                *reinterpret_cast<uint4*>(dst + (size_t)ch * HY * HXW * 16) = pack8bf(v);
             }
-            if (mk) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) m[j] = __ldg(mk + (size_t)min(ch * 8 + j, a.c0 - 1) * plane + p);
-            }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) v[j] = (in && ch * 8 + j < a.cin && m[j] > 0.f) ? v[j] : 0.f;
-            *reinterpret_cast<uint4*>(sH + ((size_t)(ch * HY + hy) * HXW + hx) * 16) = pack8bf(v);
         }
     };
 

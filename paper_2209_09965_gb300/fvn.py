@@ -35,7 +35,7 @@ EXPORTS = (
     "fvn_wnet_weight_count", "fvn_load_wnet_weights", "fvn_reconstruct_wnet", "fvn_filter3_fwd", "fvn_filter3_bwd",
     "fvn_wnet_join_fwd", "fvn_wnet_join_bwd", "fvn_stage_times", "fvn_render_batch_adaptive",
     "fvn_conv3x3_fwd_bf16", "fvn_conv3x3_dgrad_bf16", "fvn_train_device_status", "fvn_conv3x3_wgrad_bf16",
-    "fvn_head_kp_fwd", "fvn_head_kp_bwd",
+    "fvn_head_kp_fwd", "fvn_head_kp_bwd", "fvn_adam_step_dev",
 )
 WNET_MAX_LEVELS = 4
 MAX_VIEWS = 16
@@ -152,6 +152,7 @@ def _load():
         "fvn_conv3x3_wgrad_bf16": [P, I, P, I, I, I, I, P, P, I, P, P, P],
         "fvn_head_kp_fwd": [P, I, I, I, P, P, P, P, P, P],
         "fvn_head_kp_bwd": [P, P, P, P, P, I, I, I, P, P, P, P],
+        "fvn_adam_step_dev": [P, P, P, P, ctypes.c_size_t, P, F, F, F, F, P],
     }
     for name, args in sig.items():
         fn = getattr(lib, name)
@@ -561,3 +562,9 @@ def wnet_join_bwd(j, y, z, gx, gj, gy, gz, stream=None):
 def adam_step(p, g, m, v, step, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     _check(lib.fvn_adam_step(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), int(step), float(lr), float(beta1),
                              float(beta2), float(eps), _stream(stream)))
+
+
+def adam_step_dev(p, g, m, v, step_t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    """Adam with the step count in a device int32 tensor (read when the kernel runs)."""
+    _check(lib.fvn_adam_step_dev(_ptr(p), _ptr(g), _ptr(m), _ptr(v), p.numel(), _ptr(step_t, torch.int32), float(lr),
+                                 float(beta1), float(beta2), float(eps), _stream(stream)))

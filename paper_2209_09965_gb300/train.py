@@ -108,6 +108,55 @@ class Params:
         return self.p.detach().cpu().numpy().astype(np.float32)
 
 
+class GraphedStep:
+    """One optimiser step -- zero the gradients, forward, loss, backward,
+    Adam -- captured once as a CUDA graph and replayed: its ~46 launches cost
+    the host one graph launch, and no Python runs between the kernels.
+
+    fwd(P, xs) is the network's forward (e.g. forward with tc=True).  Each
+    call copies the batch into the graph's static inputs (when given), bumps
+    the device step counter Adam reads, replays, and returns the loss as a
+    device scalar (no host sync).  Building the graph runs the step once
+    eagerly on a side stream (lazy initialisation of the kernels) with the
+    parameters, moments and step restored afterwards."""
+
+    def __init__(self, P: Params, xs: torch.Tensor, ys: torch.Tensor, fwd, lr=1e-3, lam=1.0):
+        self.P, self.fwd, self.lr, self.lam = P, fwd, lr, lam
+        self.xs, self.ys = xs.detach().clone(), ys.detach().clone()
+        self.step_t = torch.full((1,), P.step, dtype=torch.int32, device=xs.device)
+        saved = [t.detach().clone() for t in (P.p, P.m, P.v, self.step_t)]
+        side = torch.cuda.Stream(device=xs.device)
+        side.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(side):
+            self._body()
+        torch.cuda.current_stream().wait_stream(side)
+        with torch.no_grad():
+            for t, v in zip((P.p, P.m, P.v, self.step_t), saved):
+                t.copy_(v)
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(self.graph, capture_error_mode="thread_local"):
+            self.loss = self._body()
+
+    def _body(self):
+        P = self.P
+        P.g.zero_()
+        pred = self.fwd(P, self.xs)
+        loss = _Loss.apply(pred, self.ys, self.lam)
+        loss.backward()
+        self.step_t.add_(1)
+        fvn.adam_step_dev(P.p.data, P.g, P.m, P.v, self.step_t, lr=self.lr)
+        return loss.detach()
+
+    def __call__(self, xs: torch.Tensor = None, ys: torch.Tensor = None):
+        if xs is not None:
+            self.xs.copy_(xs)
+        if ys is not None:
+            self.ys.copy_(ys)
+        self.graph.replay()
+        self.P.step += 1
+        return self.loss
+
+
 class _Conv(torch.autograd.Function):
     @staticmethod
     def forward(ctx, xa, xb, w, b, relu, gw, gb):
@@ -277,7 +326,7 @@ class _Loss(torch.autograd.Function):
     @staticmethod
     def backward(ctx, gl):
         (g,) = ctx.saved_tensors
-        return (g if float(gl) == 1.0 else g * gl), None, None
+        return g * gl, None, None   # on the device: no host sync inside the backward pass
 
 
 def forward(P: Params, sparse: torch.Tensor, direct_only: bool = False, prev: torch.Tensor = None,

@@ -171,3 +171,34 @@ def test_fused_head_and_blend(fvn, n, h, w, density):
     tol = 1e-4
     for got, ref in ((head, head_ref), (out, out_ref), (gx, gx_ref), (gw, gw_ref), (gb, gb_ref)):
         assert np.abs(N(got) - ref).max() <= tol * max(np.abs(ref).max(), 1.0)
+
+
+def test_graphed_step_matches_eager_steps(fvn):
+    """A training step captured as a CUDA graph and replayed gives the eager
+    steps' parameters (up to the order of the weight gradients' atomics) and
+    its loss falls over the replays; Adam's step count advances on the
+    device."""
+    from paper_2209_09965_gb300 import train, workloads as wl
+    rng = np.random.default_rng(3)
+    flat = wl.net_weights(5)
+    xs = torch.from_numpy(rng.uniform(size=(2, 5, 32, 48)).astype(np.float32)).to(DEV)
+    xs[:, 4] = (xs[:, 4] < 0.3).float()
+    ys = torch.from_numpy(rng.uniform(size=(2, 3, 32, 48)).astype(np.float32)).to(DEV)
+    fwd = lambda P, x: train.forward(P, x, tc=True)  # noqa: E731
+    Pe = train.Params(flat, DEV)
+    losses_e = []
+    for _ in range(4):
+        Pe.g.zero_()
+        loss = train._Loss.apply(fwd(Pe, xs), ys, 1.0)
+        loss.backward()
+        Pe.adam(1e-3)
+        losses_e.append(float(loss.detach()))
+    Pg = train.Params(flat, DEV)
+    step = train.GraphedStep(Pg, xs, ys, fwd, lr=1e-3)
+    assert torch.equal(Pg.p.detach(), train.Params(flat, DEV).p.detach())   # building left the weights alone
+    losses_g = [float(step(xs, ys)) for _ in range(4)]
+    fvn.train_device_status()
+    assert Pg.step == 4 and int(step.step_t) == 4
+    np.testing.assert_allclose(losses_g, losses_e, rtol=2e-3)
+    assert np.abs(N(Pg.p) - N(Pe.p)).max() < 2e-3
+    assert losses_g[-1] < losses_g[0]
