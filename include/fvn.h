@@ -162,6 +162,10 @@ fvn_status fvn_destroy(fvn_ctx* ctx);
  *      the bottleneck output itself instead of reading a pass's up-sampled
  *      copy (0, default); the in-kernel up-sampling interpolates in half
  *      precision, so the two differ by FP16 rounding.
+ *  FVN_OPT_WNET_TENSOR_CORES: 1 = fvn_reconstruct_wnet runs its convolutions
+ *      on the tensor cores (FP16 operands and activations, FP32
+ *      accumulation; needs every width a multiple of 8 and at most 128,
+ *      else FVN_ERR_UNSUPPORTED); 0 (default) = FP32 kernels throughout.
  * A shadowed march (shading 2) first writes, besides the padded copy, a cell
  * volume -- per padded voxel the 2 x 2 block of voxels (x..x+1, y..y+1) in
  * the voxel type -- so that a shadow sample reads two cells instead of
@@ -179,7 +183,8 @@ enum {
     FVN_OPT_CONV_ROWS_HALF = 11,
     FVN_OPT_CONV_ROWS_QUARTER = 12,
     FVN_OPT_CONV_ROWS_DEC1 = 13,
-    FVN_OPT_CONV_FUSE_UP_DEC1 = 14
+    FVN_OPT_CONV_FUSE_UP_DEC1 = 14,
+    FVN_OPT_WNET_TENSOR_CORES = 15
 };
 fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value);
 

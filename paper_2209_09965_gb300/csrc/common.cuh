@@ -105,6 +105,7 @@ struct BatchWorkspace {
 // Two-stage network: configuration, FP32 weights on the device (the flat
 // layout of fvn_wnet_weight_count) and an activation workspace for one frame
 // size.
+constexpr int kWnetMaxLayers = 64;
 struct WnetState {
     fvn_wnet_config cfg{};
     float* d_w = nullptr;
@@ -113,6 +114,16 @@ struct WnetState {
     void* ws = nullptr;
     size_t ws_bytes = 0;
     int ws_w = 0, ws_h = 0;           // padded frame the workspace was carved for
+    // tensor-core path (FVN_OPT_WNET_TENSOR_CORES): the layers' weights packed
+    // for the K-streamed convolution (FP16) and their zero-padded biases
+    int tc = 0;                       // the option
+    bool tc_ok = false;               // the widths allow the tensor-core path
+    void* d_wpk = nullptr;            // packed FP16 weights of every layer
+    float* d_bpk = nullptr;           // padded biases of every layer
+    size_t wpk_off[kWnetMaxLayers] = {}, bpk_off[kWnetMaxLayers] = {};   // per layer, in halves / floats
+    void* tws = nullptr;              // tensor-core workspace
+    size_t tws_bytes = 0;
+    int tws_w = 0, tws_h = 0;
 };
 
 // Activation tensors with an FP8 scale (per tensor, from calibration).
@@ -209,6 +220,27 @@ template <typename K>
 inline cudaError_t opt_in_smem(const fvn_ctx* ctx, K kern, int bytes, std::atomic<unsigned long long>& done) {
     return opt_in_smem(ctx->device, kern, bytes, done);
 }
+
+// K-streamed tensor-core convolution of FP16 chunk-planar tensors
+// ([chunks][H][W][8 halves]; conv_tc.cu): the input is source 0's ch0
+// chunks followed by source 1's ch1; wpk holds the weights packed as
+// [ceil((ch0 + ch1) / 2)][k * k][2][ks_coutp(cout)][8] FP16 and bias
+// ks_coutp(cout) floats (zero padded).  Writes ceil(cout / 8) chunks of out
+// and / or cout FP32 planes of out32.
+struct KsConv {
+    const void* in0;
+    int ch0;
+    const void* in1;
+    int ch1;
+    int H, W;
+    const void* wpk;
+    const float* bias;
+    int cout, k, relu;
+    void* out;
+    float* out32;
+};
+int ks_coutp(int cout);
+fvn_status ks_conv(fvn_ctx* ctx, const KsConv& c, cudaStream_t st);
 
 fvn_status set_error(fvn_ctx* ctx, fvn_status st, const char* fmt, ...);
 

@@ -575,6 +575,7 @@ __global__ void amax_f16_kernel(const __half* __restrict__ x, long long n, float
 }  // namespace fvn
 
 #include "conv_ws.cuh"
+#include "conv_ks.cuh"
 
 namespace fvn {
 
@@ -1081,6 +1082,77 @@ fvn_status calibrate_amax(fvn_ctx* ctx, const ReconPlan& B, int w, int h, float*
         FVN_LAUNCH_CHECK(ctx);
     }
     return FVN_OK;
+}
+
+// ---------------------------------------------------------------------------
+// K-streamed layers (conv_ks.cuh)
+// ---------------------------------------------------------------------------
+
+// Stages of the ring that fit in shared memory (at most 4).
+template <int COUTP, int TR, bool K1>
+constexpr int ks_stages() {
+    using L1 = ks::Layout<COUTP, TR, 1, K1>;
+    const long long per = (long long)L1::stage + 16;
+    const long long ns = (227 * 1024 - (long long)L1::bytes + per) / per;
+    return ns >= 4 ? 4 : (ns < 1 ? 1 : (int)ns);
+}
+
+template <int COUTP, int TR, bool K1>
+static fvn_status launch_ks(fvn_ctx* ctx, const KsConv& c, cudaStream_t st) {
+    constexpr int NS = ks_stages<COUTP, TR, K1>();
+    using L = ks::Layout<COUTP, TR, NS, K1>;
+    static_assert(L::bytes <= 227 * 1024, "stage ring does not fit in shared memory");
+    auto kern = ks::conv_ks_kernel<COUTP, TR, NS, K1>;
+    static std::atomic<unsigned long long> configured{0};
+    FVN_CUDA(ctx, opt_in_smem(ctx, kern, (int)L::bytes, configured));
+    ks::Args a{};
+    fvn_status s = make_map(ctx, &a.map0, c.in0, 8 * c.ch0, c.W, c.H, L::HY, false);
+    if (s != FVN_OK) return s;
+    if (c.ch1 > 0) {
+        if ((s = make_map(ctx, &a.map1, c.in1, 8 * c.ch1, c.W, c.H, L::HY, false)) != FVN_OK) return s;
+    } else {
+        a.map1 = a.map0;
+    }
+    a.ch0 = c.ch0;
+    a.has1 = c.ch1 > 0;
+    a.groups = (c.ch0 + c.ch1 + 1) / 2;
+    a.w = static_cast<const uint4*>(c.wpk);
+    a.bias = c.bias;
+    a.out = static_cast<uint4*>(c.out);
+    a.out_chunks = (c.cout + 7) / 8;
+    a.out32 = c.out32;
+    a.cout = c.cout;
+    a.relu = c.relu;
+    a.H = c.H;
+    a.W = c.W;
+    a.tiles_x = (c.W + L::TO - 1) / L::TO;
+    a.ntiles = a.tiles_x * ((c.H + TR - 1) / TR);
+    a.error = ctx->d_error;
+    const int grid = std::max(1, std::min(a.ntiles, ctx->num_sms > 0 ? ctx->num_sms : 148));
+    kern<<<grid, ks::kThreads, L::bytes, st>>>(a);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
+int ks_coutp(int cout) { return (cout + 15) / 16 * 16; }
+
+fvn_status ks_conv(fvn_ctx* ctx, const KsConv& c, cudaStream_t st) {
+    FVN_CHECK_ARG(ctx, c.in0 && c.wpk && c.bias && (c.out || c.out32) && (c.ch1 == 0 || c.in1), "null tensor");
+    FVN_CHECK_ARG(ctx, c.ch0 >= 1 && c.ch1 >= 0 && c.H >= 1 && c.W >= 1 && (c.k == 1 || c.k == 3), "bad layer");
+    const int cp = ks_coutp(c.cout);
+    const bool k1 = c.k == 1;
+#define FVN_KS(CP, TR)                                                       \
+    if (cp == CP) return k1 ? launch_ks<CP, TR, true>(ctx, c, st) : launch_ks<CP, TR, false>(ctx, c, st);
+    FVN_KS(16, 4)
+    FVN_KS(32, 4)
+    FVN_KS(48, 4)
+    FVN_KS(64, 4)
+    FVN_KS(80, 2)
+    FVN_KS(96, 2)
+    FVN_KS(112, 2)
+    FVN_KS(128, 2)
+#undef FVN_KS
+    return set_error(ctx, FVN_ERR_UNSUPPORTED, "no K-streamed convolution for %d output channels", c.cout);
 }
 
 }  // namespace fvn

@@ -135,6 +135,9 @@ extern "C" fvn_status fvn_destroy(fvn_ctx* ctx) {
     cudaFree(ctx->batch_ws.base);
     cudaFree(ctx->wnet.d_w);
     cudaFree(ctx->wnet.ws);
+    cudaFree(ctx->wnet.d_wpk);
+    cudaFree(ctx->wnet.d_bpk);
+    cudaFree(ctx->wnet.tws);
     for (void* p : ctx->batch_ws.pad) cudaFree(p);
     cudaFree(ctx->batch_ws.probe);
     delete ctx;
@@ -195,6 +198,10 @@ extern "C" fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value) {
         case FVN_OPT_CONV_FUSE_UP_DEC1:
             FVN_CHECK_ARG(ctx, value == 0 || value == 1, "decoder up-sampling option must be 0 or 1");
             ctx->conv_fuse_up_dec1 = value;
+            return FVN_OK;
+        case FVN_OPT_WNET_TENSOR_CORES:
+            FVN_CHECK_ARG(ctx, value == 0 || value == 1, "two-stage tensor-core option must be 0 or 1");
+            ctx->wnet.tc = value;
             return FVN_OK;
         case FVN_OPT_STAGE_TIMING:
             FVN_CHECK_ARG(ctx, value == 0 || value == 1, "stage-timing option must be 0 or 1");

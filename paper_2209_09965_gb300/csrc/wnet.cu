@@ -11,6 +11,7 @@
 // training kernels; this file adds the per-pixel filter, the join (forward
 // and backward) and the whole-frame forward pass behind
 // fvn_reconstruct_wnet.
+#include <cuda_fp16.h>
 #include <math.h>
 #include <string.h>
 
@@ -362,6 +363,311 @@ size_t plan_wnet(const fvn_wnet_config& c, int Wp, int Hp, WPlan* pl, char* base
     return off;
 }
 
+// ---------------------------------------------------------------------------
+// tensor-core path (FVN_OPT_WNET_TENSOR_CORES): the convolutions' tensors are
+// FP16 chunk-planar ([C / 8][H][W][8 halves]) and every convolution is the
+// K-streamed tcgen05 kernel; the 3-channel image path, the tap logits and
+// the blend logits stay FP32 planar.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void h8_to_f(uint4 u, float* f) {
+    const __half2* h = reinterpret_cast<const __half2*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const float2 t = __half22float2(h[i]);
+        f[2 * i] = t.x;
+        f[2 * i + 1] = t.y;
+    }
+}
+
+__device__ __forceinline__ uint4 f_to_h8(const float* f) {
+    uint4 u;
+    __half2* h = reinterpret_cast<__half2*>(&u);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) h[i] = __floats2half2_rn(f[2 * i], f[2 * i + 1]);
+    return u;
+}
+
+// the sparse frame (FP32 [5][h][w]) as chunk 0 of a Wp x Hp chunk-planar
+// tensor: zero outside the frame and in lanes 5..7
+__global__ void cp_frame_kernel(const float* __restrict__ rgbam, int w, int h, uint4* __restrict__ out, int Wp,
+                                int Hp) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= Wp * Hp) return;
+    const int y = r / Wp, x = r - y * Wp;
+    float f[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (x < w && y < h)
+#pragma unroll
+        for (int c = 0; c < 5; ++c) f[c] = __ldg(rgbam + ((long long)c * h + y) * w + x);
+    out[r] = f_to_h8(f);
+}
+
+// 2 x 2 average of every chunk plane (H, W even); blockIdx.y = chunk
+__global__ void cp_pool2_kernel(const uint4* __restrict__ in, int H, int W, uint4* __restrict__ out) {
+    const int ho = H / 2, wo = W / 2, r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= ho * wo) return;
+    const int y = r / wo, x = r - y * wo;
+    const uint4* p = in + (long long)blockIdx.y * H * W + (long long)(2 * y) * W + 2 * x;
+    float a[8], b[8], s[8];
+    h8_to_f(__ldg(p), s);
+    h8_to_f(__ldg(p + 1), a);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s[j] += a[j];
+    h8_to_f(__ldg(p + W), a);
+    h8_to_f(__ldg(p + W + 1), b);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) s[j] = 0.25f * (s[j] + a[j] + b[j]);
+    out[(long long)blockIdx.y * ho * wo + r] = f_to_h8(s);
+}
+
+// bilinear x2 up-sampling of every chunk plane (half-pixel centres, edge
+// clamp): h x w -> 2h x 2w; blockIdx.y = chunk
+__global__ void cp_up2_kernel(const uint4* __restrict__ in, int h, int w, uint4* __restrict__ out) {
+    const int H2 = 2 * h, W2 = 2 * w, r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= H2 * W2) return;
+    const int oy = r / W2, ox = r - oy * W2;
+    int y0, y1, x0, x1;
+    float ty, tx;
+    up_src(oy, h, y0, y1, ty);
+    up_src(ox, w, x0, x1, tx);
+    const uint4* p = in + (long long)blockIdx.y * h * w;
+    float f00[8], f01[8], f10[8], f11[8], o[8];
+    h8_to_f(__ldg(p + y0 * w + x0), f00);
+    h8_to_f(__ldg(p + y0 * w + x1), f01);
+    h8_to_f(__ldg(p + y1 * w + x0), f10);
+    h8_to_f(__ldg(p + y1 * w + x1), f11);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+        const float top = (1.f - tx) * f00[j] + tx * f01[j], bot = (1.f - tx) * f10[j] + tx * f11[j];
+        o[j] = (1.f - ty) * top + ty * bot;
+    }
+    out[(long long)blockIdx.y * H2 * W2 + r] = f_to_h8(o);
+}
+
+bool tc_widths_ok(const fvn_wnet_config& c) {
+    auto ok = [](int v) { return v % 8 == 0 && v <= 128; };
+    if (!ok(c.bot)) return false;
+    for (int s = 0; s < c.levels; ++s)
+        if (!ok(c.enc[s]) || !ok(c.dec[s])) return false;
+    return true;
+}
+
+// Every layer's weights packed for the K-streamed convolution: FP16
+// [group][tap][2 chunks][coutp][8], input channel (2 group + chunk) 8 + lane
+// (the concatenated inputs of a layer meet on a chunk boundary: every width
+// is a multiple of 8), zero past cin / cout; biases zero padded to coutp.
+void pack_tc(const WTable& t, const float* host_w, std::vector<__half>& wp, std::vector<float>& bp, size_t* woff,
+             size_t* boff) {
+    wp.clear();
+    bp.clear();
+    for (size_t li = 0; li < t.L.size(); ++li) {
+        const WLayer& l = t.L[li];
+        const int coutp = ks_coutp(l.cout), chunks = (l.cin + 7) / 8, groups = (chunks + 1) / 2, taps = l.k * l.k;
+        const float* w = host_w + l.off;
+        const float* b = w + (size_t)l.cout * l.cin * taps;
+        woff[li] = wp.size();
+        boff[li] = bp.size();
+        wp.resize(wp.size() + (size_t)groups * taps * 2 * coutp * 8, __float2half(0.f));
+        bp.resize(bp.size() + coutp, 0.f);
+        __half* dst = wp.data() + woff[li];
+        for (int g = 0; g < groups; ++g)
+            for (int tp = 0; tp < taps; ++tp)
+                for (int kk = 0; kk < 2; ++kk)
+                    for (int co = 0; co < l.cout; ++co)
+                        for (int j = 0; j < 8; ++j) {
+                            const int ci = (2 * g + kk) * 8 + j;
+                            if (ci < l.cin)
+                                dst[((((size_t)g * taps + tp) * 2 + kk) * coutp + co) * 8 + j] =
+                                    __float2half(w[((size_t)co * l.cin + ci) * taps + tp]);
+                        }
+        for (int co = 0; co < l.cout; ++co) bp[boff[li] + co] = b[co];
+    }
+}
+
+// activation buffers of the tensor-core path (chunk-planar FP16 for the
+// convolutions' tensors, FP32 planar for the image path and the heads)
+struct TPlan {
+    uint4* x;                                        // the sparse frame, one chunk
+    uint4 *T[FVN_WNET_MAX_LEVELS], *E[FVN_WNET_MAX_LEVELS], *U[FVN_WNET_MAX_LEVELS], *UPD[FVN_WNET_MAX_LEVELS];
+    uint4 *P[FVN_WNET_MAX_LEVELS + 1], *G[FVN_WNET_MAX_LEVELS], *PG[FVN_WNET_MAX_LEVELS + 1];
+    uint4 *GD[FVN_WNET_MAX_LEVELS], *UPK[FVN_WNET_MAX_LEVELS];
+    uint4 *TB, *B, *GB;
+    float *LE[FVN_WNET_MAX_LEVELS], *LD[FVN_WNET_MAX_LEVELS], *ZD[FVN_WNET_MAX_LEVELS];
+    float *I[FVN_WNET_MAX_LEVELS + 1], *J[FVN_WNET_MAX_LEVELS], *X[FVN_WNET_MAX_LEVELS], *Y[FVN_WNET_MAX_LEVELS + 1];
+    float* LB;
+};
+
+size_t plan_wnet_tc(const fvn_wnet_config& c, int Wp, int Hp, TPlan* pl, char* base) {
+    size_t off = 0;
+    auto bytes_at = [&](size_t bytes) -> char* {
+        char* p = base ? base + off : nullptr;
+        off += (bytes + 255) & ~(size_t)255;
+        return p;
+    };
+    auto half = [&](int ch, int s) {   // ch channels as chunk planes at level s
+        return reinterpret_cast<uint4*>(bytes_at((size_t)((ch + 7) / 8) * (Hp >> s) * (Wp >> s) * 16));
+    };
+    auto f32 = [&](int ch, int s) {
+        return reinterpret_cast<float*>(bytes_at((size_t)ch * (Hp >> s) * (Wp >> s) * sizeof(float)));
+    };
+    const int L = c.levels;
+    pl->x = half(8, 0);
+    for (int s = 0; s < L; ++s) {
+        const int up = s == L - 1 ? c.bot : c.dec[s + 1];
+        pl->T[s] = half(std::max(c.enc[s], c.dec[s]), s);
+        pl->E[s] = half(c.enc[s], s);
+        pl->U[s] = half(c.dec[s], s);
+        pl->UPD[s] = half(up, s);
+        pl->G[s] = half(c.enc[s], s);
+        pl->GD[s] = half(c.dec[s], s);
+        pl->UPK[s] = half(up, s);
+        pl->LE[s] = f32(kTaps, s);
+        pl->LD[s] = f32(kTaps, s);
+        pl->ZD[s] = f32(1, s);
+        pl->I[s] = f32(3, s);
+        pl->J[s] = f32(3, s);
+        pl->X[s] = f32(3, s);
+        pl->Y[s] = f32(3, s);
+    }
+    for (int s = 1; s <= L; ++s) {
+        pl->P[s] = half(c.enc[s - 1], s);
+        pl->PG[s] = half(c.enc[s - 1], s);
+    }
+    pl->I[L] = f32(3, L);
+    pl->Y[L] = f32(3, L);
+    pl->TB = half(c.bot, L);
+    pl->B = half(c.bot, L);
+    pl->GB = half(c.bot, L);
+    pl->LB = f32(kTaps, L);
+    return off;
+}
+
+dim3 cp_grid(long long plane, int chunks) { return dim3((unsigned)((plane + 255) / 256), (unsigned)chunks); }
+
+#define WK(call)                                        \
+    do {                                                \
+        const fvn_status s_ = (call);                   \
+        if (s_ != FVN_OK) return s_;                    \
+    } while (0)
+#define WQ(call)                                                                       \
+    do {                                                                               \
+        const fvn_status s_ = (call);                                                  \
+        if (s_ != FVN_OK) return set_error(ctx, s_, "%s", fvn_last_error(nullptr));    \
+    } while (0)
+
+// The forward pass of fvn_reconstruct_wnet on the tensor cores: the same
+// layers, in the same order, as the FP32 pass.
+fvn_status wnet_forward_tc(fvn_ctx* ctx, const float* rgbam, int w, int h, float* rgb, void* stream) {
+    WnetState& S = ctx->wnet;
+    const fvn_wnet_config& c = S.cfg;
+    const int L = c.levels, m = 1 << L;
+    const int Wp = (w + m - 1) / m * m, Hp = (h + m - 1) / m * m;
+    cudaStream_t st = as_stream(stream);
+    if (S.tws_w != Wp || S.tws_h != Hp) {
+        FVN_CUDA(ctx, cudaDeviceSynchronize());
+        cudaFree(S.tws);
+        S.tws = nullptr;
+        S.tws_w = S.tws_h = 0;
+        TPlan tmp;
+        const size_t bytes = plan_wnet_tc(c, Wp, Hp, &tmp, nullptr);
+        FVN_CUDA(ctx, cudaMalloc(&S.tws, bytes));
+        S.tws_bytes = bytes;
+        S.tws_w = Wp;
+        S.tws_h = Hp;
+    }
+    TPlan B;
+    plan_wnet_tc(c, Wp, Hp, &B, static_cast<char*>(S.tws));
+    const WTable t = make_table(c);
+    auto hs = [&](int s) { return Hp >> s; };
+    auto ws = [&](int s) { return Wp >> s; };
+    auto conv = [&](const uint4* xa, int ca, const uint4* xb, int cb, int s, int li, int relu, uint4* y, float* y32) {
+        KsConv k{};
+        k.in0 = xa;
+        k.ch0 = (ca + 7) / 8;
+        k.in1 = xb;
+        k.ch1 = xb ? (cb + 7) / 8 : 0;
+        k.H = hs(s);
+        k.W = ws(s);
+        k.wpk = static_cast<const __half*>(S.d_wpk) + S.wpk_off[li];
+        k.bias = S.d_bpk + S.bpk_off[li];
+        k.cout = t.L[li].cout;
+        k.k = t.L[li].k;
+        k.relu = relu;
+        k.out = y;
+        k.out32 = y32;
+        return ks_conv(ctx, k, st);
+    };
+    auto pool = [&](const uint4* x, int ch, int s, uint4* y) {   // level s -> s + 1
+        cp_pool2_kernel<<<cp_grid((long long)hs(s + 1) * ws(s + 1), (ch + 7) / 8), 256, 0, st>>>(x, hs(s), ws(s), y);
+        return cudaGetLastError() == cudaSuccess ? FVN_OK : set_error(ctx, FVN_ERR_CUDA, "pooling launch failed");
+    };
+    auto up = [&](const uint4* x, int ch, int s, uint4* y) {     // level s + 1 -> s
+        cp_up2_kernel<<<cp_grid((long long)hs(s) * ws(s), (ch + 7) / 8), 256, 0, st>>>(x, hs(s + 1), ws(s + 1), y);
+        return cudaGetLastError() == cudaSuccess ? FVN_OK : set_error(ctx, FVN_ERR_CUDA, "up-sampling launch failed");
+    };
+
+    cp_frame_kernel<<<(Wp * Hp + 255) / 256, 256, 0, st>>>(rgbam, w, h, B.x, Wp, Hp);
+    FVN_LAUNCH_CHECK(ctx);
+    // D: encoder, coarsest block, decoder, output layer
+    const uint4* in = B.x;
+    int cin = 5;
+    for (int s = 0; s < L; ++s) {
+        WK(conv(in, cin, nullptr, 0, s, t.d_enc_a[s], 1, B.T[s], nullptr));
+        WK(conv(B.T[s], c.enc[s], nullptr, 0, s, t.d_enc_b[s], 1, B.E[s], nullptr));
+        WK(pool(B.E[s], c.enc[s], s, B.P[s + 1]));
+        in = B.P[s + 1];
+        cin = c.enc[s];
+    }
+    WK(conv(B.P[L], c.enc[L - 1], nullptr, 0, L, t.d_bot_a, 1, B.TB, nullptr));
+    WK(conv(B.TB, c.bot, nullptr, 0, L, t.d_bot_b, 1, B.B, nullptr));
+    const uint4* prev = B.B;
+    int pc = c.bot;
+    for (int s = L - 1; s >= 0; --s) {
+        WK(up(prev, pc, s, B.UPD[s]));
+        WK(conv(B.UPD[s], pc, B.E[s], c.enc[s], s, t.d_dec_a[s], 1, B.T[s], nullptr));
+        WK(conv(B.T[s], c.dec[s], nullptr, 0, s, t.d_dec_b[s], 1, B.U[s], nullptr));
+        prev = B.U[s];
+        pc = c.dec[s];
+    }
+    WK(conv(B.U[0], c.dec[0], nullptr, 0, 0, t.d_out, 0, nullptr, B.I[0]));
+    // K: encoder blocks, coarsest block, decoder blocks (features and heads)
+    for (int s = 0; s < L; ++s) {
+        if (s == 0) {
+            WK(conv(B.U[0], c.dec[0], nullptr, 0, 0, t.k_enc[0], 1, B.G[0], nullptr));
+        } else {
+            WK(pool(B.G[s - 1], c.enc[s - 1], s - 1, B.PG[s]));
+            WK(conv(B.PG[s], c.enc[s - 1], B.U[s], c.dec[s], s, t.k_enc[s], 1, B.G[s], nullptr));
+        }
+        WK(conv(B.G[s], c.enc[s], nullptr, 0, s, t.k_enc_taps[s], 0, nullptr, B.LE[s]));
+    }
+    WK(pool(B.G[L - 1], c.enc[L - 1], L - 1, B.PG[L]));
+    WK(conv(B.PG[L], c.enc[L - 1], B.B, c.bot, L, t.k_bot, 1, B.GB, nullptr));
+    WK(conv(B.GB, c.bot, nullptr, 0, L, t.k_bot_taps, 0, nullptr, B.LB));
+    const uint4* kprev = B.GB;
+    pc = c.bot;
+    for (int s = L - 1; s >= 0; --s) {
+        WK(up(kprev, pc, s, B.UPK[s]));
+        WK(conv(B.UPK[s], pc, B.U[s], c.dec[s], s, t.k_dec[s], 1, B.GD[s], nullptr));
+        WK(conv(B.GD[s], c.dec[s], nullptr, 0, s, t.k_dec_taps[s], 0, nullptr, B.LD[s]));
+        WK(conv(B.GD[s], c.dec[s], nullptr, 0, s, t.k_dec_blend[s], 0, nullptr, B.ZD[s]));
+        kprev = B.GD[s];
+        pc = c.dec[s];
+    }
+    // image path (FP32): O_d through the encoder kernels, the coarsest, then
+    // the decoder joins and kernels
+    for (int s = 0; s < L; ++s) {
+        WQ(fvn_filter3_fwd(B.I[s], B.LE[s], 1, hs(s), ws(s), B.J[s], stream));
+        WQ(fvn_avgpool2_fwd(B.J[s], 3, hs(s), ws(s), B.I[s + 1], stream));
+    }
+    WQ(fvn_filter3_fwd(B.I[L], B.LB, 1, hs(L), ws(L), B.Y[L], stream));
+    for (int s = L - 1; s >= 0; --s) {
+        WQ(fvn_wnet_join_fwd(B.J[s], B.Y[s + 1], B.ZD[s], 1, hs(s), ws(s), B.X[s], stream));
+        WQ(fvn_filter3_fwd(B.X[s], B.LD[s], 1, hs(s), ws(s), B.Y[s], stream));
+    }
+    window_copy_kernel<<<grid_of(3LL * w * h), 256, 0, st>>>(B.Y[0], Wp, Hp, rgb, w, h, 3);
+    FVN_LAUNCH_CHECK(ctx);
+    return FVN_OK;
+}
+
 }  // namespace
 }  // namespace fvn
 
@@ -404,8 +710,28 @@ extern "C" fvn_status fvn_load_wnet_weights(fvn_ctx* ctx, const fvn_wnet_config*
         S.ws = nullptr;
         S.ws_bytes = 0;
         S.ws_w = S.ws_h = 0;
+        cudaFree(S.tws);
+        S.tws = nullptr;
+        S.tws_bytes = 0;
+        S.tws_w = S.tws_h = 0;
     }
     S.cfg = *cfg;
+    // the tensor-core path's packed weights
+    S.tc_ok = tc_widths_ok(*cfg);
+    if (S.tc_ok) {
+        const WTable t = make_table(*cfg);
+        std::vector<__half> wp;
+        std::vector<float> bp;
+        pack_tc(t, host_w, wp, bp, S.wpk_off, S.bpk_off);
+        cudaFree(S.d_wpk);
+        cudaFree(S.d_bpk);
+        S.d_wpk = nullptr;
+        S.d_bpk = nullptr;
+        FVN_CUDA(ctx, cudaMalloc(&S.d_wpk, wp.size() * sizeof(__half)));
+        FVN_CUDA(ctx, cudaMalloc(&S.d_bpk, bp.size() * sizeof(float)));
+        FVN_CUDA(ctx, cudaMemcpy(S.d_wpk, wp.data(), wp.size() * sizeof(__half), cudaMemcpyHostToDevice));
+        FVN_CUDA(ctx, cudaMemcpy(S.d_bpk, bp.data(), bp.size() * sizeof(float), cudaMemcpyHostToDevice));
+    }
     S.loaded = true;
     return FVN_OK;
 }
@@ -417,6 +743,12 @@ extern "C" fvn_status fvn_reconstruct_wnet(fvn_ctx* ctx, const float* rgbam, int
     FVN_CHECK_ARG(ctx, w >= 1 && h >= 1 && w <= kMaxSide && h <= kMaxSide, "bad frame size %d x %d", w, h);
     WnetState& S = ctx->wnet;
     if (!S.loaded) return set_error(ctx, FVN_ERR_STATE, "no two-stage weights (call fvn_load_wnet_weights first)");
+    if (S.tc) {
+        if (!S.tc_ok)
+            return set_error(ctx, FVN_ERR_UNSUPPORTED,
+                             "the tensor-core two-stage path needs every width a multiple of 8 and at most 128");
+        return wnet_forward_tc(ctx, rgbam, w, h, rgb, stream);
+    }
     const fvn_wnet_config& c = S.cfg;
     const int L = c.levels, m = 1 << L;
     const int Wp = (w + m - 1) / m * m, Hp = (h + m - 1) / m * m;

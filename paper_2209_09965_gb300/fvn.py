@@ -47,6 +47,7 @@ OPT_MARCH_COUNT_SHADOW = 9
 OPT_STAGE_TIMING = 10
 OPT_CONV_ROWS_HALF, OPT_CONV_ROWS_QUARTER, OPT_CONV_ROWS_DEC1 = 11, 12, 13
 OPT_CONV_FUSE_UP_DEC1 = 14
+OPT_WNET_TENSOR_CORES = 15
 STAGES = ("mask", "march_setup", "volume_prep", "march", "network")
 
 

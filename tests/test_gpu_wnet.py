@@ -217,3 +217,74 @@ def test_training_runs(fvn):
     w, log = train.train(steps=10, nvol=2, vol_n=64, log_every=5, batch=2, wnet=wl.WNET_SLIM)
     assert w.size == W.param_count(wl.WNET_SLIM)
     assert all(np.isfinite(v) for _, v in log)
+
+
+# The tensor-core path (FVN_OPT_WNET_TENSOR_CORES): FP16 operands and
+# activations, FP32 accumulation.  Bar: 2e-2 of the output's scale against
+# the FP64 oracle -- FP16 keeps 11 significant bits, and the error of some
+# 30 layers in sequence stays near 1e-2 of the scale.
+TC_TOL = 2e-2
+
+
+@pytest.mark.parametrize("cfg,h,w,seed", [
+    (wl.WNET_PAPER, 40, 48, 3),        # the paper's widths: 3x3 up to 176 input channels, 1x1 up to 176
+    (wl.WNET_PAPER, 37, 131, 4),       # ragged: padded to multiples of 8, tiles across 126-pixel rows
+    (wl.WNET_SLIM, 64, 96, 5),
+    (((8, 16), 24, (8, 16)), 9, 300, 6),
+])
+def test_reconstruct_tensor_cores_matches_oracle(fvn, cfg, h, w, seed):
+    flat = wl.wnet_weights(cfg, seed)
+    flat = flat + np.random.default_rng(seed).normal(size=flat.size).astype(np.float32) * 0.05
+    sp = sparse_input(1, h, w, seed)[0]
+    c = fvn.Context()
+    try:
+        c.load_wnet_weights(cfg, flat)
+        c.set_option(fvn.OPT_WNET_TENSOR_CORES, 1)
+        rgb = torch.full((3, h, w), 7.0, device=DEV)
+        c.reconstruct_wnet(T(sp), w, h, rgb)
+        torch.cuda.synchronize()
+        c.device_status()
+        ref = W.forward(W.unpack(flat, cfg), cfg, sp.astype(np.float64))
+        scale = max(1.0, np.abs(ref).max())
+        assert np.abs(N(rgb) - ref).max() < TC_TOL * scale
+        again = torch.empty_like(rgb)
+        c.reconstruct_wnet(T(sp), w, h, again)
+        torch.cuda.synchronize()
+        assert torch.equal(rgb, again)       # no atomics: the same result every time
+    finally:
+        c.close()
+
+
+def test_tensor_cores_full_frame_agrees_with_fp32_path(fvn):
+    """At 1080p (every tile position, 1 CTA per SM over many tiles) the
+    tensor-core pass stays within the FP16 bar of the FP32 pass."""
+    cfg = wl.WNET_PAPER
+    flat = wl.wnet_weights(cfg, 3)
+    h, w = 1080, 1920
+    sp = T(sparse_input(1, h, w, 9, density=0.1)[0])
+    c = fvn.Context()
+    try:
+        c.load_wnet_weights(cfg, flat)
+        ref = torch.empty(3, h, w, device=DEV)
+        c.reconstruct_wnet(sp, w, h, ref)
+        c.set_option(fvn.OPT_WNET_TENSOR_CORES, 1)
+        out = torch.empty(3, h, w, device=DEV)
+        c.reconstruct_wnet(sp, w, h, out)
+        torch.cuda.synchronize()
+        c.device_status()
+        scale = max(1.0, float(ref.abs().max()))
+        assert float((out - ref).abs().max()) < TC_TOL * scale
+    finally:
+        c.close()
+
+
+def test_tensor_cores_reject_unsupported_widths(fvn):
+    c = fvn.Context()
+    try:
+        c.load_wnet_weights(TINY, wl.wnet_weights(TINY, 1))
+        c.set_option(fvn.OPT_WNET_TENSOR_CORES, 1)
+        rgb = torch.empty(3, 8, 8, device=DEV)
+        with pytest.raises(fvn.FvnError, match="multiple of 8"):
+            c.reconstruct_wnet(torch.zeros(5, 8, 8, device=DEV), 8, 8, rgb)
+    finally:
+        c.close()
