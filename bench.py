@@ -773,6 +773,11 @@ def run_two_stage(fvn, wl, weights, vol, tf, mp, dev, nframes, flush):
     cfgs = {"two_stage_slim": wl.WNET_SLIM, "two_stage_paper": wl.WNET_PAPER}
     ctxs = {}
     try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        peaks = {}
+    tc_peak = float(peaks.get("bf16_tflops", 1900.0))
+    try:
         for key, path in paths.items():
             c = fvn.Context()
             ctxs[key] = c
@@ -787,6 +792,12 @@ def run_two_stage(fvn, wl, weights, vol, tf, mp, dev, nframes, flush):
                 c.load_weights(wts)
         ctxs["single_kp_on_sparse_shipped"] = fvn.Context()
         ctxs["single_kp_on_sparse_shipped"].load_weights(weights)
+        for key in list(cfgs):   # the same weights through the tensor-core path
+            c = fvn.Context()
+            ctxs[key + "_tc"] = c
+            c.load_wnet_weights(cfgs[key], np.load(paths[key]).astype(np.float32))
+            c.set_option(fvn.OPT_WNET_TENSOR_CORES, 1)
+            cfgs[key + "_tc"] = cfgs[key]
         sp = torch.empty(5, H, W, device=dev)
         dense = torch.empty(5, H, W, device=dev)
         rgb = torch.empty(3, H, W, device=dev)
@@ -824,10 +835,17 @@ def run_two_stage(fvn, wl, weights, vol, tf, mp, dev, nframes, flush):
         for key, cfg in cfgs.items():
             t = float(np.mean(ms[key])) if ms[key] else float("nan")
             fl = wnet_flops_per_px(wl, cfg)
-            timing[key] = {"ms_per_1080p_frame": t, "flops_per_px": fl,
-                           "achieved_tflops": fl * W * H / (t / 1000.0) / 1e12,
-                           "peak_tflops": FP32_PEAK_TFLOPS, "bound": "alu",
-                           "note": "FP32 CUDA-core convolutions (the training kernels)"}
+            ach = fl * W * H / (t / 1000.0) / 1e12
+            if key.endswith("_tc"):
+                timing[key] = {"ms_per_1080p_frame": t, "flops_per_px": fl, "achieved_tflops": ach,
+                               "peak_tflops": tc_peak, "frac": ach / tc_peak, "bound": "tensor",
+                               "peak_kind": "measured bf16 burst (FP16 runs at the same rate)",
+                               "note": "K-streamed tcgen05 convolutions, FP16 operands and activations, FP32 "
+                                       "accumulation (FVN_OPT_WNET_TENSOR_CORES = 1)"}
+            else:
+                timing[key] = {"ms_per_1080p_frame": t, "flops_per_px": fl, "achieved_tflops": ach,
+                               "peak_tflops": FP32_PEAK_TFLOPS, "frac": ach / FP32_PEAK_TFLOPS, "bound": "alu",
+                               "note": "FP32 CUDA-core convolutions (the training kernels)"}
         out["reconstruct"] = timing
         # the FP64 oracle beside it: the same network on a 96 x 96 crop of the
         # sparse frame, on the host, scaled to the frame's pixels
