@@ -53,6 +53,10 @@ def parse():
     p.add_argument("--profile-two-stage", action="store_true",
                    help="two untimed two-stage passes at 1080p (paper widths), for ncu")
     p.add_argument("--profile-size", default="1920x1080", help="frame size of --profile-two-stage")
+    p.add_argument("--wnet-tensor-cores", action="store_true",
+                   help="--profile-two-stage on the tensor-core engine (FVN_OPT_WNET_TENSOR_CORES)")
+    p.add_argument("--profile-train", action="store_true",
+                   help="three untimed eager training steps (8 crops of 256 x 256, tensor cores), for ncu")
     p.add_argument("--two-stage-only", action="store_true",
                    help="only the two-stage network comparison (prints its JSON)")
     p.add_argument("--sweep", action="store_true",
@@ -358,7 +362,31 @@ def run_profile_shadows():
     print("shadow profile case done")
 
 
-def run_profile_two_stage(size="1920x1080"):
+def run_profile_train(steps=3, batch=8, crop=256):
+    """Untimed eager training steps of the single network on the tensor
+    cores (the timed benchmark replays the same step as one CUDA graph), on
+    seeded uniform crops of the benchmark's shape, for an ncu launch list."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    from paper_2209_09965_gb300 import train
+    dev = torch.device("cuda")
+    weights, _ = load_weights()
+    g = torch.Generator(device=dev).manual_seed(5)
+    xs = torch.rand(batch, 5, crop, crop, device=dev, generator=g)
+    xs[:, 4] = (xs[:, 4] < 0.15).float()
+    ys = torch.rand(batch, 3, crop, crop, device=dev, generator=g)
+    P = train.Params(np.array(weights, np.float32), dev)
+    for _ in range(steps):
+        P.g.zero_()
+        train._Loss.apply(train.forward(P, xs, tc=True), ys, 1.0).backward()
+        P.adam(1e-4)
+    torch.cuda.synchronize()
+    print("training profile case done")
+
+
+def run_profile_two_stage(size="1920x1080", tensor_cores=False):
     """Two untimed passes of the two-stage network with the paper's widths
     (the trained equal-budget weights when present) over the sparse headline
     frame of orbit frame 16 (1920 x 1080, or the top-left window of the
@@ -377,6 +405,8 @@ def run_profile_two_stage(size="1920x1080"):
     path = os.path.join(WDIR, ABLATION["two_stage_paper"])
     wts = np.load(path).astype(np.float32) if os.path.exists(path) else wl.wnet_weights(wl.WNET_PAPER, 3)
     ctx.load_wnet_weights(wl.WNET_PAPER, wts)
+    if tensor_cores:
+        ctx.set_option(fvn.OPT_WNET_TENSOR_CORES, 1)
     vol = torch.from_numpy(vol_np).to(dev)
     tf = torch.from_numpy(tf_np).to(dev)
     rgb = torch.empty(3, H, W, device=dev)
@@ -1085,7 +1115,9 @@ def main():
     if args.profile_shadows:
         return run_profile_shadows()
     if args.profile_two_stage:
-        return run_profile_two_stage(args.profile_size)
+        return run_profile_two_stage(args.profile_size, args.wnet_tensor_cores)
+    if args.profile_train:
+        return run_profile_train()
     if args.sweep:
         return run_sweep()
     if args.sweep_shadows:
