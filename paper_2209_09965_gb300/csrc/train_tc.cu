@@ -310,15 +310,17 @@ struct WgArgs {
     int* error;
 };
 
-constexpr int kWgRS = 132;              // FP32 row stride of the staged rows (130 used: x0 - 1 .. x0 + 128)
+constexpr int kWgRS = 132;              // FP32 row stride of the staged dz (16-byte rows for float4 reads)
+constexpr int kWgXS = 131;              // FP32 row stride of the staged input rows (130 used: x0 - 1 .. x0 + 128);
+                                        // odd, so the 32 rows R = 9 ci + t of a warp fall in distinct banks
 constexpr int kWgCh = 16;               // input channels 128 consecutive rows R = 9 ci + t touch at most
 
 template <int COUTP>
 struct WgLayout {
     static constexpr size_t a_bytes = 16ull * 128 * 16;                 // [16 chunks][128 rows][8 px] BF16
     static constexpr size_t b_bytes = 16ull * COUTP * 16;               // [16 chunks][COUTP][8 px]
-    static constexpr size_t x_off = a_bytes + b_bytes;                  // [kWgCh][3 slots][kWgRS] FP32
-    static constexpr size_t g_off = x_off + 4ull * kWgCh * 3 * kWgRS;   // dz: [COUTP][kWgRS] FP32
+    static constexpr size_t x_off = a_bytes + b_bytes;                  // [kWgCh][3 slots][kWgXS] FP32
+    static constexpr size_t g_off = (x_off + 4ull * kWgCh * 3 * kWgXS + 15) / 16 * 16;   // dz: [COUTP][kWgRS] FP32
     static constexpr size_t bar_off = g_off + 4ull * COUTP * kWgRS;
     static constexpr size_t bytes = bar_off + 16;
     static constexpr uint32_t tmem_cols = COUTP <= 32 ? 32 : COUTP <= 64 ? 64 : COUTP <= 128 ? 128 : 256;
@@ -390,7 +392,7 @@ conv3x3_wgrad_kernel(const __grid_constant__ WgArgs a) {
             const int i = tid + k * kThreads;
             if (i < nch * 130) {
                 const int cl = i / 130, px = i - cl * 130;
-                xs[(cl * 3 + slot) * kWgRS + px] = rv[k];
+                xs[(cl * 3 + slot) * kWgXS + px] = rv[k];
             }
         }
     };
@@ -416,6 +418,29 @@ conv3x3_wgrad_kernel(const __grid_constant__ WgArgs a) {
             gs[(i >> 7) * kWgRS + (i & 127)] = mv[k] > 0.f ? gv[k] : 0.f;
         }
     };
+
+    // The A build: thread tid always fills row r = tid % 128 (chunks tid / 128
+    // + 2 k), so its (ci, tap) decomposition is fixed; the bias row of ones
+    // and the zero rows past it never change and are written once here.
+    static_assert(kThreads == 256, "the A build gives each thread one row and every other chunk");
+    const int r_own = tid & 127, c_own = tid >> 7;
+    const int R_own = mblock * 128 + r_own;
+    const bool weight_row = R_own < rows - 1;
+    int ty_own = 0;
+    const float* xrow = xs;
+    if (weight_row) {
+        const int ci = R_own / 9, t = R_own - ci * 9;
+        ty_own = t / 3;
+        xrow = xs + (ci - ci_lo) * 3 * kWgXS + (t - ty_own * 3);
+    } else {
+        float v[8];
+        const float one = R_own == rows - 1 ? 1.f : 0.f;   // dz is zero past the edge
+#pragma unroll
+        for (int j = 0; j < 8; ++j) v[j] = one;
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            *reinterpret_cast<uint4*>(sA + ((size_t)(c_own + 2 * k) * 128 + r_own) * 16) = pack8bf(v);
+    }
 
     constexpr uint32_t idesc = idesc_bf16(128, COUTP);
     uint32_t phase = 0;
@@ -453,21 +478,16 @@ conv3x3_wgrad_kernel(const __grid_constant__ WgArgs a) {
             load_dz(nimg, nx0, ny);
         }
         // ---- BF16 operands: A row R = x[ci] shifted by tap t; B = dz
-        for (int i = tid; i < 128 * 16; i += kThreads) {   // (row r, chunk c), r fastest
-            const int c = i >> 7, r = i & 127;
-            const int R = mblock * 128 + r;
-            float v[8];
-            if (R < rows - 1) {
-                const int ci = R / 9, t = R - ci * 9, ty = t / 3, tx = t - ty * 3;
-                const float* src = xs + ((ci - ci_lo) * 3 + (y + ty + 2) % 3) * kWgRS + c * 8 + tx;
+        if (weight_row) {   // row R of A: x[ci] of image row y + ty - 1 (window slot (y + ty + 2) % 3), shifted by tx
+            const float* src = xrow + ((y + ty_own + 2) % 3) * kWgXS;
 #pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = src[j];
-            } else {
-                const float one = R == rows - 1 ? 1.f : 0.f;   // dz is zero past the edge
+            for (int k = 0; k < 8; ++k) {
+                const int c = c_own + 2 * k;
+                float v[8];
 #pragma unroll
-                for (int j = 0; j < 8; ++j) v[j] = one;
+                for (int j = 0; j < 8; ++j) v[j] = src[c * 8 + j];
+                *reinterpret_cast<uint4*>(sA + ((size_t)c * 128 + r_own) * 16) = pack8bf(v);
             }
-            *reinterpret_cast<uint4*>(sA + ((size_t)c * 128 + r) * 16) = pack8bf(v);
         }
         for (int i = tid; i < COUTP * 16; i += kThreads) {   // (output channel co, chunk c), co fastest
             const int c = i / COUTP, co = i - c * COUTP;

@@ -102,6 +102,7 @@ class Params:
 
     def adam(self, lr=1e-3):
         self.step += 1
+        join_wgrad(self.g.device)
         fvn.adam_step(self.p.data, self.g, self.m, self.v, self.step, lr=lr)
 
     def numpy(self):
@@ -141,11 +142,16 @@ class GraphedStep:
         P = self.P
         P.g.zero_()
         pred = self.fwd(P, self.xs)
-        loss = _Loss.apply(pred, self.ys, self.lam)
-        loss.backward()
+        # the loss and its gradient in one kernel; the backward pass starts
+        # from that gradient (no loss node, no multiply by dL/dL = 1)
+        loss = torch.zeros(1, device=pred.device)
+        g = torch.empty_like(pred)
+        fvn.loss_l1grad(pred.detach(), self.ys, self.lam, loss, g)
+        pred.backward(g)
+        join_wgrad(P.g.device)
         self.step_t.add_(1)
         fvn.adam_step_dev(P.p.data, P.g, P.m, P.v, self.step_t, lr=self.lr)
-        return loss.detach()
+        return loss[0]
 
     def __call__(self, xs: torch.Tensor = None, ys: torch.Tensor = None):
         if xs is not None:
@@ -180,6 +186,24 @@ class _Conv(torch.autograd.Function):
         return gxa, gxb, None, None, None, None, None
 
 
+_WGRAD_STREAMS = {}
+
+
+def _wgrad_stream(device) -> torch.cuda.Stream:
+    """The side stream the tensor-core weight gradients run on (per device)."""
+    key = torch.device(device).index if torch.device(device).index is not None else torch.cuda.current_device()
+    if key not in _WGRAD_STREAMS:
+        _WGRAD_STREAMS[key] = torch.cuda.Stream(device=key)
+    return _WGRAD_STREAMS[key]
+
+
+def join_wgrad(device):
+    """Make the current stream wait for the weight gradients issued so far."""
+    key = torch.device(device).index if torch.device(device).index is not None else torch.cuda.current_device()
+    if key in _WGRAD_STREAMS:
+        torch.cuda.current_stream(key).wait_stream(_WGRAD_STREAMS[key])
+
+
 class _ConvTC(torch.autograd.Function):
     """A 3x3 layer on the tensor cores: forward and data gradient as tcgen05
     implicit GEMMs with BF16 operands and FP32 accumulation, the weight
@@ -205,7 +229,19 @@ class _ConvTC(torch.autograd.Function):
         if gxa is not None or gxb is not None:
             fvn.conv3x3_dgrad_bf16(gy, y, w.detach(), ca, cb, gxa, gxb)
         gw, gb = ctx.gwb
-        fvn.conv3x3_wgrad_bf16(xa, xb, gy, y, gw, gb)
+        # the weight gradient on a side stream (joined before the optimiser
+        # reads the gradients), beside the data gradients of this and the
+        # earlier layers
+        side = _wgrad_stream(gy.device)
+        side.wait_stream(torch.cuda.current_stream(gy.device))
+        with torch.cuda.stream(side):
+            fvn.conv3x3_wgrad_bf16(xa, xb, gy, y, gw, gb)
+        for t in (xa, xb, gy, y):
+            if t is not None:
+                t.record_stream(side)
+        # the backward pass ends with the caller's stream waiting for them
+        dev = gy.device
+        torch.autograd.Variable._execution_engine.queue_callback(lambda: join_wgrad(dev))
         return gxa, gxb, None, None, None, None, None
 
 
