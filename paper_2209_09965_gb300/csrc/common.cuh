@@ -121,6 +121,8 @@ struct WnetState {
     void* d_wpk = nullptr;            // packed FP16 weights of every layer
     float* d_bpk = nullptr;           // padded biases of every layer
     size_t wpk_off[kWnetMaxLayers] = {}, bpk_off[kWnetMaxLayers] = {};   // per layer, in halves / floats
+    // each K decoder level's tap and blend heads packed as one 10-output layer
+    size_t wpk_tb_off[FVN_WNET_MAX_LEVELS] = {}, bpk_tb_off[FVN_WNET_MAX_LEVELS] = {};
     void* tws = nullptr;              // tensor-core workspace
     size_t tws_bytes = 0;
     int tws_w = 0, tws_h = 0;

@@ -455,31 +455,56 @@ bool tc_widths_ok(const fvn_wnet_config& c) {
 // [group][tap][2 chunks][coutp][8], input channel (2 group + chunk) 8 + lane
 // (the concatenated inputs of a layer meet on a chunk boundary: every width
 // is a multiple of 8), zero past cin / cout; biases zero padded to coutp.
-void pack_tc(const WTable& t, const float* host_w, std::vector<__half>& wp, std::vector<float>& bp, size_t* woff,
-             size_t* boff) {
+// One layer's weights (FP32 [cout][cin][k][k], bias [cout]) appended to the
+// packed arrays; returns its offsets (halves, floats).
+void pack_one(const float* w, const float* b, int cin, int cout, int k, std::vector<__half>& wp,
+              std::vector<float>& bp, size_t* woff, size_t* boff) {
+    const int coutp = ks_coutp(cout), chunks = (cin + 7) / 8, groups = (chunks + 1) / 2, taps = k * k;
+    *woff = wp.size();
+    *boff = bp.size();
+    wp.resize(wp.size() + (size_t)groups * taps * 2 * coutp * 8, __float2half(0.f));
+    bp.resize(bp.size() + coutp, 0.f);
+    __half* dst = wp.data() + *woff;
+    for (int g = 0; g < groups; ++g)
+        for (int tp = 0; tp < taps; ++tp)
+            for (int kk = 0; kk < 2; ++kk)
+                for (int co = 0; co < cout; ++co)
+                    for (int j = 0; j < 8; ++j) {
+                        const int ci = (2 * g + kk) * 8 + j;
+                        if (ci < cin)
+                            dst[((((size_t)g * taps + tp) * 2 + kk) * coutp + co) * 8 + j] =
+                                __float2half(w[((size_t)co * cin + ci) * taps + tp]);
+                    }
+    for (int co = 0; co < cout; ++co) bp[*boff + co] = b[co];
+}
+
+// Every layer's weights packed for the K-streamed convolution: FP16
+// [group][tap][2 chunks][coutp][8], input channel (2 group + chunk) 8 + lane
+// (the concatenated inputs of a layer meet on a chunk boundary: every width
+// is a multiple of 8), zero past cin / cout; biases zero padded to coutp.
+// Each K decoder level's tap head (9 outputs) and blend head (1) are also
+// packed together as one 10-output layer.
+void pack_tc(const WTable& t, const fvn_wnet_config& c, const float* host_w, std::vector<__half>& wp,
+             std::vector<float>& bp, WnetState& S) {
     wp.clear();
     bp.clear();
     for (size_t li = 0; li < t.L.size(); ++li) {
         const WLayer& l = t.L[li];
-        const int coutp = ks_coutp(l.cout), chunks = (l.cin + 7) / 8, groups = (chunks + 1) / 2, taps = l.k * l.k;
         const float* w = host_w + l.off;
-        const float* b = w + (size_t)l.cout * l.cin * taps;
-        woff[li] = wp.size();
-        boff[li] = bp.size();
-        wp.resize(wp.size() + (size_t)groups * taps * 2 * coutp * 8, __float2half(0.f));
-        bp.resize(bp.size() + coutp, 0.f);
-        __half* dst = wp.data() + woff[li];
-        for (int g = 0; g < groups; ++g)
-            for (int tp = 0; tp < taps; ++tp)
-                for (int kk = 0; kk < 2; ++kk)
-                    for (int co = 0; co < l.cout; ++co)
-                        for (int j = 0; j < 8; ++j) {
-                            const int ci = (2 * g + kk) * 8 + j;
-                            if (ci < l.cin)
-                                dst[((((size_t)g * taps + tp) * 2 + kk) * coutp + co) * 8 + j] =
-                                    __float2half(w[((size_t)co * l.cin + ci) * taps + tp]);
-                        }
-        for (int co = 0; co < l.cout; ++co) bp[boff[li] + co] = b[co];
+        pack_one(w, w + (size_t)l.cout * l.cin * l.k * l.k, l.cin, l.cout, l.k, wp, bp, &S.wpk_off[li],
+                 &S.bpk_off[li]);
+    }
+    for (int s = 0; s < c.levels; ++s) {
+        const WLayer& lt = t.L[t.k_dec_taps[s]];
+        const WLayer& lb = t.L[t.k_dec_blend[s]];
+        std::vector<float> w((size_t)(kTaps + 1) * lt.cin), b(kTaps + 1);
+        const float* wt = host_w + lt.off;
+        const float* wb = host_w + lb.off;
+        std::copy(wt, wt + (size_t)kTaps * lt.cin, w.begin());
+        std::copy(wb, wb + lb.cin, w.begin() + (size_t)kTaps * lt.cin);
+        std::copy(wt + (size_t)kTaps * lt.cin, wt + (size_t)kTaps * lt.cin + kTaps, b.begin());
+        b[kTaps] = wb[lb.cin];
+        pack_one(w.data(), b.data(), lt.cin, kTaps + 1, 1, wp, bp, &S.wpk_tb_off[s], &S.bpk_tb_off[s]);
     }
 }
 
@@ -521,8 +546,8 @@ size_t plan_wnet_tc(const fvn_wnet_config& c, int Wp, int Hp, TPlan* pl, char* b
         pl->GD[s] = half(c.dec[s], s);
         pl->UPK[s] = half(up, s);
         pl->LE[s] = f32(kTaps, s);
-        pl->LD[s] = f32(kTaps, s);
-        pl->ZD[s] = f32(1, s);
+        pl->LD[s] = f32(kTaps + 1, s);   // the tap logits, then the blend logit (one head launch)
+        pl->ZD[s] = base ? pl->LD[s] + (size_t)kTaps * (Hp >> s) * (Wp >> s) : nullptr;
         pl->I[s] = f32(3, s);
         pl->J[s] = f32(3, s);
         pl->X[s] = f32(3, s);
@@ -587,10 +612,11 @@ fvn_status wnet_forward_tc(fvn_ctx* ctx, const float* rgbam, int w, int h, float
         k.ch1 = xb ? (cb + 7) / 8 : 0;
         k.H = hs(s);
         k.W = ws(s);
-        k.wpk = static_cast<const __half*>(S.d_wpk) + S.wpk_off[li];
-        k.bias = S.d_bpk + S.bpk_off[li];
-        k.cout = t.L[li].cout;
-        k.k = t.L[li].k;
+        // li < 0: the tap + blend heads of K decoder level -1 - li
+        k.wpk = static_cast<const __half*>(S.d_wpk) + (li >= 0 ? S.wpk_off[li] : S.wpk_tb_off[-1 - li]);
+        k.bias = S.d_bpk + (li >= 0 ? S.bpk_off[li] : S.bpk_tb_off[-1 - li]);
+        k.cout = li >= 0 ? t.L[li].cout : kTaps + 1;
+        k.k = li >= 0 ? t.L[li].k : 1;
         k.relu = relu;
         k.out = y;
         k.out32 = y32;
@@ -647,8 +673,7 @@ fvn_status wnet_forward_tc(fvn_ctx* ctx, const float* rgbam, int w, int h, float
     for (int s = L - 1; s >= 0; --s) {
         WK(up(kprev, pc, s, B.UPK[s]));
         WK(conv(B.UPK[s], pc, B.U[s], c.dec[s], s, t.k_dec[s], 1, B.GD[s], nullptr));
-        WK(conv(B.GD[s], c.dec[s], nullptr, 0, s, t.k_dec_taps[s], 0, nullptr, B.LD[s]));
-        WK(conv(B.GD[s], c.dec[s], nullptr, 0, s, t.k_dec_blend[s], 0, nullptr, B.ZD[s]));
+        WK(conv(B.GD[s], c.dec[s], nullptr, 0, s, -1 - s, 0, nullptr, B.LD[s]));   // taps + blend: LD, ZD
         kprev = B.GD[s];
         pc = c.dec[s];
     }
@@ -722,7 +747,7 @@ extern "C" fvn_status fvn_load_wnet_weights(fvn_ctx* ctx, const fvn_wnet_config*
         const WTable t = make_table(*cfg);
         std::vector<__half> wp;
         std::vector<float> bp;
-        pack_tc(t, host_w, wp, bp, S.wpk_off, S.bpk_off);
+        pack_tc(t, *cfg, host_w, wp, bp, S);
         cudaFree(S.d_wpk);
         cudaFree(S.d_bpk);
         S.d_wpk = nullptr;
