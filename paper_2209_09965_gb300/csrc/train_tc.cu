@@ -38,6 +38,7 @@ constexpr int TW = 128;                 // output pixels per tile row = MMA M
 constexpr int HXW = TW + 2;             // halo pixels per row
 constexpr int kThreads = 256;
 constexpr uint32_t kLimit = 1u << 26;
+constexpr size_t kSmemSM = 233472;      // shared memory of an SM (228 KB)
 
 struct Args {
     const float* src0;                  // input channels [0, c0): [N][c0][H][W]
@@ -67,7 +68,15 @@ struct Layout {
     static constexpr size_t halo_r = (halo + 127) / 128 * 128;
     static constexpr size_t w_off = 0;
     static constexpr size_t halo_off = (w_bytes + 1023) / 1024 * 1024;
-    static constexpr int NBUF = halo_off + 2 * halo_r + COUTP * 4 + 64 <= 220 * 1024 ? 2 : 1;
+    // two halo buffers (staging overlaps the MMAs) unless that costs CTAs per
+    // SM (several CTAs also overlap one another's staging; registers cap an
+    // SM at 3 of them)
+    static constexpr size_t bytes1 = halo_off + 1 * halo_r + COUTP * 4 + 16;
+    static constexpr size_t bytes2 = halo_off + 2 * halo_r + COUTP * 4 + 16;
+    static constexpr int ctas1 = (int)(kSmemSM / (bytes1 + 1024)), ctas2 = (int)(kSmemSM / (bytes2 + 1024));
+    static constexpr int NBUF = bytes2 <= 220 * 1024 && ctas2 >= (ctas1 < 3 ? ctas1 : 3) ? 2 : 1;
+    static constexpr int ctas = NBUF == 2 ? ctas2 : ctas1;                 // CTAs one SM holds by shared memory
+    static constexpr int min_blocks = ctas >= 3 ? 3 : ctas >= 2 ? 2 : 1;   // the register budget follows
     static constexpr size_t bias_off = halo_off + NBUF * halo_r;
     static constexpr size_t bar_off = bias_off + COUTP * 4;
     static constexpr size_t bytes = bar_off + 16;
@@ -97,7 +106,8 @@ __device__ __forceinline__ uint4 pack8bf(const float* v) {
 }
 
 template <int CINP, int COUTP, int TR>
-__global__ void __launch_bounds__(kThreads, 2) conv3x3_train_kernel(const __grid_constant__ Args a) {
+__global__ void __launch_bounds__(kThreads, (Layout<CINP, COUTP, TR>::min_blocks))
+    conv3x3_train_kernel(const __grid_constant__ Args a) {
     using L = Layout<CINP, COUTP, TR>;
     constexpr int CH = L::CH, HY = L::HY;
     static_assert(TR % 2 == 0, "the two warp groups of the epilogue split the rows");
