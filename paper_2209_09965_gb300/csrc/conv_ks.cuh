@@ -39,7 +39,7 @@ struct Layout {
     static constexpr uint32_t stage = halo + wgrp;
     static constexpr size_t bias_off = (size_t)NS * stage;
     static constexpr size_t bar_off = bias_off + COUTP * 4;
-    static constexpr int nbar = 2 * NS + 4;                       // full, empty, tfull, tempty
+    static constexpr int nbar = 2 * NS + 5;                       // full, empty, tfull, tempty, drain
     static constexpr size_t bytes = bar_off + nbar * 8 + 16;
     static constexpr uint32_t acc = TR * COUTP;                   // TMEM columns of one accumulator
     static constexpr uint32_t tmem_cols = 2 * acc <= 32 ? 32 : 2 * acc <= 64 ? 64 : 2 * acc <= 128 ? 128
@@ -95,6 +95,7 @@ __global__ void __launch_bounds__(kThreads) conv_ks_kernel(const __grid_constant
             tc::mbar_init(bars + 2 * NS + k, 1);
             tc::mbar_init(bars + 2 * NS + 2 + k, 4);
         }
+        tc::mbar_init(bars + 2 * NS + 4, 1);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 1) {
@@ -174,8 +175,13 @@ __global__ void __launch_bounds__(kThreads) conv_ks_kernel(const __grid_constant
                 if (failed) break;
                 tc::mma_commit(bars + 2 * NS + acc);   // the accumulator is ready for the epilogue
             }
-            // every MMA issued must finish before the TMEM is freed
+            // every MMA issued must finish before the TMEM is freed: on success the last
+            // accumulator's commit covers them, after a give-up one more commit (bounded wait)
             if (t > 0 && !failed) ws::wait(tfull0 + 8 * ((t - 1) & 1), ((t - 1) >> 1) & 1);
+            if (failed && i > 0) {
+                tc::mma_commit(bars + 2 * NS + 4);
+                ws::wait(tc::smem_addr(bars + 2 * NS + 4), 0);
+            }
         }
     } else {
         // ---- epilogue: warps 2-5, one pixel (TMEM lane) per thread
