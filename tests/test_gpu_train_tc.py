@@ -202,3 +202,27 @@ def test_graphed_step_matches_eager_steps(fvn):
     np.testing.assert_allclose(losses_g, losses_e, rtol=2e-3)
     assert np.abs(N(Pg.p) - N(Pe.p)).max() < 2e-3
     assert losses_g[-1] < losses_g[0]
+
+
+def test_new_training_entry_points_reject_bad_arguments(fvn):
+    """The tensor-core weight gradient and the fused head refuse what they
+    cannot compute, before launching anything."""
+    x = torch.zeros(1, 16, 4, 4, device=DEV)
+    gy = torch.zeros(1, 100, 4, 4, device=DEV)
+    gw = torch.zeros(100, 16, 3, 3, device=DEV)
+    gb = torch.zeros(100, device=DEV)
+    with pytest.raises(fvn.FvnError, match="no tensor-core weight gradient"):
+        fvn.conv3x3_wgrad_bf16(x, None, gy, None, gw, gb)
+    wt = torch.zeros(29, 16, 1, 1, device=DEV)
+    b = torch.zeros(29, device=DEV)
+    sp = torch.zeros(1, 5, 4, 4, device=DEV)
+    head = torch.zeros(1, 29, 4, 4, device=DEV)
+    out = torch.zeros(1, 3, 4, 4, device=DEV)
+    empty = torch.zeros(0, 16, 4, 4, device=DEV)
+    with pytest.raises(fvn.FvnError, match="null tensor|bad sizes"):   # an empty tensor has no storage
+        fvn.head_kp_fwd(empty, wt, b, sp, head, out)
+    step = torch.zeros(1, dtype=torch.int32, device=DEV)
+    p = torch.zeros(8, device=DEV)
+    with pytest.raises(TypeError):
+        fvn.adam_step_dev(p, p, p, p, step.float())   # the step count is an int32 tensor
+    fvn.train_device_status()

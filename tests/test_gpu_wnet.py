@@ -288,3 +288,12 @@ def test_tensor_cores_reject_unsupported_widths(fvn):
             c.reconstruct_wnet(torch.zeros(5, 8, 8, device=DEV), 8, 8, rgb)
     finally:
         c.close()
+
+
+def test_tensor_core_option_is_checked(fvn):
+    c = fvn.Context()
+    try:
+        with pytest.raises(fvn.FvnError, match="two-stage tensor-core option"):
+            c.set_option(fvn.OPT_WNET_TENSOR_CORES, 2)
+    finally:
+        c.close()
