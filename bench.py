@@ -1304,6 +1304,8 @@ def main():
     mask_avg_s = stage_live["mask"] / 1000.0
     net_tflops = NET_FLOPS_PER_PX * W * H / recon_avg_s / 1e12
     mask_gbs = (W * H + 4 * nrays / nq) / mask_avg_s / 1e9
+    prep_bytes = VOL_N ** 3 * 4 + (VOL_N + 4) ** 3 * 16
+    prep_gbs = prep_bytes / (stage_live["volume_prep"] / 1000.0) / 1e9 if stage_live["volume_prep"] > 0 else 0.0
 
     # ---- the same frames with the FP8 network (scales from frame 0) ----------
     fp8_info = None
@@ -1442,7 +1444,12 @@ def main():
                                 "frac": net_tflops / tc_peak, "flops_per_px": NET_FLOPS_PER_PX,
                                 "peak_kind": "measured bf16 burst (same dense rate as fp16)"},
                 "mask": {"bound": "hbm", "achieved": mask_gbs, "peak": hbm_peak, "unit": "GB/s",
-                         "frac": mask_gbs / hbm_peak, "note": "1 B mask + 4 B per id; launch-latency dominated"}},
+                         "frac": mask_gbs / hbm_peak, "note": "1 B mask + 4 B per id; launch-latency dominated"},
+                "volume_prep": {"bound": "hbm", "achieved": prep_gbs, "peak": hbm_peak, "unit": "GB/s",
+                                "frac": prep_gbs / hbm_peak, "bytes": prep_bytes,
+                                "note": "the gradient volume (v, Dx, Dy, Dz) of the padded box written once per "
+                                        "frame from the float32 volume: n^3 x 4 B read + (n + 4)^3 x 16 B written; "
+                                        "duration from the stage events inside the timed frames"}},
             "autotune": tuned,
             "e2e": {"value": e2e_val, "unit": "frames/s", "h2d_bytes_per_step": int(tf_np.nbytes),
                     "d2h_bytes_per_step": int(3 * H * W * 4)},
