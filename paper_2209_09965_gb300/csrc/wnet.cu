@@ -420,27 +420,44 @@ __global__ void cp_pool2_kernel(const uint4* __restrict__ in, int H, int W, uint
 }
 
 // bilinear x2 up-sampling of every chunk plane (half-pixel centres, edge
-// clamp): h x w -> 2h x 2w; blockIdx.y = chunk
+// clamp): h x w -> 2h x 2w; blockIdx.y = chunk.  A thread takes fine rows
+// 2m and 2m + 1 of one column: from m = 1 on they share their middle
+// coarse row, whose x interpolation is done once (the arithmetic of each
+// output is that of a single bilinear sample).
 __global__ void cp_up2_kernel(const uint4* __restrict__ in, int h, int w, uint4* __restrict__ out) {
-    const int H2 = 2 * h, W2 = 2 * w, r = blockIdx.x * blockDim.x + threadIdx.x;
-    if (r >= H2 * W2) return;
-    const int oy = r / W2, ox = r - oy * W2;
-    int y0, y1, x0, x1;
-    float ty, tx;
-    up_src(oy, h, y0, y1, ty);
+    const int W2 = 2 * w, r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= h * W2) return;
+    const int m = r / W2, ox = r - m * W2;
+    int x0, x1, y0e, y1e, y0o, y1o;
+    float tx, tye, tyo;
     up_src(ox, w, x0, x1, tx);
+    up_src(2 * m, h, y0e, y1e, tye);
+    up_src(2 * m + 1, h, y0o, y1o, tyo);
     const uint4* p = in + (long long)blockIdx.y * h * w;
-    float f00[8], f01[8], f10[8], f11[8], o[8];
-    h8_to_f(__ldg(p + y0 * w + x0), f00);
-    h8_to_f(__ldg(p + y0 * w + x1), f01);
-    h8_to_f(__ldg(p + y1 * w + x0), f10);
-    h8_to_f(__ldg(p + y1 * w + x1), f11);
+    auto xlerp = [&](int y, float* o) {   // x interpolation of coarse row y
+        float a[8], b[8];
+        h8_to_f(__ldg(p + y * w + x0), a);
+        h8_to_f(__ldg(p + y * w + x1), b);
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        const float top = (1.f - tx) * f00[j] + tx * f01[j], bot = (1.f - tx) * f10[j] + tx * f11[j];
-        o[j] = (1.f - ty) * top + ty * bot;
+        for (int j = 0; j < 8; ++j) o[j] = (1.f - tx) * a[j] + tx * b[j];
+    };
+    float te[8], be[8], to[8], bo[8], o[8];
+    xlerp(y0e, te);
+    xlerp(y1e, be);
+    if (y0o == y1e) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) to[j] = be[j];
+    } else {
+        xlerp(y0o, to);
     }
-    out[(long long)blockIdx.y * H2 * W2 + r] = f_to_h8(o);
+    xlerp(y1o, bo);
+    uint4* q = out + (long long)blockIdx.y * (2 * h) * W2 + (long long)(2 * m) * W2 + ox;
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o[j] = (1.f - tye) * te[j] + tye * be[j];
+    q[0] = f_to_h8(o);
+#pragma unroll
+    for (int j = 0; j < 8; ++j) o[j] = (1.f - tyo) * to[j] + tyo * bo[j];
+    q[W2] = f_to_h8(o);
 }
 
 bool tc_widths_ok(const fvn_wnet_config& c) {
@@ -627,7 +644,7 @@ fvn_status wnet_forward_tc(fvn_ctx* ctx, const float* rgbam, int w, int h, float
         return cudaGetLastError() == cudaSuccess ? FVN_OK : set_error(ctx, FVN_ERR_CUDA, "pooling launch failed");
     };
     auto up = [&](const uint4* x, int ch, int s, uint4* y) {     // level s + 1 -> s
-        cp_up2_kernel<<<cp_grid((long long)hs(s) * ws(s), (ch + 7) / 8), 256, 0, st>>>(x, hs(s + 1), ws(s + 1), y);
+        cp_up2_kernel<<<cp_grid((long long)hs(s + 1) * ws(s), (ch + 7) / 8), 256, 0, st>>>(x, hs(s + 1), ws(s + 1), y);
         return cudaGetLastError() == cudaSuccess ? FVN_OK : set_error(ctx, FVN_ERR_CUDA, "up-sampling launch failed");
     };
 
