@@ -821,7 +821,7 @@ static fvn_status launch_ws_headkp(fvn_ctx* ctx, const ReconView* views, int n, 
 }
 
 // Bilinear x2 up-sampling of the coarse level of every view (one launch, one
-// block per fine row of one chunk plane of one view).
+// block per pair of fine rows of one chunk plane of one view).
 struct UpArgs {
     int n, chunks;
     struct {
@@ -838,9 +838,10 @@ __global__ void __launch_bounds__(256) upsample2_views_kernel(const __grid_const
     tc::grid_dep_launch();
     int i = 0;
     while (i + 1 < u.n && (int)blockIdx.x >= u.im[i + 1].row0) ++i;
-    const int r = blockIdx.x - u.im[i].row0;        // chunk * Hl + row
-    const int c = r / u.im[i].Hl, gy = r - c * u.im[i].Hl;
-    ws::upsample2_row<F8>(u.im[i].coarse, u.im[i].fine, u.im[i].Hl, u.im[i].Wl, c, gy);
+    const int hp = u.im[i].Hl >> 1;                 // fine row pairs per chunk plane
+    const int r = blockIdx.x - u.im[i].row0;        // chunk * hp + pair
+    const int c = r / hp, my = r - c * hp;
+    ws::upsample2_rowpair<F8>(u.im[i].coarse, u.im[i].fine, u.im[i].Hl, u.im[i].Wl, c, my);
 }
 
 template <bool F8>
@@ -856,7 +857,7 @@ static fvn_status upsample_views(fvn_ctx* ctx, const void* const* coarse, void* 
         u.im[i].Hl = Hl[i];
         u.im[i].Wl = Wl[i];
         u.im[i].row0 = (int)rows;
-        rows += (long long)u.chunks * Hl[i];
+        rows += (long long)u.chunks * (Hl[i] >> 1);   // one block per pair of fine rows (Hl is even)
     }
     if (rows >= (1ll << 31)) return set_error(ctx, FVN_ERR_ARG, "up-sampling grid too large");
     if (rows > 0) {

@@ -862,45 +862,67 @@ __global__ void __launch_bounds__(kHkThreads, 1) conv3x3_ws_headkp_kernel(const 
     }
 }
 
-// Bilinear x2 up-sampling of one row of one chunk plane of a chunk-planar
-// tensor (half-pixel centres, edge clamp), the block's threads striding over
-// its pixels: the same interpolation the up-sampling layers of
+// Bilinear x2 up-sampling of fine rows 2 my and 2 my + 1 of one chunk plane
+// of a chunk-planar tensor (half-pixel centres, edge clamp; Hl even), the
+// block's threads striding over the columns: the two rows share a coarse
+// row (the middle one from my = 1 on), interpolated along x once; each
+// output is the same arithmetic as the up-sampling layers of
 // conv3x3_tc_kernel apply while staging.
 template <bool F8>
-__device__ __forceinline__ void upsample2_row(const void* __restrict__ coarse, void* __restrict__ fine, int Hl,
-                                              int Wl, int c, int gy) {
+__device__ __forceinline__ void upsample2_rowpair(const void* __restrict__ coarse, void* __restrict__ fine, int Hl,
+                                                  int Wl, int c, int my) {
     const int Hc = Hl >> 1, Wc = Wl >> 1;
-    const int my = gy >> 1;
-    const int iy0 = (gy & 1) ? my : max(my - 1, 0), iy1 = min(iy0 + 1, Hc - 1);
-    const float fy = (gy & 1) ? 0.25f : (my > 0 ? 0.75f : 0.0f);
-    const uint4* r0 = static_cast<const uint4*>(coarse) + ((long long)c * Hc + iy0) * Wc;
-    const uint4* r1 = static_cast<const uint4*>(coarse) + ((long long)c * Hc + iy1) * Wc;
-    uint4* out = static_cast<uint4*>(fine) + ((long long)c * Hl + gy) * Wl;
+    // fine row 2 my: coarse rows a, b with weight fe on b; fine row 2 my + 1: rows my, d with weight 1/4 on d
+    const int ra = max(my - 1, 0), rb = min(ra + 1, Hc - 1), rd = min(my + 1, Hc - 1);
+    const float fe = my > 0 ? 0.75f : 0.0f, fo = 0.25f;
+    const uint4* base = static_cast<const uint4*>(coarse) + (long long)c * Hc * Wc;
+    const uint4 *r0 = base + (long long)ra * Wc, *r1 = base + (long long)rb * Wc, *r2 = base + (long long)my * Wc,
+                *r3 = base + (long long)rd * Wc;
+    const bool c_is_b = my == rb, c_is_a = my == ra, d_is_b = rd == rb;
+    uint4* out0 = static_cast<uint4*>(fine) + ((long long)c * Hl + 2 * my) * Wl;
+    uint4* out1 = out0 + Wl;
     constexpr int CPC = F8 ? 16 : 8;
+    auto xlerp = [&](const uint4* row, int ix0, int ix1, float fx, float* o) {
+        float p0[16], p1[16];
+        const uint4 u0 = __ldg(row + ix0), u1 = __ldg(row + ix1);
+        if (F8) {
+            unpack16q(u0, p0);
+            unpack16q(u1, p1);
+        } else {
+            unpack8h(u0, p0);
+            unpack8h(u1, p1);
+        }
+#pragma unroll
+        for (int j = 0; j < CPC; ++j) o[j] = fmaf(fx, p1[j] - p0[j], p0[j]);
+    };
     for (int gx = threadIdx.x; gx < Wl; gx += blockDim.x) {
         const int mx = gx >> 1;
         const int ix0 = (gx & 1) ? mx : max(mx - 1, 0), ix1 = min(ix0 + 1, Wc - 1);
         const float fx = (gx & 1) ? 0.25f : (mx > 0 ? 0.75f : 0.0f);
-        const uint4 u00 = __ldg(r0 + ix0), u01 = __ldg(r0 + ix1), u10 = __ldg(r1 + ix0), u11 = __ldg(r1 + ix1);
-        float p00[16], p01[16], p10[16], p11[16], v[16];
-        if (F8) {
-            unpack16q(u00, p00);
-            unpack16q(u01, p01);
-            unpack16q(u10, p10);
-            unpack16q(u11, p11);
+        float ta[16], tb[16], tc_[16], td[16], v[16];
+        xlerp(r0, ix0, ix1, fx, ta);
+        xlerp(r1, ix0, ix1, fx, tb);
+        if (c_is_b) {
+#pragma unroll
+            for (int j = 0; j < CPC; ++j) tc_[j] = tb[j];
+        } else if (c_is_a) {
+#pragma unroll
+            for (int j = 0; j < CPC; ++j) tc_[j] = ta[j];
         } else {
-            unpack8h(u00, p00);
-            unpack8h(u01, p01);
-            unpack8h(u10, p10);
-            unpack8h(u11, p11);
+            xlerp(r2, ix0, ix1, fx, tc_);
+        }
+        if (d_is_b) {
+#pragma unroll
+            for (int j = 0; j < CPC; ++j) td[j] = tb[j];
+        } else {
+            xlerp(r3, ix0, ix1, fx, td);
         }
 #pragma unroll
-        for (int j = 0; j < CPC; ++j) {
-            const float top = fmaf(fx, p01[j] - p00[j], p00[j]);
-            const float bot = fmaf(fx, p11[j] - p10[j], p10[j]);
-            v[j] = fmaf(fy, bot - top, top);
-        }
-        out[gx] = F8 ? pack16q(v) : pack8h(v);
+        for (int j = 0; j < CPC; ++j) v[j] = fmaf(fe, tb[j] - ta[j], ta[j]);
+        out0[gx] = F8 ? pack16q(v) : pack8h(v);
+#pragma unroll
+        for (int j = 0; j < CPC; ++j) v[j] = fmaf(fo, td[j] - tc_[j], tc_[j]);
+        out1[gx] = F8 ? pack16q(v) : pack8h(v);
     }
 }
 
