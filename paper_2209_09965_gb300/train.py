@@ -229,9 +229,14 @@ class _ConvTC(torch.autograd.Function):
         if gxa is not None or gxb is not None:
             fvn.conv3x3_dgrad_bf16(gy, y, w.detach(), ca, cb, gxa, gxb)
         gw, gb = ctx.gwb
-        # the weight gradient on a side stream (joined before the optimiser
-        # reads the gradients), beside the data gradients of this and the
-        # earlier layers
+        if not torch.cuda.is_current_stream_capturing():
+            # eager: the host issues every launch, and the side stream's
+            # bookkeeping would cost more host time than its overlap saves
+            fvn.conv3x3_wgrad_bf16(xa, xb, gy, y, gw, gb)
+            return gxa, gxb, None, None, None, None, None
+        # captured in a CUDA graph: the weight gradient on a side stream (joined
+        # before the optimiser reads the gradients), beside the data gradients
+        # of this and the earlier layers
         side = _wgrad_stream(gy.device)
         side.wait_stream(torch.cuda.current_stream(gy.device))
         with torch.cuda.stream(side):
