@@ -1,7 +1,7 @@
 // Tensor-core convolutions of the training step (paper: "Training" and
 // "Model Precision & Optimization": the network is trained with FP32 master
-// weights; here its 3x3 layers' forward pass and data gradient run as
-// implicit GEMMs on the 5th-generation tensor cores).
+// weights; here its 3x3 layers' forward pass, data gradient and weight
+// gradient run as GEMMs on the 5th-generation tensor cores).
 //
 // The training pass keeps FP32 NCHW tensors ([N][C][H][W]).  A CTA stages a
 // tile's input halo (TR + 2 rows x 130 pixels) into shared memory as BF16
@@ -18,7 +18,10 @@
 // is the output gradient times the layer's ReLU mask (saved output > 0),
 // applied while staging.  Epilogue: bias and ReLU (forward), FP32 stores of
 // one pixel per thread, channel by channel (coalesced along x); the data
-// gradient's channels go to the two tensors of a concatenated input.
+// gradient's channels go to the two tensors of a concatenated input.  The
+// CTAs are persistent, as many per SM as registers and shared memory allow;
+// an instance double-buffers its halo (staging the next tile while the MMAs
+// run) only where that costs no CTAs per SM.
 //
 // The weight gradient is a GEMM over the pixels (see conv3x3_wgrad_kernel).
 //
