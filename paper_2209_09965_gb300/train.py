@@ -1,7 +1,11 @@
 """Training of the reconstruction network on self-rendered pairs.
 
-The network is trained in FP32 (paper: "Model Precision & Optimization":
-train in full precision, run with the weights truncated to 16 bit) on pairs
+The network keeps FP32 master weights, gradients and Adam state (paper:
+"Model Precision & Optimization": train in full precision, run with the
+weights truncated to 16 bit); its 3x3 layers' forward, data and weight
+gradients run on the tensor cores with BF16 operands and FP32 accumulation
+(``--fp32``: every layer on the FP32 kernels, as the shipped weights were
+trained).  It is trained on pairs
 (sparse input, dense target) rendered by this library's own ray marcher
 from seeded procedural volumes (the paper trains on renders of its CT and
 simulation datasets, "Dataset" / "Training" sections).  Loss: L1 plus L1 of
@@ -33,19 +37,19 @@ rendered frame) uses plain tensor indexing.
 
 The shipped weights were made with
 
-    python -m paper_2209_09965_gb300.train --steps 30000 --lr-final 1e-5 --log-every 1000 \
+    python -m paper_2209_09965_gb300.train --fp32 --steps 30000 --lr-final 1e-5 --log-every 1000 \
         --out paper_2209_09965_gb300/weights/fvn_16_32_64.npy
-    python -m paper_2209_09965_gb300.train --steps 8000 --direct-only \
+    python -m paper_2209_09965_gb300.train --fp32 --steps 8000 --direct-only \
         --out paper_2209_09965_gb300/weights/fvn_direct_only.npy
-    python -m paper_2209_09965_gb300.train --recurrent --steps 6000 --lr 3e-4 --lr-final 1e-5 \
+    python -m paper_2209_09965_gb300.train --fp32 --recurrent --steps 6000 --lr 3e-4 --lr-final 1e-5 \
         --init paper_2209_09965_gb300/weights/fvn_16_32_64.npy --log-every 500 \
         --out paper_2209_09965_gb300/weights/fvn_16_32_64_recurrent.npy
 
 and the equal-budget ablation of the reconstruction with
 
-    python -m paper_2209_09965_gb300.train --steps 4000 --direct-only \
+    python -m paper_2209_09965_gb300.train --fp32 --steps 4000 --direct-only \
         --out paper_2209_09965_gb300/weights/fvn_direct_only_4k.npy
-    python -m paper_2209_09965_gb300.train --steps 4000 --out paper_2209_09965_gb300/weights/fvn_16_32_64_4k.npy
+    python -m paper_2209_09965_gb300.train --fp32 --steps 4000 --out paper_2209_09965_gb300/weights/fvn_16_32_64_4k.npy
     python -m paper_2209_09965_gb300.train --steps 4000 --wnet slim \
         --out paper_2209_09965_gb300/weights/fvn_wnet_slim_4k.npy
     python -m paper_2209_09965_gb300.train --steps 4000 --wnet paper \
@@ -540,8 +544,9 @@ LAMBDA_S, LAMBDA_T = 0.8, 1.0   # Eq. 4 weights of the spatial and temporal term
 
 def train(steps=3000, batch=8, lr=1e-3, seed=100, nvol=64, vol_n=512, out=None, direct_only=False,
           init_seed=3, log_every=100, device=None, lr_final=1e-4, recurrent=False, init=None, max_angle_deg=6.0,
-          wnet=None):
-    """wnet: widths (enc, bot, dec) to train the two-stage network instead."""
+          wnet=None, tc=True):
+    """wnet: widths (enc, bot, dec) to train the two-stage network instead;
+    tc: the single network's 3x3 layers on the tensor cores (False: FP32)."""
     device = device or torch.device("cuda")
     ctx = fvn.Context()
     src = PairSource(ctx, device, nvol=nvol, vol_n=vol_n, seed=seed)
@@ -564,13 +569,13 @@ def train(steps=3000, batch=8, lr=1e-3, seed=100, nvol=64, vol_n=512, out=None, 
         if recurrent:
             x, y = src.sample_sequence(batch, max_angle_deg)
             with torch.no_grad():
-                o0 = forward(P, x[0])
-            o1 = forward(P, x[1], prev=o0)
+                o0 = forward(P, x[0], tc=tc)
+            o1 = forward(P, x[1], prev=o0, tc=tc)
             loss = LAMBDA_S * _Loss.apply(o1, y[1], 1.0) + \
                 LAMBDA_T * _Loss.apply(o1 - o0, (y[1] - y[0]).contiguous(), 0.0)
         else:
             x, y = src.sample(batch)
-            pred = wnet_forward(P, x, wnet) if wnet is not None else forward(P, x, direct_only)
+            pred = wnet_forward(P, x, wnet) if wnet is not None else forward(P, x, direct_only, tc=tc)
             loss = _Loss.apply(pred, y, 1.0)
         loss.backward()
         # cosine decay from lr to lr_final over the run
@@ -605,10 +610,13 @@ def main():
     ap.add_argument("--wnet", choices=("slim", "paper"), default=None,
                     help="train the two-stage network with the single network's widths or the paper's")
     ap.add_argument("--out", default=None)
+    ap.add_argument("--fp32", action="store_true",
+                    help="every layer on the FP32 kernels (the shipped weights were trained so)")
     a = ap.parse_args()
     cfg = {"slim": wl.WNET_SLIM, "paper": wl.WNET_PAPER}.get(a.wnet)
     train(a.steps, a.batch, a.lr, a.seed, a.nvol, a.vol_n, a.out, a.direct_only, log_every=a.log_every,
-          lr_final=a.lr_final, recurrent=a.recurrent, init=a.init, max_angle_deg=a.max_angle, wnet=cfg)
+          lr_final=a.lr_final, recurrent=a.recurrent, init=a.init, max_angle_deg=a.max_angle, wnet=cfg,
+          tc=not a.fp32)
 
 
 if __name__ == "__main__":
