@@ -718,13 +718,17 @@ __global__ void __launch_bounds__(kHkThreads, 1) conv3x3_ws_headkp_kernel(const 
             int i = 0;
             for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++i) {
                 const int s = i % NS, acc = i & 1;
-                if (!wait(full0 + 8 * s, (i / NS) & 1) || (i >= 2 && !wait(tempty0 + 8 * acc, ((i >> 1) - 1) & 1))) {
+                // the previous tile's head first, before this tile waits for its
+                // accumulator: that wait ends only when the other group has
+                // finished its kernel prediction of tile i - 2, and the head
+                // issued behind it would serialise the two groups' kernel
+                // predictions (the slow part of the epilogue) instead of
+                // overlapping them with each other and with this tile's conv
+                if (i >= 1 && !head(i - 1)) {
                     failed = true;
                     break;
                 }
-                // the previous tile's head first: its kernel prediction (the
-                // slow part of the epilogue) then overlaps this tile's conv
-                if (i >= 1 && !head(i - 1)) {
+                if (!wait(full0 + 8 * s, (i / NS) & 1) || (i >= 2 && !wait(tempty0 + 8 * acc, ((i >> 1) - 1) & 1))) {
                     failed = true;
                     break;
                 }
