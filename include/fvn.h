@@ -166,6 +166,11 @@ fvn_status fvn_destroy(fvn_ctx* ctx);
  *      on the tensor cores (FP16 operands and activations, FP32
  *      accumulation; needs every width a multiple of 8 and at most 128,
  *      else FVN_ERR_UNSUPPORTED); 0 (default) = FP32 kernels throughout.
+ *  FVN_OPT_WNET_FUSED_UPSAMPLING: 1 (default) = on the tensor cores, the
+ *      first convolution of each decoder level computes the bilinear x2
+ *      up-sampling of its coarse input itself (when that input's channels
+ *      fill whole 16-channel groups); 0 = a separate up-sampling pass writes
+ *      the fine copy it reads.  The same bits either way.
  * A shadowed march (shading 2) first writes, besides the padded copy, a cell
  * volume -- per padded voxel the 2 x 2 block of voxels (x..x+1, y..y+1) in
  * the voxel type -- so that a shadow sample reads two cells instead of
@@ -184,7 +189,8 @@ enum {
     FVN_OPT_CONV_ROWS_QUARTER = 12,
     FVN_OPT_CONV_ROWS_DEC1 = 13,
     FVN_OPT_CONV_FUSE_UP_DEC1 = 14,
-    FVN_OPT_WNET_TENSOR_CORES = 15
+    FVN_OPT_WNET_TENSOR_CORES = 15,
+    FVN_OPT_WNET_FUSED_UPSAMPLING = 16
 };
 fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value);
 

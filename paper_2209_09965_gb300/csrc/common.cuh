@@ -117,6 +117,7 @@ struct WnetState {
     // tensor-core path (FVN_OPT_WNET_TENSOR_CORES): the layers' weights packed
     // for the K-streamed convolution (FP16) and their zero-padded biases
     int tc = 0;                       // the option
+    int fuse_up = 1;                  // decoder up-sampling inside the convolutions (tensor-core path)
     bool tc_ok = false;               // the widths allow the tensor-core path
     void* d_wpk = nullptr;            // packed FP16 weights of every layer
     float* d_bpk = nullptr;           // padded biases of every layer
@@ -228,7 +229,9 @@ inline cudaError_t opt_in_smem(const fvn_ctx* ctx, K kern, int bytes, std::atomi
 // chunks followed by source 1's ch1; wpk holds the weights packed as
 // [ceil((ch0 + ch1) / 2)][k * k][2][ks_coutp(cout)][8] FP16 and bias
 // ks_coutp(cout) floats (zero padded).  Writes ceil(cout / 8) chunks of out
-// and / or cout FP32 planes of out32.
+// and / or cout FP32 planes of out32.  up = 1: source 0 is a coarse tensor of
+// H / 2 x W / 2 pixels whose bilinear x2 up-sampling the kernel computes
+// (H, W and ch0 even).
 struct KsConv {
     const void* in0;
     int ch0;
@@ -240,6 +243,7 @@ struct KsConv {
     int cout, k, relu;
     void* out;
     float* out32;
+    int up;
 };
 int ks_coutp(int cout);
 fvn_status ks_conv(fvn_ctx* ctx, const KsConv& c, cudaStream_t st);

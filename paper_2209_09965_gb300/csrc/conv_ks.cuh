@@ -15,10 +15,22 @@
 //   warp 1     MMA issuer: per stage TAPS x TR MMAs (M = 128, N = COUTP,
 //              K = 16) into one of two TMEM accumulators;
 //   warps 2-5  epilogue: one pixel per thread, bias, ReLU, FP16 chunk stores
-//              and / or FP32 planar stores (the small heads).
+//              and / or FP32 planar stores (the small heads);
+//   warps 6-13 (UP only) up-sampling, below.
+// UP (decoder layers): the first ch0 chunks of the input are the bilinear x2
+// up-sampling of source 0, a coarse tensor of half the height and width,
+// computed in the kernel: for those groups the producer loads the coarse
+// block under the tile (TR / 2 + 2 rows x 66 pixels per chunk) instead of the
+// fine halo, and the up-sampling warps interpolate it into the stage's two
+// halo planes (zero outside the frame) before the MMA warp, which waits on a
+// per-stage "ready" barrier, reads them.  The interpolation is that of the
+// separate up-sampling pass, operation for operation, so the results are
+// the same bits.
 // Every mbarrier wait has an iteration limit; a wait that gives up sets the
 // error flag and the roles leave their loops.
 #pragma once
+
+#include "resample.cuh"
 
 namespace fvn {
 namespace ks {
@@ -26,7 +38,7 @@ namespace ks {
 constexpr int kThreads = 192;
 constexpr int kHXW = 128;   // halo pixels per row (one TMA box row per chunk)
 
-template <int COUTP, int TR, int NS, bool K1>
+template <int COUTP, int TR, int NS, bool K1, bool UP = false>
 struct Layout {
     static constexpr int HY = K1 ? TR : TR + 2;
     static constexpr int TO = K1 ? kHXW : kHXW - 2;              // output pixels per tile row
@@ -36,11 +48,19 @@ struct Layout {
     static constexpr uint32_t plane = (HY * kHXW * 16 + 32 + 127) / 128 * 128;
     static constexpr uint32_t halo = 2 * plane;
     static constexpr uint32_t wgrp = TAPS * 2 * COUTP * 16;      // one group's weights
-    static constexpr uint32_t stage = halo + wgrp;
+    // UP: coarse rows / columns under the HY x 128 fine pixels of a tile
+    // (fine halo rows / columns start even - 1 for 3x3 and even for 1x1)
+    static constexpr int CR = TR / 2 + 2, CC = kHXW / 2 + 2;
+    static constexpr uint32_t cplane = (CR * CC * 16 + 127) / 128 * 128;
+    static constexpr uint32_t coarse = UP ? 2 * cplane : 0;
+    static constexpr uint32_t stage = halo + wgrp + coarse;
     static constexpr size_t bias_off = (size_t)NS * stage;
     static constexpr size_t bar_off = bias_off + COUTP * 4;
-    static constexpr int nbar = 2 * NS + 5;                       // full, empty, tfull, tempty, drain
+    static constexpr int nbar = 2 * NS + 5 + (UP ? NS : 0);      // full, empty, tfull, tempty, drain, ready
     static constexpr size_t bytes = bar_off + nbar * 8 + 16;
+    static constexpr int up_warps = 8;
+    static constexpr int threads = kThreads + (UP ? 32 * up_warps : 0);
+    static_assert(!UP || TR % 2 == 0, "up-sampled tiles start on an even fine row");
     static constexpr uint32_t acc = TR * COUTP;                   // TMEM columns of one accumulator
     static constexpr uint32_t tmem_cols = 2 * acc <= 32 ? 32 : 2 * acc <= 64 ? 64 : 2 * acc <= 128 ? 128
                                         : 2 * acc <= 256 ? 256 : 512;
@@ -61,6 +81,7 @@ struct Args {
     float* out32;                     // FP32 planar output [cout][H][W] (NULL: none)
     int cout, relu;
     int H, W, tiles_x, ntiles;
+    int Hc, Wc;                       // UP: size of the coarse source 0
     int* error;
 };
 
@@ -70,9 +91,10 @@ __device__ __forceinline__ void bulk_load(uint32_t dst, const void* src, uint32_
                  : "memory");
 }
 
-template <int COUTP, int TR, int NS, bool K1>
-__global__ void __launch_bounds__(kThreads) conv_ks_kernel(const __grid_constant__ Args a) {
-    using L = Layout<COUTP, TR, NS, K1>;
+template <int COUTP, int TR, int NS, bool K1, bool UP>
+__global__ void __launch_bounds__(Layout<COUTP, TR, NS, K1, UP>::threads)
+    conv_ks_kernel(const __grid_constant__ Args a) {
+    using L = Layout<COUTP, TR, NS, K1, UP>;
     constexpr int HY = L::HY, TO = L::TO;
     extern __shared__ __align__(1024) unsigned char smem[];
     float* sBias = reinterpret_cast<float*>(smem + L::bias_off);
@@ -80,11 +102,12 @@ __global__ void __launch_bounds__(kThreads) conv_ks_kernel(const __grid_constant
     uint32_t* tslot = reinterpret_cast<uint32_t*>(bars + L::nbar);
     const uint32_t full0 = tc::smem_addr(bars), empty0 = full0 + 8 * NS;
     const uint32_t tfull0 = full0 + 16 * NS, tempty0 = tfull0 + 16;
+    const uint32_t ready0 = tempty0 + 16 + 8;   // UP: after the drain barrier
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     {   // the ring zeroed once (the over-read slack of the halo planes stays zero), bias
         uint4* z = reinterpret_cast<uint4*>(smem);
-        for (int i = tid; i < (int)(L::bias_off / 16); i += kThreads) z[i] = make_uint4(0, 0, 0, 0);
-        for (int i = tid; i < COUTP; i += kThreads) sBias[i] = __ldg(a.bias + i);
+        for (int i = tid; i < (int)(L::bias_off / 16); i += L::threads) z[i] = make_uint4(0, 0, 0, 0);
+        for (int i = tid; i < COUTP; i += L::threads) sBias[i] = __ldg(a.bias + i);
     }
     if (tid == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -96,6 +119,8 @@ __global__ void __launch_bounds__(kThreads) conv_ks_kernel(const __grid_constant
             tc::mbar_init(bars + 2 * NS + 2 + k, 4);
         }
         tc::mbar_init(bars + 2 * NS + 4, 1);
+        if (UP)
+            for (int s = 0; s < NS; ++s) tc::mbar_init(bars + 2 * NS + 5 + s, L::up_warps);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 1) {
@@ -116,6 +141,7 @@ __global__ void __launch_bounds__(kThreads) conv_ks_kernel(const __grid_constant
             for (int tile = blockIdx.x; tile < a.ntiles && !failed; tile += gridDim.x) {
                 const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
                 const int x0 = tx * TO - (K1 ? 0 : 1), y0 = ty * TR - (K1 ? 0 : 1);
+                const int cx0 = ((x0 + 1) >> 1) - 1, cy0 = ((y0 + 1) >> 1) - 1;   // UP: coarse block origin
                 for (int g = 0; g < a.groups; ++g, ++i) {
                     const int s = i % NS, k = i / NS;
                     if (k > 0 && !ws::wait(empty0 + 8 * s, (k - 1) & 1)) {
@@ -124,13 +150,21 @@ __global__ void __launch_bounds__(kThreads) conv_ks_kernel(const __grid_constant
                     }
                     const uint32_t full = full0 + 8 * s;
                     const uint32_t dst = tc::smem_addr(smem + (size_t)s * L::stage);
-                    ws::mbar_expect_tx(full, 2u * HY * kHXW * 16 + L::wgrp);
+                    if (UP && 2 * g < a.ch0) {   // the coarse block of an up-sampled group
+                        ws::mbar_expect_tx(full, 2u * L::CR * L::CC * 16 + L::wgrp);
 #pragma unroll
-                    for (int kk = 0; kk < 2; ++kk) {
-                        const int c = 2 * g + kk;   // past the last chunk: out of the map's range, zero-filled
-                        const bool first = c < a.ch0 || !a.has1;
-                        ws::tma_load_3d(dst + kk * L::plane, first ? &a.map0 : &a.map1, 2 * x0, y0,
-                                        first ? c : c - a.ch0, full);
+                        for (int kk = 0; kk < 2; ++kk)
+                            ws::tma_load_3d(dst + L::halo + L::wgrp + kk * L::cplane, &a.map0, 2 * cx0, cy0,
+                                            2 * g + kk, full);
+                    } else {
+                        ws::mbar_expect_tx(full, 2u * HY * kHXW * 16 + L::wgrp);
+#pragma unroll
+                        for (int kk = 0; kk < 2; ++kk) {
+                            const int c = 2 * g + kk;   // past the last chunk: out of the map's range, zero-filled
+                            const bool first = !UP && (c < a.ch0 || !a.has1);
+                            ws::tma_load_3d(dst + kk * L::plane, first ? &a.map0 : &a.map1, 2 * x0, y0,
+                                            first ? c : c - a.ch0, full);
+                        }
                     }
                     bulk_load(dst + L::halo, a.w + (size_t)g * (L::wgrp / 16), L::wgrp, full);
                 }
@@ -151,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) conv_ks_kernel(const __grid_constant
                 }
                 for (int g = 0; g < a.groups; ++g, ++i) {
                     const int s = i % NS;
-                    if (!ws::wait(full0 + 8 * s, (i / NS) & 1)) {
+                    if (!ws::wait(full0 + 8 * s, (i / NS) & 1) || (UP && !ws::wait(ready0 + 8 * s, (i / NS) & 1))) {
                         failed = true;
                         break;
                     }
@@ -183,7 +217,7 @@ __global__ void __launch_bounds__(kThreads) conv_ks_kernel(const __grid_constant
                 ws::wait(tc::smem_addr(bars + 2 * NS + 4), 0);
             }
         }
-    } else {
+    } else if (warp < 6) {
         // ---- epilogue: warps 2-5, one pixel (TMEM lane) per thread
         const int q = warp & 3;
         const int px = q * 32 + lane;
@@ -230,6 +264,82 @@ __global__ void __launch_bounds__(kThreads) conv_ks_kernel(const __grid_constant
             tc::fence_before_sync();
             __syncwarp();
             if (lane == 0) ws::mbar_arrive(tempty0 + 8 * acc);
+        }
+    } else if constexpr (UP) {
+        // ---- up-sampling: warps 6-13 take every stage in the order of the
+        // ring; for an up-sampled group, thread u writes (chunk, halo column)
+        // items u, u + 256, .. down the HY halo rows, holding the x
+        // interpolations of the two coarse rows it last used (consecutive fine
+        // rows share one); then every stage is released to the MMA warp.
+        const int ut = tid - kThreads;
+        constexpr int NUT = 32 * L::up_warps;
+        int i = 0;
+        for (int tile = blockIdx.x; tile < a.ntiles && !failed; tile += gridDim.x) {
+            const int ty = tile / a.tiles_x, tx = tile - ty * a.tiles_x;
+            const int x0 = tx * TO - (K1 ? 0 : 1), y0 = ty * TR - (K1 ? 0 : 1);
+            const int cx0 = ((x0 + 1) >> 1) - 1, cy0 = ((y0 + 1) >> 1) - 1;
+            for (int g = 0; g < a.groups; ++g, ++i) {
+                const int s = i % NS;
+                if (!ws::wait(full0 + 8 * s, (i / NS) & 1)) {
+                    failed = true;
+                    break;
+                }
+                if (2 * g < a.ch0) {
+                    unsigned char* st = smem + (size_t)s * L::stage;
+                    const unsigned char* cb = st + L::halo + L::wgrp;
+                    for (int it = ut; it < 2 * kHXW; it += NUT) {
+                        const int kk = it / kHXW, p = it - kk * kHXW;
+                        uint4* dst = reinterpret_cast<uint4*>(st + kk * L::plane) + p;
+                        const int gx = x0 + p;
+                        if (gx < 0 || gx >= a.W) {
+#pragma unroll
+                            for (int j = 0; j < HY; ++j) dst[j * kHXW] = make_uint4(0, 0, 0, 0);
+                            continue;
+                        }
+                        int ix0, ix1;
+                        float fx;
+                        up_src(gx, a.Wc, ix0, ix1, fx);
+                        const uint4* crow = reinterpret_cast<const uint4*>(cb + kk * L::cplane);
+                        const int lx0 = ix0 - cx0, lx1 = ix1 - cx0;
+                        float ra[8], rb[8];   // x interpolations of local coarse rows ya, yb
+                        int ya = -1, yb = -1;
+#pragma unroll
+                        for (int j = 0; j < HY; ++j) {
+                            const int gy = y0 + j;
+                            if (gy < 0 || gy >= a.H) {
+                                dst[j * kHXW] = make_uint4(0, 0, 0, 0);
+                                continue;
+                            }
+                            int iy0, iy1;
+                            float fy;
+                            up_src(gy, a.Hc, iy0, iy1, fy);
+                            const int ly0 = iy0 - cy0, ly1 = iy1 - cy0;
+                            if (ly0 != ya) {
+                                if (ly0 == yb) {
+#pragma unroll
+                                    for (int k = 0; k < 8; ++k) ra[k] = rb[k];
+                                } else {
+                                    up_xlerp8(crow[ly0 * L::CC + lx0], crow[ly0 * L::CC + lx1], fx, ra);
+                                }
+                                ya = ly0;
+                            }
+                            if (ly1 != yb) {
+                                if (ly1 == ya) {
+#pragma unroll
+                                    for (int k = 0; k < 8; ++k) rb[k] = ra[k];
+                                } else {
+                                    up_xlerp8(crow[ly1 * L::CC + lx0], crow[ly1 * L::CC + lx1], fx, rb);
+                                }
+                                yb = ly1;
+                            }
+                            dst[j * kHXW] = up_ylerp8(ra, rb, fy);
+                        }
+                    }
+                    tc::fence_async_smem();   // generic-proxy writes, read next by the tensor core
+                }
+                __syncwarp();
+                if (lane == 0) ws::mbar_arrive(ready0 + 8 * s);
+            }
         }
     }
     if (failed) atomicExch(a.error, 1);

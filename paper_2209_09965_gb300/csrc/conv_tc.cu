@@ -1090,24 +1090,25 @@ fvn_status calibrate_amax(fvn_ctx* ctx, const ReconPlan& B, int w, int h, float*
 // ---------------------------------------------------------------------------
 
 // Stages of the ring that fit in shared memory (at most 4).
-template <int COUTP, int TR, bool K1>
+template <int COUTP, int TR, bool K1, bool UP>
 constexpr int ks_stages() {
-    using L1 = ks::Layout<COUTP, TR, 1, K1>;
+    using L1 = ks::Layout<COUTP, TR, 1, K1, UP>;
     const long long per = (long long)L1::stage + 16;
     const long long ns = (227 * 1024 - (long long)L1::bytes + per) / per;
     return ns >= 4 ? 4 : (ns < 1 ? 1 : (int)ns);
 }
 
-template <int COUTP, int TR, bool K1>
+template <int COUTP, int TR, bool K1, bool UP>
 static fvn_status launch_ks(fvn_ctx* ctx, const KsConv& c, cudaStream_t st) {
-    constexpr int NS = ks_stages<COUTP, TR, K1>();
-    using L = ks::Layout<COUTP, TR, NS, K1>;
+    constexpr int NS = ks_stages<COUTP, TR, K1, UP>();
+    using L = ks::Layout<COUTP, TR, NS, K1, UP>;
     static_assert(L::bytes <= 227 * 1024, "stage ring does not fit in shared memory");
-    auto kern = ks::conv_ks_kernel<COUTP, TR, NS, K1>;
+    auto kern = ks::conv_ks_kernel<COUTP, TR, NS, K1, UP>;
     static std::atomic<unsigned long long> configured{0};
     FVN_CUDA(ctx, opt_in_smem(ctx, kern, (int)L::bytes, configured));
     ks::Args a{};
-    fvn_status s = make_map(ctx, &a.map0, c.in0, 8 * c.ch0, c.W, c.H, L::HY, false);
+    fvn_status s = UP ? make_map(ctx, &a.map0, c.in0, 8 * c.ch0, c.W / 2, c.H / 2, L::CR, false, L::CC)
+                      : make_map(ctx, &a.map0, c.in0, 8 * c.ch0, c.W, c.H, L::HY, false);
     if (s != FVN_OK) return s;
     if (c.ch1 > 0) {
         if ((s = make_map(ctx, &a.map1, c.in1, 8 * c.ch1, c.W, c.H, L::HY, false)) != FVN_OK) return s;
@@ -1128,9 +1129,11 @@ static fvn_status launch_ks(fvn_ctx* ctx, const KsConv& c, cudaStream_t st) {
     a.W = c.W;
     a.tiles_x = (c.W + L::TO - 1) / L::TO;
     a.ntiles = a.tiles_x * ((c.H + TR - 1) / TR);
+    a.Hc = c.H / 2;
+    a.Wc = c.W / 2;
     a.error = ctx->d_error;
     const int grid = std::max(1, std::min(a.ntiles, ctx->num_sms > 0 ? ctx->num_sms : 148));
-    kern<<<grid, ks::kThreads, L::bytes, st>>>(a);
+    kern<<<grid, L::threads, L::bytes, st>>>(a);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
@@ -1140,10 +1143,15 @@ int ks_coutp(int cout) { return (cout + 15) / 16 * 16; }
 fvn_status ks_conv(fvn_ctx* ctx, const KsConv& c, cudaStream_t st) {
     FVN_CHECK_ARG(ctx, c.in0 && c.wpk && c.bias && (c.out || c.out32) && (c.ch1 == 0 || c.in1), "null tensor");
     FVN_CHECK_ARG(ctx, c.ch0 >= 1 && c.ch1 >= 0 && c.H >= 1 && c.W >= 1 && (c.k == 1 || c.k == 3), "bad layer");
+    FVN_CHECK_ARG(ctx, !c.up || (c.ch0 % 2 == 0 && c.H % 2 == 0 && c.W % 2 == 0 && c.H >= 2 && c.W >= 2),
+                  "an up-sampled source needs an even chunk count and an even frame");
     const int cp = ks_coutp(c.cout);
     const bool k1 = c.k == 1;
-#define FVN_KS(CP, TR)                                                       \
-    if (cp == CP) return k1 ? launch_ks<CP, TR, true>(ctx, c, st) : launch_ks<CP, TR, false>(ctx, c, st);
+#define FVN_KS(CP, TR)                                                                                           \
+    if (cp == CP) {                                                                                              \
+        if (c.up) return k1 ? launch_ks<CP, TR, true, true>(ctx, c, st) : launch_ks<CP, TR, false, true>(ctx, c, st); \
+        return k1 ? launch_ks<CP, TR, true, false>(ctx, c, st) : launch_ks<CP, TR, false, false>(ctx, c, st);       \
+    }
     FVN_KS(16, 4)
     FVN_KS(32, 4)
     FVN_KS(48, 4)

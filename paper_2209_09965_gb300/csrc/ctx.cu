@@ -203,6 +203,10 @@ extern "C" fvn_status fvn_set_option(fvn_ctx* ctx, int option, int value) {
             FVN_CHECK_ARG(ctx, value == 0 || value == 1, "two-stage tensor-core option must be 0 or 1");
             ctx->wnet.tc = value;
             return FVN_OK;
+        case FVN_OPT_WNET_FUSED_UPSAMPLING:
+            FVN_CHECK_ARG(ctx, value == 0 || value == 1, "two-stage fused up-sampling option must be 0 or 1");
+            ctx->wnet.fuse_up = value;
+            return FVN_OK;
         case FVN_OPT_STAGE_TIMING:
             FVN_CHECK_ARG(ctx, value == 0 || value == 1, "stage-timing option must be 0 or 1");
             if (value && !ctx->tm_ev[0])

@@ -369,23 +369,6 @@ size_t plan_wnet(const fvn_wnet_config& c, int Wp, int Hp, WPlan* pl, char* base
 // K-streamed tcgen05 kernel; the 3-channel image path, the tap logits and
 // the blend logits stay FP32 planar.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void h8_to_f(uint4 u, float* f) {
-    const __half2* h = reinterpret_cast<const __half2*>(&u);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-        const float2 t = __half22float2(h[i]);
-        f[2 * i] = t.x;
-        f[2 * i + 1] = t.y;
-    }
-}
-
-__device__ __forceinline__ uint4 f_to_h8(const float* f) {
-    uint4 u;
-    __half2* h = reinterpret_cast<__half2*>(&u);
-#pragma unroll
-    for (int i = 0; i < 4; ++i) h[i] = __floats2half2_rn(f[2 * i], f[2 * i + 1]);
-    return u;
-}
 
 // the sparse frame (FP32 [5][h][w]) as chunk 0 of a Wp x Hp chunk-planar
 // tensor: zero outside the frame and in lanes 5..7
@@ -435,13 +418,9 @@ __global__ void cp_up2_kernel(const uint4* __restrict__ in, int h, int w, uint4*
     up_src(2 * m + 1, h, y0o, y1o, tyo);
     const uint4* p = in + (long long)blockIdx.y * h * w;
     auto xlerp = [&](int y, float* o) {   // x interpolation of coarse row y
-        float a[8], b[8];
-        h8_to_f(__ldg(p + y * w + x0), a);
-        h8_to_f(__ldg(p + y * w + x1), b);
-#pragma unroll
-        for (int j = 0; j < 8; ++j) o[j] = (1.f - tx) * a[j] + tx * b[j];
+        up_xlerp8(__ldg(p + y * w + x0), __ldg(p + y * w + x1), tx, o);
     };
-    float te[8], be[8], to[8], bo[8], o[8];
+    float te[8], be[8], to[8], bo[8];
     xlerp(y0e, te);
     xlerp(y1e, be);
     if (y0o == y1e) {
@@ -452,12 +431,8 @@ __global__ void cp_up2_kernel(const uint4* __restrict__ in, int h, int w, uint4*
     }
     xlerp(y1o, bo);
     uint4* q = out + (long long)blockIdx.y * (2 * h) * W2 + (long long)(2 * m) * W2 + ox;
-#pragma unroll
-    for (int j = 0; j < 8; ++j) o[j] = (1.f - tye) * te[j] + tye * be[j];
-    q[0] = f_to_h8(o);
-#pragma unroll
-    for (int j = 0; j < 8; ++j) o[j] = (1.f - tyo) * to[j] + tyo * bo[j];
-    q[W2] = f_to_h8(o);
+    q[0] = up_ylerp8(te, be, tye);
+    q[W2] = up_ylerp8(to, bo, tyo);
 }
 
 bool tc_widths_ok(const fvn_wnet_config& c) {
@@ -621,8 +596,11 @@ fvn_status wnet_forward_tc(fvn_ctx* ctx, const float* rgbam, int w, int h, float
     const WTable t = make_table(c);
     auto hs = [&](int s) { return Hp >> s; };
     auto ws = [&](int s) { return Wp >> s; };
-    auto conv = [&](const uint4* xa, int ca, const uint4* xb, int cb, int s, int li, int relu, uint4* y, float* y32) {
+    // upx: xa is the level below (coarse), up-sampled inside the convolution
+    auto convx = [&](const uint4* xa, int ca, const uint4* xb, int cb, int s, int li, int relu, uint4* y, float* y32,
+                     bool upx) {
         KsConv k{};
+        k.up = upx;
         k.in0 = xa;
         k.ch0 = (ca + 7) / 8;
         k.in1 = xb;
@@ -639,6 +617,9 @@ fvn_status wnet_forward_tc(fvn_ctx* ctx, const float* rgbam, int w, int h, float
         k.out32 = y32;
         return ks_conv(ctx, k, st);
     };
+    auto conv = [&](const uint4* xa, int ca, const uint4* xb, int cb, int s, int li, int relu, uint4* y, float* y32) {
+        return convx(xa, ca, xb, cb, s, li, relu, y, y32, false);
+    };
     auto pool = [&](const uint4* x, int ch, int s, uint4* y) {   // level s -> s + 1
         cp_pool2_kernel<<<cp_grid((long long)hs(s + 1) * ws(s + 1), (ch + 7) / 8), 256, 0, st>>>(x, hs(s), ws(s), y);
         return cudaGetLastError() == cudaSuccess ? FVN_OK : set_error(ctx, FVN_ERR_CUDA, "pooling launch failed");
@@ -646,6 +627,13 @@ fvn_status wnet_forward_tc(fvn_ctx* ctx, const float* rgbam, int w, int h, float
     auto up = [&](const uint4* x, int ch, int s, uint4* y) {     // level s + 1 -> s
         cp_up2_kernel<<<cp_grid((long long)hs(s + 1) * ws(s), (ch + 7) / 8), 256, 0, st>>>(x, hs(s + 1), ws(s + 1), y);
         return cudaGetLastError() == cudaSuccess ? FVN_OK : set_error(ctx, FVN_ERR_CUDA, "up-sampling launch failed");
+    };
+    // a decoder level's first layer on [up(x), skip]: up-sampled inside the
+    // convolution where the chunks of x form whole groups, else by a pass
+    auto conv_up = [&](const uint4* x, int ch, const uint4* skip, int cs, int s, int li, uint4* upbuf, uint4* y) {
+        if (S.fuse_up && ((ch + 7) / 8) % 2 == 0) return convx(x, ch, skip, cs, s, li, 1, y, nullptr, true);
+        const fvn_status us = up(x, ch, s, upbuf);
+        return us != FVN_OK ? us : conv(upbuf, ch, skip, cs, s, li, 1, y, nullptr);
     };
 
     cp_frame_kernel<<<(Wp * Hp + 255) / 256, 256, 0, st>>>(rgbam, w, h, B.x, Wp, Hp);
@@ -665,8 +653,7 @@ fvn_status wnet_forward_tc(fvn_ctx* ctx, const float* rgbam, int w, int h, float
     const uint4* prev = B.B;
     int pc = c.bot;
     for (int s = L - 1; s >= 0; --s) {
-        WK(up(prev, pc, s, B.UPD[s]));
-        WK(conv(B.UPD[s], pc, B.E[s], c.enc[s], s, t.d_dec_a[s], 1, B.T[s], nullptr));
+        WK(conv_up(prev, pc, B.E[s], c.enc[s], s, t.d_dec_a[s], B.UPD[s], B.T[s]));
         WK(conv(B.T[s], c.dec[s], nullptr, 0, s, t.d_dec_b[s], 1, B.U[s], nullptr));
         prev = B.U[s];
         pc = c.dec[s];
@@ -688,8 +675,7 @@ fvn_status wnet_forward_tc(fvn_ctx* ctx, const float* rgbam, int w, int h, float
     const uint4* kprev = B.GB;
     pc = c.bot;
     for (int s = L - 1; s >= 0; --s) {
-        WK(up(kprev, pc, s, B.UPK[s]));
-        WK(conv(B.UPK[s], pc, B.U[s], c.dec[s], s, t.k_dec[s], 1, B.GD[s], nullptr));
+        WK(conv_up(kprev, pc, B.U[s], c.dec[s], s, t.k_dec[s], B.UPK[s], B.GD[s]));
         WK(conv(B.GD[s], c.dec[s], nullptr, 0, s, -1 - s, 0, nullptr, B.LD[s]));   // taps + blend: LD, ZD
         kprev = B.GD[s];
         pc = c.dec[s];

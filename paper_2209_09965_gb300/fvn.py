@@ -48,6 +48,7 @@ OPT_STAGE_TIMING = 10
 OPT_CONV_ROWS_HALF, OPT_CONV_ROWS_QUARTER, OPT_CONV_ROWS_DEC1 = 11, 12, 13
 OPT_CONV_FUSE_UP_DEC1 = 14
 OPT_WNET_TENSOR_CORES = 15
+OPT_WNET_FUSED_UPSAMPLING = 16
 STAGES = ("mask", "march_setup", "volume_prep", "march", "network")
 
 

@@ -297,3 +297,44 @@ def test_tensor_core_option_is_checked(fvn):
             c.set_option(fvn.OPT_WNET_TENSOR_CORES, 2)
     finally:
         c.close()
+
+
+@pytest.mark.parametrize("cfg,h,w,seed", [
+    (wl.WNET_PAPER, 40, 48, 3),
+    (wl.WNET_PAPER, 37, 131, 4),       # ragged: padded frame, tiles across 126- and 128-pixel rows
+    (wl.WNET_SLIM, 64, 96, 5),
+    (((8, 16), 24, (8, 16)), 9, 300, 6),   # a 24-channel coarse input (3 chunks) keeps the separate pass
+    (wl.WNET_PAPER, 1080, 1920, 7),
+])
+def test_fused_upsampling_equals_the_separate_pass(fvn, cfg, h, w, seed):
+    """The decoder convolutions that up-sample their coarse input themselves
+    (FVN_OPT_WNET_FUSED_UPSAMPLING = 1, the default) give the same bits as
+    the separate up-sampling pass: the same interpolation, operation for
+    operation, only computed in shared memory."""
+    flat = wl.wnet_weights(cfg, seed)
+    flat = flat + np.random.default_rng(seed).normal(size=flat.size).astype(np.float32) * 0.05
+    sp = T(sparse_input(1, h, w, seed, density=0.1)[0])
+    c = fvn.Context()
+    try:
+        c.load_wnet_weights(cfg, flat)
+        c.set_option(fvn.OPT_WNET_TENSOR_CORES, 1)
+        fused = torch.full((3, h, w), 7.0, device=DEV)
+        c.reconstruct_wnet(sp, w, h, fused)
+        c.set_option(fvn.OPT_WNET_FUSED_UPSAMPLING, 0)
+        sep = torch.full((3, h, w), -7.0, device=DEV)
+        c.reconstruct_wnet(sp, w, h, sep)
+        torch.cuda.synchronize()
+        c.device_status()
+        assert torch.equal(fused, sep)
+        assert bool(torch.isfinite(fused).all())
+    finally:
+        c.close()
+
+
+def test_fused_upsampling_option_is_checked(fvn):
+    c = fvn.Context()
+    try:
+        with pytest.raises(fvn.FvnError, match="fused up-sampling option"):
+            c.set_option(fvn.OPT_WNET_FUSED_UPSAMPLING, 2)
+    finally:
+        c.close()
