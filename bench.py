@@ -1313,6 +1313,10 @@ def main():
         cam, fov = frames[0]
         ctx.render(vol, tf, cam, fov, mp, rgb, rgbam_out=rgbam)
         ctx.calibrate_fp8(rgbam, W, H, reset=True)
+        tiles8 = None
+        if tuned is not None:   # the FP8 network's own tile shapes, the FP16 ones restored below
+            tiles8 = autotune.tune_conv_tiles(ctx, rgbam, W, H, rgb, precision=fvn.PREC_FP8)
+            tiles8.pop("candidates")
         f8_ms, f8_psnr = [], []
         for i in range(min(args.steps, ORBIT)):
             cam, fov = frames[i % ORBIT]
@@ -1327,9 +1331,17 @@ def main():
             f8_psnr.append(psnr_t(rgb, dense[:3]))
         fp8_info = {"frames_per_s": len(f8_ms) / (sum(f8_ms) / 1000.0), "ms_per_frame": float(np.mean(f8_ms)),
                     "psnr_vs_dense_db": {"mean": float(np.mean(f8_psnr)), "min": float(np.min(f8_psnr))},
-                    "note": "fvn_render with the FP8 E4M3 network, activation scales calibrated on frame 0"}
+                    "conv_tiles": tiles8,
+                    "note": "fvn_render with the FP8 E4M3 network, activation scales calibrated on frame 0, "
+                            "tile shapes tuned for it"}
     except Exception as exc:   # reported, not part of the metric
         fp8_info = {"error": str(exc)[:200]}
+    if tuned is not None:
+        t16 = tuned["conv_tiles"]
+        ctx.set_option(fvn.OPT_CONV_ROWS_HALF, t16["rows_half"])
+        ctx.set_option(fvn.OPT_CONV_ROWS_QUARTER, t16["rows_quarter"])
+        ctx.set_option(fvn.OPT_CONV_ROWS_DEC1, t16["rows_dec1"])
+        ctx.set_option(fvn.OPT_CONV_FUSE_UP_DEC1, t16["fuse_up_dec1"])
 
     # ---- the frame captured once in a CUDA graph and replayed ----------------
     graph_info = None

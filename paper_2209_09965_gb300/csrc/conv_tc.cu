@@ -682,10 +682,10 @@ struct WsSpec {
 };
 
 // Stages of the shared-memory ring that fit next to the resident weights.
-template <int CIN, int COUT, int TR, bool F8, bool FUSE, int UPC = 0>
+template <int CIN, int COUT, int TR, bool F8, bool FUSE, int UPC = 0, bool CB1 = false>
 constexpr int ws_stages() {
-    using L1 = ws::Layout<CIN, COUT, TR, 1, F8, FUSE, UPC>;
-    const long long per = (long long)L1::stage + L1::coarse + 8 * (UPC ? 3 : 2);   // bytes of one stage
+    using L1 = ws::Layout<CIN, COUT, TR, 1, F8, FUSE, UPC, CB1>;
+    const long long per = (long long)L1::stage + (CB1 ? 0 : L1::coarse) + 8 * (UPC ? 3 : 2);   // bytes of one stage
     const long long budget = 227 * 1024 - (long long)L1::bytes + per;             // bytes for the stages
     const long long ns = budget / per;
     return ns >= 4 ? 4 : (ns < 1 ? 1 : (int)ns);
@@ -696,11 +696,17 @@ constexpr int ws_stages() {
 template <int CIN, int CHG, int CH0, int COUT, int TR, bool POOL, bool F8, bool FUSE = false, int UPC = 0>
 static fvn_status launch_ws(fvn_ctx* ctx, const WsSpec* spec, int n, const ConvW& w, float out_q, float pool_q,
                             cudaStream_t st) {
-    constexpr int NS = ws_stages<CIN, COUT, TR, F8, FUSE, UPC>();
-    using L = ws::Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>;
+    // an up-sampled layer left with a single stage by a coarse buffer per
+    // stage shares one coarse buffer among the stages instead, where that
+    // makes room for a second stage
+    constexpr int NS_PER = ws_stages<CIN, COUT, TR, F8, FUSE, UPC>();
+    constexpr int NS_ONE = UPC > 0 ? ws_stages<CIN, COUT, TR, F8, FUSE, UPC, (UPC > 0)>() : 0;
+    constexpr bool CB1 = NS_PER == 1 && NS_ONE > 1;
+    constexpr int NS = CB1 ? NS_ONE : NS_PER;
+    using L = ws::Layout<CIN, COUT, TR, NS, F8, FUSE, UPC, CB1>;
     static_assert(L::bytes <= 227 * 1024, "stage ring does not fit in shared memory");
     static_assert(sizeof(ws::Args) <= 32764, "kernel arguments exceed the parameter space");
-    auto kern = ws::conv3x3_ws_kernel<CIN, CHG, CH0, COUT, TR, NS, POOL, F8, FUSE, UPC>;
+    auto kern = ws::conv3x3_ws_kernel<CIN, CHG, CH0, COUT, TR, NS, POOL, F8, FUSE, UPC, CB1>;
     static std::atomic<unsigned long long> configured{0};
     FVN_CUDA(ctx, opt_in_smem(ctx, kern, (int)L::bytes, configured));
     int smem_sm = 0;

@@ -80,8 +80,11 @@ __device__ __forceinline__ bool wait(uint32_t bar, uint32_t parity) {
 // bilinear x2 up-sampling of a coarse tensor, computed in the kernel: the
 // producer loads the coarse rows / columns under the tile (CR x CC pixels
 // per chunk) next to each stage, and up-sampling warps interpolate them into
-// the stage's first UPC chunk planes before the MMAs read it.
-template <int CIN, int COUT, int TR, int NS, bool F8, bool FUSE = false, int UPC = 0>
+// the stage's first UPC chunk planes before the MMAs read it.  CB1: one
+// coarse buffer for all stages (where per-stage ones would leave room for
+// fewer stages): the producer loads a tile's coarse block once the
+// up-sampling warps have released the previous one.
+template <int CIN, int COUT, int TR, int NS, bool F8, bool FUSE = false, int UPC = 0, bool CB1 = false>
 struct Layout {
     static constexpr int EB = F8 ? 1 : 2;
     static constexpr int CPC = 16 / EB;                      // channels per 16-byte chunk
@@ -100,13 +103,14 @@ struct Layout {
     static constexpr size_t zero_off = stage_off + (size_t)NS * stage;   // zero A operand (FUSE)
     static constexpr size_t zero_bytes = FUSE ? 2 * kTW * 16 : 0;
     static constexpr size_t coarse_off = zero_off + zero_bytes;
-    static constexpr size_t bias_off = coarse_off + (size_t)NS * coarse;
+    static constexpr size_t bias_off = coarse_off + (size_t)(CB1 ? 1 : NS) * coarse;
     static constexpr size_t bar_off = bias_off + 2 * COUT * 4;
-    static constexpr int nbar = 2 * NS + 4 + (UPC ? NS : 0);          // full, empty, tfull, tempty, ready
+    static constexpr int nbar = 2 * NS + 4 + (UPC ? NS : 0) + (CB1 ? 1 : 0);   // full, empty, tfull, tempty, ready, coarse free
     static constexpr size_t bytes = bar_off + nbar * 8 + 16;
     static constexpr int up_warps = 8;                                 // up-sampling warps (UPC > 0)
     static constexpr int threads = 64 + 32 * 4 + (UPC ? 32 * up_warps : 0);
     static_assert(UPC == 0 || 2 * CC <= 256, "coarse box wider than a TMA box");
+    static_assert(!CB1 || UPC > 0, "a shared coarse buffer needs up-sampled chunks");
     static constexpr uint32_t acc = (FUSE ? TR + 4 : TR) * COUT;   // TMEM columns of one accumulator
     static constexpr uint32_t tmem_cols = 2 * acc <= 32 ? 32 : 2 * acc <= 64 ? 64 : 2 * acc <= 128 ? 128
                                         : 2 * acc <= 256 ? 256 : 512;
@@ -219,10 +223,11 @@ __device__ __forceinline__ void coarse_hlerp(const uint4* row, int lx0, int lx1,
 // CIN: K per tap (padded); CHG: chunks read from memory (the others stay
 // zero); CH0: chunks from source 0 (UPC > 0: CH0 == UPC chunks up-sampled
 // from the coarse tensor of source 0).
-template <int CIN, int CHG, int CH0, int COUT, int TR, int NS, bool POOL, bool F8, bool FUSE, int UPC = 0>
-__global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>::threads)
+template <int CIN, int CHG, int CH0, int COUT, int TR, int NS, bool POOL, bool F8, bool FUSE, int UPC = 0,
+          bool CB1 = false>
+__global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC, CB1>::threads)
     conv3x3_ws_kernel(const __grid_constant__ Args a) {
-    using L = Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>;
+    using L = Layout<CIN, COUT, TR, NS, F8, FUSE, UPC, CB1>;
     constexpr int CH = L::CH, HY = L::HY, kThreads = L::threads;
     static_assert(UPC == 0 || UPC == CH0, "up-sampled chunks are source 0");
     extern __shared__ __align__(1024) unsigned char smem[];
@@ -235,6 +240,7 @@ __global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>::thre
     const uint32_t full0 = tc::smem_addr(bars), empty0 = full0 + 8 * NS;
     const uint32_t tfull0 = full0 + 16 * NS, tempty0 = tfull0 + 16;
     const uint32_t ready0 = tempty0 + 16;   // UPC: stage's up-sampled planes written
+    const uint32_t cfree0 = ready0 + 8 * NS;   // CB1: the coarse buffer read by the up-sampling warps
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     {   // resident weights, bias, scales; chunks never loaded stay zero
@@ -276,6 +282,7 @@ __global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>::thre
         }
         if (UPC)
             for (int k = 0; k < NS; ++k) tc::mbar_init(bars + 2 * NS + 4 + k, L::up_warps);
+        if (CB1) tc::mbar_init(bars + 3 * NS + 4, L::up_warps);
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
     }
     if (warp == 1) {
@@ -298,7 +305,9 @@ __global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>::thre
             int i = 0;
             for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++i) {
                 const int s = i % NS, k = i / NS;
-                if (k > 0 && !wait(empty0 + 8 * s, (k - 1) & 1)) {
+                // CB1: the previous tile's coarse block read before this tile's
+                // is loaded over it (nothing of this tile is issued before)
+                if ((k > 0 && !wait(empty0 + 8 * s, (k - 1) & 1)) || (CB1 && i > 0 && !wait(cfree0, (i - 1) & 1))) {
                     failed = true;
                     break;
                 }
@@ -311,7 +320,7 @@ __global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>::thre
                     // the coarse rows / columns under the tile (source 0), then
                     // the fine chunks of source 1 straight into the stage
                     mbar_expect_tx(full, (uint32_t)(CHG - UPC) * HY * kHXW * 16 + (uint32_t)UPC * L::CR * L::CC * 16);
-                    const uint32_t cdst = tc::smem_addr(smem + L::coarse_off + (size_t)s * L::coarse);
+                    const uint32_t cdst = tc::smem_addr(smem + L::coarse_off + (CB1 ? 0 : (size_t)s * L::coarse));
 #pragma unroll
                     for (int c = 0; c < UPC; ++c)
                         tma_load_3d(cdst + c * L::cchunk, &im.map0, 2 * (((tx * kTO) >> 1) - 1), ((ty * TR) >> 1) - 1,
@@ -474,7 +483,7 @@ __global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>::thre
             const int Hc = im.Hl >> 1, Wc = im.Wl >> 1;
             const int cy0 = (y0 >> 1) - 1, cx0 = (x0 >> 1) - 1;   // coarse origin of the loaded block
             unsigned char* stg = sStage + (size_t)s * L::stage;
-            const unsigned char* cbuf = smem + L::coarse_off + (size_t)s * L::coarse;
+            const unsigned char* cbuf = smem + L::coarse_off + (CB1 ? 0 : (size_t)s * L::coarse);
             for (int item = t; item < UPC * kHXW; item += 32 * L::up_warps) {
                 const int c = item / kHXW, p = item - c * kHXW;
                 uint4* dst = reinterpret_cast<uint4*>(stg + (size_t)c * L::plane) + p;
@@ -529,7 +538,10 @@ __global__ void __launch_bounds__(Layout<CIN, COUT, TR, NS, F8, FUSE, UPC>::thre
             }
             tc::fence_async_smem();   // generic-proxy writes, read next by the tensor core
             __syncwarp();
-            if (lane == 0) mbar_arrive(ready0 + 8 * s);
+            if (lane == 0) {
+                mbar_arrive(ready0 + 8 * s);
+                if (CB1) mbar_arrive(cfree0);
+            }
         }
     }
     if (failed) atomicExch(a.error, 1);
