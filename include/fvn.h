@@ -630,14 +630,16 @@ fvn_status fvn_reconstruct_wnet(fvn_ctx* ctx, const float* rgbam, int w, int h, 
 /* Training pieces of the two-stage network (FP32, NCHW, device pointers).
  * fvn_filter3_fwd: out[n][c] (p) = sum_q w_q(p) img[n][c](p + q), c < 3,
  * w = softmax of logits[n][0..8](p) over the taps q = (q/3 - 1, q%3 - 1)
- * with p + q inside the h x w frame.  fvn_filter3_bwd: dL/dimg and
- * dL/dlogits (overwritten) from dL/dout. */
+ * with p + q inside the h x w frame (h and n at most 65535, else
+ * FVN_ERR_ARG).  fvn_filter3_bwd: dL/dimg and dL/dlogits (overwritten)
+ * from dL/dout. */
 fvn_status fvn_filter3_fwd(const float* img, const float* logits, int n, int h, int w_, float* out, void* stream);
 fvn_status fvn_filter3_bwd(const float* img, const float* logits, int n, int h, int w_, const float* gout,
                            float* gimg, float* glogits, void* stream);
 
 /* fvn_wnet_join_fwd: x = j + sigmoid(z) up(y - pool j), j / x [N][3][h][w],
- * y [N][3][h/2][w/2], z [N][1][h][w]; h, w even.  fvn_wnet_join_bwd: dL/dj,
+ * y [N][3][h/2][w/2], z [N][1][h][w]; h, w even; the forward pass takes h
+ * and N up to 65535.  fvn_wnet_join_bwd: dL/dj,
  * dL/dy and dL/dz (overwritten) from dL/dx. */
 fvn_status fvn_wnet_join_fwd(const float* j, const float* y, const float* z, int n, int h, int w_, float* x,
                              void* stream);

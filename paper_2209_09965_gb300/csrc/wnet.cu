@@ -67,24 +67,29 @@ __device__ __forceinline__ void tap_weights(const float* __restrict__ lg, long l
     for (int q = 0; q < kTaps; ++q) wq[q] *= inv;
 }
 
-__global__ void filter3_fwd_kernel(const float* __restrict__ img, const float* __restrict__ logits, int n, int h,
-                                   int w, float* __restrict__ out) {
-    const long long hw = (long long)h * w, total = n * hw;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long b = i / hw, p = i - b * hw;
-        const int y = (int)(p / w), x = (int)(p - (long long)y * w);
-        float wq[kTaps];
-        tap_weights(logits + b * kTaps * hw + p, hw, h, w, y, x, wq);
+// The image-path kernels of the forward pass run on a (column block, row,
+// image) grid of kRowThreads-pixel row segments: the pixel comes from the
+// block and thread indices, with no division.
+constexpr int kRowThreads = 128;
+
+dim3 row_grid(int w, int h, int n) { return dim3((unsigned)((w + kRowThreads - 1) / kRowThreads), (unsigned)h, (unsigned)n); }
+
+__global__ void __launch_bounds__(kRowThreads) filter3_fwd_kernel(const float* __restrict__ img,
+                                                                   const float* __restrict__ logits, int n, int h,
+                                                                   int w, float* __restrict__ out) {
+    const int x = blockIdx.x * kRowThreads + threadIdx.x, y = blockIdx.y, b = blockIdx.z;
+    if (x >= w) return;
+    const long long hw = (long long)h * w, p = (long long)y * w + x;
+    float wq[kTaps];
+    tap_weights(logits + b * kTaps * hw + p, hw, h, w, y, x, wq);
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float* im = img + (b * 3 + c) * hw + p;
-            float acc = 0.f;
+    for (int c = 0; c < 3; ++c) {
+        const float* im = img + (b * 3 + c) * hw + p;
+        float acc = 0.f;
 #pragma unroll
-            for (int q = 0; q < kTaps; ++q)
-                if (tap_inside(q, y, x, h, w)) acc = fmaf(wq[q], __ldg(im + (q / 3 - 1) * w + (q % 3 - 1)), acc);
-            out[(b * 3 + c) * hw + p] = acc;
-        }
+        for (int q = 0; q < kTaps; ++q)
+            if (tap_inside(q, y, x, h, w)) acc = fmaf(wq[q], __ldg(im + (q / 3 - 1) * w + (q % 3 - 1)), acc);
+        out[(b * 3 + c) * hw + p] = acc;
     }
 }
 
@@ -160,22 +165,21 @@ __device__ __forceinline__ float join_detail(const float* __restrict__ jc, const
     return (1.f - ty) * top + ty * bot;
 }
 
-__global__ void join_fwd_kernel(const float* __restrict__ j, const float* __restrict__ yv,
-                                const float* __restrict__ z, int n, int h, int w, float* __restrict__ xo) {
-    const long long hw = (long long)h * w, total = n * hw;
+__global__ void __launch_bounds__(kRowThreads) join_fwd_kernel(const float* __restrict__ j,
+                                                                const float* __restrict__ yv,
+                                                                const float* __restrict__ z, int n, int h, int w,
+                                                                float* __restrict__ xo) {
+    const int x = blockIdx.x * kRowThreads + threadIdx.x, y = blockIdx.y, b = blockIdx.z;
+    if (x >= w) return;
+    const long long hw = (long long)h * w, p = (long long)y * w + x;
     const int hc = h / 2, wc = w / 2;
     const long long hwc = (long long)hc * wc;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long b = i / hw, p = i - b * hw;
-        const int y = (int)(p / w), x = (int)(p - (long long)y * w);
-        const float a = sigmoidf_(__ldg(z + b * hw + p));
+    const float a = sigmoidf_(__ldg(z + b * hw + p));
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float* jc = j + (b * 3 + c) * hw;
-            const float u = join_detail(jc, yv + (b * 3 + c) * hwc, w, hc, wc, y, x);
-            xo[(b * 3 + c) * hw + p] = __ldg(jc + p) + a * u;
-        }
+    for (int c = 0; c < 3; ++c) {
+        const float* jc = j + (b * 3 + c) * hw;
+        const float u = join_detail(jc, yv + (b * 3 + c) * hwc, w, hc, wc, y, x);
+        xo[(b * 3 + c) * hw + p] = __ldg(jc + p) + a * u;
     }
 }
 
@@ -232,15 +236,11 @@ __global__ void join_bwd_fine_kernel(const float* __restrict__ j, const float* _
 }
 
 // dst[c][y][x] = src[c][y][x] inside src's sw x sh frame, 0 outside; dst is dw x dh
-__global__ void window_copy_kernel(const float* __restrict__ src, int sw, int sh, float* __restrict__ dst, int dw,
-                                   int dh, int nc) {
-    const long long dhw = (long long)dw * dh, total = nc * dhw;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
-         i += (long long)gridDim.x * blockDim.x) {
-        const long long c = i / dhw, p = i - c * dhw;
-        const int y = (int)(p / dw), x = (int)(p - (long long)y * dw);
-        dst[i] = (y < sh && x < sw) ? __ldg(src + (c * sh + y) * (long long)sw + x) : 0.f;
-    }
+__global__ void __launch_bounds__(kRowThreads) window_copy_kernel(const float* __restrict__ src, int sw, int sh,
+                                                                   float* __restrict__ dst, int dw, int dh, int nc) {
+    const int x = blockIdx.x * kRowThreads + threadIdx.x, y = blockIdx.y, c = blockIdx.z;
+    if (x >= dw) return;
+    dst[((long long)c * dh + y) * dw + x] = (y < sh && x < sw) ? __ldg(src + ((long long)c * sh + y) * sw + x) : 0.f;
 }
 
 // ---------------------------------------------------------------------------
@@ -691,7 +691,7 @@ fvn_status wnet_forward_tc(fvn_ctx* ctx, const float* rgbam, int w, int h, float
         WQ(fvn_wnet_join_fwd(B.J[s], B.Y[s + 1], B.ZD[s], 1, hs(s), ws(s), B.X[s], stream));
         WQ(fvn_filter3_fwd(B.X[s], B.LD[s], 1, hs(s), ws(s), B.Y[s], stream));
     }
-    window_copy_kernel<<<grid_of(3LL * w * h), 256, 0, st>>>(B.Y[0], Wp, Hp, rgb, w, h, 3);
+    window_copy_kernel<<<row_grid(w, h, 3), kRowThreads, 0, st>>>(B.Y[0], Wp, Hp, rgb, w, h, 3);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
@@ -805,7 +805,7 @@ extern "C" fvn_status fvn_reconstruct_wnet(fvn_ctx* ctx, const float* rgbam, int
     auto hs = [&](int s) { return Hp >> s; };
     auto ws = [&](int s) { return Wp >> s; };
 
-    window_copy_kernel<<<grid_of(5LL * Wp * Hp), 256, 0, st>>>(rgbam, w, h, B.x, Wp, Hp, 5);
+    window_copy_kernel<<<row_grid(Wp, Hp, 5), kRowThreads, 0, st>>>(rgbam, w, h, B.x, Wp, Hp, 5);
     FVN_LAUNCH_CHECK(ctx);
     // D: encoder, coarsest block, decoder, output layer
     const float* in = B.x;
@@ -863,7 +863,7 @@ extern "C" fvn_status fvn_reconstruct_wnet(fvn_ctx* ctx, const float* rgbam, int
         WN(fvn_wnet_join_fwd(B.J[s], B.Y[s + 1], B.ZD[s], 1, hs(s), ws(s), B.X[s], stream));
         WN(fvn_filter3_fwd(B.X[s], B.LD[s], 1, hs(s), ws(s), B.Y[s], stream));
     }
-    window_copy_kernel<<<grid_of(3LL * w * h), 256, 0, st>>>(B.Y[0], Wp, Hp, rgb, w, h, 3);
+    window_copy_kernel<<<row_grid(w, h, 3), kRowThreads, 0, st>>>(B.Y[0], Wp, Hp, rgb, w, h, 3);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
@@ -872,7 +872,8 @@ extern "C" fvn_status fvn_filter3_fwd(const float* img, const float* logits, int
                                       void* stream) {
     fvn_ctx* ctx = nullptr;
     FVN_CHECK_ARG(ctx, img && logits && out && n >= 1 && h >= 1 && w_ >= 1, "bad filter arguments");
-    filter3_fwd_kernel<<<grid_of((long long)n * h * w_), 256, 0, as_stream(stream)>>>(img, logits, n, h, w_, out);
+    FVN_CHECK_ARG(ctx, h <= 65535 && n <= 65535, "bad filter arguments");
+    filter3_fwd_kernel<<<row_grid(w_, h, n), kRowThreads, 0, as_stream(stream)>>>(img, logits, n, h, w_, out);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
@@ -895,7 +896,8 @@ extern "C" fvn_status fvn_wnet_join_fwd(const float* j, const float* y, const fl
     fvn_ctx* ctx = nullptr;
     FVN_CHECK_ARG(ctx, j && y && z && x && n >= 1 && h >= 2 && w_ >= 2 && h % 2 == 0 && w_ % 2 == 0,
                   "bad join arguments");
-    join_fwd_kernel<<<grid_of((long long)n * h * w_), 256, 0, as_stream(stream)>>>(j, y, z, n, h, w_, x);
+    FVN_CHECK_ARG(ctx, h <= 65535 && n <= 65535, "bad join arguments");
+    join_fwd_kernel<<<row_grid(w_, h, n), kRowThreads, 0, as_stream(stream)>>>(j, y, z, n, h, w_, x);
     FVN_LAUNCH_CHECK(ctx);
     return FVN_OK;
 }
