@@ -265,3 +265,50 @@ def test_integer_dtypes_normalise():
     a, amb, _ = om.march(h, tf, cam, mp)
     b, _, _ = om.march(h.astype(np.float32), tf, cam, mp)
     assert np.array_equal(a, b)
+
+
+# Plausible mistakes planted in a copy of the oracle's source (the oracle
+# itself is not touched): each mutant is built with the oracle's own compiler
+# flags and must break at least one of the pins above.
+MUTANTS = [
+    ("compositing without the accumulated transmittance",
+     "double w = (1.0 - A) * alpha;", "double w = alpha;",
+     ["test_constant_slab_closed_form"]),
+    ("background added unattenuated",
+     "rgba[0] = C[0] + (1.0 - A) * bg[0];", "rgba[0] = C[0] + bg[0];",
+     ["test_constant_slab_closed_form", "test_empty_volume_and_miss_give_background"]),
+    ("specular exponent 16 instead of 32",
+     "for (int s = 0; s < 5; ++s) spec = spec * spec; /* ndl^32 */",
+     "for (int s = 0; s < 4; ++s) spec = spec * spec; /* ndl^32 */",
+     ["test_phong_constant_gradient_closed_form"]),
+    ("transfer-function index scaled by n instead of n - 1",
+     "double x = val * (double)(ntf - 1);", "double x = val * (double)ntf;",
+     ["test_linear_ramp_gamma_closed_form"]),
+    ("trilinear fractions of x and y swapped",
+     "double tx = ux - fx, ty = uy - fy, tz = uz - fz;", "double tx = uy - fy, ty = ux - fx, tz = uz - fz;",
+     ["test_trilinear_matches_library_interpolator"]),
+    ("early termination past the threshold",
+     "if (A >= term) { ++k; break; }", "if (A >= term + 0.005) { ++k; break; }",
+     ["test_early_termination_count"]),
+]
+
+
+@pytest.mark.parametrize("what,old,new,pins", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistakes_fail_the_pins(what, old, new, pins, tmp_path, monkeypatch):
+    import subprocess
+    src = open(om._SRC).read()
+    assert src.count(old) == 1, what
+    c = tmp_path / "mutant.c"
+    c.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so),
+                           str(c), "-lm"])
+    monkeypatch.setattr(om, "_lib", None)
+    monkeypatch.setattr(om, "build", lambda force=False: str(so))
+    caught = []
+    for name in pins:
+        try:
+            globals()[name]()
+        except AssertionError:
+            caught.append(name)
+    assert caught, f"no pin caught: {what}"

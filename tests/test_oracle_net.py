@@ -391,3 +391,82 @@ def test_temporal_loss_closed_form_and_gradient():
         e[idx] = 1e-7
         fd = (on.loss_temporal(o1 + e, o0, y1, y0)[0] - on.loss_temporal(o1 - e, o0, y1, y0)[0]) / 2e-7
         assert abs(fd - g[idx]) < 1e-6
+
+
+def test_loss_gradient_terms_closed_form():
+    """A prediction that differs from the target by a linear ramp a x + b y:
+    the L1 term is the mean of |a x + b y|, and the forward differences are a
+    along x and b along y at every pixel, so the two gradient terms add
+    lam_g (|a| + |b|) (paper, "Loss": L1 plus the L1 of the image gradients)."""
+    rng = np.random.default_rng(21)
+    h, w, a, b = 6, 7, 0.03, -0.05
+    yy, xx = np.mgrid[0:h, 0:w]
+    d = a * xx + b * yy
+    t = rng.uniform(size=(2, 3, h, w))
+    for lam in (1.0, 0.5, 0.0):
+        loss, _ = on.loss_l1_grad(t + d, t, lam)
+        assert abs(loss - (np.abs(d).mean() + lam * (abs(a) + abs(b)))) < 1e-12
+
+
+def _fails(pin, *args):
+    with pytest.raises(AssertionError):
+        pin(*args)
+
+
+def test_planted_mistakes_fail_the_pins(monkeypatch):
+    """Plausible mistakes planted in the oracle -- a transposed tap order, the
+    sample mask missing from the kernel-prediction weights, the blend
+    inverted, align-corners up-sampling, max instead of average pooling, a
+    flipped convolution kernel, the gradient terms of the loss dropped, Adam
+    without bias correction -- each break one of the pins above."""
+    good_nb, good_upw, good_sig = on._neighbours, on._up_axis_weights, on.sigmoid
+    good_conv, good_loss = on.conv2d, on.loss_l1_grad
+
+    def nb_transposed(img, r=on.KP_R):   # taps ordered dx-major instead of dy-major
+        n, c, h, w = img.shape
+        p = np.zeros((n, c, h + 2 * r, w + 2 * r))
+        p[:, :, r:r + h, r:r + w] = img
+        return np.stack([p[:, :, r + dy:r + dy + h, r + dx:r + dx + w]
+                         for dx in range(-r, r + 1) for dy in range(-r, r + 1)], axis=2)
+
+    def nb_mask_ones(img, r=on.KP_R):    # every tap counted as sampled
+        out = good_nb(img, r)
+        return np.ones_like(out) if img.shape[1] == 1 else out
+
+    def up_align_corners(n_in):
+        m = np.zeros((2 * n_in, n_in))
+        for o in range(2 * n_in):
+            s = o * (n_in - 1) / (2 * n_in - 1)
+            i0 = int(np.floor(s))
+            i1 = min(i0 + 1, n_in - 1)
+            m[o, i0] += 1.0 - (s - i0)
+            m[o, i1] += s - i0
+        return m
+
+    def max_pool(x):
+        n, c, h, w = x.shape
+        return x.reshape(n, c, h // 2, 2, w // 2, 2).max(axis=(3, 5))
+
+    def adam_no_bias_correction(p, g, m, v, step, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+        m = b1 * m + (1.0 - b1) * g
+        v = b2 * v + (1.0 - b2) * g * g
+        return p - lr * m / (np.sqrt(v) + eps), m, v
+
+    plants = [
+        ("_neighbours", nb_transposed, test_kp_one_hot_is_shifted_copy),
+        ("_neighbours", nb_mask_ones, test_kp_uniform_logits_is_masked_box_filter_and_empty_window_falls_back),
+        ("sigmoid", lambda z: good_sig(-z), test_kp_one_hot_is_shifted_copy),
+        ("_up_axis_weights", up_align_corners, test_pool_and_upsample_match_torch),
+        ("avgpool2", max_pool, test_pool_and_upsample_match_torch),
+        ("conv2d", lambda x, w, b: good_conv(x, w[:, :, ::-1, ::-1].copy(), b), test_conv_matches_direct_sum),
+        ("loss_l1_grad", lambda p, t, lam_g=1.0: good_loss(p, t, 0.0), test_loss_gradient_terms_closed_form),
+        ("adam_step", adam_no_bias_correction, test_adam_first_steps_closed_form),
+    ]
+    for name, bad, pin in plants:
+        monkeypatch.setattr(on, name, bad)
+        _fails(pin)
+        monkeypatch.undo()
+    # with the oracle restored every pin passes again
+    for _, _, pin in plants:
+        pin()
+    assert on._neighbours is good_nb and on._up_axis_weights is good_upw
