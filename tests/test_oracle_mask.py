@@ -143,3 +143,63 @@ def test_blue_noise_tiles_give_the_expected_density():
             # a rank shift of a permutation: the count of values below the
             # threshold in each tile is p n to within one
             assert abs(m.mean() - p) <= 2.0 / (32 * 32)
+
+
+def test_threshold_comparison_is_strict():
+    """M = 1 iff N < T (strict, Eq. 2 as read): noise equal to the threshold
+    samples nothing, one below it samples everything."""
+    w, h, p = 40, 24, 0.3
+    thr = int(np.floor(float(np.float32(p)) * (1 << 24)))
+    at = np.full((1, 8, 8), thr, np.uint32)
+    below = np.full((1, 8, 8), thr - 1, np.uint32)
+    m_at, ids_at, _ = om.make_mask(w, h, (20.0, 12.0), noise=at, **_flat_profile(p))
+    m_below, _, _ = om.make_mask(w, h, (20.0, 12.0), noise=below, **_flat_profile(p))
+    assert not m_at.any() and ids_at.size == 0
+    assert m_below.all()
+
+
+@pytest.mark.parametrize("w,h", [(1920, 1080), (333, 200)])
+def test_fovea_is_symmetric_about_a_centred_focal_point(w, h):
+    """Distances are measured from pixel centres: with the focal point at the
+    frame's centre, a fovea-only mask (tau 0 or 1, so no noise enters) is
+    mirror-symmetric in x and in y."""
+    m, _, _ = om.make_mask(w, h, (w / 2.0, h / 2.0), fovea_radius=0.1, falloff_sigma=0.0, p_base=0.0, seed=3)
+    assert 0 < m.sum() < w * h
+    assert np.array_equal(m, m[:, ::-1]) and np.array_equal(m, m[::-1, :])
+
+
+# Plausible mistakes planted in a copy of the oracle's source (the oracle
+# itself is not touched); each must break at least one of the pins above.
+MASK_MUTANTS = [
+    ("non-strict comparison", "m = (n24 < thr[b].astype(np.int64))", "m = (n24 <= thr[b].astype(np.int64))",
+     ["test_threshold_comparison_is_strict"]),
+    ("distances from pixel corners", "q = (2 * xs + 1 - f2x) ** 2 + (2 * ys + 1 - f2y) ** 2",
+     "q = (2 * xs - f2x) ** 2 + (2 * ys - f2y) ** 2", ["test_fovea_is_symmetric_about_a_centred_focal_point"]),
+    ("Gaussian without the factor 1/2", "pf = math.exp(-0.5 * z * z)", "pf = math.exp(-z * z)",
+     ["test_tau_table_matches_eq2_closed_form"]),
+    ("P_b added without scaling the falloff", "return (1.0 - p_base) * pf + p_base", "return pf + p_base",
+     ["test_tau_table_matches_eq2_closed_form"]),
+    ("threshold rounded up", "thr[b] = int(math.floor(t * ONE24))", "thr[b] = int(math.ceil(t * ONE24))",
+     ["test_tau_table_matches_eq2_closed_form"]),
+]
+
+
+@pytest.mark.parametrize("what,old,new,pins", MASK_MUTANTS, ids=[m[0] for m in MASK_MUTANTS])
+def test_planted_mistakes_fail_the_pins(what, old, new, pins, monkeypatch):
+    import types
+    src = open(om.__file__).read()
+    assert src.count(old) == 1, what
+    mutant = types.ModuleType("mask_mutant")
+    exec(compile(src.replace(old, new), "mask_mutant", "exec"), mutant.__dict__)
+    monkeypatch.setitem(globals(), "om", mutant)
+    caught = []
+    for name in pins:
+        fn = globals()[name]
+        try:
+            if name == "test_fovea_is_symmetric_about_a_centred_focal_point":
+                fn(1920, 1080)
+            else:
+                fn()
+        except AssertionError:
+            caught.append(name)
+    assert caught, f"no pin caught: {what}"
