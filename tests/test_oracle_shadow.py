@@ -295,3 +295,45 @@ def test_headlight_mode_unchanged_by_light_fields():
     b, _, _ = om.march(vol, tf, cam, MarchParams(0.5, 0.99, (0, 0, 0), 1, light_dir=(1.0, -2.0, 0.5),
                                                  shadow_rate=2))
     assert np.array_equal(a, b)
+
+
+# Plausible mistakes planted in a compiled copy of the oracle's source (the
+# oracle itself is not touched); each must break at least one pin above.
+SHADOW_MUTANTS = [
+    ("no partial last step", "if (e > 1.0) e = 1.0;", "e = 1.0;",
+     [lambda: test_homogeneous_shadow_closed_form(4, 0.5)]),
+    ("a shadow sample at the point itself", "for (int64_t j = 1; (double)j * ds < se; ++j) {",
+     "for (int64_t j = 0; (double)j * ds < se; ++j) {", [lambda: test_homogeneous_shadow_closed_form(4, 0.5)]),
+    ("exit face flipped", "double s = ((L[a] > 0.0 ? (double)v->n[a] : 0.0) - p[a]) / L[a];",
+     "double s = ((L[a] > 0.0 ? 0.0 : (double)v->n[a]) - p[a]) / L[a];",
+     [lambda: test_homogeneous_shadow_closed_form(4, 0.5), test_shadow_direction_sign_and_axis_lights]),
+    ("L + dir as the half vector", "double h[3] = {L[0] - d[0], L[1] - d[1], L[2] - d[2]};",
+     "double h[3] = {L[0] + d[0], L[1] + d[1], L[2] + d[2]};", [test_shadowed_phong_constant_gradient_closed_form]),
+    ("unshadowed specular term", "col[ch] = clamp01(col[ch] * (0.2 + 0.7 * T * ndl) + 0.3 * T * spec);",
+     "col[ch] = clamp01(col[ch] * (0.2 + 0.7 * T * ndl) + 0.3 * spec);",
+     [test_shadowed_phong_constant_gradient_closed_form]),
+    ("unshadowed flat-region term", "for (int ch = 0; ch < 3; ++ch) col[ch] = clamp01(col[ch] * (0.2 + 0.7 * T));",
+     "for (int ch = 0; ch < 3; ++ch) col[ch] = clamp01(col[ch] * (0.2 + 0.7));",
+     [test_shadowed_pixel_constant_medium_closed_form]),
+]
+
+
+@pytest.mark.parametrize("what,old,new,pins", SHADOW_MUTANTS, ids=[m[0] for m in SHADOW_MUTANTS])
+def test_planted_mistakes_fail_the_pins(what, old, new, pins, tmp_path, monkeypatch):
+    import subprocess
+    src = open(om._SRC).read()
+    assert src.count(old) == 1, what
+    c = tmp_path / "mutant.c"
+    c.write_text(src.replace(old, new))
+    so = tmp_path / "libmutant.so"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-ffp-contract=off", "-fPIC", "-shared", "-o", str(so),
+                           str(c), "-lm"])
+    monkeypatch.setattr(om, "_lib", None)
+    monkeypatch.setattr(om, "build", lambda force=False: str(so))
+    caught = 0
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            caught += 1
+    assert caught, f"no pin caught: {what}"
