@@ -183,6 +183,43 @@ __global__ void __launch_bounds__(kRowThreads) join_fwd_kernel(const float* __re
     }
 }
 
+// The join of the tensor-core pass in two steps: the coarse difference
+// y - pool(j) once per coarse pixel (the term join_detail recomputes for
+// each fine pixel it feeds), then x = j + sigmoid(z) up(d); one image, the
+// same expressions as join_fwd_kernel.
+__global__ void __launch_bounds__(kRowThreads) join_diff_kernel(const float* __restrict__ j,
+                                                                 const float* __restrict__ yv, int h, int w,
+                                                                 float* __restrict__ d) {
+    const int cx = blockIdx.x * kRowThreads + threadIdx.x, cy = blockIdx.y, c = blockIdx.z;
+    const int hc = h / 2, wc = w / 2;
+    if (cx >= wc) return;
+    const float* q = j + (long long)c * h * w + (long long)(2 * cy) * w + 2 * cx;
+    const long long o = ((long long)c * hc + cy) * wc + cx;
+    d[o] = __ldg(yv + o) - 0.25f * (__ldg(q) + __ldg(q + 1) + __ldg(q + w) + __ldg(q + w + 1));
+}
+
+__global__ void __launch_bounds__(kRowThreads) join_up_kernel(const float* __restrict__ j,
+                                                               const float* __restrict__ d,
+                                                               const float* __restrict__ z, int h, int w,
+                                                               float* __restrict__ xo) {
+    const int x = blockIdx.x * kRowThreads + threadIdx.x, y = blockIdx.y;
+    if (x >= w) return;
+    const int hc = h / 2, wc = w / 2;
+    const long long hw = (long long)h * w, p = (long long)y * w + x;
+    int y0, y1, x0, x1;
+    float ty, tx;
+    up_src(y, hc, y0, y1, ty);
+    up_src(x, wc, x0, x1, tx);
+    const float a = sigmoidf_(__ldg(z + p));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float* dc = d + (long long)c * hc * wc;
+        const float top = (1.f - tx) * __ldg(dc + (long long)y0 * wc + x0) + tx * __ldg(dc + (long long)y0 * wc + x1);
+        const float bot = (1.f - tx) * __ldg(dc + (long long)y1 * wc + x0) + tx * __ldg(dc + (long long)y1 * wc + x1);
+        xo[c * hw + p] = __ldg(j + c * hw + p) + a * ((1.f - ty) * top + ty * bot);
+    }
+}
+
 // dL/dY = up^T(sigmoid(z) gx) at every coarse pixel (the up-sampling's adjoint)
 __global__ void join_bwd_coarse_kernel(const float* __restrict__ z, const float* __restrict__ gx, int n, int h,
                                        int w, float* __restrict__ gy) {
@@ -511,6 +548,7 @@ struct TPlan {
     float *LE[FVN_WNET_MAX_LEVELS], *LD[FVN_WNET_MAX_LEVELS], *ZD[FVN_WNET_MAX_LEVELS];
     float *I[FVN_WNET_MAX_LEVELS + 1], *J[FVN_WNET_MAX_LEVELS], *X[FVN_WNET_MAX_LEVELS], *Y[FVN_WNET_MAX_LEVELS + 1];
     float* LB;
+    float* D[FVN_WNET_MAX_LEVELS + 1];               // coarse differences of the joins (3 planes at level s)
 };
 
 size_t plan_wnet_tc(const fvn_wnet_config& c, int Wp, int Hp, TPlan* pl, char* base) {
@@ -555,6 +593,7 @@ size_t plan_wnet_tc(const fvn_wnet_config& c, int Wp, int Hp, TPlan* pl, char* b
     pl->B = half(c.bot, L);
     pl->GB = half(c.bot, L);
     pl->LB = f32(kTaps, L);
+    for (int s = 1; s <= L; ++s) pl->D[s] = f32(3, s);
     return off;
 }
 
@@ -688,7 +727,12 @@ fvn_status wnet_forward_tc(fvn_ctx* ctx, const float* rgbam, int w, int h, float
     }
     WQ(fvn_filter3_fwd(B.I[L], B.LB, 1, hs(L), ws(L), B.Y[L], stream));
     for (int s = L - 1; s >= 0; --s) {
-        WQ(fvn_wnet_join_fwd(B.J[s], B.Y[s + 1], B.ZD[s], 1, hs(s), ws(s), B.X[s], stream));
+        join_diff_kernel<<<row_grid(ws(s + 1), hs(s + 1), 3), kRowThreads, 0, st>>>(B.J[s], B.Y[s + 1], hs(s), ws(s),
+                                                                                 B.D[s + 1]);
+        FVN_LAUNCH_CHECK(ctx);
+        join_up_kernel<<<row_grid(ws(s), hs(s), 1), kRowThreads, 0, st>>>(B.J[s], B.D[s + 1], B.ZD[s], hs(s), ws(s),
+                                                                          B.X[s]);
+        FVN_LAUNCH_CHECK(ctx);
         WQ(fvn_filter3_fwd(B.X[s], B.LD[s], 1, hs(s), ws(s), B.Y[s], stream));
     }
     window_copy_kernel<<<row_grid(w, h, 3), kRowThreads, 0, st>>>(B.Y[0], Wp, Hp, rgb, w, h, 3);
