@@ -470,3 +470,62 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
     for _, _, pin in plants:
         pin()
     assert on._neighbours is good_nb and on._up_axis_weights is good_upw
+
+
+def test_ssim_brute_force_windows():
+    """SSIM against an explicit loop over every valid 11 x 11 window with the
+    normalised 2-D Gaussian weights (sigma 1.5) and centred (co)variances,
+    per channel, then averaged (Wang et al. 2004)."""
+    rng = np.random.default_rng(31)
+    a = rng.uniform(size=(2, 14, 17))
+    b = np.clip(a + rng.normal(0, 0.1, a.shape), 0, 1)
+    x = np.arange(-5, 6)
+    g1 = np.exp(-0.5 * (x / 1.5) ** 2)
+    w2 = np.outer(g1, g1)
+    w2 /= w2.sum()
+    c1, c2 = 0.01 ** 2, 0.03 ** 2
+    vals = []
+    for ch in range(a.shape[0]):
+        s = []
+        for i in range(a.shape[1] - 10):
+            for j in range(a.shape[2] - 10):
+                pa, pb = a[ch, i:i + 11, j:j + 11], b[ch, i:i + 11, j:j + 11]
+                ma, mb = (w2 * pa).sum(), (w2 * pb).sum()
+                va, vb = (w2 * (pa - ma) ** 2).sum(), (w2 * (pb - mb) ** 2).sum()
+                cab = (w2 * (pa - ma) * (pb - mb)).sum()
+                s.append((2 * ma * mb + c1) * (2 * cab + c2) / ((ma ** 2 + mb ** 2 + c1) * (va + vb + c2)))
+        vals.append(np.mean(s))
+    assert abs(metrics.ssim(a, b) - np.mean(vals)) < 1e-12
+
+
+METRIC_MUTANTS = [
+    ("SSIM over the padded border", "return out[r:img.shape[0] - r, r:img.shape[1] - r]", "return out",
+     ["test_ssim_brute_force_windows"]),
+    ("covariance without the means", "sxy = _filter_valid(x * y, g) - mx * my", "sxy = _filter_valid(x * y, g)",
+     ["test_psnr_ssim_closed_forms", "test_ssim_brute_force_windows"]),
+    ("window not normalised", "return g / g.sum()", "return g", ["test_ssim_brute_force_windows"]),
+    ("PSNR with a peak of 255", "return float(-10.0 * np.log10(mse))\n\n\ndef _gauss_window",
+     "return float(20.0 * np.log10(255.0) - 10.0 * np.log10(mse))\n\n\ndef _gauss_window",
+     ["test_psnr_ssim_closed_forms"]),
+    ("tPSNR without the reference's change", "d = (c(o) - c(o_prev)) - (c(y) - c(y_prev))",
+     "d = c(o) - c(o_prev)", ["test_tpsnr_closed_form_and_device_metric"]),
+]
+
+
+@pytest.mark.parametrize("what,old,new,pins", METRIC_MUTANTS, ids=[m[0] for m in METRIC_MUTANTS])
+def test_planted_metric_mistakes_fail_the_pins(what, old, new, pins, monkeypatch):
+    """Each mistake, planted in a copy of the metrics oracle's source (the
+    oracle itself is not touched), breaks at least one pin above."""
+    import types
+    src = open(metrics.__file__).read()
+    assert src.count(old) == 1, what
+    mutant = types.ModuleType("metrics_mutant")
+    exec(compile(src.replace(old, new), "metrics_mutant", "exec"), mutant.__dict__)
+    monkeypatch.setitem(globals(), "metrics", mutant)
+    caught = []
+    for name in pins:
+        try:
+            globals()[name]()
+        except AssertionError:
+            caught.append(name)
+    assert caught, f"no pin caught: {what}"
