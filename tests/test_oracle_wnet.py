@@ -211,3 +211,35 @@ def test_flops_of_the_benchmark_roofline():
     filters = (1 + 1 / 4 + 1 / 16) * 2 + 1 / 64        # encoder and decoder filters per scale, the coarsest
     assert bench.wnet_flops_per_px(wl, W.PAPER) == pytest.approx(conv + filters * 54, rel=1e-12)
     assert 470e3 < conv < 480e3
+
+
+WNET_MUTANTS = [
+    ("filter taps in transposed order",
+     "    for dy in (-1, 0, 1):\n        for dx in (-1, 0, 1):\n            vals.append(",
+     "    for dx in (-1, 0, 1):\n        for dy in (-1, 0, 1):\n            vals.append(",
+     [lambda: test_filter_one_hot_logits_shift(1)]),
+    ("join blend inverted", "a = on.sigmoid(z)[:, None]", "a = on.sigmoid(-z)[:, None]",
+     [test_join_matches_torch_resampling]),
+    ("filter weights not normalised", "wq = e / e.sum(axis=1, keepdims=True)", "wq = e",
+     [test_filter_uniform_logits_is_a_normalised_box]),
+]
+
+
+@pytest.mark.parametrize("what,old,new,pins", WNET_MUTANTS, ids=[m[0] for m in WNET_MUTANTS])
+def test_planted_source_mistakes_fail_the_pins(what, old, new, pins, monkeypatch):
+    """Each mistake, planted in a copy of the two-stage oracle's source (the
+    oracle itself is not touched), breaks at least one pin above."""
+    import types
+    src = open(W.__file__).read()
+    assert src.count(old) == 1, what
+    mutant = types.ModuleType("oracle.wnet_mutant")
+    mutant.__package__ = "oracle"
+    exec(compile(src.replace(old, new), "wnet_mutant", "exec"), mutant.__dict__)
+    monkeypatch.setitem(globals(), "W", mutant)
+    caught = 0
+    for pin in pins:
+        try:
+            pin()
+        except AssertionError:
+            caught += 1
+    assert caught, f"no pin caught: {what}"
