@@ -529,3 +529,34 @@ def test_planted_metric_mistakes_fail_the_pins(what, old, new, pins, monkeypatch
         except AssertionError:
             caught.append(name)
     assert caught, f"no pin caught: {what}"
+
+
+NET_SOURCE_MUTANTS = [
+    ("history not clamped", "else np.clip(np.asarray(prev, np.float64), 0.0, 1.0)",
+     "else np.asarray(prev, np.float64)", ["test_recurrent_with_zero_history_weights_is_the_plain_network"]),
+    ("history before the sparse channels", "x = _pad4(np.concatenate([x_in, pv], axis=1))",
+     "x = _pad4(np.concatenate([pv, x_in], axis=1))", ["test_recurrent_history_enters_the_first_convolution_linearly"]),
+    ("temporal loss without the reference's change",
+     "d = (np.asarray(o, np.float64) - o_prev) - (np.asarray(y, np.float64) - y_prev)",
+     "d = np.asarray(o, np.float64) - o_prev", ["test_temporal_loss_closed_form_and_gradient"]),
+]
+
+
+@pytest.mark.parametrize("what,old,new,pins", NET_SOURCE_MUTANTS, ids=[m[0] for m in NET_SOURCE_MUTANTS])
+def test_planted_recurrent_mistakes_fail_the_pins(what, old, new, pins, monkeypatch):
+    """Each mistake, planted in a copy of the network oracle's source (the
+    oracle itself is not touched), breaks at least one pin above."""
+    import types
+    src = open(on.__file__).read()
+    assert src.count(old) == 1, what
+    mutant = types.ModuleType("oracle.net_mutant")
+    mutant.__package__ = "oracle"
+    exec(compile(src.replace(old, new), "net_mutant", "exec"), mutant.__dict__)
+    monkeypatch.setitem(globals(), "on", mutant)
+    caught = []
+    for name in pins:
+        try:
+            globals()[name]()
+        except AssertionError:
+            caught.append(name)
+    assert caught, f"no pin caught: {what}"
